@@ -1,0 +1,968 @@
+// Plain FP64 CPU oracle of the split-form DGSEM time derivative and its
+// low-storage Runge-Kutta loop (GALAEXI, Sec. 3.1, Eqs. 1-3).
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+// reference that the CUDA path is checked against.  Only the test suite, the
+// smoke entry and the benchmark's CPU-baseline leg may load it; the CUDA
+// library never links, includes or calls it, and it shares no code with it.
+//
+// Everything is nested loops in the order of the mathematics; the scalar type
+// is a template parameter so that the same code evaluates the tangent-linear
+// operator with forward-mode dual numbers.
+//
+// Readings where the paper is silent (each listed in the design notes):
+//  * p = (gamma-1) rho eps (the printed (1-gamma) is a sign typo, Sec. 3.1).
+//  * LGL collocation, strong split form; curl-form metric terms (Kopriva 2006).
+//  * Surface flux: local Lax-Friedrichs (or the two-point EC flux itself);
+//    viscous surface flux = arithmetic mean of both sides (BR1, Sec. 3.1).
+//  * BR1 lifting of (u, v, w, T) with the non-conservative strong volume part.
+//  * Two-point flux of Chandrashekar (2013) with the kinetic-energy term
+//    1/2 * mean of |u|^2 (the form that satisfies Tadmor's condition).
+//  * Logarithmic mean by the Ismail-Roe (2009) series/log split, with the
+//    switch at xi^2 < 1e-4 and four series terms (truncation < 1e-17).
+//  * Constant viscosity, Stokes hypothesis, lambda = mu c_p / Pr.
+//  * LSERK4-5 of Carpenter and Kennedy (1994), 2N storage.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+namespace orc {
+
+// ---------------------------------------------------------------------------
+// Forward-mode dual number (value, one tangent direction).
+struct Dual {
+  double v, d;
+  Dual() : v(0), d(0) {}
+  Dual(double a) : v(a), d(0) {}
+  Dual(double a, double b) : v(a), d(b) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) {
+  double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
+inline Dual& operator*=(Dual& a, Dual b) { a = a * b; return a; }
+inline Dual sqrt(Dual a) { double s = std::sqrt(a.v); return Dual(s, a.d / (2.0 * s)); }
+inline Dual log(Dual a) { return Dual(std::log(a.v), a.d / a.v); }
+inline Dual fabs(Dual a) { return a.v < 0 ? -a : a; }     // branch follows the value
+inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
+inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
+inline double val(Dual a) { return a.v; }
+inline double val(double a) { return a; }
+using std::sqrt; using std::log; using std::fabs;
+// max with ties going to the first argument (the value decides the branch)
+template <class T> inline T vmax(T a, T b) { return (val(b) > val(a)) ? b : a; }
+
+// ---------------------------------------------------------------------------
+// 1-D basis on Legendre-Gauss-Lobatto nodes (Sec. 3.1: collocation at LGL
+// nodes).  Nodes: +-1 and the roots of P'_N, found by Newton's method on
+// q = P_{N+1} - P_{N-1} (which is proportional to (1-x^2) P'_N).
+static void legendre_q(int N, double x, double& q, double& dq, double& LN) {
+  // Three-term recurrence for P_k and P'_k.
+  double Lm2 = 1.0, Lm1 = x, dLm2 = 0.0, dLm1 = 1.0;
+  double L = x, dL = 1.0;
+  std::vector<double> Ls(N + 2), dLs(N + 2);
+  Ls[0] = 1.0; dLs[0] = 0.0; Ls[1] = x; dLs[1] = 1.0;
+  for (int k = 2; k <= N + 1; ++k) {
+    L = ((2.0 * k - 1.0) * x * Lm1 - (k - 1.0) * Lm2) / k;
+    dL = dLm2 + (2.0 * k - 1.0) * Lm1;
+    Lm2 = Lm1; Lm1 = L; dLm2 = dLm1; dLm1 = dL;
+    Ls[k] = L; dLs[k] = dL;
+  }
+  q = Ls[N + 1] - Ls[N - 1];
+  dq = dLs[N + 1] - dLs[N - 1];
+  LN = Ls[N];
+}
+
+struct Basis {
+  int N, n;
+  std::vector<double> x, w, D;   // D[i*n + j] = l_j'(x_i)
+};
+
+static Basis make_basis(int N) {
+  Basis b; b.N = N; b.n = N + 1;
+  int n = N + 1;
+  b.x.assign(n, 0.0); b.w.assign(n, 0.0); b.D.assign(n * n, 0.0);
+  b.x[0] = -1.0; b.x[N] = 1.0;
+  for (int j = 1; j < N; ++j) {
+    double xj = -std::cos(M_PI * j / N);   // Chebyshev-Gauss-Lobatto start
+    for (int it = 0; it < 100; ++it) {
+      double q, dq, LN;
+      legendre_q(N, xj, q, dq, LN);
+      double dx = -q / dq;
+      xj += dx;
+      if (std::fabs(dx) <= 1e-16 * std::fabs(xj)) break;
+    }
+    b.x[j] = xj;
+  }
+  // exact symmetry about 0
+  for (int j = 0; j < n / 2; ++j) {
+    double m = 0.5 * (b.x[N - j] - b.x[j]);
+    b.x[j] = -m; b.x[N - j] = m;
+  }
+  if (N % 2 == 0) b.x[N / 2] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double q, dq, LN;
+    legendre_q(N, b.x[j], q, dq, LN);
+    b.w[j] = 2.0 / (N * (N + 1.0) * LN * LN);
+  }
+  // Differentiation matrix from barycentric weights; diagonal by the
+  // negative-sum rule so that D applied to a constant is exactly zero.
+  std::vector<double> lam(n, 1.0);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k)
+      if (k != j) lam[j] /= (b.x[j] - b.x[k]);
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double d = (lam[j] / lam[i]) / (b.x[i] - b.x[j]);
+      b.D[i * n + j] = d;
+      s += d;
+    }
+    b.D[i * n + i] = -s;
+  }
+  return b;
+}
+
+// Lagrange interpolation matrix from ngeo+1 equispaced points on [-1,1] to
+// the LGL nodes: V[i*(ngeo+1) + k] = l_k(x_i).
+static std::vector<double> equi_to_lgl(int ngeo, const Basis& b) {
+  int m = ngeo + 1;
+  std::vector<double> eta(m), V(b.n * m);
+  for (int k = 0; k < m; ++k) eta[k] = -1.0 + 2.0 * k / ngeo;
+  for (int i = 0; i < b.n; ++i)
+    for (int k = 0; k < m; ++k) {
+      double l = 1.0;
+      for (int j = 0; j < m; ++j)
+        if (j != k) l *= (b.x[i] - eta[j]) / (eta[k] - eta[j]);
+      V[i * m + k] = l;
+    }
+  return V;
+}
+
+// ---------------------------------------------------------------------------
+struct Params {
+  double gamma, R, Pr, mu;
+  int surf_flux;   // 0: local Lax-Friedrichs, 1: entropy-conservative two-point flux
+  int source;      // 0: none, 1: density-wave manufactured solution
+  double mms_amp;
+  int vol_flux;    // 0: Chandrashekar EC/KEP two-point flux; 1: arithmetic mean of
+                   //    the Euler flux (a test variant equal to the standard DGSEM)
+};
+
+struct Ctx {
+  int N, n, P, E;
+  Params prm;
+  Basis b;
+  std::vector<double> X;      // [e][c][P]
+  std::vector<double> Ja;     // [e][d][l][P]  contravariant metric J a^d, component l
+  std::vector<double> J;      // [e][P]
+  std::vector<int> nbr;       // [e][6][3]
+  std::vector<int> face_id;   // [e][6]
+  std::vector<int> master;    // [e][6] 1 if (e,f) is the master side
+  int nfaces;
+  std::vector<double> fn;     // [face][3][n*n]  unit normal of the master side
+  std::vector<double> fsJ;    // [face][n*n]     surface element of the master side
+  std::string err;
+};
+
+static inline int vidx(int n, int i, int j, int k) { return i + n * (j + n * k); }
+
+// Volume node of face node (p,q) of local face f = 2d + s.
+static inline int face_vol(int n, int f, int p, int q) {
+  int d = f / 2, s = f % 2, N = n - 1;
+  int e = s * N;
+  if (d == 0) return vidx(n, e, p, q);
+  if (d == 1) return vidx(n, p, e, q);
+  return vidx(n, p, q, e);
+}
+
+// Face-node map of the mesh format's orientation code.
+static inline void flip_map(int flip, int N, int p, int q, int& p2, int& q2) {
+  int a = (flip & 1) ? q : p;
+  int bq = (flip & 1) ? p : q;
+  p2 = (flip & 2) ? N - a : a;
+  q2 = (flip & 4) ? N - bq : bq;
+}
+
+// Derivative along reference direction d of a nodal field u[P] at node (i,j,k).
+static inline double dxi(const Ctx& c, const double* u, int d, int i, int j, int k) {
+  int n = c.n;
+  double s = 0.0;
+  for (int m = 0; m < n; ++m) {
+    int id = (d == 0) ? vidx(n, m, j, k) : (d == 1) ? vidx(n, i, m, k) : vidx(n, i, j, m);
+    int row = (d == 0) ? i : (d == 1) ? j : k;
+    s += c.b.D[row * n + m] * u[id];
+  }
+  return s;
+}
+
+// Geometry: node positions by interpolation of the equispaced samples, the
+// Jacobian determinant from the derivative of the interpolant, and the
+// contravariant metric terms in Kopriva's conservative curl form
+//   (J a^d)_nc = -e_d . curl_xi( X_l grad_xi X_m ),  (nc, m, l) cyclic,
+// which makes the discrete metric identities hold exactly (Sec. 3.1 mapping
+// chi and its Jacobian; free-stream preservation).
+static bool build_geometry(Ctx& c, int ngeo, const double* xgeo) {
+  int n = c.n, P = c.P, m = ngeo + 1, mP = m * m * m;
+  std::vector<double> V = equi_to_lgl(ngeo, c.b);
+  c.X.assign((size_t)c.E * 3 * P, 0.0);
+  c.Ja.assign((size_t)c.E * 9 * P, 0.0);
+  c.J.assign((size_t)c.E * P, 0.0);
+  std::vector<double> dX(9 * P), v(3 * P);
+  for (int e = 0; e < c.E; ++e) {
+    for (int cc = 0; cc < 3; ++cc) {
+      const double* g = xgeo + ((size_t)e * 3 + cc) * mP;
+      double* Xo = &c.X[((size_t)e * 3 + cc) * P];
+      for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j)
+          for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int c3 = 0; c3 < m; ++c3)
+              for (int b3 = 0; b3 < m; ++b3)
+                for (int a3 = 0; a3 < m; ++a3)
+                  s += V[i * m + a3] * V[j * m + b3] * V[k * m + c3] * g[a3 + m * (b3 + m * c3)];
+            Xo[vidx(n, i, j, k)] = s;
+          }
+    }
+    const double* Xe = &c.X[(size_t)e * 3 * P];
+    // dX[cc][d] = d X_cc / d xi_d
+    for (int cc = 0; cc < 3; ++cc)
+      for (int d = 0; d < 3; ++d)
+        for (int k = 0; k < n; ++k)
+          for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i)
+              dX[(cc * 3 + d) * P + vidx(n, i, j, k)] = dxi(c, Xe + cc * P, d, i, j, k);
+    for (int id = 0; id < P; ++id) {
+      double a[3][3];
+      for (int cc = 0; cc < 3; ++cc)
+        for (int d = 0; d < 3; ++d) a[cc][d] = dX[(cc * 3 + d) * P + id];
+      double det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1])
+                 - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0])
+                 + a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+      c.J[(size_t)e * P + id] = det;
+      if (!(det > 0.0)) { c.err = "non-positive Jacobian"; return false; }
+    }
+    for (int nc = 0; nc < 3; ++nc) {
+      int mm = (nc + 1) % 3, ll = (nc + 2) % 3;
+      // v_r = X_l * d X_m / d xi_r
+      for (int r = 0; r < 3; ++r)
+        for (int id = 0; id < P; ++id)
+          v[r * P + id] = Xe[ll * P + id] * dX[(mm * 3 + r) * P + id];
+      for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j)
+          for (int i = 0; i < n; ++i) {
+            int id = vidx(n, i, j, k);
+            double c0 = dxi(c, &v[2 * P], 1, i, j, k) - dxi(c, &v[1 * P], 2, i, j, k);
+            double c1 = dxi(c, &v[0 * P], 2, i, j, k) - dxi(c, &v[2 * P], 0, i, j, k);
+            double c2 = dxi(c, &v[1 * P], 0, i, j, k) - dxi(c, &v[0 * P], 1, i, j, k);
+            c.Ja[(((size_t)e * 3 + 0) * 3 + nc) * P + id] = -c0;
+            c.Ja[(((size_t)e * 3 + 1) * 3 + nc) * P + id] = -c1;
+            c.Ja[(((size_t)e * 3 + 2) * 3 + nc) * P + id] = -c2;
+          }
+    }
+  }
+  return true;
+}
+
+static bool build_faces(Ctx& c, const int* face_nbr) {
+  int E = c.E, n = c.n, nn = n * n;
+  c.nbr.assign(face_nbr, face_nbr + (size_t)E * 18);
+  c.face_id.assign(E * 6, -1);
+  c.master.assign(E * 6, 0);
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1];
+      int fl = c.nbr[(e * 6 + f) * 3 + 2];
+      if (e2 < 0 || e2 >= E || f2 < 0 || f2 > 5 || fl < 0 || fl > 7) { c.err = "connectivity out of range"; return false; }
+      if (c.nbr[(e2 * 6 + f2) * 3 + 0] != e || c.nbr[(e2 * 6 + f2) * 3 + 1] != f) { c.err = "connectivity not reciprocal"; return false; }
+    }
+  int nf = 0;
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1];
+      if (e * 6 + f < e2 * 6 + f2) { c.master[e * 6 + f] = 1; c.face_id[e * 6 + f] = nf++; }
+    }
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f)
+      if (!c.master[e * 6 + f]) {
+        int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1];
+        c.face_id[e * 6 + f] = c.face_id[e2 * 6 + f2];
+      }
+  c.nfaces = nf;
+  c.fn.assign((size_t)nf * 3 * nn, 0.0);
+  c.fsJ.assign((size_t)nf * nn, 0.0);
+  // Face geometry of the master side: n sJ = (2s-1) J a^d at the face node.
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      if (!c.master[e * 6 + f]) continue;
+      int d = f / 2, s = f % 2, id = c.face_id[e * 6 + f];
+      for (int q = 0; q < n; ++q)
+        for (int p = 0; p < n; ++p) {
+          int node = face_vol(n, f, p, q);
+          double nv[3], s2 = 0.0;
+          for (int l = 0; l < 3; ++l) {
+            nv[l] = (2.0 * s - 1.0) * c.Ja[(((size_t)e * 3 + d) * 3 + l) * c.P + node];
+            s2 += nv[l] * nv[l];
+          }
+          double sJ = std::sqrt(s2);
+          for (int l = 0; l < 3; ++l) c.fn[((size_t)id * 3 + l) * nn + p + n * q] = nv[l] / sJ;
+          c.fsJ[(size_t)id * nn + p + n * q] = sJ;
+        }
+    }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Physics (Sec. 3.1, Eq. 1).
+template <class T> struct Prim { T rho, u[3], p, T_; };
+
+template <class T>
+static inline Prim<T> cons2prim(const Params& pr, const T q[5]) {
+  Prim<T> w;
+  w.rho = q[0];
+  for (int a = 0; a < 3; ++a) w.u[a] = q[1 + a] / q[0];
+  T ke = 0.5 * (q[1] * w.u[0] + q[2] * w.u[1] + q[3] * w.u[2]);
+  w.p = (pr.gamma - 1.0) * (q[4] - ke);
+  w.T_ = w.p / (q[0] * pr.R);
+  return w;
+}
+
+template <class T>
+static inline void prim2cons(const Params& pr, const Prim<T>& w, T q[5]) {
+  q[0] = w.rho;
+  for (int a = 0; a < 3; ++a) q[1 + a] = w.rho * w.u[a];
+  q[4] = w.p / (pr.gamma - 1.0) + 0.5 * w.rho * (w.u[0] * w.u[0] + w.u[1] * w.u[1] + w.u[2] * w.u[2]);
+}
+
+// Inviscid flux in the direction of the (not necessarily unit) vector nv.
+template <class T>
+static inline void euler_flux(const T q[5], const Prim<T>& w, const T nv[3], T out[5]) {
+  T un = w.u[0] * nv[0] + w.u[1] * nv[1] + w.u[2] * nv[2];
+  out[0] = q[0] * un;
+  for (int a = 0; a < 3; ++a) out[1 + a] = q[1 + a] * un + w.p * nv[a];
+  out[4] = (q[4] + w.p) * un;
+}
+
+// Viscous flux (stress + Fourier heat flux) in direction nv, from the lifted
+// gradients g[phi*3 + l] = d phi / d x_l, phi in (u, v, w, T).
+template <class T>
+static inline void visc_flux(const Params& pr, const Prim<T>& w, const T* g, const T& mu,
+                             const T nv[3], T out[5]) {
+  T div = g[0 * 3 + 0] + g[1 * 3 + 1] + g[2 * 3 + 2];
+  T tau[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int bb = 0; bb < 3; ++bb) {
+      tau[a][bb] = mu * (g[a * 3 + bb] + g[bb * 3 + a]);
+      if (a == bb) tau[a][bb] = tau[a][bb] - (2.0 / 3.0) * mu * div;
+    }
+  double cp = pr.gamma * pr.R / (pr.gamma - 1.0);
+  T lam = mu * (cp / pr.Pr);
+  out[0] = T(0.0);
+  for (int bb = 0; bb < 3; ++bb) {
+    T s = T(0.0);
+    for (int l = 0; l < 3; ++l) s += nv[l] * tau[l][bb];
+    out[1 + bb] = s;
+  }
+  T e = T(0.0);
+  for (int l = 0; l < 3; ++l) {
+    T tu = tau[l][0] * w.u[0] + tau[l][1] * w.u[1] + tau[l][2] * w.u[2];
+    e += nv[l] * (tu + lam * g[3 * 3 + l]);
+  }
+  out[4] = e;
+}
+
+// Logarithmic mean (a - b) / (ln a - ln b), Ismail & Roe (2009): with
+// zeta = a/b, f = (zeta - 1)/(zeta + 1), u = f^2, the mean is (a + b)/(2 F)
+// where F = ln(zeta)/(2 f) = 1 + u/3 + u^2/5 + u^3/7 + ...
+template <class T>
+static inline T log_mean(T a, T b) {
+  T zeta = a / b;
+  T f = (zeta - 1.0) / (zeta + 1.0);
+  T u = f * f;
+  T F;
+  if (val(u) < 1e-4) F = 1.0 + u / 3.0 + u * u / 5.0 + u * u * u / 7.0;
+  else F = log(zeta) / (2.0 * f);
+  return (a + b) / (2.0 * F);
+}
+
+// Entropy-conserving, kinetic-energy-preserving two-point flux of
+// Chandrashekar (2013) in direction nv (Sec. 3.1, entropy-stable DGSEM).
+template <class T>
+static inline void ec_flux(const Params& pr, const Prim<T>& L, const Prim<T>& Rr,
+                           const T nv[3], T out[5]) {
+  T bL = L.rho / (2.0 * L.p), bR = Rr.rho / (2.0 * Rr.p);
+  T rho_ln = log_mean(L.rho, Rr.rho);
+  T beta_ln = log_mean(bL, bR);
+  T rho_av = 0.5 * (L.rho + Rr.rho);
+  T beta_av = 0.5 * (bL + bR);
+  T u_av[3];
+  for (int a = 0; a < 3; ++a) u_av[a] = 0.5 * (L.u[a] + Rr.u[a]);
+  T p_hat = rho_av / (2.0 * beta_av);
+  T u2L = L.u[0] * L.u[0] + L.u[1] * L.u[1] + L.u[2] * L.u[2];
+  T u2R = Rr.u[0] * Rr.u[0] + Rr.u[1] * Rr.u[1] + Rr.u[2] * Rr.u[2];
+  T u2_av = 0.5 * (u2L + u2R);
+  T un = u_av[0] * nv[0] + u_av[1] * nv[1] + u_av[2] * nv[2];
+  T f_rho = rho_ln * un;
+  out[0] = f_rho;
+  for (int a = 0; a < 3; ++a) out[1 + a] = f_rho * u_av[a] + p_hat * nv[a];
+  out[4] = f_rho * (1.0 / (2.0 * (pr.gamma - 1.0) * beta_ln) - 0.5 * u2_av)
+         + u_av[0] * out[1] + u_av[1] * out[2] + u_av[2] * out[3];
+}
+
+// Local Lax-Friedrichs flux in unit direction nv.
+template <class T>
+static inline void llf_flux(const Params& pr, const T qL[5], const Prim<T>& L,
+                            const T qR[5], const Prim<T>& Rr, const T nv[3], T out[5]) {
+  T fL[5], fR[5];
+  euler_flux(qL, L, nv, fL);
+  euler_flux(qR, Rr, nv, fR);
+  T cL = sqrt(pr.gamma * L.p / L.rho), cR = sqrt(pr.gamma * Rr.p / Rr.rho);
+  T unL = L.u[0] * nv[0] + L.u[1] * nv[1] + L.u[2] * nv[2];
+  T unR = Rr.u[0] * nv[0] + Rr.u[1] * nv[1] + Rr.u[2] * nv[2];
+  T lmax = vmax(fabs(unL) + cL, fabs(unR) + cR);
+  for (int v = 0; v < 5; ++v) out[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lmax * (qR[v] - qL[v]);
+}
+
+// Density-wave manufactured solution rho = 2 + A sin(pi (x+y+z-t)), u = (1,1,1),
+// p = 1; its residual q_t + div F(q) worked out by hand:
+//   r' = pi A cos(phi);  mass, momenta: 2 r';  energy: 3 r' - lambda Lap(T),
+//   Lap(T) = 3 [pi^2 A sin(phi) / (R rho^2) + 2 r'^2 / (R rho^3)],  T = 1/(R rho).
+static void mms_source(const Params& pr, const double x[3], double t, double out[5]) {
+  double A = pr.mms_amp;
+  double phi = M_PI * (x[0] + x[1] + x[2] - t);
+  double rho = 2.0 + A * std::sin(phi);
+  double rp = M_PI * A * std::cos(phi);
+  double cp = pr.gamma * pr.R / (pr.gamma - 1.0);
+  double lam = pr.mu * cp / pr.Pr;
+  double lapT = 3.0 * (M_PI * M_PI * A * std::sin(phi) / (pr.R * rho * rho) + 2.0 * rp * rp / (pr.R * rho * rho * rho));
+  out[0] = 2.0 * rp; out[1] = 2.0 * rp; out[2] = 2.0 * rp; out[3] = 2.0 * rp;
+  out[4] = 3.0 * rp - lam * lapT;
+}
+
+// BR1 lifting (Sec. 3.1, Eq. 3) in strong form for the primitive scalars
+// phi = (u, v, w, T) of every element:
+//   g_l = (1/J) [ sum_d Ja^d_l (D_d phi) + sum_faces (phi* - phi) (n_l sJ) / w_end ],
+// phi* = 1/2 (phi + phi_neighbour), n sJ the element's own outward normal.
+template <class T>
+static void lifting(const Ctx& c, const T* phi, T* G) {
+  int n = c.n, P = c.P, E = c.E, N = c.N;
+  const std::vector<double>& D = c.b.D;
+  double wend = c.b.w[0];
+  for (int e = 0; e < E; ++e) {
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          int id = vidx(n, i, j, k);
+          int ijk[3] = {i, j, k};
+          for (int ph = 0; ph < 4; ++ph) {
+            const T* f = &phi[((size_t)e * 4 + ph) * P];
+            T dd[3];
+            for (int d = 0; d < 3; ++d) {
+              T s = T(0.0);
+              for (int m = 0; m < n; ++m) {
+                int mid = (d == 0) ? vidx(n, m, j, k) : (d == 1) ? vidx(n, i, m, k) : vidx(n, i, j, m);
+                s += D[ijk[d] * n + m] * f[mid];
+              }
+              dd[d] = s;
+            }
+            for (int l = 0; l < 3; ++l) {
+              T s = T(0.0);
+              for (int d = 0; d < 3; ++d) s += c.Ja[(((size_t)e * 3 + d) * 3 + l) * P + id] * dd[d];
+              G[((size_t)e * 12 + ph * 3 + l) * P + id] = s;
+            }
+          }
+        }
+    // surface part
+    for (int f = 0; f < 6; ++f) {
+      int d = f / 2, s = f % 2;
+      int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1], fl = c.nbr[(e * 6 + f) * 3 + 2];
+      for (int q = 0; q < n; ++q)
+        for (int p = 0; p < n; ++p) {
+          int id = face_vol(n, f, p, q);
+          int p2, q2;
+          flip_map(fl, N, p, q, p2, q2);
+          int id2 = face_vol(n, f2, p2, q2);
+          for (int ph = 0; ph < 4; ++ph) {
+            T mine = phi[((size_t)e * 4 + ph) * P + id];
+            T other = phi[((size_t)e2 * 4 + ph) * P + id2];
+            T star = 0.5 * (mine + other);
+            for (int l = 0; l < 3; ++l) {
+              double nsJ = (2.0 * s - 1.0) * c.Ja[(((size_t)e * 3 + d) * 3 + l) * P + id];
+              G[((size_t)e * 12 + ph * 3 + l) * P + id] += (star - mine) * (nsJ / wend);
+            }
+          }
+        }
+    }
+    for (int r = 0; r < 12; ++r)
+      for (int id = 0; id < P; ++id)
+        G[((size_t)e * 12 + r) * P + id] = G[((size_t)e * 12 + r) * P + id] / c.J[(size_t)e * P + id];
+  }
+}
+
+// Split-form advective volume term of element e (Sec. 3.1, entropy-stable
+// DGSEM):  acc_i += sum_d sum_m 2 D_{i m} F#_d(q_i, q_m),
+// F#_d evaluated with the averaged metric 1/2 (Ja^d_i + Ja^d_m).
+template <class T>
+static void volume_advective(const Ctx& c, int e, const Prim<T>* W, T* acc) {
+  const Params& pr = c.prm;
+  int n = c.n, P = c.P;
+  const std::vector<double>& D = c.b.D;
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        int id = vidx(n, i, j, k);
+        int ijk[3] = {i, j, k};
+        for (int d = 0; d < 3; ++d)
+          for (int m = 0; m < n; ++m) {
+            int mid = (d == 0) ? vidx(n, m, j, k) : (d == 1) ? vidx(n, i, m, k) : vidx(n, i, j, m);
+            double Dim = D[ijk[d] * n + m];
+            T nv[3];
+            for (int l = 0; l < 3; ++l) {
+              double ji = c.Ja[(((size_t)e * 3 + d) * 3 + l) * P + id];
+              double jm = c.Ja[(((size_t)e * 3 + d) * 3 + l) * P + mid];
+              nv[l] = T(0.5 * (ji + jm));
+            }
+            T fs[5];
+            if (pr.vol_flux == 0) {
+              ec_flux(pr, W[id], W[mid], nv, fs);
+            } else {
+              T qa[5], qb[5], fa[5], fb[5];
+              prim2cons(pr, W[id], qa); prim2cons(pr, W[mid], qb);
+              euler_flux(qa, W[id], nv, fa); euler_flux(qb, W[mid], nv, fb);
+              for (int v = 0; v < 5; ++v) fs[v] = 0.5 * (fa[v] + fb[v]);
+            }
+            for (int v = 0; v < 5; ++v) acc[(size_t)v * P + id] += 2.0 * Dim * fs[v];
+          }
+      }
+}
+
+// Viscous volume term of element e:  acc_i -= sum_d sum_m D_{i m} (f_v . Ja^d)_m.
+template <class T>
+static void volume_viscous(const Ctx& c, int e, const Prim<T>* W, const T* G, T mu, T* acc) {
+  const Params& pr = c.prm;
+  int n = c.n, P = c.P;
+  const std::vector<double>& D = c.b.D;
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        int id = vidx(n, i, j, k);
+        int ijk[3] = {i, j, k};
+        for (int d = 0; d < 3; ++d)
+          for (int m = 0; m < n; ++m) {
+            int mid = (d == 0) ? vidx(n, m, j, k) : (d == 1) ? vidx(n, i, m, k) : vidx(n, i, j, m);
+            double Dim = D[ijk[d] * n + m];
+            T nvm[3], gm[12], fv[5];
+            for (int l = 0; l < 3; ++l) nvm[l] = T(c.Ja[(((size_t)e * 3 + d) * 3 + l) * P + mid]);
+            for (int r = 0; r < 12; ++r) gm[r] = G[(size_t)r * P + mid];
+            visc_flux(pr, W[mid], gm, mu, nvm, fv);
+            for (int v = 0; v < 5; ++v) acc[(size_t)v * P + id] -= Dim * fv[v];
+          }
+      }
+}
+
+// ---------------------------------------------------------------------------
+// U_t = R(U): BR1 lifting, face fluxes, split-form volume integral, surface
+// integral and Jacobian scaling (Sec. 3.1, Eqs. 2-3), in strong form:
+//   g_l = (1/J) [ sum_d Ja^d_l d_d phi + sum_faces (phi* - phi) (n_l sJ) / w_end ]
+//   V   = sum_d [ sum_m 2 D_im F#_d(q_i, q_m) - sum_m D_im (f_v . Ja^d)_m ]
+//   S   = sum_faces [ F*_out - (f - f_v)(q_i, g_i) . (n sJ) ] / w_end
+//   U_t = -(V + S) / J + Q
+template <class T>
+static void rhs(const Ctx& c, const T* U, T* Ut, double t, T mu) {
+  const Params& pr = c.prm;
+  int n = c.n, P = c.P, E = c.E, N = c.N, nn = n * n;
+  const std::vector<double>& D = c.b.D;
+  double wend = c.b.w[0];
+  std::vector<Prim<T>> W((size_t)E * P);
+  std::vector<T> phi((size_t)E * 4 * P);       // [e][4][P]: u, v, w, T
+  for (int e = 0; e < E; ++e)
+    for (int id = 0; id < P; ++id) {
+      T q[5];
+      for (int v = 0; v < 5; ++v) q[v] = U[((size_t)e * 5 + v) * P + id];
+      Prim<T> w = cons2prim(pr, q);
+      W[(size_t)e * P + id] = w;
+      phi[((size_t)e * 4 + 0) * P + id] = w.u[0];
+      phi[((size_t)e * 4 + 1) * P + id] = w.u[1];
+      phi[((size_t)e * 4 + 2) * P + id] = w.u[2];
+      phi[((size_t)e * 4 + 3) * P + id] = w.T_;
+    }
+  // --- BR1 lifting
+  std::vector<T> G((size_t)E * 12 * P);        // [e][phi*3+l][P]
+  lifting(c, phi.data(), G.data());
+  auto grad_at = [&](int e, int id, T g[12]) {
+    for (int r = 0; r < 12; ++r) g[r] = G[((size_t)e * 12 + r) * P + id];
+  };
+  auto q_at = [&](int e, int id, T q[5]) {
+    for (int v = 0; v < 5; ++v) q[v] = U[((size_t)e * 5 + v) * P + id];
+  };
+  // --- face fluxes on master faces: F* = (F_adv - F_visc) sJ, master orientation
+  std::vector<T> Fs((size_t)c.nfaces * 5 * nn);
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      if (!c.master[e * 6 + f]) continue;
+      int fid = c.face_id[e * 6 + f];
+      int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1], fl = c.nbr[(e * 6 + f) * 3 + 2];
+      for (int q = 0; q < n; ++q)
+        for (int p = 0; p < n; ++p) {
+          int id = face_vol(n, f, p, q);
+          int p2, q2;
+          flip_map(fl, N, p, q, p2, q2);
+          int id2 = face_vol(n, f2, p2, q2);
+          T qL[5], qR[5], gL[12], gR[12];
+          q_at(e, id, qL); q_at(e2, id2, qR);
+          grad_at(e, id, gL); grad_at(e2, id2, gR);
+          const Prim<T>& L = W[(size_t)e * P + id];
+          const Prim<T>& Rr = W[(size_t)e2 * P + id2];
+          T nv[3];
+          for (int l = 0; l < 3; ++l) nv[l] = T(c.fn[((size_t)fid * 3 + l) * nn + p + n * q]);
+          double sJ = c.fsJ[(size_t)fid * nn + p + n * q];
+          T fa[5], fvL[5], fvR[5];
+          if (pr.surf_flux == 1) ec_flux(pr, L, Rr, nv, fa);
+          else llf_flux(pr, qL, L, qR, Rr, nv, fa);
+          visc_flux(pr, L, gL, mu, nv, fvL);
+          visc_flux(pr, Rr, gR, mu, nv, fvR);
+          for (int v = 0; v < 5; ++v)
+            Fs[((size_t)fid * 5 + v) * nn + p + n * q] = (fa[v] - 0.5 * (fvL[v] + fvR[v])) * sJ;
+        }
+    }
+  // --- volume integral, surface integral, Jacobian
+  for (int e = 0; e < E; ++e) {
+    std::vector<T> acc((size_t)5 * P, T(0.0));
+    volume_advective(c, e, &W[(size_t)e * P], acc.data());
+    volume_viscous(c, e, &W[(size_t)e * P], &G[(size_t)e * 12 * P], mu, acc.data());
+    // surface integral
+    for (int f = 0; f < 6; ++f) {
+      int d = f / 2, s = f % 2;
+      int fid = c.face_id[e * 6 + f];
+      int ism = c.master[e * 6 + f];
+      int fl = c.nbr[(e * 6 + f) * 3 + 2];
+      for (int q = 0; q < n; ++q)
+        for (int p = 0; p < n; ++p) {
+          int id = face_vol(n, f, p, q);
+          T Fout[5];
+          if (ism) {
+            for (int v = 0; v < 5; ++v) Fout[v] = Fs[((size_t)fid * 5 + v) * nn + p + n * q];
+          } else {
+            int p2, q2;
+            flip_map(fl, N, p, q, p2, q2);
+            for (int v = 0; v < 5; ++v) Fout[v] = -Fs[((size_t)fid * 5 + v) * nn + p2 + n * q2];
+          }
+          T nsJ[3];
+          for (int l = 0; l < 3; ++l) nsJ[l] = T((2.0 * s - 1.0) * c.Ja[(((size_t)e * 3 + d) * 3 + l) * P + id]);
+          T qi[5], gi[12], fa[5], fv[5];
+          q_at(e, id, qi);
+          grad_at(e, id, gi);
+          euler_flux(qi, W[(size_t)e * P + id], nsJ, fa);
+          visc_flux(pr, W[(size_t)e * P + id], gi, mu, nsJ, fv);
+          for (int v = 0; v < 5; ++v)
+            acc[(size_t)v * P + id] += (Fout[v] - (fa[v] - fv[v])) / wend;
+        }
+    }
+    for (int id = 0; id < P; ++id) {
+      double Qs[5] = {0, 0, 0, 0, 0};
+      if (pr.source == 1) {
+        double x[3] = {c.X[((size_t)e * 3 + 0) * P + id], c.X[((size_t)e * 3 + 1) * P + id], c.X[((size_t)e * 3 + 2) * P + id]};
+        mms_source(pr, x, t, Qs);
+      }
+      for (int v = 0; v < 5; ++v)
+        Ut[((size_t)e * 5 + v) * P + id] = -acc[(size_t)v * P + id] / c.J[(size_t)e * P + id] + Qs[v];
+    }
+  }
+}
+
+// LSERK4-5 of Carpenter & Kennedy (1994), 2N storage (Sec. 3.1, RK4-5).
+static const double RK_A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+static const double RK_B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                               2277821191437.0 / 14882151754819.0};
+static const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                               2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+
+template <class T>
+static void rk_steps(const Ctx& c, T* U, double t, double dt, int nsteps, T mu) {
+  size_t len = (size_t)c.E * 5 * c.P;
+  std::vector<T> G(len), Ut(len);
+  for (int st = 0; st < nsteps; ++st) {
+    for (size_t a = 0; a < len; ++a) G[a] = T(0.0);
+    for (int s = 0; s < 5; ++s) {
+      rhs(c, U, Ut.data(), t + RK_C[s] * dt, mu);
+      for (size_t a = 0; a < len; ++a) {
+        G[a] = RK_A[s] * G[a] + dt * Ut[a];
+        U[a] = U[a] + RK_B[s] * G[a];
+      }
+    }
+    t += dt;
+  }
+}
+
+}  // namespace orc
+
+using namespace orc;
+
+extern "C" {
+
+// Create an oracle context.  prm = {gamma, R, Pr, mu, mms_amp}; returns NULL
+// and fills errbuf on a bad mesh.
+void* orc_create(int N, int n_elems, int ngeo, const double* xgeo, const int* face_nbr,
+                 const double* prm, int surf_flux, int source, char* errbuf, int errlen) {
+  Ctx* c = new Ctx();
+  c->N = N; c->n = N + 1; c->P = c->n * c->n * c->n; c->E = n_elems;
+  c->prm.gamma = prm[0]; c->prm.R = prm[1]; c->prm.Pr = prm[2]; c->prm.mu = prm[3];
+  c->prm.mms_amp = prm[4];
+  c->prm.surf_flux = surf_flux; c->prm.source = source; c->prm.vol_flux = 0;
+  c->b = make_basis(N);
+  if (!build_geometry(*c, ngeo, xgeo) || !build_faces(*c, face_nbr)) {
+    if (errbuf && errlen > 0) std::snprintf(errbuf, errlen, "%s", c->err.c_str());
+    delete c;
+    return nullptr;
+  }
+  return c;
+}
+
+void orc_destroy(void* h) { delete (Ctx*)h; }
+
+// Test hook: select the volume two-point flux (0: Chandrashekar, 1: central).
+void orc_set_vol_flux(void* h, int kind) { ((Ctx*)h)->prm.vol_flux = kind; }
+
+// Lifted gradients G [E][12][P] (row phi*3 + l = d phi / d x_l).
+void orc_lifting(void* h, const double* U, double* G) {
+  Ctx* c = (Ctx*)h;
+  int P = c->P;
+  std::vector<double> phi((size_t)c->E * 4 * P);
+  for (int e = 0; e < c->E; ++e)
+    for (int id = 0; id < P; ++id) {
+      double q[5];
+      for (int v = 0; v < 5; ++v) q[v] = U[((size_t)e * 5 + v) * P + id];
+      Prim<double> w = cons2prim(c->prm, q);
+      for (int a = 0; a < 3; ++a) phi[((size_t)e * 4 + a) * P + id] = w.u[a];
+      phi[((size_t)e * 4 + 3) * P + id] = w.T_;
+    }
+  lifting(*c, phi.data(), G);
+}
+
+// Advective split-form volume term only: out [E][5][P] = V (before -1/J).
+void orc_volume_term(void* h, const double* U, double* out) {
+  Ctx* c = (Ctx*)h;
+  int P = c->P;
+  std::vector<Prim<double>> W((size_t)P);
+  for (int e = 0; e < c->E; ++e) {
+    for (int id = 0; id < P; ++id) {
+      double q[5];
+      for (int v = 0; v < 5; ++v) q[v] = U[((size_t)e * 5 + v) * P + id];
+      W[id] = cons2prim(c->prm, q);
+    }
+    std::fill(out + (size_t)e * 5 * P, out + (size_t)(e + 1) * 5 * P, 0.0);
+    volume_advective(*c, e, W.data(), out + (size_t)e * 5 * P);
+  }
+}
+
+int orc_nfaces(void* h) { return ((Ctx*)h)->nfaces; }
+
+void orc_basis(int N, double* x, double* w, double* D) {
+  Basis b = make_basis(N);
+  std::memcpy(x, b.x.data(), sizeof(double) * b.n);
+  std::memcpy(w, b.w.data(), sizeof(double) * b.n);
+  std::memcpy(D, b.D.data(), sizeof(double) * b.n * b.n);
+}
+
+// Geometry outputs: X [E][3][P], Ja [E][3][3][P], J [E][P].
+void orc_geometry(void* h, double* X, double* Ja, double* J) {
+  Ctx* c = (Ctx*)h;
+  if (X) std::memcpy(X, c->X.data(), sizeof(double) * c->X.size());
+  if (Ja) std::memcpy(Ja, c->Ja.data(), sizeof(double) * c->Ja.size());
+  if (J) std::memcpy(J, c->J.data(), sizeof(double) * c->J.size());
+}
+
+void orc_time_derivative(void* h, const double* U, double* Ut, double t) {
+  Ctx* c = (Ctx*)h;
+  rhs<double>(*c, U, Ut, t, c->prm.mu);
+}
+
+// Tangent-linear: Ut = R(U) and dUt = dR/dU . dU + dR/dmu . dmu.
+void orc_time_derivative_tl(void* h, const double* U, const double* dU, double dmu,
+                            double* Ut, double* dUt, double t) {
+  Ctx* c = (Ctx*)h;
+  size_t len = (size_t)c->E * 5 * c->P;
+  std::vector<Dual> Ud(len), Utd(len);
+  for (size_t a = 0; a < len; ++a) Ud[a] = Dual(U[a], dU ? dU[a] : 0.0);
+  rhs<Dual>(*c, Ud.data(), Utd.data(), t, Dual(c->prm.mu, dmu));
+  for (size_t a = 0; a < len; ++a) { if (Ut) Ut[a] = Utd[a].v; if (dUt) dUt[a] = Utd[a].d; }
+}
+
+void orc_rk_steps(void* h, double* U, double t, double dt, int nsteps) {
+  Ctx* c = (Ctx*)h;
+  rk_steps<double>(*c, U, t, dt, nsteps, c->prm.mu);
+}
+
+// Tangent-linear of nsteps LSERK steps: U and dU advanced together.
+void orc_rk_steps_tl(void* h, double* U, double* dU, double dmu, double t, double dt, int nsteps) {
+  Ctx* c = (Ctx*)h;
+  size_t len = (size_t)c->E * 5 * c->P;
+  std::vector<Dual> Ud(len);
+  for (size_t a = 0; a < len; ++a) Ud[a] = Dual(U[a], dU[a]);
+  rk_steps<Dual>(*c, Ud.data(), t, dt, nsteps, Dual(c->prm.mu, dmu));
+  for (size_t a = 0; a < len; ++a) { U[a] = Ud[a].v; dU[a] = Ud[a].d; }
+}
+
+void orc_rk_coeffs(double* A, double* B, double* C) {
+  std::memcpy(A, RK_A, sizeof(RK_A)); std::memcpy(B, RK_B, sizeof(RK_B)); std::memcpy(C, RK_C, sizeof(RK_C));
+}
+
+// Two-point flux, LLF flux and log mean exposed for the pin tests.
+void orc_ec_flux(const double* prm, const double* qL, const double* qR, const double* nv, double* out) {
+  Params pr{prm[0], prm[1], prm[2], prm[3], 0, 0, 0.0, 0};
+  Prim<double> L = cons2prim(pr, qL), Rr = cons2prim(pr, qR);
+  ec_flux(pr, L, Rr, nv, out);
+}
+void orc_llf_flux(const double* prm, const double* qL, const double* qR, const double* nv, double* out) {
+  Params pr{prm[0], prm[1], prm[2], prm[3], 0, 0, 0.0, 0};
+  Prim<double> L = cons2prim(pr, qL), Rr = cons2prim(pr, qR);
+  llf_flux(pr, qL, L, qR, Rr, nv, out);
+}
+double orc_log_mean(double a, double b) { return log_mean<double>(a, b); }
+
+// Volume integrals (Sec. 4.2 diagnostics) with the LGL quadrature:
+// out = {int rho, int rho u, int rho v, int rho w, int rho E,
+//        E_k = 1/(2|Omega|) int rho |u|^2, eps_S = mu/|Omega| int |omega|^2,
+//        min p}; rho0 = U0 = L = 1 and mu/mu0 = 1 (constant viscosity).
+void orc_integrals(void* h, const double* U, double* out) {
+  Ctx* c = (Ctx*)h;
+  int n = c->n, P = c->P;
+  const Params& pr = c->prm;
+  // gradients from the lifting: reuse rhs machinery through a local copy
+  size_t len = (size_t)c->E * 5 * P;
+  (void)len;
+  double tot[5] = {0, 0, 0, 0, 0}, vol = 0.0, ek = 0.0, ens = 0.0, pmin = 1e300;
+  // lifted gradient of the velocity (same BR1 operator as in rhs)
+  std::vector<double> phi((size_t)c->E * 3 * P);
+  for (int e = 0; e < c->E; ++e)
+    for (int id = 0; id < P; ++id) {
+      double q[5];
+      for (int v = 0; v < 5; ++v) q[v] = U[((size_t)e * 5 + v) * P + id];
+      for (int a = 0; a < 3; ++a) phi[((size_t)e * 3 + a) * P + id] = q[1 + a] / q[0];
+    }
+  for (int e = 0; e < c->E; ++e)
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          int id = vidx(n, i, j, k);
+          double wq = c->b.w[i] * c->b.w[j] * c->b.w[k] * c->J[(size_t)e * P + id];
+          double q[5];
+          for (int v = 0; v < 5; ++v) q[v] = U[((size_t)e * 5 + v) * P + id];
+          Prim<double> w = cons2prim(pr, q);
+          for (int v = 0; v < 5; ++v) tot[v] += wq * q[v];
+          vol += wq;
+          ek += wq * q[0] * (w.u[0] * w.u[0] + w.u[1] * w.u[1] + w.u[2] * w.u[2]);
+          pmin = std::min(pmin, w.p);
+        }
+  // vorticity from the BR1 lifted velocity gradient
+  int N = c->N;
+  double wend = c->b.w[0];
+  for (int e = 0; e < c->E; ++e) {
+    std::vector<double> g((size_t)9 * P, 0.0);   // [a*3+l]
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          int id = vidx(n, i, j, k);
+          for (int a = 0; a < 3; ++a) {
+            const double* f = &phi[((size_t)e * 3 + a) * P];
+            double dd[3];
+            for (int d = 0; d < 3; ++d) dd[d] = dxi(*c, f, d, i, j, k);
+            for (int l = 0; l < 3; ++l) {
+              double s = 0.0;
+              for (int d = 0; d < 3; ++d) s += c->Ja[(((size_t)e * 3 + d) * 3 + l) * P + id] * dd[d];
+              g[(a * 3 + l) * P + id] = s;
+            }
+          }
+        }
+    for (int f = 0; f < 6; ++f) {
+      int d = f / 2, s = f % 2;
+      int e2 = c->nbr[(e * 6 + f) * 3 + 0], f2 = c->nbr[(e * 6 + f) * 3 + 1], fl = c->nbr[(e * 6 + f) * 3 + 2];
+      for (int q = 0; q < n; ++q)
+        for (int p = 0; p < n; ++p) {
+          int id = face_vol(n, f, p, q);
+          int p2, q2;
+          flip_map(fl, N, p, q, p2, q2);
+          int id2 = face_vol(n, f2, p2, q2);
+          for (int a = 0; a < 3; ++a) {
+            double mine = phi[((size_t)e * 3 + a) * P + id];
+            double other = phi[((size_t)e2 * 3 + a) * P + id2];
+            double star = 0.5 * (mine + other);
+            for (int l = 0; l < 3; ++l) {
+              double nsJ = (2.0 * s - 1.0) * c->Ja[(((size_t)e * 3 + d) * 3 + l) * P + id];
+              g[(a * 3 + l) * P + id] += (star - mine) * nsJ / wend;
+            }
+          }
+        }
+    }
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          int id = vidx(n, i, j, k);
+          double Jv = c->J[(size_t)e * P + id];
+          double wq = c->b.w[i] * c->b.w[j] * c->b.w[k] * Jv;
+          double gg[9];
+          for (int r = 0; r < 9; ++r) gg[r] = g[r * P + id] / Jv;
+          double om0 = gg[2 * 3 + 1] - gg[1 * 3 + 2];
+          double om1 = gg[0 * 3 + 2] - gg[2 * 3 + 0];
+          double om2 = gg[1 * 3 + 0] - gg[0 * 3 + 1];
+          ens += wq * (om0 * om0 + om1 * om1 + om2 * om2);
+        }
+  }
+  for (int v = 0; v < 5; ++v) out[v] = tot[v];
+  out[5] = 0.5 * ek / vol;
+  out[6] = pr.mu * ens / vol;
+  out[7] = pmin;
+}
+
+// Node positions [E][3][P] (interpolated geometry at the LGL nodes).
+void orc_node_coords(void* h, double* X) {
+  Ctx* c = (Ctx*)h;
+  std::memcpy(X, c->X.data(), sizeof(double) * c->X.size());
+}
+
+// Initial states at the LGL nodes.
+//  kind 0: Taylor-Green vortex (Sec. 4.2, Eq. 6) with rho0 = U0 = L = R = 1,
+//          p0 = prm0, T0 = p0, rho = p / (R T0).
+//  kind 1: density-wave manufactured solution at time prm0.
+void orc_initial_state(void* h, int kind, double prm0, double* U) {
+  Ctx* c = (Ctx*)h;
+  int P = c->P;
+  double g = c->prm.gamma;
+  for (int e = 0; e < c->E; ++e)
+    for (int id = 0; id < P; ++id) {
+      double x = c->X[((size_t)e * 3 + 0) * P + id];
+      double y = c->X[((size_t)e * 3 + 1) * P + id];
+      double z = c->X[((size_t)e * 3 + 2) * P + id];
+      double rho, u[3], p;
+      if (kind == 0) {
+        double p0 = prm0;
+        u[0] = std::sin(x) * std::cos(y) * std::cos(z);
+        u[1] = -std::cos(x) * std::sin(y) * std::cos(z);
+        u[2] = 0.0;
+        p = p0 + (1.0 / 16.0) * (std::cos(2.0 * x) + std::cos(2.0 * y)) * (2.0 + std::cos(2.0 * z));
+        rho = p / (c->prm.R * p0);
+      } else {
+        rho = 2.0 + c->prm.mms_amp * std::sin(M_PI * (x + y + z - prm0));
+        u[0] = u[1] = u[2] = 1.0;
+        p = 1.0;
+      }
+      U[((size_t)e * 5 + 0) * P + id] = rho;
+      for (int a = 0; a < 3; ++a) U[((size_t)e * 5 + 1 + a) * P + id] = rho * u[a];
+      U[((size_t)e * 5 + 4) * P + id] = p / (g - 1.0) + 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,196 @@
+"""ctypes binding of the plain C++ FP64 oracle (test infrastructure only).
+
+The oracle follows the method of GALAEXI Sec. 3.1 (Eqs. 1-3) step by step; see
+``dgsem_oracle.cpp`` for the readings taken where the paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dgsem_oracle.cpp")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+
+def lib_path() -> str:
+    return _LIB
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (plain -O2, no vectorisation flags)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    L = C.CDLL(_LIB)
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _ip, _dp, C.c_int, C.c_int, C.c_char_p, C.c_int]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_nfaces.argtypes = [C.c_void_p]
+    L.orc_nfaces.restype = C.c_int
+    L.orc_basis.argtypes = [C.c_int, _dp, _dp, _dp]
+    L.orc_geometry.argtypes = [C.c_void_p, _dp, _dp, _dp]
+    L.orc_time_derivative.argtypes = [C.c_void_p, _dp, _dp, C.c_double]
+    L.orc_time_derivative_tl.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp, _dp, C.c_double]
+    L.orc_rk_steps.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, C.c_int]
+    L.orc_rk_steps_tl.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_double, C.c_double, C.c_int]
+    L.orc_rk_coeffs.argtypes = [_dp, _dp, _dp]
+    L.orc_ec_flux.argtypes = [_dp, _dp, _dp, _dp, _dp]
+    L.orc_llf_flux.argtypes = [_dp, _dp, _dp, _dp, _dp]
+    L.orc_log_mean.argtypes = [C.c_double, C.c_double]
+    L.orc_log_mean.restype = C.c_double
+    L.orc_integrals.argtypes = [C.c_void_p, _dp, _dp]
+    L.orc_node_coords.argtypes = [C.c_void_p, _dp]
+    L.orc_initial_state.argtypes = [C.c_void_p, C.c_int, C.c_double, _dp]
+    L.orc_set_vol_flux.argtypes = [C.c_void_p, C.c_int]
+    L.orc_lifting.argtypes = [C.c_void_p, _dp, _dp]
+    L.orc_volume_term.argtypes = [C.c_void_p, _dp, _dp]
+    _lib = L
+    return L
+
+
+def basis(N: int):
+    """LGL nodes, weights and differentiation matrix D[i, j] = l_j'(x_i)."""
+    L = _load()
+    n = N + 1
+    x, w, D = np.zeros(n), np.zeros(n), np.zeros(n * n)
+    L.orc_basis(N, x, w, D)
+    return x, w, D.reshape(n, n)
+
+
+def rk_coeffs():
+    L = _load()
+    A, B, Cc = np.zeros(5), np.zeros(5), np.zeros(5)
+    L.orc_rk_coeffs(A, B, Cc)
+    return A, B, Cc
+
+
+def _prm(gamma, R, Pr, mu, amp=0.1):
+    return np.array([gamma, R, Pr, mu, amp], dtype=np.float64)
+
+
+def ec_flux(qL, qR, nv, gamma=1.4):
+    out = np.zeros(5)
+    _load().orc_ec_flux(_prm(gamma, 1.0, 0.72, 0.0), np.ascontiguousarray(qL, dtype=np.float64),
+                        np.ascontiguousarray(qR, dtype=np.float64), np.ascontiguousarray(nv, dtype=np.float64), out)
+    return out
+
+
+def llf_flux(qL, qR, nv, gamma=1.4):
+    out = np.zeros(5)
+    _load().orc_llf_flux(_prm(gamma, 1.0, 0.72, 0.0), np.ascontiguousarray(qL, dtype=np.float64),
+                         np.ascontiguousarray(qR, dtype=np.float64), np.ascontiguousarray(nv, dtype=np.float64), out)
+    return out
+
+
+def log_mean(a, b):
+    return _load().orc_log_mean(float(a), float(b))
+
+
+class Oracle:
+    """FP64 CPU DGSEM on a mesh in the format of ``workloads.mesh``.
+
+    surf_flux: 0 = local Lax-Friedrichs, 1 = entropy-conservative two-point flux.
+    source: 0 = none, 1 = density-wave manufactured solution.
+    """
+
+    def __init__(self, mesh, N: int, gamma=1.4, R=1.0, Pr=0.72, mu=0.0,
+                 surf_flux: int = 0, source: int = 0, mms_amp: float = 0.1):
+        L = _load()
+        self.N, self.n, self.P = N, N + 1, (N + 1) ** 3
+        self.E = int(mesh.xgeo.shape[0])
+        self.gamma, self.R, self.Pr, self.mu = gamma, R, Pr, mu
+        xgeo = np.ascontiguousarray(mesh.xgeo, dtype=np.float64)
+        nbr = np.ascontiguousarray(mesh.face_nbr, dtype=np.int32)
+        err = C.create_string_buffer(256)
+        h = L.orc_create(N, self.E, int(mesh.xgeo.shape[-1]) - 1, xgeo, nbr,
+                         _prm(gamma, R, Pr, mu, mms_amp), surf_flux, source, err, 256)
+        if not h:
+            raise ValueError("oracle: " + err.value.decode())
+        self._h = C.c_void_p(h)
+        self._L = L
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self._L.orc_destroy(self._h)
+            self._h = None
+
+    @property
+    def shape(self):
+        return (self.E, 5, self.n, self.n, self.n)
+
+    def geometry(self):
+        X = np.zeros((self.E, 3, self.P))
+        Ja = np.zeros((self.E, 3, 3, self.P))
+        J = np.zeros((self.E, self.P))
+        self._L.orc_geometry(self._h, X, Ja, J)
+        return X, Ja, J
+
+    def time_derivative(self, U, t=0.0):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        out = np.zeros_like(U)
+        self._L.orc_time_derivative(self._h, U, out, float(t))
+        return out
+
+    def time_derivative_tl(self, U, dU, dmu=0.0, t=0.0):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        dU = np.ascontiguousarray(dU, dtype=np.float64)
+        Ut, dUt = np.zeros_like(U), np.zeros_like(U)
+        self._L.orc_time_derivative_tl(self._h, U, dU, float(dmu), Ut, dUt, float(t))
+        return Ut, dUt
+
+    def rk_steps(self, U, t, dt, nsteps):
+        U = np.array(U, dtype=np.float64, copy=True, order="C")
+        self._L.orc_rk_steps(self._h, U, float(t), float(dt), int(nsteps))
+        return U
+
+    def rk_steps_tl(self, U, dU, dmu, t, dt, nsteps):
+        U = np.array(U, dtype=np.float64, copy=True, order="C")
+        dU = np.array(dU, dtype=np.float64, copy=True, order="C")
+        self._L.orc_rk_steps_tl(self._h, U, dU, float(dmu), float(t), float(dt), int(nsteps))
+        return U, dU
+
+    def set_vol_flux(self, kind: int):
+        self._L.orc_set_vol_flux(self._h, int(kind))
+
+    def lifting(self, U):
+        G = np.zeros((self.E, 12, self.P))
+        self._L.orc_lifting(self._h, np.ascontiguousarray(U, dtype=np.float64), G)
+        return G
+
+    def volume_term(self, U):
+        out = np.zeros((self.E, 5, self.P))
+        self._L.orc_volume_term(self._h, np.ascontiguousarray(U, dtype=np.float64), out)
+        return out
+
+    def integrals(self, U):
+        out = np.zeros(8)
+        self._L.orc_integrals(self._h, np.ascontiguousarray(U, dtype=np.float64), out)
+        return out
+
+    def node_coords(self):
+        X = np.zeros((self.E, 3, self.P))
+        self._L.orc_node_coords(self._h, X)
+        return X
+
+    def initial_state(self, kind: str, prm0: float):
+        U = np.zeros(self.shape)
+        self._L.orc_initial_state(self._h, {"tgv": 0, "mms": 1}[kind], float(prm0), U)
+        return U

@@ -1,0 +1,97 @@
+"""Oracle pins: two-point flux, logarithmic mean and LLF flux (GALAEXI Sec. 3.1)."""
+import mpmath
+import numpy as np
+import pytest
+
+GAMMA = 1.4
+
+
+def _rand_state(rng):
+    r = rng.uniform(0.3, 3.0)
+    u = rng.uniform(-2.0, 2.0, 3)
+    p = rng.uniform(0.3, 3.0)
+    return np.array([r, *(r * u), p / (GAMMA - 1) + 0.5 * r * u @ u])
+
+
+def _prim(q):
+    r = q[0]
+    u = q[1:4] / r
+    p = (GAMMA - 1) * (q[4] - 0.5 * r * u @ u)
+    return r, u, p
+
+
+def _euler(q, n):
+    r, u, p = _prim(q)
+    un = u @ n
+    return np.array([r * un, *(q[1:4] * un + p * n), (q[4] + p) * un])
+
+
+def _entropy_vars(q):
+    r, u, p = _prim(q)
+    s = np.log(p * r ** -GAMMA)
+    return np.array([(GAMMA - s) / (GAMMA - 1) - r * (u @ u) / (2 * p), *(r * u / p), -r / p])
+
+
+def test_log_mean_against_multiprecision(orc):
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(1)
+    # ratios spanning both sides of the series/log switch
+    for _ in range(2000):
+        a = rng.uniform(0.1, 10.0)
+        ratio = np.exp(rng.normal(0, 1) * 10.0 ** rng.uniform(-9, 0))
+        b = a * ratio
+        got = orc.log_mean(a, b)
+        A, B = mpmath.mpf(a), mpmath.mpf(b)
+        ref = A if A == B else (A - B) / (mpmath.log(A) - mpmath.log(B))
+        assert abs(got - float(ref)) <= 3e-15 * float(ref), (a, b)
+    assert orc.log_mean(1.7, 1.7) == 1.7
+
+
+def test_ec_flux_consistency_symmetry_tadmor(orc):
+    rng = np.random.default_rng(2)
+    worst = 0.0
+    for _ in range(10000):
+        qL, qR = _rand_state(rng), _rand_state(rng)
+        n = rng.normal(size=3)
+        f = orc.ec_flux(qL, qR, n)
+        # symmetry
+        np.testing.assert_allclose(orc.ec_flux(qR, qL, n), f, rtol=1e-13, atol=1e-13)
+        # Tadmor's entropy-conservation condition  [[w]] . f = [[rho u . n]]
+        lhs = (_entropy_vars(qR) - _entropy_vars(qL)) @ f
+        rhs = (qR[1:4] - qL[1:4]) @ n
+        worst = max(worst, abs(lhs - rhs) / max(1.0, np.abs(f).max()))
+        # consistency
+    assert worst < 1e-12, worst
+    for _ in range(200):
+        q = _rand_state(rng)
+        n = rng.normal(size=3)
+        np.testing.assert_allclose(orc.ec_flux(q, q, n), _euler(q, n), rtol=1e-14, atol=1e-14)
+
+
+def test_ec_flux_is_kinetic_energy_preserving(orc):
+    """Jameson's KEP condition: f_m = {u} f_rho + p_tilde n with p_tilde a
+    consistent pressure average (Chandrashekar 2013, Sec. 3)."""
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        qL, qR = _rand_state(rng), _rand_state(rng)
+        n = rng.normal(size=3)
+        f = orc.ec_flux(qL, qR, n)
+        uL, uR = qL[1:4] / qL[0], qR[1:4] / qR[0]
+        resid = f[1:4] - 0.5 * (uL + uR) * f[0]
+        # the residual is parallel to n
+        assert np.linalg.norm(np.cross(resid, n)) < 1e-12 * (1 + np.linalg.norm(resid))
+
+
+def test_llf_flux(orc):
+    rng = np.random.default_rng(4)
+    for _ in range(500):
+        qL, qR = _rand_state(rng), _rand_state(rng)
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        f = orc.llf_flux(qL, qR, n)
+        rL, uL, pL = _prim(qL)
+        rR, uR, pR = _prim(qR)
+        lam = max(abs(uL @ n) + np.sqrt(GAMMA * pL / rL), abs(uR @ n) + np.sqrt(GAMMA * pR / rR))
+        ref = 0.5 * (_euler(qL, n) + _euler(qR, n)) - 0.5 * lam * (qR - qL)
+        np.testing.assert_allclose(f, ref, rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(orc.llf_flux(qL, qL, n), _euler(qL, n), rtol=1e-14, atol=1e-14)
