@@ -1,0 +1,338 @@
+"""Throughput of the DGSEM hot path: one step = one LSERK4-5 step (five stages
+of lifting, face fluxes, split-form volume integral, surface integral,
+Jacobian and stage update) of the density-wave manufactured solution on the
+16^3-element curvilinear mesh with randomly rotated element frames.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--order 7] [--impl reference]
+
+Prints one JSON line (rank 0).  Metric: DOF*stage/s = (nodes x 5 stages x K)
+/ time; PID = 1 / that, in ns.  `--impl reference` times the plain CPU oracle
+on the same workload (one R(U) evaluation of the whole mesh per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF·stage/s (1/PID) of R(U)+RK at N=3..7 on 1 GB300 vs fp64 plain; % roofline"
+UNIT = "DOF*stage/s"
+K_ELEMS = 16
+MMS_SEED = 20260528
+DT = 1e-3
+
+
+def workload_name(N):
+    return ("MMS density wave rho=2+0.1sin(pi(x+y+z-t)), u=(1,1,1), p=1 on [-1,1]^3, %d^3 curvilinear hexes "
+            "(x_i += 0.1 prod sin(pi x_j)), seeded rotated element frames, N=%d LGL, LLF + BR1 + "
+            "Chandrashekar split form, LSERK4-5, dt=1e-3" % (K_ELEMS, N))
+
+
+def build_mesh(N):
+    from workloads import box_mesh
+    return box_mesh(K_ELEMS, N, deform="sinprod", rotate_seed=MMS_SEED)
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic FP64 operation count of the volume kernel per node and stage
+# (FMA = 2 flops; a divide, square root or logarithm counts as 1).  The
+# two-point flux with symmetric reuse is evaluated 3(n-1)/2 times per node.
+def volume_flops_per_dof(N):
+    n = N + 1
+    pair = 97.0                        # Chandrashekar flux + metric average + both accumulations
+    diag = 3 * 2.0 * 5                 # D_ii terms folded into the accumulators
+    visc = 20.0 + 3 * 26.0 + 12 * n * 2.0
+    prim = 13.0
+    surf = (6.0 / n) * 25.0
+    epi = 5 * 6.0
+    return 1.5 * (n - 1) * pair + diag + visc + prim + surf + epi
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        if not self.rows:
+            return None
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(N, n_evals=2):
+    """The plain oracle (single thread) on the same workload: seconds per R(U)
+    of the whole mesh -> DOF*stage/s."""
+    import oracle
+    from workloads import mms_params
+    prm = mms_params()
+    mesh = build_mesh(N)
+    o = oracle.Oracle(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1)
+    U = o.initial_state("mms", 0.0)
+    dof = mesh.n_elems * (N + 1) ** 3
+    t0 = time.perf_counter()
+    for _ in range(n_evals):
+        o.time_derivative(U, t=0.0)
+    dt = (time.perf_counter() - t0) / n_evals
+    return dof / dt, dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    N = args.order
+    import oracle
+    from workloads import mms_params
+    prm = mms_params()
+    mesh = build_mesh(N)
+    o = oracle.Oracle(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1)
+    U = o.initial_state("mms", 0.0)
+    dof = mesh.n_elems * (N + 1) ** 3
+    for _ in range(args.warmup):
+        o.time_derivative(U, t=0.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.time_derivative(U, t=0.0)
+    el = time.perf_counter() - t0
+    val = dof * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(N), "elements": mesh.n_elems, "N": N, "dof": dof,
+                   "pid_ns": 1e9 / val},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "each step = one R(U) evaluation (one RK stage) of the whole mesh by the "
+                                   "single-threaded plain C++ oracle"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--order", type=int, default=7)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", default="3,4,5,6,7", help="extra orders timed for the per-N table ('' = none)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import paper_2605_28627_gb300 as dg
+    from workloads import mms_params
+
+    torch.cuda.set_device(local)
+    dev = "cuda:%d" % local
+    N = args.order
+    prm = mms_params()
+    mesh = build_mesh(N)
+    solver = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=dg.SOURCE_MMS,
+                       device=local)
+    dof = solver.E * (N + 1) ** 3
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        U = solver.initial_state("mms", 0.0, stream=stream)
+        G = torch.empty_like(U)
+        U0 = U.clone()
+    stream.synchronize()
+
+    # warm-up (also captures the one-step graph)
+    t = 0.0
+    for _ in range(args.warmup):
+        solver.rk_step(U, G, t, DT, 1, stream=stream)
+        t += DT
+    stream.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        solver.rk_step(U, G, t, DT, 1, stream=stream)
+        t += DT
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms_total = max_over_ranks(ms_total, world)
+    ms_step = ms_total / args.steps
+    value = world * dof * 5 * args.steps / (ms_total * 1e-3)
+    launches_per_step = 5 * 3 + 1 + 1   # stages x (lift, face, volume) + clock advance + clock set
+    gpu_launches = launches_per_step * args.steps
+
+    # per-kernel times on the same stream, same inputs
+    ms3 = solver.profile_stages(U, G, DT, reps=10, stream=stream)
+    fp64_peak, fp32_peak = dg.probe_peaks(local)
+    vol_flops = volume_flops_per_dof(N) * dof
+    achieved = vol_flops / (ms3[2] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "kernel": "k_volume<%d> (split-form volume + surface + Jacobian + LSERK update)" % N,
+                "peak_source": "measured FP64 DFMA chain throughput on this GPU (dg_probe_peaks)",
+                "stage_ms": {"lift": ms3[0], "face": ms3[1], "volume": ms3[2]}}
+
+    # end to end through the C ABI with host buffers (pinned)
+    host = U0.cpu().pin_memory()
+    solver.advance_host(host, 0.0, DT, 1, stream=stream)      # allocate the context's buffers
+    torch.cuda.synchronize()
+    nb = host.numel() * 8
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solver.advance_host(host, 0.0, DT, 1, stream=stream)
+    el = time.perf_counter() - t0
+    el = max_over_ranks(el, world)
+    e2e = {"value": world * dof * 5 * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": nb,
+           "d2h_bytes_per_step": nb}
+
+    sweep = {}
+    if args.sweep and rank == 0:
+        for Ns in [int(v) for v in args.sweep.split(",") if v]:
+            if Ns == N:
+                sweep[str(Ns)] = {"dof_stage_per_s": value / world, "pid_ns": 1e9 * world / value}
+                continue
+            ms = sweep_rate(dg, Ns, local, prm)
+            dofs = K_ELEMS ** 3 * (Ns + 1) ** 3
+            sweep[str(Ns)] = {"dof_stage_per_s": dofs * 5 / (ms * 1e-3), "pid_ns": ms * 1e6 / (dofs * 5)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, sec = cpu_oracle_rate(N, n_evals=2)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "2 evaluations of R(U) (one RK stage each) on the whole %d^3, N=%d mesh, single-threaded "
+                         "plain C++ oracle, %.1f s each" % (K_ELEMS, N, sec)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(N), "elements": solver.E, "N": N, "dof": dof,
+                       "pid_ns": 1e9 * world / value, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2: %.0f MB of state, metrics, gradients and face data touched "
+                             "per stage" % working_set_mb(solver)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clk, "sweep": sweep,
+            "peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
+        }
+        print(json.dumps(line))
+    solver.close()
+    return 0
+
+
+def working_set_mb(s):
+    P, NN, E = s.P, s.n * s.n, s.E
+    F = 3 * E
+    doubles = E * P * (5 + 5 + 10 + 12 + 3) + F * NN * (4 + 5)
+    return doubles * 8 / 1e6
+
+
+def sweep_rate(dg, N, dev, prm, steps=5):
+    import torch
+    mesh = build_mesh(N)
+    s = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=dg.SOURCE_MMS,
+                  device=dev)
+    st = torch.cuda.Stream(device="cuda:%d" % dev)
+    with torch.cuda.stream(st):
+        U = s.initial_state("mms", 0.0, stream=st)
+        G = torch.empty_like(U)
+    for i in range(3):
+        s.rk_step(U, G, i * DT, DT, 1, stream=st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for i in range(steps):
+        s.rk_step(U, G, (3 + i) * DT, DT, 1, stream=st)
+    e1.record(st)
+    e1.synchronize()
+    s.close()
+    return e0.elapsed_time(e1) / steps
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,163 @@
+/*
+ * dgsem.h -- C ABI of the GB300 (sm_103a) split-form DGSEM hot path.
+ *
+ * The operator is the semi-discrete DG time derivative U_t = R(U) of the 3-D
+ * compressible Navier-Stokes-Fourier equations (GALAEXI, Sec. 3.1, Eq. 1) on
+ * curvilinear, unstructured hexahedral meshes, discretised by the DGSEM on
+ * Legendre-Gauss-Lobatto nodes (Sec. 3.1, Eq. 2) with
+ *   - BR1 lifting of the primitive gradients (Sec. 3.1, Eq. 3),
+ *   - a Riemann flux plus the averaged viscous flux on faces (Sec. 3.1),
+ *   - the entropy-stable split-form volume integral with the two-point flux of
+ *     Chandrashekar (2013) and curvilinear metric terms (Sec. 3.1),
+ *   - the surface integral and the Jacobian scaling,
+ * advanced by the five-stage low-storage RK4-5 of Carpenter & Kennedy (1994)
+ * (Sec. 3.1, "RK4-5").
+ *
+ * Conventions for every entry point:
+ *   - State arrays are caller-owned DEVICE buffers of float64, element-blocked
+ *     and contiguous: U[e][v][k][j][i], v = (rho, rho u, rho v, rho w, rho E),
+ *     i fastest, (N+1) nodes per direction; dg_state_len() doubles in total.
+ *     They must be 16-byte aligned.
+ *   - Calls are stream-ordered on the given CUDA stream (a cudaStream_t;
+ *     NULL = legacy default stream) and return without synchronising, unless
+ *     documented otherwise.
+ *   - Every call returns a dg_status; on failure dg_last_error() describes it.
+ *     The library never aborts the process and never falls back to the CPU.
+ */
+#ifndef DGSEM_H
+#define DGSEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_ctx dg_ctx;           /* opaque: geometry, face maps, work buffers */
+typedef struct CUstream_st* dg_stream;  /* identical to cudaStream_t */
+
+typedef enum {
+  DG_OK = 0,
+  DG_EINVAL = 1,        /* bad argument (null pointer, size, range) */
+  DG_ENOMEM = 2,        /* device allocation failed */
+  DG_ECUDA = 3,         /* a CUDA runtime call failed */
+  DG_EMESH = 4,         /* mesh rejected: connectivity or a non-positive Jacobian */
+  DG_ENONFINITE = 5,    /* a reduction met NaN or Inf */
+  DG_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
+  DG_EUNSUPPORTED = 7   /* polynomial degree or option not built */
+} dg_status;
+
+enum { DG_FLUX_LLF = 0, DG_FLUX_EC = 1 };         /* surface Riemann flux */
+enum { DG_FP64 = 0, DG_FP32OP = 1 };              /* operator arithmetic */
+enum { DG_SOURCE_NONE = 0, DG_SOURCE_MMS = 1 };   /* volume source term */
+enum { DG_IC_TGV = 0, DG_IC_MMS = 1 };            /* built-in initial states */
+
+/*
+ * Mesh (Sec. 3.1: non-overlapping hexahedra, each the image of E = [-1,1]^3
+ * under a mapping chi).  Host arrays, read only during dg_init.
+ *   xgeo[e][c][k][j][i]: coordinate c of element e at the equispaced reference
+ *       point (-1 + 2i/ngeo, -1 + 2j/ngeo, -1 + 2k/ngeo) of its local frame.
+ *   face_nbr[e][f][0..2] = (e2, f2, flip): local face f = 2d + s (d: reference
+ *       direction, s = 0 at -1, 1 at +1) of e touches local face f2 of e2.  A
+ *       face node is (p, q) along the two other directions in increasing
+ *       order; flip maps (p, q) on (e, f) to (p2, q2) on (e2, f2):
+ *       (a, b) = flip & 1 ? (q, p) : (p, q);  p2 = flip & 2 ? N - a : a;
+ *       q2 = flip & 4 ? N - b : b.  Every face must have a neighbour
+ *       (periodic meshes); the relation must be reciprocal.
+ */
+typedef struct {
+  int32_t n_elems;
+  int32_t ngeo;               /* >= 1 */
+  const double* xgeo;
+  const int32_t* face_nbr;
+} dg_mesh;
+
+/* Gas and discretisation (Sec. 3.1, Eq. 1: perfect gas p = (gamma-1) rho eps,
+ * p = rho R T, Newtonian stress with constant mu, Fourier heat flux with
+ * lambda = mu c_p / Pr). */
+typedef struct {
+  int32_t N;                  /* polynomial degree, 1..9 */
+  double gamma, R, Pr, mu;
+  int32_t surf_flux;          /* DG_FLUX_LLF or DG_FLUX_EC */
+  int32_t precision;          /* DG_FP64 or DG_FP32OP */
+  int32_t source;             /* DG_SOURCE_NONE or DG_SOURCE_MMS */
+  double mms_amp;             /* amplitude A of rho = 2 + A sin(pi(x+y+z-t)) */
+} dg_params;
+
+/* Build a context on CUDA device `device`: LGL basis, geometry (node
+ * positions, curl-form metric terms, Jacobian, face normals) computed on the
+ * GPU from the mesh, face maps and work buffers.  Synchronous.
+ * Errors: DG_EINVAL (null/size), DG_EUNSUPPORTED (N), DG_EMESH (connectivity
+ * out of range or not reciprocal, Jacobian <= 0 at a node), DG_ENOMEM,
+ * DG_ECUDA.  On failure *out is NULL. */
+dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out);
+
+/* Free everything the context owns.  Synchronises the device. */
+dg_status dg_destroy(dg_ctx* ctx);
+
+/* Number of doubles in one state array: n_elems * 5 * (N+1)^3. */
+size_t dg_state_len(const dg_ctx* ctx);
+
+/* Ut = R(U, t) (Sec. 3.1, Eqs. 2-3 in strong form).  dU, dUt: device, may not
+ * alias. */
+dg_status dg_time_derivative(dg_ctx* ctx, const double* dU, double* dUt, double t, dg_stream stream);
+
+/* nsteps steps of LSERK4-5 (Sec. 3.1) in place: per stage s,
+ *   G <- A_s G + dt R(U, t + c_s dt);  U <- U + B_s G,
+ * with G (device, dg_state_len doubles, caller-owned scratch) zeroed at the
+ * start of every step.  The sequence of launches is captured once per
+ * (dU, dG, nsteps) into a CUDA graph and replayed. */
+dg_status dg_rk_step(dg_ctx* ctx, double* dU, double* dG, double t, double dt, int32_t nsteps,
+                     dg_stream stream);
+
+/* End-to-end variant with HOST buffers: copies hU (host, dg_state_len doubles)
+ * to the device, advances nsteps steps, and copies the result back into hU.
+ * Device state and register live in the context.  Synchronises the stream. */
+dg_status dg_advance_host(dg_ctx* ctx, double* hU, double t, double dt, int32_t nsteps, dg_stream stream);
+
+/* Volume integrals with the LGL quadrature (Sec. 4.2 diagnostics), host_out8 =
+ * { int rho, int rho u, int rho v, int rho w, int rho E,
+ *   E_k = 1/(2|Omega|) int rho |u|^2, eps = mu/|Omega| int |omega|^2 (vorticity
+ *   from the BR1-lifted velocity gradient), min p }, in units rho0 = U0 = L = 1.
+ * Synchronises the stream.  DG_ENONFINITE if any value is NaN/Inf. */
+dg_status dg_integrals(dg_ctx* ctx, const double* dU, double* host_out8, dg_stream stream);
+
+/* Time step of Sec. 3.1 ("CFL = 0.9, same for the viscous restriction"):
+ * dt = min(cfl * 2/((2N+1) max_nodes sum_d lambda_d),
+ *          dfl * (2/(2N+1))^2 / max_nodes (mu_eff sum_d |Ja^d|^2 / J^2)),
+ * lambda_d = (|u . Ja^d| + c |Ja^d|) / J, mu_eff = max(4/3, gamma/Pr) mu / rho.
+ * Synchronises the stream. */
+dg_status dg_max_dt(dg_ctx* ctx, const double* dU, double cfl, double dfl, double* host_dt, dg_stream stream);
+
+/* Built-in initial states at the LGL nodes: DG_IC_TGV (Sec. 4.2, Eq. 6) with
+ * rho0 = U0 = L = R = 1 and p0 = prm0; DG_IC_MMS at time prm0. */
+dg_status dg_initial_state(dg_ctx* ctx, int32_t kind, double prm0, double* dU, dg_stream stream);
+
+/* Physical node positions X[e][c][k][j][i] (device, n_elems*3*(N+1)^3). */
+dg_status dg_node_coords(dg_ctx* ctx, double* dX, dg_stream stream);
+
+/* Geometry as used by the kernels: Ja[e][d][l][P] (J a^d, component l) and
+ * J[e][P]; either pointer may be NULL.  Device buffers. */
+dg_status dg_geometry(dg_ctx* ctx, double* dJa, double* dJ, dg_stream stream);
+
+/* Measurement helper: runs `reps` LSERK stages on (dU, dG) (state advanced
+ * with dt) and times each stage kernel with CUDA events on `stream`;
+ * host_ms3 = average milliseconds per launch of { lifting, face flux,
+ * volume + update }.  Synchronises the stream. */
+dg_status dg_profile_stages(dg_ctx* ctx, double* dU, double* dG, double dt, int32_t reps, float* host_ms3,
+                            dg_stream stream);
+
+/* Measurement helper: throughput of dependent-chain FP64 DFMA and FP32 FFMA
+ * on `device` in TFLOP/s (FMA = 2 flop), host_out2 = {fp64, fp32}.  Used as
+ * the arithmetic roof for the FP64-pipe-bound kernels.  Synchronous. */
+dg_status dg_probe_peaks(int device, double* host_out2);
+
+/* Human-readable description of the last error on ctx (or of the last failed
+ * dg_init when ctx is NULL).  Never NULL. */
+const char* dg_last_error(const dg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGSEM_H */

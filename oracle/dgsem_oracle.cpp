@@ -221,8 +221,16 @@ static bool build_geometry(Ctx& c, int ngeo, const double* xgeo) {
   c.J.assign((size_t)c.E * P, 0.0);
   std::vector<double> dX(9 * P), v(3 * P);
   for (int e = 0; e < c.E; ++e) {
+    // Interpolation, metric terms and Jacobian are invariant under a
+    // translation of the coordinates (the interpolant reproduces constants;
+    // tensor-product derivatives along different directions commute), so they
+    // are computed from coordinates relative to the element's first sample
+    // (its corner, which is also the first LGL node); this removes the
+    // cancellation that large absolute coordinates would cause.
+    std::vector<double> Xrel(3 * P);
     for (int cc = 0; cc < 3; ++cc) {
       const double* g = xgeo + ((size_t)e * 3 + cc) * mP;
+      const double g0 = g[0];
       double* Xo = &c.X[((size_t)e * 3 + cc) * P];
       for (int k = 0; k < n; ++k)
         for (int j = 0; j < n; ++j)
@@ -231,11 +239,12 @@ static bool build_geometry(Ctx& c, int ngeo, const double* xgeo) {
             for (int c3 = 0; c3 < m; ++c3)
               for (int b3 = 0; b3 < m; ++b3)
                 for (int a3 = 0; a3 < m; ++a3)
-                  s += V[i * m + a3] * V[j * m + b3] * V[k * m + c3] * g[a3 + m * (b3 + m * c3)];
-            Xo[vidx(n, i, j, k)] = s;
+                  s += V[i * m + a3] * V[j * m + b3] * V[k * m + c3] * (g[a3 + m * (b3 + m * c3)] - g0);
+            Xrel[cc * P + vidx(n, i, j, k)] = s;
+            Xo[vidx(n, i, j, k)] = s + g0;
           }
     }
-    const double* Xe = &c.X[(size_t)e * 3 * P];
+    const double* Xe = Xrel.data();
     // dX[cc][d] = d X_cc / d xi_d
     for (int cc = 0; cc < 3; ++cc)
       for (int d = 0; d < 3; ++d)

@@ -1,0 +1,241 @@
+"""GB300-native split-form DGSEM hot path (GALAEXI, arXiv 2605.28627).
+
+Thin Python binding over the C ABI declared in ``include/dgsem.h``.  Every
+numerical step runs in the CUDA library ``libdgsem.so``; this module only
+marshals arguments (device pointers of torch tensors, the current CUDA
+stream).  There is no CPU fallback: if the library or a GPU is missing, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+# dg_status codes
+DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_EMESH, DG_ENONFINITE, DG_ETIMEOUT, DG_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["DG_OK", "DG_EINVAL", "DG_ENOMEM", "DG_ECUDA", "DG_EMESH", "DG_ENONFINITE", "DG_ETIMEOUT",
+                "DG_EUNSUPPORTED"]
+FLUX_LLF, FLUX_EC = 0, 1
+FP64, FP32OP = 0, 1
+SOURCE_NONE, SOURCE_MMS = 0, 1
+IC_TGV, IC_MMS = 0, 1
+
+# Every symbol that include/dgsem.h declares.
+EXPORTS = ["dg_init", "dg_destroy", "dg_state_len", "dg_time_derivative", "dg_rk_step", "dg_advance_host",
+           "dg_integrals", "dg_max_dt", "dg_initial_state", "dg_node_coords", "dg_geometry", "dg_profile_stages",
+           "dg_probe_peaks", "dg_last_error"]
+
+
+class DGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 8 else status, msg))
+
+
+class dg_mesh(C.Structure):
+    _fields_ = [("n_elems", C.c_int32), ("ngeo", C.c_int32), ("xgeo", C.POINTER(C.c_double)),
+                ("face_nbr", C.POINTER(C.c_int32))]
+
+
+class dg_params(C.Structure):
+    _fields_ = [("N", C.c_int32), ("gamma", C.c_double), ("R", C.c_double), ("Pr", C.c_double),
+                ("mu", C.c_double), ("surf_flux", C.c_int32), ("precision", C.c_int32),
+                ("source", C.c_int32), ("mms_amp", C.c_double)]
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libdgsem.so (building it in-tree with nvcc if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError("libdgsem.so is not built (run __graft_entry__.build())")
+        _build.build()
+    L = C.CDLL(LIB_PATH)
+    vp, dp, i32, f64 = C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.c_double
+    L.dg_init.argtypes = [C.POINTER(dg_mesh), C.POINTER(dg_params), C.c_int, C.POINTER(vp)]
+    L.dg_destroy.argtypes = [vp]
+    L.dg_state_len.argtypes = [vp]
+    L.dg_state_len.restype = C.c_size_t
+    L.dg_time_derivative.argtypes = [vp, vp, vp, f64, vp]
+    L.dg_rk_step.argtypes = [vp, vp, vp, f64, f64, i32, vp]
+    L.dg_advance_host.argtypes = [vp, vp, f64, f64, i32, vp]
+    L.dg_integrals.argtypes = [vp, vp, dp, vp]
+    L.dg_max_dt.argtypes = [vp, vp, f64, f64, dp, vp]
+    L.dg_initial_state.argtypes = [vp, i32, f64, vp, vp]
+    L.dg_node_coords.argtypes = [vp, vp, vp]
+    L.dg_geometry.argtypes = [vp, vp, vp, vp]
+    L.dg_profile_stages.argtypes = [vp, vp, vp, f64, i32, C.POINTER(C.c_float), vp]
+    L.dg_probe_peaks.argtypes = [C.c_int, dp]
+    L.dg_last_error.argtypes = [vp]
+    L.dg_last_error.restype = C.c_char_p
+    for name in ("dg_init", "dg_destroy", "dg_time_derivative", "dg_rk_step", "dg_advance_host", "dg_integrals",
+                 "dg_max_dt", "dg_initial_state", "dg_node_coords", "dg_geometry", "dg_profile_stages",
+                 "dg_probe_peaks"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """A DGSEM context on one GPU: geometry and work buffers live in the
+    library; states are caller-owned float64 CUDA tensors of shape
+    ``[E, 5, N+1, N+1, N+1]``."""
+
+    def __init__(self, mesh, N: int, gamma=1.4, R=1.0, Pr=0.72, mu=0.0, surf_flux=FLUX_LLF,
+                 precision=FP64, source=SOURCE_NONE, mms_amp=0.1, device: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2605_28627_gb300 needs a CUDA GPU; there is no CPU fallback")
+        self._L = load()
+        self.N, self.n, self.P = N, N + 1, (N + 1) ** 3
+        self.device = device
+        xgeo = np.ascontiguousarray(mesh.xgeo, dtype=np.float64)
+        nbr = np.ascontiguousarray(mesh.face_nbr, dtype=np.int32)
+        self.E = int(xgeo.shape[0])
+        m = dg_mesh(self.E, int(xgeo.shape[-1]) - 1, xgeo.ctypes.data_as(C.POINTER(C.c_double)),
+                    nbr.ctypes.data_as(C.POINTER(C.c_int32)))
+        p = dg_params(N, gamma, R, Pr, mu, surf_flux, precision, source, mms_amp)
+        h = C.c_void_p()
+        torch.cuda.set_device(device)
+        st = self._L.dg_init(C.byref(m), C.byref(p), device, C.byref(h))
+        if st != DG_OK:
+            raise DGError(st, self._L.dg_last_error(None).decode())
+        self._h = h
+        self.mu = mu
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.dg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != DG_OK:
+            raise DGError(st, self._L.dg_last_error(self._h).decode())
+
+    @property
+    def shape(self):
+        return (self.E, 5, self.n, self.n, self.n)
+
+    def state_len(self) -> int:
+        return int(self._L.dg_state_len(self._h))
+
+    def empty_state(self):
+        import torch
+        return torch.empty(self.shape, dtype=torch.float64, device="cuda:%d" % self.device)
+
+    def _chk_state(self, U):
+        import torch
+        if not (isinstance(U, torch.Tensor) and U.is_cuda and U.dtype == torch.float64 and U.is_contiguous()
+                and U.numel() == self.state_len()):
+            raise ValueError("state must be a contiguous float64 CUDA tensor with %d elements" % self.state_len())
+
+    def time_derivative(self, U, Ut=None, t=0.0, stream=None):
+        self._chk_state(U)
+        if Ut is None:
+            Ut = self.empty_state()
+        self._chk_state(Ut)
+        self._check(self._L.dg_time_derivative(self._h, _ptr(U), _ptr(Ut), float(t), _stream_handle(stream)))
+        return Ut
+
+    def rk_step(self, U, G, t, dt, nsteps=1, stream=None):
+        self._chk_state(U)
+        self._chk_state(G)
+        self._check(self._L.dg_rk_step(self._h, _ptr(U), _ptr(G), float(t), float(dt), int(nsteps),
+                                       _stream_handle(stream)))
+        return U
+
+    def advance_host(self, U_host, t, dt, nsteps=1, stream=None):
+        """End to end through host memory: U_host (float64 numpy array or
+        pinned CPU tensor, contiguous) is copied in, advanced and copied back."""
+        import torch
+        if isinstance(U_host, torch.Tensor):
+            assert U_host.device.type == "cpu" and U_host.dtype == torch.float64 and U_host.is_contiguous()
+            ptr = C.c_void_p(U_host.data_ptr())
+            n = U_host.numel()
+        else:
+            assert U_host.dtype == np.float64 and U_host.flags["C_CONTIGUOUS"]
+            ptr = C.c_void_p(U_host.ctypes.data)
+            n = U_host.size
+        if n != self.state_len():
+            raise ValueError("host state has the wrong size")
+        self._check(self._L.dg_advance_host(self._h, ptr, float(t), float(dt), int(nsteps), _stream_handle(stream)))
+        return U_host
+
+    def integrals(self, U, stream=None):
+        self._chk_state(U)
+        out = (C.c_double * 8)()
+        self._check(self._L.dg_integrals(self._h, _ptr(U), out, _stream_handle(stream)))
+        return np.array(out[:])
+
+    def max_dt(self, U, cfl=0.9, dfl=0.9, stream=None):
+        self._chk_state(U)
+        dt = C.c_double()
+        self._check(self._L.dg_max_dt(self._h, _ptr(U), float(cfl), float(dfl), C.byref(dt), _stream_handle(stream)))
+        return dt.value
+
+    def initial_state(self, kind: str, prm0: float, U=None, stream=None):
+        if U is None:
+            U = self.empty_state()
+        self._chk_state(U)
+        self._check(self._L.dg_initial_state(self._h, {"tgv": IC_TGV, "mms": IC_MMS}[kind], float(prm0), _ptr(U),
+                                             _stream_handle(stream)))
+        return U
+
+    def node_coords(self, stream=None):
+        import torch
+        X = torch.empty((self.E, 3, self.P), dtype=torch.float64, device="cuda:%d" % self.device)
+        self._check(self._L.dg_node_coords(self._h, _ptr(X), _stream_handle(stream)))
+        return X
+
+    def profile_stages(self, U, G, dt, reps=5, stream=None):
+        """Average milliseconds per launch of (lifting, face flux, volume)."""
+        self._chk_state(U)
+        self._chk_state(G)
+        ms = (C.c_float * 3)()
+        self._check(self._L.dg_profile_stages(self._h, _ptr(U), _ptr(G), float(dt), int(reps), ms,
+                                              _stream_handle(stream)))
+        return [float(v) for v in ms]
+
+    def geometry(self, stream=None):
+        import torch
+        Ja = torch.empty((self.E, 3, 3, self.P), dtype=torch.float64, device="cuda:%d" % self.device)
+        J = torch.empty((self.E, self.P), dtype=torch.float64, device="cuda:%d" % self.device)
+        self._check(self._L.dg_geometry(self._h, _ptr(Ja), _ptr(J), _stream_handle(stream)))
+        return Ja, J
+
+
+def probe_peaks(device: int = 0):
+    """Measured FP64 and FP32 FMA throughput in TFLOP/s on `device`."""
+    L = load()
+    out = (C.c_double * 2)()
+    st = L.dg_probe_peaks(int(device), out)
+    if st != DG_OK:
+        raise DGError(st, "dg_probe_peaks failed")
+    return float(out[0]), float(out[1])

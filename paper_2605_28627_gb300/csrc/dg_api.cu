@@ -1,0 +1,437 @@
+// C ABI of the DGSEM hot path: context set-up (mesh checks, LGL basis, face
+// maps, GPU geometry), stage sequencing of R(U) and of LSERK4-5 (captured in a
+// CUDA graph), host-buffer end-to-end entry, diagnostics.
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <new>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+static thread_local std::string g_init_error = "no error";
+
+// LSERK4-5 of Carpenter & Kennedy (1994), five stages, 2N storage (Sec. 3.1).
+static const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+static const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                               2277821191437.0 / 14882151754819.0};
+static const double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                               2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+
+// Legendre polynomial P_N and its first two derivatives at x (three-term
+// recurrence; second derivative from Legendre's equation).
+static void legendre(int N, double x, double& L, double& dL, double& d2L) {
+  double a = 1.0, b = x;
+  if (N == 0) { L = 1.0; dL = 0.0; d2L = 0.0; return; }
+  for (int k = 1; k < N; ++k) {
+    const double c = ((2.0 * k + 1.0) * x * b - k * a) / (k + 1.0);
+    a = b; b = c;
+  }
+  L = b;
+  // (1 - x^2) P_N' = N (P_{N-1} - x P_N)
+  dL = N * (a - x * b) / (1.0 - x * x);
+  d2L = (2.0 * x * dL - N * (N + 1.0) * L) / (1.0 - x * x);
+}
+
+// LGL nodes (+-1 and the zeros of P_N'), weights 2/(N(N+1) P_N^2) and the
+// collocation derivative matrix D_ij = P_N(x_i) / (P_N(x_j) (x_i - x_j)),
+// with the diagonal set so that every row sums to zero (D 1 = 0 exactly).
+static void lgl_basis(int N, std::vector<double>& x, std::vector<double>& w, std::vector<double>& D) {
+  const int n = N + 1;
+  x.assign(n, 0.0); w.assign(n, 0.0); D.assign((size_t)n * n, 0.0);
+  x[0] = -1.0; x[N] = 1.0;
+  for (int j = 1; j <= N / 2; ++j) {
+    // Newton on P_N' from a Chebyshev-Lobatto start; symmetric partner mirrored
+    double t = -std::cos(M_PI * j / N);
+    for (int it = 0; it < 60; ++it) {
+      double L, dL, d2L;
+      legendre(N, t, L, dL, d2L);
+      const double step = dL / d2L;
+      t -= step;
+      if (std::fabs(step) < 1e-17) break;
+    }
+    x[j] = t;
+    x[N - j] = -t;
+  }
+  if (N % 2 == 0) x[N / 2] = 0.0;
+  std::vector<double> LN(n);
+  for (int j = 0; j < n; ++j) {
+    double L = 1.0, a = 1.0, b = x[j];
+    for (int k = 1; k < N; ++k) {
+      const double c = ((2.0 * k + 1.0) * x[j] * b - k * a) / (k + 1.0);
+      a = b; b = c;
+    }
+    L = N == 0 ? 1.0 : b;
+    LN[j] = L;
+    w[j] = 2.0 / (N * (N + 1.0) * L * L);
+  }
+  for (int i = 0; i < n; ++i) {
+    double row = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (i == j) continue;
+      const double dij = LN[i] / (LN[j] * (x[i] - x[j]));
+      D[(size_t)i * n + j] = dij;
+      row += dij;
+    }
+    D[(size_t)i * n + i] = -row;
+  }
+}
+
+static dg_status fail(Ctx* c, dg_status st, const char* what, cudaError_t e = cudaSuccess) {
+  char buf[512];
+  if (e != cudaSuccess) std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  else std::snprintf(buf, sizeof buf, "%s", what);
+  if (c) c->err = buf; else g_init_error = buf;
+  return st;
+}
+
+#define DG_CUDA(call, ctx, what)                                   \
+  do {                                                             \
+    cudaError_t _e = (call);                                       \
+    if (_e != cudaSuccess)                                         \
+      return fail(ctx, _e == cudaErrorMemoryAllocation ? DG_ENOMEM : DG_ECUDA, what, _e); \
+  } while (0)
+
+static void release(Ctx* c) {
+  if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  double* dbl[] = {c->d_D, c->d_metrics, c->d_J, c->d_X, c->d_facegeo, c->d_grad, c->d_fstar,
+                   c->d_red, c->d_w, c->d_clock, c->d_U, c->d_G};
+  for (double* p : dbl) if (p) cudaFree(p);
+  if (c->d_faces) cudaFree(c->d_faces);
+  if (c->d_elem_face) cudaFree(c->d_elem_face);
+  if (c->d_elem_nbr) cudaFree(c->d_elem_nbr);
+  if (c->d_minmask) cudaFree(c->d_minmask);
+  if (c->h_out) cudaFreeHost(c->h_out);
+  if (c->h_clock) cudaFreeHost(c->h_clock);
+}
+
+// The RK step sequence for one call: per step, zero the register, five stages
+// of (lift, face, volume+update), advance the clock.
+static cudaError_t enqueue_steps(Ctx& c, double* U, double* G, int nsteps, cudaStream_t s) {
+  cudaError_t err = cudaSuccess;
+  const size_t bytes = sizeof(double) * (size_t)c.E * 5 * c.P;
+  for (int st = 0; st < nsteps; ++st) {
+    if ((err = cudaMemsetAsync(G, 0, bytes, s)) != cudaSuccess) return err;
+    for (int k = 0; k < 5; ++k) {
+      if ((err = launch_lift(c, U, s)) != cudaSuccess) return err;
+      if ((err = launch_face(c, U, s)) != cudaSuccess) return err;
+      StageArgs a{U, U, G, nullptr, c.d_clock, kRkC[k], kRkA[k], kRkB[k], 1};
+      if ((err = launch_volume(c, a, s)) != cudaSuccess) return err;
+    }
+    if ((err = launch_clock_advance(c.d_clock, s)) != cudaSuccess) return err;
+  }
+  return err;
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+struct dg_ctx : public dg::Ctx {};
+
+extern "C" {
+
+dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out) {
+  if (out) *out = nullptr;
+  if (!mesh || !prm || !out) return fail(nullptr, DG_EINVAL, "dg_init: null argument");
+  if (prm->N < 1 || prm->N > 7) return fail(nullptr, DG_EUNSUPPORTED, "dg_init: N must be in 1..7 in this build");
+  if (prm->precision != DG_FP64) return fail(nullptr, DG_EUNSUPPORTED, "dg_init: only DG_FP64 is built");
+  if (prm->surf_flux != DG_FLUX_LLF && prm->surf_flux != DG_FLUX_EC)
+    return fail(nullptr, DG_EINVAL, "dg_init: unknown surface flux");
+  if (prm->source != DG_SOURCE_NONE && prm->source != DG_SOURCE_MMS)
+    return fail(nullptr, DG_EINVAL, "dg_init: unknown source");
+  if (!(prm->gamma > 1.0) || !(prm->R > 0.0) || !(prm->Pr > 0.0) || !(prm->mu >= 0.0))
+    return fail(nullptr, DG_EINVAL, "dg_init: gas constants out of range");
+  if (mesh->n_elems < 1 || mesh->ngeo < 1 || mesh->ngeo > 12 || !mesh->xgeo || !mesh->face_nbr)
+    return fail(nullptr, DG_EINVAL, "dg_init: bad mesh sizes or null arrays");
+  const int E = mesh->n_elems;
+  // connectivity checks: range and reciprocity
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      const int* r = mesh->face_nbr + (size_t)(e * 6 + f) * 3;
+      if (r[0] < 0 || r[0] >= E || r[1] < 0 || r[1] > 5 || r[2] < 0 || r[2] > 7)
+        return fail(nullptr, DG_EMESH, "dg_init: face connectivity out of range");
+      const int* b = mesh->face_nbr + (size_t)(r[0] * 6 + r[1]) * 3;
+      if (b[0] != e || b[1] != f) return fail(nullptr, DG_EMESH, "dg_init: face connectivity not reciprocal");
+      if (r[0] == e && r[1] == f) return fail(nullptr, DG_EMESH, "dg_init: face is its own neighbour");
+    }
+  dg_ctx* c = new (std::nothrow) dg_ctx();
+  if (!c) return fail(nullptr, DG_ENOMEM, "dg_init: host allocation failed");
+  auto bail = [&](dg_status st) {
+    g_init_error = c->err;
+    release(c);
+    delete c;
+    return st;
+  };
+  c->device = device;
+  c->N = prm->N; c->n = prm->N + 1; c->P = c->n * c->n * c->n; c->NN = c->n * c->n; c->E = E;
+  c->prm = *prm;
+  Gas& g = c->gas;
+  g.gamma = prm->gamma; g.R = prm->R; g.Pr = prm->Pr; g.mu = prm->mu;
+  g.gm1 = prm->gamma - 1.0; g.inv_gm1 = 1.0 / g.gm1;
+  g.kappa = prm->gamma * prm->R / (prm->gamma - 1.0) / prm->Pr;
+  g.inv_R = 1.0 / prm->R;
+  g.mms_amp = prm->mms_amp; g.surf_flux = prm->surf_flux; g.source = prm->source;
+  lgl_basis(c->N, c->x, c->w, c->D);
+  // faces: the side with the smaller (e*6 + f) is the master
+  std::vector<FaceInfo> faces;
+  std::vector<int> elem_face((size_t)E * 6), elem_nbr((size_t)E * 6);
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      const int* r = mesh->face_nbr + (size_t)(e * 6 + f) * 3;
+      elem_nbr[e * 6 + f] = r[0] * 8 + r[1];
+      if (e * 6 + f < r[0] * 6 + r[1]) {
+        elem_face[e * 6 + f] = (int)faces.size() * 16 + 8 + r[2];
+        faces.push_back(FaceInfo{e * 8 + f, r[0] * 8 + r[1], r[2], 0});
+      }
+    }
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      const int* r = mesh->face_nbr + (size_t)(e * 6 + f) * 3;
+      if (e * 6 + f > r[0] * 6 + r[1]) elem_face[e * 6 + f] = (elem_face[r[0] * 6 + r[1]] >> 4) * 16 + r[2];
+    }
+  c->nfaces = (int)faces.size();
+  if (cudaSetDevice(device) != cudaSuccess) { fail(c, DG_ECUDA, "dg_init: cudaSetDevice"); return bail(DG_ECUDA); }
+  const size_t P = c->P, NN = c->NN;
+  auto alloc = [&](void** p, size_t bytes, const char* what) -> bool {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) { fail(c, e == cudaErrorMemoryAllocation ? DG_ENOMEM : DG_ECUDA, what, e); return false; }
+    return true;
+  };
+  const int red_rows = 152 * 8;
+  c->red_len = red_rows;
+  if (!alloc((void**)&c->d_D, sizeof(double) * NN, "alloc D") ||
+      !alloc((void**)&c->d_metrics, sizeof(double) * E * 10 * P, "alloc metrics") ||
+      !alloc((void**)&c->d_J, sizeof(double) * E * P, "alloc J") ||
+      !alloc((void**)&c->d_X, sizeof(double) * E * 3 * P, "alloc X") ||
+      !alloc((void**)&c->d_facegeo, sizeof(double) * c->nfaces * 4 * NN, "alloc facegeo") ||
+      !alloc((void**)&c->d_faces, sizeof(FaceInfo) * c->nfaces, "alloc faces") ||
+      !alloc((void**)&c->d_elem_face, sizeof(int) * E * 6, "alloc elem_face") ||
+      !alloc((void**)&c->d_elem_nbr, sizeof(int) * E * 6, "alloc elem_nbr") ||
+      !alloc((void**)&c->d_grad, sizeof(double) * E * 12 * P, "alloc grad") ||
+      !alloc((void**)&c->d_fstar, sizeof(double) * c->nfaces * 5 * NN, "alloc fstar") ||
+      !alloc((void**)&c->d_red, sizeof(double) * (red_rows + 1) * kRedValues, "alloc reduction") ||
+      !alloc((void**)&c->d_w, sizeof(double) * c->n, "alloc w") ||
+      !alloc((void**)&c->d_minmask, sizeof(int), "alloc mask") ||
+      !alloc((void**)&c->d_clock, sizeof(double) * 2, "alloc clock"))
+    return bail(c->err.find("out of memory") != std::string::npos ? DG_ENOMEM : DG_ECUDA);
+  if (cudaMallocHost((void**)&c->h_out, sizeof(double) * 16) != cudaSuccess ||
+      cudaMallocHost((void**)&c->h_clock, sizeof(double) * 2) != cudaSuccess) {
+    fail(c, DG_ENOMEM, "dg_init: pinned host allocation failed");
+    return bail(DG_ENOMEM);
+  }
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    fail(c, DG_ECUDA, "dg_init: stream");
+    return bail(DG_ECUDA);
+  }
+  const int minmask = 1 << 8;
+  double* d_xgeo = nullptr;
+  int* d_bad = nullptr;
+  const size_t m3 = (size_t)(mesh->ngeo + 1) * (mesh->ngeo + 1) * (mesh->ngeo + 1);
+  cudaError_t err = cudaMalloc(&d_xgeo, sizeof(double) * E * 3 * m3);
+  if (err == cudaSuccess) err = cudaMalloc(&d_bad, sizeof(int));
+  if (err == cudaSuccess) err = cudaMemcpyAsync(d_xgeo, mesh->xgeo, sizeof(double) * E * 3 * m3, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(d_bad, 0, sizeof(int), s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_D, c->D.data(), sizeof(double) * NN, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_w, c->w.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_minmask, &minmask, sizeof(int), cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_faces, faces.data(), sizeof(FaceInfo) * c->nfaces, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_elem_face, elem_face.data(), sizeof(int) * E * 6, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_elem_nbr, elem_nbr.data(), sizeof(int) * E * 6, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = setup_kernels(c->N);
+  if (err == cudaSuccess) err = build_geometry(*c, d_xgeo, mesh->ngeo, d_bad, s);
+  int bad = 0;
+  if (err == cudaSuccess) err = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+  if (d_xgeo) cudaFree(d_xgeo);
+  if (d_bad) cudaFree(d_bad);
+  cudaStreamDestroy(s);
+  if (err != cudaSuccess) {
+    fail(c, err == cudaErrorMemoryAllocation ? DG_ENOMEM : DG_ECUDA, "dg_init: geometry", err);
+    return bail(err == cudaErrorMemoryAllocation ? DG_ENOMEM : DG_ECUDA);
+  }
+  if (bad) {
+    fail(c, DG_EMESH, "dg_init: non-positive Jacobian at a node");
+    return bail(DG_EMESH);
+  }
+  c->err = "no error";
+  *out = c;
+  return DG_OK;
+}
+
+dg_status dg_destroy(dg_ctx* c) {
+  if (!c) return DG_EINVAL;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  release(c);
+  delete c;
+  return DG_OK;
+}
+
+size_t dg_state_len(const dg_ctx* c) { return c ? (size_t)c->E * 5 * c->P : 0; }
+
+const char* dg_last_error(const dg_ctx* c) { return c ? c->err.c_str() : g_init_error.c_str(); }
+
+dg_status dg_time_derivative(dg_ctx* c, const double* dU, double* dUt, double t, dg_stream stream) {
+  if (!c || !dU || !dUt) return fail(c, DG_EINVAL, "dg_time_derivative: null argument");
+  if (dU == dUt) return fail(c, DG_EINVAL, "dg_time_derivative: dU and dUt alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  DG_CUDA(launch_set_clock(c->d_clock, t, 0.0, s), c, "clock");
+  DG_CUDA(launch_lift(*c, dU, s), c, "lift kernel");
+  DG_CUDA(launch_face(*c, dU, s), c, "face kernel");
+  StageArgs a{dU, nullptr, nullptr, dUt, c->d_clock, 0.0, 0.0, 0.0, 0};
+  DG_CUDA(launch_volume(*c, a, s), c, "volume kernel");
+  return DG_OK;
+}
+
+dg_status dg_rk_step(dg_ctx* c, double* dU, double* dG, double t, double dt, int32_t nsteps, dg_stream stream) {
+  if (!c || !dU || !dG) return fail(c, DG_EINVAL, "dg_rk_step: null argument");
+  if (nsteps < 0) return fail(c, DG_EINVAL, "dg_rk_step: nsteps < 0");
+  if (dU == dG) return fail(c, DG_EINVAL, "dg_rk_step: dU and dG alias");
+  if (nsteps == 0) return DG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  DG_CUDA(launch_set_clock(c->d_clock, t, dt, s), c, "clock");
+  if (!c->graph || c->graph_U != dU || c->graph_G != dG || c->graph_nsteps != nsteps) {
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    cudaStream_t cs;
+    DG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), c, "capture stream");
+    cudaGraph_t gr = nullptr;
+    cudaError_t err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+      cudaError_t e1 = enqueue_steps(*c, dU, dG, nsteps, cs);
+      err = cudaStreamEndCapture(cs, &gr);
+      if (e1 != cudaSuccess) err = e1;
+    }
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&c->graph, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    cudaStreamDestroy(cs);
+    if (err != cudaSuccess) { c->graph = nullptr; return fail(c, DG_ECUDA, "dg_rk_step: graph capture", err); }
+    c->graph_U = dU; c->graph_G = dG; c->graph_nsteps = nsteps;
+  }
+  DG_CUDA(cudaGraphLaunch(c->graph, s), c, "dg_rk_step: graph launch");
+  return DG_OK;
+}
+
+dg_status dg_advance_host(dg_ctx* c, double* hU, double t, double dt, int32_t nsteps, dg_stream stream) {
+  if (!c || !hU) return fail(c, DG_EINVAL, "dg_advance_host: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * dg_state_len(c);
+  DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  if (!c->d_U) DG_CUDA(cudaMalloc(&c->d_U, bytes), c, "dg_advance_host: state allocation");
+  if (!c->d_G) DG_CUDA(cudaMalloc(&c->d_G, bytes), c, "dg_advance_host: register allocation");
+  DG_CUDA(cudaMemcpyAsync(c->d_U, hU, bytes, cudaMemcpyHostToDevice, s), c, "dg_advance_host: H2D");
+  dg_status st = dg_rk_step(c, c->d_U, c->d_G, t, dt, nsteps, stream);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaMemcpyAsync(hU, c->d_U, bytes, cudaMemcpyDeviceToHost, s), c, "dg_advance_host: D2H");
+  DG_CUDA(cudaStreamSynchronize(s), c, "dg_advance_host: sync");
+  return DG_OK;
+}
+
+dg_status dg_integrals(dg_ctx* c, const double* dU, double* out, dg_stream stream) {
+  if (!c || !dU || !out) return fail(c, DG_EINVAL, "dg_integrals: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  DG_CUDA(launch_integrals(*c, dU, s), c, "integrals kernel");
+  const int rows = reduction_rows(*c);
+  DG_CUDA(cudaMemcpyAsync(c->h_out, c->d_red + (size_t)rows * kRedValues, sizeof(double) * kRedValues,
+                          cudaMemcpyDeviceToHost, s), c, "integrals copy");
+  DG_CUDA(cudaStreamSynchronize(s), c, "integrals sync");
+  const double* h = c->h_out;
+  for (int a = 0; a < 5; ++a) out[a] = h[a];
+  const double vol = h[5];
+  out[5] = 0.5 * h[6] / vol;
+  out[6] = c->prm.mu * h[7] / vol;
+  out[7] = h[8];
+  for (int a = 0; a < 8; ++a)
+    if (!std::isfinite(out[a])) return fail(c, DG_ENONFINITE, "dg_integrals: non-finite value");
+  return DG_OK;
+}
+
+dg_status dg_max_dt(dg_ctx* c, const double* dU, double cfl, double dfl, double* host_dt, dg_stream stream) {
+  if (!c || !dU || !host_dt) return fail(c, DG_EINVAL, "dg_max_dt: null argument");
+  if (!(cfl > 0.0) || !(dfl > 0.0)) return fail(c, DG_EINVAL, "dg_max_dt: cfl and dfl must be > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  DG_CUDA(launch_max_dt(*c, dU, cfl, dfl, s), c, "dt kernel");
+  const int rows = reduction_rows(*c);
+  DG_CUDA(cudaMemcpyAsync(c->h_out, c->d_red + (size_t)rows * 2, sizeof(double) * 2, cudaMemcpyDeviceToHost, s),
+          c, "dt copy");
+  DG_CUDA(cudaStreamSynchronize(s), c, "dt sync");
+  const double lc = c->h_out[0], lv = c->h_out[1];
+  if (!std::isfinite(lc) || !std::isfinite(lv)) return fail(c, DG_ENONFINITE, "dg_max_dt: non-finite value");
+  const double h = 2.0 / (2.0 * c->N + 1.0);
+  double dt = lc > 0.0 ? cfl * h / lc : HUGE_VAL;
+  if (lv > 0.0) dt = std::fmin(dt, dfl * h * h / lv);
+  *host_dt = dt;
+  return DG_OK;
+}
+
+dg_status dg_initial_state(dg_ctx* c, int32_t kind, double prm0, double* dU, dg_stream stream) {
+  if (!c || !dU) return fail(c, DG_EINVAL, "dg_initial_state: null argument");
+  if (kind != DG_IC_TGV && kind != DG_IC_MMS) return fail(c, DG_EINVAL, "dg_initial_state: unknown kind");
+  DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  DG_CUDA(launch_initial_state(*c, kind, prm0, dU, (cudaStream_t)stream), c, "initial state kernel");
+  return DG_OK;
+}
+
+dg_status dg_node_coords(dg_ctx* c, double* dX, dg_stream stream) {
+  if (!c || !dX) return fail(c, DG_EINVAL, "dg_node_coords: null argument");
+  DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  DG_CUDA(cudaMemcpyAsync(dX, c->d_X, sizeof(double) * (size_t)c->E * 3 * c->P, cudaMemcpyDeviceToDevice,
+                          (cudaStream_t)stream), c, "node coords copy");
+  return DG_OK;
+}
+
+dg_status dg_geometry(dg_ctx* c, double* dJa, double* dJ, dg_stream stream) {
+  if (!c) return fail(c, DG_EINVAL, "dg_geometry: null context");
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  const size_t P = c->P;
+  if (dJa)
+    DG_CUDA(cudaMemcpy2DAsync(dJa, sizeof(double) * 9 * P, c->d_metrics, sizeof(double) * 10 * P,
+                              sizeof(double) * 9 * P, c->E, cudaMemcpyDeviceToDevice, s), c, "geometry copy");
+  if (dJ) DG_CUDA(cudaMemcpyAsync(dJ, c->d_J, sizeof(double) * c->E * P, cudaMemcpyDeviceToDevice, s), c, "J copy");
+  return DG_OK;
+}
+
+dg_status dg_profile_stages(dg_ctx* c, double* dU, double* dG, double dt, int32_t reps, float* ms3,
+                            dg_stream stream) {
+  if (!c || !dU || !dG || !ms3 || reps < 1) return fail(c, DG_EINVAL, "dg_profile_stages: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  cudaEvent_t ev[4];
+  for (int a = 0; a < 4; ++a) DG_CUDA(cudaEventCreate(&ev[a]), c, "event");
+  double tot[3] = {0, 0, 0};
+  DG_CUDA(launch_set_clock(c->d_clock, 0.0, dt, s), c, "clock");
+  DG_CUDA(cudaMemsetAsync(dG, 0, sizeof(double) * dg_state_len(c), s), c, "memset");
+  cudaError_t err = cudaSuccess;
+  for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+    const int k = r % 5;
+    StageArgs a{dU, dU, dG, nullptr, c->d_clock, kRkC[k], kRkA[k], kRkB[k], 1};
+    cudaEventRecord(ev[0], s);
+    err = launch_lift(*c, dU, s);
+    cudaEventRecord(ev[1], s);
+    if (err == cudaSuccess) err = launch_face(*c, dU, s);
+    cudaEventRecord(ev[2], s);
+    if (err == cudaSuccess) err = launch_volume(*c, a, s);
+    cudaEventRecord(ev[3], s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(ev[3]);
+    for (int q = 0; q < 3 && err == cudaSuccess; ++q) {
+      float ms = 0.f;
+      err = cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
+      tot[q] += ms;
+    }
+  }
+  for (int a = 0; a < 4; ++a) cudaEventDestroy(ev[a]);
+  if (err != cudaSuccess) return fail(c, DG_ECUDA, "dg_profile_stages", err);
+  for (int q = 0; q < 3; ++q) ms3[q] = (float)(tot[q] / reps);
+  return DG_OK;
+}
+
+}  // extern "C"

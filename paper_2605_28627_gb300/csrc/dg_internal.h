@@ -1,0 +1,104 @@
+// Internal declarations of the DGSEM runtime (context, launch plans).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dgsem.h"
+
+namespace dg {
+
+constexpr int kMaxN = 9;
+
+// Gas constants and derived coefficients, passed by value to kernels.
+struct Gas {
+  double gamma, R, Pr, mu;
+  double gm1;        // gamma - 1
+  double inv_gm1;    // 1 / (gamma - 1)
+  double kappa;      // lambda / mu = c_p / Pr
+  double inv_R;
+  double mms_amp;
+  int surf_flux;
+  int source;
+};
+
+// Face descriptor (master orientation): elements and local faces of both sides
+// packed as e*8 + f, and the orientation code taking a master face node to the
+// slave's node.
+struct FaceInfo {
+  int master;   // eM * 8 + fM
+  int slave;    // eS * 8 + fS
+  int flip;
+  int pad;
+};
+
+// Operands of one stage launch.
+struct StageArgs {
+  const double* U;       // state (read)
+  double* Uw;            // state written by the RK epilogue (== U in place) or NULL
+  double* Gk;            // LSERK register or NULL
+  double* Ut;            // time-derivative output (mode 0) or NULL
+  const double* clock;   // device {t, dt}
+  double c_stage, A, B;  // stage time fraction and LSERK coefficients
+  int mode;              // 0: write Ut; 1: LSERK update
+};
+
+struct Ctx {
+  int device = 0;
+  int N = 0, n = 0, P = 0, NN = 0;
+  int E = 0, nfaces = 0;
+  dg_params prm{};
+  Gas gas{};
+  std::vector<double> x, w, D;   // host LGL basis
+  // device geometry
+  double* d_D = nullptr;         // [n][n]
+  double* d_metrics = nullptr;   // [E][10][P]: J a^d_l at row d*3+l, row 9 = 1/J
+  double* d_J = nullptr;         // [E][P]
+  double* d_X = nullptr;         // [E][3][P]
+  double* d_facegeo = nullptr;   // [F][4][NN]: unit normal (3), surface element
+  FaceInfo* d_faces = nullptr;   // [F]
+  int* d_elem_face = nullptr;    // [E][6]: face_id * 16 + master * 8 + flip (own -> neighbour)
+  int* d_elem_nbr = nullptr;     // [E][6]: e2 * 8 + f2
+  // work buffers
+  double* d_grad = nullptr;      // [E][12][P]: d phi / d x_l, phi = (u, v, w, T), row phi*3+l
+  double* d_fstar = nullptr;     // [F][5][NN]: surface flux times sJ, master orientation
+  double* d_red = nullptr;       // reduction partials [red_len + 1][9]; the last row holds the fold
+  int red_len = 0;               // maximum number of partial rows
+  double* d_w = nullptr;         // [n] LGL weights
+  int* d_minmask = nullptr;      // bit a set: value a of the integrals is a minimum
+  double* d_clock = nullptr;     // {t, dt}
+  double* h_clock = nullptr;     // pinned staging for the clock
+  double* h_out = nullptr;       // pinned staging for reductions
+  // host-buffer path
+  double* d_U = nullptr;
+  double* d_G = nullptr;
+  // captured RK graph
+  cudaGraphExec_t graph = nullptr;
+  const double* graph_U = nullptr;
+  const double* graph_G = nullptr;
+  int graph_nsteps = 0;
+  std::string err;
+};
+
+// Launchers implemented per polynomial degree (dg_operator.cu).
+cudaError_t launch_lift(const Ctx& c, const double* U, cudaStream_t s);
+cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s);
+cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s);
+cudaError_t setup_kernels(int N);
+
+// Geometry kernels (dg_geometry.cu).
+cudaError_t build_geometry(Ctx& c, const double* d_xgeo, int ngeo, int* d_bad, cudaStream_t s);
+
+// Diagnostics kernels (dg_diag.cu).
+cudaError_t launch_integrals(Ctx& c, const double* U, cudaStream_t s);
+cudaError_t launch_max_dt(Ctx& c, const double* U, double cfl, double dfl, cudaStream_t s);
+cudaError_t launch_initial_state(Ctx& c, int kind, double prm0, double* U, cudaStream_t s);
+cudaError_t launch_set_clock(double* clock, double t, double dt, cudaStream_t s);
+cudaError_t launch_clock_advance(double* clock, cudaStream_t s);
+int reduction_rows(const Ctx& c);   // partial rows used by the last reduction
+constexpr int kRedValues = 9;
+
+}  // namespace dg
