@@ -40,7 +40,10 @@ __device__ __forceinline__ R log_mean(R a, R b) {
   if (u < R(1e-4)) {
     F = R(1) + u * (R(1) / R(3) + u * (R(1) / R(5) + u * (R(1) / R(7))));
   } else {
-    F = log(a / b) / (R(2) * f);
+    // ratio form: ln(zeta) and (zeta - 1)/(zeta + 1) see the same rounded zeta,
+    // so its rounding error cancels in the quotient
+    const R z = a / b;
+    F = log(z) / (R(2) * ((z - R(1)) / (z + R(1))));
   }
   return s / (R(2) * F);
 }

@@ -87,11 +87,26 @@ def test_time_derivative_parity_mms_source(orc, dg, N):
     ref = o.time_derivative(U, t=0.37)
     got = s.time_derivative(_cuda(U), t=0.37).cpu().numpy()
     # R of the exact solution is a small residual of large cancelling terms:
-    # scale by the size of the split-form volume term V / J (per variable)
-    _, _, J = o.geometry()
-    V = o.volume_term(U) / J[:, None, :]
-    for v in range(5):
-        assert np.abs(got[:, v] - ref[:, v]).max() < RTOL_R * np.abs(V[:, v]).max(), v
+    # scale by the size of those terms, sum_m |2 D_im| |f . Ja| / J
+    assert (np.abs(got - ref) < RTOL_R * _term_scale(orc, o, U, N)[None, :, None, None, None]).all()
+
+
+def _term_scale(orc, o, U, N):
+    """Per variable: max_i sum_m |2 D_im| x 3 max |f(q) . Ja^d| / min J, the size
+    of the individual flux-differencing terms whose sum is R."""
+    _, Ja, J = o.geometry()
+    _, _, D = orc.basis(N)
+    Uf = U.reshape(U.shape[0], 5, -1)
+    r = Uf[:, 0]
+    u = Uf[:, 1:4] / r[:, None]
+    p = 0.4 * (Uf[:, 4] - 0.5 * r * (u ** 2).sum(1))
+    out = np.zeros(5)
+    for d in range(3):
+        un = np.einsum("elp,elp->ep", u, Ja[:, d])
+        f = [r * un] + [Uf[:, 1 + a] * un + p * Ja[:, d, a] for a in range(3)] + [(Uf[:, 4] + p) * un]
+        for v in range(5):
+            out[v] = max(out[v], np.abs(f[v]).max())
+    return 3 * out * 2 * np.abs(D).sum(1).max() / J.min()
 
 
 def test_free_stream_on_gpu(dg):
