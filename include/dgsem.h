@@ -153,6 +153,26 @@ dg_status dg_profile_stages(dg_ctx* ctx, double* dU, double* dG, double dt, int3
  * the arithmetic roof for the FP64-pipe-bound kernels.  Synchronous. */
 dg_status dg_probe_peaks(int device, double* host_out2);
 
+/* Conservation totals sum_nodes w_i w_j w_k J q_v (v = rho, rho u, rho v,
+ * rho w, rho E), the first five values of dg_integrals, for callers that may
+ * not allocate device memory while they run: a host framework that owns every
+ * device buffer and only lends inputs and outputs to foreign code, or an
+ * application that keeps the allocator out of its time loop.  The paper has
+ * no counterpart; this entry exists for such callers.
+ *   dU: device state [n_elems][5][P]; dJ: device Jacobian [n_elems][P] (e.g.
+ *   from dg_geometry); N: degree 1..9; dOut5: device, receives 5 doubles.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Its only
+ * scratch is a fixed device array of n_elems <= 131072 rows of 5 doubles
+ * (5 MiB) that every GPU loading the library holds until the process exits;
+ * larger meshes are rejected with DG_EINVAL.  The array is shared by all
+ * calls on a device and keeps the last call's contents, so calls that
+ * overlap on the GPU (other streams, other threads) race.  The first call on
+ * each device looks up the array's device address with that device current
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Runs on the current device and stream; does not synchronise. */
+dg_status dg_conserved_totals_noalloc(const double* dU, const double* dJ, int32_t N, int32_t n_elems,
+                                      double* dOut5, dg_stream stream);
+
 /* Human-readable description of the last error on ctx (or of the last failed
  * dg_init when ctx is NULL).  Never NULL. */
 const char* dg_last_error(const dg_ctx* ctx);

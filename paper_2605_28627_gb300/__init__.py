@@ -29,7 +29,7 @@ IC_TGV, IC_MMS = 0, 1
 # Every symbol that include/dgsem.h declares.
 EXPORTS = ["dg_init", "dg_destroy", "dg_state_len", "dg_time_derivative", "dg_rk_step", "dg_advance_host",
            "dg_integrals", "dg_max_dt", "dg_initial_state", "dg_node_coords", "dg_geometry", "dg_profile_stages",
-           "dg_probe_peaks", "dg_last_error"]
+           "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_last_error"]
 
 
 class DGError(RuntimeError):
@@ -77,11 +77,12 @@ def load(build_if_missing: bool = True):
     L.dg_geometry.argtypes = [vp, vp, vp, vp]
     L.dg_profile_stages.argtypes = [vp, vp, vp, f64, i32, C.POINTER(C.c_float), vp]
     L.dg_probe_peaks.argtypes = [C.c_int, dp]
+    L.dg_conserved_totals_noalloc.argtypes = [vp, vp, i32, i32, vp, vp]
     L.dg_last_error.argtypes = [vp]
     L.dg_last_error.restype = C.c_char_p
     for name in ("dg_init", "dg_destroy", "dg_time_derivative", "dg_rk_step", "dg_advance_host", "dg_integrals",
                  "dg_max_dt", "dg_initial_state", "dg_node_coords", "dg_geometry", "dg_profile_stages",
-                 "dg_probe_peaks"):
+                 "dg_probe_peaks", "dg_conserved_totals_noalloc"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -239,3 +240,17 @@ def probe_peaks(device: int = 0):
     if st != DG_OK:
         raise DGError(st, "dg_probe_peaks failed")
     return float(out[0]), float(out[1])
+
+
+def conserved_totals_noalloc(U, J, N: int, out=None, stream=None):
+    """Conservation totals of U (device float64) with Jacobian J (device,
+    [E, P]) through the allocation-free entry point; returns the device
+    tensor `out` (5 doubles)."""
+    import torch
+    L = load()
+    if out is None:
+        out = torch.empty(5, dtype=torch.float64, device=U.device)
+    st = L.dg_conserved_totals_noalloc(_ptr(U), _ptr(J), int(N), int(J.shape[0]), _ptr(out), _stream_handle(stream))
+    if st != DG_OK:
+        raise DGError(st, "dg_conserved_totals_noalloc rejected its arguments")
+    return out
