@@ -88,6 +88,7 @@ cudaError_t launch_lift(const Ctx& c, const double* U, cudaStream_t s);
 cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s);
 cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s);
 cudaError_t setup_kernels(int N);
+cudaError_t setup_volume(int N);
 
 // Geometry kernels (dg_geometry.cu).
 cudaError_t build_geometry(Ctx& c, const double* d_xgeo, int ngeo, int* d_bad, cudaStream_t s);

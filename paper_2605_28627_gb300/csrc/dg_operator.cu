@@ -2,9 +2,8 @@
 // volume or face node:
 //   lift   : BR1 lifting of (u, v, w, T) -> grad          (element kernel)
 //   face   : Riemann + averaged viscous flux -> fstar     (face-node kernel)
-//   volume : split-form volume integral + viscous volume term + surface
-//            integral + Jacobian + source, then write U_t or apply the LSERK
-//            stage update                                   (element kernel)
+// The volume kernel (split-form volume integral, surface integral, Jacobian,
+// source, LSERK update) is in dg_volume.cu.
 #include "dg_physics.cuh"
 
 namespace dg {
@@ -167,157 +166,6 @@ k_face(const double* __restrict__ U, const double* __restrict__ grad, const Face
 }
 
 // ---------------------------------------------------------------------------
-// Volume kernel: split-form flux differencing with the Chandrashekar flux and
-// the metric average 1/2 (Ja^d_i + Ja^d_m), the viscous volume term
-// -sum_m D_im (f_v . Ja^d)_m, the surface integral
-// sum_faces (F*_out - (f - f_v) . n sJ)/w_0, U_t = -(.)/J + Q, then either
-// U_t is stored (mode 0) or the LSERK stage G <- A G + dt U_t, U <- U + B G.
-template <int N>
-__global__ void __launch_bounds__(Shape<N>::THREADS)
-k_volume(StageArgs a, const double* __restrict__ metrics, const double* __restrict__ grad,
-         const double* __restrict__ fstar, const int* __restrict__ elem_face, const double* __restrict__ X,
-         const double* __restrict__ Dg, int E, Gas g, double inv_w0) {
-  using S = Shape<N>;
-  constexpr int n = S::n, P = S::P, NN = S::NN, EPB = S::EPB;
-  extern __shared__ double smem[];
-  double* sD = smem;                              // n*n
-  double* sprim = sD + ((n * n + 1) & ~1);        // [EPB][6][P]: rho, u, v, w, p, beta
-  double* sJa = sprim + EPB * 6 * P;              // [EPB][9][P]
-  double* sFv = sJa + EPB * 9 * P;                // [EPB][3][4][P]: (f_v . Ja^d), momentum + energy
-  const int le = threadIdx.x / P, id = threadIdx.x % P;
-  const int e = blockIdx.x * EPB + le;
-  const bool active = e < E;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = Dg[t];
-  double q[5] = {0, 0, 0, 0, 0}, Ja[9], iJ = 0, u = 0, v = 0, w = 0, p = 0;
-  double* mp = sprim + le * 6 * P;
-  double* mJ = sJa + le * 9 * P;
-  double* mF = sFv + le * 12 * P;
-  if (active) {
-#pragma unroll
-    for (int r = 0; r < 5; ++r) q[r] = a.U[((size_t)e * 5 + r) * P + id];
-    const double* mt = metrics + (size_t)e * 10 * P + id;
-#pragma unroll
-    for (int r = 0; r < 9; ++r) { Ja[r] = mt[r * P]; mJ[r * P + id] = Ja[r]; }
-    iJ = mt[9 * P];
-    const double ir = 1.0 / q[0];
-    u = q[1] * ir; v = q[2] * ir; w = q[3] * ir;
-    p = g.gm1 * (q[4] - 0.5 * (q[1] * u + q[2] * v + q[3] * w));
-    mp[0 * P + id] = q[0]; mp[1 * P + id] = u; mp[2 * P + id] = v; mp[3 * P + id] = w;
-    mp[4 * P + id] = p; mp[5 * P + id] = 0.5 * q[0] / p;
-    double gr[12];
-    const double* gg = grad + (size_t)e * 12 * P + id;
-#pragma unroll
-    for (int r = 0; r < 12; ++r) gr[r] = gg[r * P];
-    const double lam = g.mu * g.kappa;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      double fv[4];
-      visc_flux<double>(gr, u, v, w, g.mu, lam, Ja[d * 3], Ja[d * 3 + 1], Ja[d * 3 + 2], fv);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) mF[(d * 4 + c) * P + id] = fv[c];
-    }
-  } else {
-#pragma unroll
-    for (int r = 0; r < 9; ++r) Ja[r] = 0.0;
-  }
-  __syncthreads();
-  if (!active) return;
-  const int i = id % n, j = (id / n) % n, k = id / (n * n);
-  const int ijk[3] = {i, j, k};
-  NodePrim<double> me{mp[id], u, v, w, p, mp[5 * P + id]};
-  double acc[5] = {0, 0, 0, 0, 0};
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int row = ijk[d];
-#pragma unroll 1
-    for (int m = 0; m < n; ++m) {
-      const int mid = d == 0 ? vidx<n>(m, j, k) : (d == 1 ? vidx<n>(i, m, k) : vidx<n>(i, j, m));
-      const double Dim = sD[row * n + m];
-      NodePrim<double> ot{mp[mid], mp[P + mid], mp[2 * P + mid], mp[3 * P + mid], mp[4 * P + mid], mp[5 * P + mid]};
-      const double nx = 0.5 * (Ja[d * 3] + mJ[(d * 3) * P + mid]);
-      const double ny = 0.5 * (Ja[d * 3 + 1] + mJ[(d * 3 + 1) * P + mid]);
-      const double nz = 0.5 * (Ja[d * 3 + 2] + mJ[(d * 3 + 2) * P + mid]);
-      double fs[5];
-      ec_flux<double>(me, ot, nx, ny, nz, g.inv_gm1, fs);
-      const double D2 = 2.0 * Dim;
-      acc[0] += D2 * fs[0];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[1 + c] += D2 * fs[1 + c] - Dim * mF[(d * 4 + c) * P + mid];
-    }
-  }
-  // surface integral
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int id_d = ijk[d];
-    if (id_d != 0 && id_d != N) continue;
-    const int s = id_d == N ? 1 : 0;
-    const int f = 2 * d + s;
-    const int code = elem_face[e * 6 + f];
-    const int fid = code >> 4;
-    const int pp = d == 0 ? j : i;
-    const int qq = d == 2 ? j : k;
-    double Fo[5];
-    if (code & 8) {
-      const double* fsr = fstar + (size_t)fid * 5 * NN + pp + n * qq;
-#pragma unroll
-      for (int c = 0; c < 5; ++c) Fo[c] = fsr[c * NN];
-    } else {
-      int p2, q2;
-      apply_flip<n>(code & 7, pp, qq, p2, q2);
-      const double* fsr = fstar + (size_t)fid * 5 * NN + p2 + n * q2;
-#pragma unroll
-      for (int c = 0; c < 5; ++c) Fo[c] = -fsr[c * NN];
-    }
-    const double sg = s ? 1.0 : -1.0;
-    double fe[5];
-    euler_flux<double>(q, u, v, w, p, sg * Ja[d * 3], sg * Ja[d * 3 + 1], sg * Ja[d * 3 + 2], fe);
-    acc[0] += (Fo[0] - fe[0]) * inv_w0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[1 + c] += (Fo[1 + c] - fe[1 + c] + sg * mF[(d * 4 + c) * P + id]) * inv_w0;
-  }
-  const double t = a.clock[0] + a.c_stage * a.clock[1];
-  double src[5] = {0, 0, 0, 0, 0};
-  if (g.source == DG_SOURCE_MMS) {
-    const double x = X[((size_t)e * 3 + 0) * P + id], y = X[((size_t)e * 3 + 1) * P + id],
-                 z = X[((size_t)e * 3 + 2) * P + id];
-    // density wave rho = 2 + A sin(pi (x+y+z-t)), u = (1,1,1), p = 1:
-    // residual of Eq. 1 = [2r', 2r', 2r', 2r', 3r' - lambda Lap T], r' = pi A cos(phi)
-    double sphi, cphi;
-    sincospi(x + y + z - t, &sphi, &cphi);
-    const double A = g.mms_amp;
-    const double rho = 2.0 + A * sphi;
-    const double rp = M_PI * A * cphi;
-    const double lapT = 3.0 * g.inv_R * (M_PI * M_PI * A * sphi + 2.0 * rp * rp / rho) / (rho * rho);
-    src[0] = src[1] = src[2] = src[3] = 2.0 * rp;
-    src[4] = 3.0 * rp - g.mu * g.kappa * lapT;
-  }
-  if (a.mode == 0) {
-#pragma unroll
-    for (int c = 0; c < 5; ++c) a.Ut[((size_t)e * 5 + c) * P + id] = src[c] - acc[c] * iJ;
-  } else {
-    const double dt = a.clock[1];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      const size_t o = ((size_t)e * 5 + c) * P + id;
-      const double gk = a.A * a.Gk[o] + dt * (src[c] - acc[c] * iJ);
-      a.Gk[o] = gk;
-      a.Uw[o] = q[c] + a.B * gk;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-template <int N>
-static size_t volume_smem() {
-  using S = Shape<N>;
-  return sizeof(double) * (((S::n * S::n + 1) & ~1) + S::EPB * (6 + 9 + 12) * S::P);
-}
-
-template <int N>
-static cudaError_t setup_N() {
-  return cudaFuncSetAttribute(k_volume<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)volume_smem<N>());
-}
-
 template <int N>
 static cudaError_t lift_N(const Ctx& c, const double* U, cudaStream_t s) {
   using S = Shape<N>;
@@ -335,15 +183,6 @@ static cudaError_t face_N(const Ctx& c, const double* U, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int N>
-static cudaError_t volume_N(const Ctx& c, const StageArgs& a, cudaStream_t s) {
-  using S = Shape<N>;
-  const int blocks = (c.E + S::EPB - 1) / S::EPB;
-  k_volume<N><<<blocks, S::THREADS, volume_smem<N>(), s>>>(a, c.d_metrics, c.d_grad, c.d_fstar, c.d_elem_face,
-                                                           c.d_X, c.d_D, c.E, c.gas, 1.0 / c.w[0]);
-  return cudaGetLastError();
-}
-
 #define DG_DISPATCH(FN, ...)                 \
   switch (c.N) {                             \
     case 1: return FN<1>(__VA_ARGS__);       \
@@ -358,18 +197,6 @@ static cudaError_t volume_N(const Ctx& c, const StageArgs& a, cudaStream_t s) {
 
 cudaError_t launch_lift(const Ctx& c, const double* U, cudaStream_t s) { DG_DISPATCH(lift_N, c, U, s) }
 cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s) { DG_DISPATCH(face_N, c, U, s) }
-cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s) { DG_DISPATCH(volume_N, c, a, s) }
-cudaError_t setup_kernels(int N) {
-  switch (N) {
-    case 1: return setup_N<1>();
-    case 2: return setup_N<2>();
-    case 3: return setup_N<3>();
-    case 4: return setup_N<4>();
-    case 5: return setup_N<5>();
-    case 6: return setup_N<6>();
-    case 7: return setup_N<7>();
-    default: return cudaErrorInvalidValue;
-  }
-}
+cudaError_t setup_kernels(int N) { return setup_volume(N); }
 
 }  // namespace dg
