@@ -43,6 +43,11 @@ def build_mesh(N):
     return box_mesh(K_ELEMS, N, deform="sinprod", rotate_seed=MMS_SEED)
 
 
+# DRAM bytes (read + write) per launch of the volume kernel from one ncu capture
+# of the current kernel version on this workload; absent = not captured.
+MEASURED_TRAFFIC = {(7, "fp64"): 619.648768e6 + 145.288448e6}
+
+
 # ---------------------------------------------------------------------------
 # Algorithmic FP64 operation count of the volume kernel per node and stage
 # (FMA = 2 flops; a divide, square root or logarithm counts as 1).  The
@@ -253,8 +258,8 @@ def main():
     vol_flops = volume_flops_per_dof(N) * dof
     achieved = vol_flops / (ms3[2] * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None,
-                "kernel": "k_volume<%d> (split-form volume + surface + Jacobian + LSERK update)" % N,
+                "frac": achieved / fp64_peak, "traffic": MEASURED_TRAFFIC.get((N, "fp64")),
+                "kernel": "k_volume2<%d> (split-form volume + surface + Jacobian + LSERK update)" % N,
                 "peak_source": "measured FP64 DFMA chain throughput on this GPU (dg_probe_peaks)",
                 "stage_ms": {"lift": ms3[0], "face": ms3[1], "volume": ms3[2]}}
 
