@@ -189,6 +189,58 @@ def run_reference(args, world, rank):
     return 0
 
 
+def run_tgv_large(args, local):
+    """Large Taylor-Green vortex: 48^3 Cartesian elements, N=7 (56.6 M nodes),
+    Ma 0.1, Re 1600, LSERK4-5 at CFL 0.9 (dt from the initial state), run once
+    with the FP64 operator and once with the FP32 operator.  Reports PID of
+    both and the error of the kinetic-energy dissipation rate
+    eps = -dE_k/dt (central differences of the per-step E_k):
+    max_t |eps_32 - eps_64| / max_t |eps_64|."""
+    import torch
+    import paper_2605_28627_gb300 as dg
+    from workloads import box_mesh, tgv_params
+    K, N, nsteps = 48, 7, args.tgv_steps
+    prm = tgv_params(Ma=0.1, Re=1600.0)
+    mesh = box_mesh(K, 1, lo=0.0, hi=2 * math.pi)
+    dofs = mesh.n_elems * (N + 1) ** 3
+    out, hist, dt = {}, {}, None
+    for name, prec in (("fp64", dg.FP64), ("fp32op", dg.FP32OP)):
+        s = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], precision=prec,
+                      device=local)
+        st = torch.cuda.Stream(device="cuda:%d" % local)
+        U = s.initial_state("tgv", prm["p0"], stream=st)
+        G = torch.empty_like(U)
+        if dt is None:
+            dt = s.max_dt(U, cfl=0.9, dfl=0.9, stream=st)
+        ek = [s.integrals(U, stream=st)[5]]
+        ms_tot = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for k in range(nsteps):
+            e0.record(st)
+            s.rk_step(U, G, k * dt, dt, 1, stream=st)
+            e1.record(st)
+            e1.synchronize()
+            ms_tot += e0.elapsed_time(e1)
+            ek.append(s.integrals(U, stream=st)[5])
+        hist[name] = np.array(ek)
+        rate = dofs * 5 * nsteps / (ms_tot * 1e-3)
+        out[name] = {"dof_stage_per_s": rate, "pid_ns": 1e9 / rate, "ms_per_step": ms_tot / nsteps,
+                     "ek_final": float(ek[-1])}
+        del U, G
+        s.close()
+        torch.cuda.empty_cache()
+    eps = {k: -(v[2:] - v[:-2]) / (2 * dt) for k, v in hist.items()}
+    err = float(np.abs(eps["fp32op"] - eps["fp64"]).max() / np.abs(eps["fp64"]).max())
+    line = {"experiment": "Taylor-Green vortex 48^3 elements, N=7, Ma 0.1, Re 1600, %d LSERK4-5 steps" % nsteps,
+            "dof": dofs, "dt": dt, "fp64": out["fp64"], "fp32op": out["fp32op"],
+            "speedup_fp32op_vs_fp64": out["fp64"]["ms_per_step"] / out["fp32op"]["ms_per_step"],
+            "dissipation_rate_rel_err": err,
+            "ek_rel_diff_final": abs(out["fp32op"]["ek_final"] - out["fp64"]["ek_final"]) / out["fp64"]["ek_final"],
+            "eps_fp64_first_last": [float(eps["fp64"][0]), float(eps["fp64"][-1])]}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,9 +250,13 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", default="3,4,5,6,7", help="extra orders timed for the per-N table ('' = none)")
+    ap.add_argument("--tgv-large", action="store_true", help="run the 48^3, N=7 FP64-vs-FP32 Taylor-Green study")
+    ap.add_argument("--tgv-steps", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args.gpus)
+    if args.tgv_large:
+        return run_tgv_large(args, local) if rank == 0 else 0
     if args.impl == "reference":
         return run_reference(args, world, rank)
 
@@ -276,6 +332,8 @@ def main():
     e2e = {"value": world * dof * 5 * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": nb,
            "d2h_bytes_per_step": nb}
 
+    fp32 = fp32_operator_rate(dg, N, local, prm, U0, args.steps, value / world) if rank == 0 else None
+
     sweep = {}
     if args.sweep and rank == 0:
         for Ns in [int(v) for v in args.sweep.split(",") if v]:
@@ -303,12 +361,50 @@ def main():
                        "l2": "inputs larger than L2: %.0f MB of state, metrics, gradients and face data touched "
                              "per stage" % working_set_mb(solver)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-            "clocks": clk, "sweep": sweep,
+            "clocks": clk, "sweep": sweep, "fp32_operator": fp32,
             "peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
         }
         print(json.dumps(line))
     solver.close()
     return 0
+
+
+def fp32_operator_rate(dg, N, dev, prm, U0, steps, fp64_rate):
+    """The FP32-operator path on the same workload: throughput, speedup over
+    the FP64 path, and its deviation from the FP64 path after warm-up + steps."""
+    import torch
+    mesh = build_mesh(N)
+    out = {}
+    results = {}
+    for name, prec in (("fp64", dg.FP64), ("fp32op", dg.FP32OP)):
+        s = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=dg.SOURCE_MMS,
+                      precision=prec, device=dev)
+        st = torch.cuda.Stream(device="cuda:%d" % dev)
+        with torch.cuda.stream(st):
+            U = U0.clone()
+            G = torch.empty_like(U)
+        st.synchronize()
+        for i in range(3):
+            s.rk_step(U, G, i * DT, DT, 1, stream=st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for i in range(steps):
+            s.rk_step(U, G, (3 + i) * DT, DT, 1, stream=st)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        results[name] = (U, s.integrals(U, stream=st), ms)
+        s.close()
+    dofs = mesh.n_elems * (N + 1) ** 3
+    U64, I64, ms64 = results["fp64"]
+    U32, I32, ms32 = results["fp32op"]
+    rate = dofs * 5 / (ms32 * 1e-3)
+    out = {"value": rate, "unit": UNIT, "pid_ns": 1e9 / rate, "speedup_vs_fp64": ms64 / ms32,
+           "steps_compared": 3 + steps,
+           "max_rel_state_diff_vs_fp64": float((U32 - U64).abs().max() / U64.abs().max()),
+           "ek_rel_diff_vs_fp64": float(abs(I32[5] - I64[5]) / abs(I64[5])),
+           "note": "same workload and steps as the headline; operator arithmetic FP32, state/RK/reductions FP64"}
+    return out
 
 
 def working_set_mb(s):

@@ -98,9 +98,9 @@ static dg_status fail(Ctx* c, dg_status st, const char* what, cudaError_t e = cu
 static void release(Ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
-  double* dbl[] = {c->d_D, c->d_metrics, c->d_J, c->d_X, c->d_facegeo, c->d_grad, c->d_fstar,
-                   c->d_red, c->d_w, c->d_clock, c->d_U, c->d_G};
-  for (double* p : dbl) if (p) cudaFree(p);
+  void* bufs[] = {c->d_D, c->d_metrics, c->d_J, c->d_X, c->d_facegeo, c->d_metrics_f, c->d_facegeo_f,
+                  c->d_grad, c->d_fstar, c->d_red, c->d_w, c->d_clock, c->d_U, c->d_G};
+  for (void* p : bufs) if (p) cudaFree(p);
   if (c->d_faces) cudaFree(c->d_faces);
   if (c->d_elem_face) cudaFree(c->d_elem_face);
   if (c->d_elem_nbr) cudaFree(c->d_elem_nbr);
@@ -139,7 +139,8 @@ dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx*
   if (out) *out = nullptr;
   if (!mesh || !prm || !out) return fail(nullptr, DG_EINVAL, "dg_init: null argument");
   if (prm->N < 1 || prm->N > 7) return fail(nullptr, DG_EUNSUPPORTED, "dg_init: N must be in 1..7 in this build");
-  if (prm->precision != DG_FP64) return fail(nullptr, DG_EUNSUPPORTED, "dg_init: only DG_FP64 is built");
+  if (prm->precision != DG_FP64 && prm->precision != DG_FP32OP)
+    return fail(nullptr, DG_EINVAL, "dg_init: unknown precision");
   if (prm->surf_flux != DG_FLUX_LLF && prm->surf_flux != DG_FLUX_EC)
     return fail(nullptr, DG_EINVAL, "dg_init: unknown surface flux");
   if (prm->source != DG_SOURCE_NONE && prm->source != DG_SOURCE_MMS)
@@ -217,7 +218,10 @@ dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx*
       !alloc((void**)&c->d_red, sizeof(double) * (red_rows + 1) * kRedValues, "alloc reduction") ||
       !alloc((void**)&c->d_w, sizeof(double) * c->n, "alloc w") ||
       !alloc((void**)&c->d_minmask, sizeof(int), "alloc mask") ||
-      !alloc((void**)&c->d_clock, sizeof(double) * 2, "alloc clock"))
+      !alloc((void**)&c->d_clock, sizeof(double) * 2, "alloc clock") ||
+      (prm->precision == DG_FP32OP &&
+       (!alloc((void**)&c->d_metrics_f, sizeof(float) * E * 10 * P, "alloc metrics (fp32)") ||
+        !alloc((void**)&c->d_facegeo_f, sizeof(float) * c->nfaces * 4 * NN, "alloc facegeo (fp32)"))))
     return bail(c->err.find("out of memory") != std::string::npos ? DG_ENOMEM : DG_ECUDA);
   if (cudaMallocHost((void**)&c->h_out, sizeof(double) * 16) != cudaSuccess ||
       cudaMallocHost((void**)&c->h_clock, sizeof(double) * 2) != cudaSuccess) {
@@ -245,6 +249,11 @@ dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx*
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_elem_nbr, elem_nbr.data(), sizeof(int) * E * 6, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = setup_kernels(c->N);
   if (err == cudaSuccess) err = build_geometry(*c, d_xgeo, mesh->ngeo, d_bad, s);
+  if (err == cudaSuccess && prm->precision == DG_FP32OP) {
+    err = launch_to_float(c->d_metrics, c->d_metrics_f, (size_t)E * 10 * P, s);
+    if (err == cudaSuccess) err = launch_to_float(c->d_facegeo, c->d_facegeo_f, (size_t)c->nfaces * 4 * NN, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  }
   int bad = 0;
   if (err == cudaSuccess) err = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
   if (d_xgeo) cudaFree(d_xgeo);

@@ -197,7 +197,7 @@ static int red_blocks(const Ctx& c) {
 template <int N>
 static cudaError_t integrals_N(Ctx& c, const double* U, double* d_w, cudaStream_t s) {
   const int nb = red_blocks(c);
-  k_integrals<N><<<nb, kRedThreads, 0, s>>>(U, c.d_J, c.d_grad, d_w, c.d_red, c.E, c.gas.gm1);
+  k_integrals<N><<<nb, kRedThreads, 0, s>>>(U, c.d_J, (const double*)c.d_grad, d_w, c.d_red, c.E, c.gas.gm1);
   return cudaGetLastError();
 }
 
@@ -212,7 +212,7 @@ static cudaError_t dt_N(Ctx& c, const double* U, cudaStream_t s) {
 }
 
 cudaError_t launch_integrals(Ctx& c, const double* U, cudaStream_t s) {
-  cudaError_t err = launch_lift(c, U, s);
+  cudaError_t err = launch_lift_fp64(c, U, s);   // diagnostics stay FP64 on every path
   if (err != cudaSuccess) return err;
   double* d_w = c.d_w;
   switch (c.N) {

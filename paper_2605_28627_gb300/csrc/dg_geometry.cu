@@ -139,6 +139,18 @@ static cudaError_t geometry_N(Ctx& c, const double* d_xgeo, int ngeo, const doub
   return cudaGetLastError();
 }
 
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    b[t] = (float)a[t];
+}
+
+// FP32 copy of FP64 geometry for the FP32-operator path.
+cudaError_t launch_to_float(const double* a, float* b, size_t n, cudaStream_t s) {
+  const size_t blocks = (n + 255) / 256;
+  k_to_float<<<(unsigned)(blocks < 152 * 32 ? blocks : 152 * 32), 256, 0, s>>>(a, b, n);
+  return cudaGetLastError();
+}
+
 cudaError_t build_geometry(Ctx& c, const double* d_xgeo, int ngeo, int* d_bad, cudaStream_t s) {
   // Lagrange interpolation matrix from ngeo+1 equispaced points to the LGL nodes.
   const int m = ngeo + 1;

@@ -59,12 +59,14 @@ struct Ctx {
   double* d_J = nullptr;         // [E][P]
   double* d_X = nullptr;         // [E][3][P]
   double* d_facegeo = nullptr;   // [F][4][NN]: unit normal (3), surface element
+  float* d_metrics_f = nullptr;  // FP32 copies for the FP32-operator path
+  float* d_facegeo_f = nullptr;
   FaceInfo* d_faces = nullptr;   // [F]
   int* d_elem_face = nullptr;    // [E][6]: face_id * 16 + master * 8 + flip (own -> neighbour)
   int* d_elem_nbr = nullptr;     // [E][6]: e2 * 8 + f2
   // work buffers
-  double* d_grad = nullptr;      // [E][12][P]: d phi / d x_l, phi = (u, v, w, T), row phi*3+l
-  double* d_fstar = nullptr;     // [F][5][NN]: surface flux times sJ, master orientation
+  void* d_grad = nullptr;        // [E][12][P]: d phi / d x_l, phi = (u, v, w, T), row phi*3+l (operator type)
+  void* d_fstar = nullptr;       // [F][5][NN]: surface flux times sJ, master orientation (operator type)
   double* d_red = nullptr;       // reduction partials [red_len + 1][9]; the last row holds the fold
   int red_len = 0;               // maximum number of partial rows
   double* d_w = nullptr;         // [n] LGL weights
@@ -85,6 +87,7 @@ struct Ctx {
 
 // Launchers implemented per polynomial degree (dg_operator.cu).
 cudaError_t launch_lift(const Ctx& c, const double* U, cudaStream_t s);
+cudaError_t launch_lift_fp64(const Ctx& c, const double* U, cudaStream_t s);   // diagnostics: always FP64
 cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s);
 cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s);
 cudaError_t setup_kernels(int N);
@@ -92,6 +95,7 @@ cudaError_t setup_volume(int N);
 
 // Geometry kernels (dg_geometry.cu).
 cudaError_t build_geometry(Ctx& c, const double* d_xgeo, int ngeo, int* d_bad, cudaStream_t s);
+cudaError_t launch_to_float(const double* a, float* b, size_t n, cudaStream_t s);
 
 // Diagnostics kernels (dg_diag.cu).
 cudaError_t launch_integrals(Ctx& c, const double* U, cudaStream_t s);

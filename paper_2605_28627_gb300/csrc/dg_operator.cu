@@ -17,40 +17,57 @@ struct Shape {
   static constexpr int THREADS = EPB * P;
 };
 
+// rcp for the operator type: FP64 by hardware approximation + one cubic
+// Newton-Raphson step (below 1 ulp); FP32 by the approximation alone (1 ulp).
+__device__ __forceinline__ double rcp_lf(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+__device__ __forceinline__ float rcp_lf(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // ---------------------------------------------------------------------------
 // BR1 lifting (Sec. 3.1, Eq. 3), strong form with the non-conservative volume
 // part: g_l = (1/J)[ sum_d Ja^d_l D_d phi + sum_faces (phi* - phi) n_l sJ / w_0 ]
 // with phi* = (phi + phi_nbr)/2 and the element's own outward n sJ = (2s-1) Ja^d.
-template <int N>
+// R is the operator arithmetic; metrics and the output gradients are in R.
+template <int N, typename R>
 __global__ void __launch_bounds__(Shape<N>::THREADS)
-k_lift(const double* __restrict__ U, const double* __restrict__ metrics, const int* __restrict__ elem_nbr,
-       const int* __restrict__ elem_face, const double* __restrict__ Dg, double* __restrict__ grad, int E,
-       Gas g, double inv_w0) {
+k_lift(const double* __restrict__ U, const R* __restrict__ metrics, const int* __restrict__ elem_nbr,
+       const int* __restrict__ elem_face, const double* __restrict__ Dg, R* __restrict__ grad, int E, Gas g,
+       double inv_w0d) {
   using S = Shape<N>;
   constexpr int n = S::n, P = S::P;
-  __shared__ double sD[n * n];
-  __shared__ double sphi[S::EPB][4][P];
+  __shared__ R sD[n * n];
+  __shared__ R sphi[S::EPB][4][P];
   const int le = threadIdx.x / P, id = threadIdx.x % P;
   const int e = blockIdx.x * S::EPB + le;
   const bool active = e < E;
-  for (int a = threadIdx.x; a < n * n; a += blockDim.x) sD[a] = Dg[a];
-  double phi[4] = {0, 0, 0, 0};
+  for (int a = threadIdx.x; a < n * n; a += blockDim.x) sD[a] = R(Dg[a]);
+  const R gm1 = R(g.gm1), inv_R = R(g.inv_R), inv_w0 = R(inv_w0d);
+  R phi[4] = {0, 0, 0, 0};
   if (active) {
     const double* q = U + (size_t)e * 5 * P + id;
-    const double rho = q[0], ir = 1.0 / rho;
-    const double u = q[P] * ir, v = q[2 * P] * ir, w = q[3 * P] * ir;
-    const double p = g.gm1 * (q[4 * P] - 0.5 * (q[P] * u + q[2 * P] * v + q[3 * P] * w));
-    phi[0] = u; phi[1] = v; phi[2] = w; phi[3] = p * ir * g.inv_R;
+    const R rho = R(q[0]), ir = rcp_lf(rho);
+    const R m0 = R(q[P]), m1 = R(q[2 * P]), m2 = R(q[3 * P]);
+    const R u = m0 * ir, v = m1 * ir, w = m2 * ir;
+    const R p = gm1 * (R(q[4 * P]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
+    phi[0] = u; phi[1] = v; phi[2] = w; phi[3] = p * ir * inv_R;
     for (int a = 0; a < 4; ++a) sphi[le][a][id] = phi[a];
   }
   __syncthreads();
   if (!active) return;
   const int i = id % n, j = (id / n) % n, k = id / (n * n);
   const int ijk[3] = {i, j, k};
-  double dd[4][3];
+  R dd[4][3];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    double s0 = 0, s1 = 0, s2 = 0;
+    R s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
     for (int m = 0; m < n; ++m) {
       s0 += sD[i * n + m] * sphi[le][a][vidx<n>(m, j, k)];
@@ -59,11 +76,11 @@ k_lift(const double* __restrict__ U, const double* __restrict__ metrics, const i
     }
     dd[a][0] = s0; dd[a][1] = s1; dd[a][2] = s2;
   }
-  const double* mt = metrics + (size_t)e * 10 * P + id;
-  double Ja[9];
+  const R* mt = metrics + (size_t)e * 10 * P + id;
+  R Ja[9];
 #pragma unroll
   for (int r = 0; r < 9; ++r) Ja[r] = mt[r * P];
-  double gr[12];
+  R gr[12];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -84,20 +101,21 @@ k_lift(const double* __restrict__ U, const double* __restrict__ metrics, const i
     apply_flip<n>(code & 7, p, qq, p2, q2);
     const int id2 = face_node<n>(f2, p2, q2);
     const double* q = U + (size_t)e2 * 5 * P + id2;
-    const double rho = q[0], ir = 1.0 / rho;
-    const double u = q[P] * ir, v = q[2 * P] * ir, w = q[3 * P] * ir;
-    const double pr = g.gm1 * (q[4 * P] - 0.5 * (q[P] * u + q[2 * P] * v + q[3 * P] * w));
-    const double onb[4] = {u, v, w, pr * ir * g.inv_R};
-    const double sg = s ? inv_w0 : -inv_w0;
+    const R rho = R(q[0]), ir = rcp_lf(rho);
+    const R m0 = R(q[P]), m1 = R(q[2 * P]), m2 = R(q[3 * P]);
+    const R u = m0 * ir, v = m1 * ir, w = m2 * ir;
+    const R pr = gm1 * (R(q[4 * P]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
+    const R onb[4] = {u, v, w, pr * ir * inv_R};
+    const R sg = s ? inv_w0 : -inv_w0;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const double jump = 0.5 * (onb[a] - phi[a]) * sg;
+      const R jump = R(0.5) * (onb[a] - phi[a]) * sg;
 #pragma unroll
       for (int l = 0; l < 3; ++l) gr[a * 3 + l] += jump * Ja[d * 3 + l];
     }
   }
-  const double iJ = mt[9 * P];
-  double* go = grad + (size_t)e * 12 * P + id;
+  const R iJ = mt[9 * P];
+  R* go = grad + (size_t)e * 12 * P + id;
 #pragma unroll
   for (int r = 0; r < 12; ++r) go[r * P] = gr[r] * iJ;
 }
@@ -106,10 +124,10 @@ k_lift(const double* __restrict__ U, const double* __restrict__ metrics, const i
 // Surface flux on every face node, master orientation (Sec. 3.1): Riemann flux
 // (LLF, or the two-point EC flux) minus the BR1 average of the viscous fluxes,
 // times the surface element:  F* = (F_adv(qM, qS; n) - 1/2 (f_v,M + f_v,S) . n) sJ.
-template <int N>
+template <int N, typename R>
 __global__ void __launch_bounds__(128)
-k_face(const double* __restrict__ U, const double* __restrict__ grad, const FaceInfo* __restrict__ faces,
-       const double* __restrict__ facegeo, double* __restrict__ fstar, int F, Gas g) {
+k_face(const double* __restrict__ U, const R* __restrict__ grad, const FaceInfo* __restrict__ faces,
+       const R* __restrict__ facegeo, R* __restrict__ fstar, int F, Gas g) {
   constexpr int n = N + 1, P = n * n * n, NN = n * n;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long)F * NN) return;
@@ -120,67 +138,80 @@ k_face(const double* __restrict__ U, const double* __restrict__ grad, const Face
   int p2, q2;
   apply_flip<n>(fi.flip, p, q, p2, q2);
   const int idM = face_node<n>(fM, p, q), idS = face_node<n>(fS, p2, q2);
-  double qL[5], qR[5];
+  R qL[5], qR[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    qL[v] = U[((size_t)eM * 5 + v) * P + idM];
-    qR[v] = U[((size_t)eS * 5 + v) * P + idS];
+    qL[v] = R(U[((size_t)eM * 5 + v) * P + idM]);
+    qR[v] = R(U[((size_t)eS * 5 + v) * P + idS]);
   }
-  const double* fg = facegeo + (size_t)f * 4 * NN + pq;
-  const double nx = fg[0], ny = fg[NN], nz = fg[2 * NN], sJ = fg[3 * NN];
-  const double irL = 1.0 / qL[0], irR = 1.0 / qR[0];
-  const double uL = qL[1] * irL, vL = qL[2] * irL, wL = qL[3] * irL;
-  const double uR = qR[1] * irR, vR = qR[2] * irR, wR = qR[3] * irR;
-  const double pL = g.gm1 * (qL[4] - 0.5 * (qL[1] * uL + qL[2] * vL + qL[3] * wL));
-  const double pR = g.gm1 * (qR[4] - 0.5 * (qR[1] * uR + qR[2] * vR + qR[3] * wR));
-  double fa[5];
+  const R gm1 = R(g.gm1), gam = R(g.gamma);
+  const R* fg = facegeo + (size_t)f * 4 * NN + pq;
+  const R nx = fg[0], ny = fg[NN], nz = fg[2 * NN], sJ = fg[3 * NN];
+  const R irL = rcp_lf(qL[0]), irR = rcp_lf(qR[0]);
+  const R uL = qL[1] * irL, vL = qL[2] * irL, wL = qL[3] * irL;
+  const R uR = qR[1] * irR, vR = qR[2] * irR, wR = qR[3] * irR;
+  const R pL = gm1 * (qL[4] - R(0.5) * (qL[1] * uL + qL[2] * vL + qL[3] * wL));
+  const R pR = gm1 * (qR[4] - R(0.5) * (qR[1] * uR + qR[2] * vR + qR[3] * wR));
+  R fa[5];
   if (g.surf_flux == DG_FLUX_EC) {
-    NodePrim<double> a{qL[0], uL, vL, wL, pL, 0.5 * qL[0] / pL};
-    NodePrim<double> b{qR[0], uR, vR, wR, pR, 0.5 * qR[0] / pR};
-    ec_flux<double>(a, b, nx, ny, nz, g.inv_gm1, fa);
+    NodePrim<R> a{qL[0], uL, vL, wL, pL, R(0.5) * qL[0] / pL};
+    NodePrim<R> b{qR[0], uR, vR, wR, pR, R(0.5) * qR[0] / pR};
+    ec_flux<R>(a, b, nx, ny, nz, R(g.inv_gm1), fa);
   } else {
-    double fL[5], fR[5];
-    euler_flux<double>(qL, uL, vL, wL, pL, nx, ny, nz, fL);
-    euler_flux<double>(qR, uR, vR, wR, pR, nx, ny, nz, fR);
-    const double cL = sqrt(g.gamma * pL * irL), cR = sqrt(g.gamma * pR * irR);
-    const double lL = fabs(uL * nx + vL * ny + wL * nz) + cL;
-    const double lR = fabs(uR * nx + vR * ny + wR * nz) + cR;
-    const double lmax = lR > lL ? lR : lL;
+    R fL[5], fR[5];
+    euler_flux<R>(qL, uL, vL, wL, pL, nx, ny, nz, fL);
+    euler_flux<R>(qR, uR, vR, wR, pR, nx, ny, nz, fR);
+    const R cL = sqrt(gam * pL * irL), cR = sqrt(gam * pR * irR);
+    const R lL = fabs(uL * nx + vL * ny + wL * nz) + cL;
+    const R lR = fabs(uR * nx + vR * ny + wR * nz) + cR;
+    const R lmax = lR > lL ? lR : lL;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) fa[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lmax * (qR[v] - qL[v]);
+    for (int v = 0; v < 5; ++v) fa[v] = R(0.5) * (fL[v] + fR[v]) - R(0.5) * lmax * (qR[v] - qL[v]);
   }
-  double gL[12], gR[12];
+  R gL[12], gR[12];
 #pragma unroll
   for (int r = 0; r < 12; ++r) {
     gL[r] = grad[((size_t)eM * 12 + r) * P + idM];
     gR[r] = grad[((size_t)eS * 12 + r) * P + idS];
   }
-  double fvL[4], fvR[4];
-  const double lam = g.mu * g.kappa;
-  visc_flux<double>(gL, uL, vL, wL, g.mu, lam, nx, ny, nz, fvL);
-  visc_flux<double>(gR, uR, vR, wR, g.mu, lam, nx, ny, nz, fvR);
-  double* fo = fstar + (size_t)f * 5 * NN + pq;
+  R fvL[4], fvR[4];
+  const R mu = R(g.mu), lam = R(g.mu * g.kappa);
+  visc_flux<R>(gL, uL, vL, wL, mu, lam, nx, ny, nz, fvL);
+  visc_flux<R>(gR, uR, vR, wR, mu, lam, nx, ny, nz, fvR);
+  R* fo = fstar + (size_t)f * 5 * NN + pq;
   fo[0] = fa[0] * sJ;
 #pragma unroll
-  for (int v = 1; v < 5; ++v) fo[(size_t)v * NN] = (fa[v] - 0.5 * (fvL[v - 1] + fvR[v - 1])) * sJ;
+  for (int v = 1; v < 5; ++v) fo[(size_t)v * NN] = (fa[v] - R(0.5) * (fvL[v - 1] + fvR[v - 1])) * sJ;
 }
 
 // ---------------------------------------------------------------------------
-template <int N>
-static cudaError_t lift_N(const Ctx& c, const double* U, cudaStream_t s) {
+template <int N, typename R>
+static cudaError_t lift_NR(const Ctx& c, const double* U, cudaStream_t s) {
   using S = Shape<N>;
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
-  k_lift<N><<<blocks, S::THREADS, 0, s>>>(U, c.d_metrics, c.d_elem_nbr, c.d_elem_face, c.d_D, c.d_grad, c.E,
-                                          c.gas, 1.0 / c.w[0]);
+  const R* metrics = (const R*)(sizeof(R) == 8 ? (const void*)c.d_metrics : (const void*)c.d_metrics_f);
+  k_lift<N, R><<<blocks, S::THREADS, 0, s>>>(U, metrics, c.d_elem_nbr, c.d_elem_face, c.d_D, (R*)c.d_grad, c.E,
+                                             c.gas, 1.0 / c.w[0]);
   return cudaGetLastError();
+}
+
+template <int N, typename R>
+static cudaError_t face_NR(const Ctx& c, const double* U, cudaStream_t s) {
+  const long tot = (long)c.nfaces * (N + 1) * (N + 1);
+  const int blocks = (int)((tot + 127) / 128);
+  const R* fgeo = (const R*)(sizeof(R) == 8 ? (const void*)c.d_facegeo : (const void*)c.d_facegeo_f);
+  k_face<N, R><<<blocks, 128, 0, s>>>(U, (const R*)c.d_grad, c.d_faces, fgeo, (R*)c.d_fstar, c.nfaces, c.gas);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t lift_N(const Ctx& c, const double* U, bool fp64, cudaStream_t s) {
+  return fp64 ? lift_NR<N, double>(c, U, s) : lift_NR<N, float>(c, U, s);
 }
 
 template <int N>
 static cudaError_t face_N(const Ctx& c, const double* U, cudaStream_t s) {
-  const long tot = (long)c.nfaces * (N + 1) * (N + 1);
-  const int blocks = (int)((tot + 127) / 128);
-  k_face<N><<<blocks, 128, 0, s>>>(U, c.d_grad, c.d_faces, c.d_facegeo, c.d_fstar, c.nfaces, c.gas);
-  return cudaGetLastError();
+  return c.prm.precision == DG_FP32OP ? face_NR<N, float>(c, U, s) : face_NR<N, double>(c, U, s);
 }
 
 #define DG_DISPATCH(FN, ...)                 \
@@ -195,7 +226,10 @@ static cudaError_t face_N(const Ctx& c, const double* U, cudaStream_t s) {
     default: return cudaErrorInvalidValue;   \
   }
 
-cudaError_t launch_lift(const Ctx& c, const double* U, cudaStream_t s) { DG_DISPATCH(lift_N, c, U, s) }
+cudaError_t launch_lift(const Ctx& c, const double* U, cudaStream_t s) {
+  DG_DISPATCH(lift_N, c, U, c.prm.precision != DG_FP32OP, s)
+}
+cudaError_t launch_lift_fp64(const Ctx& c, const double* U, cudaStream_t s) { DG_DISPATCH(lift_N, c, U, true, s) }
 cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s) { DG_DISPATCH(face_N, c, U, s) }
 cudaError_t setup_kernels(int N) { return setup_volume(N); }
 

@@ -33,88 +33,103 @@ struct VShape {
 };
 
 // 1/x: hardware reciprocal approximation refined by one cubic Newton-Raphson
-// step y <- y (1 + e + e^2), e = 1 - x y, which cubes the relative error.
-__device__ __forceinline__ double rcp64(double x) {
+// step y <- y (1 + e + e^2), e = 1 - x y, which cubes the relative error
+// (2^-20 -> below 1 ulp).  In FP32 the approximation alone is within 1 ulp.
+__device__ __forceinline__ double rcp_op(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
   const double e = fma(-x, y, 1.0);
   const double t = fma(e, e, e);
   return fma(y, t, y);
 }
+__device__ __forceinline__ float rcp_op(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
-// u < 1e-4 for u >= 0, decided on the high word (exact enough for a switch
-// between two formulas that agree to rounding there).
+// Switch of the logarithmic mean between the series and the logarithm.  In
+// FP64 below u = 1e-4 (four series terms are exact to rounding; decided on the
+// high word in integer ALU), in FP32 below u = 1e-2 (truncation < 1e-9).
 __device__ __forceinline__ bool small_u(double u) { return __double2hiint(u) < 0x3F1A36E2; }
+__device__ __forceinline__ bool small_u(float u) { return u < 1e-2f; }
 
 // 1/F(u) = u^(1/2) / atanh(u^(1/2)) = 1 - u/3 - 4u^2/45 - 44u^3/945 - ...
-__device__ __forceinline__ double inv_atanh_ratio(double u) {
-  return fma(u, fma(u, fma(u, -44.0 / 945.0, -4.0 / 45.0), -1.0 / 3.0), 1.0);
+template <typename R>
+__device__ __forceinline__ R inv_atanh_ratio(R u) {
+  return fma(u, fma(u, fma(u, R(-44.0 / 945.0), R(-4.0 / 45.0)), R(-1.0 / 3.0)), R(1));
 }
 // F(u) = atanh(u^(1/2)) / u^(1/2) = 1 + u/3 + u^2/5 + u^3/7 + ...
-__device__ __forceinline__ double atanh_ratio(double u) {
-  return fma(u, fma(u, fma(u, 1.0 / 7.0, 1.0 / 5.0), 1.0 / 3.0), 1.0);
+template <typename R>
+__device__ __forceinline__ R atanh_ratio(R u) {
+  return fma(u, fma(u, fma(u, R(1.0 / 7.0), R(1.0 / 5.0)), R(1.0 / 3.0)), R(1));
 }
 // F for the logarithmic branch, in the ratio form of Ismail & Roe.
-__device__ __noinline__ double atanh_ratio_log(double a, double b) {
-  const double z = a / b;
-  return log(z) / (2.0 * ((z - 1.0) / (z + 1.0)));
+template <typename R>
+__device__ __noinline__ R atanh_ratio_log(R a, R b) {
+  const R z = a / b;
+  return log(z) / (R(2) * ((z - R(1)) / (z + R(1))));
 }
 
-template <int N>
+// R is the operator arithmetic: double (FP64 path) or float (FP32-operator
+// path, state and RK update stay FP64).  metrics, grad and fstar are stored in R.
+template <int N, typename R>
 __global__ void __launch_bounds__(VShape<N>::THREADS)
-k_volume2(StageArgs a, const double* __restrict__ metrics, const double* __restrict__ grad,
-          const double* __restrict__ fstar, const int* __restrict__ elem_face, const double* __restrict__ X,
-          const double* __restrict__ Dg, int E, Gas g, double inv_w0) {
+k_volume2(StageArgs a, const R* __restrict__ metrics, const double* __restrict__ iJ64,
+          const R* __restrict__ grad, const R* __restrict__ fstar, const int* __restrict__ elem_face,
+          const double* __restrict__ X, const double* __restrict__ Dg, int E, Gas g, double inv_w0d) {
   using S = VShape<N>;
   constexpr int n = S::n, P = S::P, NN = S::NN, EPB = S::EPB;
-  extern __shared__ double smem[];
-  double* sD = smem;                  // D
-  double* sT0 = sD + n * n;           // D/4   (mass: X = 8 f_rho)
-  double* sT1 = sT0 + n * n;          // D/8   (momentum: M = 16 f_m)
-  double* sT2 = sT1 + n * n;          // D/16  (energy: 32 f_E)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* smem = reinterpret_cast<R*>(smem_raw);
+  R* sD = smem;                       // D
+  R* sT0 = sD + n * n;                // D/4   (mass: X = 8 f_rho)
+  R* sT1 = sT0 + n * n;               // D/8   (momentum: M = 16 f_m)
+  R* sT2 = sT1 + n * n;               // D/16  (energy: 32 f_E)
   const int le = threadIdx.x / P, id = threadIdx.x - le * P;
-  double* base = sT2 + ((n * n + 1) & ~1) + le * S::PER_ELEM;
-  double* sR = base;                  // rho
-  double* sU = sR + P;                // u, v, w
-  double* sB = sU + 3 * P;            // beta = rho / (2 p)
-  double* sK = sB + P;                // |u|^2
-  double* sJa = sK + P;               // [9][P]  Ja^d_l at row d*3+l
-  double* sFv = sJa + 9 * P;          // [3][4][P] (f_v . Ja^d), momentum + energy
-  double* sX = sFv + 12 * P;          // [5][P] exchange of partner shares
+  R* base = sT2 + ((n * n + 3) & ~3) + le * S::PER_ELEM;
+  R* sR = base;                       // rho
+  R* sU = sR + P;                     // u, v, w
+  R* sB = sU + 3 * P;                 // beta = rho / (2 p)
+  R* sK = sB + P;                     // |u|^2
+  R* sJa = sK + P;                    // [9][P]  Ja^d_l at row d*3+l
+  R* sFv = sJa + 9 * P;               // [3][4][P] (f_v . Ja^d), momentum + energy
+  R* sX = sFv + 12 * P;               // [5][P] exchange of partner shares
   const int e = blockIdx.x * EPB + le;
   const bool active = e < E;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const double d = Dg[t];
-    sD[t] = d;
-    sT0[t] = 0.25 * d;
-    sT1[t] = 0.125 * d;
-    sT2[t] = 0.0625 * d;
+    sD[t] = R(d);
+    sT0[t] = R(0.25 * d);
+    sT1[t] = R(0.125 * d);
+    sT2[t] = R(0.0625 * d);
   }
-  double q[5] = {0, 0, 0, 0, 0}, Ja[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, iJ = 0.0;
-  double rho = 1.0, u = 0, v = 0, w = 0, beta = 0, kk = 0;
+  const R inv_w0 = R(inv_w0d);
+  double q[5] = {0, 0, 0, 0, 0};
+  R Ja[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  R rho = R(1), u = 0, v = 0, w = 0, beta = 0, kk = 0;
   if (active) {
 #pragma unroll
     for (int r = 0; r < 5; ++r) q[r] = a.U[((size_t)e * 5 + r) * P + id];
-    const double* mt = metrics + (size_t)e * 10 * P + id;
+    const R* mt = metrics + (size_t)e * 10 * P + id;
 #pragma unroll
     for (int r = 0; r < 9; ++r) { Ja[r] = mt[r * P]; sJa[r * P + id] = Ja[r]; }
-    iJ = mt[9 * P];
-    rho = q[0];
-    const double ir = rcp64(rho);
-    u = q[1] * ir; v = q[2] * ir; w = q[3] * ir;
+    rho = R(q[0]);
+    const R ir = rcp_op(rho);
+    u = R(q[1]) * ir; v = R(q[2]) * ir; w = R(q[3]) * ir;
     kk = u * u + v * v + w * w;
-    const double p = g.gm1 * fma(-0.5 * rho, kk, q[4]);
-    beta = 0.5 * rho * rcp64(p);
+    const R p = R(g.gm1) * fma(R(-0.5) * rho, kk, R(q[4]));
+    beta = R(0.5) * rho * rcp_op(p);
     sR[id] = rho; sU[id] = u; sU[P + id] = v; sU[2 * P + id] = w; sB[id] = beta; sK[id] = kk;
-    double gr[12];
-    const double* gg = grad + (size_t)e * 12 * P + id;
+    R gr[12];
+    const R* gg = grad + (size_t)e * 12 * P + id;
 #pragma unroll
     for (int r = 0; r < 12; ++r) gr[r] = gg[r * P];
-    const double lam = g.mu * g.kappa;
+    const R mu = R(g.mu), lam = R(g.mu * g.kappa);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      double fv[4];
-      visc_flux<double>(gr, u, v, w, g.mu, lam, Ja[d * 3], Ja[d * 3 + 1], Ja[d * 3 + 2], fv);
+      R fv[4];
+      visc_flux<R>(gr, u, v, w, mu, lam, Ja[d * 3], Ja[d * 3 + 1], Ja[d * 3 + 2], fv);
 #pragma unroll
       for (int c = 0; c < 4; ++c) sFv[(d * 4 + c) * P + id] = fv[c];
     }
@@ -122,8 +137,8 @@ k_volume2(StageArgs a, const double* __restrict__ metrics, const double* __restr
   __syncthreads();
   const int i = id % n, j = (id / n) % n, k = id / NN;
   const int ijk[3] = {i, j, k};
-  const double inv4 = 4.0 * g.inv_gm1;
-  double acc[5] = {0, 0, 0, 0, 0};
+  const R inv4 = R(4.0 * g.inv_gm1);
+  R acc[5] = {0, 0, 0, 0, 0};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int r = ijk[d];
@@ -135,28 +150,28 @@ k_volume2(StageArgs a, const double* __restrict__ metrics, const double* __restr
       const int m = r + s < n ? r + s : r + s - n;
       const int mid = line0 + m * stride;
       if (active && !(half && r >= s)) {
-        const double rb = sR[mid], bb = sB[mid];
-        const double sr = rho + rb, sb = beta + bb;
-        const double rr = rcp64(sr), rbt = rcp64(sb);
-        const double fr = (rho - rb) * rr, fb = (beta - bb) * rbt;
-        const double ur = fr * fr, ub = fb * fb;
-        double rln2, hib;                    // 2 rho_ln and 1/(2 beta_ln)
+        const R rb = sR[mid], bb = sB[mid];
+        const R sr = rho + rb, sb = beta + bb;
+        const R rr = rcp_op(sr), rbt = rcp_op(sb);
+        const R fr = (rho - rb) * rr, fb = (beta - bb) * rbt;
+        const R ur = fr * fr, ub = fb * fb;
+        R rln2, hib;                    // 2 rho_ln and 1/(2 beta_ln)
         if (small_u(ur)) rln2 = sr * inv_atanh_ratio(ur);
         else rln2 = sr / atanh_ratio_log(rho, rb);
         if (small_u(ub)) hib = atanh_ratio(ub) * rbt;
         else hib = atanh_ratio_log(beta, bb) * rbt;
-        const double su0 = u + sU[mid], su1 = v + sU[P + mid], su2 = w + sU[2 * P + mid];
-        const double sn0 = Ja[d * 3] + sJa[(d * 3) * P + mid];
-        const double sn1 = Ja[d * 3 + 1] + sJa[(d * 3 + 1) * P + mid];
-        const double sn2 = Ja[d * 3 + 2] + sJa[(d * 3 + 2) * P + mid];
-        const double un4 = fma(su0, sn0, fma(su1, sn1, su2 * sn2));
-        const double Xf = rln2 * un4;                      // 8 f_rho
-        const double Y4 = 4.0 * sr * rbt;                  // 16 p_hat / |n_avg| scale
-        const double M0 = fma(Xf, su0, Y4 * sn0);          // 16 f_m
-        const double M1 = fma(Xf, su1, Y4 * sn1);
-        const double M2 = fma(Xf, su2, Y4 * sn2);
-        const double Z = fma(hib, inv4, -(kk + sK[mid]));
-        const double E32 = fma(Xf, Z, fma(su0, M0, fma(su1, M1, su2 * M2)));   // 32 f_E
+        const R su0 = u + sU[mid], su1 = v + sU[P + mid], su2 = w + sU[2 * P + mid];
+        const R sn0 = Ja[d * 3] + sJa[(d * 3) * P + mid];
+        const R sn1 = Ja[d * 3 + 1] + sJa[(d * 3 + 1) * P + mid];
+        const R sn2 = Ja[d * 3 + 2] + sJa[(d * 3 + 2) * P + mid];
+        const R un4 = fma(su0, sn0, fma(su1, sn1, su2 * sn2));
+        const R Xf = rln2 * un4;                      // 8 f_rho
+        const R Y4 = R(4) * sr * rbt;                  // 16 p_hat / |n_avg| scale
+        const R M0 = fma(Xf, su0, Y4 * sn0);          // 16 f_m
+        const R M1 = fma(Xf, su1, Y4 * sn1);
+        const R M2 = fma(Xf, su2, Y4 * sn2);
+        const R Z = fma(hib, inv4, -(kk + sK[mid]));
+        const R E32 = fma(Xf, Z, fma(su0, M0, fma(su1, M1, su2 * M2)));   // 32 f_E
         const int rm = r * n + m;
         acc[0] = fma(sT0[rm], Xf, acc[0]);
         acc[1] = fma(sT1[rm], M0, acc[1]);
@@ -185,10 +200,10 @@ k_volume2(StageArgs a, const double* __restrict__ metrics, const double* __restr
     const int r = ijk[d];
     const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
     const int line0 = id - r * stride;
-    double v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+    R v0 = 0, v1 = 0, v2 = 0, v3 = 0;
 #pragma unroll
     for (int m = 0; m < n; ++m) {
-      const double Drm = sD[r * n + m];
+      const R Drm = sD[r * n + m];
       const int mid = line0 + m * stride;
       v0 = fma(Drm, sFv[(d * 4 + 0) * P + mid], v0);
       v1 = fma(Drm, sFv[(d * 4 + 1) * P + mid], v1);
@@ -208,8 +223,8 @@ k_volume2(StageArgs a, const double* __restrict__ metrics, const double* __restr
     const int fid = code >> 4;
     const int pp = d == 0 ? j : i;
     const int qq = d == 2 ? j : k;
-    const double* fsr;
-    double fs_sign;
+    const R* fsr;
+    R fs_sign;
     if (code & 8) {
       fsr = fstar + (size_t)fid * 5 * NN + pp + n * qq;
       fs_sign = inv_w0;
@@ -219,7 +234,7 @@ k_volume2(StageArgs a, const double* __restrict__ metrics, const double* __restr
       fsr = fstar + (size_t)fid * 5 * NN + p2 + n * q2;
       fs_sign = -inv_w0;
     }
-    const double vs = sgn ? inv_w0 : -inv_w0;
+    const R vs = sgn ? inv_w0 : -inv_w0;
     acc[0] = fma(fs_sign, fsr[0], acc[0]);
 #pragma unroll
     for (int c = 0; c < 4; ++c)
@@ -241,63 +256,79 @@ k_volume2(StageArgs a, const double* __restrict__ metrics, const double* __restr
     src[0] = src[1] = src[2] = src[3] = 2.0 * rp;
     src[4] = 3.0 * rp - g.mu * g.kappa * lapT;
   }
+  // Jacobian, source and RK update in FP64
+  const double iJ = iJ64[(size_t)e * 10 * P + 9 * P + id];
   if (a.mode == 0) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) a.Ut[((size_t)e * 5 + c) * P + id] = fma(-acc[c], iJ, src[c]);
+    for (int c = 0; c < 5; ++c) a.Ut[((size_t)e * 5 + c) * P + id] = fma(-(double)acc[c], iJ, src[c]);
   } else {
     const double dt = a.clock[1];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       const size_t o = ((size_t)e * 5 + c) * P + id;
-      const double gk = fma(a.A, a.Gk[o], dt * fma(-acc[c], iJ, src[c]));
+      const double gk = fma(a.A, a.Gk[o], dt * fma(-(double)acc[c], iJ, src[c]));
       a.Gk[o] = gk;
       a.Uw[o] = fma(a.B, gk, q[c]);
     }
   }
 }
 
-template <int N>
+template <int N, typename R>
 static size_t volume2_smem() {
   using S = VShape<N>;
-  return sizeof(double) * (3 * S::n * S::n + ((S::n * S::n + 1) & ~1) + S::EPB * S::PER_ELEM);
+  return sizeof(R) * (3 * S::n * S::n + ((S::n * S::n + 3) & ~3) + S::EPB * S::PER_ELEM);
 }
 
-template <int N>
+template <int N, typename R>
 cudaError_t volume2_setup() {
-  return cudaFuncSetAttribute(k_volume2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)volume2_smem<N>());
+  return cudaFuncSetAttribute(k_volume2<N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)volume2_smem<N, R>());
 }
 
-template <int N>
+template <int N, typename R>
 cudaError_t volume2_launch(const Ctx& c, const StageArgs& a, cudaStream_t s) {
   using S = VShape<N>;
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
-  k_volume2<N><<<blocks, S::THREADS, volume2_smem<N>(), s>>>(a, c.d_metrics, c.d_grad, c.d_fstar, c.d_elem_face,
-                                                             c.d_X, c.d_D, c.E, c.gas, 1.0 / c.w[0]);
+  const R* metrics = (const R*)(sizeof(R) == 8 ? (const void*)c.d_metrics : (const void*)c.d_metrics_f);
+  k_volume2<N, R><<<blocks, S::THREADS, volume2_smem<N, R>(), s>>>(
+      a, metrics, c.d_metrics, (const R*)c.d_grad, (const R*)c.d_fstar, c.d_elem_face, c.d_X, c.d_D, c.E, c.gas,
+      1.0 / c.w[0]);
   return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t volume_any(const Ctx& c, const StageArgs& a, cudaStream_t s) {
+  return c.prm.precision == DG_FP32OP ? volume2_launch<N, float>(c, a, s) : volume2_launch<N, double>(c, a, s);
+}
+
+template <int N>
+static cudaError_t setup_any() {
+  cudaError_t e = volume2_setup<N, double>();
+  return e != cudaSuccess ? e : volume2_setup<N, float>();
 }
 
 cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s) {
   switch (c.N) {
-    case 1: return volume2_launch<1>(c, a, s);
-    case 2: return volume2_launch<2>(c, a, s);
-    case 3: return volume2_launch<3>(c, a, s);
-    case 4: return volume2_launch<4>(c, a, s);
-    case 5: return volume2_launch<5>(c, a, s);
-    case 6: return volume2_launch<6>(c, a, s);
-    case 7: return volume2_launch<7>(c, a, s);
+    case 1: return volume_any<1>(c, a, s);
+    case 2: return volume_any<2>(c, a, s);
+    case 3: return volume_any<3>(c, a, s);
+    case 4: return volume_any<4>(c, a, s);
+    case 5: return volume_any<5>(c, a, s);
+    case 6: return volume_any<6>(c, a, s);
+    case 7: return volume_any<7>(c, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t setup_volume(int N) {
   switch (N) {
-    case 1: return volume2_setup<1>();
-    case 2: return volume2_setup<2>();
-    case 3: return volume2_setup<3>();
-    case 4: return volume2_setup<4>();
-    case 5: return volume2_setup<5>();
-    case 6: return volume2_setup<6>();
-    case 7: return volume2_setup<7>();
+    case 1: return setup_any<1>();
+    case 2: return setup_any<2>();
+    case 3: return setup_any<3>();
+    case 4: return setup_any<4>();
+    case 5: return setup_any<5>();
+    case 6: return setup_any<6>();
+    case 7: return setup_any<7>();
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,0 +1,72 @@
+"""FP32-operator path (volume flux differencing, lifting and face fluxes in
+FP32; state, metrics precomputation, stage update and reductions in FP64)
+against the FP64 oracle.  The bars state the errors FP32 arithmetic allows;
+they are not parity tolerances."""
+import math
+
+import numpy as np
+import pytest
+
+from workloads import box_mesh, random_state, tgv_params
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import paper_2605_28627_gb300 as m
+    m.load()
+    return m
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 7])
+def test_fp32_time_derivative_vs_oracle(orc, dg, N):
+    K = 3 if N <= 4 else 2
+    mesh = box_mesh(K, N, deform="sinprod", rotate_seed=400 + N)
+    o = orc.Oracle(mesh, N, mu=0.02)
+    s = dg.Solver(mesh, N, mu=0.02, precision=dg.FP32OP)
+    U = random_state(mesh.n_elems, N, seed=500 + N)
+    ref = o.time_derivative(U).reshape(mesh.n_elems, 5, -1)
+    got = s.time_derivative(torch.from_numpy(U).cuda()).cpu().numpy().reshape(mesh.n_elems, 5, -1)
+    for v in range(5):
+        err = np.abs(got[:, v] - ref[:, v]).max() / np.abs(ref[:, v]).max()
+        assert err < 2e-5, (v, err)
+
+
+def test_fp32_tgv_rk_vs_oracle(orc, dg):
+    prm = tgv_params(Ma=0.1, Re=1600.0)
+    N = 3
+    mesh = box_mesh(4, 1, lo=0.0, hi=2 * math.pi)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"])
+    o = orc.Oracle(mesh, N, **kw)
+    s = dg.Solver(mesh, N, precision=dg.FP32OP, **kw)
+    U0 = o.initial_state("tgv", prm["p0"])
+    Ud = torch.from_numpy(U0).cuda()
+    dt = s.max_dt(Ud)
+    ref = o.rk_steps(U0, 0.0, dt, 10)
+    G = torch.empty_like(Ud)
+    s.rk_step(Ud, G, 0.0, dt, 10)
+    got = Ud.cpu().numpy()
+    # state: FP32 rounding of the stage updates relative to |U|
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-6
+    # kinetic energy (the quantity the FP32 path is judged on)
+    ek_ref, ek = o.integrals(ref)[5], s.integrals(Ud)[5]
+    assert abs(ek - ek_ref) / ek_ref < 1e-6
+    # mass stays conserved: FP32 flux rounding only
+    I0 = o.integrals(U0)
+    assert abs(s.integrals(Ud)[0] - I0[0]) / I0[0] < 1e-7
+
+
+def test_fp32_free_stream(dg):
+    N = 5
+    mesh = box_mesh(3, N, deform="sinprod", rotate_seed=7)
+    s = dg.Solver(mesh, N, mu=0.01, precision=dg.FP32OP)
+    U = np.zeros(s.shape)
+    r, u, p = 1.2, np.array([0.3, -0.2, 0.45]), 0.9
+    U[:, 0] = r
+    U[:, 1:4] = (r * u)[None, :, None, None, None]
+    U[:, 4] = p / 0.4 + 0.5 * r * u @ u
+    R = s.time_derivative(torch.from_numpy(U).cuda()).cpu().numpy()
+    # FP32 rounding of terms of size |D| |f . Ja| / J ~ 1e2
+    assert np.abs(R).max() < 1e-3
