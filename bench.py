@@ -241,6 +241,88 @@ def run_tgv_large(args, local):
     return 0
 
 
+def run_ensemble(args, local):
+    """Batched ensemble: 64 uneven Taylor-Green runs (seed 20260529: K ~ U{8..24}
+    elements per direction, N ~ U{3..7}, Ma ~ U[0.1, 0.5], Re ~ U[400, 1600]),
+    each with its own CFL-0.9 time step, FP32 operator with FP64 state, 10
+    steps in one graph launch of the autotuned ensemble kernels.  Compared
+    with the same 64 runs advanced one after the other by the single-context
+    path, in FP64 and in FP32-operator precision."""
+    import torch
+    import paper_2605_28627_gb300 as dg
+    from workloads import box_mesh, ensemble_members, tgv_params
+    specs = ensemble_members(64, 20260529)
+    nsteps = args.ens_steps
+    dev = "cuda:%d" % local
+    st = torch.cuda.Stream(device=dev)
+
+    def member(spec, precision):
+        prm = tgv_params(Ma=spec["Ma"], Re=spec["Re"])
+        mesh = box_mesh(spec["K"], 1, lo=0.0, hi=2 * math.pi)
+        s = dg.Solver(mesh, spec["N"], gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"],
+                      precision=precision, device=local)
+        U = s.initial_state("tgv", prm["p0"], stream=st)
+        dt = s.max_dt(U, cfl=0.9, dfl=0.9, stream=st)
+        return s, U, dt
+
+    dofs = [sp["K"] ** 3 * (sp["N"] + 1) ** 3 for sp in specs]
+    total = sum(dofs)
+    runs = [member(sp, dg.FP32OP) for sp in specs]
+    ens = dg.Ensemble([r[0] for r in runs], tune_cache_path=os.path.join(ROOT, "gpurun_out", "ensemble_tune.txt")
+                      if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    Us = [r[1] for r in runs]
+    Gs = [torch.empty_like(U) for U in Us]
+    dts = [r[2] for r in runs]
+    t0 = time.perf_counter()
+    ens.step(Us, Gs, [0.0] * 64, dts, nsteps=1, stream=st)       # tunes, captures
+    st.synchronize()
+    tune_s = time.perf_counter() - t0
+    ens.step(Us, Gs, dts, dts, nsteps=nsteps, stream=st)         # warm-up of the timed graph
+    st.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tt = [(1 + nsteps) * d for d in dts]
+    e0.record(st)
+    ens.step(Us, Gs, tt, dts, nsteps=nsteps, stream=st)
+    e1.record(st)
+    e1.synchronize()
+    ms_ens = e0.elapsed_time(e1)
+    plan = ens.plan()
+    ens.close()
+    for r in runs:
+        r[0].close()
+    del runs, Us, Gs
+    torch.cuda.empty_cache()
+
+    def sequential(precision):
+        ms_tot = 0.0
+        for sp in specs:
+            s, U, dt = member(sp, precision)
+            G = torch.empty_like(U)
+            s.rk_step(U, G, 0.0, dt, nsteps, stream=st)           # warm-up + graph capture
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            s.rk_step(U, G, nsteps * dt, dt, nsteps, stream=st)
+            b.record(st)
+            b.synchronize()
+            ms_tot += a.elapsed_time(b)
+            s.close()
+            del U, G
+        return ms_tot
+
+    ms_seq64 = sequential(dg.FP64)
+    ms_seq32 = sequential(dg.FP32OP)
+    rate = total * 5 * nsteps / (ms_ens * 1e-3)
+    line = {"experiment": "ensemble of 64 uneven Taylor-Green runs (seed 20260529), FP32 operator / FP64 state, "
+                          "%d LSERK4-5 steps in one graph launch" % nsteps,
+            "members": 64, "total_dof": total, "value": rate, "unit": UNIT, "pid_ns": 1e9 / rate,
+            "ms_per_step": ms_ens / nsteps,
+            "sequential_fp64_ms_per_step": ms_seq64 / nsteps, "sequential_fp32op_ms_per_step": ms_seq32 / nsteps,
+            "speedup_vs_sequential_fp64": ms_seq64 / ms_ens, "speedup_vs_sequential_fp32op": ms_seq32 / ms_ens,
+            "first_step_with_tuning_s": tune_s, "plan": plan}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -252,11 +334,15 @@ def main():
     ap.add_argument("--sweep", default="3,4,5,6,7", help="extra orders timed for the per-N table ('' = none)")
     ap.add_argument("--tgv-large", action="store_true", help="run the 48^3, N=7 FP64-vs-FP32 Taylor-Green study")
     ap.add_argument("--tgv-steps", type=int, default=200)
+    ap.add_argument("--ensemble", action="store_true", help="run the 64-member batched ensemble study")
+    ap.add_argument("--ens-steps", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args.gpus)
     if args.tgv_large:
         return run_tgv_large(args, local) if rank == 0 else 0
+    if args.ensemble:
+        return run_ensemble(args, local) if rank == 0 else 0
     if args.impl == "reference":
         return run_reference(args, world, rank)
 

@@ -141,6 +141,33 @@ dg_status dg_node_coords(dg_ctx* ctx, double* dX, dg_stream stream);
  * J[e][P]; either pointer may be NULL.  Device buffers. */
 dg_status dg_geometry(dg_ctx* ctx, double* dJa, double* dJ, dg_stream stream);
 
+/* ---- Batched ensemble (independent runs advanced together) ----------------
+ * An ensemble groups existing contexts on one device (each with its own mesh,
+ * N, gas constants; all with the same precision).  Members of equal N are
+ * advanced by persistent kernels that walk a tile table over all of those
+ * members; the nsteps step sequence of all members is one CUDA graph.  Tile
+ * shape (elements per block) and grid sizes per N are chosen by an autotuner
+ * on the first dg_ensemble_step (timing the candidates on the members' data
+ * without changing their states) and cached in the text file
+ * tune_cache_path (NULL: no cache), keyed by GPU name, N and precision. */
+typedef struct dg_ensemble dg_ensemble;
+
+/* The members stay owned by the caller and must outlive the ensemble.
+ * DG_EINVAL if a member is NULL or on another device or precision. */
+dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune_cache_path, dg_ensemble** out);
+dg_status dg_ensemble_destroy(dg_ensemble* ens);
+
+/* nsteps LSERK4-5 steps of every member r: state dU[r] with register dG[r]
+ * (device arrays of the member's dg_state_len), from time t[r] with step
+ * dt[r] (host arrays of n doubles).  Identical per member to dg_rk_step.
+ * Waits for earlier work on `stream`, then enqueues one graph launch. */
+dg_status dg_ensemble_step(dg_ensemble* ens, double* const* dU, double* const* dG, const double* t,
+                           const double* dt, int32_t nsteps, dg_stream stream);
+
+/* The tuned plan as JSON text (per N: members, elements per block, grids). */
+dg_status dg_ensemble_plan(const dg_ensemble* ens, char* buf, size_t len);
+const char* dg_ensemble_last_error(const dg_ensemble* ens);
+
 /* Measurement helper: runs `reps` LSERK stages on (dU, dG) (state advanced
  * with dt) and times each stage kernel with CUDA events on `stream`;
  * host_ms3 = average milliseconds per launch of { lifting, face flux,

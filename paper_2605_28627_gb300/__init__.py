@@ -29,7 +29,8 @@ IC_TGV, IC_MMS = 0, 1
 # Every symbol that include/dgsem.h declares.
 EXPORTS = ["dg_init", "dg_destroy", "dg_state_len", "dg_time_derivative", "dg_rk_step", "dg_advance_host",
            "dg_integrals", "dg_max_dt", "dg_initial_state", "dg_node_coords", "dg_geometry", "dg_profile_stages",
-           "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_last_error"]
+           "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
+           "dg_ensemble_step", "dg_ensemble_plan", "dg_ensemble_last_error", "dg_last_error"]
 
 
 class DGError(RuntimeError):
@@ -78,11 +79,18 @@ def load(build_if_missing: bool = True):
     L.dg_profile_stages.argtypes = [vp, vp, vp, f64, i32, C.POINTER(C.c_float), vp]
     L.dg_probe_peaks.argtypes = [C.c_int, dp]
     L.dg_conserved_totals_noalloc.argtypes = [vp, vp, i32, i32, vp, vp]
+    L.dg_ensemble_create.argtypes = [C.POINTER(vp), i32, C.c_char_p, C.POINTER(vp)]
+    L.dg_ensemble_destroy.argtypes = [vp]
+    L.dg_ensemble_step.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), dp, dp, i32, vp]
+    L.dg_ensemble_plan.argtypes = [vp, C.c_char_p, C.c_size_t]
+    L.dg_ensemble_last_error.argtypes = [vp]
+    L.dg_ensemble_last_error.restype = C.c_char_p
     L.dg_last_error.argtypes = [vp]
     L.dg_last_error.restype = C.c_char_p
     for name in ("dg_init", "dg_destroy", "dg_time_derivative", "dg_rk_step", "dg_advance_host", "dg_integrals",
                  "dg_max_dt", "dg_initial_state", "dg_node_coords", "dg_geometry", "dg_profile_stages",
-                 "dg_probe_peaks", "dg_conserved_totals_noalloc"):
+                 "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
+                 "dg_ensemble_step", "dg_ensemble_plan"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -254,3 +262,50 @@ def conserved_totals_noalloc(U, J, N: int, out=None, stream=None):
     if st != DG_OK:
         raise DGError(st, "dg_conserved_totals_noalloc rejected its arguments")
     return out
+
+
+class Ensemble:
+    """Independent runs (Solver objects on one GPU, same precision) advanced
+    together by the batched, autotuned ensemble kernels."""
+
+    def __init__(self, solvers, tune_cache_path=None):
+        self._L = load()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s._h.value for s in self.solvers])
+        h = C.c_void_p()
+        path = tune_cache_path.encode() if tune_cache_path else None
+        st = self._L.dg_ensemble_create(arr, len(self.solvers), path, C.byref(h))
+        if st != DG_OK:
+            raise DGError(st, "dg_ensemble_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.dg_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, Us, Gs, t, dt, nsteps=1, stream=None):
+        n = len(self.solvers)
+        for s, U, G in zip(self.solvers, Us, Gs):
+            s._chk_state(U)
+            s._chk_state(G)
+        pu = (C.c_void_p * n)(*[U.data_ptr() for U in Us])
+        pg = (C.c_void_p * n)(*[G.data_ptr() for G in Gs])
+        tt = (C.c_double * n)(*[float(v) for v in t])
+        dd = (C.c_double * n)(*[float(v) for v in dt])
+        st = self._L.dg_ensemble_step(self._h, pu, pg, tt, dd, int(nsteps), _stream_handle(stream))
+        if st != DG_OK:
+            raise DGError(st, self._L.dg_ensemble_last_error(self._h).decode())
+
+    def plan(self):
+        import json
+        buf = C.create_string_buffer(1 << 16)
+        if self._L.dg_ensemble_plan(self._h, buf, len(buf)) != DG_OK:
+            return None
+        return json.loads(buf.value.decode()) if buf.value else None

@@ -1,0 +1,455 @@
+// Stage-kernel bodies of R(U) (GALAEXI Sec. 3.1, Eqs. 2-3), shared by the
+// single-context kernels and the persistent ensemble kernels.  Each body
+// processes one tile (EPB elements, or one block of face nodes) given by an
+// explicit tile index, so the same code runs with blockIdx or a tile table.
+//
+// Volume body -- FP64-pipe-aware design (also used in FP32):
+//  * Symmetric pair reuse: F#(q_i, q_m) = F#(q_m, q_i), so each unordered
+//    pair on a line is evaluated once, in rounds of a fixed cyclic shift s;
+//    the partner's share goes through shared memory.
+//  * The diagonal terms 2 D_ii f(q_i) . Ja_i vanish for interior LGL nodes
+//    and cancel exactly against the -f . n sJ / w_0 part of the surface term
+//    at the two end nodes (2 D_00 = -1/w_0, 2 D_NN = 1/w_0), so neither is
+//    evaluated.
+//  * Reciprocals instead of divides, logarithmic means by the Ismail-Roe
+//    series with the reciprocal series for 1/F, constant factors folded into
+//    scaled copies of D, the series/log switch decided in integer ALU.
+#pragma once
+
+#include "dg_physics.cuh"
+
+namespace dg {
+
+// Element tiles: EPB elements per block, one thread per node.  The default
+// packs small elements until a block has at least 128 threads.
+constexpr int default_epb(int P) { return P >= 128 ? 1 : (128 + P - 1) / P; }
+
+template <int N, int EPB_ = default_epb((N + 1) * (N + 1) * (N + 1))>
+struct Shape {
+  static constexpr int n = N + 1;
+  static constexpr int P = n * n * n;
+  static constexpr int NN = n * n;
+  static constexpr int EPB = EPB_;
+  static constexpr int THREADS = EPB * P;
+};
+
+template <int N, int EPB_ = default_epb((N + 1) * (N + 1) * (N + 1))>
+struct VShape : Shape<N, EPB_> {
+  static constexpr int ROUNDS = (N + 1) / 2;    // shifts s = 1..n/2 (s = n/2 half-used for even n)
+  static constexpr int PER_ELEM = 32 * (N + 1) * (N + 1) * (N + 1);   // operator words of smem per element
+};
+
+template <int N, typename R, int EPB>
+constexpr size_t volume_smem_bytes() {
+  return sizeof(R) * (3 * (N + 1) * (N + 1) + (((N + 1) * (N + 1) + 3) & ~3) + EPB * VShape<N, EPB>::PER_ELEM);
+}
+
+// rcp for the operator type: FP64 by hardware approximation + one cubic
+// Newton-Raphson step (below 1 ulp); FP32 by the approximation alone (1 ulp).
+__device__ __forceinline__ double rcp_lf(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+__device__ __forceinline__ float rcp_lf(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ---------------------------------------------------------------------------
+// BR1 lifting (Sec. 3.1, Eq. 3), strong form with the non-conservative volume
+// part: g_l = (1/J)[ sum_d Ja^d_l D_d phi + sum_faces (phi* - phi) n_l sJ / w_0 ]
+// with phi* = (phi + phi_nbr)/2 and the element's own outward n sJ = (2s-1) Ja^d.
+// R is the operator arithmetic; metrics and the output gradients are in R.
+template <int N, typename R, int EPB>
+__device__ __forceinline__ void lift_body(const double* __restrict__ U, const R* __restrict__ metrics,
+                                          const int* __restrict__ elem_nbr, const int* __restrict__ elem_face,
+                                          const double* __restrict__ Dg, R* __restrict__ grad, int E, const Gas& g,
+                                          double inv_w0d, int blk) {
+  using S = Shape<N, EPB>;
+  constexpr int n = S::n, P = S::P;
+  __shared__ R sD[n * n];
+  __shared__ R sphi[S::EPB][4][P];
+  const int le = threadIdx.x / P, id = threadIdx.x % P;
+  const int e = blk * S::EPB + le;
+  const bool active = e < E;
+  for (int a = threadIdx.x; a < n * n; a += blockDim.x) sD[a] = R(Dg[a]);
+  const R gm1 = R(g.gm1), inv_R = R(g.inv_R), inv_w0 = R(inv_w0d);
+  R phi[4] = {0, 0, 0, 0};
+  if (active) {
+    const double* q = U + (size_t)e * 5 * P + id;
+    const R rho = R(q[0]), ir = rcp_lf(rho);
+    const R m0 = R(q[P]), m1 = R(q[2 * P]), m2 = R(q[3 * P]);
+    const R u = m0 * ir, v = m1 * ir, w = m2 * ir;
+    const R p = gm1 * (R(q[4 * P]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
+    phi[0] = u; phi[1] = v; phi[2] = w; phi[3] = p * ir * inv_R;
+    for (int a = 0; a < 4; ++a) sphi[le][a][id] = phi[a];
+  }
+  __syncthreads();
+  if (!active) return;
+  const int i = id % n, j = (id / n) % n, k = id / (n * n);
+  const int ijk[3] = {i, j, k};
+  R dd[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    R s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      s0 += sD[i * n + m] * sphi[le][a][vidx<n>(m, j, k)];
+      s1 += sD[j * n + m] * sphi[le][a][vidx<n>(i, m, k)];
+      s2 += sD[k * n + m] * sphi[le][a][vidx<n>(i, j, m)];
+    }
+    dd[a][0] = s0; dd[a][1] = s1; dd[a][2] = s2;
+  }
+  const R* mt = metrics + (size_t)e * 10 * P + id;
+  R Ja[9];
+#pragma unroll
+  for (int r = 0; r < 9; ++r) Ja[r] = mt[r * P];
+  R gr[12];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int l = 0; l < 3; ++l) gr[a * 3 + l] = Ja[0 * 3 + l] * dd[a][0] + Ja[1 * 3 + l] * dd[a][1] + Ja[2 * 3 + l] * dd[a][2];
+  // surface part: one term per face that contains the node
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int id_d = ijk[d];
+    if (id_d != 0 && id_d != N) continue;
+    const int s = id_d == N ? 1 : 0;
+    const int f = 2 * d + s;
+    const int code = elem_face[e * 6 + f];
+    const int nb = elem_nbr[e * 6 + f];
+    const int e2 = nb >> 3, f2 = nb & 7;
+    const int p = d == 0 ? j : i;
+    const int qq = d == 2 ? j : k;
+    int p2, q2;
+    apply_flip<n>(code & 7, p, qq, p2, q2);
+    const int id2 = face_node<n>(f2, p2, q2);
+    const double* q = U + (size_t)e2 * 5 * P + id2;
+    const R rho = R(q[0]), ir = rcp_lf(rho);
+    const R m0 = R(q[P]), m1 = R(q[2 * P]), m2 = R(q[3 * P]);
+    const R u = m0 * ir, v = m1 * ir, w = m2 * ir;
+    const R pr = gm1 * (R(q[4 * P]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
+    const R onb[4] = {u, v, w, pr * ir * inv_R};
+    const R sg = s ? inv_w0 : -inv_w0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const R jump = R(0.5) * (onb[a] - phi[a]) * sg;
+#pragma unroll
+      for (int l = 0; l < 3; ++l) gr[a * 3 + l] += jump * Ja[d * 3 + l];
+    }
+  }
+  const R iJ = mt[9 * P];
+  R* go = grad + (size_t)e * 12 * P + id;
+#pragma unroll
+  for (int r = 0; r < 12; ++r) go[r * P] = gr[r] * iJ;
+}
+
+// ---------------------------------------------------------------------------
+// Surface flux on every face node, master orientation (Sec. 3.1): Riemann flux
+// (LLF, or the two-point EC flux) minus the BR1 average of the viscous fluxes,
+// times the surface element:  F* = (F_adv(qM, qS; n) - 1/2 (f_v,M + f_v,S) . n) sJ.
+template <int N, typename R>
+__device__ __forceinline__ void face_body(const double* __restrict__ U, const R* __restrict__ grad,
+                                          const FaceInfo* __restrict__ faces, const R* __restrict__ facegeo,
+                                          R* __restrict__ fstar, int F, const Gas& g, long gid) {
+  constexpr int n = N + 1, P = n * n * n, NN = n * n;
+  if (gid >= (long)F * NN) return;
+  const int f = (int)(gid / NN), pq = (int)(gid % NN);
+  const int p = pq % n, q = pq / n;
+  const FaceInfo fi = faces[f];
+  const int eM = fi.master >> 3, fM = fi.master & 7, eS = fi.slave >> 3, fS = fi.slave & 7;
+  int p2, q2;
+  apply_flip<n>(fi.flip, p, q, p2, q2);
+  const int idM = face_node<n>(fM, p, q), idS = face_node<n>(fS, p2, q2);
+  R qL[5], qR[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    qL[v] = R(U[((size_t)eM * 5 + v) * P + idM]);
+    qR[v] = R(U[((size_t)eS * 5 + v) * P + idS]);
+  }
+  const R gm1 = R(g.gm1), gam = R(g.gamma);
+  const R* fg = facegeo + (size_t)f * 4 * NN + pq;
+  const R nx = fg[0], ny = fg[NN], nz = fg[2 * NN], sJ = fg[3 * NN];
+  const R irL = rcp_lf(qL[0]), irR = rcp_lf(qR[0]);
+  const R uL = qL[1] * irL, vL = qL[2] * irL, wL = qL[3] * irL;
+  const R uR = qR[1] * irR, vR = qR[2] * irR, wR = qR[3] * irR;
+  const R pL = gm1 * (qL[4] - R(0.5) * (qL[1] * uL + qL[2] * vL + qL[3] * wL));
+  const R pR = gm1 * (qR[4] - R(0.5) * (qR[1] * uR + qR[2] * vR + qR[3] * wR));
+  R fa[5];
+  if (g.surf_flux == DG_FLUX_EC) {
+    NodePrim<R> a{qL[0], uL, vL, wL, pL, R(0.5) * qL[0] / pL};
+    NodePrim<R> b{qR[0], uR, vR, wR, pR, R(0.5) * qR[0] / pR};
+    ec_flux<R>(a, b, nx, ny, nz, R(g.inv_gm1), fa);
+  } else {
+    R fL[5], fR[5];
+    euler_flux<R>(qL, uL, vL, wL, pL, nx, ny, nz, fL);
+    euler_flux<R>(qR, uR, vR, wR, pR, nx, ny, nz, fR);
+    const R cL = sqrt(gam * pL * irL), cR = sqrt(gam * pR * irR);
+    const R lL = fabs(uL * nx + vL * ny + wL * nz) + cL;
+    const R lR = fabs(uR * nx + vR * ny + wR * nz) + cR;
+    const R lmax = lR > lL ? lR : lL;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) fa[v] = R(0.5) * (fL[v] + fR[v]) - R(0.5) * lmax * (qR[v] - qL[v]);
+  }
+  R gL[12], gR[12];
+#pragma unroll
+  for (int r = 0; r < 12; ++r) {
+    gL[r] = grad[((size_t)eM * 12 + r) * P + idM];
+    gR[r] = grad[((size_t)eS * 12 + r) * P + idS];
+  }
+  R fvL[4], fvR[4];
+  const R mu = R(g.mu), lam = R(g.mu * g.kappa);
+  visc_flux<R>(gL, uL, vL, wL, mu, lam, nx, ny, nz, fvL);
+  visc_flux<R>(gR, uR, vR, wR, mu, lam, nx, ny, nz, fvR);
+  R* fo = fstar + (size_t)f * 5 * NN + pq;
+  fo[0] = fa[0] * sJ;
+#pragma unroll
+  for (int v = 1; v < 5; ++v) fo[(size_t)v * NN] = (fa[v] - R(0.5) * (fvL[v - 1] + fvR[v - 1])) * sJ;
+}
+
+// 1/x: hardware reciprocal approximation refined by one cubic Newton-Raphson
+// step y <- y (1 + e + e^2), e = 1 - x y, which cubes the relative error
+// (2^-20 -> below 1 ulp).  In FP32 the approximation alone is within 1 ulp.
+__device__ __forceinline__ double rcp_op(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y, 1.0);
+  const double t = fma(e, e, e);
+  return fma(y, t, y);
+}
+__device__ __forceinline__ float rcp_op(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Switch of the logarithmic mean between the series and the logarithm.  In
+// FP64 below u = 1e-4 (four series terms are exact to rounding; decided on the
+// high word in integer ALU), in FP32 below u = 1e-2 (truncation < 1e-9).
+__device__ __forceinline__ bool small_u(double u) { return __double2hiint(u) < 0x3F1A36E2; }
+__device__ __forceinline__ bool small_u(float u) { return u < 1e-2f; }
+
+// 1/F(u) = u^(1/2) / atanh(u^(1/2)) = 1 - u/3 - 4u^2/45 - 44u^3/945 - ...
+template <typename R>
+__device__ __forceinline__ R inv_atanh_ratio(R u) {
+  return fma(u, fma(u, fma(u, R(-44.0 / 945.0), R(-4.0 / 45.0)), R(-1.0 / 3.0)), R(1));
+}
+// F(u) = atanh(u^(1/2)) / u^(1/2) = 1 + u/3 + u^2/5 + u^3/7 + ...
+template <typename R>
+__device__ __forceinline__ R atanh_ratio(R u) {
+  return fma(u, fma(u, fma(u, R(1.0 / 7.0), R(1.0 / 5.0)), R(1.0 / 3.0)), R(1));
+}
+// F for the logarithmic branch, in the ratio form of Ismail & Roe.
+template <typename R>
+__device__ __noinline__ R atanh_ratio_log(R a, R b) {
+  const R z = a / b;
+  return log(z) / (R(2) * ((z - R(1)) / (z + R(1))));
+}
+
+// R is the operator arithmetic: double (FP64 path) or float (FP32-operator
+// path, state and RK update stay FP64).  metrics, grad and fstar are stored in R.
+template <int N, typename R, int EPB_>
+__device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restrict__ metrics,
+                                            const double* __restrict__ iJ64, const R* __restrict__ grad,
+                                            const R* __restrict__ fstar, const int* __restrict__ elem_face,
+                                            const double* __restrict__ X, const double* __restrict__ Dg, int E,
+                                            const Gas& g, double inv_w0d, int blk) {
+  using S = VShape<N, EPB_>;
+  constexpr int n = S::n, P = S::P, NN = S::NN, EPB = S::EPB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* smem = reinterpret_cast<R*>(smem_raw);
+  R* sD = smem;                       // D
+  R* sT0 = sD + n * n;                // D/4   (mass: X = 8 f_rho)
+  R* sT1 = sT0 + n * n;               // D/8   (momentum: M = 16 f_m)
+  R* sT2 = sT1 + n * n;               // D/16  (energy: 32 f_E)
+  const int le = threadIdx.x / P, id = threadIdx.x - le * P;
+  R* base = sT2 + ((n * n + 3) & ~3) + le * S::PER_ELEM;
+  R* sR = base;                       // rho
+  R* sU = sR + P;                     // u, v, w
+  R* sB = sU + 3 * P;                 // beta = rho / (2 p)
+  R* sK = sB + P;                     // |u|^2
+  R* sJa = sK + P;                    // [9][P]  Ja^d_l at row d*3+l
+  R* sFv = sJa + 9 * P;               // [3][4][P] (f_v . Ja^d), momentum + energy
+  R* sX = sFv + 12 * P;               // [5][P] exchange of partner shares
+  const int e = blk * EPB + le;
+  const bool active = e < E;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const double d = Dg[t];
+    sD[t] = R(d);
+    sT0[t] = R(0.25 * d);
+    sT1[t] = R(0.125 * d);
+    sT2[t] = R(0.0625 * d);
+  }
+  const R inv_w0 = R(inv_w0d);
+  double q[5] = {0, 0, 0, 0, 0};
+  R Ja[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  R rho = R(1), u = 0, v = 0, w = 0, beta = 0, kk = 0;
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < 5; ++r) q[r] = a.U[((size_t)e * 5 + r) * P + id];
+    const R* mt = metrics + (size_t)e * 10 * P + id;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) { Ja[r] = mt[r * P]; sJa[r * P + id] = Ja[r]; }
+    rho = R(q[0]);
+    const R ir = rcp_op(rho);
+    u = R(q[1]) * ir; v = R(q[2]) * ir; w = R(q[3]) * ir;
+    kk = u * u + v * v + w * w;
+    const R p = R(g.gm1) * fma(R(-0.5) * rho, kk, R(q[4]));
+    beta = R(0.5) * rho * rcp_op(p);
+    sR[id] = rho; sU[id] = u; sU[P + id] = v; sU[2 * P + id] = w; sB[id] = beta; sK[id] = kk;
+    R gr[12];
+    const R* gg = grad + (size_t)e * 12 * P + id;
+#pragma unroll
+    for (int r = 0; r < 12; ++r) gr[r] = gg[r * P];
+    const R mu = R(g.mu), lam = R(g.mu * g.kappa);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      R fv[4];
+      visc_flux<R>(gr, u, v, w, mu, lam, Ja[d * 3], Ja[d * 3 + 1], Ja[d * 3 + 2], fv);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) sFv[(d * 4 + c) * P + id] = fv[c];
+    }
+  }
+  __syncthreads();
+  const int i = id % n, j = (id / n) % n, k = id / NN;
+  const int ijk[3] = {i, j, k};
+  const R inv4 = R(4.0 * g.inv_gm1);
+  R acc[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int r = ijk[d];
+    const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
+    const int line0 = id - r * stride;
+#pragma unroll 1
+    for (int s = 1; s <= S::ROUNDS; ++s) {
+      const bool half = (2 * s == n);
+      const int m = r + s < n ? r + s : r + s - n;
+      const int mid = line0 + m * stride;
+      if (active && !(half && r >= s)) {
+        const R rb = sR[mid], bb = sB[mid];
+        const R sr = rho + rb, sb = beta + bb;
+        const R rr = rcp_op(sr), rbt = rcp_op(sb);
+        const R fr = (rho - rb) * rr, fb = (beta - bb) * rbt;
+        const R ur = fr * fr, ub = fb * fb;
+        R rln2, hib;                    // 2 rho_ln and 1/(2 beta_ln)
+        if (small_u(ur)) rln2 = sr * inv_atanh_ratio(ur);
+        else rln2 = sr / atanh_ratio_log(rho, rb);
+        if (small_u(ub)) hib = atanh_ratio(ub) * rbt;
+        else hib = atanh_ratio_log(beta, bb) * rbt;
+        const R su0 = u + sU[mid], su1 = v + sU[P + mid], su2 = w + sU[2 * P + mid];
+        const R sn0 = Ja[d * 3] + sJa[(d * 3) * P + mid];
+        const R sn1 = Ja[d * 3 + 1] + sJa[(d * 3 + 1) * P + mid];
+        const R sn2 = Ja[d * 3 + 2] + sJa[(d * 3 + 2) * P + mid];
+        const R un4 = fma(su0, sn0, fma(su1, sn1, su2 * sn2));
+        const R Xf = rln2 * un4;                      // 8 f_rho
+        const R Y4 = R(4) * sr * rbt;                  // 16 p_hat / |n_avg| scale
+        const R M0 = fma(Xf, su0, Y4 * sn0);          // 16 f_m
+        const R M1 = fma(Xf, su1, Y4 * sn1);
+        const R M2 = fma(Xf, su2, Y4 * sn2);
+        const R Z = fma(hib, inv4, -(kk + sK[mid]));
+        const R E32 = fma(Xf, Z, fma(su0, M0, fma(su1, M1, su2 * M2)));   // 32 f_E
+        const int rm = r * n + m;
+        acc[0] = fma(sT0[rm], Xf, acc[0]);
+        acc[1] = fma(sT1[rm], M0, acc[1]);
+        acc[2] = fma(sT1[rm], M1, acc[2]);
+        acc[3] = fma(sT1[rm], M2, acc[3]);
+        acc[4] = fma(sT2[rm], E32, acc[4]);
+        sX[mid] = Xf; sX[P + mid] = M0; sX[2 * P + mid] = M1; sX[3 * P + mid] = M2; sX[4 * P + mid] = E32;
+      }
+      __syncthreads();
+      const int src = r - s >= 0 ? r - s : r - s + n;   // the node whose pair (src, r) wrote here
+      if (active && !(half && src >= s)) {
+        const int rm = r * n + src;
+        acc[0] = fma(sT0[rm], sX[id], acc[0]);
+        acc[1] = fma(sT1[rm], sX[P + id], acc[1]);
+        acc[2] = fma(sT1[rm], sX[2 * P + id], acc[2]);
+        acc[3] = fma(sT1[rm], sX[3 * P + id], acc[3]);
+        acc[4] = fma(sT2[rm], sX[4 * P + id], acc[4]);
+      }
+      __syncthreads();
+    }
+  }
+  if (!active) return;
+  // viscous volume term: -sum_m D_rm (f_v . Ja^d)_m
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int r = ijk[d];
+    const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
+    const int line0 = id - r * stride;
+    R v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      const R Drm = sD[r * n + m];
+      const int mid = line0 + m * stride;
+      v0 = fma(Drm, sFv[(d * 4 + 0) * P + mid], v0);
+      v1 = fma(Drm, sFv[(d * 4 + 1) * P + mid], v1);
+      v2 = fma(Drm, sFv[(d * 4 + 2) * P + mid], v2);
+      v3 = fma(Drm, sFv[(d * 4 + 3) * P + mid], v3);
+    }
+    acc[1] -= v0; acc[2] -= v1; acc[3] -= v2; acc[4] -= v3;
+  }
+  // surface integral: (F*_out + f_v . n sJ) / w_0 at each face containing the
+  // node (the -f . n sJ part has cancelled against the diagonal volume term)
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int id_d = ijk[d];
+    if (id_d != 0 && id_d != N) continue;
+    const int sgn = id_d == N ? 1 : 0;
+    const int code = elem_face[e * 6 + 2 * d + sgn];
+    const int fid = code >> 4;
+    const int pp = d == 0 ? j : i;
+    const int qq = d == 2 ? j : k;
+    const R* fsr;
+    R fs_sign;
+    if (code & 8) {
+      fsr = fstar + (size_t)fid * 5 * NN + pp + n * qq;
+      fs_sign = inv_w0;
+    } else {
+      int p2, q2;
+      apply_flip<n>(code & 7, pp, qq, p2, q2);
+      fsr = fstar + (size_t)fid * 5 * NN + p2 + n * q2;
+      fs_sign = -inv_w0;
+    }
+    const R vs = sgn ? inv_w0 : -inv_w0;
+    acc[0] = fma(fs_sign, fsr[0], acc[0]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      acc[1 + c] = fma(fs_sign, fsr[(c + 1) * NN], fma(vs, sFv[(d * 4 + c) * P + id], acc[1 + c]));
+  }
+  const double t = a.clock[0] + a.c_stage * a.clock[1];
+  double src[5] = {0, 0, 0, 0, 0};
+  if (g.source == DG_SOURCE_MMS) {
+    const double x = X[((size_t)e * 3 + 0) * P + id], y = X[((size_t)e * 3 + 1) * P + id],
+                 z = X[((size_t)e * 3 + 2) * P + id];
+    // density wave rho = 2 + A sin(pi (x+y+z-t)), u = (1,1,1), p = 1:
+    // residual of Eq. 1 = [2r', 2r', 2r', 2r', 3r' - lambda Lap T], r' = pi A cos(phi)
+    double sphi, cphi;
+    sincospi(x + y + z - t, &sphi, &cphi);
+    const double A = g.mms_amp;
+    const double rw = 2.0 + A * sphi;
+    const double rp = M_PI * A * cphi;
+    const double lapT = 3.0 * g.inv_R * (M_PI * M_PI * A * sphi + 2.0 * rp * rp / rw) / (rw * rw);
+    src[0] = src[1] = src[2] = src[3] = 2.0 * rp;
+    src[4] = 3.0 * rp - g.mu * g.kappa * lapT;
+  }
+  // Jacobian, source and RK update in FP64
+  const double iJ = iJ64[(size_t)e * 10 * P + 9 * P + id];
+  if (a.mode == 0) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) a.Ut[((size_t)e * 5 + c) * P + id] = fma(-(double)acc[c], iJ, src[c]);
+  } else {
+    const double dt = a.clock[1];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const size_t o = ((size_t)e * 5 + c) * P + id;
+      const double gk = fma(a.A, a.Gk[o], dt * fma(-(double)acc[c], iJ, src[c]));
+      a.Gk[o] = gk;
+      a.Uw[o] = fma(a.B, gk, q[c]);
+    }
+  }
+}
+
+}  // namespace dg
