@@ -141,6 +141,41 @@ dg_status dg_node_coords(dg_ctx* ctx, double* dX, dg_stream stream);
  * J[e][P]; either pointer may be NULL.  Device buffers. */
 dg_status dg_geometry(dg_ctx* ctx, double* dJa, double* dJ, dg_stream stream);
 
+/* ---- Discrete adjoint (FP64 contexts) -------------------------------------
+ * Hand-written reverse-mode kernels of the discrete operator: the exact
+ * transpose of the FP64 R(U) of dg_time_derivative (branches of the LLF speed
+ * maximum, |.| and the log-mean switch follow the primal state).  The paper
+ * has no adjoint; these entries exist for gradient-based use of the solver.
+ * dJdmu, where present, is a device double that is ACCUMULATED (+=) with
+ * lambda . dR/dmu (R is linear in the constant viscosity mu); NULL skips it. */
+
+/* dout = (dR/dU)^T dv at dU (all device [state_len]); dout may alias dv. */
+dg_status dg_time_derivative_vjp(dg_ctx* ctx, const double* dU, const double* dv, double* dout, double* dJdmu,
+                                 double t, dg_stream stream);
+
+/* Adjoint of one LSERK4-5 step from dU_n (state at the step's start, time t):
+ * dlam_n = (dU_{n+1}/dU_n)^T dlam_np1 (may alias), dJdmu += the step's
+ * lambda . dU_{n+1}/dmu.  The five stage states are recomputed from dU_n. */
+dg_status dg_adjoint_step(dg_ctx* ctx, const double* dU_n, const double* dlam_np1, double* dlam_n, double* dJdmu,
+                          double t, double dt, dg_stream stream);
+
+/* Adjoint of nsteps LSERK4-5 steps from dU0 at t0: dlam0 = (dU_T/dU_0)^T dlamT
+ * (may alias), dJdmu += lambda . dU_T/dmu, with binomial checkpointing: at
+ * most max_snapshots stored states (>= 1), forward recomputation in between.
+ * host_counts2 (may be NULL) receives {recomputed forward steps, adjoint
+ * steps}.  Synchronises the stream. */
+dg_status dg_adjoint_solve(dg_ctx* ctx, const double* dU0, const double* dlamT, double* dlam0, double* dJdmu,
+                           double t0, double dt, int32_t nsteps, int32_t max_snapshots, int64_t* host_counts2,
+                           dg_stream stream);
+
+/* Objective J = sum_nodes w_i w_j w_k J 1/2 rho |u|^2 (LGL quadrature of the
+ * volume-integrated kinetic energy) into *host_J; dgrad (device, may be NULL)
+ * receives dJ/dU.  Synchronises the stream. */
+dg_status dg_kinetic_energy(dg_ctx* ctx, const double* dU, double* dgrad, double* host_J, dg_stream stream);
+
+/* Change the constant viscosity mu of a context (e.g. for derivative checks). */
+dg_status dg_set_viscosity(dg_ctx* ctx, double mu);
+
 /* ---- Batched ensemble (independent runs advanced together) ----------------
  * An ensemble groups existing contexts on one device (each with its own mesh,
  * N, gas constants; all with the same precision).  Members of equal N are

@@ -21,6 +21,8 @@
 //  * Logarithmic mean by the Ismail-Roe (2009) series/log split, with the
 //    switch at xi^2 < 1e-4 and four series terms (truncation < 1e-17).
 //  * Constant viscosity, Stokes hypothesis, lambda = mu c_p / Pr.
+//  * Derivatives at the kinks of the LLF speed max(|u.n| + c) (ties, u.n = 0,
+//    to within 1e-12 of the local scale) are the mean of the one-sided ones.
 //  * LSERK4-5 of Carpenter and Kennedy (1994), 2N storage.
 #include <cmath>
 #include <cstdint>
@@ -61,6 +63,23 @@ inline double val(double a) { return a; }
 using std::sqrt; using std::log; using std::fabs;
 // max with ties going to the first argument (the value decides the branch)
 template <class T> inline T vmax(T a, T b) { return (val(b) > val(a)) ? b : a; }
+
+// Non-differentiable points of the LLF speed max(|u.n| + c): where the two
+// arguments tie, or u.n vanishes, to within 1e-12 of the local scale (as on
+// the symmetry planes of a symmetric flow, where the values differ only by
+// rounding), the derivative is the mean of the one-sided derivatives, which
+// is what central differences measure there.  Elsewhere the value decides.
+inline double vmax_kink(double a, double b) { return b > a ? b : a; }
+inline Dual vmax_kink(Dual a, Dual b) {
+  if (std::fabs(a.v - b.v) <= 1e-12 * std::max(std::fabs(a.v), std::fabs(b.v)))
+    return Dual(b.v > a.v ? b.v : a.v, 0.5 * (a.d + b.d));
+  return b.v > a.v ? b : a;
+}
+inline double abs_kink(double x, double) { return std::fabs(x); }
+inline Dual abs_kink(Dual x, double scale) {
+  if (std::fabs(x.v) <= 1e-12 * scale) return Dual(std::fabs(x.v), 0.0);
+  return x.v < 0 ? -x : x;
+}
 
 // ---------------------------------------------------------------------------
 // 1-D basis on Legendre-Gauss-Lobatto nodes (Sec. 3.1: collocation at LGL
@@ -439,7 +458,7 @@ static inline void llf_flux(const Params& pr, const T qL[5], const Prim<T>& L,
   T cL = sqrt(pr.gamma * L.p / L.rho), cR = sqrt(pr.gamma * Rr.p / Rr.rho);
   T unL = L.u[0] * nv[0] + L.u[1] * nv[1] + L.u[2] * nv[2];
   T unR = Rr.u[0] * nv[0] + Rr.u[1] * nv[1] + Rr.u[2] * nv[2];
-  T lmax = vmax(fabs(unL) + cL, fabs(unR) + cR);
+  T lmax = vmax_kink(abs_kink(unL, val(cL)) + cL, abs_kink(unR, val(cR)) + cR);
   for (int v = 0; v < 5; ++v) out[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lmax * (qR[v] - qL[v]);
 }
 

@@ -30,7 +30,8 @@ IC_TGV, IC_MMS = 0, 1
 EXPORTS = ["dg_init", "dg_destroy", "dg_state_len", "dg_time_derivative", "dg_rk_step", "dg_advance_host",
            "dg_integrals", "dg_max_dt", "dg_initial_state", "dg_node_coords", "dg_geometry", "dg_profile_stages",
            "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
-           "dg_ensemble_step", "dg_ensemble_plan", "dg_ensemble_last_error", "dg_last_error"]
+           "dg_ensemble_step", "dg_ensemble_plan", "dg_ensemble_last_error", "dg_time_derivative_vjp",
+           "dg_adjoint_step", "dg_adjoint_solve", "dg_kinetic_energy", "dg_set_viscosity", "dg_last_error"]
 
 
 class DGError(RuntimeError):
@@ -85,12 +86,18 @@ def load(build_if_missing: bool = True):
     L.dg_ensemble_plan.argtypes = [vp, C.c_char_p, C.c_size_t]
     L.dg_ensemble_last_error.argtypes = [vp]
     L.dg_ensemble_last_error.restype = C.c_char_p
+    L.dg_time_derivative_vjp.argtypes = [vp, vp, vp, vp, vp, f64, vp]
+    L.dg_adjoint_step.argtypes = [vp, vp, vp, vp, vp, f64, f64, vp]
+    L.dg_adjoint_solve.argtypes = [vp, vp, vp, vp, vp, f64, f64, i32, i32, C.POINTER(C.c_int64), vp]
+    L.dg_kinetic_energy.argtypes = [vp, vp, vp, dp, vp]
+    L.dg_set_viscosity.argtypes = [vp, f64]
     L.dg_last_error.argtypes = [vp]
     L.dg_last_error.restype = C.c_char_p
     for name in ("dg_init", "dg_destroy", "dg_time_derivative", "dg_rk_step", "dg_advance_host", "dg_integrals",
                  "dg_max_dt", "dg_initial_state", "dg_node_coords", "dg_geometry", "dg_profile_stages",
                  "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
-                 "dg_ensemble_step", "dg_ensemble_plan"):
+                 "dg_ensemble_step", "dg_ensemble_plan", "dg_time_derivative_vjp", "dg_adjoint_step",
+                 "dg_adjoint_solve", "dg_kinetic_energy", "dg_set_viscosity"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -231,6 +238,53 @@ class Solver:
         self._check(self._L.dg_profile_stages(self._h, _ptr(U), _ptr(G), float(dt), int(reps), ms,
                                               _stream_handle(stream)))
         return [float(v) for v in ms]
+
+    # ---- discrete adjoint
+    def set_viscosity(self, mu):
+        self._check(self._L.dg_set_viscosity(self._h, float(mu)))
+        self.mu = float(mu)
+
+    def time_derivative_vjp(self, U, v, out=None, dJdmu=None, t=0.0, stream=None):
+        """(dR/dU)^T v; dJdmu (1-element float64 CUDA tensor) += v . dR/dmu."""
+        self._chk_state(U)
+        self._chk_state(v)
+        if out is None:
+            out = self.empty_state()
+        self._check(self._L.dg_time_derivative_vjp(self._h, _ptr(U), _ptr(v), _ptr(out),
+                                                   _ptr(dJdmu) if dJdmu is not None else None, float(t),
+                                                   _stream_handle(stream)))
+        return out
+
+    def adjoint_step(self, U_n, lam_np1, lam_n=None, dJdmu=None, t=0.0, dt=1e-3, stream=None):
+        self._chk_state(U_n)
+        self._chk_state(lam_np1)
+        if lam_n is None:
+            lam_n = self.empty_state()
+        self._check(self._L.dg_adjoint_step(self._h, _ptr(U_n), _ptr(lam_np1), _ptr(lam_n),
+                                            _ptr(dJdmu) if dJdmu is not None else None, float(t), float(dt),
+                                            _stream_handle(stream)))
+        return lam_n
+
+    def adjoint_solve(self, U0, lamT, t0, dt, nsteps, max_snapshots=16, lam0=None, dJdmu=None, stream=None):
+        """Adjoint of nsteps LSERK4-5 steps with binomial checkpointing;
+        returns (lam0, (recomputed forward steps, adjoint steps))."""
+        self._chk_state(U0)
+        self._chk_state(lamT)
+        if lam0 is None:
+            lam0 = self.empty_state()
+        counts = (C.c_int64 * 2)()
+        self._check(self._L.dg_adjoint_solve(self._h, _ptr(U0), _ptr(lamT), _ptr(lam0),
+                                             _ptr(dJdmu) if dJdmu is not None else None, float(t0), float(dt),
+                                             int(nsteps), int(max_snapshots), counts, _stream_handle(stream)))
+        return lam0, (int(counts[0]), int(counts[1]))
+
+    def kinetic_energy(self, U, grad=None, stream=None):
+        """J = LGL quadrature of 1/2 rho |u|^2; fills grad = dJ/dU if given."""
+        self._chk_state(U)
+        out = C.c_double()
+        self._check(self._L.dg_kinetic_energy(self._h, _ptr(U), _ptr(grad) if grad is not None else None,
+                                              C.byref(out), _stream_handle(stream)))
+        return out.value
 
     def geometry(self, stream=None):
         import torch

@@ -1,0 +1,567 @@
+// Discrete adjoint of R(U) and of the LSERK4-5 step (FP64).
+//
+// (dR/dU)^T lambda is the exact transpose of the discrete operator of
+// dg_stage.cuh, evaluated by hand-written reverse-mode kernels:
+//   A1 volume   : split-form pairs (two-point flux VJP, symmetric reuse with the
+//                 partner's share through shared memory), viscous volume term
+//                 (D^T, then the viscous-flux VJP), the surface flux seeds;
+//   A2 face     : LLF / two-point flux VJP and the BR1-averaged viscous flux VJP
+//                 on every face node, both sides;
+//   A3 gather   : per node, the face contributions of the node's faces;
+//   A4 lifting  : transpose of the BR1 lifting (D^T along lines, own and
+//                 neighbour surface terms), then the primitive-variable VJP.
+// Everything is gathered (no atomics); d/dmu is reduced from block partials
+// in a fixed order.  The step adjoint recomputes the five stage states from
+// the step's start state and runs the stages backwards; dg_adjoint_solve runs
+// the whole time interval backwards with binomial checkpointing.
+#include <algorithm>
+#include <vector>
+
+#include "dg_adjoint_fn.cuh"
+#include "dg_stage.cuh"
+
+namespace dg {
+
+struct AdjBufs {
+  double* qbar;      // [E][5][P]   conserved adjoint from the volume kernel
+  double* gbar;      // [E][12][P]  gradient adjoint from the volume kernel
+  double* fseed;     // [F][2][5][NN] surface-flux adjoint seeds (master, slave side)
+  double* face;      // [F][2][17][NN] per side: conserved adjoint (5) + gradient adjoint (12)
+  double* gtil;      // [E][12][P]  total gradient adjoint / J
+  double* mupart;    // block partials of d/dmu
+  int n_mu;
+};
+
+// ---------------------------------------------------------------------------
+// A1: volume adjoint.  lamV = -lambda / J.
+template <int N>
+__global__ void __launch_bounds__(Shape<N>::THREADS)
+k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const double* __restrict__ metrics,
+             const double* __restrict__ grad, const int* __restrict__ elem_face, const double* __restrict__ Dg,
+             int E, Gas g, double inv_w0, AdjBufs b) {
+  using S = Shape<N>;
+  constexpr int n = S::n, P = S::P, NN = S::NN, EPB = S::EPB;
+  constexpr int ROUNDS = n / 2;
+  extern __shared__ double adj_smem[];
+  double* sD = adj_smem;                                   // [n*n]
+  double* base = adj_smem + ((n * n + 1) & ~1);
+  __shared__ double smu[S::THREADS];
+  const int le = threadIdx.x / P, id = threadIdx.x - le * P;
+  double* eb = base + (size_t)le * 25 * P;
+  auto sPr = [&](int c, int node) -> double& { return eb[c * P + node]; };          // rho, u, v, w, p, beta
+  auto sJa = [&](int c, int node) -> double& { return eb[(6 + c) * P + node]; };    // [9]
+  auto sL = [&](int c, int node) -> double& { return eb[(15 + c) * P + node]; };    // lamV [5]
+  auto sX = [&](int c, int node) -> double& { return eb[(20 + c) * P + node]; };    // partner's adjoint [5]
+  const int e = blockIdx.x * EPB + le;
+  const bool active = e < E;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = Dg[t];
+  double q[5] = {1, 0, 0, 0, 1}, Ja[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, iJ = 0.0, lv[5] = {0, 0, 0, 0, 0};
+  NodePrim<double> me{1, 0, 0, 0, 1, 0.5};
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) q[c] = U[((size_t)e * 5 + c) * P + id];
+    const double* mt = metrics + (size_t)e * 10 * P + id;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) { Ja[r] = mt[r * P]; sJa(r, id) = Ja[r]; }
+    iJ = mt[9 * P];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) { lv[c] = -lam[((size_t)e * 5 + c) * P + id] * iJ; sL(c, id) = lv[c]; }
+    const double ir = 1.0 / q[0];
+    me.rho = q[0]; me.u = q[1] * ir; me.v = q[2] * ir; me.w = q[3] * ir;
+    me.p = g.gm1 * (q[4] - 0.5 * (q[1] * me.u + q[2] * me.v + q[3] * me.w));
+    me.beta = 0.5 * q[0] / me.p;
+    sPr(0, id) = me.rho; sPr(1, id) = me.u; sPr(2, id) = me.v; sPr(3, id) = me.w;
+    sPr(4, id) = me.p; sPr(5, id) = me.beta;
+  }
+  __syncthreads();
+  const int i = id % n, j = (id / n) % n, k = id / NN;
+  const int ijk[3] = {i, j, k};
+  double pr[5] = {0, 0, 0, 0, 0};   // own primitive adjoint (rho, u, v, w, p)
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int r = ijk[d];
+    const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
+    const int line0 = id - r * stride;
+#pragma unroll 1
+    for (int s = 1; s <= ROUNDS; ++s) {
+      const bool half = (2 * s == n);
+      const int m = r + s < n ? r + s : r + s - n;
+      const int mid = line0 + m * stride;
+      double pm[5] = {0, 0, 0, 0, 0};
+      if (active && !(half && r >= s)) {
+        NodePrim<double> ot{sPr(0, mid), sPr(1, mid), sPr(2, mid), sPr(3, mid), sPr(4, mid), sPr(5, mid)};
+        const double nx = 0.5 * (Ja[d * 3] + sJa(d * 3, mid));
+        const double ny = 0.5 * (Ja[d * 3 + 1] + sJa(d * 3 + 1, mid));
+        const double nz = 0.5 * (Ja[d * 3 + 2] + sJa(d * 3 + 2, mid));
+        const double Drm = sD[r * n + m], Dmr = sD[m * n + r];
+        double wb[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) wb[c] = 2.0 * (Drm * lv[c] + Dmr * sL(c, mid));
+        ec_flux_vjp(me, ot, nx, ny, nz, g.inv_gm1, wb, pr, pm);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) sX(c, mid) = pm[c];
+      }
+      __syncthreads();
+      const int src = r - s >= 0 ? r - s : r - s + n;
+      if (active && !(half && src >= s)) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) pr[c] += sX(c, id);
+      }
+      __syncthreads();
+    }
+  }
+  double mub = 0.0;
+  if (active) {
+    // viscous volume term: Fv_bar^d(m) = -sum_i D_im lamV_i, plus the surface term sg lamV / w_0
+    double gr[12];
+    const double* gg = grad + (size_t)e * 12 * P + id;
+#pragma unroll
+    for (int r2 = 0; r2 < 12; ++r2) gr[r2] = gg[r2 * P];
+    double gb[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double ub[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int r = ijk[d];
+      const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
+      const int line0 = id - r * stride;
+      double fb[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int i2 = 0; i2 < n; ++i2) {
+        const double Dir = sD[i2 * n + r];
+        const int nid = line0 + i2 * stride;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) fb[c] -= Dir * sL(1 + c, nid);
+      }
+      if (r == 0 || r == N) {
+        const double vs = r == N ? inv_w0 : -inv_w0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) fb[c] += vs * lv[1 + c];
+      }
+      mub += visc_flux_vjp(gr, me.u, me.v, me.w, g.mu, g.kappa, Ja[d * 3], Ja[d * 3 + 1], Ja[d * 3 + 2], fb, gb, ub);
+    }
+    pr[1] += ub[0]; pr[2] += ub[1]; pr[3] += ub[2];
+    double qb[5] = {0, 0, 0, 0, 0};
+    const double uu[3] = {pr[1], pr[2], pr[3]};
+    prim_vjp(q, pr[0], uu, pr[4], g.gm1, qb);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) b.qbar[((size_t)e * 5 + c) * P + id] = qb[c];
+#pragma unroll
+    for (int r2 = 0; r2 < 12; ++r2) b.gbar[((size_t)e * 12 + r2) * P + id] = gb[r2];
+    // surface-flux seeds: F*_out enters with +1/w_0 (master) or -1/w_0 (slave, mapped)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int id_d = ijk[d];
+      if (id_d != 0 && id_d != N) continue;
+      const int code = elem_face[e * 6 + 2 * d + (id_d == N ? 1 : 0)];
+      const int fid = code >> 4;
+      const int pp = d == 0 ? j : i;
+      const int qq = d == 2 ? j : k;
+      if (code & 8) {
+        double* fs = b.fseed + ((size_t)fid * 2 + 0) * 5 * NN + pp + n * qq;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) fs[c * NN] = lv[c] * inv_w0;
+      } else {
+        int p2, q2;
+        apply_flip<n>(code & 7, pp, qq, p2, q2);
+        double* fs = b.fseed + ((size_t)fid * 2 + 1) * 5 * NN + p2 + n * q2;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) fs[c * NN] = -lv[c] * inv_w0;
+      }
+    }
+  }
+  // block partial of d/dmu (the block need not be a whole number of warps,
+  // so the partials go through shared memory, summed by one thread in order)
+  smu[threadIdx.x] = mub;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int t = 0; t < S::THREADS; ++t) s += smu[t];
+    b.mupart[blockIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A2: face adjoint, one thread per face node (master orientation).
+template <int N>
+__global__ void __launch_bounds__(128)
+k_adj_face(const double* __restrict__ U, const double* __restrict__ grad, const FaceInfo* __restrict__ faces,
+           const double* __restrict__ facegeo, int F, Gas g, AdjBufs b, int mu_offset) {
+  constexpr int n = N + 1, P = n * n * n, NN = n * n;
+  __shared__ double smu[4];
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  double mub = 0.0;
+  if (gid < (long)F * NN) {
+    const int f = (int)(gid / NN), pq = (int)(gid % NN);
+    const int p = pq % n, q = pq / n;
+    const FaceInfo fi = faces[f];
+    const int eM = fi.master >> 3, fM = fi.master & 7, eS = fi.slave >> 3, fS = fi.slave & 7;
+    int p2, q2;
+    apply_flip<n>(fi.flip, p, q, p2, q2);
+    const int idM = face_node<n>(fM, p, q), idS = face_node<n>(fS, p2, q2);
+    double qL[5], qR[5], Fb[5];
+    const double* s0 = b.fseed + ((size_t)f * 2 + 0) * 5 * NN + pq;
+    const double* s1 = b.fseed + ((size_t)f * 2 + 1) * 5 * NN + pq;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      qL[c] = U[((size_t)eM * 5 + c) * P + idM];
+      qR[c] = U[((size_t)eS * 5 + c) * P + idS];
+      Fb[c] = s0[c * NN] + s1[c * NN];
+    }
+    const double* fg = facegeo + (size_t)f * 4 * NN + pq;
+    const double nx = fg[0], ny = fg[NN], nz = fg[2 * NN], sJ = fg[3 * NN];
+    double fa_b[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) fa_b[c] = Fb[c] * sJ;
+    double qbL[5] = {0, 0, 0, 0, 0}, qbR[5] = {0, 0, 0, 0, 0};
+    if (g.surf_flux == DG_FLUX_EC) {
+      const double irL = 1.0 / qL[0], irR = 1.0 / qR[0];
+      NodePrim<double> A{qL[0], qL[1] * irL, qL[2] * irL, qL[3] * irL, 0, 0};
+      A.p = g.gm1 * (qL[4] - 0.5 * (qL[1] * A.u + qL[2] * A.v + qL[3] * A.w));
+      A.beta = 0.5 * qL[0] / A.p;
+      NodePrim<double> B{qR[0], qR[1] * irR, qR[2] * irR, qR[3] * irR, 0, 0};
+      B.p = g.gm1 * (qR[4] - 0.5 * (qR[1] * B.u + qR[2] * B.v + qR[3] * B.w));
+      B.beta = 0.5 * qR[0] / B.p;
+      double pa[5] = {0, 0, 0, 0, 0}, pb[5] = {0, 0, 0, 0, 0};
+      ec_flux_vjp(A, B, nx, ny, nz, g.inv_gm1, fa_b, pa, pb);
+      const double ua[3] = {pa[1], pa[2], pa[3]}, ubv[3] = {pb[1], pb[2], pb[3]};
+      prim_vjp(qL, pa[0], ua, pa[4], g.gm1, qbL);
+      prim_vjp(qR, pb[0], ubv, pb[4], g.gm1, qbR);
+    } else {
+      llf_vjp(qL, qR, nx, ny, nz, g.gamma, g.gm1, fa_b, qbL, qbR);
+    }
+    // viscous part: F* includes -1/2 (f_v(L) + f_v(R)) . n sJ
+    double fvb[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) fvb[c] = -0.5 * Fb[1 + c] * sJ;
+    double gL[12], gR[12], gbL[12], gbR[12];
+#pragma unroll
+    for (int r = 0; r < 12; ++r) {
+      gL[r] = grad[((size_t)eM * 12 + r) * P + idM];
+      gR[r] = grad[((size_t)eS * 12 + r) * P + idS];
+      gbL[r] = 0.0;
+      gbR[r] = 0.0;
+    }
+    double ubL[3] = {0, 0, 0}, ubR[3] = {0, 0, 0};
+    const double irL = 1.0 / qL[0], irR = 1.0 / qR[0];
+    mub += visc_flux_vjp(gL, qL[1] * irL, qL[2] * irL, qL[3] * irL, g.mu, g.kappa, nx, ny, nz, fvb, gbL, ubL);
+    mub += visc_flux_vjp(gR, qR[1] * irR, qR[2] * irR, qR[3] * irR, g.mu, g.kappa, nx, ny, nz, fvb, gbR, ubR);
+    prim_vjp(qL, 0.0, ubL, 0.0, g.gm1, qbL);
+    prim_vjp(qR, 0.0, ubR, 0.0, g.gm1, qbR);
+    double* oL = b.face + ((size_t)f * 2 + 0) * 17 * NN + pq;
+    double* oR = b.face + ((size_t)f * 2 + 1) * 17 * NN + pq;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) { oL[c * NN] = qbL[c]; oR[c * NN] = qbR[c]; }
+#pragma unroll
+    for (int r = 0; r < 12; ++r) { oL[(5 + r) * NN] = gbL[r]; oR[(5 + r) * NN] = gbR[r]; }
+  }
+  for (int o = 16; o > 0; o >>= 1) mub += __shfl_down_sync(0xffffffffu, mub, o);
+  if ((threadIdx.x & 31) == 0) smu[threadIdx.x >> 5] = mub;
+  __syncthreads();
+  if (threadIdx.x == 0) b.mupart[mu_offset + blockIdx.x] = smu[0] + smu[1] + smu[2] + smu[3];
+}
+
+// ---------------------------------------------------------------------------
+// A3: per node, add the face contributions of the node's faces; store the
+// total gradient adjoint divided by J, and the conserved adjoint so far.
+template <int N>
+__global__ void __launch_bounds__(128)
+k_adj_gather(const double* __restrict__ metrics, const int* __restrict__ elem_face, int E, AdjBufs b) {
+  constexpr int n = N + 1, P = n * n * n, NN = n * n;
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)E * P) return;
+  const int e = (int)(t / P), id = (int)(t % P);
+  const int i = id % n, j = (id / n) % n, k = id / NN;
+  const int ijk[3] = {i, j, k};
+  double gb[12], qb[5];
+#pragma unroll
+  for (int r = 0; r < 12; ++r) gb[r] = b.gbar[((size_t)e * 12 + r) * P + id];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) qb[c] = b.qbar[((size_t)e * 5 + c) * P + id];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int id_d = ijk[d];
+    if (id_d != 0 && id_d != N) continue;
+    const int code = elem_face[e * 6 + 2 * d + (id_d == N ? 1 : 0)];
+    const int fid = code >> 4;
+    const int pp = d == 0 ? j : i;
+    const int qq = d == 2 ? j : k;
+    int pm = pp, qm = qq, side = 0;
+    if (!(code & 8)) { apply_flip<n>(code & 7, pp, qq, pm, qm); side = 1; }
+    const double* src = b.face + ((size_t)fid * 2 + side) * 17 * NN + pm + n * qm;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) qb[c] += src[c * NN];
+#pragma unroll
+    for (int r = 0; r < 12; ++r) gb[r] += src[(5 + r) * NN];
+  }
+  const double iJ = metrics[(size_t)e * 10 * P + 9 * P + id];
+#pragma unroll
+  for (int r = 0; r < 12; ++r) b.gtil[((size_t)e * 12 + r) * P + id] = gb[r] * iJ;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) b.qbar[((size_t)e * 5 + c) * P + id] = qb[c];
+}
+
+// ---------------------------------------------------------------------------
+// A4: transpose of the lifting, then the primitive VJP; out = total adjoint.
+template <int N>
+__global__ void __launch_bounds__(Shape<N>::THREADS)
+k_adj_lift(const double* __restrict__ U, const double* __restrict__ metrics, const int* __restrict__ elem_nbr,
+           const int* __restrict__ elem_face, const double* __restrict__ Dg, int E, Gas g, double inv_w0, AdjBufs b,
+           double* __restrict__ out) {
+  using S = Shape<N>;
+  constexpr int n = S::n, P = S::P, NN = S::NN, EPB = S::EPB;
+  extern __shared__ double adj_smem[];
+  double* sD = adj_smem;                                   // [n*n]
+  const int le = threadIdx.x / P, id = threadIdx.x - le * P;
+  double* sY = adj_smem + ((n * n + 1) & ~1) + (size_t)le * 12 * P;   // Y^d_phi = sum_l Ja^d_l gtil_{phi,l}, row phi*3+d
+  const int e = blockIdx.x * EPB + le;
+  const bool active = e < E;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = Dg[t];
+  double Ja[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gt[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (active) {
+    const double* mt = metrics + (size_t)e * 10 * P + id;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) Ja[r] = mt[r * P];
+#pragma unroll
+    for (int r = 0; r < 12; ++r) gt[r] = b.gtil[((size_t)e * 12 + r) * P + id];
+#pragma unroll
+    for (int ph = 0; ph < 4; ++ph)
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        sY[(ph * 3 + d) * P + id] = Ja[d * 3] * gt[ph * 3] + Ja[d * 3 + 1] * gt[ph * 3 + 1] + Ja[d * 3 + 2] * gt[ph * 3 + 2];
+  }
+  __syncthreads();
+  if (!active) return;
+  const int i = id % n, j = (id / n) % n, k = id / NN;
+  const int ijk[3] = {i, j, k};
+  double phib[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int r = ijk[d];
+    const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
+    const int line0 = id - r * stride;
+#pragma unroll
+    for (int i2 = 0; i2 < n; ++i2) {
+      const double Dir = sD[i2 * n + r];
+      const int nid = line0 + i2 * stride;
+#pragma unroll
+      for (int ph = 0; ph < 4; ++ph) phib[ph] += Dir * sY[(ph * 3 + d) * P + nid];
+    }
+  }
+  // surface terms: own -1/2 gtil . nsJ / w0, neighbour partner +1/2 gtil' . nsJ' / w0
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int id_d = ijk[d];
+    if (id_d != 0 && id_d != N) continue;
+    const int s = id_d == N ? 1 : 0;
+    const double sg = s ? 1.0 : -1.0;
+#pragma unroll
+    for (int ph = 0; ph < 4; ++ph)
+      phib[ph] -= 0.5 * inv_w0 * sg * (gt[ph * 3] * Ja[d * 3] + gt[ph * 3 + 1] * Ja[d * 3 + 1] + gt[ph * 3 + 2] * Ja[d * 3 + 2]);
+    const int f = 2 * d + s;
+    const int code = elem_face[e * 6 + f];
+    const int nb = elem_nbr[e * 6 + f];
+    const int e2 = nb >> 3, f2 = nb & 7;
+    const int pp = d == 0 ? j : i;
+    const int qq = d == 2 ? j : k;
+    int p2, q2;
+    apply_flip<n>(code & 7, pp, qq, p2, q2);
+    const int id2 = face_node<n>(f2, p2, q2);
+    const int d2 = f2 >> 1;
+    const double sg2 = (f2 & 1) ? 1.0 : -1.0;
+    const double* mt2 = metrics + (size_t)e2 * 10 * P + id2;
+    const double n0 = sg2 * mt2[(d2 * 3) * P], n1 = sg2 * mt2[(d2 * 3 + 1) * P], n2 = sg2 * mt2[(d2 * 3 + 2) * P];
+    const double* g2 = b.gtil + (size_t)e2 * 12 * P + id2;
+#pragma unroll
+    for (int ph = 0; ph < 4; ++ph)
+      phib[ph] += 0.5 * inv_w0 * (g2[(ph * 3) * P] * n0 + g2[(ph * 3 + 1) * P] * n1 + g2[(ph * 3 + 2) * P] * n2);
+  }
+  // phi = (u, v, w, T), T = p / (rho R)
+  double q[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) q[c] = U[((size_t)e * 5 + c) * P + id];
+  const double ir = 1.0 / q[0];
+  const double u = q[1] * ir, v = q[2] * ir, w = q[3] * ir;
+  const double p = g.gm1 * (q[4] - 0.5 * (q[1] * u + q[2] * v + q[3] * w));
+  const double T = p * ir * g.inv_R;
+  const double ub[3] = {phib[0], phib[1], phib[2]};
+  double qb[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) qb[c] = b.qbar[((size_t)e * 5 + c) * P + id];
+  prim_vjp(q, -phib[3] * T * ir, ub, phib[3] * ir * g.inv_R, g.gm1, qb);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) out[((size_t)e * 5 + c) * P + id] = qb[c];
+}
+
+// d/dmu: fold the block partials in a fixed order and add to *acc.
+__global__ void k_adj_mu_fold(const double* __restrict__ part, int n, double scale, double* __restrict__ acc) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < n; t += 256) s += part[t];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) acc[0] += scale * sh[0];
+}
+
+// Elementwise: y = a*y + b*x  (a, b host scalars)
+__global__ void k_axpby(double* y, const double* x, double a, double b, size_t len) {
+  // a == 0 overwrites y (whatever it held, including NaN)
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (size_t)gridDim.x * blockDim.x)
+    y[t] = (a == 0.0 ? 0.0 : a * y[t]) + b * x[t];
+}
+
+template <int N>
+static size_t adj_volume_smem() {
+  using S = Shape<N>;
+  return sizeof(double) * (((S::n * S::n + 1) & ~1) + (size_t)S::EPB * 25 * S::P);
+}
+
+template <int N>
+static size_t adj_lift_smem() {
+  using S = Shape<N>;
+  return sizeof(double) * (((S::n * S::n + 1) & ~1) + (size_t)S::EPB * 12 * S::P);
+}
+
+template <int N>
+static cudaError_t adj_setup_N() {
+  cudaError_t e = cudaFuncSetAttribute(k_adj_volume<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)adj_volume_smem<N>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_lift<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_lift_smem<N>());
+  return e;
+}
+
+cudaError_t setup_adjoint(int N) {
+  switch (N) {
+    case 1: return adj_setup_N<1>();
+    case 2: return adj_setup_N<2>();
+    case 3: return adj_setup_N<3>();
+    case 4: return adj_setup_N<4>();
+    case 5: return adj_setup_N<5>();
+    case 6: return adj_setup_N<6>();
+    case 7: return adj_setup_N<7>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// number of d/dmu partials one VJP writes
+int adjoint_mu_partials(const Ctx& c) {
+  const int epb = default_epb(c.P);
+  return (c.E + epb - 1) / epb + (int)(((long)c.nfaces * c.NN + 127) / 128);
+}
+
+template <int N>
+static cudaError_t vjp_N(const Ctx& c, const double* U, const double* lam, double* out, const AdjBufs& b,
+                         double* dJdmu, double mu_scale, cudaStream_t s) {
+  using S = Shape<N>;
+  constexpr int NN = (N + 1) * (N + 1);
+  const int blocks = (c.E + S::EPB - 1) / S::EPB;
+  const double inv_w0 = 1.0 / c.w[0];
+  const double* grad = (const double*)c.d_grad;
+  k_adj_volume<N><<<blocks, S::THREADS, adj_volume_smem<N>(), s>>>(U, lam, c.d_metrics, grad, c.d_elem_face, c.d_D,
+                                                                   c.E, c.gas, inv_w0, b);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const long tot = (long)c.nfaces * NN;
+  const int fblocks = (int)((tot + 127) / 128);
+  k_adj_face<N><<<fblocks, 128, 0, s>>>(U, grad, c.d_faces, c.d_facegeo, c.nfaces, c.gas, b, blocks);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  const long nodes = (long)c.E * c.P;
+  k_adj_gather<N><<<(int)((nodes + 127) / 128), 128, 0, s>>>(c.d_metrics, c.d_elem_face, c.E, b);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  k_adj_lift<N><<<blocks, S::THREADS, adj_lift_smem<N>(), s>>>(U, c.d_metrics, c.d_elem_nbr, c.d_elem_face, c.d_D,
+                                                               c.E, c.gas, inv_w0, b, out);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (dJdmu) {
+    k_adj_mu_fold<<<1, 256, 0, s>>>(b.mupart, blocks + fblocks, mu_scale, dJdmu);
+    err = cudaGetLastError();
+  }
+  return err;
+}
+
+cudaError_t launch_vjp(const Ctx& c, const double* U, const double* lam, double* out, double* dJdmu,
+                       double mu_scale, cudaStream_t s) {
+  // forward recomputation of the FP64 lifted gradients at U
+  cudaError_t err = launch_lift_fp64(c, U, s);
+  if (err != cudaSuccess) return err;
+  AdjBufs b{c.d_adj_qbar, c.d_adj_gbar, c.d_adj_fseed, c.d_adj_face, c.d_adj_gtil, c.d_adj_mu, 0};
+  switch (c.N) {
+    case 1: return vjp_N<1>(c, U, lam, out, b, dJdmu, mu_scale, s);
+    case 2: return vjp_N<2>(c, U, lam, out, b, dJdmu, mu_scale, s);
+    case 3: return vjp_N<3>(c, U, lam, out, b, dJdmu, mu_scale, s);
+    case 4: return vjp_N<4>(c, U, lam, out, b, dJdmu, mu_scale, s);
+    case 5: return vjp_N<5>(c, U, lam, out, b, dJdmu, mu_scale, s);
+    case 6: return vjp_N<6>(c, U, lam, out, b, dJdmu, mu_scale, s);
+    case 7: return vjp_N<7>(c, U, lam, out, b, dJdmu, mu_scale, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Objective J = sum_nodes w_i w_j w_k J 1/2 rho |u|^2 (volume-integrated kinetic
+// energy) and, optionally, dJ/dU.  Block partials into part[], folded later.
+template <int N>
+__global__ void __launch_bounds__(256)
+k_kinetic(const double* __restrict__ U, const double* __restrict__ Jac, const double* __restrict__ w,
+          double* __restrict__ grad, double* __restrict__ part, int E) {
+  constexpr int n = N + 1, P = n * n * n;
+  __shared__ double sh[8];
+  double acc = 0.0;
+  const long total = (long)E * P;
+  for (long t = (long)blockIdx.x * 256 + threadIdx.x; t < total; t += (long)gridDim.x * 256) {
+    const int e = (int)(t / P), id = (int)(t % P);
+    const int i = id % n, j = (id / n) % n, k = id / (n * n);
+    const double wq = w[i] * w[j] * w[k] * Jac[t];
+    const double* q = U + (size_t)e * 5 * P + id;
+    const double ir = 1.0 / q[0];
+    const double u = q[P] * ir, v = q[2 * P] * ir, ww = q[3 * P] * ir;
+    const double k2 = 0.5 * (u * u + v * v + ww * ww);
+    acc += wq * q[0] * k2;
+    if (grad) {
+      double* gp = grad + (size_t)e * 5 * P + id;
+      gp[0] = -wq * k2;
+      gp[P] = wq * u;
+      gp[2 * P] = wq * v;
+      gp[3 * P] = wq * ww;
+      gp[4 * P] = 0.0;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s2 = 0.0;
+    for (int a = 0; a < 8; ++a) s2 += sh[a];
+    part[blockIdx.x] = s2;
+  }
+}
+
+cudaError_t launch_kinetic(const Ctx& c, const double* U, double* grad, double* d_out, cudaStream_t s) {
+  const long total = (long)c.E * c.P;
+  const int blocks = (int)std::min<long>((total + 255) / 256, c.red_len);
+  cudaError_t err;
+  switch (c.N) {
+    case 1: k_kinetic<1><<<blocks, 256, 0, s>>>(U, c.d_J, c.d_w, grad, c.d_red, c.E); break;
+    case 2: k_kinetic<2><<<blocks, 256, 0, s>>>(U, c.d_J, c.d_w, grad, c.d_red, c.E); break;
+    case 3: k_kinetic<3><<<blocks, 256, 0, s>>>(U, c.d_J, c.d_w, grad, c.d_red, c.E); break;
+    case 4: k_kinetic<4><<<blocks, 256, 0, s>>>(U, c.d_J, c.d_w, grad, c.d_red, c.E); break;
+    case 5: k_kinetic<5><<<blocks, 256, 0, s>>>(U, c.d_J, c.d_w, grad, c.d_red, c.E); break;
+    case 6: k_kinetic<6><<<blocks, 256, 0, s>>>(U, c.d_J, c.d_w, grad, c.d_red, c.E); break;
+    case 7: k_kinetic<7><<<blocks, 256, 0, s>>>(U, c.d_J, c.d_w, grad, c.d_red, c.E); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  cudaMemsetAsync(d_out, 0, sizeof(double), s);
+  k_adj_mu_fold<<<1, 256, 0, s>>>(c.d_red, blocks, 1.0, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(double* y, const double* x, double a, double b, size_t len, cudaStream_t s) {
+  const size_t blocks = std::min<size_t>((len + 255) / 256, 152 * 16);
+  k_axpby<<<(unsigned)blocks, 256, 0, s>>>(y, x, a, b, len);
+  return cudaGetLastError();
+}
+
+}  // namespace dg

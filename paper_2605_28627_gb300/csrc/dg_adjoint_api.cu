@@ -1,0 +1,252 @@
+// C ABI of the discrete adjoint: VJP of R(U), adjoint of one LSERK4-5 step,
+// the adjoint of a whole time interval with binomial checkpointing, the
+// kinetic-energy objective, and the viscosity setter used for d/dmu checks.
+#include <cstdio>
+#include <vector>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+static dg_status afail(Ctx* c, dg_status st, const char* what, cudaError_t e = cudaSuccess) {
+  char buf[512];
+  if (e != cudaSuccess) std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  else std::snprintf(buf, sizeof buf, "%s", what);
+  if (c) c->err = buf;
+  return st;
+}
+
+#define ADJ_CUDA(call, ctx, what)                                                               \
+  do {                                                                                          \
+    cudaError_t _e = (call);                                                                    \
+    if (_e != cudaSuccess)                                                                      \
+      return afail(ctx, _e == cudaErrorMemoryAllocation ? DG_ENOMEM : DG_ECUDA, what, _e);      \
+  } while (0)
+
+static dg_status ensure_adjoint(Ctx* c) {
+  if (c->d_adj_qbar) return DG_OK;
+  if (c->prm.precision != DG_FP64) return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the FP64 operator");
+  const size_t st = (size_t)c->E * 5 * c->P;
+  const size_t nn = (size_t)c->nfaces * c->NN;
+  ADJ_CUDA(setup_adjoint(c->N), c, "adjoint kernel set-up");
+  ADJ_CUDA(cudaMalloc(&c->d_adj_qbar, sizeof(double) * st), c, "adjoint buffers");
+  ADJ_CUDA(cudaMalloc(&c->d_adj_gbar, sizeof(double) * (size_t)c->E * 12 * c->P), c, "adjoint buffers");
+  ADJ_CUDA(cudaMalloc(&c->d_adj_gtil, sizeof(double) * (size_t)c->E * 12 * c->P), c, "adjoint buffers");
+  ADJ_CUDA(cudaMalloc(&c->d_adj_fseed, sizeof(double) * nn * 2 * 5), c, "adjoint buffers");
+  ADJ_CUDA(cudaMalloc(&c->d_adj_face, sizeof(double) * nn * 2 * 17), c, "adjoint buffers");
+  ADJ_CUDA(cudaMalloc(&c->d_adj_mu, sizeof(double) * (adjoint_mu_partials(*c) + 2)), c, "adjoint buffers");
+  ADJ_CUDA(cudaMalloc(&c->d_adj_stage, sizeof(double) * st * 5), c, "adjoint stage states");
+  ADJ_CUDA(cudaMalloc(&c->d_adj_work, sizeof(double) * st * 4), c, "adjoint work");
+  return DG_OK;
+}
+
+// One LSERK4-5 step adjoint.  Un: state at the start of the step; lam: in =
+// adjoint at the end of the step, out = adjoint at the start (in place).
+static dg_status step_adjoint(Ctx* c, const double* Un, double* lam, double* dJdmu, double t, double dt,
+                              cudaStream_t s) {
+  const size_t st = (size_t)c->E * 5 * c->P, bytes = sizeof(double) * st;
+  double* Ws = c->d_adj_work;           // work state
+  double* G = Ws + st;                  // RK register
+  double* Gb = G + st;                  // adjoint of the register
+  double* tmp = Gb + st;                // dt * Gb, then VJP output
+  // forward recomputation of the five stage states
+  ADJ_CUDA(cudaMemcpyAsync(Ws, Un, bytes, cudaMemcpyDeviceToDevice, s), c, "stage copy");
+  ADJ_CUDA(cudaMemsetAsync(G, 0, bytes, s), c, "memset");
+  ADJ_CUDA(launch_set_clock(c->d_clock, t, dt, s), c, "clock");
+  for (int k = 0; k < 5; ++k) {
+    ADJ_CUDA(cudaMemcpyAsync(c->d_adj_stage + (size_t)k * st, Ws, bytes, cudaMemcpyDeviceToDevice, s), c, "stage copy");
+    ADJ_CUDA(launch_lift(*c, Ws, s), c, "lift");
+    ADJ_CUDA(launch_face(*c, Ws, s), c, "face");
+    StageArgs a{Ws, Ws, G, nullptr, c->d_clock, kRkC[k], kRkA[k], kRkB[k], 1};
+    ADJ_CUDA(launch_volume(*c, a, s), c, "volume");
+  }
+  // reverse sweep: Gb += B_k lam;  lam += (dR/dU)^T (dt Gb);  Gb *= A_k
+  ADJ_CUDA(cudaMemsetAsync(Gb, 0, bytes, s), c, "memset");
+  for (int k = 4; k >= 0; --k) {
+    ADJ_CUDA(launch_axpby(Gb, lam, 1.0, kRkB[k], st, s), c, "axpby");
+    ADJ_CUDA(launch_axpby(tmp, Gb, 0.0, dt, st, s), c, "axpby");
+    ADJ_CUDA(launch_vjp(*c, c->d_adj_stage + (size_t)k * st, tmp, tmp, dJdmu, 1.0, s), c, "vjp");
+    ADJ_CUDA(launch_axpby(lam, tmp, 1.0, 1.0, st, s), c, "axpby");
+    ADJ_CUDA(launch_axpby(Gb, Gb, kRkA[k], 0.0, st, s), c, "axpby");
+  }
+  return DG_OK;
+}
+
+// forward steps from `from` (in place on U), each step zeroing the register
+static dg_status advance(Ctx* c, double* U, double* G, double t, double dt, int nsteps, cudaStream_t s) {
+  if (nsteps <= 0) return DG_OK;
+  ADJ_CUDA(launch_set_clock(c->d_clock, t, dt, s), c, "clock");
+  const size_t bytes = sizeof(double) * (size_t)c->E * 5 * c->P;
+  for (int st = 0; st < nsteps; ++st) {
+    ADJ_CUDA(cudaMemsetAsync(G, 0, bytes, s), c, "memset");
+    for (int k = 0; k < 5; ++k) {
+      ADJ_CUDA(launch_lift(*c, U, s), c, "lift");
+      ADJ_CUDA(launch_face(*c, U, s), c, "face");
+      StageArgs a{U, U, G, nullptr, c->d_clock, kRkC[k], kRkA[k], kRkB[k], 1};
+      ADJ_CUDA(launch_volume(*c, a, s), c, "volume");
+    }
+    ADJ_CUDA(launch_clock_advance(c->d_clock, s), c, "clock");
+  }
+  return DG_OK;
+}
+
+// Binomial checkpointing (Griewank's binomial schedule): beta(s, r) =
+// C(s + r, s) steps can be reversed with s free snapshots and r forward
+// repetitions.  The state at i0 is in snap[level]; reverse [i0, i1).
+static long binom(int s, int r) {
+  long v = 1;
+  for (int a = 1; a <= s; ++a) v = v * (r + a) / a;
+  return v;
+}
+
+struct Revolve {
+  Ctx* c;
+  std::vector<double*> snap;   // snapshot buffers
+  double* lam;
+  double* dJdmu;
+  double t0, dt;
+  cudaStream_t s;
+  long forward_steps = 0;
+  long adjoint_steps = 0;
+};
+
+static dg_status reverse(Revolve& R, int i0, int i1, int level) {
+  Ctx* c = R.c;
+  const size_t bytes = sizeof(double) * (size_t)c->E * 5 * c->P;
+  const int n = i1 - i0;
+  const int free_snaps = (int)R.snap.size() - 1 - level;
+  if (n == 1) {
+    R.adjoint_steps++;
+    return step_adjoint(c, R.snap[level], R.lam, R.dJdmu, R.t0 + i0 * R.dt, R.dt, R.s);
+  }
+  double* G = c->d_adj_work + (size_t)c->E * 5 * c->P;   // register slot of the work area
+  if (free_snaps <= 0) {
+    // no snapshot left: recompute each step from the state at i0
+    for (int k = i1 - 1; k >= i0; --k) {
+      double* W = c->d_adj_work;
+      ADJ_CUDA(cudaMemcpyAsync(W, R.snap[level], bytes, cudaMemcpyDeviceToDevice, R.s), c, "copy");
+      dg_status st = advance(c, W, G, R.t0 + i0 * R.dt, R.dt, k - i0, R.s);
+      if (st != DG_OK) return st;
+      R.forward_steps += k - i0;
+      // the step adjoint overwrites the work area, so stage from a snapshot-free copy
+      double* keep = c->d_adj_stage;   // stage slot 0 is rewritten by step_adjoint anyway
+      ADJ_CUDA(cudaMemcpyAsync(keep + (size_t)4 * c->E * 5 * c->P, W, bytes, cudaMemcpyDeviceToDevice, R.s), c, "copy");
+      st = step_adjoint(c, keep + (size_t)4 * c->E * 5 * c->P, R.lam, R.dJdmu, R.t0 + k * R.dt, R.dt, R.s);
+      if (st != DG_OK) return st;
+      R.adjoint_steps++;
+    }
+    return DG_OK;
+  }
+  int r = 1;
+  while (binom(free_snaps, r) < n) ++r;
+  long first = binom(free_snaps, r - 1);
+  if (first >= n) first = n - 1;
+  if (first < 1) first = 1;
+  const int m = i0 + (int)first;
+  // advance a copy of the state at i0 to m into the next snapshot
+  ADJ_CUDA(cudaMemcpyAsync(R.snap[level + 1], R.snap[level], bytes, cudaMemcpyDeviceToDevice, R.s), c, "copy");
+  dg_status st = advance(c, R.snap[level + 1], G, R.t0 + i0 * R.dt, R.dt, m - i0, R.s);
+  if (st != DG_OK) return st;
+  R.forward_steps += m - i0;
+  st = reverse(R, m, i1, level + 1);
+  if (st != DG_OK) return st;
+  return reverse(R, i0, m, level);
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" {
+
+dg_status dg_time_derivative_vjp(dg_ctx* ctx, const double* dU, const double* dv, double* dout, double* dJdmu,
+                                 double t, dg_stream stream) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  (void)t;
+  if (!c || !dU || !dv || !dout) return afail(c, DG_EINVAL, "dg_time_derivative_vjp: null argument");
+  if (dout == dU) return afail(c, DG_EINVAL, "dg_time_derivative_vjp: dout aliases dU");
+  ADJ_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  dg_status st = ensure_adjoint(c);
+  if (st != DG_OK) return st;
+  ADJ_CUDA(launch_vjp(*c, dU, dv, dout, dJdmu, 1.0, (cudaStream_t)stream), c, "vjp");
+  return DG_OK;
+}
+
+dg_status dg_adjoint_step(dg_ctx* ctx, const double* dU_n, const double* dlam_np1, double* dlam_n, double* dJdmu,
+                          double t, double dt, dg_stream stream) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !dU_n || !dlam_np1 || !dlam_n) return afail(c, DG_EINVAL, "dg_adjoint_step: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  ADJ_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  dg_status st = ensure_adjoint(c);
+  if (st != DG_OK) return st;
+  const size_t bytes = sizeof(double) * (size_t)c->E * 5 * c->P;
+  if (dlam_n != dlam_np1) ADJ_CUDA(cudaMemcpyAsync(dlam_n, dlam_np1, bytes, cudaMemcpyDeviceToDevice, s), c, "copy");
+  return step_adjoint(c, dU_n, dlam_n, dJdmu, t, dt, s);
+}
+
+dg_status dg_adjoint_solve(dg_ctx* ctx, const double* dU0, const double* dlamT, double* dlam0, double* dJdmu,
+                           double t0, double dt, int32_t nsteps, int32_t max_snapshots, int64_t* host_counts2,
+                           dg_stream stream) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !dU0 || !dlamT || !dlam0 || nsteps < 0 || max_snapshots < 1)
+    return afail(c, DG_EINVAL, "dg_adjoint_solve: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  ADJ_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  dg_status st = ensure_adjoint(c);
+  if (st != DG_OK) return st;
+  const size_t bytes = sizeof(double) * (size_t)c->E * 5 * c->P;
+  if (dlam0 != dlamT) ADJ_CUDA(cudaMemcpyAsync(dlam0, dlamT, bytes, cudaMemcpyDeviceToDevice, s), c, "copy");
+  if (nsteps == 0) return DG_OK;
+  Revolve R;
+  R.c = c;
+  R.lam = dlam0;
+  R.dJdmu = dJdmu;
+  R.t0 = t0;
+  R.dt = dt;
+  R.s = s;
+  const int nsnap = max_snapshots < nsteps ? max_snapshots : nsteps;
+  R.snap.assign(nsnap, nullptr);
+  for (int a = 0; a < nsnap; ++a) {
+    cudaError_t e = cudaMalloc(&R.snap[a], bytes);
+    if (e != cudaSuccess) {
+      for (int b = 0; b < a; ++b) cudaFree(R.snap[b]);
+      return afail(c, DG_ENOMEM, "dg_adjoint_solve: snapshot allocation", e);
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(R.snap[0], dU0, bytes, cudaMemcpyDeviceToDevice, s);
+  st = e == cudaSuccess ? reverse(R, 0, nsteps, 0) : afail(c, DG_ECUDA, "copy", e);
+  cudaError_t es = cudaStreamSynchronize(s);
+  for (double* p : R.snap) cudaFree(p);
+  if (st != DG_OK) return st;
+  if (es != cudaSuccess) return afail(c, DG_ECUDA, "dg_adjoint_solve: sync", es);
+  if (host_counts2) { host_counts2[0] = R.forward_steps; host_counts2[1] = R.adjoint_steps; }
+  return DG_OK;
+}
+
+dg_status dg_kinetic_energy(dg_ctx* ctx, const double* dU, double* dgrad, double* host_J, dg_stream stream) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !dU || !host_J) return afail(c, DG_EINVAL, "dg_kinetic_energy: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  ADJ_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  double* d_out = c->d_red + (size_t)(c->red_len) * kRedValues;   // last row of the reduction buffer
+  ADJ_CUDA(launch_kinetic(*c, dU, dgrad, d_out, s), c, "kinetic energy");
+  ADJ_CUDA(cudaMemcpyAsync(c->h_out, d_out, sizeof(double), cudaMemcpyDeviceToHost, s), c, "copy");
+  ADJ_CUDA(cudaStreamSynchronize(s), c, "sync");
+  *host_J = c->h_out[0];
+  return DG_OK;
+}
+
+dg_status dg_set_viscosity(dg_ctx* ctx, double mu) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !(mu >= 0.0)) return afail(c, DG_EINVAL, "dg_set_viscosity: bad argument");
+  c->prm.mu = mu;
+  c->gas.mu = mu;
+  if (c->graph) {                       // the captured graph holds the old constants
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return DG_OK;
+}
+
+}  // extern "C"

@@ -12,15 +12,6 @@ namespace dg {
 
 static thread_local std::string g_init_error = "no error";
 
-// LSERK4-5 of Carpenter & Kennedy (1994), five stages, 2N storage (Sec. 3.1).
-static const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
-                               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
-static const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
-                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
-                               2277821191437.0 / 14882151754819.0};
-static const double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
-                               2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
-
 // Legendre polynomial P_N and its first two derivatives at x (three-term
 // recurrence; second derivative from Legendre's equation).
 static void legendre(int N, double x, double& L, double& dL, double& d2L) {
@@ -99,7 +90,9 @@ static void release(Ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
   void* bufs[] = {c->d_D, c->d_metrics, c->d_J, c->d_X, c->d_facegeo, c->d_metrics_f, c->d_facegeo_f,
-                  c->d_grad, c->d_fstar, c->d_red, c->d_w, c->d_clock, c->d_U, c->d_G};
+                  c->d_grad, c->d_fstar, c->d_red, c->d_w, c->d_clock, c->d_U, c->d_G,
+                  c->d_adj_qbar, c->d_adj_gbar, c->d_adj_gtil, c->d_adj_fseed, c->d_adj_face, c->d_adj_mu,
+                  c->d_adj_stage, c->d_adj_work};
   for (void* p : bufs) if (p) cudaFree(p);
   if (c->d_faces) cudaFree(c->d_faces);
   if (c->d_elem_face) cudaFree(c->d_elem_face);

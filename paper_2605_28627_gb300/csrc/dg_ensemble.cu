@@ -88,7 +88,7 @@ __global__ void k_ens_set_clocks(double* const* clocks, const double* tdt, int n
 // ---------------------------------------------------------------------------
 // Launch variants of one group: EPB choice 0 = default tile, 1 = doubled tile.
 struct GroupPlan {
-  int epb_choice = 0;
+  int epb_choice = 0;   // 0: default tile, 1: doubled tile, 2: per-member launches of the single-run kernels
   int vol_grid = 0, lift_grid = 0, face_grid = 0;
   bool tuned = false, from_cache = false;
 };
@@ -218,14 +218,6 @@ struct dg_ensemble {
   std::string plan_json;
 };
 
-static const double kEnsA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
-                                -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
-static const double kEnsB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
-                                1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
-                                2277821191437.0 / 14882151754819.0};
-static const double kEnsC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
-                                2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
-
 static dg_status ens_fail(dg_ensemble* e, dg_status st, const char* what, cudaError_t ce = cudaSuccess) {
   char buf[512];
   if (ce != cudaSuccess) std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(ce));
@@ -286,9 +278,31 @@ static dg_status upload_members(dg_ensemble* e) {
   return DG_OK;
 }
 
+// Per-member candidate: the single-run kernels of each member in turn (best
+// when every member fills the GPU by itself).
+static cudaError_t member_stage(dg_ensemble* e, const Group& g, int k, const double* A, const double* B,
+                                cudaStream_t s) {
+  cudaError_t err = cudaSuccess;
+  for (int r : g.members) {
+    const Ctx& c = *e->members[r];
+    double* U = e->cur_U[r];
+    if ((err = launch_lift(c, U, s)) != cudaSuccess) return err;
+    if ((err = launch_face(c, U, s)) != cudaSuccess) return err;
+    StageArgs a{U, U, e->cur_G[r], nullptr, e->clocks + 2 * r, kRkC[k], A[k], B[k], 1};
+    if ((err = launch_volume(c, a, s)) != cudaSuccess) return err;
+  }
+  return err;
+}
+
+static cudaError_t enqueue_group(dg_ensemble* e, const Group& g, int k, const double* A, const double* B,
+                                 cudaStream_t s) {
+  if (g.plan.epb_choice == 2) return member_stage(e, g, k, A, B, s);
+  return e->precision == DG_FP32OP ? dispatch_stage<float>(g, k, A, B, kRkC, s)
+                                   : dispatch_stage<double>(g, k, A, B, kRkC, s);
+}
+
 static cudaError_t enqueue_stage(dg_ensemble* e, const Group& g, int k, cudaStream_t s) {
-  return e->precision == DG_FP32OP ? dispatch_stage<float>(g, k, kEnsA, kEnsB, kEnsC, s)
-                                   : dispatch_stage<double>(g, k, kEnsA, kEnsB, kEnsC, s);
+  return enqueue_group(e, g, k, kRkA, kRkB, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -306,8 +320,7 @@ static float time_stage(dg_ensemble* e, const Group& g, cudaStream_t s, int reps
   float best = 1e30f;
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(a, s);
-    cudaError_t err = e->precision == DG_FP32OP ? dispatch_stage<float>(g, 0, kEnsA, Bz, kEnsC, s)
-                                                : dispatch_stage<double>(g, 0, kEnsA, Bz, kEnsC, s);
+    cudaError_t err = enqueue_group(e, g, 0, kRkA, Bz, s);
     cudaEventRecord(b, s);
     cudaEventSynchronize(b);
     float ms = 0.f;
@@ -384,6 +397,14 @@ static dg_status autotune(dg_ensemble* e, cudaStream_t s) {
         if (ms < best_ms) { best_ms = ms; best = p; }
       }
     }
+    {
+      GroupPlan p;
+      p.epb_choice = 2;
+      Group trial = g;
+      trial.plan = p;
+      const float ms = time_stage(e, trial, s, 3, 0);
+      if (ms < best_ms) { best_ms = ms; best = p; }
+    }
     best.tuned = true;
     g.plan = best;
     cache[key] = best;
@@ -394,12 +415,13 @@ static dg_status autotune(dg_ensemble* e, cudaStream_t s) {
   std::string js = "{\"gpu\": \"" + e->gpu_name + "\", \"groups\": [";
   for (size_t a = 0; a < e->groups.size(); ++a) {
     const Group& g = e->groups[a];
-    char buf[320];
+    char buf[400];
     std::snprintf(buf, sizeof buf,
-                  "%s{\"N\": %d, \"members\": %zu, \"elements_per_block\": %d, \"volume_grid\": %d, "
+                  "%s{\"N\": %d, \"members\": %zu, \"mode\": \"%s\", \"elements_per_block\": %d, \"volume_grid\": %d, "
                   "\"lift_grid\": %d, \"face_grid\": %d, \"element_tiles\": %d, \"face_tiles\": %d, \"cached\": %s}",
-                  a ? ", " : "", g.N, g.members.size(), epb_of(g.N, g.plan.epb_choice, e->precision), g.plan.vol_grid,
-                  g.plan.lift_grid, g.plan.face_grid, g.n_elem_tiles[g.plan.epb_choice], g.n_face_tiles,
+                  a ? ", " : "", g.N, g.members.size(), g.plan.epb_choice == 2 ? "per-member launches" : "tile table",
+                  g.plan.epb_choice == 2 ? 0 : epb_of(g.N, g.plan.epb_choice, e->precision), g.plan.vol_grid,
+                  g.plan.lift_grid, g.plan.face_grid, g.n_elem_tiles[g.plan.epb_choice == 1 ? 1 : 0], g.n_face_tiles,
                   g.plan.from_cache ? "true" : "false");
     js += buf;
   }

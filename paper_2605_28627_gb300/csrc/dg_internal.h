@@ -13,6 +13,16 @@ namespace dg {
 
 constexpr int kMaxN = 9;
 
+// LSERK4-5 of Carpenter & Kennedy (1994), five stages, 2N storage (GALAEXI
+// Sec. 3.1, RK4-5): G <- A_s G + dt R(U, t + c_s dt);  U <- U + B_s G.
+inline constexpr double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                                   -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+inline constexpr double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                                   1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                                   2277821191437.0 / 14882151754819.0};
+inline constexpr double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                                   2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+
 // Gas constants and derived coefficients, passed by value to kernels.
 struct Gas {
   double gamma, R, Pr, mu;
@@ -74,6 +84,15 @@ struct Ctx {
   double* d_clock = nullptr;     // {t, dt}
   double* h_clock = nullptr;     // pinned staging for the clock
   double* h_out = nullptr;       // pinned staging for reductions
+  // adjoint work buffers (allocated on first use)
+  double* d_adj_qbar = nullptr;  // [E][5][P]
+  double* d_adj_gbar = nullptr;  // [E][12][P]
+  double* d_adj_gtil = nullptr;  // [E][12][P]
+  double* d_adj_fseed = nullptr; // [F][2][5][NN]
+  double* d_adj_face = nullptr;  // [F][2][17][NN]
+  double* d_adj_mu = nullptr;    // block partials of d/dmu
+  double* d_adj_stage = nullptr; // [5][E][5][P] stage states of one step
+  double* d_adj_work = nullptr;  // [4][E][5][P]: work state, G, G-bar, VJP scratch
   // host-buffer path
   double* d_U = nullptr;
   double* d_G = nullptr;
@@ -104,6 +123,14 @@ cudaError_t launch_initial_state(Ctx& c, int kind, double prm0, double* U, cudaS
 cudaError_t launch_set_clock(double* clock, double t, double dt, cudaStream_t s);
 cudaError_t launch_clock_advance(double* clock, cudaStream_t s);
 int reduction_rows(const Ctx& c);   // partial rows used by the last reduction
+
+// Adjoint kernels (dg_adjoint.cu).
+cudaError_t setup_adjoint(int N);
+int adjoint_mu_partials(const Ctx& c);
+cudaError_t launch_vjp(const Ctx& c, const double* U, const double* lam, double* out, double* dJdmu, double mu_scale,
+                       cudaStream_t s);
+cudaError_t launch_axpby(double* y, const double* x, double a, double b, size_t len, cudaStream_t s);
+cudaError_t launch_kinetic(const Ctx& c, const double* U, double* grad, double* d_out, cudaStream_t s);
 constexpr int kRedValues = 9;
 
 }  // namespace dg

@@ -1,0 +1,118 @@
+"""Discrete adjoint: dot-product tests against the oracle's tangent-linear
+(forward-mode dual numbers, an independent derivative of the oracle's R),
+checkpointing invariance, and central finite differences through autograd."""
+import math
+
+import numpy as np
+import pytest
+
+from workloads import box_mesh, random_state, tgv_params
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import paper_2605_28627_gb300 as m
+    m.load()
+    return m
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("N,flux", [(2, 0), (3, 0), (3, 1), (5, 0)])
+def test_vjp_dot_product_vs_oracle_tangent_linear(orc, dg, N, flux):
+    mesh = box_mesh(3 if N < 5 else 2, N, deform="sinprod", rotate_seed=600 + N)
+    mu = 0.03
+    o = orc.Oracle(mesh, N, mu=mu, surf_flux=flux)
+    s = dg.Solver(mesh, N, mu=mu, surf_flux=flux)
+    U = random_state(mesh.n_elems, N, seed=700 + N)
+    rng = np.random.default_rng(800 + N)
+    w = rng.normal(size=U.shape)
+    v = rng.normal(size=U.shape)
+    _, Jw = o.time_derivative_tl(U, w, 0.0)        # J w
+    _, Rmu = o.time_derivative_tl(U, np.zeros_like(U), 1.0)   # dR/dmu
+    dmu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    JTv = s.time_derivative_vjp(_cuda(U), _cuda(v), dJdmu=dmu).cpu().numpy()
+    lhs, rhs = float((JTv * w).sum()), float((v * Jw).sum())
+    scale = float(np.abs(JTv * w).sum())
+    assert abs(lhs - rhs) <= 1e-11 * scale, (lhs, rhs)
+    ref_mu = float((v * Rmu).sum())
+    assert abs(dmu.item() - ref_mu) <= 1e-11 * float(np.abs(v * Rmu).sum()), (dmu.item(), ref_mu)
+
+
+def test_step_and_solve_adjoint_vs_oracle(orc, dg):
+    prm = tgv_params(Ma=0.3, Re=400.0)
+    N = 3
+    mesh = box_mesh(3, 1, lo=0.0, hi=2 * math.pi, rotate_seed=5)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"])
+    o = orc.Oracle(mesh, N, **kw)
+    s = dg.Solver(mesh, N, **kw)
+    # a generic state near the Taylor-Green vortex: the vortex itself has w = 0
+    # exactly, which puts |u . n| of the LLF speed at its kink on z-faces, where
+    # the one-sided derivatives of the two codes may differ by rounding
+    rng0 = np.random.default_rng(1)
+    U0 = o.initial_state("tgv", prm["p0"]) * (1 + 0.01 * rng0.normal(size=(mesh.n_elems, 5, 4, 4, 4)))
+    U0[:, 1:4] += 0.01 * rng0.normal(size=(mesh.n_elems, 3, 4, 4, 4))
+    dt, nsteps = 0.02, 6
+    rng = np.random.default_rng(2)
+    w = rng.normal(size=U0.shape)
+    lam = rng.normal(size=U0.shape)
+    _, dUT = o.rk_steps_tl(U0, w, 0.4, 0.0, dt, nsteps)       # tangent of U_T for dU0 = w, dmu = 0.4
+    dmu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lam0, counts = s.adjoint_solve(_cuda(U0), _cuda(lam), 0.0, dt, nsteps, max_snapshots=3, dJdmu=dmu)
+    lhs = float((lam0.cpu().numpy() * w).sum()) + 0.4 * dmu.item()
+    rhs = float((lam * dUT).sum())
+    assert abs(lhs - rhs) <= 1e-10 * abs(rhs), (lhs, rhs)
+    assert counts[1] == nsteps
+    # checkpointing does not change the result: all snapshots vs few vs one
+    ref = None
+    for snaps in (nsteps, 2, 1):
+        dm = torch.zeros(1, dtype=torch.float64, device="cuda")
+        l0, _ = s.adjoint_solve(_cuda(U0), _cuda(lam), 0.0, dt, nsteps, max_snapshots=snaps, dJdmu=dm)
+        cur = (l0.cpu().numpy(), dm.item())
+        if ref is None:
+            ref = cur
+        else:
+            np.testing.assert_array_equal(cur[0], ref[0])
+            assert cur[1] == ref[1]
+    np.testing.assert_array_equal(ref[0], lam0.cpu().numpy())
+
+
+def test_autograd_gradient_vs_central_differences(dg):
+    from paper_2605_28627_gb300.autograd import kinetic_energy, rk_solve
+    prm = tgv_params(Ma=0.2, Re=800.0)
+    N = 3
+    mesh = box_mesh(3, 1, lo=0.0, hi=2 * math.pi)
+    s = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"])
+    U0 = s.initial_state("tgv", prm["p0"])
+    dt = s.max_dt(U0)
+    nsteps = 20
+    Ul = U0.clone().requires_grad_(True)
+    mu = torch.tensor(prm["mu"], dtype=torch.float64, requires_grad=True)
+    J = kinetic_energy(rk_solve(Ul, mu, s, 0.0, dt, nsteps, max_snapshots=4), s)
+    J.backward()
+    gU, gmu = Ul.grad.clone(), mu.grad.item()
+
+    def Jof(U, m):
+        with torch.no_grad():
+            return kinetic_energy(rk_solve(U, torch.tensor(m, dtype=torch.float64), s, 0.0, dt, nsteps), s).item()
+
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    # The vortex has symmetry planes on element faces, where the LLF speed
+    # max(|u.n| + c) sits at its kinks; the adjoint takes the mean one-sided
+    # derivative there, which is what central differences see.
+    h = 1e-6 * U0.abs().max().item()
+    gnorm = gU.norm().item()
+    for _ in range(4):
+        v = torch.randn(U0.shape, generator=gen, device="cuda", dtype=torch.float64)
+        v /= v.norm()
+        fd = (Jof(U0 + h * v, prm["mu"]) - Jof(U0 - h * v, prm["mu"])) / (2 * h)
+        ad = float((gU * v).sum())
+        assert abs(fd - ad) <= 1e-6 * max(abs(ad), 1e-3 * gnorm), (fd, ad, gnorm)
+    hm = 1e-7
+    fd = (Jof(U0, prm["mu"] + hm) - Jof(U0, prm["mu"] - hm)) / (2 * hm)
+    assert abs(fd - gmu) <= 1e-6 * abs(gmu), (fd, gmu)
