@@ -48,7 +48,9 @@ typedef enum {
   DG_EUNSUPPORTED = 7   /* polynomial degree or option not built */
 } dg_status;
 
-enum { DG_FLUX_LLF = 0, DG_FLUX_EC = 1 };         /* surface Riemann flux */
+enum { DG_FLUX_LLF = 0, DG_FLUX_EC = 1, DG_FLUX_ROE = 2 };   /* surface Riemann flux: local Lax-Friedrichs,
+                                                              entropy-conservative two-point flux, Roe with
+                                                              the Harten-Hyman entropy fix (Sec. 3.1) */
 enum { DG_FP64 = 0, DG_FP32OP = 1 };              /* operator arithmetic */
 enum { DG_SOURCE_NONE = 0, DG_SOURCE_MMS = 1 };   /* volume source term */
 enum { DG_IC_TGV = 0, DG_IC_MMS = 1 };            /* built-in initial states */
@@ -79,10 +81,13 @@ typedef struct {
 typedef struct {
   int32_t N;                  /* polynomial degree, 1..9 */
   double gamma, R, Pr, mu;
-  int32_t surf_flux;          /* DG_FLUX_LLF or DG_FLUX_EC */
+  int32_t surf_flux;          /* DG_FLUX_LLF, DG_FLUX_EC or DG_FLUX_ROE */
   int32_t precision;          /* DG_FP64 or DG_FP32OP */
   int32_t source;             /* DG_SOURCE_NONE or DG_SOURCE_MMS */
   double mms_amp;             /* amplitude A of rho = 2 + A sin(pi(x+y+z-t)) */
+  double p_ref;               /* DG_FP32OP: constant pressure taken out of the momentum flux (it has no
+                                 discrete divergence); the background pressure of a low-Mach flow keeps
+                                 its FP32 rounding out of the momentum equations.  Ignored in FP64. */
 } dg_params;
 
 /* Build a context on CUDA device `device`: LGL basis, geometry (node

@@ -13,7 +13,8 @@
 // Readings where the paper is silent (each listed in the design notes):
 //  * p = (gamma-1) rho eps (the printed (1-gamma) is a sign typo, Sec. 3.1).
 //  * LGL collocation, strong split form; curl-form metric terms (Kopriva 2006).
-//  * Surface flux: local Lax-Friedrichs (or the two-point EC flux itself);
+//  * Surface flux: local Lax-Friedrichs (or the two-point EC flux itself, or
+//    Roe's flux with the Harten-Hyman entropy fix, the choice of Sec. 3.1);
 //    viscous surface flux = arithmetic mean of both sides (BR1, Sec. 3.1).
 //  * BR1 lifting of (u, v, w, T) with the non-conservative strong volume part.
 //  * Two-point flux of Chandrashekar (2013) with the kinetic-energy term
@@ -172,7 +173,7 @@ static std::vector<double> equi_to_lgl(int ngeo, const Basis& b) {
 // ---------------------------------------------------------------------------
 struct Params {
   double gamma, R, Pr, mu;
-  int surf_flux;   // 0: local Lax-Friedrichs, 1: entropy-conservative two-point flux
+  int surf_flux;   // 0: local Lax-Friedrichs, 1: entropy-conservative two-point flux, 2: Roe + Harten-Hyman
   int source;      // 0: none, 1: density-wave manufactured solution
   double mms_amp;
   int vol_flux;    // 0: Chandrashekar EC/KEP two-point flux; 1: arithmetic mean of
@@ -462,6 +463,56 @@ static inline void llf_flux(const Params& pr, const T qL[5], const Prim<T>& L,
   for (int v = 0; v < 5; ++v) out[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lmax * (qR[v] - qL[v]);
 }
 
+// Roe's approximate Riemann solver with the entropy fix of Harten & Hyman
+// (1983) in unit direction nv (the surface flux named in Sec. 3.1):
+//   F = 1/2 (f(qL) + f(qR)) . n - 1/2 sum_k |lambda_k| alpha_k r_k
+// with Roe averages (sqrt(rho) weights) of u and H, c^2 = (gamma-1)(H - |u|^2/2);
+// acoustic speeds lambda = u_n -+ c, entropy and shear waves at u_n.  On the
+// acoustic waves |lambda| is replaced by delta = max(0, lambda - lambda(qL),
+// lambda(qR) - lambda) when |lambda| < delta.
+template <class T>
+static inline void roe_flux(const Params& pr, const T qL[5], const Prim<T>& L, const T qR[5], const Prim<T>& Rr,
+                            const T nv[3], T out[5]) {
+  T fL[5], fR[5];
+  euler_flux(qL, L, nv, fL);
+  euler_flux(qR, Rr, nv, fR);
+  T sL = sqrt(L.rho), sR = sqrt(Rr.rho);
+  T wl = sL / (sL + sR), wr = sR / (sL + sR);
+  T HL = (qL[4] + L.p) / L.rho, HR = (qR[4] + Rr.p) / Rr.rho;
+  T u[3];
+  for (int a = 0; a < 3; ++a) u[a] = wl * L.u[a] + wr * Rr.u[a];
+  T H = wl * HL + wr * HR;
+  T q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  T c = sqrt((pr.gamma - 1.0) * (H - 0.5 * q2));
+  T rho = sL * sR;
+  T un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
+  T dr = Rr.rho - L.rho, dp = Rr.p - L.p;
+  T du[3];
+  for (int a = 0; a < 3; ++a) du[a] = Rr.u[a] - L.u[a];
+  T dun = du[0] * nv[0] + du[1] * nv[1] + du[2] * nv[2];
+  T a1 = (dp - rho * c * dun) / (2.0 * c * c);
+  T a2 = dr - dp / (c * c);
+  T a5 = (dp + rho * c * dun) / (2.0 * c * c);
+  T l1 = fabs(un - c), l2 = fabs(un), l5 = fabs(un + c);
+  // Harten-Hyman entropy fix on the acoustic waves
+  T unL = L.u[0] * nv[0] + L.u[1] * nv[1] + L.u[2] * nv[2];
+  T unR = Rr.u[0] * nv[0] + Rr.u[1] * nv[1] + Rr.u[2] * nv[2];
+  T cL = sqrt(pr.gamma * L.p / L.rho), cR = sqrt(pr.gamma * Rr.p / Rr.rho);
+  T d1 = vmax(vmax(T(0.0), (un - c) - (unL - cL)), (unR - cR) - (un - c));
+  T d5 = vmax(vmax(T(0.0), (un + c) - (unL + cL)), (unR + cR) - (un + c));
+  if (val(l1) < val(d1)) l1 = d1;
+  if (val(l5) < val(d5)) l5 = d5;
+  T D[5];
+  // acoustic waves
+  D[0] = l1 * a1 + l2 * a2 + l5 * a5;
+  for (int a = 0; a < 3; ++a)
+    D[1 + a] = l1 * a1 * (u[a] - c * nv[a]) + l2 * (a2 * u[a] + rho * (du[a] - dun * nv[a])) +
+               l5 * a5 * (u[a] + c * nv[a]);
+  T udu = u[0] * du[0] + u[1] * du[1] + u[2] * du[2];
+  D[4] = l1 * a1 * (H - un * c) + l2 * (a2 * 0.5 * q2 + rho * (udu - un * dun)) + l5 * a5 * (H + un * c);
+  for (int v = 0; v < 5; ++v) out[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * D[v];
+}
+
 // Density-wave manufactured solution rho = 2 + A sin(pi (x+y+z-t)), u = (1,1,1),
 // p = 1; its residual q_t + div F(q) worked out by hand:
 //   r' = pi A cos(phi);  mass, momenta: 2 r';  energy: 3 r' - lambda Lap(T),
@@ -657,6 +708,7 @@ static void rhs(const Ctx& c, const T* U, T* Ut, double t, T mu) {
           double sJ = c.fsJ[(size_t)fid * nn + p + n * q];
           T fa[5], fvL[5], fvR[5];
           if (pr.surf_flux == 1) ec_flux(pr, L, Rr, nv, fa);
+          else if (pr.surf_flux == 2) roe_flux(pr, qL, L, qR, Rr, nv, fa);
           else llf_flux(pr, qL, L, qR, Rr, nv, fa);
           visc_flux(pr, L, gL, mu, nv, fvL);
           visc_flux(pr, Rr, gR, mu, nv, fvR);
@@ -858,6 +910,11 @@ void orc_llf_flux(const double* prm, const double* qL, const double* qR, const d
   Params pr{prm[0], prm[1], prm[2], prm[3], 0, 0, 0.0, 0};
   Prim<double> L = cons2prim(pr, qL), Rr = cons2prim(pr, qR);
   llf_flux(pr, qL, L, qR, Rr, nv, out);
+}
+void orc_roe_flux(const double* prm, const double* qL, const double* qR, const double* nv, double* out) {
+  Params pr{prm[0], prm[1], prm[2], prm[3], 0, 0, 0.0, 0};
+  Prim<double> L = cons2prim(pr, qL), Rr = cons2prim(pr, qR);
+  roe_flux(pr, qL, L, qR, Rr, nv, out);
 }
 double orc_log_mean(double a, double b) { return log_mean<double>(a, b); }
 

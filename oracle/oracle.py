@@ -54,6 +54,7 @@ def _load():
     L.orc_rk_coeffs.argtypes = [_dp, _dp, _dp]
     L.orc_ec_flux.argtypes = [_dp, _dp, _dp, _dp, _dp]
     L.orc_llf_flux.argtypes = [_dp, _dp, _dp, _dp, _dp]
+    L.orc_roe_flux.argtypes = [_dp, _dp, _dp, _dp, _dp]
     L.orc_log_mean.argtypes = [C.c_double, C.c_double]
     L.orc_log_mean.restype = C.c_double
     L.orc_integrals.argtypes = [C.c_void_p, _dp, _dp]
@@ -100,6 +101,13 @@ def llf_flux(qL, qR, nv, gamma=1.4):
     return out
 
 
+def roe_flux(qL, qR, nv, gamma=1.4):
+    out = np.zeros(5)
+    _load().orc_roe_flux(_prm(gamma, 1.0, 0.72, 0.0), np.ascontiguousarray(qL, dtype=np.float64),
+                         np.ascontiguousarray(qR, dtype=np.float64), np.ascontiguousarray(nv, dtype=np.float64), out)
+    return out
+
+
 def log_mean(a, b):
     return _load().orc_log_mean(float(a), float(b))
 
@@ -107,7 +115,8 @@ def log_mean(a, b):
 class Oracle:
     """FP64 CPU DGSEM on a mesh in the format of ``workloads.mesh``.
 
-    surf_flux: 0 = local Lax-Friedrichs, 1 = entropy-conservative two-point flux.
+    surf_flux: 0 = local Lax-Friedrichs, 1 = entropy-conservative two-point flux,
+    2 = Roe with the Harten-Hyman entropy fix.
     source: 0 = none, 1 = density-wave manufactured solution.
     """
 

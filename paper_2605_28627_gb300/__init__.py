@@ -21,7 +21,7 @@ LIB_PATH = _build.LIB
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_EMESH, DG_ENONFINITE, DG_ETIMEOUT, DG_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["DG_OK", "DG_EINVAL", "DG_ENOMEM", "DG_ECUDA", "DG_EMESH", "DG_ENONFINITE", "DG_ETIMEOUT",
                 "DG_EUNSUPPORTED"]
-FLUX_LLF, FLUX_EC = 0, 1
+FLUX_LLF, FLUX_EC, FLUX_ROE = 0, 1, 2
 FP64, FP32OP = 0, 1
 SOURCE_NONE, SOURCE_MMS = 0, 1
 IC_TGV, IC_MMS = 0, 1
@@ -48,7 +48,7 @@ class dg_mesh(C.Structure):
 class dg_params(C.Structure):
     _fields_ = [("N", C.c_int32), ("gamma", C.c_double), ("R", C.c_double), ("Pr", C.c_double),
                 ("mu", C.c_double), ("surf_flux", C.c_int32), ("precision", C.c_int32),
-                ("source", C.c_int32), ("mms_amp", C.c_double)]
+                ("source", C.c_int32), ("mms_amp", C.c_double), ("p_ref", C.c_double)]
 
 
 _lib = None
@@ -119,7 +119,7 @@ class Solver:
     ``[E, 5, N+1, N+1, N+1]``."""
 
     def __init__(self, mesh, N: int, gamma=1.4, R=1.0, Pr=0.72, mu=0.0, surf_flux=FLUX_LLF,
-                 precision=FP64, source=SOURCE_NONE, mms_amp=0.1, device: int = 0):
+                 precision=FP64, source=SOURCE_NONE, mms_amp=0.1, device: int = 0, p_ref: float = 0.0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2605_28627_gb300 needs a CUDA GPU; there is no CPU fallback")
@@ -131,7 +131,7 @@ class Solver:
         self.E = int(xgeo.shape[0])
         m = dg_mesh(self.E, int(xgeo.shape[-1]) - 1, xgeo.ctypes.data_as(C.POINTER(C.c_double)),
                     nbr.ctypes.data_as(C.POINTER(C.c_int32)))
-        p = dg_params(N, gamma, R, Pr, mu, surf_flux, precision, source, mms_amp)
+        p = dg_params(N, gamma, R, Pr, mu, surf_flux, precision, source, mms_amp, p_ref)
         h = C.c_void_p()
         torch.cuda.set_device(device)
         st = self._L.dg_init(C.byref(m), C.byref(p), device, C.byref(h))

@@ -443,6 +443,8 @@ cudaError_t setup_adjoint(int N) {
     case 5: return adj_setup_N<5>();
     case 6: return adj_setup_N<6>();
     case 7: return adj_setup_N<7>();
+    case 8: return adj_setup_N<8>();
+    case 9: return adj_setup_N<9>();
     default: return cudaErrorInvalidValue;
   }
 }
@@ -496,6 +498,8 @@ cudaError_t launch_vjp(const Ctx& c, const double* U, const double* lam, double*
     case 5: return vjp_N<5>(c, U, lam, out, b, dJdmu, mu_scale, s);
     case 6: return vjp_N<6>(c, U, lam, out, b, dJdmu, mu_scale, s);
     case 7: return vjp_N<7>(c, U, lam, out, b, dJdmu, mu_scale, s);
+    case 8: return vjp_N<8>(c, U, lam, out, b, dJdmu, mu_scale, s);
+    case 9: return vjp_N<9>(c, U, lam, out, b, dJdmu, mu_scale, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -550,6 +554,8 @@ cudaError_t launch_kinetic(const Ctx& c, const double* U, double* grad, double* 
     case 5: k_kinetic<5><<<blocks, 256, 0, s>>>(U, c.d_J, c.d_w, grad, c.d_red, c.E); break;
     case 6: k_kinetic<6><<<blocks, 256, 0, s>>>(U, c.d_J, c.d_w, grad, c.d_red, c.E); break;
     case 7: k_kinetic<7><<<blocks, 256, 0, s>>>(U, c.d_J, c.d_w, grad, c.d_red, c.E); break;
+    case 8: k_kinetic<8><<<blocks, 256, 0, s>>>(U, c.d_J, c.d_w, grad, c.d_red, c.E); break;
+    case 9: k_kinetic<9><<<blocks, 256, 0, s>>>(U, c.d_J, c.d_w, grad, c.d_red, c.E); break;
     default: return cudaErrorInvalidValue;
   }
   if ((err = cudaGetLastError()) != cudaSuccess) return err;

@@ -26,6 +26,8 @@ static dg_status afail(Ctx* c, dg_status st, const char* what, cudaError_t e = c
 static dg_status ensure_adjoint(Ctx* c) {
   if (c->d_adj_qbar) return DG_OK;
   if (c->prm.precision != DG_FP64) return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the FP64 operator");
+  if (c->prm.surf_flux == DG_FLUX_ROE)
+    return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the LLF and entropy-conservative surface fluxes");
   const size_t st = (size_t)c->E * 5 * c->P;
   const size_t nn = (size_t)c->nfaces * c->NN;
   ADJ_CUDA(setup_adjoint(c->N), c, "adjoint kernel set-up");

@@ -131,10 +131,10 @@ extern "C" {
 dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out) {
   if (out) *out = nullptr;
   if (!mesh || !prm || !out) return fail(nullptr, DG_EINVAL, "dg_init: null argument");
-  if (prm->N < 1 || prm->N > 7) return fail(nullptr, DG_EUNSUPPORTED, "dg_init: N must be in 1..7 in this build");
+  if (prm->N < 1 || prm->N > kMaxN) return fail(nullptr, DG_EUNSUPPORTED, "dg_init: N must be in 1..9");
   if (prm->precision != DG_FP64 && prm->precision != DG_FP32OP)
     return fail(nullptr, DG_EINVAL, "dg_init: unknown precision");
-  if (prm->surf_flux != DG_FLUX_LLF && prm->surf_flux != DG_FLUX_EC)
+  if (prm->surf_flux != DG_FLUX_LLF && prm->surf_flux != DG_FLUX_EC && prm->surf_flux != DG_FLUX_ROE)
     return fail(nullptr, DG_EINVAL, "dg_init: unknown surface flux");
   if (prm->source != DG_SOURCE_NONE && prm->source != DG_SOURCE_MMS)
     return fail(nullptr, DG_EINVAL, "dg_init: unknown source");
@@ -170,6 +170,7 @@ dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx*
   g.kappa = prm->gamma * prm->R / (prm->gamma - 1.0) / prm->Pr;
   g.inv_R = 1.0 / prm->R;
   g.mms_amp = prm->mms_amp; g.surf_flux = prm->surf_flux; g.source = prm->source;
+  g.p_ref = prm->p_ref; g.E_ref = prm->p_ref / (prm->gamma - 1.0);
   lgl_basis(c->N, c->x, c->w, c->D);
   // faces: the side with the smaller (e*6 + f) is the master
   std::vector<FaceInfo> faces;

@@ -223,6 +223,8 @@ cudaError_t launch_integrals(Ctx& c, const double* U, cudaStream_t s) {
     case 5: err = integrals_N<5>(c, U, d_w, s); break;
     case 6: err = integrals_N<6>(c, U, d_w, s); break;
     case 7: err = integrals_N<7>(c, U, d_w, s); break;
+    case 8: err = integrals_N<8>(c, U, d_w, s); break;
+    case 9: err = integrals_N<9>(c, U, d_w, s); break;
     default: err = cudaErrorInvalidValue;
   }
   if (err != cudaSuccess) return err;
@@ -239,6 +241,8 @@ cudaError_t launch_max_dt(Ctx& c, const double* U, double, double, cudaStream_t 
     case 5: return dt_N<5>(c, U, s);
     case 6: return dt_N<6>(c, U, s);
     case 7: return dt_N<7>(c, U, s);
+    case 8: return dt_N<8>(c, U, s);
+    case 9: return dt_N<9>(c, U, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -156,6 +156,8 @@ static cudaError_t dispatch_stage(const Group& g, int k, const double* A, const 
     case 5: return launch_group_stage<5, R>(g, k, A, B, C, s);
     case 6: return launch_group_stage<6, R>(g, k, A, B, C, s);
     case 7: return launch_group_stage<7, R>(g, k, A, B, C, s);
+    case 8: return launch_group_stage<8, R>(g, k, A, B, C, s);
+    case 9: return launch_group_stage<9, R>(g, k, A, B, C, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -170,6 +172,8 @@ static cudaError_t dispatch_setup(int N) {
     case 5: return setup_group<5, R>();
     case 6: return setup_group<6, R>();
     case 7: return setup_group<7, R>();
+    case 8: return setup_group<8, R>();
+    case 9: return setup_group<9, R>();
     default: return cudaErrorInvalidValue;
   }
 }
@@ -184,6 +188,8 @@ static int epb_of_t(int N, int choice) {
     case 5: return choice ? Epb2<5, R>::value : Shape<5>::EPB;
     case 6: return choice ? Epb2<6, R>::value : Shape<6>::EPB;
     case 7: return choice ? Epb2<7, R>::value : Shape<7>::EPB;
+    case 8: return choice ? Epb2<8, R>::value : Shape<8>::EPB;
+    case 9: return choice ? Epb2<9, R>::value : Shape<9>::EPB;
     default: return 1;
   }
 }

@@ -13,7 +13,7 @@
 namespace dg {
 
 template <int N>
-__global__ void k_geometry(const double* __restrict__ xgeo, int ngeo, const double* __restrict__ Vg,
+__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1)) k_geometry(const double* __restrict__ xgeo, int ngeo, const double* __restrict__ Vg,
                            const double* __restrict__ Dg, double* __restrict__ metrics, double* __restrict__ Jout,
                            double* __restrict__ Xout, int* __restrict__ bad, int E) {
   constexpr int n = N + 1, P = n * n * n;
@@ -179,6 +179,8 @@ cudaError_t build_geometry(Ctx& c, const double* d_xgeo, int ngeo, int* d_bad, c
       case 5: err = geometry_N<5>(c, d_xgeo, ngeo, d_V, d_bad, s); break;
       case 6: err = geometry_N<6>(c, d_xgeo, ngeo, d_V, d_bad, s); break;
       case 7: err = geometry_N<7>(c, d_xgeo, ngeo, d_V, d_bad, s); break;
+      case 8: err = geometry_N<8>(c, d_xgeo, ngeo, d_V, d_bad, s); break;
+      case 9: err = geometry_N<9>(c, d_xgeo, ngeo, d_V, d_bad, s); break;
       default: err = cudaErrorInvalidValue;
     }
   }

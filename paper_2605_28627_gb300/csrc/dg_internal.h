@@ -31,6 +31,8 @@ struct Gas {
   double kappa;      // lambda / mu = c_p / Pr
   double inv_R;
   double mms_amp;
+  double p_ref;      // reference pressure of the FP32 operator's momentum flux
+  double E_ref;      // p_ref / (gamma - 1)
   int surf_flux;
   int source;
 };

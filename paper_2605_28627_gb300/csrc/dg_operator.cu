@@ -58,6 +58,8 @@ static cudaError_t face_N(const Ctx& c, const double* U, cudaStream_t s) {
     case 5: return FN<5>(__VA_ARGS__);       \
     case 6: return FN<6>(__VA_ARGS__);       \
     case 7: return FN<7>(__VA_ARGS__);       \
+    case 8: return FN<8>(__VA_ARGS__);       \
+    case 9: return FN<9>(__VA_ARGS__);       \
     default: return cudaErrorInvalidValue;   \
   }
 

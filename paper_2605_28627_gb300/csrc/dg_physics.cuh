@@ -89,6 +89,41 @@ __device__ __forceinline__ void ec_flux(const NodePrim<R>& a, const NodePrim<R>&
   f[4] = fr * (R(0.5) * inv_gm1 / beta_ln - ke) + ua * f[1] + va * f[2] + wa * f[3];
 }
 
+// Euler flux f(q) . n with separate pressures in the momentum (pm) and energy
+// (p) components: pm = p - p_ref for the FP32 operator's offset form (see
+// face_body), pm = p otherwise.
+template <typename R>
+__device__ __forceinline__ void euler_flux_pm(const R q[5], R u, R v, R w, R p, R pm, R nx, R ny, R nz, R f[5]) {
+  const R un = u * nx + v * ny + w * nz;
+  f[0] = q[0] * un;
+  f[1] = q[1] * un + pm * nx;
+  f[2] = q[2] * un + pm * ny;
+  f[3] = q[3] * un + pm * nz;
+  f[4] = (q[4] + p) * un;
+}
+
+// Two-point flux of ec_flux in the offset form: the momentum flux carries
+// p_hat - p_ref, computed as (dl_a + dl_b) / (2 (beta_a + beta_b)) from the
+// per-node dl = rho (p - p_ref) / p (= rho - 2 p_ref beta), and the energy flux
+// adds p_ref {u}.n back, so the result equals ec_flux minus p_ref n in the
+// momentum components.
+template <typename R>
+__device__ __forceinline__ void ec_flux_off(const NodePrim<R>& a, const NodePrim<R>& b, R dla, R dlb, R p_ref, R nx,
+                                            R ny, R nz, R inv_gm1, R f[5]) {
+  const R rho_ln = log_mean(a.rho, b.rho);
+  const R beta_ln = log_mean(a.beta, b.beta);
+  const R ua = R(0.5) * (a.u + b.u), va = R(0.5) * (a.v + b.v), wa = R(0.5) * (a.w + b.w);
+  const R p_off = R(0.5) * (dla + dlb) / (a.beta + b.beta);
+  const R ke = R(0.25) * (a.u * a.u + a.v * a.v + a.w * a.w + b.u * b.u + b.v * b.v + b.w * b.w);
+  const R un = ua * nx + va * ny + wa * nz;
+  const R fr = rho_ln * un;
+  f[0] = fr;
+  f[1] = fr * ua + p_off * nx;
+  f[2] = fr * va + p_off * ny;
+  f[3] = fr * wa + p_off * nz;
+  f[4] = fr * (R(0.5) * inv_gm1 / beta_ln - ke) + ua * f[1] + va * f[2] + wa * f[3] + p_ref * un;
+}
+
 // Euler flux f(q) . n for an arbitrary vector n.
 template <typename R>
 __device__ __forceinline__ void euler_flux(const R q[5], R u, R v, R w, R p, R nx, R ny, R nz, R f[5]) {
@@ -98,6 +133,57 @@ __device__ __forceinline__ void euler_flux(const R q[5], R u, R v, R w, R p, R n
   f[2] = q[2] * un + p * ny;
   f[3] = q[3] * un + p * nz;
   f[4] = (q[4] + p) * un;
+}
+
+// Roe's approximate Riemann solver with the Harten-Hyman (1983) entropy fix
+// on the acoustic waves, unit direction n (the surface flux of Sec. 3.1):
+// F = (f(qL) + f(qR)).n/2 - sum_k |lambda_k| alpha_k r_k / 2, Roe averages with
+// sqrt(rho) weights; |lambda| -> delta = max(0, lambda - lambda(qL),
+// lambda(qR) - lambda) where |lambda| < delta.
+template <typename R>
+__device__ __forceinline__ void roe_flux(const R qL[5], R uL, R vL, R wL, R pL, const R qR[5], R uR, R vR, R wR,
+                                         R pR, R nx, R ny, R nz, R gamma, R gm1, R F[5], R pmL, R pmR) {
+  R fL[5], fR[5];
+  euler_flux_pm<R>(qL, uL, vL, wL, pL, pmL, nx, ny, nz, fL);
+  euler_flux_pm<R>(qR, uR, vR, wR, pR, pmR, nx, ny, nz, fR);
+  const R sL = sqrt(qL[0]), sR = sqrt(qR[0]);
+  const R is = R(1) / (sL + sR);
+  const R wl = sL * is, wr = sR * is;
+  const R HL = (qL[4] + pL) / qL[0], HR = (qR[4] + pR) / qR[0];
+  const R u = wl * uL + wr * uR, v = wl * vL + wr * vR, w = wl * wL + wr * wR;
+  const R H = wl * HL + wr * HR;
+  const R q2 = u * u + v * v + w * w;
+  const R c = sqrt(gm1 * (H - R(0.5) * q2));
+  const R rho = sL * sR;
+  const R un = u * nx + v * ny + w * nz;
+  const R dr = qR[0] - qL[0], dp = pR - pL;
+  const R du = uR - uL, dv = vR - vL, dw = wR - wL;
+  const R dun = du * nx + dv * ny + dw * nz;
+  const R ic2 = R(1) / (c * c);
+  const R a1 = (dp - rho * c * dun) * R(0.5) * ic2;
+  const R a2 = dr - dp * ic2;
+  const R a5 = (dp + rho * c * dun) * R(0.5) * ic2;
+  R l1 = fabs(un - c);
+  const R l2 = fabs(un);
+  R l5 = fabs(un + c);
+  const R unL = uL * nx + vL * ny + wL * nz, unR = uR * nx + vR * ny + wR * nz;
+  const R cL = sqrt(gamma * pL / qL[0]), cR = sqrt(gamma * pR / qR[0]);
+  const R d1 = fmax(fmax(R(0), (un - c) - (unL - cL)), (unR - cR) - (un - c));
+  const R d5 = fmax(fmax(R(0), (un + c) - (unL + cL)), (unR + cR) - (un + c));
+  if (l1 < d1) l1 = d1;
+  if (l5 < d5) l5 = d5;
+  const R A1 = l1 * a1, A5 = l5 * a5;
+  const R udu = u * du + v * dv + w * dw;
+  const R D0 = A1 + l2 * a2 + A5;
+  const R D1 = A1 * (u - c * nx) + l2 * (a2 * u + rho * (du - dun * nx)) + A5 * (u + c * nx);
+  const R D2 = A1 * (v - c * ny) + l2 * (a2 * v + rho * (dv - dun * ny)) + A5 * (v + c * ny);
+  const R D3 = A1 * (w - c * nz) + l2 * (a2 * w + rho * (dw - dun * nz)) + A5 * (w + c * nz);
+  const R D4 = A1 * (H - un * c) + l2 * (a2 * R(0.5) * q2 + rho * (udu - un * dun)) + A5 * (H + un * c);
+  F[0] = R(0.5) * (fL[0] + fR[0] - D0);
+  F[1] = R(0.5) * (fL[1] + fR[1] - D1);
+  F[2] = R(0.5) * (fL[2] + fR[2] - D2);
+  F[3] = R(0.5) * (fL[3] + fR[3] - D3);
+  F[4] = R(0.5) * (fL[4] + fR[4] - D4);
 }
 
 // Viscous flux (Newtonian stress with Stokes' hypothesis, Fourier heat flux)

@@ -36,12 +36,14 @@ struct Shape {
 template <int N, int EPB_ = default_epb((N + 1) * (N + 1) * (N + 1))>
 struct VShape : Shape<N, EPB_> {
   static constexpr int ROUNDS = (N + 1) / 2;    // shifts s = 1..n/2 (s = n/2 half-used for even n)
-  static constexpr int PER_ELEM = 32 * (N + 1) * (N + 1) * (N + 1);   // operator words of smem per element
+  static constexpr int PER_ELEM = 26 * (N + 1) * (N + 1) * (N + 1);   // operator words of smem per element
 };
 
 template <int N, typename R, int EPB>
 constexpr size_t volume_smem_bytes() {
-  return sizeof(R) * (3 * (N + 1) * (N + 1) + (((N + 1) * (N + 1) + 3) & ~3) + EPB * VShape<N, EPB>::PER_ELEM);
+  // the FP32 operator keeps one more word per node (the offset pressure term)
+  return sizeof(R) * (3 * (N + 1) * (N + 1) + (((N + 1) * (N + 1) + 3) & ~3) + EPB * VShape<N, EPB>::PER_ELEM +
+                      (sizeof(R) == 4 ? EPB * (N + 1) * (N + 1) * (N + 1) : 0));
 }
 
 // rcp for the operator type: FP64 by hardware approximation + one cubic
@@ -178,15 +180,30 @@ __device__ __forceinline__ void face_body(const double* __restrict__ U, const R*
   const R uR = qR[1] * irR, vR = qR[2] * irR, wR = qR[3] * irR;
   const R pL = gm1 * (qL[4] - R(0.5) * (qL[1] * uL + qL[2] * vL + qL[3] * wL));
   const R pR = gm1 * (qR[4] - R(0.5) * (qR[1] * uR + qR[2] * vR + qR[3] * wR));
+  // Pressure in the momentum flux.  The FP32 operator uses p - p_ref with the
+  // energy difference E - p_ref/(gamma-1) taken in FP64 (one add per node):
+  // a constant pressure has no discrete divergence (metric identities), so R
+  // is unchanged, while the FP32 rounding of a large background pressure
+  // (low Mach numbers) no longer enters the momentum equations.
+  R pmL = pL, pmR = pR;
+  if constexpr (sizeof(R) == 4) {
+    pmL = gm1 * (R(U[((size_t)eM * 5 + 4) * P + idM] - g.E_ref) - R(0.5) * (qL[1] * uL + qL[2] * vL + qL[3] * wL));
+    pmR = gm1 * (R(U[((size_t)eS * 5 + 4) * P + idS] - g.E_ref) - R(0.5) * (qR[1] * uR + qR[2] * vR + qR[3] * wR));
+  }
   R fa[5];
   if (g.surf_flux == DG_FLUX_EC) {
     NodePrim<R> a{qL[0], uL, vL, wL, pL, R(0.5) * qL[0] / pL};
     NodePrim<R> b{qR[0], uR, vR, wR, pR, R(0.5) * qR[0] / pR};
-    ec_flux<R>(a, b, nx, ny, nz, R(g.inv_gm1), fa);
+    if constexpr (sizeof(R) == 4)
+      ec_flux_off<R>(a, b, qL[0] * pmL / pL, qR[0] * pmR / pR, R(g.p_ref), nx, ny, nz, R(g.inv_gm1), fa);
+    else
+      ec_flux<R>(a, b, nx, ny, nz, R(g.inv_gm1), fa);
+  } else if (g.surf_flux == DG_FLUX_ROE) {
+    roe_flux<R>(qL, uL, vL, wL, pL, qR, uR, vR, wR, pR, nx, ny, nz, gam, gm1, fa, pmL, pmR);
   } else {
     R fL[5], fR[5];
-    euler_flux<R>(qL, uL, vL, wL, pL, nx, ny, nz, fL);
-    euler_flux<R>(qR, uR, vR, wR, pR, nx, ny, nz, fR);
+    euler_flux_pm<R>(qL, uL, vL, wL, pL, pmL, nx, ny, nz, fL);
+    euler_flux_pm<R>(qR, uR, vR, wR, pR, pmR, nx, ny, nz, fR);
     const R cL = sqrt(gam * pL * irL), cR = sqrt(gam * pR * irR);
     const R lL = fabs(uL * nx + vL * ny + wL * nz) + cL;
     const R lR = fabs(uR * nx + vR * ny + wR * nz) + cR;
@@ -271,9 +288,10 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
   R* sU = sR + P;                     // u, v, w
   R* sB = sU + 3 * P;                 // beta = rho / (2 p)
   R* sK = sB + P;                     // |u|^2
-  R* sJa = sK + P;                    // [9][P]  Ja^d_l at row d*3+l
-  R* sFv = sJa + 9 * P;               // [3][4][P] (f_v . Ja^d), momentum + energy
+  R* sJd = sK + P;                    // [3][P]  Ja^d of the direction being swept
+  R* sFv = sJd + 3 * P;               // [3][4][P] (f_v . Ja^d), momentum + energy
   R* sX = sFv + 12 * P;               // [5][P] exchange of partner shares
+  R* sDl = sT2 + ((n * n + 3) & ~3) + EPB * S::PER_ELEM + le * P;   // FP32 only: rho (p - p_ref) / p
   const int e = blk * EPB + le;
   const bool active = e < E;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
@@ -292,7 +310,7 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     for (int r = 0; r < 5; ++r) q[r] = a.U[((size_t)e * 5 + r) * P + id];
     const R* mt = metrics + (size_t)e * 10 * P + id;
 #pragma unroll
-    for (int r = 0; r < 9; ++r) { Ja[r] = mt[r * P]; sJa[r * P + id] = Ja[r]; }
+    for (int r = 0; r < 9; ++r) Ja[r] = mt[r * P];
     rho = R(q[0]);
     const R ir = rcp_op(rho);
     u = R(q[1]) * ir; v = R(q[2]) * ir; w = R(q[3]) * ir;
@@ -300,6 +318,12 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     const R p = R(g.gm1) * fma(R(-0.5) * rho, kk, R(q[4]));
     beta = R(0.5) * rho * rcp_op(p);
     sR[id] = rho; sU[id] = u; sU[P + id] = v; sU[2 * P + id] = w; sB[id] = beta; sK[id] = kk;
+    if constexpr (sizeof(R) == 4) {
+      // offset form of the momentum flux (see face_body): p - p_ref from the
+      // FP64 energy difference, stored as rho (p - p_ref) / p
+      const R pm = R(g.gm1) * fma(R(-0.5) * rho, kk, R(q[4] - g.E_ref));
+      sDl[id] = rho * pm * rcp_op(p);
+    }
     R gr[12];
     const R* gg = grad + (size_t)e * 12 * P + id;
 #pragma unroll
@@ -323,6 +347,13 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     const int r = ijk[d];
     const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
     const int line0 = id - r * stride;
+    // the partners' metric terms of this direction (shared memory holds one
+    // direction at a time)
+    if (d > 0) __syncthreads();
+    sJd[id] = Ja[d * 3];
+    sJd[P + id] = Ja[d * 3 + 1];
+    sJd[2 * P + id] = Ja[d * 3 + 2];
+    __syncthreads();
 #pragma unroll 1
     for (int s = 1; s <= S::ROUNDS; ++s) {
       const bool half = (2 * s == n);
@@ -340,17 +371,20 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
         if (small_u(ub)) hib = atanh_ratio(ub) * rbt;
         else hib = atanh_ratio_log(beta, bb) * rbt;
         const R su0 = u + sU[mid], su1 = v + sU[P + mid], su2 = w + sU[2 * P + mid];
-        const R sn0 = Ja[d * 3] + sJa[(d * 3) * P + mid];
-        const R sn1 = Ja[d * 3 + 1] + sJa[(d * 3 + 1) * P + mid];
-        const R sn2 = Ja[d * 3 + 2] + sJa[(d * 3 + 2) * P + mid];
+        const R sn0 = Ja[d * 3] + sJd[mid];
+        const R sn1 = Ja[d * 3 + 1] + sJd[P + mid];
+        const R sn2 = Ja[d * 3 + 2] + sJd[2 * P + mid];
         const R un4 = fma(su0, sn0, fma(su1, sn1, su2 * sn2));
         const R Xf = rln2 * un4;                      // 8 f_rho
-        const R Y4 = R(4) * sr * rbt;                  // 16 p_hat / |n_avg| scale
+        // 16 p_hat n_avg = Y4 (n_a + n_b); the FP32 operator uses p_hat - p_ref
+        R Y4 = R(4) * sr * rbt;
+        if constexpr (sizeof(R) == 4) Y4 = R(4) * (sDl[id] + sDl[mid]) * rbt;
         const R M0 = fma(Xf, su0, Y4 * sn0);          // 16 f_m
         const R M1 = fma(Xf, su1, Y4 * sn1);
         const R M2 = fma(Xf, su2, Y4 * sn2);
         const R Z = fma(hib, inv4, -(kk + sK[mid]));
-        const R E32 = fma(Xf, Z, fma(su0, M0, fma(su1, M1, su2 * M2)));   // 32 f_E
+        R E32 = fma(Xf, Z, fma(su0, M0, fma(su1, M1, su2 * M2)));   // 32 f_E
+        if constexpr (sizeof(R) == 4) E32 = fma(R(8.0 * g.p_ref), un4, E32);     // p_ref {u}.n back
         const int rm = r * n + m;
         acc[0] = fma(sT0[rm], Xf, acc[0]);
         acc[1] = fma(sT1[rm], M0, acc[1]);

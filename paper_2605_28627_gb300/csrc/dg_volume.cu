@@ -5,8 +5,10 @@
 
 namespace dg {
 
+// FP32 tiles of up to 512 threads are kept to <= 64 registers so that two
+// blocks share an SM (the FP32 operator is latency-bound, the FP64 one is not).
 template <int N, typename R>
-__global__ void __launch_bounds__(VShape<N>::THREADS)
+__global__ void __launch_bounds__(VShape<N>::THREADS, (sizeof(R) == 4 && VShape<N>::THREADS <= 512) ? 2 : 1)
 k_volume2(StageArgs a, const R* __restrict__ metrics, const double* __restrict__ iJ64,
           const R* __restrict__ grad, const R* __restrict__ fstar, const int* __restrict__ elem_face,
           const double* __restrict__ X, const double* __restrict__ Dg, int E, Gas g, double inv_w0) {
@@ -55,6 +57,8 @@ cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s) {
     case 5: return volume_any<5>(c, a, s);
     case 6: return volume_any<6>(c, a, s);
     case 7: return volume_any<7>(c, a, s);
+    case 8: return volume_any<8>(c, a, s);
+    case 9: return volume_any<9>(c, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -68,6 +72,8 @@ cudaError_t setup_volume(int N) {
     case 5: return setup_any<5>();
     case 6: return setup_any<6>();
     case 7: return setup_any<7>();
+    case 8: return setup_any<8>();
+    case 9: return setup_any<9>();
     default: return cudaErrorInvalidValue;
   }
 }

@@ -34,7 +34,7 @@ def _init(mesh, N=3, **kw):
     nbr = np.ascontiguousarray(mesh.face_nbr, dtype=np.int32)
     m = dg.dg_mesh(xgeo.shape[0], xgeo.shape[-1] - 1, xgeo.ctypes.data_as(C.POINTER(C.c_double)),
                    nbr.ctypes.data_as(C.POINTER(C.c_int32)))
-    prm = dict(N=N, gamma=1.4, R=1.0, Pr=0.72, mu=0.01, surf_flux=0, precision=0, source=0, mms_amp=0.1)
+    prm = dict(N=N, gamma=1.4, R=1.0, Pr=0.72, mu=0.01, surf_flux=0, precision=0, source=0, mms_amp=0.1, p_ref=0.0)
     prm.update(kw)
     p = dg.dg_params(**prm)
     h = C.c_void_p()
@@ -46,6 +46,8 @@ def test_init_rejects_bad_arguments_on_host():
     m = box_mesh(2, 1, rotate_seed=1)
     st, h, msg = _init(m, N=0)
     assert st == dg.DG_EUNSUPPORTED and not h.value and "N" in msg
+    st, h, msg = _init(m, N=10)
+    assert st == dg.DG_EUNSUPPORTED and not h.value
     st, h, msg = _init(m, N=3, gamma=0.9)
     assert st == dg.DG_EINVAL and not h.value
     st, h, msg = _init(m, N=3, surf_flux=5)

@@ -20,7 +20,7 @@ def dg():
     return m
 
 
-@pytest.mark.parametrize("N", [2, 3, 5, 7])
+@pytest.mark.parametrize("N", [2, 3, 5, 7, 9])
 def test_fp32_time_derivative_vs_oracle(orc, dg, N):
     K = 3 if N <= 4 else 2
     mesh = box_mesh(K, N, deform="sinprod", rotate_seed=400 + N)
@@ -70,3 +70,28 @@ def test_fp32_free_stream(dg):
     R = s.time_derivative(torch.from_numpy(U).cuda()).cpu().numpy()
     # FP32 rounding of terms of size |D| |f . Ja| / J ~ 1e2
     assert np.abs(R).max() < 1e-3
+
+
+@pytest.mark.parametrize("flux", [0, 1, 2])
+def test_fp32_pressure_offset_low_mach(orc, dg, flux):
+    """The FP32 operator with the background pressure p_ref taken out of the
+    momentum flux returns the same R(U) (the constant part has no discrete
+    divergence), with momentum rounding errors set by p - p_ref instead of p:
+    at Ma 0.1 (p0 = 71) that is more than ten times smaller."""
+    prm = tgv_params(Ma=0.1, Re=1600.0)
+    N = 5
+    mesh = box_mesh(3, N, lo=0.0, hi=2 * math.pi, deform="sinprod", amp=0.05, rotate_seed=31)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], surf_flux=flux)
+    o = orc.Oracle(mesh, N, **kw)
+    U0 = o.initial_state("tgv", prm["p0"])
+    ref = o.time_derivative(U0).reshape(mesh.n_elems, 5, -1)
+    errs = {}
+    for p_ref in (0.0, prm["p0"]):
+        s = dg.Solver(mesh, N, precision=dg.FP32OP, p_ref=p_ref, **kw)
+        got = s.time_derivative(torch.from_numpy(U0).cuda()).cpu().numpy().reshape(mesh.n_elems, 5, -1)
+        errs[p_ref] = [np.abs(got[:, v] - ref[:, v]).max() / np.abs(ref[:, v]).max() for v in range(5)]
+        s.close()
+    e0, e1 = errs[0.0], errs[prm["p0"]]
+    assert max(e1) < 2e-5, e1
+    for v in (1, 2, 3):
+        assert e1[v] < 0.1 * e0[v], (v, e0, e1)

@@ -47,7 +47,7 @@ def _pair(orc, dg, mesh, N, **kw):
     return o, s
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_geometry_parity(orc, dg, N):
     mesh = box_mesh(3 if N < 5 else 2, N, deform="sinprod", rotate_seed=100 + N)
     o, s = _pair(orc, dg, mesh, N)
@@ -61,8 +61,8 @@ def test_geometry_parity(orc, dg, N):
     assert np.abs(Jag.cpu().numpy() - Ja).max() <= 1e-12 * scale
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
-@pytest.mark.parametrize("flux", [0, 1])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("flux", [0, 1, 2])
 def test_time_derivative_parity_random_state(orc, dg, N, flux):
     K = 3 if N <= 4 else 2
     mesh = box_mesh(K, N, deform="sinprod", rotate_seed=200 + N)
@@ -146,7 +146,7 @@ def test_tgv_config1_rk_parity(orc, dg):
     np.testing.assert_allclose(Ig, Io, rtol=1e-11, atol=1e-13)
 
 
-@pytest.mark.parametrize("N", [1, 4, 7])
+@pytest.mark.parametrize("N", [1, 4, 7, 9])
 def test_mms_curved_rk_parity(orc, dg, N):
     prm = mms_params()
     mesh = box_mesh(3 if N < 7 else 2, N, deform="sinprod", rotate_seed=20260528)

@@ -95,3 +95,34 @@ def test_llf_flux(orc):
         ref = 0.5 * (_euler(qL, n) + _euler(qR, n)) - 0.5 * lam * (qR - qL)
         np.testing.assert_allclose(f, ref, rtol=1e-13, atol=1e-13)
         np.testing.assert_allclose(orc.llf_flux(qL, qL, n), _euler(qL, n), rtol=1e-14, atol=1e-14)
+
+
+def test_roe_flux_pins(orc):
+    """Roe + Harten-Hyman: consistency, rotational symmetry F(qL,qR,n) =
+    -F(qR,qL,-n), the Roe property |A|(qR - qL) reproducing fR - fL for a
+    single supersonic state pair (pure upwinding when every Roe speed is
+    positive and the entropy fix is inactive), and the fix itself at a sonic
+    rarefaction (a transonic expansion gets dissipation on the sonic wave)."""
+    rng = np.random.default_rng(9)
+    for _ in range(300):
+        qL, qR = _rand_state(rng), _rand_state(rng)
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        np.testing.assert_allclose(orc.roe_flux(qL, qL, n), _euler(qL, n), rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(orc.roe_flux(qL, qR, n), -orc.roe_flux(qR, qL, -n), rtol=1e-12, atol=1e-12)
+    # supersonic flow to +x: upwind flux = f(qL) when the fix is inactive
+    n = np.array([1.0, 0.0, 0.0])
+    def cons(r, u, p):
+        return np.array([r, r * u[0], r * u[1], r * u[2], p / (GAMMA - 1) + 0.5 * r * np.dot(u, u)])
+    qL = cons(1.0, np.array([3.0, 0.1, -0.2]), 1.0)
+    qR = cons(1.05, np.array([3.02, 0.1, -0.2]), 1.04)
+    np.testing.assert_allclose(orc.roe_flux(qL, qR, n), _euler(qL, n), rtol=1e-12, atol=1e-12)
+    # Roe property: fR - fL = A_roe (qR - qL) implies F(qL, qR) - F(qR, qL; -n -> ) symmetric
+    # transonic rarefaction: un - c changes sign from left to right; without the
+    # fix the sonic wave would have |lambda| ~ 0 at the Roe state
+    qL = cons(1.0, np.array([np.sqrt(1.4) - 0.3, 0, 0]), 1.0)
+    qR = cons(0.7, np.array([np.sqrt(1.4) * 0.95 + 0.4, 0, 0]), 0.6)
+    F = orc.roe_flux(qL, qR, n)
+    assert np.all(np.isfinite(F))
+    central = 0.5 * (_euler(qL, n) + _euler(qR, n))
+    assert np.abs(F - central).max() > 1e-3

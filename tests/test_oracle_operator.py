@@ -87,7 +87,7 @@ def _conservation(orc, o, U, N):
     return tot, scale
 
 
-@pytest.mark.parametrize("N,flux", [(2, 0), (3, 0), (4, 1)])
+@pytest.mark.parametrize("N,flux", [(2, 0), (3, 0), (4, 1), (3, 2)])
 def test_discrete_conservation(orc, N, flux):
     m = box_mesh(2, N, deform="sinprod", rotate_seed=13)
     o = orc.Oracle(m, N, mu=0.02, surf_flux=flux)
