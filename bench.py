@@ -334,6 +334,62 @@ def run_ensemble(args, local):
     return 0
 
 
+def run_pid(args, local):
+    """Free-stream PID runs in the setups of the paper's performance section:
+    16.78 M DOF at N=3 (64^3 Cartesian elements; the paper's node-level PID
+    comparison, there on Gauss nodes) and N=9 at 20^3 elements (8.0 M DOF,
+    the per-GPU load of the paper's weak-scaling runs of the split-form LGL
+    operator), 10 LSERK4-5 steps each, FP64 and FP32 operator.  Uniform flow
+    rho = 1, u = (0.1, 0.05, 0.02), p = 1/gamma, mu = 1/1600; every kernel
+    does its full work on it.  Reports DOF*stage/s, PID and the free-stream
+    preservation error max|U - U0| / max|U0| after the steps."""
+    import torch
+    import paper_2605_28627_gb300 as dg
+    from workloads import box_mesh
+    cases = (("N3_64cubed", 3, 64), ("N9_20cubed", 9, 20))
+    gamma, nsteps = 1.4, args.pid_steps
+    out = {}
+    for name, N, K in cases:
+        mesh = box_mesh(K, 1, lo=0.0, hi=2 * math.pi)
+        dofs = mesh.n_elems * (N + 1) ** 3
+        res = {"N": N, "elements": mesh.n_elems, "dof": dofs}
+        for prec_name, prec in (("fp64", dg.FP64), ("fp32op", dg.FP32OP)):
+            s = dg.Solver(mesh, N, gamma=gamma, R=1.0, Pr=0.72, mu=1.0 / 1600.0, precision=prec, device=local)
+            st = torch.cuda.Stream(device="cuda:%d" % local)
+            with torch.cuda.stream(st):
+                U = torch.zeros(s.shape, dtype=torch.float64, device="cuda:%d" % local)
+                u = (0.1, 0.05, 0.02)
+                U[:, 0] = 1.0
+                for a in range(3):
+                    U[:, 1 + a] = u[a]
+                U[:, 4] = 1.0 / gamma / (gamma - 1.0) + 0.5 * sum(c * c for c in u)
+                U0 = U.clone()
+                G = torch.empty_like(U)
+            dt = s.max_dt(U, cfl=0.9, dfl=0.9, stream=st)
+            for i in range(3):
+                s.rk_step(U, G, i * dt, dt, 1, stream=st)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            s.rk_step(U, G, 3 * dt, dt, nsteps, stream=st)
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            rate = dofs * 5 * nsteps / (ms * 1e-3)
+            drift = float((U - U0).abs().max() / U0.abs().max())
+            res[prec_name] = {"dof_stage_per_s": rate, "pid_ns": 1e9 / rate, "ms_per_step": ms / nsteps,
+                              "freestream_drift": drift}
+            del U, U0, G
+            s.close()
+            torch.cuda.empty_cache()
+        out[name] = res
+    line = {"experiment": "free-stream PID, %d LSERK4-5 steps after 3 warm-up steps, one graph launch" % nsteps,
+            "cases": out,
+            "paper_context": {"pid_ns_full_dg_N3_16.78M_dof_per_MI300A_gauss_nodes": 3.56864,
+                              "weak_scaling_N9_dof_per_gpu_range": [1.024e6, 8.192e6]}}
+    print(json.dumps(line))
+    return 0
+
+
 def run_adjoint(args, local):
     """Discrete adjoint: 16^3 Cartesian elements, N=5 (884,736 nodes), Taylor-
     Green vortex at Ma 0.2, Re 800, FP64, 200 LSERK4-5 steps at CFL 0.9.
@@ -424,12 +480,14 @@ def main():
     ap.add_argument("--order", type=int, default=7)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sweep", default="3,4,5,6,7", help="extra orders timed for the per-N table ('' = none)")
+    ap.add_argument("--sweep", default="1,2,3,4,5,6,7,8,9", help="extra orders timed for the per-N table ('' = none)")
     ap.add_argument("--tgv-large", action="store_true", help="run the 48^3, N=7 FP64-vs-FP32 Taylor-Green study")
     ap.add_argument("--tgv-steps", type=int, default=200)
     ap.add_argument("--ensemble", action="store_true", help="run the 64-member batched ensemble study")
     ap.add_argument("--ens-steps", type=int, default=10)
     ap.add_argument("--adjoint", action="store_true", help="run the 16^3, N=5 discrete-adjoint study")
+    ap.add_argument("--pid", action="store_true", help="run the free-stream PID study (N=3 at 64^3, N=9 at 20^3)")
+    ap.add_argument("--pid-steps", type=int, default=10)
     ap.add_argument("--adj-steps", type=int, default=200)
     ap.add_argument("--adj-dirs", type=int, default=32)
     args = ap.parse_args()
@@ -439,6 +497,8 @@ def main():
         return run_tgv_large(args, local) if rank == 0 else 0
     if args.ensemble:
         return run_ensemble(args, local) if rank == 0 else 0
+    if args.pid:
+        return run_pid(args, local) if rank == 0 else 0
     if args.adjoint:
         return run_adjoint(args, local) if rank == 0 else 0
     if args.impl == "reference":

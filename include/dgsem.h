@@ -53,6 +53,10 @@ enum { DG_FLUX_LLF = 0, DG_FLUX_EC = 1, DG_FLUX_ROE = 2 };   /* surface Riemann 
                                                               the Harten-Hyman entropy fix (Sec. 3.1) */
 enum { DG_FP64 = 0, DG_FP32OP = 1 };              /* operator arithmetic */
 enum { DG_SOURCE_NONE = 0, DG_SOURCE_MMS = 1 };   /* volume source term */
+enum { DG_VISC_CONSTANT = 0, DG_VISC_SUTHERLAND = 1 };   /* viscosity law: constant mu, or Sutherland's law
+                                                           mu (T/T_ref)^(3/2) (T_ref + S)/(T + S) at each
+                                                           node's temperature (the law of the dissipation
+                                                           diagnostic, Sec. 4.2) */
 enum { DG_IC_TGV = 0, DG_IC_MMS = 1 };            /* built-in initial states */
 
 /*
@@ -88,6 +92,8 @@ typedef struct {
   double p_ref;               /* DG_FP32OP: constant pressure taken out of the momentum flux (it has no
                                  discrete divergence); the background pressure of a low-Mach flow keeps
                                  its FP32 rounding out of the momentum equations.  Ignored in FP64. */
+  int32_t visc_law;           /* DG_VISC_CONSTANT (mu above) or DG_VISC_SUTHERLAND (mu = mu(T_ref)) */
+  double T_ref, S_suth;       /* Sutherland reference temperature (> 0) and constant (>= 0) */
 } dg_params;
 
 /* Build a context on CUDA device `device`: LGL basis, geometry (node
@@ -219,6 +225,16 @@ dg_status dg_profile_stages(dg_ctx* ctx, double* dU, double* dG, double dt, int3
  * on `device` in TFLOP/s (FMA = 2 flop), host_out2 = {fp64, fp32}.  Used as
  * the arithmetic roof for the FP64-pipe-bound kernels.  Synchronous. */
 dg_status dg_probe_peaks(int device, double* host_out2);
+
+/* Check of the FP64 <-> FP32 conversions the FP32 operator uses (integer
+ * operations on the bit patterns; no counterpart in the paper, which does not
+ * describe the conversion).  For the n device values d_x: d_f[0..n) = the
+ * operator's FP32 narrowing, d_f[n..2n) = the hardware round-to-nearest
+ * conversion, d_d[0..n) = the operator's widening of d_f[0..n), d_d[n..2n) =
+ * the hardware widening of the same.  All pointers are device memory owned
+ * by the caller; d_f holds 2n floats and d_d 2n doubles.  Synchronises the
+ * stream.  DG_EINVAL for n < 0 or null pointers with n > 0. */
+dg_status dg_check_conversions(const double* d_x, int32_t n, float* d_f, double* d_d, dg_stream stream);
 
 /* Conservation totals sum_nodes w_i w_j w_k J q_v (v = rho, rho u, rho v,
  * rho w, rho E), the first five values of dg_integrals, for callers that may

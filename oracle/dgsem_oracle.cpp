@@ -21,7 +21,10 @@
 //    1/2 * mean of |u|^2 (the form that satisfies Tadmor's condition).
 //  * Logarithmic mean by the Ismail-Roe (2009) series/log split, with the
 //    switch at xi^2 < 1e-4 and four series terms (truncation < 1e-17).
-//  * Constant viscosity, Stokes hypothesis, lambda = mu c_p / Pr.
+//  * Viscosity constant or by Sutherland's law mu0 (T/T_ref)^(3/2)
+//    (T_ref + S)/(T + S) at each node's own temperature (the law the paper
+//    names for its dissipation diagnostic, Sec. 4.2); Stokes hypothesis,
+//    lambda = mu(T) c_p / Pr.
 //  * Derivatives at the kinks of the LLF speed max(|u.n| + c) (ties, u.n = 0,
 //    to within 1e-12 of the local scale) are the mean of the one-sided ones.
 //  * LSERK4-5 of Carpenter and Kennedy (1994), 2N storage.
@@ -178,6 +181,8 @@ struct Params {
   double mms_amp;
   int vol_flux;    // 0: Chandrashekar EC/KEP two-point flux; 1: arithmetic mean of
                    //    the Euler flux (a test variant equal to the standard DGSEM)
+  int visc_law;    // 0: constant mu; 1: Sutherland's law
+  double T_ref, S_suth;   // Sutherland reference temperature and constant
 };
 
 struct Ctx {
@@ -383,11 +388,22 @@ static inline void euler_flux(const T q[5], const Prim<T>& w, const T nv[3], T o
   out[4] = (q[4] + w.p) * un;
 }
 
-// Viscous flux (stress + Fourier heat flux) in direction nv, from the lifted
-// gradients g[phi*3 + l] = d phi / d x_l, phi in (u, v, w, T).
+// Dynamic viscosity at temperature Tt: mu0 itself, or Sutherland's (1893) law
+// mu0 (Tt/T_ref)^(3/2) (T_ref + S) / (Tt + S).
 template <class T>
-static inline void visc_flux(const Params& pr, const Prim<T>& w, const T* g, const T& mu,
+static inline T visc_mu(const Params& pr, const T& mu0, const T& Tt) {
+  if (pr.visc_law != 1) return mu0;
+  T x = Tt / pr.T_ref;
+  return mu0 * x * sqrt(x) * ((pr.T_ref + pr.S_suth) / (Tt + pr.S_suth));
+}
+
+// Viscous flux (stress + Fourier heat flux) in direction nv, from the lifted
+// gradients g[phi*3 + l] = d phi / d x_l, phi in (u, v, w, T); mu0 is the
+// reference viscosity, taken at the node's temperature by visc_mu.
+template <class T>
+static inline void visc_flux(const Params& pr, const Prim<T>& w, const T* g, const T& mu0,
                              const T nv[3], T out[5]) {
+  const T mu = visc_mu(pr, mu0, w.T_);
   T div = g[0 * 3 + 0] + g[1 * 3 + 1] + g[2 * 3 + 2];
   T tau[3][3];
   for (int a = 0; a < 3; ++a)
@@ -801,7 +817,13 @@ void* orc_create(int N, int n_elems, int ngeo, const double* xgeo, const int* fa
   c->N = N; c->n = N + 1; c->P = c->n * c->n * c->n; c->E = n_elems;
   c->prm.gamma = prm[0]; c->prm.R = prm[1]; c->prm.Pr = prm[2]; c->prm.mu = prm[3];
   c->prm.mms_amp = prm[4];
+  c->prm.visc_law = (int)prm[5]; c->prm.T_ref = prm[6]; c->prm.S_suth = prm[7];
   c->prm.surf_flux = surf_flux; c->prm.source = source; c->prm.vol_flux = 0;
+  if (c->prm.visc_law != 0 && c->prm.visc_law != 1) {
+    if (errbuf && errlen > 0) std::snprintf(errbuf, errlen, "unknown viscosity law %d", c->prm.visc_law);
+    delete c;
+    return nullptr;
+  }
   c->b = make_basis(N);
   if (!build_geometry(*c, ngeo, xgeo) || !build_faces(*c, face_nbr)) {
     if (errbuf && errlen > 0) std::snprintf(errbuf, errlen, "%s", c->err.c_str());
@@ -902,17 +924,17 @@ void orc_rk_coeffs(double* A, double* B, double* C) {
 
 // Two-point flux, LLF flux and log mean exposed for the pin tests.
 void orc_ec_flux(const double* prm, const double* qL, const double* qR, const double* nv, double* out) {
-  Params pr{prm[0], prm[1], prm[2], prm[3], 0, 0, 0.0, 0};
+  Params pr{prm[0], prm[1], prm[2], prm[3], 0, 0, 0.0, 0, 0, 1.0, 0.0};
   Prim<double> L = cons2prim(pr, qL), Rr = cons2prim(pr, qR);
   ec_flux(pr, L, Rr, nv, out);
 }
 void orc_llf_flux(const double* prm, const double* qL, const double* qR, const double* nv, double* out) {
-  Params pr{prm[0], prm[1], prm[2], prm[3], 0, 0, 0.0, 0};
+  Params pr{prm[0], prm[1], prm[2], prm[3], 0, 0, 0.0, 0, 0, 1.0, 0.0};
   Prim<double> L = cons2prim(pr, qL), Rr = cons2prim(pr, qR);
   llf_flux(pr, qL, L, qR, Rr, nv, out);
 }
 void orc_roe_flux(const double* prm, const double* qL, const double* qR, const double* nv, double* out) {
-  Params pr{prm[0], prm[1], prm[2], prm[3], 0, 0, 0.0, 0};
+  Params pr{prm[0], prm[1], prm[2], prm[3], 0, 0, 0.0, 0, 0, 1.0, 0.0};
   Prim<double> L = cons2prim(pr, qL), Rr = cons2prim(pr, qR);
   roe_flux(pr, qL, L, qR, Rr, nv, out);
 }
@@ -920,8 +942,8 @@ double orc_log_mean(double a, double b) { return log_mean<double>(a, b); }
 
 // Volume integrals (Sec. 4.2 diagnostics) with the LGL quadrature:
 // out = {int rho, int rho u, int rho v, int rho w, int rho E,
-//        E_k = 1/(2|Omega|) int rho |u|^2, eps_S = mu/|Omega| int |omega|^2,
-//        min p}; rho0 = U0 = L = 1 and mu/mu0 = 1 (constant viscosity).
+//        E_k = 1/(2|Omega|) int rho |u|^2, eps_S = 1/|Omega| int mu(T) |omega|^2,
+//        min p}; rho0 = U0 = L = 1, mu0 = 1/Re, mu(T) by the viscosity law.
 void orc_integrals(void* h, const double* U, double* out) {
   Ctx* c = (Ctx*)h;
   int n = c->n, P = c->P;
@@ -1003,12 +1025,15 @@ void orc_integrals(void* h, const double* U, double* out) {
           double om0 = gg[2 * 3 + 1] - gg[1 * 3 + 2];
           double om1 = gg[0 * 3 + 2] - gg[2 * 3 + 0];
           double om2 = gg[1 * 3 + 0] - gg[0 * 3 + 1];
-          ens += wq * (om0 * om0 + om1 * om1 + om2 * om2);
+          double q[5];
+          for (int v = 0; v < 5; ++v) q[v] = U[((size_t)e * 5 + v) * P + id];
+          const double mu_n = visc_mu(pr, pr.mu, cons2prim(pr, q).T_);
+          ens += wq * mu_n * (om0 * om0 + om1 * om1 + om2 * om2);
         }
   }
   for (int v = 0; v < 5; ++v) out[v] = tot[v];
   out[5] = 0.5 * ek / vol;
-  out[6] = pr.mu * ens / vol;
+  out[6] = ens / vol;
   out[7] = pmin;
 }
 

@@ -83,8 +83,8 @@ def rk_coeffs():
     return A, B, Cc
 
 
-def _prm(gamma, R, Pr, mu, amp=0.1):
-    return np.array([gamma, R, Pr, mu, amp], dtype=np.float64)
+def _prm(gamma, R, Pr, mu, amp=0.1, visc_law=0, T_ref=1.0, S_suth=0.0):
+    return np.array([gamma, R, Pr, mu, amp, visc_law, T_ref, S_suth], dtype=np.float64)
 
 
 def ec_flux(qL, qR, nv, gamma=1.4):
@@ -118,10 +118,12 @@ class Oracle:
     surf_flux: 0 = local Lax-Friedrichs, 1 = entropy-conservative two-point flux,
     2 = Roe with the Harten-Hyman entropy fix.
     source: 0 = none, 1 = density-wave manufactured solution.
+    visc_law: 0 = constant mu, 1 = Sutherland's law mu (T/T_ref)^1.5 (T_ref + S)/(T + S).
     """
 
     def __init__(self, mesh, N: int, gamma=1.4, R=1.0, Pr=0.72, mu=0.0,
-                 surf_flux: int = 0, source: int = 0, mms_amp: float = 0.1):
+                 surf_flux: int = 0, source: int = 0, mms_amp: float = 0.1,
+                 visc_law: int = 0, T_ref: float = 1.0, S_suth: float = 0.0):
         L = _load()
         self.N, self.n, self.P = N, N + 1, (N + 1) ** 3
         self.E = int(mesh.xgeo.shape[0])
@@ -130,7 +132,7 @@ class Oracle:
         nbr = np.ascontiguousarray(mesh.face_nbr, dtype=np.int32)
         err = C.create_string_buffer(256)
         h = L.orc_create(N, self.E, int(mesh.xgeo.shape[-1]) - 1, xgeo, nbr,
-                         _prm(gamma, R, Pr, mu, mms_amp), surf_flux, source, err, 256)
+                         _prm(gamma, R, Pr, mu, mms_amp, visc_law, T_ref, S_suth), surf_flux, source, err, 256)
         if not h:
             raise ValueError("oracle: " + err.value.decode())
         self._h = C.c_void_p(h)

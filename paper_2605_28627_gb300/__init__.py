@@ -24,6 +24,7 @@ STATUS_NAMES = ["DG_OK", "DG_EINVAL", "DG_ENOMEM", "DG_ECUDA", "DG_EMESH", "DG_E
 FLUX_LLF, FLUX_EC, FLUX_ROE = 0, 1, 2
 FP64, FP32OP = 0, 1
 SOURCE_NONE, SOURCE_MMS = 0, 1
+VISC_CONSTANT, VISC_SUTHERLAND = 0, 1
 IC_TGV, IC_MMS = 0, 1
 
 # Every symbol that include/dgsem.h declares.
@@ -31,7 +32,8 @@ EXPORTS = ["dg_init", "dg_destroy", "dg_state_len", "dg_time_derivative", "dg_rk
            "dg_integrals", "dg_max_dt", "dg_initial_state", "dg_node_coords", "dg_geometry", "dg_profile_stages",
            "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
            "dg_ensemble_step", "dg_ensemble_plan", "dg_ensemble_last_error", "dg_time_derivative_vjp",
-           "dg_adjoint_step", "dg_adjoint_solve", "dg_kinetic_energy", "dg_set_viscosity", "dg_last_error"]
+           "dg_adjoint_step", "dg_adjoint_solve", "dg_kinetic_energy", "dg_set_viscosity", "dg_check_conversions",
+           "dg_last_error"]
 
 
 class DGError(RuntimeError):
@@ -48,7 +50,8 @@ class dg_mesh(C.Structure):
 class dg_params(C.Structure):
     _fields_ = [("N", C.c_int32), ("gamma", C.c_double), ("R", C.c_double), ("Pr", C.c_double),
                 ("mu", C.c_double), ("surf_flux", C.c_int32), ("precision", C.c_int32),
-                ("source", C.c_int32), ("mms_amp", C.c_double), ("p_ref", C.c_double)]
+                ("source", C.c_int32), ("mms_amp", C.c_double), ("p_ref", C.c_double),
+                ("visc_law", C.c_int32), ("T_ref", C.c_double), ("S_suth", C.c_double)]
 
 
 _lib = None
@@ -79,6 +82,7 @@ def load(build_if_missing: bool = True):
     L.dg_geometry.argtypes = [vp, vp, vp, vp]
     L.dg_profile_stages.argtypes = [vp, vp, vp, f64, i32, C.POINTER(C.c_float), vp]
     L.dg_probe_peaks.argtypes = [C.c_int, dp]
+    L.dg_check_conversions.argtypes = [vp, i32, vp, vp, vp]
     L.dg_conserved_totals_noalloc.argtypes = [vp, vp, i32, i32, vp, vp]
     L.dg_ensemble_create.argtypes = [C.POINTER(vp), i32, C.c_char_p, C.POINTER(vp)]
     L.dg_ensemble_destroy.argtypes = [vp]
@@ -97,7 +101,7 @@ def load(build_if_missing: bool = True):
                  "dg_max_dt", "dg_initial_state", "dg_node_coords", "dg_geometry", "dg_profile_stages",
                  "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
                  "dg_ensemble_step", "dg_ensemble_plan", "dg_time_derivative_vjp", "dg_adjoint_step",
-                 "dg_adjoint_solve", "dg_kinetic_energy", "dg_set_viscosity"):
+                 "dg_adjoint_solve", "dg_kinetic_energy", "dg_set_viscosity", "dg_check_conversions"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -119,7 +123,8 @@ class Solver:
     ``[E, 5, N+1, N+1, N+1]``."""
 
     def __init__(self, mesh, N: int, gamma=1.4, R=1.0, Pr=0.72, mu=0.0, surf_flux=FLUX_LLF,
-                 precision=FP64, source=SOURCE_NONE, mms_amp=0.1, device: int = 0, p_ref: float = 0.0):
+                 precision=FP64, source=SOURCE_NONE, mms_amp=0.1, device: int = 0, p_ref: float = 0.0,
+                 visc_law: int = VISC_CONSTANT, T_ref: float = 1.0, S_suth: float = 0.0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2605_28627_gb300 needs a CUDA GPU; there is no CPU fallback")
@@ -131,7 +136,7 @@ class Solver:
         self.E = int(xgeo.shape[0])
         m = dg_mesh(self.E, int(xgeo.shape[-1]) - 1, xgeo.ctypes.data_as(C.POINTER(C.c_double)),
                     nbr.ctypes.data_as(C.POINTER(C.c_int32)))
-        p = dg_params(N, gamma, R, Pr, mu, surf_flux, precision, source, mms_amp, p_ref)
+        p = dg_params(N, gamma, R, Pr, mu, surf_flux, precision, source, mms_amp, p_ref, visc_law, T_ref, S_suth)
         h = C.c_void_p()
         torch.cuda.set_device(device)
         st = self._L.dg_init(C.byref(m), C.byref(p), device, C.byref(h))
@@ -302,6 +307,22 @@ def probe_peaks(device: int = 0):
     if st != DG_OK:
         raise DGError(st, "dg_probe_peaks failed")
     return float(out[0]), float(out[1])
+
+
+def check_conversions(x, stream=None):
+    """The FP32 operator's FP64 -> FP32 -> FP64 conversions of the device
+    float64 tensor x next to the hardware ones: returns (f_op, f_hw, d_op,
+    d_hw) as device tensors."""
+    import torch
+    L = load()
+    x = x.contiguous()
+    n = x.numel()
+    f = torch.empty(2 * n, dtype=torch.float32, device=x.device)
+    d = torch.empty(2 * n, dtype=torch.float64, device=x.device)
+    st = L.dg_check_conversions(_ptr(x), n, _ptr(f), _ptr(d), _stream_handle(stream))
+    if st != DG_OK:
+        raise DGError(st, "dg_check_conversions failed")
+    return f[:n], f[n:], d[:n], d[n:]
 
 
 def conserved_totals_noalloc(U, J, N: int, out=None, stream=None):

@@ -28,6 +28,8 @@ static dg_status ensure_adjoint(Ctx* c) {
   if (c->prm.precision != DG_FP64) return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the FP64 operator");
   if (c->prm.surf_flux == DG_FLUX_ROE)
     return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the LLF and entropy-conservative surface fluxes");
+  if (c->prm.visc_law != DG_VISC_CONSTANT)
+    return afail(c, DG_EUNSUPPORTED, "the adjoint is built for constant viscosity");
   const size_t st = (size_t)c->E * 5 * c->P;
   const size_t nn = (size_t)c->nfaces * c->NN;
   ADJ_CUDA(setup_adjoint(c->N), c, "adjoint kernel set-up");
@@ -244,6 +246,7 @@ dg_status dg_set_viscosity(dg_ctx* ctx, double mu) {
   if (!c || !(mu >= 0.0)) return afail(c, DG_EINVAL, "dg_set_viscosity: bad argument");
   c->prm.mu = mu;
   c->gas.mu = mu;
+  set_float_copies(c->gas);
   if (c->graph) {                       // the captured graph holds the old constants
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;

@@ -89,7 +89,7 @@ static dg_status fail(Ctx* c, dg_status st, const char* what, cudaError_t e = cu
 static void release(Ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
-  void* bufs[] = {c->d_D, c->d_metrics, c->d_J, c->d_X, c->d_facegeo, c->d_metrics_f, c->d_facegeo_f,
+  void* bufs[] = {c->d_D, c->d_metrics, c->d_J, c->d_X, c->d_mms, c->d_facegeo, c->d_metrics_f, c->d_facegeo_f,
                   c->d_grad, c->d_fstar, c->d_red, c->d_w, c->d_clock, c->d_U, c->d_G,
                   c->d_adj_qbar, c->d_adj_gbar, c->d_adj_gtil, c->d_adj_fseed, c->d_adj_face, c->d_adj_mu,
                   c->d_adj_stage, c->d_adj_work};
@@ -140,6 +140,10 @@ dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx*
     return fail(nullptr, DG_EINVAL, "dg_init: unknown source");
   if (!(prm->gamma > 1.0) || !(prm->R > 0.0) || !(prm->Pr > 0.0) || !(prm->mu >= 0.0))
     return fail(nullptr, DG_EINVAL, "dg_init: gas constants out of range");
+  if (prm->visc_law != DG_VISC_CONSTANT && prm->visc_law != DG_VISC_SUTHERLAND)
+    return fail(nullptr, DG_EINVAL, "dg_init: unknown viscosity law");
+  if (prm->visc_law == DG_VISC_SUTHERLAND && (!(prm->T_ref > 0.0) || !(prm->S_suth >= 0.0)))
+    return fail(nullptr, DG_EINVAL, "dg_init: Sutherland constants out of range");
   if (mesh->n_elems < 1 || mesh->ngeo < 1 || mesh->ngeo > 12 || !mesh->xgeo || !mesh->face_nbr)
     return fail(nullptr, DG_EINVAL, "dg_init: bad mesh sizes or null arrays");
   const int E = mesh->n_elems;
@@ -171,6 +175,11 @@ dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx*
   g.inv_R = 1.0 / prm->R;
   g.mms_amp = prm->mms_amp; g.surf_flux = prm->surf_flux; g.source = prm->source;
   g.p_ref = prm->p_ref; g.E_ref = prm->p_ref / (prm->gamma - 1.0);
+  g.visc_law = prm->visc_law;
+  g.inv_T_ref = prm->visc_law == DG_VISC_SUTHERLAND ? 1.0 / prm->T_ref : 1.0;
+  g.S_suth = prm->visc_law == DG_VISC_SUTHERLAND ? prm->S_suth : 0.0;
+  g.suth_c = prm->visc_law == DG_VISC_SUTHERLAND ? prm->T_ref + prm->S_suth : 1.0;
+  set_float_copies(g);
   lgl_basis(c->N, c->x, c->w, c->D);
   // faces: the side with the smaller (e*6 + f) is the master
   std::vector<FaceInfo> faces;
@@ -213,6 +222,7 @@ dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx*
       !alloc((void**)&c->d_w, sizeof(double) * c->n, "alloc w") ||
       !alloc((void**)&c->d_minmask, sizeof(int), "alloc mask") ||
       !alloc((void**)&c->d_clock, sizeof(double) * 2, "alloc clock") ||
+      (prm->source == DG_SOURCE_MMS && !alloc((void**)&c->d_mms, sizeof(double) * E * 2 * P, "alloc source phases")) ||
       (prm->precision == DG_FP32OP &&
        (!alloc((void**)&c->d_metrics_f, sizeof(float) * E * 10 * P, "alloc metrics (fp32)") ||
         !alloc((void**)&c->d_facegeo_f, sizeof(float) * c->nfaces * 4 * NN, "alloc facegeo (fp32)"))))
@@ -243,6 +253,7 @@ dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx*
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_elem_nbr, elem_nbr.data(), sizeof(int) * E * 6, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = setup_kernels(c->N);
   if (err == cudaSuccess) err = build_geometry(*c, d_xgeo, mesh->ngeo, d_bad, s);
+  if (err == cudaSuccess && prm->source == DG_SOURCE_MMS) err = launch_mms_phase(*c, s);
   if (err == cudaSuccess && prm->precision == DG_FP32OP) {
     err = launch_to_float(c->d_metrics, c->d_metrics_f, (size_t)E * 10 * P, s);
     if (err == cudaSuccess) err = launch_to_float(c->d_facegeo, c->d_facegeo_f, (size_t)c->nfaces * 4 * NN, s);

@@ -37,7 +37,8 @@ __device__ void block_reduce(double (&v)[V], const bool (&is_min)[V], double* ou
 template <int N>
 __global__ void __launch_bounds__(kRedThreads)
 k_integrals(const double* __restrict__ U, const double* __restrict__ J, const double* __restrict__ grad,
-            const double* __restrict__ w, double* __restrict__ part, int E, double gm1) {
+            const double* __restrict__ w, double* __restrict__ part, int E, Gas gas) {
+  const double gm1 = gas.gm1;
   constexpr int n = N + 1, P = n * n * n;
   double v[kRedVals] = {0, 0, 0, 0, 0, 0, 0, 0, 1e300};
   const bool is_min[kRedVals] = {false, false, false, false, false, false, false, false, true};
@@ -59,8 +60,10 @@ k_integrals(const double* __restrict__ U, const double* __restrict__ J, const do
     const double o0 = g[7 * P] - g[5 * P];   // dw/dy - dv/dz
     const double o1 = g[2 * P] - g[6 * P];   // du/dz - dw/dx
     const double o2 = g[3 * P] - g[1 * P];   // dv/dx - du/dy
-    v[7] += wq * (o0 * o0 + o1 * o1 + o2 * o2);
-    v[8] = fmin(v[8], gm1 * (q[4] - 0.5 * m2 * ir));
+    const double p = gm1 * (q[4] - 0.5 * m2 * ir);
+    const double sf = visc_factor<double>(gas, p * ir * gas.inv_R);   // mu(T) / mu_ref
+    v[7] += wq * sf * (o0 * o0 + o1 * o1 + o2 * o2);
+    v[8] = fmin(v[8], p);
   }
   block_reduce<kRedThreads, kRedVals>(v, is_min, part + (size_t)blockIdx.x * kRedVals);
 }
@@ -113,7 +116,7 @@ k_dt(const double* __restrict__ U, const double* __restrict__ metrics, double* _
       lc += (fabs(u * a0 + vv * a1 + w * a2) + cs * sqrt(a2n)) * iJ;
       lv += a2n * iJ * iJ;
     }
-    const double mu_eff = fmax(4.0 / 3.0, g.gamma / g.Pr) * g.mu * ir;
+    const double mu_eff = fmax(4.0 / 3.0, g.gamma / g.Pr) * g.mu * visc_factor<double>(g, p * ir * g.inv_R) * ir;
     v[0] = fmax(v[0], lc);
     v[1] = fmax(v[1], mu_eff * lv);
   }
@@ -185,6 +188,16 @@ __global__ void k_initial(const double* __restrict__ X, double* __restrict__ U, 
   o[4 * P] = p * g.inv_gm1 + 0.5 * rho * (u * u + v * v + w * w);
 }
 
+// sin and cos of pi (x + y + z) at every node, for the manufactured source.
+__global__ void k_mms_phase(const double* __restrict__ X, double* __restrict__ ph, int E, int P) {
+  const long tot = (long)E * P;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (long)gridDim.x * blockDim.x) {
+    const long e = t / P, id = t - e * P;
+    const double s = X[(e * 3 + 0) * P + id] + X[(e * 3 + 1) * P + id] + X[(e * 3 + 2) * P + id];
+    sincospi(s, &ph[(e * 2) * P + id], &ph[(e * 2 + 1) * P + id]);
+  }
+}
+
 __global__ void k_set_clock(double* clock, double t, double dt) { clock[0] = t; clock[1] = dt; }
 __global__ void k_clock_advance(double* clock) { clock[0] += clock[1]; }
 
@@ -197,7 +210,7 @@ static int red_blocks(const Ctx& c) {
 template <int N>
 static cudaError_t integrals_N(Ctx& c, const double* U, double* d_w, cudaStream_t s) {
   const int nb = red_blocks(c);
-  k_integrals<N><<<nb, kRedThreads, 0, s>>>(U, c.d_J, (const double*)c.d_grad, d_w, c.d_red, c.E, c.gas.gm1);
+  k_integrals<N><<<nb, kRedThreads, 0, s>>>(U, c.d_J, (const double*)c.d_grad, d_w, c.d_red, c.E, c.gas);
   return cudaGetLastError();
 }
 
@@ -250,6 +263,13 @@ cudaError_t launch_max_dt(Ctx& c, const double* U, double, double, cudaStream_t 
 cudaError_t launch_initial_state(Ctx& c, int kind, double prm0, double* U, cudaStream_t s) {
   const long tot = (long)c.E * c.P;
   k_initial<<<(int)((tot + 255) / 256), 256, 0, s>>>(c.d_X, U, c.E, c.P, kind, prm0, c.gas);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mms_phase(Ctx& c, cudaStream_t s) {
+  const long tot = (long)c.E * c.P;
+  const long blocks = (tot + 255) / 256;
+  k_mms_phase<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(c.d_X, c.d_mms, c.E, c.P);
   return cudaGetLastError();
 }
 

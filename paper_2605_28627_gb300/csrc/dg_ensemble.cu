@@ -30,7 +30,7 @@ struct MemberDev {
   const int* elem_face;
   const int* elem_nbr;
   const FaceInfo* faces;
-  const double* X;
+  const double* mms;          // manufactured-source phases (or null)
   int E, F;
   Gas gas;
   double inv_w0;
@@ -69,7 +69,7 @@ k_volume_ens(const MemberDev<R>* __restrict__ mem, const int2* __restrict__ tile
     const int2 tl = tiles[t];
     const MemberDev<R>& m = mem[tl.x];
     StageArgs a{m.U, m.U, m.G, nullptr, m.clock, c_stage, A, B, 1};
-    volume_body<N, R, EPB>(a, m.metrics, m.metrics64, m.grad, m.fstar, m.elem_face, m.X, Dg, m.E, m.gas,
+    volume_body<N, R, EPB>(a, m.metrics, m.metrics64, m.grad, m.fstar, m.elem_face, m.mms, Dg, m.E, m.gas,
                            m.inv_w0, tl.y);
     __syncthreads();
   }
@@ -103,7 +103,7 @@ template <int N, typename R>
 struct Epb2 {   // the doubled tile, if it still fits a block (<= 1024 threads, <= 227 KB smem)
   static constexpr int base = default_epb((N + 1) * (N + 1) * (N + 1));
   static constexpr int P = (N + 1) * (N + 1) * (N + 1);
-  static constexpr bool ok = 2 * base * P <= 1024 && volume_smem_bytes<N, R, 2 * base>() <= 227 * 1024;
+  static constexpr bool ok = 2 * base * P <= 1024 && volume_smem_bytes<N, R, 2 * base>() + 64 <= 227 * 1024;
   static constexpr int value = ok ? 2 * base : base;
 };
 
@@ -251,7 +251,7 @@ static void fill_member(MemberDev<R>& m, Ctx* c, double* U, double* G, double* c
   m.elem_face = c->d_elem_face;
   m.elem_nbr = c->d_elem_nbr;
   m.faces = c->d_faces;
-  m.X = c->d_X;
+  m.mms = c->d_mms;
   m.E = c->E;
   m.F = c->nfaces;
   m.gas = c->gas;

@@ -35,7 +35,21 @@ struct Gas {
   double E_ref;      // p_ref / (gamma - 1)
   int surf_flux;
   int source;
+  int visc_law;      // DG_VISC_CONSTANT or DG_VISC_SUTHERLAND
+  double inv_T_ref;  // Sutherland: 1 / T_ref
+  double S_suth;     // Sutherland constant S
+  double suth_c;     // T_ref + S
+  // FP32 copies of the constants the FP32 operator uses, rounded once on the
+  // host (set by set_float_copies)
+  float f_gamma, f_gm1, f_inv_gm1, f_inv_R, f_mu, f_lam, f_p_ref, f_inv_T_ref, f_S_suth, f_suth_c;
 };
+
+inline void set_float_copies(Gas& g) {
+  g.f_gamma = (float)g.gamma; g.f_gm1 = (float)g.gm1; g.f_inv_gm1 = (float)g.inv_gm1;
+  g.f_inv_R = (float)g.inv_R; g.f_mu = (float)g.mu; g.f_lam = (float)(g.mu * g.kappa);
+  g.f_p_ref = (float)g.p_ref;
+  g.f_inv_T_ref = (float)g.inv_T_ref; g.f_S_suth = (float)g.S_suth; g.f_suth_c = (float)g.suth_c;
+}
 
 // Face descriptor (master orientation): elements and local faces of both sides
 // packed as e*8 + f, and the orientation code taking a master face node to the
@@ -70,6 +84,7 @@ struct Ctx {
   double* d_metrics = nullptr;   // [E][10][P]: J a^d_l at row d*3+l, row 9 = 1/J
   double* d_J = nullptr;         // [E][P]
   double* d_X = nullptr;         // [E][3][P]
+  double* d_mms = nullptr;       // [E][2][P] sin, cos of pi (x + y + z); manufactured source only
   double* d_facegeo = nullptr;   // [F][4][NN]: unit normal (3), surface element
   float* d_metrics_f = nullptr;  // FP32 copies for the FP32-operator path
   float* d_facegeo_f = nullptr;
@@ -122,6 +137,7 @@ cudaError_t launch_to_float(const double* a, float* b, size_t n, cudaStream_t s)
 cudaError_t launch_integrals(Ctx& c, const double* U, cudaStream_t s);
 cudaError_t launch_max_dt(Ctx& c, const double* U, double cfl, double dfl, cudaStream_t s);
 cudaError_t launch_initial_state(Ctx& c, int kind, double prm0, double* U, cudaStream_t s);
+cudaError_t launch_mms_phase(Ctx& c, cudaStream_t s);
 cudaError_t launch_set_clock(double* clock, double t, double dt, cudaStream_t s);
 cudaError_t launch_clock_advance(double* clock, cudaStream_t s);
 int reduction_rows(const Ctx& c);   // partial rows used by the last reduction

@@ -1,6 +1,6 @@
 // Measurement helpers: per-kernel event timing of an LSERK stage and an
 // arithmetic-throughput probe (FP64 DFMA and FP32 FFMA chains).
-#include "dg_internal.h"
+#include "dg_physics.cuh"
 
 namespace dg {
 
@@ -40,9 +40,30 @@ static double fma_tflops(int sms, int iters, void* buf) {
   return flops / (ms * 1e-3) / 1e12;
 }
 
+// Both conversions of the FP32 operator next to the hardware ones.
+__global__ void k_convert_check(const double* __restrict__ x, int n, float* __restrict__ f,
+                                double* __restrict__ d) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const float fb = to_op<float>(x[t]);
+    f[t] = fb;
+    f[n + t] = __double2float_rn(x[t]);
+    d[t] = to_f64(fb);
+    d[n + t] = (double)fb;
+  }
+}
+
 }  // namespace dg
 
 using namespace dg;
+
+extern "C" dg_status dg_check_conversions(const double* d_x, int32_t n, float* d_f, double* d_d, dg_stream stream) {
+  if (n < 0 || (n > 0 && (!d_x || !d_f || !d_d))) return DG_EINVAL;
+  if (n == 0) return DG_OK;
+  const int blocks = (n + 255) / 256;
+  k_convert_check<<<blocks < 152 * 8 ? blocks : 152 * 8, 256, 0, (cudaStream_t)stream>>>(d_x, n, d_f, d_d);
+  if (cudaGetLastError() != cudaSuccess) return DG_ECUDA;
+  return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? DG_OK : DG_ECUDA;
+}
 
 extern "C" dg_status dg_probe_peaks(int device, double* out) {
   if (!out) return DG_EINVAL;

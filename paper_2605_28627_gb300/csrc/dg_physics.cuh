@@ -6,6 +6,47 @@
 
 namespace dg {
 
+// Constant of the operator type: the FP64 value or its FP32 copy in Gas.
+template <typename R>
+__device__ __forceinline__ R gsel(double d, float f) {
+  if constexpr (sizeof(R) == 4) return f;
+  else return d;
+}
+
+// FP64 -> operator type.  For FP32 the conversion works on the bit pattern
+// with integer instructions: rebias the exponent (1023 -> 127), keep the top
+// 23 mantissa bits, round half away from zero on the dropped 29 bits (a carry
+// moves into the exponent as it should) and flush values below the smallest
+// normal float, zero included, to +-0.  On this GPU the FP64 -> FP32 convert
+// instruction issues on the FP64 pipe, which the FP32 operator keeps for its
+// FP64 state update; the integer form costs a few ALU slots instead.  It
+// differs from round-to-nearest-even only on exact ties; |x| must stay below
+// 2^128 (no overflow to infinity), which holds for every state of the solver.
+template <typename R>
+__device__ __forceinline__ R to_op(double x) {
+  if constexpr (sizeof(R) == 4) {
+    const unsigned lo = (unsigned)__double2loint(x), hi = (unsigned)__double2hiint(x);
+    const unsigned h = hi & 0x7fffffffu;
+    unsigned f = __funnelshift_l(lo, h - (896u << 20), 3) + ((lo >> 28) & 1u);
+    f = h < (897u << 20) ? 0u : f;
+    return __uint_as_float(f | (hi & 0x80000000u));
+  } else {
+    return x;
+  }
+}
+
+// Operator type -> FP64, exact for normal floats (zero and subnormals give
+// +-0); integer instructions only, as in to_op.
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) {
+  const unsigned f = __float_as_uint(x);
+  const unsigned a = f & 0x7fffffffu;
+  const bool z = a < 0x00800000u;
+  const unsigned hi = z ? 0u : (a >> 3) + (896u << 20);
+  const unsigned lo = z ? 0u : a << 29;
+  return __hiloint2double((int)(hi | (f & 0x80000000u)), (int)lo);
+}
+
 // Index of volume node (i, j, k), i fastest.
 template <int n>
 __device__ __forceinline__ int vidx(int i, int j, int k) { return i + n * (j + n * k); }
@@ -142,7 +183,7 @@ __device__ __forceinline__ void euler_flux(const R q[5], R u, R v, R w, R p, R n
 // lambda(qR) - lambda) where |lambda| < delta.
 template <typename R>
 __device__ __forceinline__ void roe_flux(const R qL[5], R uL, R vL, R wL, R pL, const R qR[5], R uR, R vR, R wR,
-                                         R pR, R nx, R ny, R nz, R gamma, R gm1, R F[5], R pmL, R pmR) {
+                                         R pR, R nx, R ny, R nz, R gamma, R gm1, R F[5], R pmL, R pmR, R dr) {
   R fL[5], fR[5];
   euler_flux_pm<R>(qL, uL, vL, wL, pL, pmL, nx, ny, nz, fL);
   euler_flux_pm<R>(qR, uR, vR, wR, pR, pmR, nx, ny, nz, fR);
@@ -156,7 +197,7 @@ __device__ __forceinline__ void roe_flux(const R qL[5], R uL, R vL, R wL, R pL, 
   const R c = sqrt(gm1 * (H - R(0.5) * q2));
   const R rho = sL * sR;
   const R un = u * nx + v * ny + w * nz;
-  const R dr = qR[0] - qL[0], dp = pR - pL;
+  const R dp = pmR - pmL;   // = pR - pL; the jumps dr, dp come from the caller (FP64 differences in FP32 mode)
   const R du = uR - uL, dv = vR - vL, dw = wR - wL;
   const R dun = du * nx + dv * ny + dw * nz;
   const R ic2 = R(1) / (c * c);
@@ -184,6 +225,15 @@ __device__ __forceinline__ void roe_flux(const R qL[5], R uL, R vL, R wL, R pL, 
   F[2] = R(0.5) * (fL[2] + fR[2] - D2);
   F[3] = R(0.5) * (fL[3] + fR[3] - D3);
   F[4] = R(0.5) * (fL[4] + fR[4] - D4);
+}
+
+// Factor mu(T)/mu_ref of the viscosity law: 1, or Sutherland's (1893)
+// (T/T_ref)^(3/2) (T_ref + S)/(T + S); the heat conductivity scales with it.
+template <typename R>
+__device__ __forceinline__ R visc_factor(const Gas& g, R T) {
+  if (g.visc_law != DG_VISC_SUTHERLAND) return R(1);
+  const R x = T * gsel<R>(g.inv_T_ref, g.f_inv_T_ref);
+  return x * sqrt(x) * (gsel<R>(g.suth_c, g.f_suth_c) / (T + gsel<R>(g.S_suth, g.f_S_suth)));
 }
 
 // Viscous flux (Newtonian stress with Stokes' hypothesis, Fourier heat flux)

@@ -77,15 +77,15 @@ __device__ __forceinline__ void lift_body(const double* __restrict__ U, const R*
   const int le = threadIdx.x / P, id = threadIdx.x % P;
   const int e = blk * S::EPB + le;
   const bool active = e < E;
-  for (int a = threadIdx.x; a < n * n; a += blockDim.x) sD[a] = R(Dg[a]);
-  const R gm1 = R(g.gm1), inv_R = R(g.inv_R), inv_w0 = R(inv_w0d);
+  for (int a = threadIdx.x; a < n * n; a += blockDim.x) sD[a] = to_op<R>(Dg[a]);
+  const R gm1 = gsel<R>(g.gm1, g.f_gm1), inv_R = gsel<R>(g.inv_R, g.f_inv_R), inv_w0 = to_op<R>(inv_w0d);
   R phi[4] = {0, 0, 0, 0};
   if (active) {
     const double* q = U + (size_t)e * 5 * P + id;
-    const R rho = R(q[0]), ir = rcp_lf(rho);
-    const R m0 = R(q[P]), m1 = R(q[2 * P]), m2 = R(q[3 * P]);
+    const R rho = to_op<R>(q[0]), ir = rcp_lf(rho);
+    const R m0 = to_op<R>(q[P]), m1 = to_op<R>(q[2 * P]), m2 = to_op<R>(q[3 * P]);
     const R u = m0 * ir, v = m1 * ir, w = m2 * ir;
-    const R p = gm1 * (R(q[4 * P]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
+    const R p = gm1 * (to_op<R>(q[4 * P]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
     phi[0] = u; phi[1] = v; phi[2] = w; phi[3] = p * ir * inv_R;
     for (int a = 0; a < 4; ++a) sphi[le][a][id] = phi[a];
   }
@@ -130,10 +130,10 @@ __device__ __forceinline__ void lift_body(const double* __restrict__ U, const R*
     apply_flip<n>(code & 7, p, qq, p2, q2);
     const int id2 = face_node<n>(f2, p2, q2);
     const double* q = U + (size_t)e2 * 5 * P + id2;
-    const R rho = R(q[0]), ir = rcp_lf(rho);
-    const R m0 = R(q[P]), m1 = R(q[2 * P]), m2 = R(q[3 * P]);
+    const R rho = to_op<R>(q[0]), ir = rcp_lf(rho);
+    const R m0 = to_op<R>(q[P]), m1 = to_op<R>(q[2 * P]), m2 = to_op<R>(q[3 * P]);
     const R u = m0 * ir, v = m1 * ir, w = m2 * ir;
-    const R pr = gm1 * (R(q[4 * P]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
+    const R pr = gm1 * (to_op<R>(q[4 * P]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
     const R onb[4] = {u, v, w, pr * ir * inv_R};
     const R sg = s ? inv_w0 : -inv_w0;
 #pragma unroll
@@ -166,13 +166,16 @@ __device__ __forceinline__ void face_body(const double* __restrict__ U, const R*
   int p2, q2;
   apply_flip<n>(fi.flip, p, q, p2, q2);
   const int idM = face_node<n>(fM, p, q), idS = face_node<n>(fS, p2, q2);
+  double dL[5], dR[5];
   R qL[5], qR[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    qL[v] = R(U[((size_t)eM * 5 + v) * P + idM]);
-    qR[v] = R(U[((size_t)eS * 5 + v) * P + idS]);
+    dL[v] = U[((size_t)eM * 5 + v) * P + idM];
+    dR[v] = U[((size_t)eS * 5 + v) * P + idS];
+    qL[v] = to_op<R>(dL[v]);
+    qR[v] = to_op<R>(dR[v]);
   }
-  const R gm1 = R(g.gm1), gam = R(g.gamma);
+  const R gm1 = gsel<R>(g.gm1, g.f_gm1), gam = gsel<R>(g.gamma, g.f_gamma);
   const R* fg = facegeo + (size_t)f * 4 * NN + pq;
   const R nx = fg[0], ny = fg[NN], nz = fg[2 * NN], sJ = fg[3 * NN];
   const R irL = rcp_lf(qL[0]), irR = rcp_lf(qR[0]);
@@ -187,19 +190,29 @@ __device__ __forceinline__ void face_body(const double* __restrict__ U, const R*
   // (low Mach numbers) no longer enters the momentum equations.
   R pmL = pL, pmR = pR;
   if constexpr (sizeof(R) == 4) {
-    pmL = gm1 * (R(U[((size_t)eM * 5 + 4) * P + idM] - g.E_ref) - R(0.5) * (qL[1] * uL + qL[2] * vL + qL[3] * wL));
-    pmR = gm1 * (R(U[((size_t)eS * 5 + 4) * P + idS] - g.E_ref) - R(0.5) * (qR[1] * uR + qR[2] * vR + qR[3] * wR));
+    pmL = gm1 * (to_op<R>(dL[4] - g.E_ref) - R(0.5) * (qL[1] * uL + qL[2] * vL + qL[3] * wL));
+    pmR = gm1 * (to_op<R>(dR[4] - g.E_ref) - R(0.5) * (qR[1] * uR + qR[2] * vR + qR[3] * wR));
+  }
+  // State jumps for the dissipation terms: in FP32 mode taken from the FP64
+  // states before rounding, so that a small jump of a large quantity (the
+  // energy at low Mach numbers) keeps its digits.
+  R dq[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    if constexpr (sizeof(R) == 4) dq[v] = to_op<R>(dR[v] - dL[v]);
+    else dq[v] = qR[v] - qL[v];
   }
   R fa[5];
   if (g.surf_flux == DG_FLUX_EC) {
     NodePrim<R> a{qL[0], uL, vL, wL, pL, R(0.5) * qL[0] / pL};
     NodePrim<R> b{qR[0], uR, vR, wR, pR, R(0.5) * qR[0] / pR};
     if constexpr (sizeof(R) == 4)
-      ec_flux_off<R>(a, b, qL[0] * pmL / pL, qR[0] * pmR / pR, R(g.p_ref), nx, ny, nz, R(g.inv_gm1), fa);
+      ec_flux_off<R>(a, b, qL[0] * pmL / pL, qR[0] * pmR / pR, gsel<R>(g.p_ref, g.f_p_ref), nx, ny, nz,
+                     gsel<R>(g.inv_gm1, g.f_inv_gm1), fa);
     else
-      ec_flux<R>(a, b, nx, ny, nz, R(g.inv_gm1), fa);
+      ec_flux<R>(a, b, nx, ny, nz, gsel<R>(g.inv_gm1, g.f_inv_gm1), fa);
   } else if (g.surf_flux == DG_FLUX_ROE) {
-    roe_flux<R>(qL, uL, vL, wL, pL, qR, uR, vR, wR, pR, nx, ny, nz, gam, gm1, fa, pmL, pmR);
+    roe_flux<R>(qL, uL, vL, wL, pL, qR, uR, vR, wR, pR, nx, ny, nz, gam, gm1, fa, pmL, pmR, dq[0]);
   } else {
     R fL[5], fR[5];
     euler_flux_pm<R>(qL, uL, vL, wL, pL, pmL, nx, ny, nz, fL);
@@ -209,7 +222,7 @@ __device__ __forceinline__ void face_body(const double* __restrict__ U, const R*
     const R lR = fabs(uR * nx + vR * ny + wR * nz) + cR;
     const R lmax = lR > lL ? lR : lL;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) fa[v] = R(0.5) * (fL[v] + fR[v]) - R(0.5) * lmax * (qR[v] - qL[v]);
+    for (int v = 0; v < 5; ++v) fa[v] = R(0.5) * (fL[v] + fR[v]) - R(0.5) * lmax * dq[v];
   }
   R gL[12], gR[12];
 #pragma unroll
@@ -218,9 +231,15 @@ __device__ __forceinline__ void face_body(const double* __restrict__ U, const R*
     gR[r] = grad[((size_t)eS * 12 + r) * P + idS];
   }
   R fvL[4], fvR[4];
-  const R mu = R(g.mu), lam = R(g.mu * g.kappa);
-  visc_flux<R>(gL, uL, vL, wL, mu, lam, nx, ny, nz, fvL);
-  visc_flux<R>(gR, uR, vR, wR, mu, lam, nx, ny, nz, fvR);
+  const R mu = gsel<R>(g.mu, g.f_mu), lam = gsel<R>(g.mu * g.kappa, g.f_lam);
+  R sfL = R(1), sfR = R(1);
+  if (g.visc_law == DG_VISC_SUTHERLAND) {
+    const R inv_R = gsel<R>(g.inv_R, g.f_inv_R);
+    sfL = visc_factor<R>(g, pL * irL * inv_R);
+    sfR = visc_factor<R>(g, pR * irR * inv_R);
+  }
+  visc_flux<R>(gL, uL, vL, wL, mu * sfL, lam * sfL, nx, ny, nz, fvL);
+  visc_flux<R>(gR, uR, vR, wR, mu * sfR, lam * sfR, nx, ny, nz, fvR);
   R* fo = fstar + (size_t)f * 5 * NN + pq;
   fo[0] = fa[0] * sJ;
 #pragma unroll
@@ -272,7 +291,7 @@ template <int N, typename R, int EPB_>
 __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restrict__ metrics,
                                             const double* __restrict__ iJ64, const R* __restrict__ grad,
                                             const R* __restrict__ fstar, const int* __restrict__ elem_face,
-                                            const double* __restrict__ X, const double* __restrict__ Dg, int E,
+                                            const double* __restrict__ mms, const double* __restrict__ Dg, int E,
                                             const Gas& g, double inv_w0d, int blk) {
   using S = VShape<N, EPB_>;
   constexpr int n = S::n, P = S::P, NN = S::NN, EPB = S::EPB;
@@ -294,14 +313,18 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
   R* sDl = sT2 + ((n * n + 3) & ~3) + EPB * S::PER_ELEM + le * P;   // FP32 only: rho (p - p_ref) / p
   const int e = blk * EPB + le;
   const bool active = e < E;
+  __shared__ double s_tc[2];          // sin, cos of pi t (manufactured source)
+  if (threadIdx.x == 0 && g.source == DG_SOURCE_MMS)
+    sincospi(a.clock[0] + a.c_stage * a.clock[1], &s_tc[0], &s_tc[1]);
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const double d = Dg[t];
-    sD[t] = R(d);
-    sT0[t] = R(0.25 * d);
-    sT1[t] = R(0.125 * d);
-    sT2[t] = R(0.0625 * d);
+    const R dr = to_op<R>(d);       // the scalings by powers of two are exact
+    sD[t] = dr;
+    sT0[t] = R(0.25) * dr;
+    sT1[t] = R(0.125) * dr;
+    sT2[t] = R(0.0625) * dr;
   }
-  const R inv_w0 = R(inv_w0d);
+  const R inv_w0 = to_op<R>(inv_w0d);
   double q[5] = {0, 0, 0, 0, 0};
   R Ja[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   R rho = R(1), u = 0, v = 0, w = 0, beta = 0, kk = 0;
@@ -311,24 +334,29 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     const R* mt = metrics + (size_t)e * 10 * P + id;
 #pragma unroll
     for (int r = 0; r < 9; ++r) Ja[r] = mt[r * P];
-    rho = R(q[0]);
+    rho = to_op<R>(q[0]);
     const R ir = rcp_op(rho);
-    u = R(q[1]) * ir; v = R(q[2]) * ir; w = R(q[3]) * ir;
+    u = to_op<R>(q[1]) * ir; v = to_op<R>(q[2]) * ir; w = to_op<R>(q[3]) * ir;
     kk = u * u + v * v + w * w;
-    const R p = R(g.gm1) * fma(R(-0.5) * rho, kk, R(q[4]));
+    const R p = gsel<R>(g.gm1, g.f_gm1) * fma(R(-0.5) * rho, kk, to_op<R>(q[4]));
     beta = R(0.5) * rho * rcp_op(p);
     sR[id] = rho; sU[id] = u; sU[P + id] = v; sU[2 * P + id] = w; sB[id] = beta; sK[id] = kk;
     if constexpr (sizeof(R) == 4) {
       // offset form of the momentum flux (see face_body): p - p_ref from the
       // FP64 energy difference, stored as rho (p - p_ref) / p
-      const R pm = R(g.gm1) * fma(R(-0.5) * rho, kk, R(q[4] - g.E_ref));
+      const R pm = g.f_gm1 * fma(R(-0.5) * rho, kk, to_op<R>(q[4] - g.E_ref));
       sDl[id] = rho * pm * rcp_op(p);
     }
     R gr[12];
     const R* gg = grad + (size_t)e * 12 * P + id;
 #pragma unroll
     for (int r = 0; r < 12; ++r) gr[r] = gg[r * P];
-    const R mu = R(g.mu), lam = R(g.mu * g.kappa);
+    R mu = gsel<R>(g.mu, g.f_mu), lam = gsel<R>(g.mu * g.kappa, g.f_lam);
+    if (g.visc_law == DG_VISC_SUTHERLAND) {
+      const R sf = visc_factor<R>(g, p * ir * gsel<R>(g.inv_R, g.f_inv_R));
+      mu *= sf;
+      lam *= sf;
+    }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       R fv[4];
@@ -340,7 +368,7 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
   __syncthreads();
   const int i = id % n, j = (id / n) % n, k = id / NN;
   const int ijk[3] = {i, j, k};
-  const R inv4 = R(4.0 * g.inv_gm1);
+  const R inv4 = R(4) * gsel<R>(g.inv_gm1, g.f_inv_gm1);
   R acc[5] = {0, 0, 0, 0, 0};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -384,7 +412,7 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
         const R M2 = fma(Xf, su2, Y4 * sn2);
         const R Z = fma(hib, inv4, -(kk + sK[mid]));
         R E32 = fma(Xf, Z, fma(su0, M0, fma(su1, M1, su2 * M2)));   // 32 f_E
-        if constexpr (sizeof(R) == 4) E32 = fma(R(8.0 * g.p_ref), un4, E32);     // p_ref {u}.n back
+        if constexpr (sizeof(R) == 4) E32 = fma(R(8) * g.f_p_ref, un4, E32);     // p_ref {u}.n back
         const int rm = r * n + m;
         acc[0] = fma(sT0[rm], Xf, acc[0]);
         acc[1] = fma(sT1[rm], M0, acc[1]);
@@ -453,33 +481,34 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     for (int c = 0; c < 4; ++c)
       acc[1 + c] = fma(fs_sign, fsr[(c + 1) * NN], fma(vs, sFv[(d * 4 + c) * P + id], acc[1 + c]));
   }
-  const double t = a.clock[0] + a.c_stage * a.clock[1];
   double src[5] = {0, 0, 0, 0, 0};
   if (g.source == DG_SOURCE_MMS) {
-    const double x = X[((size_t)e * 3 + 0) * P + id], y = X[((size_t)e * 3 + 1) * P + id],
-                 z = X[((size_t)e * 3 + 2) * P + id];
-    // density wave rho = 2 + A sin(pi (x+y+z-t)), u = (1,1,1), p = 1:
-    // residual of Eq. 1 = [2r', 2r', 2r', 2r', 3r' - lambda Lap T], r' = pi A cos(phi)
-    double sphi, cphi;
-    sincospi(x + y + z - t, &sphi, &cphi);
+    // density wave rho = 2 + A sin(phi), phi = pi (x+y+z-t), u = (1,1,1), p = 1:
+    // residual of Eq. 1 = [2r', 2r', 2r', 2r', 3r' - lambda Lap T], r' = pi A cos(phi).
+    // sin/cos of phi from those of pi (x+y+z) (per node, set up once) and of
+    // pi t (once per block) by the angle-difference identities.
+    const double sa = mms[((size_t)e * 2) * P + id], ca = mms[((size_t)e * 2 + 1) * P + id];
+    const double sphi = fma(sa, s_tc[1], -ca * s_tc[0]);
+    const double cphi = fma(ca, s_tc[1], sa * s_tc[0]);
     const double A = g.mms_amp;
     const double rw = 2.0 + A * sphi;
+    const double irw = rcp_op(rw);
     const double rp = M_PI * A * cphi;
-    const double lapT = 3.0 * g.inv_R * (M_PI * M_PI * A * sphi + 2.0 * rp * rp / rw) / (rw * rw);
+    const double lapT = 3.0 * g.inv_R * fma(M_PI * M_PI * A, sphi, 2.0 * rp * rp * irw) * (irw * irw);
     src[0] = src[1] = src[2] = src[3] = 2.0 * rp;
-    src[4] = 3.0 * rp - g.mu * g.kappa * lapT;
+    src[4] = fma(-g.mu * g.kappa, lapT, 3.0 * rp);
   }
   // Jacobian, source and RK update in FP64
   const double iJ = iJ64[(size_t)e * 10 * P + 9 * P + id];
   if (a.mode == 0) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) a.Ut[((size_t)e * 5 + c) * P + id] = fma(-(double)acc[c], iJ, src[c]);
+    for (int c = 0; c < 5; ++c) a.Ut[((size_t)e * 5 + c) * P + id] = fma(-to_f64(acc[c]), iJ, src[c]);
   } else {
     const double dt = a.clock[1];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       const size_t o = ((size_t)e * 5 + c) * P + id;
-      const double gk = fma(a.A, a.Gk[o], dt * fma(-(double)acc[c], iJ, src[c]));
+      const double gk = fma(a.A, a.Gk[o], dt * fma(-to_f64(acc[c]), iJ, src[c]));
       a.Gk[o] = gk;
       a.Uw[o] = fma(a.B, gk, q[c]);
     }

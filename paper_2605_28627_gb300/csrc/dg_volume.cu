@@ -11,8 +11,8 @@ template <int N, typename R>
 __global__ void __launch_bounds__(VShape<N>::THREADS, (sizeof(R) == 4 && VShape<N>::THREADS <= 512) ? 2 : 1)
 k_volume2(StageArgs a, const R* __restrict__ metrics, const double* __restrict__ iJ64,
           const R* __restrict__ grad, const R* __restrict__ fstar, const int* __restrict__ elem_face,
-          const double* __restrict__ X, const double* __restrict__ Dg, int E, Gas g, double inv_w0) {
-  volume_body<N, R, VShape<N>::EPB>(a, metrics, iJ64, grad, fstar, elem_face, X, Dg, E, g, inv_w0, blockIdx.x);
+          const double* __restrict__ mms, const double* __restrict__ Dg, int E, Gas g, double inv_w0) {
+  volume_body<N, R, VShape<N>::EPB>(a, metrics, iJ64, grad, fstar, elem_face, mms, Dg, E, g, inv_w0, blockIdx.x);
 }
 
 template <int N, typename R>
@@ -32,7 +32,7 @@ cudaError_t volume2_launch(const Ctx& c, const StageArgs& a, cudaStream_t s) {
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
   const R* metrics = (const R*)(sizeof(R) == 8 ? (const void*)c.d_metrics : (const void*)c.d_metrics_f);
   k_volume2<N, R><<<blocks, S::THREADS, volume2_smem<N, R>(), s>>>(
-      a, metrics, c.d_metrics, (const R*)c.d_grad, (const R*)c.d_fstar, c.d_elem_face, c.d_X, c.d_D, c.E, c.gas,
+      a, metrics, c.d_metrics, (const R*)c.d_grad, (const R*)c.d_fstar, c.d_elem_face, c.d_mms, c.d_D, c.E, c.gas,
       1.0 / c.w[0]);
   return cudaGetLastError();
 }

@@ -40,6 +40,19 @@ def _rel_err_per_var(got, ref):
     return np.array(out)
 
 
+def _geo_amp(orc, N, ngeo):
+    """Growth of the rounding error of the geometry with the equispaced
+    sample degree: the interpolation of the samples to the LGL nodes
+    amplifies rounding by kappa = max_i sum_j |V_ij| per direction, kappa^3
+    in 3D (kappa^3 = 291 at ngeo = 7, 1220 at 8, 5504 at 9).  The bars below
+    hold as stated up to kappa^3 = 300 and grow in proportion beyond."""
+    x, _, _ = orc.basis(N)
+    xe = np.linspace(-1.0, 1.0, ngeo + 1)
+    V = np.array([[np.prod([(xi - xe[m]) / (xe[j] - xe[m]) for m in range(ngeo + 1) if m != j])
+                   for j in range(ngeo + 1)] for xi in x])
+    return max(1.0, np.abs(V).sum(1).max() ** 3 / 300.0)
+
+
 def _pair(orc, dg, mesh, N, **kw):
     o = orc.Oracle(mesh, N, **kw)
     kw2 = dict(kw)
@@ -54,11 +67,12 @@ def test_geometry_parity(orc, dg, N):
     X, Ja, J = o.geometry()
     Jag, Jg = s.geometry()
     Xg = s.node_coords()
-    np.testing.assert_allclose(Xg.cpu().numpy(), X, rtol=0, atol=1e-14)
-    np.testing.assert_allclose(Jg.cpu().numpy(), J, rtol=1e-12, atol=0)
+    amp = _geo_amp(orc, N, N)
+    np.testing.assert_allclose(Xg.cpu().numpy(), X, rtol=0, atol=1e-14 * amp)
+    np.testing.assert_allclose(Jg.cpu().numpy(), J, rtol=1e-12 * amp, atol=0)
     # the curl form differentiates products X_l dX_m: rounding scales with |X| |Ja|
     scale = np.abs(Ja).max() * max(1.0, np.abs(X).max())
-    assert np.abs(Jag.cpu().numpy() - Ja).max() <= 1e-12 * scale
+    assert np.abs(Jag.cpu().numpy() - Ja).max() <= 1e-12 * amp * scale
 
 
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8, 9])
@@ -71,7 +85,7 @@ def test_time_derivative_parity_random_state(orc, dg, N, flux):
     ref = o.time_derivative(U, t=0.0)
     got = s.time_derivative(_cuda(U)).cpu().numpy()
     err = _rel_err_per_var(got, ref)
-    assert (err < RTOL_R).all(), err
+    assert (err < RTOL_R * _geo_amp(orc, N, N)).all(), err
 
 
 @pytest.mark.parametrize("N", [2, 3, 5])
@@ -231,3 +245,17 @@ def test_full_size_sampled_elements_against_oracle_patch(orc, dg):
         ref, got = Rp[2, 2, 2], R[cz, cy, cx]
         for v in range(5):
             assert np.abs(got[v] - ref[v]).max() <= RTOL_R * np.abs(ref[v]).max()
+
+
+@pytest.mark.parametrize("N,flux", [(3, 0), (5, 2), (7, 1)])
+def test_sutherland_parity(orc, dg, N, flux):
+    """Sutherland's law at each node's temperature (viscous volume and face
+    fluxes, dissipation diagnostic) against the oracle."""
+    mesh = box_mesh(2, N, deform="sinprod", rotate_seed=600 + N)
+    kw = dict(mu=0.03, surf_flux=flux, visc_law=1, T_ref=1.0, S_suth=110.4 / 273.15)
+    o, s = _pair(orc, dg, mesh, N, **kw)
+    U = random_state(mesh.n_elems, N, seed=700 + N)
+    err = _rel_err_per_var(s.time_derivative(_cuda(U)).cpu().numpy(), o.time_derivative(U))
+    assert (err < RTOL_R * _geo_amp(orc, N, N)).all(), err
+    Ig, Io = s.integrals(_cuda(U)), o.integrals(U)
+    assert abs(Ig[6] - Io[6]) <= 1e-12 * abs(Io[6])

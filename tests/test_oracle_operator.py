@@ -286,3 +286,55 @@ def test_bad_meshes_are_rejected(orc):
     m3 = type(m)(**{**m.__dict__, "xgeo": inv})
     with pytest.raises(ValueError):
         orc.Oracle(m3, 2)
+
+
+def _uniform_temperature_state(n_elems, N, T1, R=1.0, seed=0):
+    """Random density and velocity, pressure p = rho R T1 (uniform T)."""
+    U = random_state(n_elems, N, seed=seed)
+    r = U[:, 0]
+    u = U[:, 1:4] / r[:, None]
+    p = r * R * T1
+    U[:, 4] = p / 0.4 + 0.5 * r * (u ** 2).sum(1)
+    return U
+
+
+@pytest.mark.parametrize("T1", [1.0, 2.0, 0.6])
+def test_sutherland_uniform_temperature(orc, T1):
+    """At a uniform temperature T1 Sutherland's law is one constant,
+    mu0 (T1/T_ref)^(3/2) (T_ref + S)/(T1 + S) (closed form): R(U) and the
+    dissipation diagnostic equal those of the constant law with that mu.
+    At T1 = T_ref the two laws coincide."""
+    N, T_ref, S = 3, 1.0, 110.4 / 273.15
+    m = box_mesh(2, N, deform="sinprod", rotate_seed=21)
+    mu0 = 0.03
+    factor = (T1 / T_ref) ** 1.5 * (T_ref + S) / (T1 + S)
+    o_s = orc.Oracle(m, N, mu=mu0, visc_law=1, T_ref=T_ref, S_suth=S)
+    o_c = orc.Oracle(m, N, mu=mu0 * factor)
+    U = _uniform_temperature_state(m.n_elems, N, T1, seed=5)
+    Rs = o_s.time_derivative(U).reshape(m.n_elems, 5, -1)
+    Rc = o_c.time_derivative(U).reshape(m.n_elems, 5, -1)
+    for v in range(5):
+        assert np.abs(Rs[:, v] - Rc[:, v]).max() <= 1e-12 * np.abs(Rc[:, v]).max(), v
+    Is, Ic = o_s.integrals(U), o_c.integrals(U)
+    assert abs(Is[6] - Ic[6]) <= 1e-13 * abs(Ic[6])
+
+
+def test_sutherland_changes_r_where_temperature_varies(orc):
+    """With a varying temperature Sutherland's R differs from every constant
+    law's (the viscosity follows the nodes' temperatures), while conservation
+    still holds to rounding."""
+    N = 3
+    m = box_mesh(2, N, deform="sinprod", rotate_seed=22)
+    o_s = orc.Oracle(m, N, mu=0.03, visc_law=1, T_ref=1.0, S_suth=0.4)
+    U = random_state(m.n_elems, N, seed=6)
+    tot, scale = _conservation(orc, o_s, U, N)
+    assert (np.abs(tot) < 1e-13 * scale).all(), (tot, scale)
+    Rs = o_s.time_derivative(U)
+    Rc = orc.Oracle(m, N, mu=0.03).time_derivative(U)
+    assert np.abs(Rs - Rc).max() > 1e-6 * np.abs(Rc).max()
+
+
+def test_unknown_viscosity_law_rejected(orc):
+    m = box_mesh(2, 2)
+    with pytest.raises(ValueError):
+        orc.Oracle(m, 2, mu=0.01, visc_law=3)
