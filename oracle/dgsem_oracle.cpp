@@ -35,6 +35,7 @@
 #include <string>
 #include <vector>
 #include <algorithm>
+#include <type_traits>
 
 namespace orc {
 
@@ -185,10 +186,22 @@ struct Params {
   double T_ref, S_suth;   // Sutherland reference temperature and constant
 };
 
+// Legendre-Gauss basis (the alternative node set of Sec. 3.1): the N+1 roots
+// of P_{N+1}, quadrature weights, collocation derivative, the Lagrange basis at
+// the interval ends, and the LGL basis evaluated at the Gauss nodes (geometry).
+struct GaussBasis {
+  int N, n;
+  std::vector<double> x, w, D;   // D[i*n + j] = l_j'(x_i)
+  std::vector<double> lm, lp;    // l_j(-1), l_j(+1)
+  std::vector<double> VL;        // VL[i*n + j] = l^LGL_j(x_i)
+};
+
 struct Ctx {
   int N, n, P, E;
+  int nodes;                  // 0: LGL (split form), 1: Legendre-Gauss (standard weak form)
   Params prm;
   Basis b;
+  GaussBasis g;
   std::vector<double> X;      // [e][c][P]
   std::vector<double> Ja;     // [e][d][l][P]  contravariant metric J a^d, component l
   std::vector<double> J;      // [e][P]
@@ -786,6 +799,17 @@ static const double RK_B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.
 static const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
                                2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
 
+static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double mu);
+
+// R(U) on the context's node set (the Gauss-node operator is FP64 only).
+template <class T>
+static void rhs_any(const Ctx& c, const T* U, T* Ut, double t, T mu) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (c.nodes == 1) { rhs_lg(c, U, Ut, t, mu); return; }
+  }
+  rhs(c, U, Ut, t, mu);
+}
+
 template <class T>
 static void rk_steps(const Ctx& c, T* U, double t, double dt, int nsteps, T mu) {
   size_t len = (size_t)c.E * 5 * c.P;
@@ -793,7 +817,7 @@ static void rk_steps(const Ctx& c, T* U, double t, double dt, int nsteps, T mu) 
   for (int st = 0; st < nsteps; ++st) {
     for (size_t a = 0; a < len; ++a) G[a] = T(0.0);
     for (int s = 0; s < 5; ++s) {
-      rhs(c, U, Ut.data(), t + RK_C[s] * dt, mu);
+      rhs_any(c, U, Ut.data(), t + RK_C[s] * dt, mu);
       for (size_t a = 0; a < len; ++a) {
         G[a] = RK_A[s] * G[a] + dt * Ut[a];
         U[a] = U[a] + RK_B[s] * G[a];
@@ -801,6 +825,423 @@ static void rk_steps(const Ctx& c, T* U, double t, double dt, int nsteps, T mu) 
     }
     t += dt;
   }
+}
+
+
+// ---------------------------------------------------------------------------
+// Legendre-Gauss collocation: the weak form of Sec. 3.1 (Eq. 2) with the
+// lifting of Eq. 3, the N+1 Gauss points per direction serving as
+// interpolation and quadrature nodes.  There is no split form on these nodes:
+// the volume integral takes the pointwise contravariant flux, and the face
+// values are interpolated from the element (no node lies on a face).
+//
+// Geometry (reading): the curl-form metric terms and the node positions are
+// built on the LGL nodes of degree N as for the LGL operator, then evaluated
+// at the Gauss nodes and at the Gauss points of each face from that same
+// polynomial.  The face values seen from both sides then agree, and the
+// discrete metric identities hold for the polynomial, so a uniform state
+// stays uniform.
+
+// P_n and P_n' at an interior point x by the three-term recurrence.
+static void legendre_p(int n, double x, double& Pn, double& dPn) {
+  double p0 = 1.0, p1 = x;
+  for (int k = 2; k <= n; ++k) {
+    double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    p0 = p1; p1 = p2;
+  }
+  Pn = (n == 0) ? 1.0 : p1;
+  dPn = (n == 0) ? 0.0 : n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+static double lagrange(const std::vector<double>& xs, int j, double x) {
+  double l = 1.0;
+  for (size_t k = 0; k < xs.size(); ++k)
+    if ((int)k != j) l *= (x - xs[k]) / (xs[j] - xs[k]);
+  return l;
+}
+
+static GaussBasis make_gauss_basis(int N, const Basis& lgl) {
+  GaussBasis g; g.N = N; g.n = N + 1;
+  int n = N + 1;
+  g.x.assign(n, 0.0); g.w.assign(n, 0.0); g.D.assign(n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double xj = -std::cos(M_PI * (j + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double Pn, dPn;
+      legendre_p(n, xj, Pn, dPn);
+      double dx = -Pn / dPn;
+      xj += dx;
+      if (std::fabs(dx) <= 1e-16 * std::max(1.0, std::fabs(xj))) break;
+    }
+    g.x[j] = xj;
+  }
+  for (int j = 0; j < n / 2; ++j) {   // exact symmetry about 0
+    double m = 0.5 * (g.x[n - 1 - j] - g.x[j]);
+    g.x[j] = -m; g.x[n - 1 - j] = m;
+  }
+  if (n % 2 == 1) g.x[n / 2] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double Pn, dPn;
+    legendre_p(n, g.x[j], Pn, dPn);
+    g.w[j] = 2.0 / ((1.0 - g.x[j] * g.x[j]) * dPn * dPn);
+  }
+  std::vector<double> lam(n, 1.0);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k)
+      if (k != j) lam[j] /= (g.x[j] - g.x[k]);
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double d = (lam[j] / lam[i]) / (g.x[i] - g.x[j]);
+      g.D[i * n + j] = d;
+      s += d;
+    }
+    g.D[i * n + i] = -s;
+  }
+  g.lm.resize(n); g.lp.resize(n);
+  for (int j = 0; j < n; ++j) { g.lm[j] = lagrange(g.x, j, -1.0); g.lp[j] = lagrange(g.x, j, 1.0); }
+  g.VL.resize(n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) g.VL[i * n + j] = lagrange(lgl.x, j, g.x[i]);
+  return g;
+}
+
+// Volume node with index i along direction d and face-local indices (p, q)
+// along the two other directions in increasing order (the face_vol convention).
+static inline int line_node(int n, int d, int i, int p, int q) {
+  if (d == 0) return vidx(n, i, p, q);
+  if (d == 1) return vidx(n, p, i, q);
+  return vidx(n, p, q, i);
+}
+
+// Replace the LGL geometry of the context by its values at the Gauss nodes
+// (volume) and Gauss face points (master-side normals and surface elements).
+static void gauss_geometry(Ctx& c) {
+  int n = c.n, P = c.P, nn = n * n;
+  const std::vector<double>& V = c.g.VL;
+  auto interp3 = [&](const double* in, double* out) {   // LGL nodal -> Gauss nodal
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          double s = 0.0;
+          for (int c3 = 0; c3 < n; ++c3)
+            for (int b3 = 0; b3 < n; ++b3)
+              for (int a3 = 0; a3 < n; ++a3)
+                s += V[i * n + a3] * V[j * n + b3] * V[k * n + c3] * in[vidx(n, a3, b3, c3)];
+          out[vidx(n, i, j, k)] = s;
+        }
+  };
+  std::vector<double> X((size_t)c.E * 3 * P), Ja((size_t)c.E * 9 * P), J((size_t)c.E * P);
+  std::vector<double> fn((size_t)c.nfaces * 3 * nn), fsJ((size_t)c.nfaces * nn);
+  std::vector<double> rel(P), dX(9 * P), dXg(9 * P);
+  for (int e = 0; e < c.E; ++e) {
+    for (int cc = 0; cc < 3; ++cc) {
+      const double* xl = &c.X[((size_t)e * 3 + cc) * P];
+      interp3(xl, &X[((size_t)e * 3 + cc) * P]);
+      // derivative of the interpolant (translation invariant: relative coordinates)
+      for (int id = 0; id < P; ++id) rel[id] = xl[id] - xl[0];
+      for (int d = 0; d < 3; ++d)
+        for (int k = 0; k < n; ++k)
+          for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) dX[(cc * 3 + d) * P + vidx(n, i, j, k)] = dxi(c, rel.data(), d, i, j, k);
+    }
+    for (int r = 0; r < 9; ++r) {
+      interp3(&dX[(size_t)r * P], &dXg[(size_t)r * P]);
+      interp3(&c.Ja[((size_t)e * 9 + r) * P], &Ja[((size_t)e * 9 + r) * P]);
+    }
+    for (int id = 0; id < P; ++id) {
+      double a[3][3];
+      for (int cc = 0; cc < 3; ++cc)
+        for (int d = 0; d < 3; ++d) a[cc][d] = dXg[(cc * 3 + d) * P + id];
+      J[(size_t)e * P + id] = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1])
+                            - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0])
+                            + a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+    }
+    for (int f = 0; f < 6; ++f) {
+      if (!c.master[e * 6 + f]) continue;
+      int d = f / 2, s = f % 2, id = c.face_id[e * 6 + f];
+      for (int q = 0; q < n; ++q)
+        for (int p = 0; p < n; ++p) {
+          double nv[3], s2 = 0.0;
+          for (int l = 0; l < 3; ++l) {
+            double v = 0.0;
+            for (int b3 = 0; b3 < n; ++b3)
+              for (int a3 = 0; a3 < n; ++a3)
+                v += V[p * n + a3] * V[q * n + b3] * c.Ja[(((size_t)e * 3 + d) * 3 + l) * P + face_vol(n, f, a3, b3)];
+            nv[l] = (2.0 * s - 1.0) * v;
+            s2 += nv[l] * nv[l];
+          }
+          double sJ = std::sqrt(s2);
+          for (int l = 0; l < 3; ++l) fn[((size_t)id * 3 + l) * nn + p + n * q] = nv[l] / sJ;
+          fsJ[(size_t)id * nn + p + n * q] = sJ;
+        }
+    }
+  }
+  c.X.swap(X); c.Ja.swap(Ja); c.J.swap(J); c.fn.swap(fn); c.fsJ.swap(fsJ);
+  for (size_t a = 0; a < c.J.size(); ++a)
+    if (!(c.J[a] > 0.0)) c.err = "non-positive Jacobian at a Gauss node";
+}
+
+// Face values of nv nodal fields of every element: out[e][f][v][p + n q] =
+// sum_i l_i(+-1) field(line of face point (p, q)).
+static void prolong_to_faces(const Ctx& c, const double* field, int nv, std::vector<double>& out) {
+  int n = c.n, P = c.P, nn = n * n;
+  out.assign((size_t)c.E * 6 * nv * nn, 0.0);
+  for (int e = 0; e < c.E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      int d = f / 2;
+      const std::vector<double>& l = (f % 2) ? c.g.lp : c.g.lm;
+      for (int v = 0; v < nv; ++v)
+        for (int q = 0; q < n; ++q)
+          for (int p = 0; p < n; ++p) {
+            double s = 0.0;
+            for (int i = 0; i < n; ++i) s += l[i] * field[((size_t)e * nv + v) * P + line_node(n, d, i, p, q)];
+            out[(((size_t)e * 6 + f) * nv + v) * nn + p + n * q] = s;
+          }
+    }
+}
+
+// Outward n_l sJ of element e on its local face f at its face point (p, q):
+// the master's stored normal, or its negative at the mapped point.
+static inline void outward_nsJ(const Ctx& c, int e, int f, int p, int q, double nsJ[3]) {
+  int n = c.n, nn = n * n, fid = c.face_id[e * 6 + f];
+  int pp = p, qq = q;
+  double sg = 1.0;
+  if (!c.master[e * 6 + f]) {
+    flip_map(c.nbr[(e * 6 + f) * 3 + 2], c.N, p, q, pp, qq);
+    sg = -1.0;
+  }
+  double sJ = c.fsJ[(size_t)fid * nn + pp + n * qq];
+  for (int l = 0; l < 3; ++l) nsJ[l] = sg * c.fn[((size_t)fid * 3 + l) * nn + pp + n * qq] * sJ;
+}
+
+// BR1 lifting in the weak form of Eq. 3 for the fields phi [e][4][P] with
+// face values phif [e][6][4][nn]:
+//   J g_l,i = sum_faces l_{i_d}(+-1)/w_{i_d} phi* (n_l sJ) - sum_d sum_m (w_m/w_{i_d}) D_{m i_d} (phi Ja^d_l)_m,
+// phi* = (phi_own + phi_nbr)/2 at each face point.
+static void lifting_lg(const Ctx& c, const double* phi, const std::vector<double>& phif, double* G) {
+  int n = c.n, P = c.P, nn = n * n, N = c.N;
+  const std::vector<double>& w = c.g.w;
+  const std::vector<double>& D = c.g.D;
+  for (int e = 0; e < c.E; ++e) {
+    std::vector<double> acc((size_t)12 * P, 0.0);
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          int id = vidx(n, i, j, k), ijk[3] = {i, j, k};
+          for (int ph = 0; ph < 4; ++ph)
+            for (int l = 0; l < 3; ++l) {
+              double s = 0.0;
+              for (int d = 0; d < 3; ++d) {
+                int r = ijk[d];
+                for (int m = 0; m < n; ++m) {
+                  int mid = (d == 0) ? vidx(n, m, j, k) : (d == 1) ? vidx(n, i, m, k) : vidx(n, i, j, m);
+                  s += (w[m] / w[r]) * D[m * n + r] * phi[((size_t)e * 4 + ph) * P + mid] *
+                       c.Ja[(((size_t)e * 3 + d) * 3 + l) * P + mid];
+                }
+              }
+              acc[(size_t)(ph * 3 + l) * P + id] -= s;
+            }
+        }
+    for (int f = 0; f < 6; ++f) {
+      int d = f / 2;
+      int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1], fl = c.nbr[(e * 6 + f) * 3 + 2];
+      const std::vector<double>& lend = (f % 2) ? c.g.lp : c.g.lm;
+      for (int q = 0; q < n; ++q)
+        for (int p = 0; p < n; ++p) {
+          int p2, q2;
+          flip_map(fl, N, p, q, p2, q2);
+          double nsJ[3];
+          outward_nsJ(c, e, f, p, q, nsJ);
+          for (int ph = 0; ph < 4; ++ph) {
+            double mine = phif[(((size_t)e * 6 + f) * 4 + ph) * nn + p + n * q];
+            double other = phif[(((size_t)e2 * 6 + f2) * 4 + ph) * nn + p2 + n * q2];
+            double star = 0.5 * (mine + other);
+            for (int i = 0; i < n; ++i) {
+              int id = line_node(n, d, i, p, q);
+              for (int l = 0; l < 3; ++l) acc[(size_t)(ph * 3 + l) * P + id] += lend[i] / w[i] * star * nsJ[l];
+            }
+          }
+        }
+    }
+    for (int r = 0; r < 12; ++r)
+      for (int id = 0; id < P; ++id) G[((size_t)e * 12 + r) * P + id] = acc[(size_t)r * P + id] / c.J[(size_t)e * P + id];
+  }
+}
+
+// Lifting variables (u, v, w, T) at the nodes and at the faces (from the
+// face values of the conservative state).
+static void lg_phi(const Ctx& c, const double* U, std::vector<double>& phi, std::vector<double>& Uf,
+                   std::vector<double>& phif) {
+  int P = c.P, nn = c.n * c.n;
+  phi.assign((size_t)c.E * 4 * P, 0.0);
+  for (int e = 0; e < c.E; ++e)
+    for (int id = 0; id < P; ++id) {
+      double q[5];
+      for (int v = 0; v < 5; ++v) q[v] = U[((size_t)e * 5 + v) * P + id];
+      Prim<double> w = cons2prim(c.prm, q);
+      for (int a = 0; a < 3; ++a) phi[((size_t)e * 4 + a) * P + id] = w.u[a];
+      phi[((size_t)e * 4 + 3) * P + id] = w.T_;
+    }
+  prolong_to_faces(c, U, 5, Uf);
+  phif.assign((size_t)c.E * 6 * 4 * nn, 0.0);
+  for (int ef = 0; ef < c.E * 6; ++ef)
+    for (int pq = 0; pq < nn; ++pq) {
+      double q[5];
+      for (int v = 0; v < 5; ++v) q[v] = Uf[((size_t)ef * 5 + v) * nn + pq];
+      Prim<double> w = cons2prim(c.prm, q);
+      for (int a = 0; a < 3; ++a) phif[((size_t)ef * 4 + a) * nn + pq] = w.u[a];
+      phif[((size_t)ef * 4 + 3) * nn + pq] = w.T_;
+    }
+}
+
+// U_t = R(U) on Gauss nodes (Sec. 3.1, Eq. 2):
+//   J U_t,i = - sum_faces l_{i_d}(+-1)/w_{i_d} F*_out + sum_d sum_m (w_m/w_{i_d}) D_{m i_d} Ft^d_m + J Q,
+// Ft^d = (f - f_v)(q, g) . Ja^d, F*_out = (F_adv(q-, q+; n) - {f_v} . n) sJ with
+// the element's outward n, face states and gradients from prolong_to_faces.
+static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double mu) {
+  const Params& pr = c.prm;
+  int n = c.n, P = c.P, E = c.E, N = c.N, nn = n * n;
+  const std::vector<double>& w = c.g.w;
+  const std::vector<double>& D = c.g.D;
+  std::vector<double> phi, Uf, phif, Gf;
+  lg_phi(c, U, phi, Uf, phif);
+  std::vector<double> G((size_t)E * 12 * P);
+  lifting_lg(c, phi.data(), phif, G.data());
+  prolong_to_faces(c, G.data(), 12, Gf);
+  // face fluxes on master faces, master orientation
+  std::vector<double> Fs((size_t)c.nfaces * 5 * nn);
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      if (!c.master[e * 6 + f]) continue;
+      int fid = c.face_id[e * 6 + f];
+      int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1], fl = c.nbr[(e * 6 + f) * 3 + 2];
+      for (int q = 0; q < n; ++q)
+        for (int p = 0; p < n; ++p) {
+          int p2, q2;
+          flip_map(fl, N, p, q, p2, q2);
+          double qL[5], qR[5], gL[12], gR[12], nv[3];
+          for (int v = 0; v < 5; ++v) {
+            qL[v] = Uf[(((size_t)e * 6 + f) * 5 + v) * nn + p + n * q];
+            qR[v] = Uf[(((size_t)e2 * 6 + f2) * 5 + v) * nn + p2 + n * q2];
+          }
+          for (int r = 0; r < 12; ++r) {
+            gL[r] = Gf[(((size_t)e * 6 + f) * 12 + r) * nn + p + n * q];
+            gR[r] = Gf[(((size_t)e2 * 6 + f2) * 12 + r) * nn + p2 + n * q2];
+          }
+          for (int l = 0; l < 3; ++l) nv[l] = c.fn[((size_t)fid * 3 + l) * nn + p + n * q];
+          double sJ = c.fsJ[(size_t)fid * nn + p + n * q];
+          Prim<double> L = cons2prim(pr, qL), Rr = cons2prim(pr, qR);
+          double fa[5], fvL[5], fvR[5];
+          if (pr.surf_flux == 1) ec_flux(pr, L, Rr, nv, fa);
+          else if (pr.surf_flux == 2) roe_flux(pr, qL, L, qR, Rr, nv, fa);
+          else llf_flux(pr, qL, L, qR, Rr, nv, fa);
+          visc_flux(pr, L, gL, mu, nv, fvL);
+          visc_flux(pr, Rr, gR, mu, nv, fvR);
+          for (int v = 0; v < 5; ++v)
+            Fs[((size_t)fid * 5 + v) * nn + p + n * q] = (fa[v] - 0.5 * (fvL[v] + fvR[v])) * sJ;
+        }
+    }
+  for (int e = 0; e < E; ++e) {
+    // contravariant fluxes at the nodes
+    std::vector<double> Ft((size_t)3 * 5 * P);
+    for (int id = 0; id < P; ++id) {
+      double q[5], g[12];
+      for (int v = 0; v < 5; ++v) q[v] = U[((size_t)e * 5 + v) * P + id];
+      for (int r = 0; r < 12; ++r) g[r] = G[((size_t)e * 12 + r) * P + id];
+      Prim<double> W = cons2prim(pr, q);
+      for (int d = 0; d < 3; ++d) {
+        double nv[3], fa[5], fv[5];
+        for (int l = 0; l < 3; ++l) nv[l] = c.Ja[(((size_t)e * 3 + d) * 3 + l) * P + id];
+        euler_flux(q, W, nv, fa);
+        visc_flux(pr, W, g, mu, nv, fv);
+        for (int v = 0; v < 5; ++v) Ft[((size_t)d * 5 + v) * P + id] = fa[v] - fv[v];
+      }
+    }
+    std::vector<double> acc((size_t)5 * P, 0.0);
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          int id = vidx(n, i, j, k), ijk[3] = {i, j, k};
+          for (int d = 0; d < 3; ++d) {
+            int r = ijk[d];
+            for (int m = 0; m < n; ++m) {
+              int mid = (d == 0) ? vidx(n, m, j, k) : (d == 1) ? vidx(n, i, m, k) : vidx(n, i, j, m);
+              double c_ = (w[m] / w[r]) * D[m * n + r];
+              for (int v = 0; v < 5; ++v) acc[(size_t)v * P + id] -= c_ * Ft[((size_t)d * 5 + v) * P + mid];
+            }
+          }
+        }
+    for (int f = 0; f < 6; ++f) {
+      int d = f / 2, fid = c.face_id[e * 6 + f];
+      const std::vector<double>& lend = (f % 2) ? c.g.lp : c.g.lm;
+      for (int q = 0; q < n; ++q)
+        for (int p = 0; p < n; ++p) {
+          double Fout[5];
+          if (c.master[e * 6 + f]) {
+            for (int v = 0; v < 5; ++v) Fout[v] = Fs[((size_t)fid * 5 + v) * nn + p + n * q];
+          } else {
+            int p2, q2;
+            flip_map(c.nbr[(e * 6 + f) * 3 + 2], N, p, q, p2, q2);
+            for (int v = 0; v < 5; ++v) Fout[v] = -Fs[((size_t)fid * 5 + v) * nn + p2 + n * q2];
+          }
+          for (int i = 0; i < n; ++i) {
+            int id = line_node(n, d, i, p, q);
+            for (int v = 0; v < 5; ++v) acc[(size_t)v * P + id] += lend[i] / w[i] * Fout[v];
+          }
+        }
+    }
+    for (int id = 0; id < P; ++id) {
+      double Qs[5] = {0, 0, 0, 0, 0};
+      if (pr.source == 1) {
+        double x[3] = {c.X[((size_t)e * 3 + 0) * P + id], c.X[((size_t)e * 3 + 1) * P + id], c.X[((size_t)e * 3 + 2) * P + id]};
+        mms_source(pr, x, t, Qs);
+      }
+      for (int v = 0; v < 5; ++v) Ut[((size_t)e * 5 + v) * P + id] = -acc[(size_t)v * P + id] / c.J[(size_t)e * P + id] + Qs[v];
+    }
+  }
+}
+
+// Lifted gradients on either node set (test hook and diagnostics).
+static void lifted_gradients(const Ctx& c, const double* U, double* G) {
+  std::vector<double> phi, Uf, phif;
+  lg_phi(c, U, phi, Uf, phif);
+  lifting_lg(c, phi.data(), phif, G);
+}
+
+
+// Volume integrals on Gauss nodes: the same quantities as orc_integrals, with
+// the Gauss weights and the weak-form lifted velocity gradient.
+static void integrals_lg(const Ctx& c, const double* U, double* out) {
+  int n = c.n, P = c.P;
+  const Params& pr = c.prm;
+  std::vector<double> G((size_t)c.E * 12 * P);
+  lifted_gradients(c, U, G.data());
+  double tot[5] = {0, 0, 0, 0, 0}, vol = 0.0, ek = 0.0, ens = 0.0, pmin = 1e300;
+  for (int e = 0; e < c.E; ++e)
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          int id = vidx(n, i, j, k);
+          double wq = c.g.w[i] * c.g.w[j] * c.g.w[k] * c.J[(size_t)e * P + id];
+          double q[5];
+          for (int v = 0; v < 5; ++v) q[v] = U[((size_t)e * 5 + v) * P + id];
+          Prim<double> w = cons2prim(pr, q);
+          for (int v = 0; v < 5; ++v) tot[v] += wq * q[v];
+          vol += wq;
+          ek += wq * q[0] * (w.u[0] * w.u[0] + w.u[1] * w.u[1] + w.u[2] * w.u[2]);
+          pmin = std::min(pmin, w.p);
+          const double* g = &G[(size_t)e * 12 * P + id];
+          double om0 = g[(2 * 3 + 1) * P] - g[(1 * 3 + 2) * P];
+          double om1 = g[(0 * 3 + 2) * P] - g[(2 * 3 + 0) * P];
+          double om2 = g[(1 * 3 + 0) * P] - g[(0 * 3 + 1) * P];
+          ens += wq * visc_mu(pr, pr.mu, w.T_) * (om0 * om0 + om1 * om1 + om2 * om2);
+        }
+  for (int v = 0; v < 5; ++v) out[v] = tot[v];
+  out[5] = 0.5 * ek / vol;
+  out[6] = ens / vol;
+  out[7] = pmin;
 }
 
 }  // namespace orc
@@ -818,6 +1259,7 @@ void* orc_create(int N, int n_elems, int ngeo, const double* xgeo, const int* fa
   c->prm.gamma = prm[0]; c->prm.R = prm[1]; c->prm.Pr = prm[2]; c->prm.mu = prm[3];
   c->prm.mms_amp = prm[4];
   c->prm.visc_law = (int)prm[5]; c->prm.T_ref = prm[6]; c->prm.S_suth = prm[7];
+  c->nodes = (int)prm[8];
   c->prm.surf_flux = surf_flux; c->prm.source = source; c->prm.vol_flux = 0;
   if (c->prm.visc_law != 0 && c->prm.visc_law != 1) {
     if (errbuf && errlen > 0) std::snprintf(errbuf, errlen, "unknown viscosity law %d", c->prm.visc_law);
@@ -825,10 +1267,20 @@ void* orc_create(int N, int n_elems, int ngeo, const double* xgeo, const int* fa
     return nullptr;
   }
   c->b = make_basis(N);
-  if (!build_geometry(*c, ngeo, xgeo) || !build_faces(*c, face_nbr)) {
+  if (c->nodes != 0 && c->nodes != 1) c->err = "unknown node set";
+  if (!c->err.empty() || !build_geometry(*c, ngeo, xgeo) || !build_faces(*c, face_nbr)) {
     if (errbuf && errlen > 0) std::snprintf(errbuf, errlen, "%s", c->err.c_str());
     delete c;
     return nullptr;
+  }
+  if (c->nodes == 1) {
+    c->g = make_gauss_basis(N, c->b);
+    gauss_geometry(*c);
+    if (!c->err.empty()) {
+      if (errbuf && errlen > 0) std::snprintf(errbuf, errlen, "%s", c->err.c_str());
+      delete c;
+      return nullptr;
+    }
   }
   return c;
 }
@@ -841,6 +1293,7 @@ void orc_set_vol_flux(void* h, int kind) { ((Ctx*)h)->prm.vol_flux = kind; }
 // Lifted gradients G [E][12][P] (row phi*3 + l = d phi / d x_l).
 void orc_lifting(void* h, const double* U, double* G) {
   Ctx* c = (Ctx*)h;
+  if (c->nodes == 1) { lifted_gradients(*c, U, G); return; }
   int P = c->P;
   std::vector<double> phi((size_t)c->E * 4 * P);
   for (int e = 0; e < c->E; ++e)
@@ -889,12 +1342,26 @@ void orc_geometry(void* h, double* X, double* Ja, double* J) {
 
 void orc_time_derivative(void* h, const double* U, double* Ut, double t) {
   Ctx* c = (Ctx*)h;
-  rhs<double>(*c, U, Ut, t, c->prm.mu);
+  rhs_any<double>(*c, U, Ut, t, c->prm.mu);
 }
+
+// Legendre-Gauss basis of degree N: nodes, weights, D, l_j(-1), l_j(+1).
+void orc_gauss_basis(int N, double* x, double* w, double* D, double* lm, double* lp) {
+  GaussBasis g = make_gauss_basis(N, make_basis(N));
+  int n = N + 1;
+  std::memcpy(x, g.x.data(), sizeof(double) * n);
+  std::memcpy(w, g.w.data(), sizeof(double) * n);
+  std::memcpy(D, g.D.data(), sizeof(double) * n * n);
+  std::memcpy(lm, g.lm.data(), sizeof(double) * n);
+  std::memcpy(lp, g.lp.data(), sizeof(double) * n);
+}
+
+int orc_nodes(void* h) { return ((Ctx*)h)->nodes; }
 
 // Tangent-linear: Ut = R(U) and dUt = dR/dU . dU + dR/dmu . dmu.
 void orc_time_derivative_tl(void* h, const double* U, const double* dU, double dmu,
                             double* Ut, double* dUt, double t) {
+  if (((Ctx*)h)->nodes != 0) return;   // the tangent-linear is built for the LGL operator
   Ctx* c = (Ctx*)h;
   size_t len = (size_t)c->E * 5 * c->P;
   std::vector<Dual> Ud(len), Utd(len);
@@ -910,6 +1377,7 @@ void orc_rk_steps(void* h, double* U, double t, double dt, int nsteps) {
 
 // Tangent-linear of nsteps LSERK steps: U and dU advanced together.
 void orc_rk_steps_tl(void* h, double* U, double* dU, double dmu, double t, double dt, int nsteps) {
+  if (((Ctx*)h)->nodes != 0) return;   // the tangent-linear is built for the LGL operator
   Ctx* c = (Ctx*)h;
   size_t len = (size_t)c->E * 5 * c->P;
   std::vector<Dual> Ud(len);
@@ -946,6 +1414,7 @@ double orc_log_mean(double a, double b) { return log_mean<double>(a, b); }
 //        min p}; rho0 = U0 = L = 1, mu0 = 1/Re, mu(T) by the viscosity law.
 void orc_integrals(void* h, const double* U, double* out) {
   Ctx* c = (Ctx*)h;
+  if (c->nodes == 1) { integrals_lg(*c, U, out); return; }
   int n = c->n, P = c->P;
   const Params& pr = c->prm;
   // gradients from the lifting: reuse rhs machinery through a local copy

@@ -46,6 +46,7 @@ def _load():
     L.orc_nfaces.argtypes = [C.c_void_p]
     L.orc_nfaces.restype = C.c_int
     L.orc_basis.argtypes = [C.c_int, _dp, _dp, _dp]
+    L.orc_gauss_basis.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp]
     L.orc_geometry.argtypes = [C.c_void_p, _dp, _dp, _dp]
     L.orc_time_derivative.argtypes = [C.c_void_p, _dp, _dp, C.c_double]
     L.orc_time_derivative_tl.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp, _dp, C.c_double]
@@ -67,6 +68,15 @@ def _load():
     return L
 
 
+def gauss_basis(N: int):
+    """Legendre-Gauss nodes, weights, D[i, j] = l_j'(x_i), l_j(-1), l_j(+1)."""
+    L = _load()
+    n = N + 1
+    x, w, D, lm, lp = np.zeros(n), np.zeros(n), np.zeros(n * n), np.zeros(n), np.zeros(n)
+    L.orc_gauss_basis(N, x, w, D, lm, lp)
+    return x, w, D.reshape(n, n), lm, lp
+
+
 def basis(N: int):
     """LGL nodes, weights and differentiation matrix D[i, j] = l_j'(x_i)."""
     L = _load()
@@ -83,8 +93,8 @@ def rk_coeffs():
     return A, B, Cc
 
 
-def _prm(gamma, R, Pr, mu, amp=0.1, visc_law=0, T_ref=1.0, S_suth=0.0):
-    return np.array([gamma, R, Pr, mu, amp, visc_law, T_ref, S_suth], dtype=np.float64)
+def _prm(gamma, R, Pr, mu, amp=0.1, visc_law=0, T_ref=1.0, S_suth=0.0, nodes=0):
+    return np.array([gamma, R, Pr, mu, amp, visc_law, T_ref, S_suth, nodes], dtype=np.float64)
 
 
 def ec_flux(qL, qR, nv, gamma=1.4):
@@ -119,20 +129,24 @@ class Oracle:
     2 = Roe with the Harten-Hyman entropy fix.
     source: 0 = none, 1 = density-wave manufactured solution.
     visc_law: 0 = constant mu, 1 = Sutherland's law mu (T/T_ref)^1.5 (T_ref + S)/(T + S).
+    nodes: 0 = LGL nodes with the split form, 1 = Legendre-Gauss nodes with the
+    standard weak form (no tangent-linear).
     """
 
     def __init__(self, mesh, N: int, gamma=1.4, R=1.0, Pr=0.72, mu=0.0,
                  surf_flux: int = 0, source: int = 0, mms_amp: float = 0.1,
-                 visc_law: int = 0, T_ref: float = 1.0, S_suth: float = 0.0):
+                 visc_law: int = 0, T_ref: float = 1.0, S_suth: float = 0.0, nodes: int = 0):
         L = _load()
         self.N, self.n, self.P = N, N + 1, (N + 1) ** 3
         self.E = int(mesh.xgeo.shape[0])
         self.gamma, self.R, self.Pr, self.mu = gamma, R, Pr, mu
+        self.nodes = nodes
         xgeo = np.ascontiguousarray(mesh.xgeo, dtype=np.float64)
         nbr = np.ascontiguousarray(mesh.face_nbr, dtype=np.int32)
         err = C.create_string_buffer(256)
         h = L.orc_create(N, self.E, int(mesh.xgeo.shape[-1]) - 1, xgeo, nbr,
-                         _prm(gamma, R, Pr, mu, mms_amp, visc_law, T_ref, S_suth), surf_flux, source, err, 256)
+                         _prm(gamma, R, Pr, mu, mms_amp, visc_law, T_ref, S_suth, nodes), surf_flux, source, err,
+                         256)
         if not h:
             raise ValueError("oracle: " + err.value.decode())
         self._h = C.c_void_p(h)
@@ -161,6 +175,8 @@ class Oracle:
         return out
 
     def time_derivative_tl(self, U, dU, dmu=0.0, t=0.0):
+        if self.nodes != 0:
+            raise ValueError("oracle: the tangent-linear is built for the LGL operator")
         U = np.ascontiguousarray(U, dtype=np.float64)
         dU = np.ascontiguousarray(dU, dtype=np.float64)
         Ut, dUt = np.zeros_like(U), np.zeros_like(U)
@@ -173,6 +189,8 @@ class Oracle:
         return U
 
     def rk_steps_tl(self, U, dU, dmu, t, dt, nsteps):
+        if self.nodes != 0:
+            raise ValueError("oracle: the tangent-linear is built for the LGL operator")
         U = np.array(U, dtype=np.float64, copy=True, order="C")
         dU = np.array(dU, dtype=np.float64, copy=True, order="C")
         self._L.orc_rk_steps_tl(self._h, U, dU, float(dmu), float(t), float(dt), int(nsteps))
