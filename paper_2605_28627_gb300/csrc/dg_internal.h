@@ -41,7 +41,7 @@ struct Gas {
   double suth_c;     // T_ref + S
   // FP32 copies of the constants the FP32 operator uses, rounded once on the
   // host (set by set_float_copies)
-  float f_gamma, f_gm1, f_inv_gm1, f_inv_R, f_mu, f_lam, f_p_ref, f_inv_T_ref, f_S_suth, f_suth_c;
+  float f_gamma, f_gm1, f_inv_gm1, f_inv_R, f_mu, f_lam, f_p_ref, f_inv_T_ref, f_S_suth, f_suth_c, f_mms_amp;
 };
 
 inline void set_float_copies(Gas& g) {
@@ -49,6 +49,7 @@ inline void set_float_copies(Gas& g) {
   g.f_inv_R = (float)g.inv_R; g.f_mu = (float)g.mu; g.f_lam = (float)(g.mu * g.kappa);
   g.f_p_ref = (float)g.p_ref;
   g.f_inv_T_ref = (float)g.inv_T_ref; g.f_S_suth = (float)g.S_suth; g.f_suth_c = (float)g.suth_c;
+  g.f_mms_amp = (float)g.mms_amp;
 }
 
 // Face descriptor (master orientation): elements and local faces of both sides

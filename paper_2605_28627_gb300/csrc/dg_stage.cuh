@@ -153,31 +153,20 @@ __device__ __forceinline__ void lift_body(const double* __restrict__ U, const R*
 // Surface flux on every face node, master orientation (Sec. 3.1): Riemann flux
 // (LLF, or the two-point EC flux) minus the BR1 average of the viscous fluxes,
 // times the surface element:  F* = (F_adv(qM, qS; n) - 1/2 (f_v,M + f_v,S) . n) sJ.
-template <int N, typename R>
-__device__ __forceinline__ void face_body(const double* __restrict__ U, const R* __restrict__ grad,
-                                          const FaceInfo* __restrict__ faces, const R* __restrict__ facegeo,
-                                          R* __restrict__ fstar, int F, const Gas& g, long gid) {
-  constexpr int n = N + 1, P = n * n * n, NN = n * n;
-  if (gid >= (long)F * NN) return;
-  const int f = (int)(gid / NN), pq = (int)(gid % NN);
-  const int p = pq % n, q = pq / n;
-  const FaceInfo fi = faces[f];
-  const int eM = fi.master >> 3, fM = fi.master & 7, eS = fi.slave >> 3, fS = fi.slave & 7;
-  int p2, q2;
-  apply_flip<n>(fi.flip, p, q, p2, q2);
-  const int idM = face_node<n>(fM, p, q), idS = face_node<n>(fS, p2, q2);
-  double dL[5], dR[5];
+// Numerical flux at one face point from the two sides' FP64 states (dL, dR)
+// and lifted gradients (gL, gR), unit normal n of the master side and surface
+// element sJ: writes F* (5 values, `stride` apart) to fo.
+template <typename R>
+__device__ __forceinline__ void face_flux_core(const double dL[5], const double dR[5], const R gL[12],
+                                               const R gR[12], R nx, R ny, R nz, R sJ, const Gas& g, R* fo,
+                                               size_t stride) {
   R qL[5], qR[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    dL[v] = U[((size_t)eM * 5 + v) * P + idM];
-    dR[v] = U[((size_t)eS * 5 + v) * P + idS];
     qL[v] = to_op<R>(dL[v]);
     qR[v] = to_op<R>(dR[v]);
   }
   const R gm1 = gsel<R>(g.gm1, g.f_gm1), gam = gsel<R>(g.gamma, g.f_gamma);
-  const R* fg = facegeo + (size_t)f * 4 * NN + pq;
-  const R nx = fg[0], ny = fg[NN], nz = fg[2 * NN], sJ = fg[3 * NN];
   const R irL = rcp_lf(qL[0]), irR = rcp_lf(qR[0]);
   const R uL = qL[1] * irL, vL = qL[2] * irL, wL = qL[3] * irL;
   const R uR = qR[1] * irR, vR = qR[2] * irR, wR = qR[3] * irR;
@@ -224,12 +213,6 @@ __device__ __forceinline__ void face_body(const double* __restrict__ U, const R*
 #pragma unroll
     for (int v = 0; v < 5; ++v) fa[v] = R(0.5) * (fL[v] + fR[v]) - R(0.5) * lmax * dq[v];
   }
-  R gL[12], gR[12];
-#pragma unroll
-  for (int r = 0; r < 12; ++r) {
-    gL[r] = grad[((size_t)eM * 12 + r) * P + idM];
-    gR[r] = grad[((size_t)eS * 12 + r) * P + idS];
-  }
   R fvL[4], fvR[4];
   const R mu = gsel<R>(g.mu, g.f_mu), lam = gsel<R>(g.mu * g.kappa, g.f_lam);
   R sfL = R(1), sfR = R(1);
@@ -240,10 +223,38 @@ __device__ __forceinline__ void face_body(const double* __restrict__ U, const R*
   }
   visc_flux<R>(gL, uL, vL, wL, mu * sfL, lam * sfL, nx, ny, nz, fvL);
   visc_flux<R>(gR, uR, vR, wR, mu * sfR, lam * sfR, nx, ny, nz, fvR);
-  R* fo = fstar + (size_t)f * 5 * NN + pq;
   fo[0] = fa[0] * sJ;
 #pragma unroll
-  for (int v = 1; v < 5; ++v) fo[(size_t)v * NN] = (fa[v] - R(0.5) * (fvL[v - 1] + fvR[v - 1])) * sJ;
+  for (int v = 1; v < 5; ++v) fo[(size_t)v * stride] = (fa[v] - R(0.5) * (fvL[v - 1] + fvR[v - 1])) * sJ;
+}
+
+template <int N, typename R>
+__device__ __forceinline__ void face_body(const double* __restrict__ U, const R* __restrict__ grad,
+                                          const FaceInfo* __restrict__ faces, const R* __restrict__ facegeo,
+                                          R* __restrict__ fstar, int F, const Gas& g, long gid) {
+  constexpr int n = N + 1, P = n * n * n, NN = n * n;
+  if (gid >= (long)F * NN) return;
+  const int f = (int)(gid / NN), pq = (int)(gid % NN);
+  const int p = pq % n, q = pq / n;
+  const FaceInfo fi = faces[f];
+  const int eM = fi.master >> 3, fM = fi.master & 7, eS = fi.slave >> 3, fS = fi.slave & 7;
+  int p2, q2;
+  apply_flip<n>(fi.flip, p, q, p2, q2);
+  const int idM = face_node<n>(fM, p, q), idS = face_node<n>(fS, p2, q2);
+  double dL[5], dR[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    dL[v] = U[((size_t)eM * 5 + v) * P + idM];
+    dR[v] = U[((size_t)eS * 5 + v) * P + idS];
+  }
+  R gL[12], gR[12];
+#pragma unroll
+  for (int r = 0; r < 12; ++r) {
+    gL[r] = grad[((size_t)eM * 12 + r) * P + idM];
+    gR[r] = grad[((size_t)eS * 12 + r) * P + idS];
+  }
+  const R* fg = facegeo + (size_t)f * 4 * NN + pq;
+  face_flux_core<R>(dL, dR, gL, gR, fg[0], fg[NN], fg[2 * NN], fg[3 * NN], g, fstar + (size_t)f * 5 * NN + pq, NN);
 }
 
 // 1/x: hardware reciprocal approximation refined by one cubic Newton-Raphson
@@ -481,34 +492,54 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     for (int c = 0; c < 4; ++c)
       acc[1 + c] = fma(fs_sign, fsr[(c + 1) * NN], fma(vs, sFv[(d * 4 + c) * P + id], acc[1 + c]));
   }
-  double src[5] = {0, 0, 0, 0, 0};
+  // Manufactured source, density wave rho = 2 + A sin(phi), phi = pi (x+y+z-t),
+  // u = (1,1,1), p = 1: residual of Eq. 1 = [2r', 2r', 2r', 2r', 3r' - lambda Lap T],
+  // r' = pi A cos(phi).  sin/cos of phi from those of pi (x+y+z) (per node, set
+  // up once) and of pi t (once per block) by the angle-difference identities.
+  // Evaluated in the operator type.
+  R src[5] = {0, 0, 0, 0, 0};
   if (g.source == DG_SOURCE_MMS) {
-    // density wave rho = 2 + A sin(phi), phi = pi (x+y+z-t), u = (1,1,1), p = 1:
-    // residual of Eq. 1 = [2r', 2r', 2r', 2r', 3r' - lambda Lap T], r' = pi A cos(phi).
-    // sin/cos of phi from those of pi (x+y+z) (per node, set up once) and of
-    // pi t (once per block) by the angle-difference identities.
-    const double sa = mms[((size_t)e * 2) * P + id], ca = mms[((size_t)e * 2 + 1) * P + id];
-    const double sphi = fma(sa, s_tc[1], -ca * s_tc[0]);
-    const double cphi = fma(ca, s_tc[1], sa * s_tc[0]);
-    const double A = g.mms_amp;
-    const double rw = 2.0 + A * sphi;
-    const double irw = rcp_op(rw);
-    const double rp = M_PI * A * cphi;
-    const double lapT = 3.0 * g.inv_R * fma(M_PI * M_PI * A, sphi, 2.0 * rp * rp * irw) * (irw * irw);
-    src[0] = src[1] = src[2] = src[3] = 2.0 * rp;
-    src[4] = fma(-g.mu * g.kappa, lapT, 3.0 * rp);
+    const R sa = to_op<R>(mms[((size_t)e * 2) * P + id]), ca = to_op<R>(mms[((size_t)e * 2 + 1) * P + id]);
+    const R st = to_op<R>(s_tc[0]), ct = to_op<R>(s_tc[1]);
+    const R sphi = fma(sa, ct, -ca * st);
+    const R cphi = fma(ca, ct, sa * st);
+    const R A = gsel<R>(g.mms_amp, g.f_mms_amp);
+    const R rw = R(2) + A * sphi;
+    const R irw = rcp_op(rw);
+    const R rp = R(M_PI) * A * cphi;
+    const R lapT = R(3) * gsel<R>(g.inv_R, g.f_inv_R) * fma(R(M_PI) * R(M_PI) * A, sphi, R(2) * rp * rp * irw) *
+                   (irw * irw);
+    src[0] = src[1] = src[2] = src[3] = R(2) * rp;
+    src[4] = fma(-gsel<R>(g.mu * g.kappa, g.f_lam), lapT, R(3) * rp);
   }
-  // Jacobian, source and RK update in FP64
-  const double iJ = iJ64[(size_t)e * 10 * P + 9 * P + id];
+  const size_t o0 = (size_t)e * 5 * P + id;
   if (a.mode == 0) {
+    // R(U) itself, scaled by 1/J in FP64
+    const double iJ = iJ64[(size_t)e * 10 * P + 9 * P + id];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) a.Ut[((size_t)e * 5 + c) * P + id] = fma(-to_f64(acc[c]), iJ, src[c]);
-  } else {
+    for (int c = 0; c < 5; ++c) a.Ut[o0 + (size_t)c * P] = fma(-to_f64(acc[c]), iJ, to_f64(src[c]));
+  } else if constexpr (sizeof(R) == 8) {
+    // Jacobian, source and the LSERK register update in FP64
+    const double iJ = iJ64[(size_t)e * 10 * P + 9 * P + id];
     const double dt = a.clock[1];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      const size_t o = ((size_t)e * 5 + c) * P + id;
-      const double gk = fma(a.A, a.Gk[o], dt * fma(-to_f64(acc[c]), iJ, src[c]));
+      const size_t o = o0 + (size_t)c * P;
+      const double gk = fma(a.A, a.Gk[o], dt * fma(-acc[c], iJ, src[c]));
+      a.Gk[o] = gk;
+      a.Uw[o] = fma(a.B, gk, q[c]);
+    }
+  } else {
+    // FP32 operator: the register G (an O(dt R) increment, stored in FP64) is
+    // accumulated in FP32 with the FP32 1/J; only U + B G is an FP64 operation.
+    // G's rounding (2^-24 of dt |R|) is far below the operator's own FP32
+    // error, and the FP64 pipe is left to the state update.
+    const R iJ = metrics[(size_t)e * 10 * P + 9 * P + id];
+    const R dtf = to_op<R>(a.clock[1]), Af = to_op<R>(a.A);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const size_t o = o0 + (size_t)c * P;
+      const double gk = to_f64(fma(Af, to_op<R>(a.Gk[o]), dtf * fma(-acc[c], iJ, src[c])));
       a.Gk[o] = gk;
       a.Uw[o] = fma(a.B, gk, q[c]);
     }
