@@ -337,24 +337,35 @@ def run_ensemble(args, local):
 def run_pid(args, local):
     """Free-stream PID runs in the setups of the paper's performance section:
     16.78 M DOF at N=3 (64^3 Cartesian elements; the paper's node-level PID
-    comparison, there on Gauss nodes) and N=9 at 20^3 elements (8.0 M DOF,
+    comparison, run there on Gauss nodes) and N=9 at 20^3 elements (8.0 M DOF,
     the per-GPU load of the paper's weak-scaling runs of the split-form LGL
-    operator), 10 LSERK4-5 steps each, FP64 and FP32 operator.  Uniform flow
+    operator), 10 LSERK4-5 steps each: LGL split form in FP64 and with the FP32
+    operator, Gauss nodes (standard weak form) in FP64.  Uniform flow
     rho = 1, u = (0.1, 0.05, 0.02), p = 1/gamma, mu = 1/1600; every kernel
     does its full work on it.  Reports DOF*stage/s, PID and the free-stream
     preservation error max|U - U0| / max|U0| after the steps."""
     import torch
     import paper_2605_28627_gb300 as dg
     from workloads import box_mesh
-    cases = (("N3_64cubed", 3, 64), ("N9_20cubed", 9, 20))
+    cases = (("N3_64cubed", 3, 64, dg.NODES_LGL), ("N3_64cubed_gauss", 3, 64, dg.NODES_LG),
+             ("N9_20cubed", 9, 20, dg.NODES_LGL), ("N9_20cubed_gauss", 9, 20, dg.NODES_LG))
+    if args.pid_cases:
+        keep = args.pid_cases.split(",")
+        cases = tuple(c for c in cases if c[0] in keep)
+    if args.pid_K:   # smaller meshes of the same cases (for profiler captures)
+        cases = tuple(("N%d_%dcubed%s" % (N, args.pid_K, "_gauss" if nd == dg.NODES_LG else ""), N, args.pid_K, nd)
+                      for _, N, _, nd in cases)
     gamma, nsteps = 1.4, args.pid_steps
     out = {}
-    for name, N, K in cases:
+    for name, N, K, nodes in cases:
         mesh = box_mesh(K, 1, lo=0.0, hi=2 * math.pi)
         dofs = mesh.n_elems * (N + 1) ** 3
-        res = {"N": N, "elements": mesh.n_elems, "dof": dofs}
-        for prec_name, prec in (("fp64", dg.FP64), ("fp32op", dg.FP32OP)):
-            s = dg.Solver(mesh, N, gamma=gamma, R=1.0, Pr=0.72, mu=1.0 / 1600.0, precision=prec, device=local)
+        res = {"N": N, "elements": mesh.n_elems, "dof": dofs,
+               "nodes": "Legendre-Gauss, standard weak form" if nodes == dg.NODES_LG else "LGL, split form"}
+        precs = (("fp64", dg.FP64),) if nodes == dg.NODES_LG else (("fp64", dg.FP64), ("fp32op", dg.FP32OP))
+        for prec_name, prec in precs:
+            s = dg.Solver(mesh, N, gamma=gamma, R=1.0, Pr=0.72, mu=1.0 / 1600.0, precision=prec, device=local,
+                          nodes=nodes)
             st = torch.cuda.Stream(device="cuda:%d" % local)
             with torch.cuda.stream(st):
                 U = torch.zeros(s.shape, dtype=torch.float64, device="cuda:%d" % local)
@@ -488,6 +499,8 @@ def main():
     ap.add_argument("--adjoint", action="store_true", help="run the 16^3, N=5 discrete-adjoint study")
     ap.add_argument("--pid", action="store_true", help="run the free-stream PID study (N=3 at 64^3, N=9 at 20^3)")
     ap.add_argument("--pid-steps", type=int, default=10)
+    ap.add_argument("--pid-cases", default="", help="comma list of PID case names ('' = all)")
+    ap.add_argument("--pid-K", type=int, default=0, help="elements per direction instead of the cases' own")
     ap.add_argument("--adj-steps", type=int, default=200)
     ap.add_argument("--adj-dirs", type=int, default=32)
     args = ap.parse_args()

@@ -53,6 +53,9 @@ enum { DG_FLUX_LLF = 0, DG_FLUX_EC = 1, DG_FLUX_ROE = 2 };   /* surface Riemann 
                                                               the Harten-Hyman entropy fix (Sec. 3.1) */
 enum { DG_FP64 = 0, DG_FP32OP = 1 };              /* operator arithmetic */
 enum { DG_SOURCE_NONE = 0, DG_SOURCE_MMS = 1 };   /* volume source term */
+enum { DG_NODES_LGL = 0, DG_NODES_LG = 1 };   /* collocation nodes (Sec. 3.1): Legendre-Gauss-Lobatto with the
+                                                  entropy-stable split form, or Legendre-Gauss with the standard
+                                                  weak form (Eqs. 2-3); LG is FP64 only */
 enum { DG_VISC_CONSTANT = 0, DG_VISC_SUTHERLAND = 1 };   /* viscosity law: constant mu, or Sutherland's law
                                                            mu (T/T_ref)^(3/2) (T_ref + S)/(T + S) at each
                                                            node's temperature (the law of the dissipation
@@ -94,6 +97,7 @@ typedef struct {
                                  its FP32 rounding out of the momentum equations.  Ignored in FP64. */
   int32_t visc_law;           /* DG_VISC_CONSTANT (mu above) or DG_VISC_SUTHERLAND (mu = mu(T_ref)) */
   double T_ref, S_suth;       /* Sutherland reference temperature (> 0) and constant (>= 0) */
+  int32_t nodes;              /* DG_NODES_LGL or DG_NODES_LG */
 } dg_params;
 
 /* Build a context on CUDA device `device`: LGL basis, geometry (node

@@ -89,7 +89,7 @@ static dg_status fail(Ctx* c, dg_status st, const char* what, cudaError_t e = cu
 static void release(Ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
-  void* bufs[] = {c->d_D, c->d_metrics, c->d_J, c->d_X, c->d_mms, c->d_facegeo, c->d_metrics_f, c->d_facegeo_f,
+  void* bufs[] = {c->d_D, c->d_metrics, c->d_J, c->d_X, c->d_mms, c->d_Uf, c->d_gf, c->d_lgb, c->d_facegeo, c->d_metrics_f, c->d_facegeo_f,
                   c->d_grad, c->d_fstar, c->d_red, c->d_w, c->d_clock, c->d_U, c->d_G,
                   c->d_adj_qbar, c->d_adj_gbar, c->d_adj_gtil, c->d_adj_fseed, c->d_adj_face, c->d_adj_mu,
                   c->d_adj_stage, c->d_adj_work};
@@ -140,6 +140,10 @@ dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx*
     return fail(nullptr, DG_EINVAL, "dg_init: unknown source");
   if (!(prm->gamma > 1.0) || !(prm->R > 0.0) || !(prm->Pr > 0.0) || !(prm->mu >= 0.0))
     return fail(nullptr, DG_EINVAL, "dg_init: gas constants out of range");
+  if (prm->nodes != DG_NODES_LGL && prm->nodes != DG_NODES_LG)
+    return fail(nullptr, DG_EINVAL, "dg_init: unknown node set");
+  if (prm->nodes == DG_NODES_LG && prm->precision != DG_FP64)
+    return fail(nullptr, DG_EUNSUPPORTED, "dg_init: the Gauss-node operator is built in FP64 only");
   if (prm->visc_law != DG_VISC_CONSTANT && prm->visc_law != DG_VISC_SUTHERLAND)
     return fail(nullptr, DG_EINVAL, "dg_init: unknown viscosity law");
   if (prm->visc_law == DG_VISC_SUTHERLAND && (!(prm->T_ref > 0.0) || !(prm->S_suth >= 0.0)))
@@ -223,6 +227,10 @@ dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx*
       !alloc((void**)&c->d_minmask, sizeof(int), "alloc mask") ||
       !alloc((void**)&c->d_clock, sizeof(double) * 2, "alloc clock") ||
       (prm->source == DG_SOURCE_MMS && !alloc((void**)&c->d_mms, sizeof(double) * E * 2 * P, "alloc source phases")) ||
+      (prm->nodes == DG_NODES_LG &&
+       (!alloc((void**)&c->d_Uf, sizeof(double) * E * 6 * 5 * NN, "alloc face states") ||
+        !alloc((void**)&c->d_gf, sizeof(double) * E * 6 * 12 * NN, "alloc face gradients") ||
+        !alloc((void**)&c->d_lgb, sizeof(double) * (2 * NN + 5 * c->n), "alloc Gauss basis"))) ||
       (prm->precision == DG_FP32OP &&
        (!alloc((void**)&c->d_metrics_f, sizeof(float) * E * 10 * P, "alloc metrics (fp32)") ||
         !alloc((void**)&c->d_facegeo_f, sizeof(float) * c->nfaces * 4 * NN, "alloc facegeo (fp32)"))))
@@ -246,13 +254,25 @@ dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx*
   if (err == cudaSuccess) err = cudaMemcpyAsync(d_xgeo, mesh->xgeo, sizeof(double) * E * 3 * m3, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemsetAsync(d_bad, 0, sizeof(int), s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_D, c->D.data(), sizeof(double) * NN, cudaMemcpyHostToDevice, s);
-  if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_w, c->w.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice, s);
+  std::vector<double> gtab;
+  if (prm->nodes == DG_NODES_LG) {
+    gauss_table(c->N, c->x, gtab);
+    c->dt_factor = gauss_dt_factor(c->N, c->x, c->w, c->D, gtab);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(c->d_lgb, gtab.data(), sizeof(double) * gtab.size(), cudaMemcpyHostToDevice, s);
+    // quadrature weights of the Gauss nodes for the integrals
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(c->d_w, gtab.data() + 2 * NN + 4 * c->n, sizeof(double) * c->n, cudaMemcpyHostToDevice, s);
+  } else if (err == cudaSuccess) {
+    err = cudaMemcpyAsync(c->d_w, c->w.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice, s);
+  }
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_minmask, &minmask, sizeof(int), cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_faces, faces.data(), sizeof(FaceInfo) * c->nfaces, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_elem_face, elem_face.data(), sizeof(int) * E * 6, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_elem_nbr, elem_nbr.data(), sizeof(int) * E * 6, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = setup_kernels(c->N);
   if (err == cudaSuccess) err = build_geometry(*c, d_xgeo, mesh->ngeo, d_bad, s);
+  if (err == cudaSuccess && prm->nodes == DG_NODES_LG) err = gauss_geometry(*c, d_bad, s);
   if (err == cudaSuccess && prm->source == DG_SOURCE_MMS) err = launch_mms_phase(*c, s);
   if (err == cudaSuccess && prm->precision == DG_FP32OP) {
     err = launch_to_float(c->d_metrics, c->d_metrics_f, (size_t)E * 10 * P, s);
@@ -380,8 +400,11 @@ dg_status dg_max_dt(dg_ctx* c, const double* dU, double cfl, double dfl, double*
   const double lc = c->h_out[0], lv = c->h_out[1];
   if (!std::isfinite(lc) || !std::isfinite(lv)) return fail(c, DG_ENONFINITE, "dg_max_dt: non-finite value");
   const double h = 2.0 / (2.0 * c->N + 1.0);
-  double dt = lc > 0.0 ? cfl * h / lc : HUGE_VAL;
-  if (lv > 0.0) dt = std::fmin(dt, dfl * h * h / lv);
+  // node-set factor on the convective bound, its square on the viscous one
+  // (the second-derivative operator's spectral radius scales as the square)
+  const double fa = c->dt_factor;
+  double dt = lc > 0.0 ? fa * cfl * h / lc : HUGE_VAL;
+  if (lv > 0.0) dt = std::fmin(dt, fa * fa * dfl * h * h / lv);
   *host_dt = dt;
   return DG_OK;
 }

@@ -457,6 +457,10 @@ dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune
       delete e;
       return DG_EINVAL;
     }
+    if (c->prm.nodes != DG_NODES_LGL) {   // the ensemble kernels are the LGL split-form ones
+      delete e;
+      return DG_EUNSUPPORTED;
+    }
     e->members.push_back(c);
   }
   if (cudaSetDevice(e->device) != cudaSuccess) { delete e; return DG_ECUDA; }

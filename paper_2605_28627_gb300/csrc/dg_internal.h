@@ -80,6 +80,7 @@ struct Ctx {
   dg_params prm{};
   Gas gas{};
   std::vector<double> x, w, D;   // host LGL basis
+  double dt_factor = 1.0;        // time-step factor of the node set (Gauss: < 1)
   // device geometry
   double* d_D = nullptr;         // [n][n]
   double* d_metrics = nullptr;   // [E][10][P]: J a^d_l at row d*3+l, row 9 = 1/J
@@ -95,9 +96,13 @@ struct Ctx {
   // work buffers
   void* d_grad = nullptr;        // [E][12][P]: d phi / d x_l, phi = (u, v, w, T), row phi*3+l (operator type)
   void* d_fstar = nullptr;       // [F][5][NN]: surface flux times sJ, master orientation (operator type)
+  // Gauss nodes only
+  double* d_Uf = nullptr;        // [E][6][5][NN]: face values of U from each element
+  double* d_gf = nullptr;        // [E][6][12][NN]: face values of the lifted gradients
+  double* d_lgb = nullptr;       // Gauss basis table (layout GaussTab in dg_gauss.cu)
   double* d_red = nullptr;       // reduction partials [red_len + 1][9]; the last row holds the fold
   int red_len = 0;               // maximum number of partial rows
-  double* d_w = nullptr;         // [n] LGL weights
+  double* d_w = nullptr;         // [n] quadrature weights of the node set
   int* d_minmask = nullptr;      // bit a set: value a of the integrals is a minimum
   double* d_clock = nullptr;     // {t, dt}
   double* h_clock = nullptr;     // pinned staging for the clock
@@ -128,6 +133,15 @@ cudaError_t launch_lift_fp64(const Ctx& c, const double* U, cudaStream_t s);   /
 cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s);
 cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s);
 cudaError_t setup_kernels(int N);
+// Gauss-node operator (dg_gauss.cu)
+void gauss_table(int N, const std::vector<double>& xl, std::vector<double>& tab);
+double gauss_dt_factor(int N, const std::vector<double>& xl, const std::vector<double>& wl,
+                       const std::vector<double>& Dl, const std::vector<double>& tab);
+cudaError_t setup_gauss(int N);
+cudaError_t gauss_geometry(Ctx& c, int* d_bad, cudaStream_t s);
+cudaError_t launch_lift_lg(const Ctx& c, const double* U, cudaStream_t s);
+cudaError_t launch_face_lg(const Ctx& c, cudaStream_t s);
+cudaError_t launch_volume_lg(const Ctx& c, const StageArgs& a, cudaStream_t s);
 cudaError_t setup_volume(int N);
 
 // Geometry kernels (dg_geometry.cu).

@@ -63,11 +63,23 @@ static cudaError_t face_N(const Ctx& c, const double* U, cudaStream_t s) {
     default: return cudaErrorInvalidValue;   \
   }
 
+// On Gauss nodes the lifting launcher also computes the face values of U
+// first (k_prolong_lg), and the face kernel works on face values.
 cudaError_t launch_lift(const Ctx& c, const double* U, cudaStream_t s) {
+  if (c.prm.nodes == DG_NODES_LG) return launch_lift_lg(c, U, s);
   DG_DISPATCH(lift_N, c, U, c.prm.precision != DG_FP32OP, s)
 }
-cudaError_t launch_lift_fp64(const Ctx& c, const double* U, cudaStream_t s) { DG_DISPATCH(lift_N, c, U, true, s) }
-cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s) { DG_DISPATCH(face_N, c, U, s) }
-cudaError_t setup_kernels(int N) { return setup_volume(N); }
+cudaError_t launch_lift_fp64(const Ctx& c, const double* U, cudaStream_t s) {
+  if (c.prm.nodes == DG_NODES_LG) return launch_lift_lg(c, U, s);
+  DG_DISPATCH(lift_N, c, U, true, s)
+}
+cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s) {
+  if (c.prm.nodes == DG_NODES_LG) return launch_face_lg(c, s);
+  DG_DISPATCH(face_N, c, U, s)
+}
+cudaError_t setup_kernels(int N) {
+  cudaError_t e = setup_volume(N);
+  return e == cudaSuccess ? setup_gauss(N) : e;
+}
 
 }  // namespace dg

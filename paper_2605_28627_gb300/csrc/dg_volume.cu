@@ -49,6 +49,7 @@ static cudaError_t setup_any() {
 }
 
 cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s) {
+  if (c.prm.nodes == DG_NODES_LG) return launch_volume_lg(c, a, s);
   switch (c.N) {
     case 1: return volume_any<1>(c, a, s);
     case 2: return volume_any<2>(c, a, s);

@@ -1,0 +1,175 @@
+"""Gauss-node operator (standard weak-form DGSEM, GALAEXI Sec. 3.1 Eqs. 2-3)
+on the GPU against the Gauss-node oracle, element by element, through the C
+ABI: geometry at Gauss nodes and face points, R(U) for LLF, EC and Roe faces,
+the manufactured source, ten LSERK4-5 steps, the integrals, and the options
+the Gauss path rejects.  Same bars as the LGL parity tests."""
+import math
+
+import numpy as np
+import pytest
+
+from workloads import box_mesh, mms_params, random_state, tgv_params
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL_R = 1e-12
+RTOL_RK = 1e-10
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import paper_2605_28627_gb300 as m
+    m.load()
+    return m
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _geo_amp(orc, N, ngeo):
+    """Rounding growth of the equispaced-sample interpolation (kappa^3 / 300,
+    at least 1), as in the LGL parity tests."""
+    x, _, _ = orc.basis(N)
+    xe = np.linspace(-1.0, 1.0, ngeo + 1)
+    V = np.array([[np.prod([(xi - xe[m]) / (xe[j] - xe[m]) for m in range(ngeo + 1) if m != j])
+                   for j in range(ngeo + 1)] for xi in x])
+    return max(1.0, np.abs(V).sum(1).max() ** 3 / 300.0)
+
+
+def _state(mesh, N, seed):
+    # admissible after extrapolation to the faces (|l_j(+-1)| sums grow with N)
+    return random_state(mesh.n_elems, N, seed=seed, rho=(0.95, 1.05), vel=0.2, p=(0.95, 1.05))
+
+
+def _rel_err(got, ref):
+    got = got.reshape(got.shape[0], 5, -1)
+    ref = ref.reshape(ref.shape[0], 5, -1)
+    return np.array([np.abs(got[:, v] - ref[:, v]).max() / max(np.abs(ref[:, v]).max(), 1e-300) for v in range(5)])
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 7, 9])
+def test_gauss_geometry_parity(orc, dg, N):
+    mesh = box_mesh(3 if N < 5 else 2, N, deform="sinprod", rotate_seed=800 + N)
+    o = orc.Oracle(mesh, N, nodes=1)
+    s = dg.Solver(mesh, N, nodes=dg.NODES_LG)
+    X, Ja, J = o.geometry()
+    Jag, Jg = s.geometry()
+    amp = _geo_amp(orc, N, N)
+    np.testing.assert_allclose(s.node_coords().cpu().numpy(), X, rtol=0, atol=1e-14 * amp)
+    np.testing.assert_allclose(Jg.cpu().numpy(), J, rtol=1e-12 * amp, atol=0)
+    scale = np.abs(Ja).max() * max(1.0, np.abs(X).max())
+    assert np.abs(Jag.cpu().numpy() - Ja).max() <= 1e-12 * amp * scale
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("flux", [0, 1, 2])
+def test_gauss_time_derivative_parity(orc, dg, N, flux):
+    K = 3 if N <= 4 else 2
+    mesh = box_mesh(K, N, deform="sinprod", rotate_seed=900 + N)
+    o = orc.Oracle(mesh, N, mu=0.02, surf_flux=flux, nodes=1)
+    s = dg.Solver(mesh, N, mu=0.02, surf_flux=flux, nodes=dg.NODES_LG)
+    U = _state(mesh, N, 1000 + N)
+    err = _rel_err(s.time_derivative(_cuda(U)).cpu().numpy(), o.time_derivative(U))
+    assert (err < RTOL_R * _geo_amp(orc, N, N)).all(), err
+
+
+def test_gauss_free_stream_on_gpu(dg):
+    N = 5
+    mesh = box_mesh(3, N, deform="sinprod", rotate_seed=71)
+    s = dg.Solver(mesh, N, mu=0.01, nodes=dg.NODES_LG)
+    U = np.zeros(s.shape)
+    r, u, p = 1.2, np.array([0.3, -0.2, 0.45]), 0.9
+    U[:, 0] = r
+    U[:, 1:4] = (r * u)[None, :, None, None, None]
+    U[:, 4] = p / 0.4 + 0.5 * r * u @ u
+    assert np.abs(s.time_derivative(_cuda(U)).cpu().numpy()).max() < 2e-12 * N * N
+
+
+@pytest.mark.parametrize("N", [3, 7])
+def test_gauss_mms_rk_parity(orc, dg, N):
+    prm = mms_params()
+    mesh = box_mesh(3 if N < 7 else 2, N, deform="sinprod", rotate_seed=20260528)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1)
+    o = orc.Oracle(mesh, N, nodes=1, **kw)
+    s = dg.Solver(mesh, N, nodes=dg.NODES_LG, **kw)
+    U0 = o.initial_state("mms", 0.0)
+    np.testing.assert_allclose(s.initial_state("mms", 0.0).cpu().numpy(), U0, rtol=1e-14, atol=1e-14)
+    ref = o.rk_steps(U0, 0.0, 1e-3, 10)
+    Ud = _cuda(U0)
+    G = torch.empty_like(Ud)
+    s.rk_step(Ud, G, 0.0, 1e-3, 4)
+    s.rk_step(Ud, G, 4e-3, 1e-3, 6)
+    assert np.abs(Ud.cpu().numpy() - ref).max() / np.abs(ref).max() < RTOL_RK
+
+
+def test_gauss_integrals_parity(orc, dg):
+    prm = tgv_params(Ma=0.1, Re=1600.0)
+    N = 4
+    mesh = box_mesh(3, 1, lo=0.0, hi=2 * math.pi)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"])
+    o = orc.Oracle(mesh, N, nodes=1, **kw)
+    s = dg.Solver(mesh, N, nodes=dg.NODES_LG, **kw)
+    U = o.initial_state("tgv", prm["p0"])
+    Io, Ig = o.integrals(U), s.integrals(_cuda(U))
+    for a in (0, 4, 5, 6, 7):
+        assert abs(Ig[a] - Io[a]) <= 1e-12 * abs(Io[a]), (a, Ig[a], Io[a])
+    for a in (1, 2, 3):
+        assert abs(Ig[a] - Io[a]) <= 1e-12 * abs(Io[0])
+
+
+def test_gauss_rejections(dg):
+    mesh = box_mesh(2, 2)
+    with pytest.raises(dg.DGError):
+        dg.Solver(mesh, 2, nodes=dg.NODES_LG, precision=dg.FP32OP)
+    s = dg.Solver(mesh, 2, mu=0.01, nodes=dg.NODES_LG)
+    U = torch.from_numpy(_state(mesh, 2, 5)).cuda()
+    with pytest.raises(dg.DGError):
+        s.time_derivative_vjp(U, torch.ones_like(U))
+    with pytest.raises(dg.DGError):
+        dg.Ensemble([s])
+
+
+def _dg1d_radius(w, D, lm, lp, K=8):
+    """Spectral radius of the 1-D upwind DG operator of u_t + u_x = 0 on K
+    periodic elements (weak form with the node set's quadrature), from the
+    eigenvalues."""
+    n = len(w)
+    A = np.zeros((n * K, n * K))
+    for e in range(K):
+        el = (e - 1) % K
+        for i in range(n):
+            for m in range(n):
+                A[e * n + i, e * n + m] += w[m] / w[i] * D[m, i] - lp[i] / w[i] * lp[m]
+                A[e * n + i, el * n + m] += lm[i] / w[i] * lp[m]
+    return np.abs(np.linalg.eigvals(A)).max()
+
+
+@pytest.mark.parametrize("N", [3, 9])
+def test_gauss_time_step_factor_and_stability(orc, dg, N):
+    """max_dt on Gauss nodes = the LGL bound times rho_LGL / rho_LG of the 1-D
+    upwind DG operators (here from their eigenvalues), and a perturbed uniform
+    flow stays bounded over 20 steps at CFL 0.9."""
+    n = N + 1
+    xl, wl, Dl = orc.basis(N)
+    eL, eR = np.zeros(n), np.zeros(n)
+    eL[0], eR[-1] = 1.0, 1.0
+    _, wg, Dg, lm, lp = orc.gauss_basis(N)
+    ratio = _dg1d_radius(wl, Dl, eL, eR) / _dg1d_radius(wg, Dg, lm, lp)
+    mesh = box_mesh(3, 1, lo=0.0, hi=2 * math.pi)
+    s_l = dg.Solver(mesh, N, mu=1.0 / 1600.0)
+    s_g = dg.Solver(mesh, N, mu=1.0 / 1600.0, nodes=dg.NODES_LG)
+    U = np.zeros(s_g.shape)
+    u = np.array([0.1, 0.05, 0.02])
+    U[:, 0] = 1.0
+    U[:, 1:4] = u[None, :, None, None, None]
+    U[:, 4] = 1.0 / 1.4 / 0.4 + 0.5 * u @ u
+    Ud = _cuda(U)
+    dt_l, dt_g = s_l.max_dt(Ud, cfl=0.9, dfl=0.9), s_g.max_dt(Ud, cfl=0.9, dfl=0.9)
+    assert abs(dt_g / dt_l / ratio - 1.0) < 2e-3, (dt_g / dt_l, ratio)
+    rng = np.random.default_rng(N)
+    Up = _cuda(U + 1e-10 * rng.standard_normal(U.shape))
+    G = torch.empty_like(Up)
+    s_g.rk_step(Up, G, 0.0, dt_g, 20)
+    assert np.abs(Up.cpu().numpy() - U).max() < 1e-8
