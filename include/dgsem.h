@@ -100,12 +100,15 @@ typedef struct {
   int32_t nodes;              /* DG_NODES_LGL or DG_NODES_LG */
 } dg_params;
 
-/* Build a context on CUDA device `device`: LGL basis, geometry (node
- * positions, curl-form metric terms, Jacobian, face normals) computed on the
- * GPU from the mesh, face maps and work buffers.  Synchronous.
- * Errors: DG_EINVAL (null/size), DG_EUNSUPPORTED (N), DG_EMESH (connectivity
- * out of range or not reciprocal, Jacobian <= 0 at a node), DG_ENOMEM,
- * DG_ECUDA.  On failure *out is NULL. */
+/* Build a context on CUDA device `device`: basis of the node set, geometry
+ * (node positions, curl-form metric terms, Jacobian, face normals) computed on
+ * the GPU from the mesh, face maps and work buffers.  On Gauss nodes the
+ * metric terms are those of the LGL construction evaluated at the Gauss nodes
+ * and face points (Sec. 3.1 leaves this open).  Synchronous.
+ * Errors: DG_EINVAL (null/size, unknown option, constants out of range),
+ * DG_EUNSUPPORTED (N outside 1..9, Gauss nodes with DG_FP32OP), DG_EMESH
+ * (connectivity out of range or not reciprocal, Jacobian <= 0 at a node),
+ * DG_ENOMEM, DG_ECUDA.  On failure *out is NULL. */
 dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out);
 
 /* Free everything the context owns.  Synchronises the device. */
@@ -158,9 +161,12 @@ dg_status dg_geometry(dg_ctx* ctx, double* dJa, double* dJ, dg_stream stream);
 
 /* ---- Discrete adjoint (FP64 contexts) -------------------------------------
  * Hand-written reverse-mode kernels of the discrete operator: the exact
- * transpose of the FP64 R(U) of dg_time_derivative (branches of the LLF speed
- * maximum, |.| and the log-mean switch follow the primal state).  The paper
- * has no adjoint; these entries exist for gradient-based use of the solver.
+ * transpose of the FP64 R(U) of dg_time_derivative (branches of |.| and the
+ * log-mean switch follow the primal state; at a kink of the LLF speed maximum
+ * the mean of the one-sided derivatives is taken).  The paper has no
+ * adjoint; these entries exist for gradient-based use of the solver.  Built
+ * for LGL nodes, the LLF and EC surface fluxes and constant viscosity; other
+ * contexts get DG_EUNSUPPORTED.
  * dJdmu, where present, is a device double that is ACCUMULATED (+=) with
  * lambda . dR/dmu (R is linear in the constant viscosity mu); NULL skips it. */
 
@@ -203,7 +209,9 @@ dg_status dg_set_viscosity(dg_ctx* ctx, double mu);
 typedef struct dg_ensemble dg_ensemble;
 
 /* The members stay owned by the caller and must outlive the ensemble.
- * DG_EINVAL if a member is NULL or on another device or precision. */
+ * DG_EINVAL if a member is NULL or on another device or precision;
+ * DG_EUNSUPPORTED for a member on Gauss nodes (the ensemble kernels are the
+ * LGL split-form ones). */
 dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune_cache_path, dg_ensemble** out);
 dg_status dg_ensemble_destroy(dg_ensemble* ens);
 
