@@ -173,3 +173,33 @@ def test_gauss_time_step_factor_and_stability(orc, dg, N):
     G = torch.empty_like(Up)
     s_g.rk_step(Up, G, 0.0, dt_g, 20)
     assert np.abs(Up.cpu().numpy() - U).max() < 1e-8
+
+
+def test_gauss_full_size_pid_mesh_properties(dg):
+    """At the full size of the free-stream PID run (64^3 elements, N=3, 16.78 M
+    DOF, Gauss nodes), properties that hold at any size: a uniform flow stays
+    uniform, and with nodal noise on it the five conservation totals do not
+    change over two LSERK4-5 steps (periodic box, no source)."""
+    N, K = 3, 64
+    mesh = box_mesh(K, 1, lo=0.0, hi=2 * math.pi)
+    s = dg.Solver(mesh, N, mu=1.0 / 1600.0, nodes=dg.NODES_LG)
+    U = torch.zeros(s.shape, dtype=torch.float64, device="cuda")
+    u = (0.1, 0.05, 0.02)
+    U[:, 0] = 1.0
+    for a in range(3):
+        U[:, 1 + a] = u[a]
+    U[:, 4] = 1.0 / 1.4 / 0.4 + 0.5 * sum(c * c for c in u)
+    U0 = U.clone()
+    dt = s.max_dt(U, cfl=0.9, dfl=0.9)
+    G = torch.empty_like(U)
+    s.rk_step(U, G, 0.0, dt, 2)
+    assert float((U - U0).abs().max()) < 1e-13 * float(U0.abs().max())
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    V = U0 * (1.0 + 1e-3 * torch.randn(U0.shape, generator=gen, device="cuda", dtype=torch.float64))
+    I0 = s.integrals(V)
+    s.rk_step(V, G, 0.0, dt, 2)
+    I1 = s.integrals(V)
+    for a in range(5):
+        assert abs(I1[a] - I0[a]) <= 1e-12 * abs(I0[0] if a in (1, 2, 3) else I0[a]), (a, I0[a], I1[a])
+    del U, U0, V, G
+    s.close()
