@@ -27,7 +27,8 @@
 //    lambda = mu(T) c_p / Pr.
 //  * Derivatives at the kinks of the LLF speed max(|u.n| + c) (ties, u.n = 0,
 //    to within 1e-12 of the local scale) are the mean of the one-sided ones.
-//  * LSERK4-5 of Carpenter and Kennedy (1994), 2N storage.
+//  * LSERK4-5 of Carpenter and Kennedy (1994), or RK4-14 of Niegemann, Diehl
+//    and Busch (2012), 2N storage.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -199,6 +200,7 @@ struct GaussBasis {
 struct Ctx {
   int N, n, P, E;
   int nodes;                  // 0: LGL (split form), 1: Legendre-Gauss (standard weak form)
+  int rk;                     // 0: LSERK4-5, 1: RK4-14
   Params prm;
   Basis b;
   GaussBasis g;
@@ -799,6 +801,23 @@ static const double RK_B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.
 static const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
                                2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
 
+// RK4-14 of Niegemann, Diehl & Busch (2012), 2N storage, fourteen stages
+// (the paper's alternative scheme, Sec. 3.1), to the published sixteen digits.
+static const double RK14_A[14] = {0.0, -0.7188012108672410, -0.7785331173421570, -0.0053282796654044,
+                                  -0.8552979934029281, -3.9564138245774565, -1.5780575380587385,
+                                  -2.0837094552574054, -0.7483334182761610, -0.7032861106563359,
+                                  0.0013917096117681, -0.0932075369637460, -0.9514200470875948,
+                                  -7.1151571693922548};
+static const double RK14_B[14] = {0.0367762454319673, 0.3136296607553959, 0.1531848691869027, 0.0030097086818182,
+                                  0.3326293790646110, 0.2440251405350864, 0.3718879239592277, 0.6204126221582444,
+                                  0.1524043173028741, 0.0760894927419266, 0.0077604214040978, 0.0024647284755382,
+                                  0.0780348340049386, 5.5059777270269628};
+static const double RK14_C[14] = {0.0, 0.0367762454319673, 0.1249685262725025, 0.2446177702277698,
+                                  0.2476149531070420, 0.2969311120382472, 0.3978149645802642,
+                                  0.5270854589440328, 0.6981269994175695, 0.8190890835352128,
+                                  0.8527059887098624, 0.8604711817462826, 0.8627060376969976,
+                                  0.8734213127600976};
+
 static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double mu);
 
 // R(U) on the context's node set (the Gauss-node operator is FP64 only).
@@ -810,17 +829,22 @@ static void rhs_any(const Ctx& c, const T* U, T* Ut, double t, T mu) {
   rhs(c, U, Ut, t, mu);
 }
 
+// nsteps steps of the context's 2N-storage scheme (RK4-5 or RK4-14).
 template <class T>
 static void rk_steps(const Ctx& c, T* U, double t, double dt, int nsteps, T mu) {
   size_t len = (size_t)c.E * 5 * c.P;
+  const int ns = c.rk == 1 ? 14 : 5;
+  const double* rA = c.rk == 1 ? RK14_A : RK_A;
+  const double* rB = c.rk == 1 ? RK14_B : RK_B;
+  const double* rC = c.rk == 1 ? RK14_C : RK_C;
   std::vector<T> G(len), Ut(len);
   for (int st = 0; st < nsteps; ++st) {
     for (size_t a = 0; a < len; ++a) G[a] = T(0.0);
-    for (int s = 0; s < 5; ++s) {
-      rhs_any(c, U, Ut.data(), t + RK_C[s] * dt, mu);
+    for (int s = 0; s < ns; ++s) {
+      rhs_any(c, U, Ut.data(), t + rC[s] * dt, mu);
       for (size_t a = 0; a < len; ++a) {
-        G[a] = RK_A[s] * G[a] + dt * Ut[a];
-        U[a] = U[a] + RK_B[s] * G[a];
+        G[a] = rA[s] * G[a] + dt * Ut[a];
+        U[a] = U[a] + rB[s] * G[a];
       }
     }
     t += dt;
@@ -1260,6 +1284,7 @@ void* orc_create(int N, int n_elems, int ngeo, const double* xgeo, const int* fa
   c->prm.mms_amp = prm[4];
   c->prm.visc_law = (int)prm[5]; c->prm.T_ref = prm[6]; c->prm.S_suth = prm[7];
   c->nodes = (int)prm[8];
+  c->rk = (int)prm[9];
   c->prm.surf_flux = surf_flux; c->prm.source = source; c->prm.vol_flux = 0;
   if (c->prm.visc_law != 0 && c->prm.visc_law != 1) {
     if (errbuf && errlen > 0) std::snprintf(errbuf, errlen, "unknown viscosity law %d", c->prm.visc_law);
@@ -1268,6 +1293,7 @@ void* orc_create(int N, int n_elems, int ngeo, const double* xgeo, const int* fa
   }
   c->b = make_basis(N);
   if (c->nodes != 0 && c->nodes != 1) c->err = "unknown node set";
+  if (c->rk != 0 && c->rk != 1) c->err = "unknown Runge-Kutta scheme";
   if (!c->err.empty() || !build_geometry(*c, ngeo, xgeo) || !build_faces(*c, face_nbr)) {
     if (errbuf && errlen > 0) std::snprintf(errbuf, errlen, "%s", c->err.c_str());
     delete c;
@@ -1388,6 +1414,11 @@ void orc_rk_steps_tl(void* h, double* U, double* dU, double dmu, double t, doubl
 
 void orc_rk_coeffs(double* A, double* B, double* C) {
   std::memcpy(A, RK_A, sizeof(RK_A)); std::memcpy(B, RK_B, sizeof(RK_B)); std::memcpy(C, RK_C, sizeof(RK_C));
+}
+
+// Coefficients of RK4-14 (14 values each).
+void orc_rk14_coeffs(double* A, double* B, double* C) {
+  std::memcpy(A, RK14_A, sizeof(RK14_A)); std::memcpy(B, RK14_B, sizeof(RK14_B)); std::memcpy(C, RK14_C, sizeof(RK14_C));
 }
 
 // Two-point flux, LLF flux and log mean exposed for the pin tests.

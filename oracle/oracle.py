@@ -53,6 +53,7 @@ def _load():
     L.orc_rk_steps.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, C.c_int]
     L.orc_rk_steps_tl.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_double, C.c_double, C.c_int]
     L.orc_rk_coeffs.argtypes = [_dp, _dp, _dp]
+    L.orc_rk14_coeffs.argtypes = [_dp, _dp, _dp]
     L.orc_ec_flux.argtypes = [_dp, _dp, _dp, _dp, _dp]
     L.orc_llf_flux.argtypes = [_dp, _dp, _dp, _dp, _dp]
     L.orc_roe_flux.argtypes = [_dp, _dp, _dp, _dp, _dp]
@@ -86,6 +87,13 @@ def basis(N: int):
     return x, w, D.reshape(n, n)
 
 
+def rk14_coeffs():
+    L = _load()
+    A, B, Cc = np.zeros(14), np.zeros(14), np.zeros(14)
+    L.orc_rk14_coeffs(A, B, Cc)
+    return A, B, Cc
+
+
 def rk_coeffs():
     L = _load()
     A, B, Cc = np.zeros(5), np.zeros(5), np.zeros(5)
@@ -93,8 +101,8 @@ def rk_coeffs():
     return A, B, Cc
 
 
-def _prm(gamma, R, Pr, mu, amp=0.1, visc_law=0, T_ref=1.0, S_suth=0.0, nodes=0):
-    return np.array([gamma, R, Pr, mu, amp, visc_law, T_ref, S_suth, nodes], dtype=np.float64)
+def _prm(gamma, R, Pr, mu, amp=0.1, visc_law=0, T_ref=1.0, S_suth=0.0, nodes=0, rk=0):
+    return np.array([gamma, R, Pr, mu, amp, visc_law, T_ref, S_suth, nodes, rk], dtype=np.float64)
 
 
 def ec_flux(qL, qR, nv, gamma=1.4):
@@ -131,11 +139,12 @@ class Oracle:
     visc_law: 0 = constant mu, 1 = Sutherland's law mu (T/T_ref)^1.5 (T_ref + S)/(T + S).
     nodes: 0 = LGL nodes with the split form, 1 = Legendre-Gauss nodes with the
     standard weak form (no tangent-linear).
+    rk: 0 = LSERK4-5 (Carpenter & Kennedy), 1 = RK4-14 (Niegemann et al.).
     """
 
     def __init__(self, mesh, N: int, gamma=1.4, R=1.0, Pr=0.72, mu=0.0,
                  surf_flux: int = 0, source: int = 0, mms_amp: float = 0.1,
-                 visc_law: int = 0, T_ref: float = 1.0, S_suth: float = 0.0, nodes: int = 0):
+                 visc_law: int = 0, T_ref: float = 1.0, S_suth: float = 0.0, nodes: int = 0, rk: int = 0):
         L = _load()
         self.N, self.n, self.P = N, N + 1, (N + 1) ** 3
         self.E = int(mesh.xgeo.shape[0])
@@ -145,7 +154,7 @@ class Oracle:
         nbr = np.ascontiguousarray(mesh.face_nbr, dtype=np.int32)
         err = C.create_string_buffer(256)
         h = L.orc_create(N, self.E, int(mesh.xgeo.shape[-1]) - 1, xgeo, nbr,
-                         _prm(gamma, R, Pr, mu, mms_amp, visc_law, T_ref, S_suth, nodes), surf_flux, source, err,
+                         _prm(gamma, R, Pr, mu, mms_amp, visc_law, T_ref, S_suth, nodes, rk), surf_flux, source, err,
                          256)
         if not h:
             raise ValueError("oracle: " + err.value.decode())

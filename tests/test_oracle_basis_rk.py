@@ -109,3 +109,55 @@ def test_lserk_time_order_on_dg_system(orc):
         errs.append(np.abs(o.rk_steps(U0, 0.0, T / nst, nst) - ref).max())
     eoc = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert min(eoc) > 3.6, (errs, eoc)
+
+
+def test_rk414_coefficients_and_order(orc):
+    """RK4-14 (Niegemann, Diehl & Busch 2012): the oracle's table equals the
+    published sixteen digits; with those decimals taken exactly, the stage
+    times are the row sums of the Butcher form, the eight conditions of order
+    four hold to the rounding of the sixteenth digit, and a fifth-order
+    condition fails."""
+    gold = json.load(open(os.path.join(GOLD, "rk414_niegemann.json")))
+    A, B, Cc = orc.rk14_coeffs()
+    fA = [Fraction(s) for s in gold["A"]]
+    fB = [Fraction(s) for s in gold["B"]]
+    fC = [Fraction(s) for s in gold["c"]]
+    np.testing.assert_allclose(A, [float(v) for v in fA], rtol=1e-16, atol=0)
+    np.testing.assert_allclose(B, [float(v) for v in fB], rtol=1e-16, atol=0)
+    np.testing.assert_allclose(Cc, [float(v) for v in fC], rtol=1e-16, atol=0)
+    a, b = _butcher_from_2n(fA, fB)
+    s = range(14)
+    c = [sum(r, Fraction(0)) for r in a]
+    for i in s:
+        assert abs(float(c[i] - fC[i])) < 2e-15, i
+    conds = [
+        (sum(b[i] for i in s), 1),
+        (sum(b[i] * c[i] for i in s), Fraction(1, 2)),
+        (sum(b[i] * c[i] ** 2 for i in s), Fraction(1, 3)),
+        (sum(b[i] * a[i][j] * c[j] for i in s for j in s), Fraction(1, 6)),
+        (sum(b[i] * c[i] ** 3 for i in s), Fraction(1, 4)),
+        (sum(b[i] * c[i] * a[i][j] * c[j] for i in s for j in s), Fraction(1, 8)),
+        (sum(b[i] * a[i][j] * c[j] ** 2 for i in s for j in s), Fraction(1, 12)),
+        (sum(b[i] * a[i][j] * a[j][k] * c[k] for i in s for j in s for k in s), Fraction(1, 24)),
+    ]
+    for got, want in conds:
+        assert abs(float(got - want)) < 5e-15, float(got - want)
+    assert abs(float(sum(b[i] * c[i] ** 4 for i in s) - Fraction(1, 5))) > 1e-6
+
+
+def test_rk414_time_order_on_dg_system(orc):
+    """Observed fourth-order convergence in dt of the oracle's RK4-14 loop, and
+    agreement with RK4-5 to the schemes' truncation error."""
+    from workloads import box_mesh, tgv_params
+    prm = tgv_params(Ma=0.3, Re=100.0)
+    m = box_mesh(2, 2, lo=0.0, hi=2 * np.pi)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"])
+    o = orc.Oracle(m, 2, rk=1, **kw)
+    U0 = o.initial_state("tgv", prm["p0"])
+    T = 0.4
+    ref = o.rk_steps(U0, 0.0, T / 32, 32)
+    errs = [np.abs(o.rk_steps(U0, 0.0, T / nst, nst) - ref).max() for nst in (2, 4, 8)]
+    eoc = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(eoc) > 3.5, (errs, eoc)
+    ref45 = orc.Oracle(m, 2, **kw).rk_steps(U0, 0.0, T / 64, 64)
+    assert np.abs(ref - ref45).max() < 1e-8 * np.abs(ref45).max()
