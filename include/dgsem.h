@@ -56,6 +56,9 @@ enum { DG_SOURCE_NONE = 0, DG_SOURCE_MMS = 1 };   /* volume source term */
 enum { DG_NODES_LGL = 0, DG_NODES_LG = 1 };   /* collocation nodes (Sec. 3.1): Legendre-Gauss-Lobatto with the
                                                   entropy-stable split form, or Legendre-Gauss with the standard
                                                   weak form (Eqs. 2-3); LG is FP64 only */
+enum { DG_RK45 = 0, DG_RK414 = 1 };   /* 2N-storage time schemes of Sec. 3.1: LSERK4-5 (Carpenter & Kennedy
+                                         1994) or RK4-14 (Niegemann, Diehl & Busch 2012); the stage update
+                                         is the same, the stage count 5 or 14 */
 enum { DG_VISC_CONSTANT = 0, DG_VISC_SUTHERLAND = 1 };   /* viscosity law: constant mu, or Sutherland's law
                                                            mu (T/T_ref)^(3/2) (T_ref + S)/(T + S) at each
                                                            node's temperature (the law of the dissipation
@@ -98,6 +101,7 @@ typedef struct {
   int32_t visc_law;           /* DG_VISC_CONSTANT (mu above) or DG_VISC_SUTHERLAND (mu = mu(T_ref)) */
   double T_ref, S_suth;       /* Sutherland reference temperature (> 0) and constant (>= 0) */
   int32_t nodes;              /* DG_NODES_LGL or DG_NODES_LG */
+  int32_t rk_scheme;          /* DG_RK45 or DG_RK414 (dg_rk_step, dg_advance_host) */
 } dg_params;
 
 /* Build a context on CUDA device `device`: basis of the node set, geometry
@@ -121,7 +125,8 @@ size_t dg_state_len(const dg_ctx* ctx);
  * alias. */
 dg_status dg_time_derivative(dg_ctx* ctx, const double* dU, double* dUt, double t, dg_stream stream);
 
-/* nsteps steps of LSERK4-5 (Sec. 3.1) in place: per stage s,
+/* nsteps steps of the context's 2N-storage scheme (LSERK4-5 or RK4-14,
+ * Sec. 3.1) in place: per stage s,
  *   G <- A_s G + dt R(U, t + c_s dt);  U <- U + B_s G,
  * with G (device, dg_state_len doubles, caller-owned scratch) zeroed at the
  * start of every step.  The sequence of launches is captured once per
@@ -165,8 +170,8 @@ dg_status dg_geometry(dg_ctx* ctx, double* dJa, double* dJ, dg_stream stream);
  * log-mean switch follow the primal state; at a kink of the LLF speed maximum
  * the mean of the one-sided derivatives is taken).  The paper has no
  * adjoint; these entries exist for gradient-based use of the solver.  Built
- * for LGL nodes, the LLF and EC surface fluxes and constant viscosity; other
- * contexts get DG_EUNSUPPORTED.
+ * for LGL nodes, the LLF and EC surface fluxes, constant viscosity and
+ * LSERK4-5; other contexts get DG_EUNSUPPORTED.
  * dJdmu, where present, is a device double that is ACCUMULATED (+=) with
  * lambda . dR/dmu (R is linear in the constant viscosity mu); NULL skips it. */
 
@@ -210,8 +215,8 @@ typedef struct dg_ensemble dg_ensemble;
 
 /* The members stay owned by the caller and must outlive the ensemble.
  * DG_EINVAL if a member is NULL or on another device or precision;
- * DG_EUNSUPPORTED for a member on Gauss nodes (the ensemble kernels are the
- * LGL split-form ones). */
+ * DG_EUNSUPPORTED for a member on Gauss nodes or with RK4-14 (the ensemble
+ * kernels are the LGL split-form ones, its steps LSERK4-5). */
 dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune_cache_path, dg_ensemble** out);
 dg_status dg_ensemble_destroy(dg_ensemble* ens);
 

@@ -26,6 +26,7 @@ FP64, FP32OP = 0, 1
 SOURCE_NONE, SOURCE_MMS = 0, 1
 VISC_CONSTANT, VISC_SUTHERLAND = 0, 1
 NODES_LGL, NODES_LG = 0, 1
+RK45, RK414 = 0, 1
 IC_TGV, IC_MMS = 0, 1
 
 # Every symbol that include/dgsem.h declares.
@@ -52,7 +53,8 @@ class dg_params(C.Structure):
     _fields_ = [("N", C.c_int32), ("gamma", C.c_double), ("R", C.c_double), ("Pr", C.c_double),
                 ("mu", C.c_double), ("surf_flux", C.c_int32), ("precision", C.c_int32),
                 ("source", C.c_int32), ("mms_amp", C.c_double), ("p_ref", C.c_double),
-                ("visc_law", C.c_int32), ("T_ref", C.c_double), ("S_suth", C.c_double), ("nodes", C.c_int32)]
+                ("visc_law", C.c_int32), ("T_ref", C.c_double), ("S_suth", C.c_double), ("nodes", C.c_int32),
+                ("rk_scheme", C.c_int32)]
 
 
 _lib = None
@@ -125,7 +127,8 @@ class Solver:
 
     def __init__(self, mesh, N: int, gamma=1.4, R=1.0, Pr=0.72, mu=0.0, surf_flux=FLUX_LLF,
                  precision=FP64, source=SOURCE_NONE, mms_amp=0.1, device: int = 0, p_ref: float = 0.0,
-                 visc_law: int = VISC_CONSTANT, T_ref: float = 1.0, S_suth: float = 0.0, nodes: int = NODES_LGL):
+                 visc_law: int = VISC_CONSTANT, T_ref: float = 1.0, S_suth: float = 0.0, nodes: int = NODES_LGL,
+                 rk_scheme: int = RK45):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2605_28627_gb300 needs a CUDA GPU; there is no CPU fallback")
@@ -138,7 +141,7 @@ class Solver:
         m = dg_mesh(self.E, int(xgeo.shape[-1]) - 1, xgeo.ctypes.data_as(C.POINTER(C.c_double)),
                     nbr.ctypes.data_as(C.POINTER(C.c_int32)))
         p = dg_params(N, gamma, R, Pr, mu, surf_flux, precision, source, mms_amp, p_ref, visc_law, T_ref, S_suth,
-                      nodes)
+                      nodes, rk_scheme)
         h = C.c_void_p()
         torch.cuda.set_device(device)
         st = self._L.dg_init(C.byref(m), C.byref(p), device, C.byref(h))

@@ -28,6 +28,8 @@ static dg_status ensure_adjoint(Ctx* c) {
   if (c->prm.precision != DG_FP64) return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the FP64 operator");
   if (c->prm.surf_flux == DG_FLUX_ROE)
     return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the LLF and entropy-conservative surface fluxes");
+  if (c->prm.rk_scheme != DG_RK45)
+    return afail(c, DG_EUNSUPPORTED, "the adjoint is built for LSERK4-5");
   if (c->prm.nodes != DG_NODES_LGL)
     return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the LGL operator");
   if (c->prm.visc_law != DG_VISC_CONSTANT)

@@ -107,12 +107,13 @@ static void release(Ctx* c) {
 static cudaError_t enqueue_steps(Ctx& c, double* U, double* G, int nsteps, cudaStream_t s) {
   cudaError_t err = cudaSuccess;
   const size_t bytes = sizeof(double) * (size_t)c.E * 5 * c.P;
+  const RkScheme rk = rk_scheme(c.prm.rk_scheme);
   for (int st = 0; st < nsteps; ++st) {
     if ((err = cudaMemsetAsync(G, 0, bytes, s)) != cudaSuccess) return err;
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < rk.stages; ++k) {
       if ((err = launch_lift(c, U, s)) != cudaSuccess) return err;
       if ((err = launch_face(c, U, s)) != cudaSuccess) return err;
-      StageArgs a{U, U, G, nullptr, c.d_clock, kRkC[k], kRkA[k], kRkB[k], 1};
+      StageArgs a{U, U, G, nullptr, c.d_clock, rk.C[k], rk.A[k], rk.B[k], 1};
       if ((err = launch_volume(c, a, s)) != cudaSuccess) return err;
     }
     if ((err = launch_clock_advance(c.d_clock, s)) != cudaSuccess) return err;
@@ -140,6 +141,8 @@ dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx*
     return fail(nullptr, DG_EINVAL, "dg_init: unknown source");
   if (!(prm->gamma > 1.0) || !(prm->R > 0.0) || !(prm->Pr > 0.0) || !(prm->mu >= 0.0))
     return fail(nullptr, DG_EINVAL, "dg_init: gas constants out of range");
+  if (prm->rk_scheme != DG_RK45 && prm->rk_scheme != DG_RK414)
+    return fail(nullptr, DG_EINVAL, "dg_init: unknown Runge-Kutta scheme");
   if (prm->nodes != DG_NODES_LGL && prm->nodes != DG_NODES_LG)
     return fail(nullptr, DG_EINVAL, "dg_init: unknown node set");
   if (prm->nodes == DG_NODES_LG && prm->precision != DG_FP64)
@@ -448,9 +451,10 @@ dg_status dg_profile_stages(dg_ctx* c, double* dU, double* dG, double dt, int32_
   DG_CUDA(launch_set_clock(c->d_clock, 0.0, dt, s), c, "clock");
   DG_CUDA(cudaMemsetAsync(dG, 0, sizeof(double) * dg_state_len(c), s), c, "memset");
   cudaError_t err = cudaSuccess;
+  const RkScheme rk = rk_scheme(c->prm.rk_scheme);
   for (int r = 0; r < reps && err == cudaSuccess; ++r) {
-    const int k = r % 5;
-    StageArgs a{dU, dU, dG, nullptr, c->d_clock, kRkC[k], kRkA[k], kRkB[k], 1};
+    const int k = r % rk.stages;
+    StageArgs a{dU, dU, dG, nullptr, c->d_clock, rk.C[k], rk.A[k], rk.B[k], 1};
     cudaEventRecord(ev[0], s);
     err = launch_lift(*c, dU, s);
     cudaEventRecord(ev[1], s);

@@ -457,7 +457,7 @@ dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune
       delete e;
       return DG_EINVAL;
     }
-    if (c->prm.nodes != DG_NODES_LGL) {   // the ensemble kernels are the LGL split-form ones
+    if (c->prm.nodes != DG_NODES_LGL || c->prm.rk_scheme != DG_RK45) {   // LGL split form, LSERK4-5
       delete e;
       return DG_EUNSUPPORTED;
     }

@@ -23,6 +23,35 @@ inline constexpr double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677
 inline constexpr double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
                                    2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
 
+// RK4-14 of Niegemann, Diehl & Busch (2012), fourteen stages, 2N storage (the
+// paper's alternative scheme, Sec. 3.1), to the published sixteen digits.
+inline constexpr double kRk14A[14] = {0.0, -0.7188012108672410, -0.7785331173421570, -0.0053282796654044,
+                                      -0.8552979934029281, -3.9564138245774565, -1.5780575380587385,
+                                      -2.0837094552574054, -0.7483334182761610, -0.7032861106563359,
+                                      0.0013917096117681, -0.0932075369637460, -0.9514200470875948,
+                                      -7.1151571693922548};
+inline constexpr double kRk14B[14] = {0.0367762454319673, 0.3136296607553959, 0.1531848691869027,
+                                      0.0030097086818182, 0.3326293790646110, 0.2440251405350864,
+                                      0.3718879239592277, 0.6204126221582444, 0.1524043173028741,
+                                      0.0760894927419266, 0.0077604214040978, 0.0024647284755382,
+                                      0.0780348340049386, 5.5059777270269628};
+inline constexpr double kRk14C[14] = {0.0, 0.0367762454319673, 0.1249685262725025, 0.2446177702277698,
+                                      0.2476149531070420, 0.2969311120382472, 0.3978149645802642,
+                                      0.5270854589440328, 0.6981269994175695, 0.8190890835352128,
+                                      0.8527059887098624, 0.8604711817462826, 0.8627060376969976,
+                                      0.8734213127600976};
+
+// A 2N-storage scheme: number of stages and coefficient tables.
+struct RkScheme {
+  int stages;
+  const double* A;
+  const double* B;
+  const double* C;
+};
+inline RkScheme rk_scheme(int which) {
+  return which == DG_RK414 ? RkScheme{14, kRk14A, kRk14B, kRk14C} : RkScheme{5, kRkA, kRkB, kRkC};
+}
+
 // Gas constants and derived coefficients, passed by value to kernels.
 struct Gas {
   double gamma, R, Pr, mu;

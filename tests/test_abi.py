@@ -34,7 +34,7 @@ def _init(mesh, N=3, **kw):
     nbr = np.ascontiguousarray(mesh.face_nbr, dtype=np.int32)
     m = dg.dg_mesh(xgeo.shape[0], xgeo.shape[-1] - 1, xgeo.ctypes.data_as(C.POINTER(C.c_double)),
                    nbr.ctypes.data_as(C.POINTER(C.c_int32)))
-    prm = dict(N=N, gamma=1.4, R=1.0, Pr=0.72, mu=0.01, surf_flux=0, precision=0, source=0, mms_amp=0.1, p_ref=0.0, visc_law=0, T_ref=1.0, S_suth=0.0, nodes=0)
+    prm = dict(N=N, gamma=1.4, R=1.0, Pr=0.72, mu=0.01, surf_flux=0, precision=0, source=0, mms_amp=0.1, p_ref=0.0, visc_law=0, T_ref=1.0, S_suth=0.0, nodes=0, rk_scheme=0)
     prm.update(kw)
     p = dg.dg_params(**prm)
     h = C.c_void_p()

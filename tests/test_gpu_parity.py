@@ -259,3 +259,25 @@ def test_sutherland_parity(orc, dg, N, flux):
     assert (err < RTOL_R * _geo_amp(orc, N, N)).all(), err
     Ig, Io = s.integrals(_cuda(U)), o.integrals(U)
     assert abs(Ig[6] - Io[6]) <= 1e-12 * abs(Io[6])
+
+
+@pytest.mark.parametrize("nodes", [0, 1])
+def test_rk414_parity(orc, dg, nodes):
+    """Ten RK4-14 steps (fourteen stages each) on the curved MMS mesh against
+    the oracle's RK4-14, on both node sets."""
+    prm = mms_params()
+    N = 4
+    mesh = box_mesh(3, N, deform="sinprod", rotate_seed=20260528)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1, nodes=nodes)
+    o = orc.Oracle(mesh, N, rk=1, **kw)
+    s = dg.Solver(mesh, N, rk_scheme=dg.RK414, **kw)
+    U0 = o.initial_state("mms", 0.0)
+    ref = o.rk_steps(U0, 0.0, 2e-3, 10)
+    Ud = _cuda(U0)
+    G = torch.empty_like(Ud)
+    s.rk_step(Ud, G, 0.0, 2e-3, 3)
+    s.rk_step(Ud, G, 6e-3, 2e-3, 7)
+    assert np.abs(Ud.cpu().numpy() - ref).max() / np.abs(ref).max() < RTOL_RK
+    # the adjoint and the ensemble are built for LSERK4-5
+    with pytest.raises(dg.DGError):
+        s.time_derivative_vjp(Ud, torch.ones_like(Ud))
