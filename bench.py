@@ -279,8 +279,9 @@ def run_ensemble(args, local):
     dofs = [sp["K"] ** 3 * (sp["N"] + 1) ** 3 for sp in specs]
     total = sum(dofs)
     runs = [member(sp, dg.FP32OP) for sp in specs]
-    ens = dg.Ensemble([r[0] for r in runs], tune_cache_path=os.path.join(ROOT, "gpurun_out", "ensemble_tune.txt")
-                      if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    cache_dir = os.path.join(ROOT, "paper_2605_28627_gb300", "_build")
+    ens = dg.Ensemble([r[0] for r in runs],
+                      tune_cache_path=os.path.join(cache_dir, "ensemble_tune.txt") if os.path.isdir(cache_dir) else None)
     Us = [r[1] for r in runs]
     Gs = [torch.empty_like(U) for U in Us]
     dts = [r[2] for r in runs]
@@ -297,6 +298,7 @@ def run_ensemble(args, local):
     e1.record(st)
     e1.synchronize()
     ms_ens = e0.elapsed_time(e1)
+    ek_ens = [r[0].integrals(U, stream=st)[5] for r, U in zip(runs, Us)]
     plan = ens.plan()
     ens.close()
     for r in runs:
@@ -305,23 +307,27 @@ def run_ensemble(args, local):
     torch.cuda.empty_cache()
 
     def sequential(precision):
-        ms_tot = 0.0
+        # the same 1 + 2 nsteps steps as the ensemble members took
+        ms_tot, ek = 0.0, []
         for sp in specs:
             s, U, dt = member(sp, precision)
             G = torch.empty_like(U)
-            s.rk_step(U, G, 0.0, dt, nsteps, stream=st)           # warm-up + graph capture
+            s.rk_step(U, G, 0.0, dt, 1, stream=st)
+            s.rk_step(U, G, dt, dt, nsteps, stream=st)            # warm-up + graph capture
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(st)
-            s.rk_step(U, G, nsteps * dt, dt, nsteps, stream=st)
+            s.rk_step(U, G, (1 + nsteps) * dt, dt, nsteps, stream=st)
             b.record(st)
             b.synchronize()
             ms_tot += a.elapsed_time(b)
+            ek.append(s.integrals(U, stream=st)[5])
             s.close()
             del U, G
-        return ms_tot
+        return ms_tot, ek
 
-    ms_seq64 = sequential(dg.FP64)
-    ms_seq32 = sequential(dg.FP32OP)
+    ms_seq64, ek64 = sequential(dg.FP64)
+    ms_seq32, ek32 = sequential(dg.FP32OP)
+    ek_err = [abs(a - b) / abs(b) for a, b in zip(ek_ens, ek64)]
     rate = total * 5 * nsteps / (ms_ens * 1e-3)
     line = {"experiment": "ensemble of 64 uneven Taylor-Green runs (seed 20260529), FP32 operator / FP64 state, "
                           "%d LSERK4-5 steps in one graph launch" % nsteps,
@@ -329,7 +335,10 @@ def run_ensemble(args, local):
             "ms_per_step": ms_ens / nsteps,
             "sequential_fp64_ms_per_step": ms_seq64 / nsteps, "sequential_fp32op_ms_per_step": ms_seq32 / nsteps,
             "speedup_vs_sequential_fp64": ms_seq64 / ms_ens, "speedup_vs_sequential_fp32op": ms_seq32 / ms_ens,
-            "first_step_with_tuning_s": tune_s, "plan": plan}
+            "first_step_with_tuning_s": tune_s,
+            "ek_rel_err_vs_fp64_max": max(ek_err), "ek_rel_err_vs_fp64_median": float(np.median(ek_err)),
+            "ek_rel_diff_ensemble_vs_sequential_fp32op_max": max(abs(a - b) / abs(b) for a, b in zip(ek_ens, ek32)),
+            "steps_compared": 1 + 2 * nsteps, "plan": plan}
     print(json.dumps(line))
     return 0
 
@@ -599,11 +608,15 @@ def main():
     if args.sweep and rank == 0:
         for Ns in [int(v) for v in args.sweep.split(",") if v]:
             if Ns == N:
-                sweep[str(Ns)] = {"dof_stage_per_s": value / world, "pid_ns": 1e9 * world / value}
+                sweep[str(Ns)] = {"dof_stage_per_s": value / world, "pid_ns": 1e9 * world / value,
+                                  "volume_ms": ms3[2], "volume_roofline_frac": roofline["frac"]}
                 continue
-            ms = sweep_rate(dg, Ns, local, prm)
+            ms, ms3n = sweep_rate(dg, Ns, local, prm)
             dofs = K_ELEMS ** 3 * (Ns + 1) ** 3
-            sweep[str(Ns)] = {"dof_stage_per_s": dofs * 5 / (ms * 1e-3), "pid_ns": ms * 1e6 / (dofs * 5)}
+            # roofline of the volume kernel at this N: algorithmic FP64 flops / its event time
+            ach = volume_flops_per_dof(Ns) * dofs / (ms3n[2] * 1e-3) / 1e12
+            sweep[str(Ns)] = {"dof_stage_per_s": dofs * 5 / (ms * 1e-3), "pid_ns": ms * 1e6 / (dofs * 5),
+                              "volume_ms": ms3n[2], "volume_roofline_frac": ach / fp64_peak}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -671,7 +684,7 @@ def fp32_operator_rate(dg, N, dev, prm, U0, steps, fp64_rate):
 def working_set_mb(s):
     P, NN, E = s.P, s.n * s.n, s.E
     F = 3 * E
-    doubles = E * P * (5 + 5 + 10 + 12 + 3) + F * NN * (4 + 5)
+    doubles = E * P * (5 + 5 + 10 + 12 + 2) + F * NN * (4 + 5)
     return doubles * 8 / 1e6
 
 
@@ -692,8 +705,9 @@ def sweep_rate(dg, N, dev, prm, steps=5):
         s.rk_step(U, G, (3 + i) * DT, DT, 1, stream=st)
     e1.record(st)
     e1.synchronize()
+    ms3 = s.profile_stages(U, G, DT, reps=10, stream=st)
     s.close()
-    return e0.elapsed_time(e1) / steps
+    return e0.elapsed_time(e1) / steps, ms3
 
 
 if __name__ == "__main__":
