@@ -170,8 +170,8 @@ dg_status dg_geometry(dg_ctx* ctx, double* dJa, double* dJ, dg_stream stream);
  * log-mean switch follow the primal state; at a kink of the LLF speed maximum
  * the mean of the one-sided derivatives is taken).  The paper has no
  * adjoint; these entries exist for gradient-based use of the solver.  Built
- * for LGL nodes, the LLF and EC surface fluxes, constant viscosity and
- * LSERK4-5; other contexts get DG_EUNSUPPORTED.
+ * for LGL nodes, the LLF and EC surface fluxes and constant viscosity, for
+ * both time schemes; other contexts get DG_EUNSUPPORTED.
  * dJdmu, where present, is a device double that is ACCUMULATED (+=) with
  * lambda . dR/dmu (R is linear in the constant viscosity mu); NULL skips it. */
 
@@ -179,13 +179,13 @@ dg_status dg_geometry(dg_ctx* ctx, double* dJa, double* dJ, dg_stream stream);
 dg_status dg_time_derivative_vjp(dg_ctx* ctx, const double* dU, const double* dv, double* dout, double* dJdmu,
                                  double t, dg_stream stream);
 
-/* Adjoint of one LSERK4-5 step from dU_n (state at the step's start, time t):
+/* Adjoint of one step (the context's scheme) from dU_n (state at the step's start, time t):
  * dlam_n = (dU_{n+1}/dU_n)^T dlam_np1 (may alias), dJdmu += the step's
- * lambda . dU_{n+1}/dmu.  The five stage states are recomputed from dU_n. */
+ * lambda . dU_{n+1}/dmu.  The stage states are recomputed from dU_n. */
 dg_status dg_adjoint_step(dg_ctx* ctx, const double* dU_n, const double* dlam_np1, double* dlam_n, double* dJdmu,
                           double t, double dt, dg_stream stream);
 
-/* Adjoint of nsteps LSERK4-5 steps from dU0 at t0: dlam0 = (dU_T/dU_0)^T dlamT
+/* Adjoint of nsteps steps (the context's scheme) from dU0 at t0: dlam0 = (dU_T/dU_0)^T dlamT
  * (may alias), dJdmu += lambda . dU_T/dmu, with binomial checkpointing: at
  * most max_snapshots stored states (>= 1), forward recomputation in between.
  * host_counts2 (may be NULL) receives {recomputed forward steps, adjoint

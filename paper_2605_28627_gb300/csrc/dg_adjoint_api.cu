@@ -28,8 +28,6 @@ static dg_status ensure_adjoint(Ctx* c) {
   if (c->prm.precision != DG_FP64) return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the FP64 operator");
   if (c->prm.surf_flux == DG_FLUX_ROE)
     return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the LLF and entropy-conservative surface fluxes");
-  if (c->prm.rk_scheme != DG_RK45)
-    return afail(c, DG_EUNSUPPORTED, "the adjoint is built for LSERK4-5");
   if (c->prm.nodes != DG_NODES_LGL)
     return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the LGL operator");
   if (c->prm.visc_law != DG_VISC_CONSTANT)
@@ -43,39 +41,42 @@ static dg_status ensure_adjoint(Ctx* c) {
   ADJ_CUDA(cudaMalloc(&c->d_adj_fseed, sizeof(double) * nn * 2 * 5), c, "adjoint buffers");
   ADJ_CUDA(cudaMalloc(&c->d_adj_face, sizeof(double) * nn * 2 * 17), c, "adjoint buffers");
   ADJ_CUDA(cudaMalloc(&c->d_adj_mu, sizeof(double) * (adjoint_mu_partials(*c) + 2)), c, "adjoint buffers");
-  ADJ_CUDA(cudaMalloc(&c->d_adj_stage, sizeof(double) * st * 5), c, "adjoint stage states");
+  ADJ_CUDA(cudaMalloc(&c->d_adj_stage, sizeof(double) * st * rk_scheme(c->prm.rk_scheme).stages), c,
+           "adjoint stage states");
   ADJ_CUDA(cudaMalloc(&c->d_adj_work, sizeof(double) * st * 4), c, "adjoint work");
   return DG_OK;
 }
 
-// One LSERK4-5 step adjoint.  Un: state at the start of the step; lam: in =
-// adjoint at the end of the step, out = adjoint at the start (in place).
+// Adjoint of one step of the context's 2N-storage scheme (LSERK4-5 or
+// RK4-14).  Un: state at the start of the step; lam: in = adjoint at the end
+// of the step, out = adjoint at the start (in place).
 static dg_status step_adjoint(Ctx* c, const double* Un, double* lam, double* dJdmu, double t, double dt,
                               cudaStream_t s) {
+  const RkScheme rk = rk_scheme(c->prm.rk_scheme);
   const size_t st = (size_t)c->E * 5 * c->P, bytes = sizeof(double) * st;
   double* Ws = c->d_adj_work;           // work state
   double* G = Ws + st;                  // RK register
   double* Gb = G + st;                  // adjoint of the register
   double* tmp = Gb + st;                // dt * Gb, then VJP output
-  // forward recomputation of the five stage states
+  // forward recomputation of the stage states
   ADJ_CUDA(cudaMemcpyAsync(Ws, Un, bytes, cudaMemcpyDeviceToDevice, s), c, "stage copy");
   ADJ_CUDA(cudaMemsetAsync(G, 0, bytes, s), c, "memset");
   ADJ_CUDA(launch_set_clock(c->d_clock, t, dt, s), c, "clock");
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < rk.stages; ++k) {
     ADJ_CUDA(cudaMemcpyAsync(c->d_adj_stage + (size_t)k * st, Ws, bytes, cudaMemcpyDeviceToDevice, s), c, "stage copy");
     ADJ_CUDA(launch_lift(*c, Ws, s), c, "lift");
     ADJ_CUDA(launch_face(*c, Ws, s), c, "face");
-    StageArgs a{Ws, Ws, G, nullptr, c->d_clock, kRkC[k], kRkA[k], kRkB[k], 1};
+    StageArgs a{Ws, Ws, G, nullptr, c->d_clock, rk.C[k], rk.A[k], rk.B[k], 1};
     ADJ_CUDA(launch_volume(*c, a, s), c, "volume");
   }
   // reverse sweep: Gb += B_k lam;  lam += (dR/dU)^T (dt Gb);  Gb *= A_k
   ADJ_CUDA(cudaMemsetAsync(Gb, 0, bytes, s), c, "memset");
-  for (int k = 4; k >= 0; --k) {
-    ADJ_CUDA(launch_axpby(Gb, lam, 1.0, kRkB[k], st, s), c, "axpby");
+  for (int k = rk.stages - 1; k >= 0; --k) {
+    ADJ_CUDA(launch_axpby(Gb, lam, 1.0, rk.B[k], st, s), c, "axpby");
     ADJ_CUDA(launch_axpby(tmp, Gb, 0.0, dt, st, s), c, "axpby");
     ADJ_CUDA(launch_vjp(*c, c->d_adj_stage + (size_t)k * st, tmp, tmp, dJdmu, 1.0, s), c, "vjp");
     ADJ_CUDA(launch_axpby(lam, tmp, 1.0, 1.0, st, s), c, "axpby");
-    ADJ_CUDA(launch_axpby(Gb, Gb, kRkA[k], 0.0, st, s), c, "axpby");
+    ADJ_CUDA(launch_axpby(Gb, Gb, rk.A[k], 0.0, st, s), c, "axpby");
   }
   return DG_OK;
 }
@@ -85,12 +86,13 @@ static dg_status advance(Ctx* c, double* U, double* G, double t, double dt, int 
   if (nsteps <= 0) return DG_OK;
   ADJ_CUDA(launch_set_clock(c->d_clock, t, dt, s), c, "clock");
   const size_t bytes = sizeof(double) * (size_t)c->E * 5 * c->P;
+  const RkScheme rk = rk_scheme(c->prm.rk_scheme);
   for (int st = 0; st < nsteps; ++st) {
     ADJ_CUDA(cudaMemsetAsync(G, 0, bytes, s), c, "memset");
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < rk.stages; ++k) {
       ADJ_CUDA(launch_lift(*c, U, s), c, "lift");
       ADJ_CUDA(launch_face(*c, U, s), c, "face");
-      StageArgs a{U, U, G, nullptr, c->d_clock, kRkC[k], kRkA[k], kRkB[k], 1};
+      StageArgs a{U, U, G, nullptr, c->d_clock, rk.C[k], rk.A[k], rk.B[k], 1};
       ADJ_CUDA(launch_volume(*c, a, s), c, "volume");
     }
     ADJ_CUDA(launch_clock_advance(c->d_clock, s), c, "clock");

@@ -44,13 +44,16 @@ def test_vjp_dot_product_vs_oracle_tangent_linear(orc, dg, N, flux):
     assert abs(dmu.item() - ref_mu) <= 1e-11 * float(np.abs(v * Rmu).sum()), (dmu.item(), ref_mu)
 
 
-def test_step_and_solve_adjoint_vs_oracle(orc, dg):
+@pytest.mark.parametrize("rk", [0, 1])
+def test_step_and_solve_adjoint_vs_oracle(orc, dg, rk):
+    """Adjoint of LSERK4-5 (rk 0) and RK4-14 (rk 1) steps against the oracle's
+    tangent-linear of the same scheme."""
     prm = tgv_params(Ma=0.3, Re=400.0)
     N = 3
     mesh = box_mesh(3, 1, lo=0.0, hi=2 * math.pi, rotate_seed=5)
     kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"])
-    o = orc.Oracle(mesh, N, **kw)
-    s = dg.Solver(mesh, N, **kw)
+    o = orc.Oracle(mesh, N, rk=rk, **kw)
+    s = dg.Solver(mesh, N, rk_scheme=rk, **kw)
     # a generic state near the Taylor-Green vortex: the vortex itself has w = 0
     # exactly, which puts |u . n| of the LLF speed at its kink on z-faces, where
     # the one-sided derivatives of the two codes may differ by rounding
