@@ -5,19 +5,10 @@
 
 namespace dg {
 
-// Blocks per SM the register allocation must allow: FP32 tiles of up to 512
-// threads are kept to <= 64 registers so that two blocks share an SM (the FP32
-// operator is latency-bound); the FP64 tiles of 128 threads (N = 1, 3) to
-// <= 102 registers, five blocks (20 warps) instead of four, which the compiler
-// reaches without spilling; other FP64 tiles are left alone (capping them
-// spills).
+// FP32 tiles of up to 512 threads are kept to <= 64 registers so that two
+// blocks share an SM (the FP32 operator is latency-bound, the FP64 one is not).
 template <int N, typename R>
-constexpr int volume_min_blocks() {
-  return sizeof(R) == 4 ? (VShape<N>::THREADS <= 512 ? 2 : 1) : (VShape<N>::THREADS <= 128 ? 5 : 1);
-}
-
-template <int N, typename R>
-__global__ void __launch_bounds__(VShape<N>::THREADS, volume_min_blocks<N, R>())
+__global__ void __launch_bounds__(VShape<N>::THREADS, (sizeof(R) == 4 && VShape<N>::THREADS <= 512) ? 2 : 1)
 k_volume2(StageArgs a, const R* __restrict__ metrics, const double* __restrict__ iJ64,
           const R* __restrict__ grad, const R* __restrict__ fstar, const int* __restrict__ elem_face,
           const double* __restrict__ mms, const double* __restrict__ Dg, int E, Gas g, double inv_w0) {
