@@ -36,13 +36,24 @@ struct Shape {
 template <int N, int EPB_ = default_epb((N + 1) * (N + 1) * (N + 1))>
 struct VShape : Shape<N, EPB_> {
   static constexpr int ROUNDS = (N + 1) / 2;    // shifts s = 1..n/2 (s = n/2 half-used for even n)
-  static constexpr int PER_ELEM = 26 * (N + 1) * (N + 1) * (N + 1);   // operator words of smem per element
+};
+
+// Exchange buffers of the pair loop: one per round when they fit (all rounds
+// of a direction then share one barrier), else one (a barrier per round).
+template <int N, typename R, int EPB>
+struct VXbuf {
+  static constexpr int P = (N + 1) * (N + 1) * (N + 1), ROUNDS = (N + 1) / 2;
+  static constexpr size_t base_words = 3 * (N + 1) * (N + 1) + (((N + 1) * (N + 1) + 3) & ~3) +
+                                       (size_t)EPB * (21 + (sizeof(R) == 4 ? 1 : 0)) * P;
+  static constexpr int value =
+      sizeof(R) * (base_words + (size_t)EPB * 5 * P * ROUNDS) <= 200 * 1024 ? ROUNDS : 1;
+  static constexpr int PER_ELEM = (21 + 5 * value) * P;   // operator words of smem per element
 };
 
 template <int N, typename R, int EPB>
 constexpr size_t volume_smem_bytes() {
   // the FP32 operator keeps one more word per node (the offset pressure term)
-  return sizeof(R) * (3 * (N + 1) * (N + 1) + (((N + 1) * (N + 1) + 3) & ~3) + EPB * VShape<N, EPB>::PER_ELEM +
+  return sizeof(R) * (3 * (N + 1) * (N + 1) + (((N + 1) * (N + 1) + 3) & ~3) + EPB * VXbuf<N, R, EPB>::PER_ELEM +
                       (sizeof(R) == 4 ? EPB * (N + 1) * (N + 1) * (N + 1) : 0));
 }
 
@@ -313,15 +324,17 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
   R* sT1 = sT0 + n * n;               // D/8   (momentum: M = 16 f_m)
   R* sT2 = sT1 + n * n;               // D/16  (energy: 32 f_E)
   const int le = threadIdx.x / P, id = threadIdx.x - le * P;
-  R* base = sT2 + ((n * n + 3) & ~3) + le * S::PER_ELEM;
+  constexpr int XB = VXbuf<N, R, EPB_>::value;
+  constexpr int PER_ELEM = VXbuf<N, R, EPB_>::PER_ELEM;
+  R* base = sT2 + ((n * n + 3) & ~3) + le * PER_ELEM;
   R* sR = base;                       // rho
   R* sU = sR + P;                     // u, v, w
   R* sB = sU + 3 * P;                 // beta = rho / (2 p)
   R* sK = sB + P;                     // |u|^2
   R* sJd = sK + P;                    // [3][P]  Ja^d of the direction being swept
   R* sFv = sJd + 3 * P;               // [3][4][P] (f_v . Ja^d), momentum + energy
-  R* sX = sFv + 12 * P;               // [5][P] exchange of partner shares
-  R* sDl = sT2 + ((n * n + 3) & ~3) + EPB * S::PER_ELEM + le * P;   // FP32 only: rho (p - p_ref) / p
+  R* sX = sFv + 12 * P;               // [XB][5][P] exchange of partner shares (one per round if XB > 1)
+  R* sDl = sT2 + ((n * n + 3) & ~3) + EPB * PER_ELEM + le * P;   // FP32 only: rho (p - p_ref) / p
   const int e = blk * EPB + le;
   const bool active = e < E;
   __shared__ double s_tc[2];          // sin, cos of pi t (manufactured source)
@@ -398,6 +411,7 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
       const bool half = (2 * s == n);
       const int m = r + s < n ? r + s : r + s - n;
       const int mid = line0 + m * stride;
+      R* sXs = sX + (XB > 1 ? (s - 1) * 5 * P : 0);
       if (active && !(half && r >= s)) {
         const R rb = sR[mid], bb = sB[mid];
         const R sr = rho + rb, sb = beta + bb;
@@ -430,19 +444,39 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
         acc[2] = fma(sT1[rm], M1, acc[2]);
         acc[3] = fma(sT1[rm], M2, acc[3]);
         acc[4] = fma(sT2[rm], E32, acc[4]);
-        sX[mid] = Xf; sX[P + mid] = M0; sX[2 * P + mid] = M1; sX[3 * P + mid] = M2; sX[4 * P + mid] = E32;
+        sXs[mid] = Xf; sXs[P + mid] = M0; sXs[2 * P + mid] = M1; sXs[3 * P + mid] = M2; sXs[4 * P + mid] = E32;
       }
-      __syncthreads();
-      const int src = r - s >= 0 ? r - s : r - s + n;   // the node whose pair (src, r) wrote here
-      if (active && !(half && src >= s)) {
-        const int rm = r * n + src;
-        acc[0] = fma(sT0[rm], sX[id], acc[0]);
-        acc[1] = fma(sT1[rm], sX[P + id], acc[1]);
-        acc[2] = fma(sT1[rm], sX[2 * P + id], acc[2]);
-        acc[3] = fma(sT1[rm], sX[3 * P + id], acc[3]);
-        acc[4] = fma(sT2[rm], sX[4 * P + id], acc[4]);
+      if constexpr (XB == 1) {
+        __syncthreads();
+        const int src = r - s >= 0 ? r - s : r - s + n;   // the node whose pair (src, r) wrote here
+        if (active && !(half && src >= s)) {
+          const int rm = r * n + src;
+          acc[0] = fma(sT0[rm], sX[id], acc[0]);
+          acc[1] = fma(sT1[rm], sX[P + id], acc[1]);
+          acc[2] = fma(sT1[rm], sX[2 * P + id], acc[2]);
+          acc[3] = fma(sT1[rm], sX[3 * P + id], acc[3]);
+          acc[4] = fma(sT2[rm], sX[4 * P + id], acc[4]);
+        }
+        __syncthreads();
       }
+    }
+    if constexpr (XB > 1) {
+      // every round wrote its own buffer: one barrier, then the partners' shares
       __syncthreads();
+#pragma unroll 1
+      for (int s = 1; s <= S::ROUNDS; ++s) {
+        const bool half = (2 * s == n);
+        const int src = r - s >= 0 ? r - s : r - s + n;   // the node whose pair (src, r) wrote here
+        const R* sXs = sX + (s - 1) * 5 * P;
+        if (active && !(half && src >= s)) {
+          const int rm = r * n + src;
+          acc[0] = fma(sT0[rm], sXs[id], acc[0]);
+          acc[1] = fma(sT1[rm], sXs[P + id], acc[1]);
+          acc[2] = fma(sT1[rm], sXs[2 * P + id], acc[2]);
+          acc[3] = fma(sT1[rm], sXs[3 * P + id], acc[3]);
+          acc[4] = fma(sT2[rm], sXs[4 * P + id], acc[4]);
+        }
+      }
     }
   }
   if (!active) return;
