@@ -6,7 +6,12 @@
 // Volume body -- FP64-pipe-aware design (also used in FP32):
 //  * Symmetric pair reuse: F#(q_i, q_m) = F#(q_m, q_i), so each unordered
 //    pair on a line is evaluated once, in rounds of a fixed cyclic shift s;
-//    the partner's share goes through shared memory.
+//    the partner's share goes through shared memory.  For even n the last
+//    shift (s = n/2) pairs each node with the opposite one, so it holds only
+//    half as many pairs as nodes: those are packed onto the first half of the
+//    block's threads (whole warps idle instead of every other lane, which the
+//    narrow FP64 pipe would still charge) and both shares go through shared
+//    memory.
 //  * The diagonal terms 2 D_ii f(q_i) . Ja_i vanish for interior LGL nodes
 //    and cancel exactly against the -f . n sJ / w_0 part of the surface term
 //    at the two end nodes (2 D_00 = -1/w_0, 2 D_NN = 1/w_0), so neither is
@@ -278,6 +283,18 @@ __device__ __forceinline__ double rcp_op(double x) {
   const double t = fma(e, e, e);
   return fma(y, t, y);
 }
+// 1/x with one quadratic Newton-Raphson step y <- y + y e (relative error
+// ~2^-40), for reciprocals whose error is damped by the use
+__device__ __forceinline__ double rcp_op_q(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return fma(y, fma(-x, y, 1.0), y);
+}
+__device__ __forceinline__ float rcp_op_q(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float rcp_op(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -307,6 +324,40 @@ __device__ __noinline__ R atanh_ratio_log(R a, R b) {
   return log(z) / (R(2) * ((z - R(1)) / (z + R(1))));
 }
 
+// Chandrashekar's two-point flux of one node pair (a, b) in one direction,
+// scaled for the scaled copies of D: F = (8 f_rho, 16 f_m, 32 f_E).  Taken as
+// densities and b = beta/4 = rho/(8p) of both nodes and the pair sums of
+// velocity su = u_a + u_b, |u|^2 (sk), metric term sn = Ja^d_a + Ja^d_b and,
+// for the FP32 operator, rho (p - p_ref)/p (sdl; unused in FP64).  The factor
+// 1/4 on beta (exact) folds the 4 of 16 p_hat into the reciprocal.
+template <typename R>
+__device__ __forceinline__ void ec_pair(R ra, R rb, R ba, R bb, R su0, R su1, R su2, R sk, R sdl, R sn0, R sn1,
+                                        R sn2, R inv_gm1, const Gas& g, R F[5]) {
+  const R sr = ra + rb, sb = ba + bb;
+  // 1/(rho_a + rho_b) enters only through u_rho = fr^2 < 1e-4 on the series
+  // branch, so one quadratic Newton step (relative error ~1e-12) suffices
+  const R rr = rcp_op_q(sr), rbt = rcp_op(sb);   // rbt = 4/(beta_a + beta_b)
+  const R fr = (ra - rb) * rr, fb = (ba - bb) * rbt;
+  const R ur = fr * fr, ubt = fb * fb;
+  R rln2, hib;                    // 2 rho_ln and 2/beta_ln
+  if (small_u(ur)) rln2 = sr * inv_atanh_ratio(ur);
+  else rln2 = sr / atanh_ratio_log(ra, rb);
+  if (small_u(ubt)) hib = atanh_ratio(ubt) * rbt;
+  else hib = atanh_ratio_log(ba, bb) * rbt;
+  const R un4 = fma(su0, sn0, fma(su1, sn1, su2 * sn2));
+  const R Xf = rln2 * un4;                      // 8 f_rho
+  // 16 p_hat n_avg = Y4 (n_a + n_b); the FP32 operator uses p_hat - p_ref
+  R Y4 = sr * rbt;
+  if constexpr (sizeof(R) == 4) Y4 = sdl * rbt;
+  const R M0 = fma(Xf, su0, Y4 * sn0);          // 16 f_m
+  const R M1 = fma(Xf, su1, Y4 * sn1);
+  const R M2 = fma(Xf, su2, Y4 * sn2);
+  const R Z = fma(hib, inv_gm1, -sk);
+  R E32 = fma(Xf, Z, fma(su0, M0, fma(su1, M1, su2 * M2)));   // 32 f_E
+  if constexpr (sizeof(R) == 4) E32 = fma(R(8) * g.f_p_ref, un4, E32);     // p_ref {u}.n back
+  F[0] = Xf; F[1] = M0; F[2] = M1; F[3] = M2; F[4] = E32;
+}
+
 // R is the operator arithmetic: double (FP64 path) or float (FP32-operator
 // path, state and RK update stay FP64).  metrics, grad and fstar are stored in R.
 template <int N, typename R, int EPB_>
@@ -326,15 +377,16 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
   const int le = threadIdx.x / P, id = threadIdx.x - le * P;
   constexpr int XB = VXbuf<N, R, EPB_>::value;
   constexpr int PER_ELEM = VXbuf<N, R, EPB_>::PER_ELEM;
-  R* base = sT2 + ((n * n + 3) & ~3) + le * PER_ELEM;
+  R* const tile0 = sT2 + ((n * n + 3) & ~3);   // element tiles, PER_ELEM words each
+  R* base = tile0 + le * PER_ELEM;
   R* sR = base;                       // rho
   R* sU = sR + P;                     // u, v, w
-  R* sB = sU + 3 * P;                 // beta = rho / (2 p)
+  R* sB = sU + 3 * P;                 // beta / 4 = rho / (8 p)
   R* sK = sB + P;                     // |u|^2
   R* sJd = sK + P;                    // [3][P]  Ja^d of the direction being swept
   R* sFv = sJd + 3 * P;               // [3][4][P] (f_v . Ja^d), momentum + energy
   R* sX = sFv + 12 * P;               // [XB][5][P] exchange of partner shares (one per round if XB > 1)
-  R* sDl = sT2 + ((n * n + 3) & ~3) + EPB * PER_ELEM + le * P;   // FP32 only: rho (p - p_ref) / p
+  R* sDl = tile0 + EPB * PER_ELEM + le * P;   // FP32 only: rho (p - p_ref) / p
   const int e = blk * EPB + le;
   const bool active = e < E;
   __shared__ double s_tc[2];          // sin, cos of pi t (manufactured source)
@@ -363,7 +415,7 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     u = to_op<R>(q[1]) * ir; v = to_op<R>(q[2]) * ir; w = to_op<R>(q[3]) * ir;
     kk = u * u + v * v + w * w;
     const R p = gsel<R>(g.gm1, g.f_gm1) * fma(R(-0.5) * rho, kk, to_op<R>(q[4]));
-    beta = R(0.5) * rho * rcp_op(p);
+    beta = R(0.125) * rho * rcp_op(p);   // beta / 4
     sR[id] = rho; sU[id] = u; sU[P + id] = v; sU[2 * P + id] = w; sB[id] = beta; sK[id] = kk;
     if constexpr (sizeof(R) == 4) {
       // offset form of the momentum flux (see face_body): p - p_ref from the
@@ -392,8 +444,11 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
   __syncthreads();
   const int i = id % n, j = (id / n) % n, k = id / NN;
   const int ijk[3] = {i, j, k};
-  const R inv4 = R(4) * gsel<R>(g.inv_gm1, g.f_inv_gm1);
+  const R inv_gm1 = gsel<R>(g.inv_gm1, g.f_inv_gm1);
   R acc[5] = {0, 0, 0, 0, 0};
+  constexpr int FULL = (n - 1) / 2;       // shifts with a pair for every node
+  constexpr bool HALF = (n % 2) == 0;     // the shift n/2, half as many pairs
+  static_assert(FULL + (HALF ? 1 : 0) == S::ROUNDS, "pair-loop rounds");
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int r = ijk[d];
@@ -406,76 +461,88 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     sJd[P + id] = Ja[d * 3 + 1];
     sJd[2 * P + id] = Ja[d * 3 + 2];
     __syncthreads();
+    // the partner's share of a pair, written to this node's slot of xs
+    auto take_share = [&](const R* xs, int src) {
+      const int rm = r * n + src;
+      acc[0] = fma(sT0[rm], xs[id], acc[0]);
+      acc[1] = fma(sT1[rm], xs[P + id], acc[1]);
+      acc[2] = fma(sT1[rm], xs[2 * P + id], acc[2]);
+      acc[3] = fma(sT1[rm], xs[3 * P + id], acc[3]);
+      acc[4] = fma(sT2[rm], xs[4 * P + id], acc[4]);
+    };
 #pragma unroll 1
-    for (int s = 1; s <= S::ROUNDS; ++s) {
-      const bool half = (2 * s == n);
+    for (int s = 1; s <= FULL; ++s) {
       const int m = r + s < n ? r + s : r + s - n;
       const int mid = line0 + m * stride;
       R* sXs = sX + (XB > 1 ? (s - 1) * 5 * P : 0);
-      if (active && !(half && r >= s)) {
-        const R rb = sR[mid], bb = sB[mid];
-        const R sr = rho + rb, sb = beta + bb;
-        const R rr = rcp_op(sr), rbt = rcp_op(sb);
-        const R fr = (rho - rb) * rr, fb = (beta - bb) * rbt;
-        const R ur = fr * fr, ub = fb * fb;
-        R rln2, hib;                    // 2 rho_ln and 1/(2 beta_ln)
-        if (small_u(ur)) rln2 = sr * inv_atanh_ratio(ur);
-        else rln2 = sr / atanh_ratio_log(rho, rb);
-        if (small_u(ub)) hib = atanh_ratio(ub) * rbt;
-        else hib = atanh_ratio_log(beta, bb) * rbt;
-        const R su0 = u + sU[mid], su1 = v + sU[P + mid], su2 = w + sU[2 * P + mid];
-        const R sn0 = Ja[d * 3] + sJd[mid];
-        const R sn1 = Ja[d * 3 + 1] + sJd[P + mid];
-        const R sn2 = Ja[d * 3 + 2] + sJd[2 * P + mid];
-        const R un4 = fma(su0, sn0, fma(su1, sn1, su2 * sn2));
-        const R Xf = rln2 * un4;                      // 8 f_rho
-        // 16 p_hat n_avg = Y4 (n_a + n_b); the FP32 operator uses p_hat - p_ref
-        R Y4 = R(4) * sr * rbt;
-        if constexpr (sizeof(R) == 4) Y4 = R(4) * (sDl[id] + sDl[mid]) * rbt;
-        const R M0 = fma(Xf, su0, Y4 * sn0);          // 16 f_m
-        const R M1 = fma(Xf, su1, Y4 * sn1);
-        const R M2 = fma(Xf, su2, Y4 * sn2);
-        const R Z = fma(hib, inv4, -(kk + sK[mid]));
-        R E32 = fma(Xf, Z, fma(su0, M0, fma(su1, M1, su2 * M2)));   // 32 f_E
-        if constexpr (sizeof(R) == 4) E32 = fma(R(8) * g.f_p_ref, un4, E32);     // p_ref {u}.n back
+      if (active) {
+        R F[5];
+        R sdl = 0;
+        if constexpr (sizeof(R) == 4) sdl = sDl[id] + sDl[mid];
+        ec_pair<R>(rho, sR[mid], beta, sB[mid], u + sU[mid], v + sU[P + mid], w + sU[2 * P + mid], kk + sK[mid], sdl,
+                   Ja[d * 3] + sJd[mid], Ja[d * 3 + 1] + sJd[P + mid], Ja[d * 3 + 2] + sJd[2 * P + mid], inv_gm1, g, F);
         const int rm = r * n + m;
-        acc[0] = fma(sT0[rm], Xf, acc[0]);
-        acc[1] = fma(sT1[rm], M0, acc[1]);
-        acc[2] = fma(sT1[rm], M1, acc[2]);
-        acc[3] = fma(sT1[rm], M2, acc[3]);
-        acc[4] = fma(sT2[rm], E32, acc[4]);
-        sXs[mid] = Xf; sXs[P + mid] = M0; sXs[2 * P + mid] = M1; sXs[3 * P + mid] = M2; sXs[4 * P + mid] = E32;
+        acc[0] = fma(sT0[rm], F[0], acc[0]);
+        acc[1] = fma(sT1[rm], F[1], acc[1]);
+        acc[2] = fma(sT1[rm], F[2], acc[2]);
+        acc[3] = fma(sT1[rm], F[3], acc[3]);
+        acc[4] = fma(sT2[rm], F[4], acc[4]);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) sXs[c * P + mid] = F[c];
       }
       if constexpr (XB == 1) {
         __syncthreads();
-        const int src = r - s >= 0 ? r - s : r - s + n;   // the node whose pair (src, r) wrote here
-        if (active && !(half && src >= s)) {
-          const int rm = r * n + src;
-          acc[0] = fma(sT0[rm], sX[id], acc[0]);
-          acc[1] = fma(sT1[rm], sX[P + id], acc[1]);
-          acc[2] = fma(sT1[rm], sX[2 * P + id], acc[2]);
-          acc[3] = fma(sT1[rm], sX[3 * P + id], acc[3]);
-          acc[4] = fma(sT2[rm], sX[4 * P + id], acc[4]);
-        }
+        if (active) take_share(sX, r - s >= 0 ? r - s : r - s + n);   // written by the pair (r - s, r)
         __syncthreads();
       }
     }
-    if constexpr (XB > 1) {
+    if constexpr (HALF) {
+      // s = n/2: the pairs (r, r + n/2), r < n/2, P/2 per element, numbered in
+      // node order within each element and over the block's elements, taken
+      // by the first EPB P/2 threads; both shares go to the exchange buffer
+      constexpr int H = n / 2;
+      const int t = threadIdx.x;
+      const int le2 = t / (P / 2), w2 = t - le2 * (P / 2);
+      if (t < EPB * (P / 2) && blk * EPB + le2 < E) {
+        const int hi = w2 / stride;
+        const int ia = w2 - hi * stride + stride * (hi % H + n * (hi / H));   // node with r < n/2
+        const int ib = ia + H * stride;                                          // its partner
+        const R* b2 = tile0 + le2 * PER_ELEM;
+        const R* r2 = b2;
+        const R* u2 = r2 + P;
+        const R* be2 = u2 + 3 * P;
+        const R* k2 = be2 + P;
+        const R* j2 = k2 + P;
+        R sdl = 0;
+        if constexpr (sizeof(R) == 4) {
+          const R* dl2 = tile0 + EPB * PER_ELEM + le2 * P;
+          sdl = dl2[ia] + dl2[ib];
+        }
+        R F[5];
+        ec_pair<R>(r2[ia], r2[ib], be2[ia], be2[ib], u2[ia] + u2[ib], u2[P + ia] + u2[P + ib],
+                   u2[2 * P + ia] + u2[2 * P + ib], k2[ia] + k2[ib], sdl, j2[ia] + j2[ib], j2[P + ia] + j2[P + ib],
+                   j2[2 * P + ia] + j2[2 * P + ib], inv_gm1, g, F);
+        R* xh = tile0 + le2 * PER_ELEM + 21 * P + (XB > 1 ? FULL * 5 * P : 0);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          xh[c * P + ia] = F[c];
+          xh[c * P + ib] = F[c];
+        }
+      }
+    }
+    if constexpr (XB == 1) {
+      if constexpr (HALF) {
+        __syncthreads();
+        if (active) take_share(sX, r >= n / 2 ? r - n / 2 : r + n / 2);
+        __syncthreads();
+      }
+    } else {
       // every round wrote its own buffer: one barrier, then the partners' shares
       __syncthreads();
+      if (active) {
 #pragma unroll 1
-      for (int s = 1; s <= S::ROUNDS; ++s) {
-        const bool half = (2 * s == n);
-        const int src = r - s >= 0 ? r - s : r - s + n;   // the node whose pair (src, r) wrote here
-        const R* sXs = sX + (s - 1) * 5 * P;
-        if (active && !(half && src >= s)) {
-          const int rm = r * n + src;
-          acc[0] = fma(sT0[rm], sXs[id], acc[0]);
-          acc[1] = fma(sT1[rm], sXs[P + id], acc[1]);
-          acc[2] = fma(sT1[rm], sXs[2 * P + id], acc[2]);
-          acc[3] = fma(sT1[rm], sXs[3 * P + id], acc[3]);
-          acc[4] = fma(sT2[rm], sXs[4 * P + id], acc[4]);
-        }
+        for (int s = 1; s <= FULL; ++s) take_share(sX + (s - 1) * 5 * P, r - s >= 0 ? r - s : r - s + n);
+        if constexpr (HALF) take_share(sX + FULL * 5 * P, r >= n / 2 ? r - n / 2 : r + n / 2);
       }
     }
   }
