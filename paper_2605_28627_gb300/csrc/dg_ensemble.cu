@@ -126,8 +126,8 @@ static cudaError_t launch_group_stage(const Group& g, int k, const double* A, co
   const MemberDev<R>* mem = (const MemberDev<R>*)g.d_mem;
   const int ch = g.plan.epb_choice;
   // lifting always uses the default tile (its tile table is choice 0)
-  k_lift_ens<N, R, e0><<<g.plan.lift_grid, Shape<N, e0>::THREADS, 0, s>>>(mem, g.d_elem_tiles[0], g.n_elem_tiles[0],
-                                                                          g.d_D);
+  k_lift_ens<N, R, e0><<<g.plan.lift_grid, Shape<N, e0>::THREADS, lift_smem_bytes<N, R, e0>(), s>>>(
+      mem, g.d_elem_tiles[0], g.n_elem_tiles[0], g.d_D);
   k_face_ens<N, R><<<g.plan.face_grid, 128, 0, s>>>(mem, g.d_face_tiles, g.n_face_tiles);
   if (ch == 0)
     k_volume_ens<N, R, e0><<<g.plan.vol_grid, VShape<N, e0>::THREADS, volume_smem_bytes<N, R, e0>(), s>>>(
@@ -140,7 +140,9 @@ static cudaError_t launch_group_stage(const Group& g, int k, const double* A, co
 
 template <int N, typename R>
 static cudaError_t setup_group() {
-  cudaError_t e = set_vol_attr<N, R, Shape<N>::EPB>();
+  cudaError_t e = cudaFuncSetAttribute(k_lift_ens<N, R, Shape<N>::EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)lift_smem_bytes<N, R, Shape<N>::EPB>());
+  if (e == cudaSuccess) e = set_vol_attr<N, R, Shape<N>::EPB>();
   if (e == cudaSuccess) e = set_vol_attr<N, R, Epb2<N, R>::value>();
   return e;
 }

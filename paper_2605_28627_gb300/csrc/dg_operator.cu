@@ -25,8 +25,8 @@ static cudaError_t lift_NR(const Ctx& c, const double* U, cudaStream_t s) {
   using S = Shape<N>;
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
   const R* metrics = (const R*)(sizeof(R) == 8 ? (const void*)c.d_metrics : (const void*)c.d_metrics_f);
-  k_lift<N, R><<<blocks, S::THREADS, 0, s>>>(U, metrics, c.d_elem_nbr, c.d_elem_face, c.d_D, (R*)c.d_grad, c.E,
-                                             c.gas, 1.0 / c.w[0]);
+  k_lift<N, R><<<blocks, S::THREADS, lift_smem_bytes<N, R, S::EPB>(), s>>>(
+      U, metrics, c.d_elem_nbr, c.d_elem_face, c.d_D, (R*)c.d_grad, c.E, c.gas, 1.0 / c.w[0]);
   return cudaGetLastError();
 }
 
@@ -77,8 +77,31 @@ cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s) {
   if (c.prm.nodes == DG_NODES_LG) return launch_face_lg(c, s);
   DG_DISPATCH(face_N, c, U, s)
 }
+template <int N>
+static cudaError_t setup_lift_N() {
+  cudaError_t e = cudaFuncSetAttribute(k_lift<N, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)lift_smem_bytes<N, double, Shape<N>::EPB>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_lift<N, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lift_smem_bytes<N, float, Shape<N>::EPB>());
+  return e;
+}
+
 cudaError_t setup_kernels(int N) {
-  cudaError_t e = setup_volume(N);
+  cudaError_t e;
+  switch (N) {
+    case 1: e = setup_lift_N<1>(); break;
+    case 2: e = setup_lift_N<2>(); break;
+    case 3: e = setup_lift_N<3>(); break;
+    case 4: e = setup_lift_N<4>(); break;
+    case 5: e = setup_lift_N<5>(); break;
+    case 6: e = setup_lift_N<6>(); break;
+    case 7: e = setup_lift_N<7>(); break;
+    case 8: e = setup_lift_N<8>(); break;
+    case 9: e = setup_lift_N<9>(); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e == cudaSuccess) e = setup_volume(N);
   return e == cudaSuccess ? setup_gauss(N) : e;
 }
 

@@ -81,80 +81,125 @@ __device__ __forceinline__ float rcp_lf(float x) {
 // part: g_l = (1/J)[ sum_d Ja^d_l D_d phi + sum_faces (phi* - phi) n_l sJ / w_0 ]
 // with phi* = (phi + phi_nbr)/2 and the element's own outward n sJ = (2s-1) Ja^d.
 // R is the operator arithmetic; metrics and the output gradients are in R.
+//
+// The face jumps (phi* - phi)(+-1/w_0) are computed once per face point by
+// threads packed over the element's 6 (N+1)^2 face points (the neighbour
+// primitives and the differences would otherwise run on every node thread of
+// a warp that holds one face node: on the narrow FP64 pipe masked lanes cost
+// as much as active ones), kept in shared memory, and only the products with
+// the node's metric terms stay with the node thread.
+template <int N, typename R, int EPB>
+constexpr size_t lift_smem_bytes() {
+  // [EPB][4][P] primitives phi, [EPB][6][4][n^2] face jumps
+  return sizeof(R) * (size_t)EPB * (4 * (N + 1) * (N + 1) * (N + 1) + 24 * (N + 1) * (N + 1));
+}
+
 template <int N, typename R, int EPB>
 __device__ __forceinline__ void lift_body(const double* __restrict__ U, const R* __restrict__ metrics,
                                           const int* __restrict__ elem_nbr, const int* __restrict__ elem_face,
                                           const double* __restrict__ Dg, R* __restrict__ grad, int E, const Gas& g,
                                           double inv_w0d, int blk) {
   using S = Shape<N, EPB>;
-  constexpr int n = S::n, P = S::P;
+  constexpr int n = S::n, P = S::P, NN = S::NN, NF = 6 * NN;
+  constexpr int NI = (EPB * NF + S::THREADS - 1) / S::THREADS;   // face points per thread
   __shared__ R sD[n * n];
-  __shared__ R sphi[S::EPB][4][P];
+  extern __shared__ __align__(16) unsigned char lift_raw[];
+  R* sphi = reinterpret_cast<R*>(lift_raw);   // [EPB][4][P]
+  R* sjmp = sphi + EPB * 4 * P;               // [EPB][6][4][NN]
   const int le = threadIdx.x / P, id = threadIdx.x % P;
   const int e = blk * S::EPB + le;
   const bool active = e < E;
+  // neighbour state at face point t (element le2, face f, point pq)
+  auto load_nbr = [&](int t, double qv[5]) {
+    const int le2 = t / NF, r2 = t - le2 * NF;
+    const int e2 = blk * EPB + le2;
+    if (t < EPB * NF && e2 < E) {
+      const int f = r2 / NN, pq = r2 - f * NN;
+      const int code = elem_face[e2 * 6 + f], nb = elem_nbr[e2 * 6 + f];
+      int p2, q2;
+      apply_flip<n>(code & 7, pq % n, pq / n, p2, q2);
+      const double* q = U + (size_t)(nb >> 3) * 5 * P + face_node<n>(nb & 7, p2, q2);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qv[v] = q[v * P];
+    }
+  };
+  // with one face point per thread its neighbour state is loaded before the
+  // first barrier (latency hidden behind the primitives), else in the pass
+  double qn[5];
+  if constexpr (NI == 1) load_nbr(threadIdx.x, qn);
   for (int a = threadIdx.x; a < n * n; a += blockDim.x) sD[a] = to_op<R>(Dg[a]);
   const R gm1 = gsel<R>(g.gm1, g.f_gm1), inv_R = gsel<R>(g.inv_R, g.f_inv_R), inv_w0 = to_op<R>(inv_w0d);
-  R phi[4] = {0, 0, 0, 0};
   if (active) {
     const double* q = U + (size_t)e * 5 * P + id;
     const R rho = to_op<R>(q[0]), ir = rcp_lf(rho);
     const R m0 = to_op<R>(q[P]), m1 = to_op<R>(q[2 * P]), m2 = to_op<R>(q[3 * P]);
     const R u = m0 * ir, v = m1 * ir, w = m2 * ir;
     const R p = gm1 * (to_op<R>(q[4 * P]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
-    phi[0] = u; phi[1] = v; phi[2] = w; phi[3] = p * ir * inv_R;
-    for (int a = 0; a < 4; ++a) sphi[le][a][id] = phi[a];
+    const R phi[4] = {u, v, w, p * ir * inv_R};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) sphi[(le * 4 + a) * P + id] = phi[a];
+  }
+  __syncthreads();
+  // face jumps (phi_nbr - phi)/2 (+-1/w_0), whole warps over the face points
+#pragma unroll 1
+  for (int it = 0; it < NI; ++it) {
+    const int t = threadIdx.x + it * S::THREADS;
+    const int le2 = t / NF, r2 = t - le2 * NF;
+    if constexpr (NI > 1) load_nbr(t, qn);
+    if (t < EPB * NF && blk * EPB + le2 < E) {
+      const int f = r2 / NN, pq = r2 - f * NN;
+      const int node = face_node<n>(f, pq % n, pq / n);
+      const R rho = to_op<R>(qn[0]), ir = rcp_lf(rho);
+      const R m0 = to_op<R>(qn[1]), m1 = to_op<R>(qn[2]), m2 = to_op<R>(qn[3]);
+      const R u = m0 * ir, v = m1 * ir, w = m2 * ir;
+      const R pr = gm1 * (to_op<R>(qn[4]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
+      const R onb[4] = {u, v, w, pr * ir * inv_R};
+      const R hs = (f & 1) ? R(0.5) * inv_w0 : R(-0.5) * inv_w0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        sjmp[((le2 * 6 + f) * 4 + a) * NN + pq] = (onb[a] - sphi[(le2 * 4 + a) * P + node]) * hs;
+    }
+  }
+  const int i = id % n, j = (id / n) % n, k = id / (n * n);
+  const int ijk[3] = {i, j, k};
+  R gr[12];
+  R Ja[9];
+  const R* mt = metrics + (size_t)e * 10 * P + id;
+  if (active) {
+    const R* ph = sphi + le * 4 * P;
+    R dd[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      R s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        s0 += sD[i * n + m] * ph[a * P + vidx<n>(m, j, k)];
+        s1 += sD[j * n + m] * ph[a * P + vidx<n>(i, m, k)];
+        s2 += sD[k * n + m] * ph[a * P + vidx<n>(i, j, m)];
+      }
+      dd[a][0] = s0; dd[a][1] = s1; dd[a][2] = s2;
+    }
+#pragma unroll
+    for (int r = 0; r < 9; ++r) Ja[r] = mt[r * P];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        gr[a * 3 + l] = Ja[0 * 3 + l] * dd[a][0] + Ja[1 * 3 + l] * dd[a][1] + Ja[2 * 3 + l] * dd[a][2];
   }
   __syncthreads();
   if (!active) return;
-  const int i = id % n, j = (id / n) % n, k = id / (n * n);
-  const int ijk[3] = {i, j, k};
-  R dd[4][3];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    R s0 = 0, s1 = 0, s2 = 0;
-#pragma unroll
-    for (int m = 0; m < n; ++m) {
-      s0 += sD[i * n + m] * sphi[le][a][vidx<n>(m, j, k)];
-      s1 += sD[j * n + m] * sphi[le][a][vidx<n>(i, m, k)];
-      s2 += sD[k * n + m] * sphi[le][a][vidx<n>(i, j, m)];
-    }
-    dd[a][0] = s0; dd[a][1] = s1; dd[a][2] = s2;
-  }
-  const R* mt = metrics + (size_t)e * 10 * P + id;
-  R Ja[9];
-#pragma unroll
-  for (int r = 0; r < 9; ++r) Ja[r] = mt[r * P];
-  R gr[12];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int l = 0; l < 3; ++l) gr[a * 3 + l] = Ja[0 * 3 + l] * dd[a][0] + Ja[1 * 3 + l] * dd[a][1] + Ja[2 * 3 + l] * dd[a][2];
   // surface part: one term per face that contains the node
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int id_d = ijk[d];
     if (id_d != 0 && id_d != N) continue;
-    const int s = id_d == N ? 1 : 0;
-    const int f = 2 * d + s;
-    const int code = elem_face[e * 6 + f];
-    const int nb = elem_nbr[e * 6 + f];
-    const int e2 = nb >> 3, f2 = nb & 7;
-    const int p = d == 0 ? j : i;
-    const int qq = d == 2 ? j : k;
-    int p2, q2;
-    apply_flip<n>(code & 7, p, qq, p2, q2);
-    const int id2 = face_node<n>(f2, p2, q2);
-    const double* q = U + (size_t)e2 * 5 * P + id2;
-    const R rho = to_op<R>(q[0]), ir = rcp_lf(rho);
-    const R m0 = to_op<R>(q[P]), m1 = to_op<R>(q[2 * P]), m2 = to_op<R>(q[3 * P]);
-    const R u = m0 * ir, v = m1 * ir, w = m2 * ir;
-    const R pr = gm1 * (to_op<R>(q[4 * P]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
-    const R onb[4] = {u, v, w, pr * ir * inv_R};
-    const R sg = s ? inv_w0 : -inv_w0;
+    const int f = 2 * d + (id_d == N ? 1 : 0);
+    const int pq = (d == 0 ? j : i) + n * (d == 2 ? j : k);
+    const R* jm = sjmp + (le * 6 + f) * 4 * NN + pq;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const R jump = R(0.5) * (onb[a] - phi[a]) * sg;
+      const R jump = jm[a * NN];
 #pragma unroll
       for (int l = 0; l < 3; ++l) gr[a * 3 + l] += jump * Ja[d * 3 + l];
     }
