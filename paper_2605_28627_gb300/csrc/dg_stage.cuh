@@ -369,6 +369,15 @@ __device__ __noinline__ R atanh_ratio_log(R a, R b) {
   return log(z) / (R(2) * ((z - R(1)) / (z + R(1))));
 }
 
+// Bulk prefetch of [p, p + bytes) into L2, trimmed inward to 16-byte
+// boundaries (the instruction's alignment rule); a hint, no data is returned.
+__device__ __forceinline__ void l2_prefetch(const void* p, size_t bytes) {
+  const size_t a = reinterpret_cast<size_t>(p);
+  const size_t lo = (a + 15) & ~size_t(15), hi = (a + bytes) & ~size_t(15);
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
 // Chandrashekar's two-point flux of one node pair (a, b) in one direction,
 // scaled for the scaled copies of D: F = (8 f_rho, 16 f_m, 32 f_E).  Taken as
 // densities and b = beta/4 = rho/(8p) of both nodes and the pair sums of
@@ -385,10 +394,20 @@ __device__ __forceinline__ void ec_pair(R ra, R rb, R ba, R bb, R su0, R su1, R 
   const R fr = (ra - rb) * rr, fb = (ba - bb) * rbt;
   const R ur = fr * fr, ubt = fb * fb;
   R rln2, hib;                    // 2 rho_ln and 2/beta_ln
-  if (small_u(ur)) rln2 = sr * inv_atanh_ratio(ur);
-  else rln2 = sr / atanh_ratio_log(ra, rb);
-  if (small_u(ubt)) hib = atanh_ratio(ubt) * rbt;
-  else hib = atanh_ratio_log(ba, bb) * rbt;
+  bool all_series = false;
+  // FP32 operator: one warp vote instead of two divergent branches per pair
+  // (the issue slots, not the FP32 pipe, bound that kernel); a smooth field
+  // takes the series for every pair
+  if constexpr (sizeof(R) == 4) all_series = __all_sync(__activemask(), small_u(ur) && small_u(ubt));
+  if (all_series) {
+    rln2 = sr * inv_atanh_ratio(ur);
+    hib = atanh_ratio(ubt) * rbt;
+  } else {
+    if (small_u(ur)) rln2 = sr * inv_atanh_ratio(ur);
+    else rln2 = sr / atanh_ratio_log(ra, rb);
+    if (small_u(ubt)) hib = atanh_ratio(ubt) * rbt;
+    else hib = atanh_ratio_log(ba, bb) * rbt;
+  }
   const R un4 = fma(su0, sn0, fma(su1, sn1, su2 * sn2));
   const R Xf = rln2 * un4;                      // 8 f_rho
   // 16 p_hat n_avg = Y4 (n_a + n_b); the FP32 operator uses p_hat - p_ref
@@ -437,6 +456,17 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
   __shared__ double s_tc[2];          // sin, cos of pi t (manufactured source)
   if (threadIdx.x == 0 && g.source == DG_SOURCE_MMS)
     sincospi(a.clock[0] + a.c_stage * a.clock[1], &s_tc[0], &s_tc[1]);
+  // The epilogue's operands (LSERK register, 1/J, source phases) and the face
+  // fluxes are read only after the sweeps: ask for them in L2 now, one bulk
+  // prefetch per contiguous range, so that those loads do not wait on DRAM.
+  if (active && id < 9) {
+    if (id == 0 && a.mode == 1) l2_prefetch(a.Gk + (size_t)e * 5 * P, 5 * P * sizeof(double));
+    else if (id == 1) {
+      if constexpr (sizeof(R) == 8) l2_prefetch(iJ64 + (size_t)e * 10 * P + 9 * P, P * sizeof(double));
+      else l2_prefetch(metrics + (size_t)e * 10 * P + 9 * P, P * sizeof(R));
+    } else if (id == 2 && g.source == DG_SOURCE_MMS) l2_prefetch(mms + (size_t)e * 2 * P, 2 * P * sizeof(double));
+    else if (id >= 3) l2_prefetch(fstar + (size_t)(elem_face[e * 6 + id - 3] >> 4) * 5 * NN, 5 * NN * sizeof(R));
+  }
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const double d = Dg[t];
     const R dr = to_op<R>(d);       // the scalings by powers of two are exact
@@ -493,6 +523,9 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
   R acc[5] = {0, 0, 0, 0, 0};
   constexpr int FULL = (n - 1) / 2;       // shifts with a pair for every node
   constexpr bool HALF = (n % 2) == 0;     // the shift n/2, half as many pairs
+  // FP32: one D entry per pair (one shared-memory load instead of three), the
+  // accumulators scaled by 1/4, 1/8, 1/16 after the sweeps (exact)
+  constexpr bool ONE_D = sizeof(R) == 4;
   static_assert(FULL + (HALF ? 1 : 0) == S::ROUNDS, "pair-loop rounds");
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -509,11 +542,12 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     // the partner's share of a pair, written to this node's slot of xs
     auto take_share = [&](const R* xs, int src) {
       const int rm = r * n + src;
-      acc[0] = fma(sT0[rm], xs[id], acc[0]);
-      acc[1] = fma(sT1[rm], xs[P + id], acc[1]);
-      acc[2] = fma(sT1[rm], xs[2 * P + id], acc[2]);
-      acc[3] = fma(sT1[rm], xs[3 * P + id], acc[3]);
-      acc[4] = fma(sT2[rm], xs[4 * P + id], acc[4]);
+      const R d0 = ONE_D ? sD[rm] : sT0[rm], d1 = ONE_D ? d0 : sT1[rm], d2 = ONE_D ? d0 : sT2[rm];
+      acc[0] = fma(d0, xs[id], acc[0]);
+      acc[1] = fma(d1, xs[P + id], acc[1]);
+      acc[2] = fma(d1, xs[2 * P + id], acc[2]);
+      acc[3] = fma(d1, xs[3 * P + id], acc[3]);
+      acc[4] = fma(d2, xs[4 * P + id], acc[4]);
     };
 #pragma unroll 1
     for (int s = 1; s <= FULL; ++s) {
@@ -527,11 +561,12 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
         ec_pair<R>(rho, sR[mid], beta, sB[mid], u + sU[mid], v + sU[P + mid], w + sU[2 * P + mid], kk + sK[mid], sdl,
                    Ja[d * 3] + sJd[mid], Ja[d * 3 + 1] + sJd[P + mid], Ja[d * 3 + 2] + sJd[2 * P + mid], inv_gm1, g, F);
         const int rm = r * n + m;
-        acc[0] = fma(sT0[rm], F[0], acc[0]);
-        acc[1] = fma(sT1[rm], F[1], acc[1]);
-        acc[2] = fma(sT1[rm], F[2], acc[2]);
-        acc[3] = fma(sT1[rm], F[3], acc[3]);
-        acc[4] = fma(sT2[rm], F[4], acc[4]);
+        const R d0 = ONE_D ? sD[rm] : sT0[rm], d1 = ONE_D ? d0 : sT1[rm], d2 = ONE_D ? d0 : sT2[rm];
+        acc[0] = fma(d0, F[0], acc[0]);
+        acc[1] = fma(d1, F[1], acc[1]);
+        acc[2] = fma(d1, F[2], acc[2]);
+        acc[3] = fma(d1, F[3], acc[3]);
+        acc[4] = fma(d2, F[4], acc[4]);
 #pragma unroll
         for (int c = 0; c < 5; ++c) sXs[c * P + mid] = F[c];
       }
@@ -592,6 +627,12 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     }
   }
   if (!active) return;
+  if constexpr (ONE_D) {
+    acc[0] *= R(0.25);
+#pragma unroll
+    for (int c = 1; c < 4; ++c) acc[c] *= R(0.125);
+    acc[4] *= R(0.0625);
+  }
   // viscous volume term: -sum_m D_rm (f_v . Ja^d)_m
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
