@@ -41,7 +41,8 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
              int E, Gas g, double inv_w0, AdjBufs b) {
   using S = Shape<N>;
   constexpr int n = S::n, P = S::P, NN = S::NN, EPB = S::EPB;
-  constexpr int ROUNDS = n / 2;
+  constexpr int FULL = (n - 1) / 2;       // shifts with a pair for every node
+  constexpr bool HALF = (n % 2) == 0;     // the shift n/2, half as many pairs
   extern __shared__ double adj_smem[];
   double* sD = adj_smem;                                   // [n*n]
   double* base = adj_smem + ((n * n + 1) & ~1);
@@ -83,12 +84,11 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
     const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
     const int line0 = id - r * stride;
 #pragma unroll 1
-    for (int s = 1; s <= ROUNDS; ++s) {
-      const bool half = (2 * s == n);
+    for (int s = 1; s <= FULL; ++s) {
       const int m = r + s < n ? r + s : r + s - n;
       const int mid = line0 + m * stride;
       double pm[5] = {0, 0, 0, 0, 0};
-      if (active && !(half && r >= s)) {
+      if (active) {
         NodePrim<double> ot{sPr(0, mid), sPr(1, mid), sPr(2, mid), sPr(3, mid), sPr(4, mid), sPr(5, mid)};
         const double nx = 0.5 * (Ja[d * 3] + sJa(d * 3, mid));
         const double ny = 0.5 * (Ja[d * 3 + 1] + sJa(d * 3 + 1, mid));
@@ -102,8 +102,46 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
         for (int c = 0; c < 5; ++c) sX(c, mid) = pm[c];
       }
       __syncthreads();
-      const int src = r - s >= 0 ? r - s : r - s + n;
-      if (active && !(half && src >= s)) {
+      if (active) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) pr[c] += sX(c, id);
+      }
+      __syncthreads();
+    }
+    if constexpr (HALF) {
+      // s = n/2: the pairs (r, r + n/2), r < n/2, P/2 per element, taken by
+      // the first EPB P/2 threads of the block (whole warps instead of every
+      // other lane); both adjoint shares go through shared memory
+      constexpr int H = n / 2;
+      const int t = threadIdx.x;
+      const int le2 = t / (P / 2), w2 = t - le2 * (P / 2);
+      if (t < EPB * (P / 2) && blockIdx.x * EPB + le2 < E) {
+        const int hi = w2 / stride;
+        const int ra = hi % H, rb = ra + H;
+        const int ia = w2 - hi * stride + stride * (ra + n * (hi / H));   // node with r < n/2
+        const int ib = ia + H * stride;                                     // its partner
+        double* e2 = base + (size_t)le2 * 25 * P;
+        NodePrim<double> A{e2[ia], e2[P + ia], e2[2 * P + ia], e2[3 * P + ia], e2[4 * P + ia], e2[5 * P + ia]};
+        NodePrim<double> B{e2[ib], e2[P + ib], e2[2 * P + ib], e2[3 * P + ib], e2[4 * P + ib], e2[5 * P + ib]};
+        const double* ja = e2 + (6 + d * 3) * P;
+        const double nx = 0.5 * (ja[ia] + ja[ib]);
+        const double ny = 0.5 * (ja[P + ia] + ja[P + ib]);
+        const double nz = 0.5 * (ja[2 * P + ia] + ja[2 * P + ib]);
+        const double Drm = sD[ra * n + rb], Dmr = sD[rb * n + ra];
+        const double* l2 = e2 + 15 * P;
+        double wb[5], pa[5] = {0, 0, 0, 0, 0}, pb[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < 5; ++c) wb[c] = 2.0 * (Drm * l2[c * P + ia] + Dmr * l2[c * P + ib]);
+        ec_flux_vjp(A, B, nx, ny, nz, g.inv_gm1, wb, pa, pb);
+        double* x2 = e2 + 20 * P;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          x2[c * P + ia] = pa[c];
+          x2[c * P + ib] = pb[c];
+        }
+      }
+      __syncthreads();
+      if (active) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) pr[c] += sX(c, id);
       }
