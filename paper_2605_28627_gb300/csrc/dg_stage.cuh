@@ -369,6 +369,11 @@ __device__ __noinline__ R atanh_ratio_log(R a, R b) {
   return log(z) / (R(2) * ((z - R(1)) / (z + R(1))));
 }
 
+// Named barrier: the `count` threads (whole warps) of group `id` (1..15).
+__device__ __forceinline__ void bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // Bulk prefetch of [p, p + bytes) into L2, trimmed inward to 16-byte
 // boundaries (the instruction's alignment rule); a hint, no data is returned.
 __device__ __forceinline__ void l2_prefetch(const void* p, size_t bytes) {
@@ -526,6 +531,24 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
   // FP32: one D entry per pair (one shared-memory load instead of three), the
   // accumulators scaled by 1/4, 1/8, 1/16 after the sweeps (exact)
   constexpr bool ONE_D = sizeof(R) == 4;
+  // Exchange groups of the sweeps: a direction's pairs, partner shares and
+  // metric terms stay inside its lines, so its barriers need only span the
+  // threads that hold those lines.  SCOPE 2 (n = 8, one element per block):
+  // the xi- and eta-lines of a k-plane are its 64 threads (two warps), so those
+  // directions synchronise per k-plane (named barriers 1..8) and only the
+  // zeta sweep uses the block barrier.  SCOPE 1 (elements of whole warps,
+  // several per block): one named barrier per element.  Else the block.
+  constexpr int SCOPE = (n == 8 && EPB == 1) ? 2 : ((P % 32 == 0 && EPB > 1 && EPB <= 15) ? 1 : 0);
+  auto dsync = [&](int dd) {
+    if constexpr (SCOPE == 2) {
+      if (dd < 2) bar_sync(1 + (threadIdx.x >> 6), 64);
+      else __syncthreads();
+    } else if constexpr (SCOPE == 1) {
+      bar_sync(1 + le, P);
+    } else {
+      __syncthreads();
+    }
+  };
   static_assert(FULL + (HALF ? 1 : 0) == S::ROUNDS, "pair-loop rounds");
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -534,11 +557,11 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     const int line0 = id - r * stride;
     // the partners' metric terms of this direction (shared memory holds one
     // direction at a time)
-    if (d > 0) __syncthreads();
+    if (d > 0) dsync(d);
     sJd[id] = Ja[d * 3];
     sJd[P + id] = Ja[d * 3 + 1];
     sJd[2 * P + id] = Ja[d * 3 + 2];
-    __syncthreads();
+    dsync(d);
     // the partner's share of a pair, written to this node's slot of xs
     auto take_share = [&](const R* xs, int src) {
       const int rm = r * n + src;
@@ -571,19 +594,29 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
         for (int c = 0; c < 5; ++c) sXs[c * P + mid] = F[c];
       }
       if constexpr (XB == 1) {
-        __syncthreads();
+        dsync(d);
         if (active) take_share(sX, r - s >= 0 ? r - s : r - s + n);   // written by the pair (r - s, r)
-        __syncthreads();
+        dsync(d);
       }
     }
     if constexpr (HALF) {
       // s = n/2: the pairs (r, r + n/2), r < n/2, P/2 per element, numbered in
-      // node order within each element and over the block's elements, taken
-      // by the first EPB P/2 threads; both shares go to the exchange buffer
+      // node order, taken by the first threads of the direction's exchange
+      // group (block, element, or for n = 8 the k-plane of 64 threads in the
+      // directions that stay inside it); both shares go to the exchange buffer
       constexpr int H = n / 2;
       const int t = threadIdx.x;
-      const int le2 = t / (P / 2), w2 = t - le2 * (P / 2);
-      if (t < EPB * (P / 2) && blk * EPB + le2 < E) {
+      int le2, w2;
+      bool take;
+      if constexpr (SCOPE == 2) {
+        if (d < 2) { le2 = 0; w2 = 32 * (t >> 6) + (t & 63); take = (t & 63) < 32; }
+        else { le2 = 0; w2 = t; take = t < P / 2; }
+      } else if constexpr (SCOPE == 1) {
+        le2 = le; w2 = id; take = id < P / 2;
+      } else {
+        le2 = t / (P / 2); w2 = t - le2 * (P / 2); take = t < EPB * (P / 2);
+      }
+      if (take && blk * EPB + le2 < E) {
         const int hi = w2 / stride;
         const int ia = w2 - hi * stride + stride * (hi % H + n * (hi / H));   // node with r < n/2
         const int ib = ia + H * stride;                                          // its partner
@@ -612,13 +645,13 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     }
     if constexpr (XB == 1) {
       if constexpr (HALF) {
-        __syncthreads();
+        dsync(d);
         if (active) take_share(sX, r >= n / 2 ? r - n / 2 : r + n / 2);
-        __syncthreads();
+        dsync(d);
       }
     } else {
       // every round wrote its own buffer: one barrier, then the partners' shares
-      __syncthreads();
+      dsync(d);
       if (active) {
 #pragma unroll 1
         for (int s = 1; s <= FULL; ++s) take_share(sX + (s - 1) * 5 * P, r - s >= 0 ? r - s : r - s + n);
