@@ -343,6 +343,40 @@ def run_ensemble(args, local):
     return 0
 
 
+def small_tgv_rate(dg, local, reps=20):
+    """The small Taylor-Green case (4^3 Cartesian elements of [0, 2pi]^3, N=3,
+    4096 nodes, Ma 0.1, Re 1600, LLF + BR1 + split form, dt at CFL 0.9): ten
+    LSERK4-5 steps as one graph launch, timed with CUDA events; the median of
+    `reps` launches.  At 4096 nodes this is launch- and latency-bound, so it is
+    reported as microseconds per stage, not against a roofline."""
+    import torch
+    from workloads import box_mesh, tgv_params
+    prm = tgv_params(Ma=0.1, Re=1600.0)
+    mesh = box_mesh(4, 1, lo=0.0, hi=2 * math.pi)
+    s = dg.Solver(mesh, 3, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], device=local)
+    st = torch.cuda.Stream(device="cuda:%d" % local)
+    with torch.cuda.stream(st):
+        U = s.initial_state("tgv", prm["p0"], stream=st)
+        G = torch.empty_like(U)
+    dt = s.max_dt(U, cfl=0.9, dfl=0.9, stream=st)
+    for i in range(3):
+        s.rk_step(U, G, i * dt, dt, 10, stream=st)
+    times = []
+    for i in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.rk_step(U, G, (3 + i) * dt, dt, 10, stream=st)
+        e1.record(st)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    s.close()
+    return {"workload": "Taylor-Green vortex, 4^3 Cartesian elements, N=3 (4096 nodes), Ma 0.1, Re 1600, "
+                        "10 LSERK4-5 steps per graph launch", "us_per_stage": ms * 1e3 / 50,
+            "us_per_step": ms * 1e3 / 10, "kernel_launches_per_stage": 3,
+            "dof_stage_per_s": 4096 * 50 / (ms * 1e-3)}
+
+
 def run_pid(args, local):
     """Free-stream PID runs in the setups of the paper's performance section:
     16.78 M DOF at N=3 (64^3 Cartesian elements; the paper's node-level PID
@@ -603,6 +637,7 @@ def main():
            "d2h_bytes_per_step": nb}
 
     fp32 = fp32_operator_rate(dg, N, local, prm, U0, args.steps, value / world) if rank == 0 else None
+    tgv_small = small_tgv_rate(dg, local) if rank == 0 else None
 
     sweep = {}
     if args.sweep and rank == 0:
@@ -635,7 +670,7 @@ def main():
                        "l2": "inputs larger than L2: %.0f MB of state, metrics, gradients and face data touched "
                              "per stage" % working_set_mb(solver)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-            "clocks": clk, "sweep": sweep, "fp32_operator": fp32,
+            "clocks": clk, "sweep": sweep, "fp32_operator": fp32, "tgv_small": tgv_small,
             "peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
         }
         print(json.dumps(line))
