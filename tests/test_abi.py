@@ -60,6 +60,10 @@ def test_init_rejects_bad_arguments_on_host():
     bad[3, 2, 2] = 9
     st, h, msg = _init(type(m)(**{**m.__dict__, "face_nbr": bad}))
     assert st == dg.DG_EMESH and "range" in msg
+    # an empty mesh (no elements) is an argument error, not a launch of empty grids
+    empty = type(m)(**{**m.__dict__, "xgeo": m.xgeo[:0], "face_nbr": m.face_nbr[:0]})
+    st, h, msg = _init(empty)
+    assert st == dg.DG_EINVAL and not h.value
     L = dg.load()
     assert L.dg_init(None, None, 0, None) == dg.DG_EINVAL
     assert L.dg_state_len(None) == 0
