@@ -86,8 +86,9 @@ __device__ __forceinline__ float rcp_lf(float x) {
 // threads packed over the element's 6 (N+1)^2 face points (the neighbour
 // primitives and the differences would otherwise run on every node thread of
 // a warp that holds one face node: on the narrow FP64 pipe masked lanes cost
-// as much as active ones), kept in shared memory, and only the products with
-// the node's metric terms stay with the node thread.
+// as much as active ones) and kept in shared memory; a node thread starts its
+// line sums of direction d from the jump of its d-face, so the surface term
+// costs it no arithmetic.
 template <int N, typename R, int EPB>
 constexpr size_t lift_smem_bytes() {
   // [EPB][4][P] primitives phi, [EPB][6][4][n^2] face jumps
@@ -160,50 +161,43 @@ __device__ __forceinline__ void lift_body(const double* __restrict__ U, const R*
         sjmp[((le2 * 6 + f) * 4 + a) * NN + pq] = (onb[a] - sphi[(le2 * 4 + a) * P + node]) * hs;
     }
   }
-  const int i = id % n, j = (id / n) % n, k = id / (n * n);
-  const int ijk[3] = {i, j, k};
-  R gr[12];
-  R Ja[9];
-  const R* mt = metrics + (size_t)e * 10 * P + id;
-  if (active) {
-    const R* ph = sphi + le * 4 * P;
-    R dd[4][3];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      R s0 = 0, s1 = 0, s2 = 0;
-#pragma unroll
-      for (int m = 0; m < n; ++m) {
-        s0 += sD[i * n + m] * ph[a * P + vidx<n>(m, j, k)];
-        s1 += sD[j * n + m] * ph[a * P + vidx<n>(i, m, k)];
-        s2 += sD[k * n + m] * ph[a * P + vidx<n>(i, j, m)];
-      }
-      dd[a][0] = s0; dd[a][1] = s1; dd[a][2] = s2;
-    }
-#pragma unroll
-    for (int r = 0; r < 9; ++r) Ja[r] = mt[r * P];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int l = 0; l < 3; ++l)
-        gr[a * 3 + l] = Ja[0 * 3 + l] * dd[a][0] + Ja[1 * 3 + l] * dd[a][1] + Ja[2 * 3 + l] * dd[a][2];
-  }
   __syncthreads();
   if (!active) return;
-  // surface part: one term per face that contains the node
+  // g_l = (1/J) sum_d Ja^d_l (D_d phi + jump_d): the surface term of a face in
+  // direction d multiplies the same metric term as that direction's volume
+  // term, so the jump (zero off the face) starts the line sum
+  const int i = id % n, j = (id / n) % n, k = id / (n * n);
+  const int ijk[3] = {i, j, k};
+  const R* jm[3] = {nullptr, nullptr, nullptr};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int id_d = ijk[d];
-    if (id_d != 0 && id_d != N) continue;
-    const int f = 2 * d + (id_d == N ? 1 : 0);
-    const int pq = (d == 0 ? j : i) + n * (d == 2 ? j : k);
-    const R* jm = sjmp + (le * 6 + f) * 4 * NN + pq;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const R jump = jm[a * NN];
-#pragma unroll
-      for (int l = 0; l < 3; ++l) gr[a * 3 + l] += jump * Ja[d * 3 + l];
-    }
+    if (id_d == 0 || id_d == N)
+      jm[d] = sjmp + (le * 6 + 2 * d + (id_d == N ? 1 : 0)) * 4 * NN + (d == 0 ? j : i) + n * (d == 2 ? j : k);
   }
+  const R* ph = sphi + le * 4 * P;
+  R dd[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    R s0 = jm[0] ? jm[0][a * NN] : R(0), s1 = jm[1] ? jm[1][a * NN] : R(0), s2 = jm[2] ? jm[2][a * NN] : R(0);
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      s0 += sD[i * n + m] * ph[a * P + vidx<n>(m, j, k)];
+      s1 += sD[j * n + m] * ph[a * P + vidx<n>(i, m, k)];
+      s2 += sD[k * n + m] * ph[a * P + vidx<n>(i, j, m)];
+    }
+    dd[a][0] = s0; dd[a][1] = s1; dd[a][2] = s2;
+  }
+  const R* mt = metrics + (size_t)e * 10 * P + id;
+  R Ja[9];
+#pragma unroll
+  for (int r = 0; r < 9; ++r) Ja[r] = mt[r * P];
+  R gr[12];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      gr[a * 3 + l] = Ja[0 * 3 + l] * dd[a][0] + Ja[1 * 3 + l] * dd[a][1] + Ja[2 * 3 + l] * dd[a][2];
   const R iJ = mt[9 * P];
   R* go = grad + (size_t)e * 12 * P + id;
 #pragma unroll
@@ -472,15 +466,18 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     } else if (id == 2 && g.source == DG_SOURCE_MMS) l2_prefetch(mms + (size_t)e * 2 * P, 2 * P * sizeof(double));
     else if (id >= 3) l2_prefetch(fstar + (size_t)(elem_face[e * 6 + id - 3] >> 4) * 5 * NN, 5 * NN * sizeof(R));
   }
+  const R inv_w0 = to_op<R>(inv_w0d);
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const double d = Dg[t];
     const R dr = to_op<R>(d);       // the scalings by powers of two are exact
-    sD[t] = dr;
+    // sD's diagonal is read only by the viscous line sums: at the two end
+    // nodes it carries the viscous part of the surface term too,
+    // D_00 + 1/w_0 and D_NN - 1/w_0 (the pair sweeps use m != r only)
+    sD[t] = t == 0 ? dr + inv_w0 : (t == n * n - 1 ? dr - inv_w0 : dr);
     sT0[t] = R(0.25) * dr;
     sT1[t] = R(0.125) * dr;
     sT2[t] = R(0.0625) * dr;
   }
-  const R inv_w0 = to_op<R>(inv_w0d);
   double q[5] = {0, 0, 0, 0, 0};
   R Ja[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   R rho = R(1), u = 0, v = 0, w = 0, beta = 0, kk = 0;
@@ -666,7 +663,8 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     for (int c = 1; c < 4; ++c) acc[c] *= R(0.125);
     acc[4] *= R(0.0625);
   }
-  // viscous volume term: -sum_m D_rm (f_v . Ja^d)_m
+  // viscous volume term -sum_m D_rm (f_v . Ja^d)_m and, at the end nodes, the
+  // viscous part (+-f_v . Ja^d)/w_0 of the surface term (in sD's diagonal)
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int r = ijk[d];
@@ -684,8 +682,9 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     }
     acc[1] -= v0; acc[2] -= v1; acc[3] -= v2; acc[4] -= v3;
   }
-  // surface integral: (F*_out + f_v . n sJ) / w_0 at each face containing the
-  // node (the -f . n sJ part has cancelled against the diagonal volume term)
+  // surface integral: F*_out / w_0 at each face containing the node (the
+  // -f . n sJ part has cancelled against the diagonal volume term, the
+  // viscous part is in the line sums above)
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int id_d = ijk[d];
@@ -706,11 +705,8 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
       fsr = fstar + (size_t)fid * 5 * NN + p2 + n * q2;
       fs_sign = -inv_w0;
     }
-    const R vs = sgn ? inv_w0 : -inv_w0;
-    acc[0] = fma(fs_sign, fsr[0], acc[0]);
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-      acc[1 + c] = fma(fs_sign, fsr[(c + 1) * NN], fma(vs, sFv[(d * 4 + c) * P + id], acc[1 + c]));
+    for (int c = 0; c < 5; ++c) acc[c] = fma(fs_sign, fsr[c * NN], acc[c]);
   }
   // Manufactured source, density wave rho = 2 + A sin(phi), phi = pi (x+y+z-t),
   // u = (1,1,1), p = 1: residual of Eq. 1 = [2r', 2r', 2r', 2r', 3r' - lambda Lap T],
