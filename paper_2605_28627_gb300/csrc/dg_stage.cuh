@@ -518,6 +518,10 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
       for (int c = 0; c < 4; ++c) sFv[(d * 4 + c) * P + id] = fv[c];
     }
   }
+  // the xi sweep's metric terms go out with the node data (one barrier for both)
+  sJd[id] = Ja[0];
+  sJd[P + id] = Ja[1];
+  sJd[2 * P + id] = Ja[2];
   __syncthreads();
   const int i = id % n, j = (id / n) % n, k = id / NN;
   const int ijk[3] = {i, j, k};
@@ -553,12 +557,17 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
     const int line0 = id - r * stride;
     // the partners' metric terms of this direction (shared memory holds one
-    // direction at a time)
-    if (d > 0) dsync(d);
-    sJd[id] = Ja[d * 3];
-    sJd[P + id] = Ja[d * 3 + 1];
-    sJd[2 * P + id] = Ja[d * 3 + 2];
-    dsync(d);
+    // direction at a time).  Overwriting this node's entries needs no barrier
+    // before: every read of them in the previous sweep (its pair rounds) came
+    // before that sweep's last barrier, which this thread has passed; the
+    // barrier after the writes also orders the previous sweep's share reads
+    // before this sweep's exchange-buffer writes.
+    if (d > 0) {
+      sJd[id] = Ja[d * 3];
+      sJd[P + id] = Ja[d * 3 + 1];
+      sJd[2 * P + id] = Ja[d * 3 + 2];
+      dsync(d);
+    }
     // the partner's share of a pair, written to this node's slot of xs
     auto take_share = [&](const R* xs, int src) {
       const int rm = r * n + src;
