@@ -281,3 +281,55 @@ def test_rk414_parity(orc, dg, nodes):
     # the ensemble steps LSERK4-5 only
     with pytest.raises(dg.DGError):
         dg.Ensemble([s])
+
+
+def test_init_rejects_inverted_element_on_gpu(dg):
+    """A mirrored element (left-handed frame) has a negative Jacobian at its
+    nodes: dg_init computes the geometry on the device and refuses the mesh."""
+    m = box_mesh(2, 1, rotate_seed=3)
+    inv = m.xgeo.copy()
+    inv[0] = inv[0][:, :, :, ::-1]
+    bad = type(m)(**{**m.__dict__, "xgeo": inv})
+    with pytest.raises(dg.DGError) as err:
+        dg.Solver(bad, 2)
+    assert err.value.status == dg.DG_EMESH and "Jacobian" in str(err.value)
+    # the library is still usable afterwards
+    s = dg.Solver(m, 2)
+    U = s.initial_state("tgv", 10.0)
+    assert torch.isfinite(U).all()
+    s.close()
+
+
+@pytest.mark.parametrize("N", [3, 4, 7])
+def test_inviscid_entropy_conservation_on_gpu(orc, dg, N):
+    """Degenerate case mu = 0 (Euler) with the two-point flux on the faces:
+    the GPU operator matches the oracle and conserves entropy discretely,
+    sum w J w(U) . R(U) = 0 to round-off on the curved rotated mesh; with LLF
+    faces entropy is dissipated (a property that holds at any size)."""
+    mesh = box_mesh(2, N, deform="sinprod", rotate_seed=17)
+    gamma = 1.4
+    U = random_state(mesh.n_elems, N, seed=5)
+    o = orc.Oracle(mesh, N, mu=0.0, surf_flux=dg.FLUX_EC)
+    s = dg.Solver(mesh, N, mu=0.0, surf_flux=dg.FLUX_EC)
+    R = s.time_derivative(_cuda(U)).cpu().numpy()
+    assert (_rel_err_per_var(R, o.time_derivative(U)) < RTOL_R * _geo_amp(orc, N, N)).all()
+    _, w, _ = orc.basis(N)
+    wq = np.einsum("k,j,i->kji", w, w, w).reshape(-1)
+    _, J = s.geometry()
+    J = J.cpu().numpy().reshape(mesh.n_elems, -1)
+    Uf = U.reshape(mesh.n_elems, 5, -1)
+    r = Uf[:, 0]
+    u = Uf[:, 1:4] / r[:, None]
+    p = (gamma - 1) * (Uf[:, 4] - 0.5 * r * (u ** 2).sum(1))
+    ent = np.log(p * r ** -gamma)
+    W = np.concatenate([((gamma - ent) / (gamma - 1) - r * (u ** 2).sum(1) / (2 * p))[:, None],
+                        r[:, None] * u / p[:, None], (-r / p)[:, None]], 1)
+    R = R.reshape(mesh.n_elems, 5, -1)
+    prod = np.einsum("evp,evp,ep->", W, R, J * wq)
+    scale = np.einsum("evp,evp,ep->", np.abs(W), np.abs(R), J * wq)
+    assert abs(prod) < 1e-13 * scale, (prod, scale)
+    s2 = dg.Solver(mesh, N, mu=0.0, surf_flux=dg.FLUX_LLF)
+    R2 = s2.time_derivative(_cuda(U)).cpu().numpy().reshape(mesh.n_elems, 5, -1)
+    assert np.einsum("evp,evp,ep->", W, R2, J * wq) < -1e-6 * scale
+    s.close()
+    s2.close()
