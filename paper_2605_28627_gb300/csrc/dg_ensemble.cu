@@ -204,6 +204,10 @@ static int epb_of(int N, int choice, int precision) {
 
 using namespace dg;
 
+// Side streams of the ensemble graph: how many independent work units run as
+// parallel branches within a step.
+constexpr int kEnsembleBranches = 8;
+
 struct dg_ensemble {
   std::vector<Ctx*> members;
   int device = 0;
@@ -222,6 +226,7 @@ struct dg_ensemble {
   std::vector<double*> cur_U, cur_G;
   cudaGraphExec_t graph = nullptr;
   int graph_nsteps = 0;
+  std::vector<cudaStream_t> branch;   // side streams of the captured graph's parallel branches
   std::string err;
   std::string plan_json;
 };
@@ -288,17 +293,21 @@ static dg_status upload_members(dg_ensemble* e) {
 
 // Per-member candidate: the single-run kernels of each member in turn (best
 // when every member fills the GPU by itself).
+static cudaError_t one_member_stage(dg_ensemble* e, int r, int k, const double* A, const double* B, cudaStream_t s) {
+  const Ctx& c = *e->members[r];
+  double* U = e->cur_U[r];
+  cudaError_t err;
+  if ((err = launch_lift(c, U, s)) != cudaSuccess) return err;
+  if ((err = launch_face(c, U, s)) != cudaSuccess) return err;
+  StageArgs a{U, U, e->cur_G[r], nullptr, e->clocks + 2 * r, kRkC[k], A[k], B[k], 1};
+  return launch_volume(c, a, s);
+}
+
 static cudaError_t member_stage(dg_ensemble* e, const Group& g, int k, const double* A, const double* B,
                                 cudaStream_t s) {
   cudaError_t err = cudaSuccess;
-  for (int r : g.members) {
-    const Ctx& c = *e->members[r];
-    double* U = e->cur_U[r];
-    if ((err = launch_lift(c, U, s)) != cudaSuccess) return err;
-    if ((err = launch_face(c, U, s)) != cudaSuccess) return err;
-    StageArgs a{U, U, e->cur_G[r], nullptr, e->clocks + 2 * r, kRkC[k], A[k], B[k], 1};
-    if ((err = launch_volume(c, a, s)) != cudaSuccess) return err;
-  }
+  for (int r : g.members)
+    if ((err = one_member_stage(e, r, k, A, B, s)) != cudaSuccess) return err;
   return err;
 }
 
@@ -531,6 +540,7 @@ dg_status dg_ensemble_destroy(dg_ensemble* e) {
   }
   void* bufs[] = {e->d_G, e->d_clocks, e->d_len, e->d_tdt, e->clocks};
   for (void* p : bufs) if (p) cudaFree(p);
+  for (cudaStream_t bs : e->branch) cudaStreamDestroy(bs);
   if (e->h_tdt) cudaFreeHost(e->h_tdt);
   delete e;
   return DG_OK;
@@ -574,15 +584,64 @@ dg_status dg_ensemble_step(dg_ensemble* e, double* const* dU, double* const* dG,
     cudaStream_t cs;
     ENS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), e, "capture stream");
     cudaGraph_t gr = nullptr;
-    cudaError_t err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    // Independent work units: a tile-table group (all its members in one set
+    // of launches) or one member of a per-member group.  Within a step the
+    // units are parallel branches of the graph, dealt to the side streams by
+    // size (largest first, to the least loaded), so that one unit's kernel
+    // tails and launch gaps are filled by another's blocks.
+    struct Unit { int g, r; double dof; };
+    std::vector<Unit> units;
+    for (size_t gi = 0; gi < e->groups.size(); ++gi) {
+      const Group& g = e->groups[gi];
+      if (g.plan.epb_choice == 2) {
+        for (int r : g.members) units.push_back({(int)gi, r, (double)e->members[r]->E * e->members[r]->P});
+      } else {
+        double dof = 0;
+        for (int r : g.members) dof += (double)e->members[r]->E * e->members[r]->P;
+        units.push_back({(int)gi, -1, dof});
+      }
+    }
+    std::sort(units.begin(), units.end(), [](const Unit& a, const Unit& b) { return a.dof > b.dof; });
+    const int nb = std::max(1, std::min<int>(kEnsembleBranches, (int)units.size()));
+    std::vector<std::vector<Unit>> lanes(nb);
+    std::vector<double> load(nb, 0.0);
+    for (const Unit& u : units) {
+      const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      lanes[b].push_back(u);
+      load[b] += u.dof;
+    }
+    cudaError_t err = cudaSuccess;
+    while ((int)e->branch.size() < nb && err == cudaSuccess) {
+      cudaStream_t bs;
+      err = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+      if (err == cudaSuccess) e->branch.push_back(bs);
+    }
+    std::vector<cudaEvent_t> evs;
+    auto event = [&](cudaEvent_t* ev) {
+      cudaError_t ce = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+      if (ce == cudaSuccess) evs.push_back(*ev);
+      return ce;
+    };
+    if (err == cudaSuccess) err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     for (int st = 0; st < nsteps && err == cudaSuccess; ++st) {
-      for (int r = 0; r < n && err == cudaSuccess; ++r)
-        err = cudaMemsetAsync(e->cur_G[r], 0, sizeof(double) * (size_t)e->members[r]->E * 5 * e->members[r]->P, cs);
-      for (int k = 0; k < 5 && err == cudaSuccess; ++k)
-        for (const Group& g : e->groups) {
-          err = enqueue_stage(e, g, k, cs);
-          if (err != cudaSuccess) break;
+      cudaEvent_t fork;
+      if ((err = event(&fork)) != cudaSuccess || (err = cudaEventRecord(fork, cs)) != cudaSuccess) break;
+      for (int b = 0; b < nb && err == cudaSuccess; ++b) {
+        cudaStream_t bs = e->branch[b];
+        err = cudaStreamWaitEvent(bs, fork, 0);
+        for (const Unit& u : lanes[b]) {
+          const Group& g = e->groups[u.g];
+          for (int r : g.members) {
+            if (err != cudaSuccess || (u.r >= 0 && r != u.r)) continue;
+            err = cudaMemsetAsync(e->cur_G[r], 0, sizeof(double) * (size_t)e->members[r]->E * e->members[r]->P * 5, bs);
+          }
+          for (int k = 0; k < 5 && err == cudaSuccess; ++k)
+            err = u.r >= 0 ? one_member_stage(e, u.r, k, kRkA, kRkB, bs) : enqueue_stage(e, g, k, bs);
         }
+        cudaEvent_t join;
+        if (err == cudaSuccess && (err = event(&join)) == cudaSuccess && (err = cudaEventRecord(join, bs)) == cudaSuccess)
+          err = cudaStreamWaitEvent(cs, join, 0);
+      }
       if (err == cudaSuccess) {
         k_ens_clock_advance<<<(n + 127) / 128, 128, 0, cs>>>(e->d_clocks, n);
         err = cudaGetLastError();
@@ -592,6 +651,7 @@ dg_status dg_ensemble_step(dg_ensemble* e, double* const* dU, double* const* dG,
     if (err == cudaSuccess) err = e2;
     if (err == cudaSuccess) err = cudaGraphInstantiate(&e->graph, gr, 0);
     if (gr) cudaGraphDestroy(gr);
+    for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
     cudaStreamDestroy(cs);
     if (err != cudaSuccess) { e->graph = nullptr; return ens_fail(e, DG_ECUDA, "ensemble graph capture", err); }
     e->graph_nsteps = nsteps;
