@@ -43,22 +43,40 @@ struct VShape : Shape<N, EPB_> {
   static constexpr int ROUNDS = (N + 1) / 2;    // shifts s = 1..n/2 (s = n/2 half-used for even n)
 };
 
-// Exchange buffers of the pair loop: one per round when they fit (all rounds
-// of a direction then share one barrier), else one (a barrier per round).
-template <int N, typename R, int EPB>
+// Blocks per SM the single-context volume kernel's register and shared-memory
+// budget must allow.  FP32 tiles of up to 512 threads: two (the FP32 operator
+// is latency-bound).  FP64 at N = 6, 7: two -- a hundred-odd bytes of spilled
+// registers cost less than an SM with only 11 or 16 warps to feed its FP64
+// pipe from (+2.4 % at N = 6, +0.5 % at N = 7; at N = 4, 5 a third block did
+// not pay).
+template <int N, typename R>
+constexpr int vol_min_blocks() {
+  constexpr int threads = Shape<N>::THREADS;
+  if (sizeof(R) == 4) return threads <= 512 ? 2 : 1;
+  return (N == 6 || N == 7) ? 2 : 1;
+}
+
+// Exchange buffers of the pair loop: one per round when they fit the shared
+// memory of vol_min_blocks blocks per SM (all rounds of a direction then share
+// one barrier), else one (a barrier per round).  The choice fixes the order in
+// which a node sums its pair terms, so every kernel that runs the volume body
+// for this (N, R) -- the single-context tile and both ensemble tiles -- takes
+// the same value and gives bit-identical results.
+template <int N, typename R>
 struct VXbuf {
-  static constexpr int P = (N + 1) * (N + 1) * (N + 1), ROUNDS = (N + 1) / 2;
+  static constexpr int P = (N + 1) * (N + 1) * (N + 1), ROUNDS = (N + 1) / 2, EPB = Shape<N>::EPB,
+                       MINB = vol_min_blocks<N, R>();
   static constexpr size_t base_words = 3 * (N + 1) * (N + 1) + (((N + 1) * (N + 1) + 3) & ~3) +
                                        (size_t)EPB * (21 + (sizeof(R) == 4 ? 1 : 0)) * P;
-  static constexpr int value =
-      sizeof(R) * (base_words + (size_t)EPB * 5 * P * ROUNDS) <= 200 * 1024 ? ROUNDS : 1;
+  static constexpr size_t budget = MINB == 1 ? 200 * 1024 : (226 * 1024) / MINB - 1024;
+  static constexpr int value = sizeof(R) * (base_words + (size_t)EPB * 5 * P * ROUNDS) <= budget ? ROUNDS : 1;
   static constexpr int PER_ELEM = (21 + 5 * value) * P;   // operator words of smem per element
 };
 
 template <int N, typename R, int EPB>
 constexpr size_t volume_smem_bytes() {
   // the FP32 operator keeps one more word per node (the offset pressure term)
-  return sizeof(R) * (3 * (N + 1) * (N + 1) + (((N + 1) * (N + 1) + 3) & ~3) + EPB * VXbuf<N, R, EPB>::PER_ELEM +
+  return sizeof(R) * (3 * (N + 1) * (N + 1) + (((N + 1) * (N + 1) + 3) & ~3) + EPB * VXbuf<N, R>::PER_ELEM +
                       (sizeof(R) == 4 ? EPB * (N + 1) * (N + 1) * (N + 1) : 0));
 }
 
@@ -438,8 +456,8 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
   R* sT1 = sT0 + n * n;               // D/8   (momentum: M = 16 f_m)
   R* sT2 = sT1 + n * n;               // D/16  (energy: 32 f_E)
   const int le = threadIdx.x / P, id = threadIdx.x - le * P;
-  constexpr int XB = VXbuf<N, R, EPB_>::value;
-  constexpr int PER_ELEM = VXbuf<N, R, EPB_>::PER_ELEM;
+  constexpr int XB = VXbuf<N, R>::value;
+  constexpr int PER_ELEM = VXbuf<N, R>::PER_ELEM;
   R* const tile0 = sT2 + ((n * n + 3) & ~3);   // element tiles, PER_ELEM words each
   R* base = tile0 + le * PER_ELEM;
   R* sR = base;                       // rho

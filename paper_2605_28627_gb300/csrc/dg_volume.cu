@@ -5,10 +5,8 @@
 
 namespace dg {
 
-// FP32 tiles of up to 512 threads are kept to <= 64 registers so that two
-// blocks share an SM (the FP32 operator is latency-bound, the FP64 one is not).
 template <int N, typename R>
-__global__ void __launch_bounds__(VShape<N>::THREADS, (sizeof(R) == 4 && VShape<N>::THREADS <= 512) ? 2 : 1)
+__global__ void __launch_bounds__(VShape<N>::THREADS, vol_min_blocks<N, R>())
 k_volume2(StageArgs a, const R* __restrict__ metrics, const double* __restrict__ iJ64,
           const R* __restrict__ grad, const R* __restrict__ fstar, const int* __restrict__ elem_face,
           const double* __restrict__ mms, const double* __restrict__ Dg, int E, Gas g, double inv_w0) {
