@@ -33,9 +33,10 @@ struct AdjBufs {
 };
 
 // ---------------------------------------------------------------------------
-// A1: volume adjoint.  lamV = -lambda / J.
+// A1: volume adjoint.  lamV = -lambda / J.  Two blocks per SM where a block
+// has at most 256 threads (one alone leaves the SM seven or eight warps).
 template <int N>
-__global__ void __launch_bounds__(Shape<N>::THREADS)
+__global__ void __launch_bounds__(Shape<N>::THREADS, Shape<N>::THREADS <= 256 ? 2 : 1)
 k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const double* __restrict__ metrics,
              const double* __restrict__ grad, const int* __restrict__ elem_face, const double* __restrict__ Dg,
              int E, Gas g, double inv_w0, AdjBufs b) {
