@@ -25,22 +25,34 @@ __device__ __forceinline__ void prim_vjp(const double q[5], double rb, const dou
   qb[4] += gp;
 }
 
+// 1/x for the adjoint's positive operands (densities, pressures, beta sums,
+// log means): hardware approximation and one cubic Newton-Raphson step
+// (below 1 ulp), a fraction of an IEEE division on GB300's narrow FP64 pipe.
+__device__ __forceinline__ double adj_rcp(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+
 // Logarithmic mean and its partial derivatives, consistent with log_mean():
 // series branch L = s / (2 F(u)), u = ((a-b)/s)^2, F = 1 + u/3 + u^2/5 + u^3/7;
 // logarithmic branch L = (a - b) / ln(a/b) with dL/da = (1 - L/a)/ln(a/b),
 // dL/db = (L/b - 1)/ln(a/b).
 __device__ __forceinline__ double log_mean_d(double a, double b, double& La, double& Lb) {
   const double s = a + b;
-  const double f = (a - b) / s;
+  const double is = adj_rcp(s);
+  const double f = (a - b) * is;
   const double u = f * f;
   if (u < 1e-4) {
     const double F = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
     const double Fp = 1.0 / 3.0 + u * (2.0 / 5.0 + u * (3.0 / 7.0));
-    const double L = s / (2.0 * F);
-    const double dLdu = -s * Fp / (2.0 * F * F);
-    const double is2 = 1.0 / (s * s);
-    La = 1.0 / (2.0 * F) + dLdu * 2.0 * f * (2.0 * b * is2);
-    Lb = 1.0 / (2.0 * F) + dLdu * 2.0 * f * (-2.0 * a * is2);
+    const double i2F = adj_rcp(2.0 * F);            // 1/(2F)
+    const double L = s * i2F;
+    const double dLdu = -2.0 * s * Fp * i2F * i2F;   // -s F' / (2 F^2)
+    const double is2 = is * is;
+    La = i2F + dLdu * 2.0 * f * (2.0 * b * is2);
+    Lb = i2F + dLdu * 2.0 * f * (-2.0 * a * is2);
     return L;
   }
   const double z = a / b;
@@ -62,12 +74,13 @@ __device__ __forceinline__ void ec_flux_vjp(const NodePrim<double>& A, const Nod
   const double beta_ln = log_mean_d(A.beta, B.beta, Lba, Lbb);
   const double ua = 0.5 * (A.u + B.u), va = 0.5 * (A.v + B.v), wa = 0.5 * (A.w + B.w);
   const double sr = A.rho + B.rho, sb = A.beta + B.beta;
-  const double p_hat = 0.5 * sr / sb;
+  const double isb = adj_rcp(sb), ibl = adj_rcp(beta_ln);
+  const double p_hat = 0.5 * sr * isb;
   const double K = 0.25 * (A.u * A.u + A.v * A.v + A.w * A.w + B.u * B.u + B.v * B.v + B.w * B.w);
   const double un = ua * nx + va * ny + wa * nz;
   const double f0 = rho_ln * un;
   const double fm0 = f0 * ua + p_hat * nx, fm1 = f0 * va + p_hat * ny, fm2 = f0 * wa + p_hat * nz;
-  const double H = 0.5 * inv_gm1 / beta_ln - K;
+  const double H = 0.5 * inv_gm1 * ibl - K;
   // f4 = f0 H + ubar . fm
   const double fmb0 = fb[1] + fb[4] * ua, fmb1 = fb[2] + fb[4] * va, fmb2 = fb[3] + fb[4] * wa;
   double ubb0 = fb[4] * fm0 + f0 * fmb0;
@@ -79,20 +92,21 @@ __device__ __forceinline__ void ec_flux_vjp(const NodePrim<double>& A, const Nod
   const double rlb = f0b * un;
   const double unb = f0b * rho_ln;
   ubb0 += unb * nx; ubb1 += unb * ny; ubb2 += unb * nz;
-  const double blb = -Hb * 0.5 * inv_gm1 / (beta_ln * beta_ln);
+  const double blb = -Hb * 0.5 * inv_gm1 * (ibl * ibl);
   const double Kb = -Hb;
   // ubar = (u_a + u_b)/2, K = (|u_a|^2 + |u_b|^2)/4
   pa[1] += 0.5 * ubb0 + 0.5 * Kb * A.u;  pbv[1] += 0.5 * ubb0 + 0.5 * Kb * B.u;
   pa[2] += 0.5 * ubb1 + 0.5 * Kb * A.v;  pbv[2] += 0.5 * ubb1 + 0.5 * Kb * B.v;
   pa[3] += 0.5 * ubb2 + 0.5 * Kb * A.w;  pbv[3] += 0.5 * ubb2 + 0.5 * Kb * B.w;
   // p_hat = sr / (2 sb)
-  const double srb = phb * 0.5 / sb;
-  const double sbb = -phb * p_hat / sb;
+  const double srb = phb * 0.5 * isb;
+  const double sbb = -phb * p_hat * isb;
   double rab = srb + rlb * Lra, rbb = srb + rlb * Lrb;
   const double bab = sbb + blb * Lba, bbb = sbb + blb * Lbb;
   // beta = rho / (2 p)
-  rab += bab * 0.5 / A.p;  pa[4] += -bab * A.beta / A.p;
-  rbb += bbb * 0.5 / B.p;  pbv[4] += -bbb * B.beta / B.p;
+  const double iAp = adj_rcp(A.p), iBp = adj_rcp(B.p);
+  rab += bab * 0.5 * iAp;  pa[4] += -bab * A.beta * iAp;
+  rbb += bbb * 0.5 * iBp;  pbv[4] += -bbb * B.beta * iBp;
   pa[0] += rab;
   pbv[0] += rbb;
 }
