@@ -8,17 +8,24 @@
 //    pair on a line is evaluated once, in rounds of a fixed cyclic shift s;
 //    the partner's share goes through shared memory.  For even n the last
 //    shift (s = n/2) pairs each node with the opposite one, so it holds only
-//    half as many pairs as nodes: those are packed onto the first half of the
-//    block's threads (whole warps idle instead of every other lane, which the
-//    narrow FP64 pipe would still charge) and both shares go through shared
-//    memory.
+//    half as many pairs as nodes: those are packed onto the first threads of
+//    the sweep's exchange group (whole warps idle instead of every other
+//    lane, which the narrow FP64 pipe would still charge) and both shares go
+//    through shared memory.
+//  * Barriers span only a sweep's exchange group where that is a whole
+//    number of warps (a k-plane for the xi and eta sweeps at N = 7, an
+//    element when a block holds several).
 //  * The diagonal terms 2 D_ii f(q_i) . Ja_i vanish for interior LGL nodes
 //    and cancel exactly against the -f . n sJ / w_0 part of the surface term
 //    at the two end nodes (2 D_00 = -1/w_0, 2 D_NN = 1/w_0), so neither is
 //    evaluated.
 //  * Reciprocals instead of divides, logarithmic means by the Ismail-Roe
 //    series with the reciprocal series for 1/F, constant factors folded into
-//    scaled copies of D, the series/log switch decided in integer ALU.
+//    scaled copies of D (FP64) or applied once to the sums (FP32), the
+//    series/log switch decided in integer ALU (FP64) or by one warp vote
+//    (FP32).
+//  * The viscous part of the surface term rides in the diagonal of the
+//    viscous line sums; the lifting's face jumps start its line sums.
 #pragma once
 
 #include "dg_physics.cuh"
