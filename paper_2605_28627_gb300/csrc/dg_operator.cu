@@ -4,10 +4,11 @@
 
 namespace dg {
 
-// The FP32 lifting is latency-bound: tiles of up to 512 threads are kept to
-// <= 42 registers so that three blocks share an SM.
+// The FP32 lifting is latency-bound: its register allocation must leave room
+// for 48 warps per SM (three 512-thread blocks at N = 7, twelve at N = 3).
 template <int N, typename R>
-__global__ void __launch_bounds__(Shape<N>::THREADS, (sizeof(R) == 4 && Shape<N>::THREADS <= 512) ? 3 : 1)
+__global__ void __launch_bounds__(Shape<N>::THREADS,
+                                  sizeof(R) == 4 && Shape<N>::THREADS < 1536 ? 1536 / Shape<N>::THREADS : 1)
 k_lift(const double* __restrict__ U, const R* __restrict__ metrics, const int* __restrict__ elem_nbr,
        const int* __restrict__ elem_face, const double* __restrict__ Dg, R* __restrict__ grad, int E, Gas g,
        double inv_w0) {

@@ -388,9 +388,31 @@ __device__ __noinline__ R atanh_ratio_log(R a, R b) {
   return log(z) / (R(2) * ((z - R(1)) / (z + R(1))));
 }
 
-// Named barrier: the `count` threads (whole warps) of group `id` (1..15).
-__device__ __forceinline__ void bar_sync(int id, int count) {
+// Named barrier: the `count` threads (whole warps) of group `id` (1..15), the
+// number taken from a register.  ptxas then reserves all 16 hardware barriers
+// for the kernel, which limits it to four blocks per SM: for kernels that run
+// fewer blocks anyway (one 512-thread element per block).
+__device__ __forceinline__ void bar_sync_reg(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// The same with the barrier number an immediate in every branch of a switch,
+// so that ptxas reserves only MAXID + 1 barriers (1 <= id <= MAXID <= 15): for
+// kernels of small blocks that need more than four per SM.
+template <int MAXID>
+__device__ __forceinline__ void bar_sync(int id, int count) {
+  static_assert(MAXID >= 1 && MAXID <= 15, "named barriers 1..15");
+#define DG_BAR_CASE(k) \
+  case k:              \
+    if constexpr (k <= MAXID) asm volatile("bar.sync %0, %1;" ::"n"(k), "r"(count) : "memory"); \
+    break;
+  switch (id) {
+    DG_BAR_CASE(1) DG_BAR_CASE(2) DG_BAR_CASE(3) DG_BAR_CASE(4) DG_BAR_CASE(5)
+    DG_BAR_CASE(6) DG_BAR_CASE(7) DG_BAR_CASE(8) DG_BAR_CASE(9) DG_BAR_CASE(10)
+    DG_BAR_CASE(11) DG_BAR_CASE(12) DG_BAR_CASE(13) DG_BAR_CASE(14) DG_BAR_CASE(15)
+    default: break;
+  }
+#undef DG_BAR_CASE
 }
 
 // Bulk prefetch of [p, p + bytes) into L2, trimmed inward to 16-byte
@@ -567,10 +589,10 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
   constexpr int SCOPE = (n == 8 && EPB == 1) ? 2 : ((P % 32 == 0 && EPB > 1 && EPB <= 15) ? 1 : 0);
   auto dsync = [&](int dd) {
     if constexpr (SCOPE == 2) {
-      if (dd < 2) bar_sync(1 + (threadIdx.x >> 6), 64);
+      if (dd < 2) bar_sync_reg(1 + (threadIdx.x >> 6), 64);
       else __syncthreads();
     } else if constexpr (SCOPE == 1) {
-      bar_sync(1 + le, P);
+      bar_sync<EPB>(1 + le, P);
     } else {
       __syncthreads();
     }
