@@ -45,7 +45,7 @@ def build_mesh(N):
 
 # DRAM bytes (read + write) per launch of the volume kernel from one ncu capture
 # of the current kernel version on this workload; absent = not captured.
-MEASURED_TRAFFIC = {(7, "fp64"): 602.895104e6 + 144.417280e6}
+MEASURED_TRAFFIC = {(7, "fp64"): 669.022720e6 + 218.296320e6}
 
 
 # ---------------------------------------------------------------------------
@@ -642,16 +642,20 @@ def main():
     sweep = {}
     if args.sweep and rank == 0:
         for Ns in [int(v) for v in args.sweep.split(",") if v]:
+            dofs = K_ELEMS ** 3 * (Ns + 1) ** 3
             if Ns == N:
                 sweep[str(Ns)] = {"dof_stage_per_s": value / world, "pid_ns": 1e9 * world / value,
                                   "volume_ms": ms3[2], "volume_roofline_frac": roofline["frac"]}
-                continue
-            ms, ms3n = sweep_rate(dg, Ns, local, prm)
-            dofs = K_ELEMS ** 3 * (Ns + 1) ** 3
-            # roofline of the volume kernel at this N: algorithmic FP64 flops / its event time
-            ach = volume_flops_per_dof(Ns) * dofs / (ms3n[2] * 1e-3) / 1e12
-            sweep[str(Ns)] = {"dof_stage_per_s": dofs * 5 / (ms * 1e-3), "pid_ns": ms * 1e6 / (dofs * 5),
-                              "volume_ms": ms3n[2], "volume_roofline_frac": ach / fp64_peak}
+            else:
+                ms, ms3n = sweep_rate(dg, Ns, local, prm)
+                # roofline of the volume kernel at this N: algorithmic FP64 flops / its event time
+                ach = volume_flops_per_dof(Ns) * dofs / (ms3n[2] * 1e-3) / 1e12
+                sweep[str(Ns)] = {"dof_stage_per_s": dofs * 5 / (ms * 1e-3), "pid_ns": ms * 1e6 / (dofs * 5),
+                                  "volume_ms": ms3n[2], "volume_roofline_frac": ach / fp64_peak}
+            # the FP32-operator path on the same mesh and state
+            ms32, _ = sweep_rate(dg, Ns, local, prm, precision=dg.FP32OP)
+            sweep[str(Ns)]["fp32op_dof_stage_per_s"] = dofs * 5 / (ms32 * 1e-3)
+            sweep[str(Ns)]["fp32op_speedup"] = sweep[str(Ns)]["pid_ns"] / (ms32 * 1e6 / (dofs * 5))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -723,11 +727,11 @@ def working_set_mb(s):
     return doubles * 8 / 1e6
 
 
-def sweep_rate(dg, N, dev, prm, steps=5):
+def sweep_rate(dg, N, dev, prm, steps=5, precision=None):
     import torch
     mesh = build_mesh(N)
     s = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=dg.SOURCE_MMS,
-                  device=dev)
+                  device=dev, precision=dg.FP64 if precision is None else precision)
     st = torch.cuda.Stream(device="cuda:%d" % dev)
     with torch.cuda.stream(st):
         U = s.initial_state("mms", 0.0, stream=st)
