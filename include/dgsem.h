@@ -150,7 +150,8 @@ dg_status dg_integrals(dg_ctx* ctx, const double* dU, double* host_out8, dg_stre
  * dt = min(cfl * 2/((2N+1) max_nodes sum_d lambda_d),
  *          dfl * (2/(2N+1))^2 / max_nodes (mu_eff sum_d |Ja^d|^2 / J^2)),
  * lambda_d = (|u . Ja^d| + c |Ja^d|) / J, mu_eff = max(4/3, gamma/Pr) mu / rho.
- * Synchronises the stream. */
+ * Synchronises the stream.  DG_ENONFINITE if a node's state gives a NaN or
+ * infinite speed (NaN/Inf in the state, non-positive density or pressure). */
 dg_status dg_max_dt(dg_ctx* ctx, const double* dU, double cfl, double dfl, double* host_dt, dg_stream stream);
 
 /* Built-in initial states at the LGL nodes: DG_IC_TGV (Sec. 4.2, Eq. 6) with

@@ -117,8 +117,11 @@ k_dt(const double* __restrict__ U, const double* __restrict__ metrics, double* _
       lv += a2n * iJ * iJ;
     }
     const double mu_eff = fmax(4.0 / 3.0, g.gamma / g.Pr) * g.mu * visc_factor<double>(g, p * ir * g.inv_R) * ir;
-    v[0] = fmax(v[0], lc);
-    v[1] = fmax(v[1], mu_eff * lv);
+    // fmax drops NaN operands: a non-finite node (or a negative pressure,
+    // whose sound speed is NaN) enters as +Inf so that the host sees it
+    const double vl = mu_eff * lv;
+    v[0] = fmax(v[0], isnan(lc) ? HUGE_VAL : lc);
+    v[1] = fmax(v[1], isnan(vl) ? HUGE_VAL : vl);
   }
   // max-reduce through the generic block reducer (sum slots reused as max)
   __shared__ double sh[2][kRedThreads / 32];

@@ -333,3 +333,25 @@ def test_inviscid_entropy_conservation_on_gpu(orc, dg, N):
     assert np.einsum("evp,evp,ep->", W, R2, J * wq) < -1e-6 * scale
     s.close()
     s2.close()
+
+
+def test_non_finite_state_is_reported(dg):
+    """A NaN planted (on the host) in one node of the state makes the FP64
+    reductions report DG_ENONFINITE instead of returning numbers; the context
+    stays usable for a clean state."""
+    mesh = box_mesh(2, 1, lo=0.0, hi=2 * math.pi)
+    prm = tgv_params()
+    s = dg.Solver(mesh, 3, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"])
+    U = s.initial_state("tgv", prm["p0"])
+    ok = s.integrals(U)
+    assert np.isfinite(ok).all()
+    bad = U.clone()
+    bad.view(-1)[bad.numel() // 3] = float("nan")
+    with pytest.raises(dg.DGError) as err:
+        s.integrals(bad)
+    assert err.value.status == dg.DG_ENONFINITE
+    with pytest.raises(dg.DGError) as err:
+        s.max_dt(bad)
+    assert err.value.status == dg.DG_ENONFINITE
+    np.testing.assert_array_equal(s.integrals(U), ok)
+    s.close()
