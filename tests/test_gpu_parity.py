@@ -355,3 +355,48 @@ def test_non_finite_state_is_reported(dg):
     assert err.value.status == dg.DG_ENONFINITE
     np.testing.assert_array_equal(s.integrals(U), ok)
     s.close()
+
+
+def test_bench_workload_properties(orc, dg):
+    """The headline workload's own mesh and launch configuration (16^3 curved
+    elements with seeded rotated frames, N=7, FP64): free-stream preservation
+    (R of a uniform flow vanishes) and discrete conservation of R for a random
+    state, properties that hold at any size; and after ten LSERK4-5 steps of
+    the manufactured solution the state is finite and the density stays within
+    the wave's bounds 2 -+ 0.1 (to 0.01)."""
+    N, K = 7, 16
+    mesh = box_mesh(K, N, deform="sinprod", rotate_seed=20260528)
+    s = dg.Solver(mesh, N, mu=1e-3)
+    U = np.zeros(s.shape)
+    r, u, p = 1.2, np.array([0.3, -0.2, 0.45]), 0.9
+    U[:, 0] = r
+    U[:, 1:4] = (r * u)[None, :, None, None, None]
+    U[:, 4] = p / 0.4 + 0.5 * r * u @ u
+    R = s.time_derivative(_cuda(U)).cpu().numpy()
+    # relative to the flux-differencing terms that cancel (the bar of the
+    # manufactured-solution parity test; they grow as 1/h with the mesh)
+    Ja, J = (a.cpu().numpy() for a in s.geometry())
+    _, _, D = orc.basis(N)
+    un = np.einsum("l,edlp->edp", u, Ja)
+    fmax = max(np.abs(r * un).max(), np.abs(r * u[0] * un + p * Ja[:, :, 0]).max(),
+               np.abs(r * u[1] * un + p * Ja[:, :, 1]).max(), np.abs(r * u[2] * un + p * Ja[:, :, 2]).max(),
+               np.abs((U[0, 4, 0, 0, 0] + p) * un).max())
+    term = 3 * fmax * 2 * np.abs(D).sum(1).max() / J.min()
+    assert np.abs(R).max() < RTOL_R * term, (np.abs(R).max(), term)
+    Ur = random_state(mesh.n_elems, N, seed=77)
+    R = s.time_derivative(_cuda(Ur)).reshape(s.E, 5, -1)
+    _, J = s.geometry()
+    _, w, _ = orc.basis(N)
+    wq = torch.from_numpy(np.einsum("k,j,i->kji", w, w, w).reshape(-1)).cuda()
+    tot = torch.einsum("evp,ep->v", R, J * wq)
+    scale = torch.einsum("evp,ep->v", R.abs(), J * wq)
+    assert bool((tot.abs() <= 1e-12 * scale).all()), (tot, scale)
+    s.close()
+    prm = mms_params()
+    sm = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=dg.SOURCE_MMS)
+    Um = sm.initial_state("mms", 0.0)
+    G = torch.empty_like(Um)
+    sm.rk_step(Um, G, 0.0, 1e-3, 10)
+    rho = Um[:, 0]
+    assert bool(torch.isfinite(Um).all()) and float(rho.min()) > 1.89 and float(rho.max()) < 2.11
+    sm.close()
