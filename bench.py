@@ -262,7 +262,8 @@ def run_ensemble(args, local):
     import torch
     import paper_2605_28627_gb300 as dg
     from workloads import box_mesh, ensemble_members, tgv_params
-    specs = ensemble_members(64, 20260529)
+    k_lo, k_hi = (int(v) for v in args.ens_K.split(","))
+    specs = ensemble_members(64, 20260529, k_lo, k_hi)
     nsteps = args.ens_steps
     dev = "cuda:%d" % local
     st = torch.cuda.Stream(device=dev)
@@ -280,8 +281,10 @@ def run_ensemble(args, local):
     total = sum(dofs)
     runs = [member(sp, dg.FP32OP) for sp in specs]
     cache_dir = os.path.join(ROOT, "paper_2605_28627_gb300", "_build")
+    # the tuned plan depends on the member sizes: one cache file per size range
+    cache = "ensemble_tune.txt" if (k_lo, k_hi) == (8, 24) else "ensemble_tune_K%d-%d.txt" % (k_lo, k_hi)
     ens = dg.Ensemble([r[0] for r in runs],
-                      tune_cache_path=os.path.join(cache_dir, "ensemble_tune.txt") if os.path.isdir(cache_dir) else None)
+                      tune_cache_path=os.path.join(cache_dir, cache) if os.path.isdir(cache_dir) else None)
     Us = [r[1] for r in runs]
     Gs = [torch.empty_like(U) for U in Us]
     dts = [r[2] for r in runs]
@@ -329,8 +332,8 @@ def run_ensemble(args, local):
     ms_seq32, ek32 = sequential(dg.FP32OP)
     ek_err = [abs(a - b) / abs(b) for a, b in zip(ek_ens, ek64)]
     rate = total * 5 * nsteps / (ms_ens * 1e-3)
-    line = {"experiment": "ensemble of 64 uneven Taylor-Green runs (seed 20260529), FP32 operator / FP64 state, "
-                          "%d LSERK4-5 steps in one graph launch" % nsteps,
+    line = {"experiment": "ensemble of 64 uneven Taylor-Green runs (seed 20260529, K^3 elements, K in %d..%d), "
+                          "FP32 operator / FP64 state, %d LSERK4-5 steps in one graph launch" % (k_lo, k_hi, nsteps),
             "members": 64, "total_dof": total, "value": rate, "unit": UNIT, "pid_ns": 1e9 / rate,
             "ms_per_step": ms_ens / nsteps,
             "sequential_fp64_ms_per_step": ms_seq64 / nsteps, "sequential_fp32op_ms_per_step": ms_seq32 / nsteps,
@@ -543,6 +546,7 @@ def main():
     ap.add_argument("--tgv-steps", type=int, default=200)
     ap.add_argument("--ensemble", action="store_true", help="run the 64-member batched ensemble study")
     ap.add_argument("--ens-steps", type=int, default=10)
+    ap.add_argument("--ens-K", default="8,24", help="range of elements per direction of the ensemble members")
     ap.add_argument("--adjoint", action="store_true", help="run the 16^3, N=5 discrete-adjoint study")
     ap.add_argument("--pid", action="store_true", help="run the free-stream PID study (N=3 at 64^3, N=9 at 20^3)")
     ap.add_argument("--pid-steps", type=int, default=10)

@@ -41,13 +41,13 @@ def mms_params(gamma: float = 1.4, Pr: float = 0.72, mu: float = 0.001):
     return dict(gamma=gamma, R=1.0, Pr=Pr, mu=mu, amp=0.1)
 
 
-def ensemble_members(count: int = 64, seed: int = 20260529):
-    """Uneven Taylor-Green runs: K ~ U{8..24} (K^3 elements), N ~ U{3..7},
-    Ma ~ U[0.1, 0.5], Re ~ U[400, 1600]."""
+def ensemble_members(count: int = 64, seed: int = 20260529, k_lo: int = 8, k_hi: int = 24):
+    """Uneven Taylor-Green runs: K ~ U{k_lo..k_hi} (K^3 elements; 8..24 by
+    default), N ~ U{3..7}, Ma ~ U[0.1, 0.5], Re ~ U[400, 1600]."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(count):
-        K = int(rng.integers(8, 25))
+        K = int(rng.integers(k_lo, k_hi + 1))
         N = int(rng.integers(3, 8))
         Ma = float(rng.uniform(0.1, 0.5))
         Re = float(rng.uniform(400.0, 1600.0))
