@@ -33,6 +33,10 @@ struct AdjBufs {
 };
 
 // ---------------------------------------------------------------------------
+// Words per node of the volume adjoint's element tile: primitives, 1/p and
+// |u|^2 (8), metric terms (9), lamV (5), the partner's adjoint (5).
+constexpr int kAdjVolWords = 27;
+
 // A1: volume adjoint.  lamV = -lambda / J.  Two blocks per SM where a block
 // has at most 256 threads (one alone leaves the SM seven or eight warps).
 template <int N>
@@ -46,19 +50,25 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
   constexpr bool HALF = (n % 2) == 0;     // the shift n/2, half as many pairs
   extern __shared__ double adj_smem[];
   double* sD = adj_smem;                                   // [n*n]
-  double* base = adj_smem + ((n * n + 1) & ~1);
+  double* sD2 = sD + n * n;                                // [n*n] 2 D (exact)
+  double* base = adj_smem + ((2 * n * n + 1) & ~1);
   __shared__ double smu[S::THREADS];
   const int le = threadIdx.x / P, id = threadIdx.x - le * P;
-  double* eb = base + (size_t)le * 25 * P;
-  auto sPr = [&](int c, int node) -> double& { return eb[c * P + node]; };          // rho, u, v, w, p, beta
-  auto sJa = [&](int c, int node) -> double& { return eb[(6 + c) * P + node]; };    // [9]
-  auto sL = [&](int c, int node) -> double& { return eb[(15 + c) * P + node]; };    // lamV [5]
-  auto sX = [&](int c, int node) -> double& { return eb[(20 + c) * P + node]; };    // partner's adjoint [5]
+  double* eb = base + (size_t)le * kAdjVolWords * P;
+  // rho, u, v, w, p, beta, 1/p, |u|^2
+  auto sPr = [&](int c, int node) -> double& { return eb[c * P + node]; };
+  auto sJa = [&](int c, int node) -> double& { return eb[(8 + c) * P + node]; };    // [9]
+  auto sL = [&](int c, int node) -> double& { return eb[(17 + c) * P + node]; };    // lamV [5]
+  auto sX = [&](int c, int node) -> double& { return eb[(22 + c) * P + node]; };    // partner's adjoint [5]
   const int e = blockIdx.x * EPB + le;
   const bool active = e < E;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = Dg[t];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    sD[t] = Dg[t];
+    sD2[t] = 2.0 * Dg[t];
+  }
   double q[5] = {1, 0, 0, 0, 1}, Ja[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, iJ = 0.0, lv[5] = {0, 0, 0, 0, 0};
   NodePrim<double> me{1, 0, 0, 0, 1, 0.5};
+  double ip_me = 1.0, k_me = 0.0;
   if (active) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) q[c] = U[((size_t)e * 5 + c) * P + id];
@@ -74,6 +84,9 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
     me.beta = 0.5 * q[0] / me.p;
     sPr(0, id) = me.rho; sPr(1, id) = me.u; sPr(2, id) = me.v; sPr(3, id) = me.w;
     sPr(4, id) = me.p; sPr(5, id) = me.beta;
+    ip_me = adj_rcp(me.p);
+    k_me = me.u * me.u + me.v * me.v + me.w * me.w;
+    sPr(6, id) = ip_me; sPr(7, id) = k_me;
   }
   __syncthreads();
   const int i = id % n, j = (id / n) % n, k = id / NN;
@@ -94,11 +107,11 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
         const double nx = 0.5 * (Ja[d * 3] + sJa(d * 3, mid));
         const double ny = 0.5 * (Ja[d * 3 + 1] + sJa(d * 3 + 1, mid));
         const double nz = 0.5 * (Ja[d * 3 + 2] + sJa(d * 3 + 2, mid));
-        const double Drm = sD[r * n + m], Dmr = sD[m * n + r];
+        const double Drm2 = sD2[r * n + m], Dmr2 = sD2[m * n + r];
         double wb[5];
 #pragma unroll
-        for (int c = 0; c < 5; ++c) wb[c] = 2.0 * (Drm * lv[c] + Dmr * sL(c, mid));
-        ec_flux_vjp(me, ot, nx, ny, nz, g.inv_gm1, wb, pr, pm);
+        for (int c = 0; c < 5; ++c) wb[c] = fma(Drm2, lv[c], Dmr2 * sL(c, mid));
+        ec_flux_vjp(me, ot, nx, ny, nz, g.inv_gm1, wb, pr, pm, ip_me, sPr(6, mid), k_me, sPr(7, mid));
 #pragma unroll
         for (int c = 0; c < 5; ++c) sX(c, mid) = pm[c];
       }
@@ -121,20 +134,21 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
         const int ra = hi % H, rb = ra + H;
         const int ia = w2 - hi * stride + stride * (ra + n * (hi / H));   // node with r < n/2
         const int ib = ia + H * stride;                                     // its partner
-        double* e2 = base + (size_t)le2 * 25 * P;
+        double* e2 = base + (size_t)le2 * kAdjVolWords * P;
         NodePrim<double> A{e2[ia], e2[P + ia], e2[2 * P + ia], e2[3 * P + ia], e2[4 * P + ia], e2[5 * P + ia]};
         NodePrim<double> B{e2[ib], e2[P + ib], e2[2 * P + ib], e2[3 * P + ib], e2[4 * P + ib], e2[5 * P + ib]};
-        const double* ja = e2 + (6 + d * 3) * P;
+        const double* ja = e2 + (8 + d * 3) * P;
         const double nx = 0.5 * (ja[ia] + ja[ib]);
         const double ny = 0.5 * (ja[P + ia] + ja[P + ib]);
         const double nz = 0.5 * (ja[2 * P + ia] + ja[2 * P + ib]);
-        const double Drm = sD[ra * n + rb], Dmr = sD[rb * n + ra];
-        const double* l2 = e2 + 15 * P;
+        const double Drm2 = sD2[ra * n + rb], Dmr2 = sD2[rb * n + ra];
+        const double* l2 = e2 + 17 * P;
         double wb[5], pa[5] = {0, 0, 0, 0, 0}, pb[5] = {0, 0, 0, 0, 0};
 #pragma unroll
-        for (int c = 0; c < 5; ++c) wb[c] = 2.0 * (Drm * l2[c * P + ia] + Dmr * l2[c * P + ib]);
-        ec_flux_vjp(A, B, nx, ny, nz, g.inv_gm1, wb, pa, pb);
-        double* x2 = e2 + 20 * P;
+        for (int c = 0; c < 5; ++c) wb[c] = fma(Drm2, l2[c * P + ia], Dmr2 * l2[c * P + ib]);
+        ec_flux_vjp(A, B, nx, ny, nz, g.inv_gm1, wb, pa, pb, e2[6 * P + ia], e2[6 * P + ib], e2[7 * P + ia],
+                    e2[7 * P + ib]);
+        double* x2 = e2 + 22 * P;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           x2[c * P + ia] = pa[c];
@@ -455,7 +469,7 @@ __global__ void k_axpby(double* y, const double* x, double a, double b, size_t l
 template <int N>
 static size_t adj_volume_smem() {
   using S = Shape<N>;
-  return sizeof(double) * (((S::n * S::n + 1) & ~1) + (size_t)S::EPB * 25 * S::P);
+  return sizeof(double) * (((2 * S::n * S::n + 1) & ~1) + (size_t)S::EPB * kAdjVolWords * S::P);
 }
 
 template <int N>

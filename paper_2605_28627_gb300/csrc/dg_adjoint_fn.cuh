@@ -66,9 +66,11 @@ __device__ __forceinline__ double log_mean_d(double a, double b, double& La, dou
 
 // Adjoint of the Chandrashekar two-point flux f(a, b; n) (ec_flux): given
 // fb = df-bar (5), adds to the primitive adjoints (rho, u, v, w, p) of a and b.
+// ipA, ipB are 1/p and kA, kB are |u|^2 of the two states (per node, so the
+// volume kernel computes them once per node, not once per pair).
 __device__ __forceinline__ void ec_flux_vjp(const NodePrim<double>& A, const NodePrim<double>& B, double nx,
                                             double ny, double nz, double inv_gm1, const double fb[5], double pa[5],
-                                            double pbv[5]) {
+                                            double pbv[5], double ipA, double ipB, double kA, double kB) {
   double Lra, Lrb, Lba, Lbb;
   const double rho_ln = log_mean_d(A.rho, B.rho, Lra, Lrb);
   const double beta_ln = log_mean_d(A.beta, B.beta, Lba, Lbb);
@@ -76,7 +78,7 @@ __device__ __forceinline__ void ec_flux_vjp(const NodePrim<double>& A, const Nod
   const double sr = A.rho + B.rho, sb = A.beta + B.beta;
   const double isb = adj_rcp(sb), ibl = adj_rcp(beta_ln);
   const double p_hat = 0.5 * sr * isb;
-  const double K = 0.25 * (A.u * A.u + A.v * A.v + A.w * A.w + B.u * B.u + B.v * B.v + B.w * B.w);
+  const double K = 0.25 * (kA + kB);
   const double un = ua * nx + va * ny + wa * nz;
   const double f0 = rho_ln * un;
   const double fm0 = f0 * ua + p_hat * nx, fm1 = f0 * va + p_hat * ny, fm2 = f0 * wa + p_hat * nz;
@@ -104,11 +106,17 @@ __device__ __forceinline__ void ec_flux_vjp(const NodePrim<double>& A, const Nod
   double rab = srb + rlb * Lra, rbb = srb + rlb * Lrb;
   const double bab = sbb + blb * Lba, bbb = sbb + blb * Lbb;
   // beta = rho / (2 p)
-  const double iAp = adj_rcp(A.p), iBp = adj_rcp(B.p);
-  rab += bab * 0.5 * iAp;  pa[4] += -bab * A.beta * iAp;
-  rbb += bbb * 0.5 * iBp;  pbv[4] += -bbb * B.beta * iBp;
+  rab += bab * 0.5 * ipA;  pa[4] += -bab * A.beta * ipA;
+  rbb += bbb * 0.5 * ipB;  pbv[4] += -bbb * B.beta * ipB;
   pa[0] += rab;
   pbv[0] += rbb;
+}
+
+__device__ __forceinline__ void ec_flux_vjp(const NodePrim<double>& A, const NodePrim<double>& B, double nx,
+                                            double ny, double nz, double inv_gm1, const double fb[5], double pa[5],
+                                            double pbv[5]) {
+  ec_flux_vjp(A, B, nx, ny, nz, inv_gm1, fb, pa, pbv, adj_rcp(A.p), adj_rcp(B.p), A.u * A.u + A.v * A.v + A.w * A.w,
+              B.u * B.u + B.v * B.v + B.w * B.w);
 }
 
 // Adjoint of the Euler flux f(q) . n (q conserved, n any vector): adds to qb.
