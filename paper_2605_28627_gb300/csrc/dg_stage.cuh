@@ -626,7 +626,7 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
       acc[3] = fma(d1, xs[3 * P + id], acc[3]);
       acc[4] = fma(d2, xs[4 * P + id], acc[4]);
     };
-#pragma unroll 1
+#pragma unroll (sizeof(R) == 4 && FULL > 0 ? FULL : 1)
     for (int s = 1; s <= FULL; ++s) {
       const int m = r + s < n ? r + s : r + s - n;
       const int mid = line0 + m * stride;
@@ -707,7 +707,7 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
       // every round wrote its own buffer: one barrier, then the partners' shares
       dsync(d);
       if (active) {
-#pragma unroll 1
+#pragma unroll (sizeof(R) == 4 && FULL > 0 ? FULL : 1)
         for (int s = 1; s <= FULL; ++s) take_share(sX + (s - 1) * 5 * P, r - s >= 0 ? r - s : r - s + n);
         if constexpr (HALF) take_share(sX + FULL * 5 * P, r >= n / 2 ? r - n / 2 : r + n / 2);
       }
