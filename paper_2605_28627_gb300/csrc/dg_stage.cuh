@@ -51,16 +51,21 @@ struct VShape : Shape<N, EPB_> {
 };
 
 // Blocks per SM the single-context volume kernel's register and shared-memory
-// budget must allow.  FP32 tiles of up to 512 threads: enough for 32 warps per
-// SM, at least two (the FP32 operator is latency-bound; +8 to +16 % at
-// N = 2, 4, 5 over two blocks).  FP64 at N = 6, 7: two -- a hundred-odd bytes of spilled
+// budget must allow.  FP32 (latency-bound): enough for about 32 warps per SM at
+// N <= 5 (+8 to +16 % at N = 2, 4, 5 over two blocks; 48 warps lost 6 to 23 %
+// there), 33 to 48 at N = 6..8, where a hundred-odd bytes of spilled registers
+// per thread pay.  FP64 at N = 6, 7: two -- a hundred-odd bytes of spilled
 // registers cost less than an SM with only 11 or 16 warps to feed its FP64
 // pipe from (+2.4 % at N = 6, +0.5 % at N = 7; at N = 4, 5 a third block did
 // not pay).
 template <int N, typename R>
 constexpr int vol_min_blocks() {
   constexpr int threads = Shape<N>::THREADS;
-  if (sizeof(R) == 4) return threads <= 512 ? (1024 / threads > 2 ? 1024 / threads : 2) : 1;
+  if (sizeof(R) == 4) {
+    if (N == 6 || N == 7) return 3;                 // 33 and 48 warps: +11 %, +1 %
+    if (N == 8) return 2;                           // 46 warps: +10 %
+    return threads <= 512 ? (1024 / threads > 2 ? 1024 / threads : 2) : 1;
+  }
   return (N == 6 || N == 7) ? 2 : 1;
 }
 
