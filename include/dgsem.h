@@ -207,11 +207,15 @@ dg_status dg_set_viscosity(dg_ctx* ctx, double mu);
  * An ensemble groups existing contexts on one device (each with its own mesh,
  * N, gas constants; all with the same precision).  Members of equal N are
  * advanced by persistent kernels that walk a tile table over all of those
- * members; the nsteps step sequence of all members is one CUDA graph.  Tile
- * shape (elements per block) and grid sizes per N are chosen by an autotuner
- * on the first dg_ensemble_step (timing the candidates on the members' data
- * without changing their states) and cached in the text file
- * tune_cache_path (NULL: no cache), keyed by GPU name, N and precision. */
+ * members; the nsteps step sequence of all members is one CUDA graph, in
+ * which the independent units (a tile-table group, or one member run by the
+ * single-context kernels where those won the tuning) are parallel branches.
+ * Tile shape (elements per block), grid sizes and the per-member alternative
+ * are chosen per N by an autotuner on the first dg_ensemble_step (timing the
+ * candidates on the members' data without changing their states) and cached
+ * in the text file tune_cache_path (NULL: no cache), keyed by GPU name, N and
+ * precision -- not by member sizes: ensembles of very different sizes should
+ * use different cache files. */
 typedef struct dg_ensemble dg_ensemble;
 
 /* The members stay owned by the caller and must outlive the ensemble.
