@@ -93,15 +93,29 @@ constexpr size_t volume_smem_bytes() {
                       (sizeof(R) == 4 ? EPB * (N + 1) * (N + 1) * (N + 1) : 0));
 }
 
-// rcp for the operator type: FP64 by hardware approximation + one cubic
-// Newton-Raphson step (below 1 ulp); FP32 by the approximation alone (1 ulp).
-__device__ __forceinline__ double rcp_lf(double x) {
+// 1/x: hardware reciprocal approximation refined by one cubic Newton-Raphson
+// step y <- y (1 + e + e^2), e = 1 - x y, which cubes the relative error
+// (2^-20 -> below 1 ulp).  In FP32 the approximation alone is within 1 ulp.
+__device__ __forceinline__ double rcp_op(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
   const double e = fma(-x, y, 1.0);
-  return fma(y, fma(e, e, e), y);
+  const double t = fma(e, e, e);
+  return fma(y, t, y);
 }
-__device__ __forceinline__ float rcp_lf(float x) {
+// 1/x with one quadratic Newton-Raphson step y <- y + y e (relative error
+// ~2^-40), for reciprocals whose error is damped by the use
+__device__ __forceinline__ double rcp_op_q(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return fma(y, fma(-x, y, 1.0), y);
+}
+__device__ __forceinline__ float rcp_op_q(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_op(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
@@ -163,7 +177,7 @@ __device__ __forceinline__ void lift_body(const double* __restrict__ U, const R*
   const R gm1 = gsel<R>(g.gm1, g.f_gm1), inv_R = gsel<R>(g.inv_R, g.f_inv_R), inv_w0 = to_op<R>(inv_w0d);
   if (active) {
     const double* q = U + (size_t)e * 5 * P + id;
-    const R rho = to_op<R>(q[0]), ir = rcp_lf(rho);
+    const R rho = to_op<R>(q[0]), ir = rcp_op(rho);
     const R m0 = to_op<R>(q[P]), m1 = to_op<R>(q[2 * P]), m2 = to_op<R>(q[3 * P]);
     const R u = m0 * ir, v = m1 * ir, w = m2 * ir;
     const R p = gm1 * (to_op<R>(q[4 * P]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
@@ -181,7 +195,7 @@ __device__ __forceinline__ void lift_body(const double* __restrict__ U, const R*
     if (t < EPB * NF && blk * EPB + le2 < E) {
       const int f = r2 / NN, pq = r2 - f * NN;
       const int node = face_node<n>(f, pq % n, pq / n);
-      const R rho = to_op<R>(qn[0]), ir = rcp_lf(rho);
+      const R rho = to_op<R>(qn[0]), ir = rcp_op(rho);
       const R m0 = to_op<R>(qn[1]), m1 = to_op<R>(qn[2]), m2 = to_op<R>(qn[3]);
       const R u = m0 * ir, v = m1 * ir, w = m2 * ir;
       const R pr = gm1 * (to_op<R>(qn[4]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
@@ -253,7 +267,7 @@ __device__ __forceinline__ void face_flux_core(const double dL[5], const double 
     qR[v] = to_op<R>(dR[v]);
   }
   const R gm1 = gsel<R>(g.gm1, g.f_gm1), gam = gsel<R>(g.gamma, g.f_gamma);
-  const R irL = rcp_lf(qL[0]), irR = rcp_lf(qR[0]);
+  const R irL = rcp_op(qL[0]), irR = rcp_op(qR[0]);
   const R uL = qL[1] * irL, vL = qL[2] * irL, wL = qL[3] * irL;
   const R uR = qR[1] * irR, vR = qR[2] * irR, wR = qR[3] * irR;
   const R pL = gm1 * (qL[4] - R(0.5) * (qL[1] * uL + qL[2] * vL + qL[3] * wL));
@@ -341,34 +355,6 @@ __device__ __forceinline__ void face_body(const double* __restrict__ U, const R*
   }
   const R* fg = facegeo + (size_t)f * 4 * NN + pq;
   face_flux_core<R>(dL, dR, gL, gR, fg[0], fg[NN], fg[2 * NN], fg[3 * NN], g, fstar + (size_t)f * 5 * NN + pq, NN);
-}
-
-// 1/x: hardware reciprocal approximation refined by one cubic Newton-Raphson
-// step y <- y (1 + e + e^2), e = 1 - x y, which cubes the relative error
-// (2^-20 -> below 1 ulp).  In FP32 the approximation alone is within 1 ulp.
-__device__ __forceinline__ double rcp_op(double x) {
-  double y;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  const double e = fma(-x, y, 1.0);
-  const double t = fma(e, e, e);
-  return fma(y, t, y);
-}
-// 1/x with one quadratic Newton-Raphson step y <- y + y e (relative error
-// ~2^-40), for reciprocals whose error is damped by the use
-__device__ __forceinline__ double rcp_op_q(double x) {
-  double y;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  return fma(y, fma(-x, y, 1.0), y);
-}
-__device__ __forceinline__ float rcp_op_q(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float rcp_op(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
 }
 
 // Switch of the logarithmic mean between the series and the logarithm.  In
