@@ -234,6 +234,63 @@ def test_mms_source_matches_symbolic_residual(orc):
         np.testing.assert_allclose(S[:, v].reshape(o.E, -1), ref, rtol=1e-12, atol=1e-12)
 
 
+def test_viscous_terms_match_symbolic_navier_stokes(orc):
+    """With constant mu the viscous part of R is linear in mu, so
+    (R_mu(U) - R_0(U)) / mu is the discrete div F_v of Sec. 3.1 (BR1 lifting,
+    viscous volume and surface terms). For a smooth compressible state it must
+    approach the symbolic div F_v, with F_v = (0, tau, u.tau + lambda grad T) and
+    tau = grad u + grad u^T - 2/3 (div u) I, and stay far from the usual slips:
+    the transposed gradient dropped, or the bulk term with the wrong sign or left
+    out (the Taylor-Green dissipation cannot tell these apart: there div u = 0)."""
+    sp = pytest.importorskip("sympy")
+    g, Rg, Pr, mu = 1.4, 1.0, 0.72, 0.5
+    x, y, z = sp.symbols("x y z")
+    X = [x, y, z]
+    rho = 1 + 0.2 * sp.sin(x) * sp.cos(z) + 0.1 * sp.cos(y)
+    u = [0.3 * sp.sin(y) + 0.2 * sp.sin(x) * sp.cos(z),
+         0.25 * sp.sin(z) + 0.15 * sp.cos(x) * sp.sin(y),
+         0.2 * sp.sin(x + y) + 0.1 * sp.cos(z)]
+    p = 1 + 0.1 * sp.cos(y) * sp.sin(z) + 0.05 * sp.sin(x)
+    T = p / (rho * Rg)
+    lam = g * Rg / (g - 1) / Pr          # lambda / mu = c_p / Pr
+    div = sum(sp.diff(u[j], X[j]) for j in range(3))
+
+    def div_fv(transpose=1, bulk=sp.Rational(2, 3)):
+        tau = [[sp.diff(u[i], X[j]) + transpose * sp.diff(u[j], X[i]) - (bulk * div if i == j else 0)
+                for j in range(3)] for i in range(3)]
+        out = [sp.Integer(0)] + [sum(sp.diff(tau[i][j], X[j]) for j in range(3)) for i in range(3)]
+        out.append(sum(sp.diff(sum(u[i] * tau[i][j] for i in range(3)) + lam * sp.diff(T, X[j]), X[j])
+                       for j in range(3)))
+        return [sp.lambdify((x, y, z), f, "numpy") for f in out]
+
+    cons = [rho, rho * u[0], rho * u[1], rho * u[2], p / (g - 1) + rho * sum(ui ** 2 for ui in u) / 2]
+    cons = [sp.lambdify((x, y, z), f, "numpy") for f in cons]
+    exact = div_fv()
+    slips = [div_fv(transpose=0), div_fv(bulk=-sp.Rational(2, 3)), div_fv(bulk=0)]
+
+    def at_nodes(f, Xn):
+        return f(Xn[:, 0], Xn[:, 1], Xn[:, 2]) * np.ones_like(Xn[:, 0])
+
+    errs = {}
+    for N in (5, 7):
+        m = box_mesh(4, N, lo=0.0, hi=2 * np.pi, deform="sinprod", rotate_seed=17)
+        o1 = orc.Oracle(m, N, gamma=g, R=Rg, Pr=Pr, mu=mu)
+        o0 = orc.Oracle(m, N, gamma=g, R=Rg, Pr=Pr, mu=0.0)
+        Xn = o1.node_coords()
+        U = np.stack([at_nodes(f, Xn) for f in cons], 1).reshape(o1.shape)
+        V = ((o1.time_derivative(U) - o0.time_derivative(U)) / mu).reshape(o1.E, 5, -1)
+        assert np.abs(V[:, 0]).max() < 1e-12           # no viscous mass flux
+        scale = [np.abs(at_nodes(exact[v], Xn)).max() for v in range(5)]
+        errs[N] = [np.abs(V[:, v] - at_nodes(exact[v], Xn)).max() / scale[v] for v in range(1, 5)]
+        if N == 7:
+            assert max(errs[N]) < 0.02, errs[N]
+            for s in slips:
+                es = [np.abs(V[:, v] - at_nodes(s[v], Xn)).max() / scale[v] for v in range(1, 4)]
+                assert min(es) > 0.15, es
+    # the remaining difference is discretisation error: it falls with N
+    assert all(e7 < e5 / 5 for e5, e7 in zip(errs[5], errs[7])), errs
+
+
 def test_taylor_green_closed_forms(orc):
     """E_k(0) = 1/8 up to O(Ma^2) density variation, and in the
     incompressible limit dE_k/dt(0) = -2 nu |k|^2 E_k = -3 nu / 4."""
