@@ -291,6 +291,93 @@ def test_viscous_terms_match_symbolic_navier_stokes(orc):
     assert all(e7 < e5 / 5 for e5, e7 in zip(errs[5], errs[7])), errs
 
 
+@pytest.mark.parametrize("surf_flux", [0, 1])
+def test_inviscid_operator_matches_symbolic_euler(orc, surf_flux):
+    """For a smooth state with every primitive varying in all three
+    directions, R with mu = 0 approaches -div F_c(q) of the Euler equations
+    (Sec. 3.1, Eq. 1: mass, momentum with its pressure, energy (rho E + p) u),
+    written out and differentiated symbolically here, spectrally in N on a
+    curved rotated mesh."""
+    sp = pytest.importorskip("sympy")
+    g = 1.4
+    x, y, z = sp.symbols("x y z")
+    X = [x, y, z]
+    rho = 1 + 0.2 * sp.sin(x) * sp.cos(z) + 0.1 * sp.cos(y)
+    u = [0.3 * sp.sin(y) + 0.2 * sp.sin(x) * sp.cos(z),
+         0.25 * sp.sin(z) + 0.15 * sp.cos(x) * sp.sin(y),
+         0.2 * sp.sin(x + y) + 0.1 * sp.cos(z)]
+    p = 1 + 0.1 * sp.cos(y) * sp.sin(z) + 0.05 * sp.sin(x)
+    E = p / (g - 1) + rho * sum(ui ** 2 for ui in u) / 2
+    cons = [rho, rho * u[0], rho * u[1], rho * u[2], E]
+
+    def flux(v, j):
+        if v == 0:
+            return rho * u[j]
+        if v < 4:
+            return rho * u[v - 1] * u[j] + (p if v - 1 == j else 0)
+        return (E + p) * u[j]
+
+    exact = [sp.lambdify((x, y, z), -sum(sp.diff(flux(v, j), X[j]) for j in range(3)), "numpy") for v in range(5)]
+    cons = [sp.lambdify((x, y, z), f, "numpy") for f in cons]
+    errs = {}
+    for N in (5, 7):
+        m = box_mesh(4, N, lo=0.0, hi=2 * np.pi, deform="sinprod", rotate_seed=17)
+        o = orc.Oracle(m, N, gamma=g, mu=0.0, surf_flux=surf_flux)
+        Xn = o.node_coords()
+        U = np.stack([f(Xn[:, 0], Xn[:, 1], Xn[:, 2]) * np.ones_like(Xn[:, 0]) for f in cons], 1).reshape(o.shape)
+        R = o.time_derivative(U).reshape(o.E, 5, -1)
+        errs[N] = []
+        for v in range(5):
+            r = exact[v](Xn[:, 0], Xn[:, 1], Xn[:, 2]) * np.ones_like(Xn[:, 0])
+            errs[N].append(np.abs(R[:, v] - r).max() / np.abs(r).max())
+    assert max(errs[7]) < 2e-3, errs[7]
+    assert all(e7 < e5 / 5 for e5, e7 in zip(errs[5], errs[7])), errs
+
+
+def test_integrals_match_closed_forms(orc):
+    """The diagnostics of Sec. 4.2 for a smooth periodic state on a curved
+    rotated mesh: the five conservation totals, E_k = 1/(2|Omega|) int rho |u|^2,
+    eps = mu/|Omega| int |omega|^2 and min p.  The references integrate the same
+    trigonometric polynomials with the uniform trapezoidal rule on 32^3 points,
+    which is exact for them, so they share nothing with the LGL quadrature,
+    the Jacobian or the lifted vorticity of the oracle."""
+    sp = pytest.importorskip("sympy")
+    g, mu, N = 1.4, 0.01, 7
+    x, y, z = sp.symbols("x y z")
+    rho = 1 + 0.2 * sp.sin(x) * sp.cos(z) + 0.1 * sp.cos(y)
+    u = [0.3 * sp.sin(y) + 0.2 * sp.sin(x) * sp.cos(z),
+         0.25 * sp.sin(z) + 0.15 * sp.cos(x) * sp.sin(y),
+         0.2 * sp.sin(x + y) + 0.1 * sp.cos(z)]
+    p = 1 + 0.1 * sp.cos(y) * sp.sin(z) + 0.05 * sp.sin(x)
+    cons = [rho, rho * u[0], rho * u[1], rho * u[2], p / (g - 1) + rho * sum(ui ** 2 for ui in u) / 2]
+    omega = [sp.diff(u[2], y) - sp.diff(u[1], z), sp.diff(u[0], z) - sp.diff(u[2], x),
+             sp.diff(u[1], x) - sp.diff(u[0], y)]
+    integrands = cons + [rho * sum(ui ** 2 for ui in u), sum(w ** 2 for w in omega)]
+    M = 32
+    t1 = 2 * np.pi * np.arange(M) / M
+    gx, gy, gz = np.meshgrid(t1, t1, t1, indexing="ij")
+    vol = (2 * np.pi) ** 3
+
+    def trapezoid(f):
+        vals = sp.lambdify((x, y, z), f, "numpy")(gx, gy, gz) * np.ones_like(gx)
+        return vals.mean() * vol, np.abs(vals).mean() * vol
+
+    tr = [trapezoid(f) for f in integrands]
+    ref = [tr[v][0] for v in range(5)] + [tr[5][0] / (2 * vol), mu * tr[6][0] / vol]
+    scale = [tr[v][1] for v in range(5)] + [ref[5], ref[6]]
+
+    m = box_mesh(4, N, lo=0.0, hi=2 * np.pi, deform="sinprod", rotate_seed=17)
+    o = orc.Oracle(m, N, gamma=g, mu=mu)
+    Xn = o.node_coords()
+    U = np.stack([sp.lambdify((x, y, z), f, "numpy")(Xn[:, 0], Xn[:, 1], Xn[:, 2]) * np.ones_like(Xn[:, 0])
+                  for f in cons], 1).reshape(o.shape)
+    I = o.integrals(U)
+    for v in range(7):
+        assert abs(I[v] - ref[v]) < 1e-7 * scale[v], (v, I[v], ref[v])
+    p_nodes = sp.lambdify((x, y, z), p, "numpy")(Xn[:, 0], Xn[:, 1], Xn[:, 2])
+    assert abs(I[7] - p_nodes.min()) < 1e-14
+
+
 def test_taylor_green_closed_forms(orc):
     """E_k(0) = 1/8 up to O(Ma^2) density variation, and in the
     incompressible limit dE_k/dt(0) = -2 nu |k|^2 E_k = -3 nu / 4."""
