@@ -187,13 +187,25 @@ dg_status dg_adjoint_step(dg_ctx* ctx, const double* dU_n, const double* dlam_np
                           double t, double dt, dg_stream stream);
 
 /* Adjoint of nsteps steps (the context's scheme) from dU0 at t0: dlam0 = (dU_T/dU_0)^T dlamT
- * (may alias), dJdmu += lambda . dU_T/dmu, with binomial checkpointing: at
- * most max_snapshots stored states (>= 1), forward recomputation in between.
+ * (may alias), dJdmu += lambda . dU_T/dmu, with binomial checkpointing
+ * (Griewank 1992): at most max_snapshots stored states (>= 1, the initial
+ * state included; min(max_snapshots, nsteps) device buffers of one state
+ * each are allocated for the call), forward recomputation in between, the
+ * least number of recomputed forward steps for that many states.
  * host_counts2 (may be NULL) receives {recomputed forward steps, adjoint
  * steps}.  Synchronises the stream. */
 dg_status dg_adjoint_solve(dg_ctx* ctx, const double* dU0, const double* dlamT, double* dlam0, double* dJdmu,
                            double t0, double dt, int32_t nsteps, int32_t max_snapshots, int64_t* host_counts2,
                            dg_stream stream);
+
+/* The counts dg_adjoint_solve reports for (nsteps, max_snapshots), from its
+ * schedule run without a device: host_counts2 (host, 2 values) receives
+ * {recomputed forward steps, adjoint steps}.  With s = min(max_snapshots,
+ * nsteps) states the first is t(nsteps, s) = r nsteps - C(s + r, s + 1), r the
+ * least integer with C(s + r, s) >= nsteps (t = n (n - 1) / 2 for s = 1); the
+ * second is nsteps.  DG_EINVAL for nsteps < 0, max_snapshots < 1 or a NULL
+ * pointer.  Needs no GPU and no context. */
+dg_status dg_checkpoint_schedule(int32_t nsteps, int32_t max_snapshots, int64_t* host_counts2);
 
 /* Objective J = sum_nodes w_i w_j w_k J 1/2 rho |u|^2 (LGL quadrature of the
  * volume-integrated kinetic energy) into *host_J; dgrad (device, may be NULL)

@@ -34,8 +34,8 @@ EXPORTS = ["dg_init", "dg_destroy", "dg_state_len", "dg_time_derivative", "dg_rk
            "dg_integrals", "dg_max_dt", "dg_initial_state", "dg_node_coords", "dg_geometry", "dg_profile_stages",
            "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
            "dg_ensemble_step", "dg_ensemble_plan", "dg_ensemble_last_error", "dg_time_derivative_vjp",
-           "dg_adjoint_step", "dg_adjoint_solve", "dg_kinetic_energy", "dg_set_viscosity", "dg_check_conversions",
-           "dg_last_error"]
+           "dg_adjoint_step", "dg_adjoint_solve", "dg_checkpoint_schedule", "dg_kinetic_energy", "dg_set_viscosity",
+           "dg_check_conversions", "dg_last_error"]
 
 
 class DGError(RuntimeError):
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
     L.dg_time_derivative_vjp.argtypes = [vp, vp, vp, vp, vp, f64, vp]
     L.dg_adjoint_step.argtypes = [vp, vp, vp, vp, vp, f64, f64, vp]
     L.dg_adjoint_solve.argtypes = [vp, vp, vp, vp, vp, f64, f64, i32, i32, C.POINTER(C.c_int64), vp]
+    L.dg_checkpoint_schedule.argtypes = [i32, i32, C.POINTER(C.c_int64)]
     L.dg_kinetic_energy.argtypes = [vp, vp, vp, dp, vp]
     L.dg_set_viscosity.argtypes = [vp, f64]
     L.dg_last_error.argtypes = [vp]
@@ -104,7 +105,8 @@ def load(build_if_missing: bool = True):
                  "dg_max_dt", "dg_initial_state", "dg_node_coords", "dg_geometry", "dg_profile_stages",
                  "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
                  "dg_ensemble_step", "dg_ensemble_plan", "dg_time_derivative_vjp", "dg_adjoint_step",
-                 "dg_adjoint_solve", "dg_kinetic_energy", "dg_set_viscosity", "dg_check_conversions"):
+                 "dg_adjoint_solve", "dg_checkpoint_schedule", "dg_kinetic_energy", "dg_set_viscosity",
+                 "dg_check_conversions"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -312,6 +314,18 @@ def probe_peaks(device: int = 0):
     if st != DG_OK:
         raise DGError(st, "dg_probe_peaks failed")
     return float(out[0]), float(out[1])
+
+
+def checkpoint_schedule(nsteps: int, max_snapshots: int):
+    """(recomputed forward steps, adjoint steps) of the binomial checkpointing
+    schedule that ``Solver.adjoint_solve`` runs for these arguments; host
+    arithmetic only, no GPU needed."""
+    L = load()
+    counts = (C.c_int64 * 2)()
+    st = L.dg_checkpoint_schedule(int(nsteps), int(max_snapshots), counts)
+    if st != 0:
+        raise DGError(st, "dg_checkpoint_schedule: bad argument")
+    return int(counts[0]), int(counts[1])
 
 
 def check_conversions(x, stream=None):

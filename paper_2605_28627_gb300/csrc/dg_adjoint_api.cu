@@ -100,68 +100,123 @@ static dg_status advance(Ctx* c, double* U, double* G, double t, double dt, int 
   return DG_OK;
 }
 
-// Binomial checkpointing (Griewank's binomial schedule): beta(s, r) =
-// C(s + r, s) steps can be reversed with s free snapshots and r forward
-// repetitions.  The state at i0 is in snap[level]; reverse [i0, i1).
-static long binom(int s, int r) {
-  long v = 1;
-  for (int a = 1; a <= s; ++a) v = v * (r + a) / a;
+// Binomial checkpointing (Griewank 1992; Griewank & Walther 2000).  With s
+// stored states (the one at the start of the interval included) and r forward
+// sweeps, beta(s, r) = C(s + r, s) steps can be reversed; the least number of
+// forward steps that reverses n steps is
+//   t(n, s) = r n - beta(s + 1, r - 1),  r = rho(n, s) the least r with beta(s, r) >= n,
+// and t(n, 1) = n (n - 1) / 2 (every step recomputed from the start).
+static long long binom(long long s, long long r) {   // C(s + r, s)
+  const long long k = s < r ? s : r, top = s < r ? r : s;
+  long long v = 1;
+  for (long long a = 1; a <= k; ++a) v = v * (top + a) / a;
   return v;
 }
 
-struct Revolve {
+static long long rho(long long n, long long s) {
+  if (s <= 1) return n > 1 ? n - 1 : 0;
+  long long r = 0;
+  while (binom(s, r) < n) ++r;
+  return r;
+}
+
+// Where to store the next state when n > 1 steps are reversed from a stored
+// state with s >= 2 states in all: the least m in [1, n-1] minimising
+//   F(m) = m + t(n - m, s - 1) + t(m, s)
+// (advance m steps into a new state, reverse the right part with one state
+// less, then the left part).  t(., s) is convex with increments
+// t(x + 1, s) - t(x, s) = rho(x + 1, s), so F(m + 1) - F(m) =
+// 1 + rho(m + 1, s) - rho(n - m, s - 1) is non-decreasing and the least m where
+// it is >= 0 is found by bisection.
+static long long next_split(long long n, long long s) {
+  long long lo = 1, hi = n - 1;
+  while (lo < hi) {
+    const long long mid = lo + (hi - lo) / 2;
+    if (1 + rho(mid + 1, s) - rho(n - mid, s - 1) >= 0) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Runs the schedule that reverses nsteps steps with nsnap >= 1 state slots
+// (slot 0 holds the initial state) on an executor X with
+//   dg_status store(int from_slot, int to_slot, int i0, int m):  slot to := state at m,
+//                                                                 advanced from slot from at i0;
+//   dg_status adjoint(int slot, int i):                           adjoint of step i, state i in slot;
+//   dg_status recompute_adjoint(int slot, int i0, int i):         the same, state i recomputed from
+//                                                                 slot (state i0).
+// Intervals wait on an explicit stack (right part first), so the depth of
+// nesting does not grow with the number of slots.
+template <class X>
+static dg_status run_schedule(X& x, int nsteps, int nsnap, long long* forward, long long* adjoints) {
+  struct Interval { int i0, i1, slot; };
+  std::vector<Interval> todo;
+  todo.push_back({0, nsteps, 0});
+  *forward = 0;
+  *adjoints = 0;
+  while (!todo.empty()) {
+    const Interval iv = todo.back();
+    todo.pop_back();
+    const int n = iv.i1 - iv.i0;
+    const int states = nsnap - iv.slot;   // stored states usable for this interval
+    dg_status st = DG_OK;
+    if (n == 1) {
+      st = x.adjoint(iv.slot, iv.i0);
+      ++*adjoints;
+    } else if (states <= 1) {
+      for (int k = iv.i1 - 1; k >= iv.i0 && st == DG_OK; --k) {
+        st = x.recompute_adjoint(iv.slot, iv.i0, k);
+        *forward += k - iv.i0;
+        ++*adjoints;
+      }
+    } else {
+      const int m = iv.i0 + (int)next_split(n, states);
+      st = x.store(iv.slot, iv.slot + 1, iv.i0, m);
+      *forward += m - iv.i0;
+      todo.push_back({iv.i0, m, iv.slot});
+      todo.push_back({m, iv.i1, iv.slot + 1});
+    }
+    if (st != DG_OK) return st;
+  }
+  return DG_OK;
+}
+
+// The executor of dg_adjoint_solve: state slots in device memory.
+struct DeviceCheckpoints {
   Ctx* c;
-  std::vector<double*> snap;   // snapshot buffers
+  std::vector<double*> snap;   // state slots
   double* lam;
   double* dJdmu;
   double t0, dt;
   cudaStream_t s;
-  long forward_steps = 0;
-  long adjoint_steps = 0;
+
+  size_t bytes() const { return sizeof(double) * (size_t)c->E * 5 * c->P; }
+  double* reg() const { return c->d_adj_work + (size_t)c->E * 5 * c->P; }   // register slot of the work area
+
+  dg_status store(int from, int to, int i0, int m) {
+    ADJ_CUDA(cudaMemcpyAsync(snap[to], snap[from], bytes(), cudaMemcpyDeviceToDevice, s), c, "copy");
+    return advance(c, snap[to], reg(), t0 + i0 * dt, dt, m - i0, s);
+  }
+  dg_status adjoint(int slot, int i) { return step_adjoint(c, snap[slot], lam, dJdmu, t0 + i * dt, dt, s); }
+  dg_status recompute_adjoint(int slot, int i0, int i) {
+    double* W = c->d_adj_work;
+    ADJ_CUDA(cudaMemcpyAsync(W, snap[slot], bytes(), cudaMemcpyDeviceToDevice, s), c, "copy");
+    dg_status st = advance(c, W, reg(), t0 + i0 * dt, dt, i - i0, s);
+    if (st != DG_OK) return st;
+    // the step adjoint overwrites the work area, so it starts from a copy in
+    // stage slot 4, which it reads first and rewrites only at its fifth stage
+    double* keep = c->d_adj_stage + (size_t)4 * c->E * 5 * c->P;
+    ADJ_CUDA(cudaMemcpyAsync(keep, W, bytes(), cudaMemcpyDeviceToDevice, s), c, "copy");
+    return step_adjoint(c, keep, lam, dJdmu, t0 + i * dt, dt, s);
+  }
 };
 
-static dg_status reverse(Revolve& R, int i0, int i1, int level) {
-  Ctx* c = R.c;
-  const size_t bytes = sizeof(double) * (size_t)c->E * 5 * c->P;
-  const int n = i1 - i0;
-  const int free_snaps = (int)R.snap.size() - 1 - level;
-  if (n == 1) {
-    R.adjoint_steps++;
-    return step_adjoint(c, R.snap[level], R.lam, R.dJdmu, R.t0 + i0 * R.dt, R.dt, R.s);
-  }
-  double* G = c->d_adj_work + (size_t)c->E * 5 * c->P;   // register slot of the work area
-  if (free_snaps <= 0) {
-    // no snapshot left: recompute each step from the state at i0
-    for (int k = i1 - 1; k >= i0; --k) {
-      double* W = c->d_adj_work;
-      ADJ_CUDA(cudaMemcpyAsync(W, R.snap[level], bytes, cudaMemcpyDeviceToDevice, R.s), c, "copy");
-      dg_status st = advance(c, W, G, R.t0 + i0 * R.dt, R.dt, k - i0, R.s);
-      if (st != DG_OK) return st;
-      R.forward_steps += k - i0;
-      // the step adjoint overwrites the work area, so stage from a snapshot-free copy
-      double* keep = c->d_adj_stage;   // stage slot 0 is rewritten by step_adjoint anyway
-      ADJ_CUDA(cudaMemcpyAsync(keep + (size_t)4 * c->E * 5 * c->P, W, bytes, cudaMemcpyDeviceToDevice, R.s), c, "copy");
-      st = step_adjoint(c, keep + (size_t)4 * c->E * 5 * c->P, R.lam, R.dJdmu, R.t0 + k * R.dt, R.dt, R.s);
-      if (st != DG_OK) return st;
-      R.adjoint_steps++;
-    }
-    return DG_OK;
-  }
-  int r = 1;
-  while (binom(free_snaps, r) < n) ++r;
-  long first = binom(free_snaps, r - 1);
-  if (first >= n) first = n - 1;
-  if (first < 1) first = 1;
-  const int m = i0 + (int)first;
-  // advance a copy of the state at i0 to m into the next snapshot
-  ADJ_CUDA(cudaMemcpyAsync(R.snap[level + 1], R.snap[level], bytes, cudaMemcpyDeviceToDevice, R.s), c, "copy");
-  dg_status st = advance(c, R.snap[level + 1], G, R.t0 + i0 * R.dt, R.dt, m - i0, R.s);
-  if (st != DG_OK) return st;
-  R.forward_steps += m - i0;
-  st = reverse(R, m, i1, level + 1);
-  if (st != DG_OK) return st;
-  return reverse(R, i0, m, level);
-}
+// The same schedule without a device: only the counts.
+struct CountOnly {
+  dg_status store(int, int, int, int) { return DG_OK; }
+  dg_status adjoint(int, int) { return DG_OK; }
+  dg_status recompute_adjoint(int, int, int) { return DG_OK; }
+};
 
 }  // namespace dg
 
@@ -208,29 +263,43 @@ dg_status dg_adjoint_solve(dg_ctx* ctx, const double* dU0, const double* dlamT, 
   const size_t bytes = sizeof(double) * (size_t)c->E * 5 * c->P;
   if (dlam0 != dlamT) ADJ_CUDA(cudaMemcpyAsync(dlam0, dlamT, bytes, cudaMemcpyDeviceToDevice, s), c, "copy");
   if (nsteps == 0) return DG_OK;
-  Revolve R;
-  R.c = c;
-  R.lam = dlam0;
-  R.dJdmu = dJdmu;
-  R.t0 = t0;
-  R.dt = dt;
-  R.s = s;
+  DeviceCheckpoints X;
+  X.c = c;
+  X.lam = dlam0;
+  X.dJdmu = dJdmu;
+  X.t0 = t0;
+  X.dt = dt;
+  X.s = s;
   const int nsnap = max_snapshots < nsteps ? max_snapshots : nsteps;
-  R.snap.assign(nsnap, nullptr);
+  X.snap.assign(nsnap, nullptr);
   for (int a = 0; a < nsnap; ++a) {
-    cudaError_t e = cudaMalloc(&R.snap[a], bytes);
+    cudaError_t e = cudaMalloc(&X.snap[a], bytes);
     if (e != cudaSuccess) {
-      for (int b = 0; b < a; ++b) cudaFree(R.snap[b]);
+      for (int b = 0; b < a; ++b) cudaFree(X.snap[b]);
       return afail(c, DG_ENOMEM, "dg_adjoint_solve: snapshot allocation", e);
     }
   }
-  cudaError_t e = cudaMemcpyAsync(R.snap[0], dU0, bytes, cudaMemcpyDeviceToDevice, s);
-  st = e == cudaSuccess ? reverse(R, 0, nsteps, 0) : afail(c, DG_ECUDA, "copy", e);
+  long long forward = 0, adjoints = 0;
+  cudaError_t e = cudaMemcpyAsync(X.snap[0], dU0, bytes, cudaMemcpyDeviceToDevice, s);
+  st = e == cudaSuccess ? run_schedule(X, nsteps, nsnap, &forward, &adjoints) : afail(c, DG_ECUDA, "copy", e);
   cudaError_t es = cudaStreamSynchronize(s);
-  for (double* p : R.snap) cudaFree(p);
+  for (double* p : X.snap) cudaFree(p);
   if (st != DG_OK) return st;
   if (es != cudaSuccess) return afail(c, DG_ECUDA, "dg_adjoint_solve: sync", es);
-  if (host_counts2) { host_counts2[0] = R.forward_steps; host_counts2[1] = R.adjoint_steps; }
+  if (host_counts2) { host_counts2[0] = forward; host_counts2[1] = adjoints; }
+  return DG_OK;
+}
+
+dg_status dg_checkpoint_schedule(int32_t nsteps, int32_t max_snapshots, int64_t* host_counts2) {
+  if (nsteps < 0 || max_snapshots < 1 || !host_counts2) return DG_EINVAL;
+  const int nsnap = max_snapshots < nsteps ? max_snapshots : nsteps;
+  long long forward = 0, adjoints = 0;
+  if (nsteps > 0) {
+    CountOnly X;
+    run_schedule(X, nsteps, nsnap, &forward, &adjoints);
+  }
+  host_counts2[0] = forward;
+  host_counts2[1] = adjoints;
   return DG_OK;
 }
 

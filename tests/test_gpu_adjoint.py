@@ -70,12 +70,13 @@ def test_step_and_solve_adjoint_vs_oracle(orc, dg, rk):
     lhs = float((lam0.cpu().numpy() * w).sum()) + 0.4 * dmu.item()
     rhs = float((lam * dUT).sum())
     assert abs(lhs - rhs) <= 1e-10 * abs(rhs), (lhs, rhs)
-    assert counts[1] == nsteps
+    assert counts == dg.checkpoint_schedule(nsteps, 3) and counts[1] == nsteps
     # checkpointing does not change the result: all snapshots vs few vs one
     ref = None
     for snaps in (nsteps, 2, 1):
         dm = torch.zeros(1, dtype=torch.float64, device="cuda")
-        l0, _ = s.adjoint_solve(_cuda(U0), _cuda(lam), 0.0, dt, nsteps, max_snapshots=snaps, dJdmu=dm)
+        l0, cnt = s.adjoint_solve(_cuda(U0), _cuda(lam), 0.0, dt, nsteps, max_snapshots=snaps, dJdmu=dm)
+        assert cnt == dg.checkpoint_schedule(nsteps, snaps)
         cur = (l0.cpu().numpy(), dm.item())
         if ref is None:
             ref = cur
