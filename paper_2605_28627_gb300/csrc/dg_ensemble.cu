@@ -368,6 +368,12 @@ static std::map<std::string, GroupPlan> read_cache(const std::string& path) {
     GroupPlan p;
     if (std::sscanf(line, "%255[^\t]\t%d\t%d\t%d\t%d", key, &p.epb_choice, &p.vol_grid, &p.lift_grid,
                     &p.face_grid) == 5) {
+      // a line that no tuning run writes (edited or damaged file) is ignored,
+      // so that group is tuned again
+      const bool per_member = p.epb_choice == 2;
+      const bool tiles = (p.epb_choice == 0 || p.epb_choice == 1) && p.vol_grid > 0 && p.lift_grid > 0 &&
+                         p.face_grid > 0;
+      if (!per_member && !tiles) continue;
       p.tuned = true;
       p.from_cache = true;
       m[key] = p;
@@ -396,7 +402,17 @@ static dg_status autotune(dg_ensemble* e, cudaStream_t s) {
   for (Group& g : e->groups) {
     const std::string key = cache_key(e, g.N);
     auto it = cache.find(key);
-    if (it != cache.end()) { g.plan = it->second; continue; }
+    if (it != cache.end()) {
+      // the key holds no member sizes: the cached grids may exceed this
+      // group's tile counts (the persistent kernels would only idle there)
+      g.plan = it->second;
+      if (g.plan.epb_choice != 2) {
+        g.plan.vol_grid = std::min(g.plan.vol_grid, g.n_elem_tiles[g.plan.epb_choice]);
+        g.plan.lift_grid = std::min(g.plan.lift_grid, g.n_elem_tiles[0]);
+        g.plan.face_grid = std::min(g.plan.face_grid, g.n_face_tiles);
+      }
+      continue;
+    }
     GroupPlan best;
     float best_ms = 1e30f;
     const int grids[4] = {sms, 2 * sms, 4 * sms, 0};

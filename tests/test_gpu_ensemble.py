@@ -61,3 +61,39 @@ def test_ensemble_matches_single_runs_bitwise(dg, tmp_path, precision):
     ens2.close()
     for r in runs:
         r[0].close()
+
+
+def test_damaged_tuning_cache_is_retuned(dg, tmp_path):
+    """Cache lines no tuning run writes (an unknown tile choice, a zero grid)
+    are ignored: those groups are tuned again and the results do not change."""
+    runs = [_make(dg, m, 0) for m in MEMBERS[:3]]     # N = 2 and N = 3
+    cache = tmp_path / "tune.txt"
+    dts = [r[2] for r in runs]
+    t0 = [0.0] * len(runs)
+    ens = dg.Ensemble([r[0] for r in runs], tune_cache_path=str(cache))
+    Us = [r[1].clone() for r in runs]
+    Gs = [torch.empty_like(U) for U in Us]
+    ens.step(Us, Gs, t0, dts, nsteps=1)
+    ens.close()
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 2
+    damaged = []
+    for i, line in enumerate(lines):
+        f = line.split("\t")
+        if i == 0:
+            f[1] = "7"
+        else:
+            f[1], f[2] = "0", "0"
+        damaged.append("\t".join(f))
+    cache.write_text("\n".join(damaged) + "\n")
+    ens2 = dg.Ensemble([r[0] for r in runs], tune_cache_path=str(cache))
+    Us2 = [r[1].clone() for r in runs]
+    Gs2 = [torch.empty_like(U) for U in Us2]
+    ens2.step(Us2, Gs2, t0, dts, nsteps=1)
+    torch.cuda.synchronize()
+    assert not any(g["cached"] for g in ens2.plan()["groups"])
+    ens2.close()
+    for U, U2 in zip(Us, Us2):
+        assert torch.equal(U, U2)
+    for r in runs:
+        r[0].close()
