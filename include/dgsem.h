@@ -231,7 +231,8 @@ dg_status dg_set_viscosity(dg_ctx* ctx, double mu);
 typedef struct dg_ensemble dg_ensemble;
 
 /* The members stay owned by the caller and must outlive the ensemble.
- * DG_EINVAL if a member is NULL or on another device or precision;
+ * DG_EINVAL if a member is NULL, appears twice (its work buffers would be
+ * shared by two members) or is on another device or precision;
  * DG_EUNSUPPORTED for a member on Gauss nodes or with RK4-14 (the ensemble
  * kernels are the LGL split-form ones, its steps LSERK4-5). */
 dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune_cache_path, dg_ensemble** out);
@@ -240,6 +241,7 @@ dg_status dg_ensemble_destroy(dg_ensemble* ens);
 /* nsteps LSERK4-5 steps of every member r: state dU[r] with register dG[r]
  * (device arrays of the member's dg_state_len), from time t[r] with step
  * dt[r] (host arrays of n doubles).  Identical per member to dg_rk_step.
+ * DG_EINVAL if a pointer is NULL or the 2n arrays are not all distinct.
  * Waits for earlier work on `stream`, then enqueues one graph launch. */
 dg_status dg_ensemble_step(dg_ensemble* ens, double* const* dU, double* const* dG, const double* t,
                            const double* dt, int32_t nsteps, dg_stream stream);

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -478,9 +479,11 @@ dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune
   e->device = c0->device;
   e->precision = c0->prm.precision;
   e->cache_path = tune_cache_path ? tune_cache_path : "";
+  std::set<const Ctx*> seen;
   for (int r = 0; r < n; ++r) {
     Ctx* c = reinterpret_cast<Ctx*>(members[r]);
-    if (!c || c->device != e->device || c->prm.precision != e->precision) {
+    // a context twice would have two members share its work buffers
+    if (!c || c->device != e->device || c->prm.precision != e->precision || !seen.insert(c).second) {
       delete e;
       return DG_EINVAL;
     }
@@ -492,13 +495,14 @@ dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune
   }
   if (cudaSetDevice(e->device) != cudaSuccess) { delete e; return DG_ECUDA; }
   cudaDeviceProp prop;
-  cudaGetDeviceProperties(&prop, e->device);
+  if (cudaGetDeviceProperties(&prop, e->device) != cudaSuccess) { delete e; return DG_ECUDA; }
   e->gpu_name = prop.name;
   e->sms = prop.multiProcessorCount;
   std::map<int, std::vector<int>> byN;
   for (int r = 0; r < n; ++r) byN[e->members[r]->N].push_back(r);
   for (auto& kv : byN) {
-    Group g;
+    e->groups.emplace_back();   // owned by e from here on, so bail() frees what it holds
+    Group& g = e->groups.back();
     g.N = kv.first;
     g.members = kv.second;
     g.d_D = e->members[g.members[0]]->d_D;
@@ -513,7 +517,8 @@ dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune
       }
       g.n_elem_tiles[ch] = (int)t.size();
       if (cudaMalloc(&g.d_elem_tiles[ch], sizeof(int2) * t.size()) != cudaSuccess) return bail(DG_ENOMEM);
-      cudaMemcpy(g.d_elem_tiles[ch], t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice);
+      if (cudaMemcpy(g.d_elem_tiles[ch], t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(DG_ECUDA);
     }
     std::vector<int2> ft;
     const int NN = (g.N + 1) * (g.N + 1);
@@ -523,10 +528,10 @@ dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune
     }
     g.n_face_tiles = (int)ft.size();
     if (cudaMalloc(&g.d_face_tiles, sizeof(int2) * ft.size()) != cudaSuccess) return bail(DG_ENOMEM);
-    cudaMemcpy(g.d_face_tiles, ft.data(), sizeof(int2) * ft.size(), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(g.d_face_tiles, ft.data(), sizeof(int2) * ft.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(DG_ECUDA);
     cudaError_t ce = e->precision == DG_FP32OP ? dispatch_setup<float>(g.N) : dispatch_setup<double>(g.N);
     if (ce != cudaSuccess) return bail(DG_ECUDA);
-    e->groups.push_back(g);
   }
   if (cudaMalloc(&e->d_G, sizeof(double*) * n) != cudaSuccess ||
       cudaMalloc(&e->d_clocks, sizeof(double*) * n) != cudaSuccess ||
@@ -537,7 +542,8 @@ dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune
     return bail(DG_ENOMEM);
   std::vector<size_t> len(n);
   for (int r = 0; r < n; ++r) len[r] = (size_t)e->members[r]->E * 5 * e->members[r]->P;
-  cudaMemcpy(e->d_len, len.data(), sizeof(size_t) * n, cudaMemcpyHostToDevice);
+  if (cudaMemcpy(e->d_len, len.data(), sizeof(size_t) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(DG_ECUDA);
   e->cur_U.assign(n, nullptr);
   e->cur_G.assign(n, nullptr);
   *out = e;
@@ -570,8 +576,10 @@ dg_status dg_ensemble_step(dg_ensemble* e, double* const* dU, double* const* dG,
   cudaStream_t s = (cudaStream_t)stream;
   ENS_CUDA(cudaSetDevice(e->device), e, "cudaSetDevice");
   bool changed = false;
+  std::set<const double*> distinct;
   for (int r = 0; r < n; ++r) {
-    if (!dU[r] || !dG[r] || dU[r] == dG[r]) return ens_fail(e, DG_EINVAL, "dg_ensemble_step: bad state pointers");
+    if (!dU[r] || !dG[r] || !distinct.insert(dU[r]).second || !distinct.insert(dG[r]).second)
+      return ens_fail(e, DG_EINVAL, "dg_ensemble_step: null or repeated state pointers");
     if (dU[r] != e->cur_U[r] || dG[r] != e->cur_G[r]) changed = true;
   }
   if (changed) {

@@ -97,3 +97,22 @@ def test_damaged_tuning_cache_is_retuned(dg, tmp_path):
         assert torch.equal(U, U2)
     for r in runs:
         r[0].close()
+
+
+def test_repeated_members_and_states_are_rejected(dg):
+    runs = [_make(dg, m, 0) for m in MEMBERS[:2]]
+    with pytest.raises(dg.DGError):
+        dg.Ensemble([runs[0][0], runs[1][0], runs[0][0]])
+    ens = dg.Ensemble([r[0] for r in runs])
+    Us = [r[1].clone() for r in runs]
+    Gs = [torch.empty_like(U) for U in Us]
+    dts = [r[2] for r in runs]
+    before = [U.clone() for U in Us]
+    with pytest.raises(dg.DGError):            # a member's register is its own state
+        ens.step(Us, [Us[0], Gs[1]], [0.0, 0.0], dts, nsteps=1)
+    torch.cuda.synchronize()
+    assert all(torch.equal(U, B) for U, B in zip(Us, before))
+    ens.step(Us, Gs, [0.0, 0.0], dts, nsteps=1)     # the ensemble stays usable
+    ens.close()
+    for r in runs:
+        r[0].close()
