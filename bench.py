@@ -52,9 +52,12 @@ MEASURED_TRAFFIC = {(7, "fp64"): 669.022720e6 + 218.296320e6}
 # Algorithmic FP64 operation count of the volume kernel per node and stage
 # (FMA = 2 flops; a divide, square root or logarithm counts as 1).  The
 # two-point flux with symmetric reuse is evaluated 3(n-1)/2 times per node.
+PAIR_FLOPS = 97.0                      # Chandrashekar flux + metric average + both accumulations
+
+
 def volume_flops_per_dof(N):
     n = N + 1
-    pair = 97.0                        # Chandrashekar flux + metric average + both accumulations
+    pair = PAIR_FLOPS
     diag = 3 * 2.0 * 5                 # D_ii terms folded into the accumulators
     visc = 20.0 + 3 * 26.0 + 12 * n * 2.0
     prim = 13.0

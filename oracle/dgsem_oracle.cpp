@@ -70,6 +70,33 @@ using std::sqrt; using std::log; using std::fabs;
 // max with ties going to the first argument (the value decides the branch)
 template <class T> inline T vmax(T a, T b) { return (val(b) > val(a)) ? b : a; }
 
+// Operation-counting scalar: evaluates in double and counts each arithmetic
+// operation that has a state-dependent operand (+ and - as additions, *, /,
+// sqrt and log apart; a sign change is free).  Products of geometry or basis
+// values alone stay in double and are not counted.  It serves only to count
+// the floating-point work of the operator as this oracle states it.
+struct OpCount { unsigned long long add = 0, mul = 0, div = 0, sqrt = 0, log = 0; };
+static OpCount g_ops;
+struct Counted {
+  double v;
+  Counted() : v(0) {}
+  Counted(double a) : v(a) {}
+};
+inline Counted operator+(Counted a, Counted b) { ++g_ops.add; return Counted(a.v + b.v); }
+inline Counted operator-(Counted a, Counted b) { ++g_ops.add; return Counted(a.v - b.v); }
+inline Counted operator-(Counted a) { return Counted(-a.v); }
+inline Counted operator*(Counted a, Counted b) { ++g_ops.mul; return Counted(a.v * b.v); }
+inline Counted operator/(Counted a, Counted b) { ++g_ops.div; return Counted(a.v / b.v); }
+inline Counted& operator+=(Counted& a, Counted b) { a = a + b; return a; }
+inline Counted& operator-=(Counted& a, Counted b) { a = a - b; return a; }
+inline Counted& operator*=(Counted& a, Counted b) { a = a * b; return a; }
+inline Counted sqrt(Counted a) { ++g_ops.sqrt; return Counted(std::sqrt(a.v)); }
+inline Counted log(Counted a) { ++g_ops.log; return Counted(std::log(a.v)); }
+inline Counted fabs(Counted a) { return Counted(std::fabs(a.v)); }
+inline bool operator<(Counted a, Counted b) { return a.v < b.v; }
+inline bool operator>(Counted a, Counted b) { return a.v > b.v; }
+inline double val(Counted a) { return a.v; }
+
 // Non-differentiable points of the LLF speed max(|u.n| + c): where the two
 // arguments tie, or u.n vanishes, to within 1e-12 of the local scale (as on
 // the symmetry planes of a symmetric flow, where the values differ only by
@@ -81,7 +108,9 @@ inline Dual vmax_kink(Dual a, Dual b) {
     return Dual(b.v > a.v ? b.v : a.v, 0.5 * (a.d + b.d));
   return b.v > a.v ? b : a;
 }
+inline Counted vmax_kink(Counted a, Counted b) { return b.v > a.v ? b : a; }
 inline double abs_kink(double x, double) { return std::fabs(x); }
+inline Counted abs_kink(Counted x, double) { return Counted(std::fabs(x.v)); }
 inline Dual abs_kink(Dual x, double scale) {
   if (std::fabs(x.v) <= 1e-12 * scale) return Dual(std::fabs(x.v), 0.0);
   return x.v < 0 ? -x : x;
@@ -1394,6 +1423,36 @@ void orc_time_derivative_tl(void* h, const double* U, const double* dU, double d
   for (size_t a = 0; a < len; ++a) Ud[a] = Dual(U[a], dU ? dU[a] : 0.0);
   rhs<Dual>(*c, Ud.data(), Utd.data(), t, Dual(c->prm.mu, dmu));
   for (size_t a = 0; a < len; ++a) { if (Ut) Ut[a] = Utd[a].v; if (dUt) dUt[a] = Utd[a].d; }
+}
+
+// Floating-point operations of one evaluation of R(U) by the LGL operator of
+// this oracle, counted with the Counted scalar: out5 = {additions and
+// subtractions, multiplications, divisions, square roots, logarithms}.
+void orc_count_ops(void* h, const double* U, double t, double* out5) {
+  Ctx* c = (Ctx*)h;
+  for (int k = 0; k < 5; ++k) out5[k] = 0.0;
+  if (c->nodes != 0) return;   // counted for the LGL operator
+  size_t len = (size_t)c->E * 5 * c->P;
+  std::vector<Counted> Uc(len), Utc(len);
+  for (size_t a = 0; a < len; ++a) Uc[a] = Counted(U[a]);
+  g_ops = OpCount();
+  rhs<Counted>(*c, Uc.data(), Utc.data(), t, Counted(c->prm.mu));
+  out5[0] = (double)g_ops.add; out5[1] = (double)g_ops.mul; out5[2] = (double)g_ops.div;
+  out5[3] = (double)g_ops.sqrt; out5[4] = (double)g_ops.log;
+}
+
+// The same count for one two-point flux evaluation (Chandrashekar) of the
+// conservative states qL, qR in direction nv.
+void orc_count_ec_flux_ops(const double* prm, const double* qL, const double* qR, const double* nv, double* out5) {
+  Params pr{prm[0], prm[1], prm[2], prm[3], 0, 0, 0.0, 0, 0, 1.0, 0.0};
+  Counted a[5], b[5], n3[3], f[5];
+  for (int k = 0; k < 5; ++k) { a[k] = Counted(qL[k]); b[k] = Counted(qR[k]); }
+  for (int k = 0; k < 3; ++k) n3[k] = Counted(nv[k]);
+  Prim<Counted> L = cons2prim(pr, a), Rr = cons2prim(pr, b);
+  g_ops = OpCount();
+  ec_flux(pr, L, Rr, n3, f);
+  out5[0] = (double)g_ops.add; out5[1] = (double)g_ops.mul; out5[2] = (double)g_ops.div;
+  out5[3] = (double)g_ops.sqrt; out5[4] = (double)g_ops.log;
 }
 
 void orc_rk_steps(void* h, double* U, double t, double dt, int nsteps) {

@@ -65,6 +65,8 @@ def _load():
     L.orc_set_vol_flux.argtypes = [C.c_void_p, C.c_int]
     L.orc_lifting.argtypes = [C.c_void_p, _dp, _dp]
     L.orc_volume_term.argtypes = [C.c_void_p, _dp, _dp]
+    L.orc_count_ops.argtypes = [C.c_void_p, _dp, C.c_double, _dp]
+    L.orc_count_ec_flux_ops.argtypes = [_dp, _dp, _dp, _dp, _dp]
     _lib = L
     return L
 
@@ -124,6 +126,19 @@ def roe_flux(qL, qR, nv, gamma=1.4):
     _load().orc_roe_flux(_prm(gamma, 1.0, 0.72, 0.0), np.ascontiguousarray(qL, dtype=np.float64),
                          np.ascontiguousarray(qR, dtype=np.float64), np.ascontiguousarray(nv, dtype=np.float64), out)
     return out
+
+
+_OP_NAMES = ("add", "mul", "div", "sqrt", "log")
+
+
+def count_ec_flux_ops(qL, qR, nv, gamma=1.4):
+    """Operations of one two-point flux evaluation (from the primitive states
+    on), counted by the oracle's counting scalar: dict add/mul/div/sqrt/log."""
+    out = np.zeros(5)
+    _load().orc_count_ec_flux_ops(_prm(gamma, 1.0, 0.72, 0.0), np.ascontiguousarray(qL, dtype=np.float64),
+                                  np.ascontiguousarray(qR, dtype=np.float64),
+                                  np.ascontiguousarray(nv, dtype=np.float64), out)
+    return dict(zip(_OP_NAMES, (int(v) for v in out)))
 
 
 def log_mean(a, b):
@@ -204,6 +219,13 @@ class Oracle:
         dU = np.array(dU, dtype=np.float64, copy=True, order="C")
         self._L.orc_rk_steps_tl(self._h, U, dU, float(dmu), float(t), float(dt), int(nsteps))
         return U, dU
+
+    def count_ops(self, U, t=0.0):
+        """Operations of one R(U) evaluation of this oracle (LGL operator),
+        counted by its counting scalar: dict add/mul/div/sqrt/log."""
+        out = np.zeros(5)
+        self._L.orc_count_ops(self._h, np.ascontiguousarray(U, dtype=np.float64), float(t), out)
+        return dict(zip(_OP_NAMES, (int(v) for v in out)))
 
     def set_vol_flux(self, kind: int):
         self._L.orc_set_vol_flux(self._h, int(kind))
