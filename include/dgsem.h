@@ -23,6 +23,10 @@
  *     documented otherwise.
  *   - Every call returns a dg_status; on failure dg_last_error() describes it.
  *     The library never aborts the process and never falls back to the CPU.
+ *   - A context owns the work buffers (lifted gradients, face fluxes, clock)
+ *     of the calls made on it, so those calls must not overlap on the GPU:
+ *     issue them on one stream, or order them with events.  Different
+ *     contexts are independent.  A context is not thread-safe.
  */
 #ifndef DGSEM_H
 #define DGSEM_H
