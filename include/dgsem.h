@@ -186,7 +186,8 @@ dg_status dg_time_derivative_vjp(dg_ctx* ctx, const double* dU, const double* dv
 
 /* Adjoint of one step (the context's scheme) from dU_n (state at the step's start, time t):
  * dlam_n = (dU_{n+1}/dU_n)^T dlam_np1 (may alias), dJdmu += the step's
- * lambda . dU_{n+1}/dmu.  The stage states are recomputed from dU_n. */
+ * lambda . dU_{n+1}/dmu.  The stage states are recomputed from dU_n.
+ * DG_EINVAL if either adjoint array is dU_n. */
 dg_status dg_adjoint_step(dg_ctx* ctx, const double* dU_n, const double* dlam_np1, double* dlam_n, double* dJdmu,
                           double t, double dt, dg_stream stream);
 
@@ -197,7 +198,8 @@ dg_status dg_adjoint_step(dg_ctx* ctx, const double* dU_n, const double* dlam_np
  * each are allocated for the call), forward recomputation in between, the
  * least number of recomputed forward steps for that many states.
  * host_counts2 (may be NULL) receives {recomputed forward steps, adjoint
- * steps}.  Synchronises the stream. */
+ * steps}.  DG_EINVAL if either adjoint array is dU0.  Synchronises the
+ * stream. */
 dg_status dg_adjoint_solve(dg_ctx* ctx, const double* dU0, const double* dlamT, double* dlam0, double* dJdmu,
                            double t0, double dt, int32_t nsteps, int32_t max_snapshots, int64_t* host_counts2,
                            dg_stream stream);

@@ -241,6 +241,7 @@ dg_status dg_adjoint_step(dg_ctx* ctx, const double* dU_n, const double* dlam_np
                           double t, double dt, dg_stream stream) {
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   if (!c || !dU_n || !dlam_np1 || !dlam_n) return afail(c, DG_EINVAL, "dg_adjoint_step: null argument");
+  if (dlam_n == dU_n || dlam_np1 == dU_n) return afail(c, DG_EINVAL, "dg_adjoint_step: an adjoint aliases the state");
   cudaStream_t s = (cudaStream_t)stream;
   ADJ_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
   dg_status st = ensure_adjoint(c);
@@ -256,6 +257,7 @@ dg_status dg_adjoint_solve(dg_ctx* ctx, const double* dU0, const double* dlamT, 
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   if (!c || !dU0 || !dlamT || !dlam0 || nsteps < 0 || max_snapshots < 1)
     return afail(c, DG_EINVAL, "dg_adjoint_solve: bad argument");
+  if (dlam0 == dU0 || dlamT == dU0) return afail(c, DG_EINVAL, "dg_adjoint_solve: an adjoint aliases the state");
   cudaStream_t s = (cudaStream_t)stream;
   ADJ_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
   dg_status st = ensure_adjoint(c);
