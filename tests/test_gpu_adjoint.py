@@ -120,3 +120,21 @@ def test_autograd_gradient_vs_central_differences(dg):
     hm = 1e-7
     fd = (Jof(U0, prm["mu"] + hm) - Jof(U0, prm["mu"] - hm)) / (2 * hm)
     assert abs(fd - gmu) <= 1e-6 * abs(gmu), (fd, gmu)
+
+
+def test_adjoint_arrays_may_not_be_the_state(dg):
+    prm = tgv_params(Ma=0.2, Re=800.0)
+    mesh = box_mesh(2, 1, lo=0.0, hi=2 * math.pi)
+    s = dg.Solver(mesh, 2, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"])
+    U = s.initial_state("tgv", prm["p0"])
+    lam = torch.ones_like(U)
+    before = U.clone()
+    with pytest.raises(dg.DGError):
+        s.adjoint_step(U, lam, lam_n=U)
+    with pytest.raises(dg.DGError):
+        s.adjoint_solve(U, lam, 0.0, 1e-3, 3, lam0=U)
+    torch.cuda.synchronize()
+    assert torch.equal(U, before)
+    lam0, counts = s.adjoint_solve(U, lam, 0.0, 1e-3, 3, max_snapshots=2)
+    assert counts == dg.checkpoint_schedule(3, 2) and torch.isfinite(lam0).all()
+    s.close()
