@@ -150,13 +150,13 @@ static long long next_split(long long n, long long s) {
 template <class X>
 static dg_status run_schedule(X& x, int nsteps, int nsnap, long long* forward, long long* adjoints) {
   struct Interval { int i0, i1, slot; };
-  std::vector<Interval> todo;
-  todo.push_back({0, nsteps, 0});
+  std::vector<Interval> pending;
+  pending.push_back({0, nsteps, 0});
   *forward = 0;
   *adjoints = 0;
-  while (!todo.empty()) {
-    const Interval iv = todo.back();
-    todo.pop_back();
+  while (!pending.empty()) {
+    const Interval iv = pending.back();
+    pending.pop_back();
     const int n = iv.i1 - iv.i0;
     const int states = nsnap - iv.slot;   // stored states usable for this interval
     dg_status st = DG_OK;
@@ -173,8 +173,8 @@ static dg_status run_schedule(X& x, int nsteps, int nsnap, long long* forward, l
       const int m = iv.i0 + (int)next_split(n, states);
       st = x.store(iv.slot, iv.slot + 1, iv.i0, m);
       *forward += m - iv.i0;
-      todo.push_back({iv.i0, m, iv.slot});
-      todo.push_back({m, iv.i1, iv.slot + 1});
+      pending.push_back({iv.i0, m, iv.slot});
+      pending.push_back({m, iv.i1, iv.slot + 1});
     }
     if (st != DG_OK) return st;
   }
