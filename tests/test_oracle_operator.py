@@ -234,7 +234,8 @@ def test_mms_source_matches_symbolic_residual(orc):
         np.testing.assert_allclose(S[:, v].reshape(o.E, -1), ref, rtol=1e-12, atol=1e-12)
 
 
-def test_viscous_terms_match_symbolic_navier_stokes(orc):
+@pytest.mark.parametrize("nodes", [0, 1])
+def test_viscous_terms_match_symbolic_navier_stokes(orc, nodes):
     """With constant mu the viscous part of R is linear in mu, so
     (R_mu(U) - R_0(U)) / mu is the discrete div F_v of Sec. 3.1 (BR1 lifting,
     viscous volume and surface terms). For a smooth compressible state it must
@@ -274,8 +275,8 @@ def test_viscous_terms_match_symbolic_navier_stokes(orc):
     errs = {}
     for N in (5, 7):
         m = box_mesh(4, N, lo=0.0, hi=2 * np.pi, deform="sinprod", rotate_seed=17)
-        o1 = orc.Oracle(m, N, gamma=g, R=Rg, Pr=Pr, mu=mu)
-        o0 = orc.Oracle(m, N, gamma=g, R=Rg, Pr=Pr, mu=0.0)
+        o1 = orc.Oracle(m, N, gamma=g, R=Rg, Pr=Pr, mu=mu, nodes=nodes)
+        o0 = orc.Oracle(m, N, gamma=g, R=Rg, Pr=Pr, mu=0.0, nodes=nodes)
         Xn = o1.node_coords()
         U = np.stack([at_nodes(f, Xn) for f in cons], 1).reshape(o1.shape)
         V = ((o1.time_derivative(U) - o0.time_derivative(U)) / mu).reshape(o1.E, 5, -1)
@@ -291,8 +292,8 @@ def test_viscous_terms_match_symbolic_navier_stokes(orc):
     assert all(e7 < e5 / 5 for e5, e7 in zip(errs[5], errs[7])), errs
 
 
-@pytest.mark.parametrize("surf_flux", [0, 1])
-def test_inviscid_operator_matches_symbolic_euler(orc, surf_flux):
+@pytest.mark.parametrize("nodes,surf_flux", [(0, 0), (0, 1), (1, 0), (1, 2)])
+def test_inviscid_operator_matches_symbolic_euler(orc, nodes, surf_flux):
     """For a smooth state with every primitive varying in all three
     directions, R with mu = 0 approaches -div F_c(q) of the Euler equations
     (Sec. 3.1, Eq. 1: mass, momentum with its pressure, energy (rho E + p) u),
@@ -322,7 +323,7 @@ def test_inviscid_operator_matches_symbolic_euler(orc, surf_flux):
     errs = {}
     for N in (5, 7):
         m = box_mesh(4, N, lo=0.0, hi=2 * np.pi, deform="sinprod", rotate_seed=17)
-        o = orc.Oracle(m, N, gamma=g, mu=0.0, surf_flux=surf_flux)
+        o = orc.Oracle(m, N, gamma=g, mu=0.0, surf_flux=surf_flux, nodes=nodes)
         Xn = o.node_coords()
         U = np.stack([f(Xn[:, 0], Xn[:, 1], Xn[:, 2]) * np.ones_like(Xn[:, 0]) for f in cons], 1).reshape(o.shape)
         R = o.time_derivative(U).reshape(o.E, 5, -1)
@@ -330,7 +331,9 @@ def test_inviscid_operator_matches_symbolic_euler(orc, surf_flux):
         for v in range(5):
             r = exact[v](Xn[:, 0], Xn[:, 1], Xn[:, 2]) * np.ones_like(Xn[:, 0])
             errs[N].append(np.abs(R[:, v] - r).max() / np.abs(r).max())
-    assert max(errs[7]) < 2e-3, errs[7]
+    # discretisation error only (a dropped or mis-signed flux term is O(1)):
+    # below 1e-3 on LGL nodes, 2.2e-3 with the Gauss weak form at N = 7
+    assert max(errs[7]) < 5e-3, errs[7]
     assert all(e7 < e5 / 5 for e5, e7 in zip(errs[5], errs[7])), errs
 
 
