@@ -337,7 +337,8 @@ def test_inviscid_operator_matches_symbolic_euler(orc, nodes, surf_flux):
     assert all(e7 < e5 / 5 for e5, e7 in zip(errs[5], errs[7])), errs
 
 
-def test_integrals_match_closed_forms(orc):
+@pytest.mark.parametrize("nodes", [0, 1])
+def test_integrals_match_closed_forms(orc, nodes):
     """The diagnostics of Sec. 4.2 for a smooth periodic state on a curved
     rotated mesh: the five conservation totals, E_k = 1/(2|Omega|) int rho |u|^2,
     eps = mu/|Omega| int |omega|^2 and min p.  The references integrate the same
@@ -370,7 +371,7 @@ def test_integrals_match_closed_forms(orc):
     scale = [tr[v][1] for v in range(5)] + [ref[5], ref[6]]
 
     m = box_mesh(4, N, lo=0.0, hi=2 * np.pi, deform="sinprod", rotate_seed=17)
-    o = orc.Oracle(m, N, gamma=g, mu=mu)
+    o = orc.Oracle(m, N, gamma=g, mu=mu, nodes=nodes)
     Xn = o.node_coords()
     U = np.stack([sp.lambdify((x, y, z), f, "numpy")(Xn[:, 0], Xn[:, 1], Xn[:, 2]) * np.ones_like(Xn[:, 0])
                   for f in cons], 1).reshape(o.shape)
