@@ -338,6 +338,60 @@ def test_inviscid_operator_matches_symbolic_euler(orc, nodes, surf_flux):
 
 
 @pytest.mark.parametrize("nodes", [0, 1])
+def test_sutherland_viscous_terms_match_symbolic_navier_stokes(orc, nodes):
+    """Sutherland's law (Sec. 4.2) at each node's temperature: mu = mu0 s(T),
+    s(T) = (T/T_ref)^(3/2) (T_ref + S)/(T + S), lambda = mu c_p / Pr.  The
+    viscous part is still linear in mu0, so (R_mu0 - R_0)/mu0 must approach
+    the symbolic div F_v with s(T) inside the stress and the heat flux, and
+    differ clearly from the constant-viscosity div F_v where T varies."""
+    sp = pytest.importorskip("sympy")
+    g, Rg, Pr, mu0, T_ref, S = 1.4, 1.0, 0.72, 0.5, 1.0, 110.4 / 273.15
+    x, y, z = sp.symbols("x y z")
+    X = [x, y, z]
+    rho = 1 + 0.2 * sp.sin(x) * sp.cos(z) + 0.1 * sp.cos(y)
+    u = [0.3 * sp.sin(y) + 0.2 * sp.sin(x) * sp.cos(z),
+         0.25 * sp.sin(z) + 0.15 * sp.cos(x) * sp.sin(y),
+         0.2 * sp.sin(x + y) + 0.1 * sp.cos(z)]
+    p = 1 + 0.2 * sp.cos(y) * sp.sin(z) + 0.1 * sp.sin(x)
+    T = p / (rho * Rg)
+    cp_Pr = g * Rg / (g - 1) / Pr
+    div = sum(sp.diff(u[j], X[j]) for j in range(3))
+
+    def div_fv(law):
+        tau = [[law * (sp.diff(u[i], X[j]) + sp.diff(u[j], X[i]) - (sp.Rational(2, 3) * div if i == j else 0))
+                for j in range(3)] for i in range(3)]
+        out = [sp.Integer(0)] + [sum(sp.diff(tau[i][j], X[j]) for j in range(3)) for i in range(3)]
+        out.append(sum(sp.diff(sum(u[i] * tau[i][j] for i in range(3)) + law * cp_Pr * sp.diff(T, X[j]), X[j])
+                       for j in range(3)))
+        return [sp.lambdify((x, y, z), f, "numpy") for f in out]
+
+    exact = div_fv((T / T_ref) ** sp.Rational(3, 2) * (T_ref + S) / (T + S))
+    constant = div_fv(sp.Integer(1))
+    cons = [rho, rho * u[0], rho * u[1], rho * u[2], p / (g - 1) + rho * sum(ui ** 2 for ui in u) / 2]
+    cons = [sp.lambdify((x, y, z), f, "numpy") for f in cons]
+
+    def at_nodes(f, Xn):
+        return f(Xn[:, 0], Xn[:, 1], Xn[:, 2]) * np.ones_like(Xn[:, 0])
+
+    errs = {}
+    for N in (5, 7):
+        m = box_mesh(4, N, lo=0.0, hi=2 * np.pi, deform="sinprod", rotate_seed=17)
+        kw = dict(gamma=g, R=Rg, Pr=Pr, visc_law=1, T_ref=T_ref, S_suth=S, nodes=nodes)
+        o1 = orc.Oracle(m, N, mu=mu0, **kw)
+        o0 = orc.Oracle(m, N, mu=0.0, **kw)
+        Xn = o1.node_coords()
+        U = np.stack([at_nodes(f, Xn) for f in cons], 1).reshape(o1.shape)
+        V = ((o1.time_derivative(U) - o0.time_derivative(U)) / mu0).reshape(o1.E, 5, -1)
+        scale = [np.abs(at_nodes(exact[v], Xn)).max() for v in range(5)]
+        errs[N] = [np.abs(V[:, v] - at_nodes(exact[v], Xn)).max() / scale[v] for v in range(1, 5)]
+        if N == 7:
+            assert max(errs[N]) < 0.02, errs[N]
+            off = [np.abs(V[:, v] - at_nodes(constant[v], Xn)).max() / scale[v] for v in range(1, 5)]
+            assert max(off) > 0.1, off
+    assert all(e7 < e5 / 3 for e5, e7 in zip(errs[5], errs[7])), errs
+
+
+@pytest.mark.parametrize("nodes", [0, 1])
 def test_integrals_match_closed_forms(orc, nodes):
     """The diagnostics of Sec. 4.2 for a smooth periodic state on a curved
     rotated mesh: the five conservation totals, E_k = 1/(2|Omega|) int rho |u|^2,
