@@ -476,6 +476,26 @@ def test_tangent_linear_matches_central_differences(orc):
     assert np.abs(fd - dR).max() < 1e-6 * np.abs(dR).max()
 
 
+@pytest.mark.parametrize("rk", [0, 1])
+def test_tangent_linear_of_rk_steps_matches_central_differences(orc, rk):
+    """The tangent of several steps of either 2N-storage scheme (the reference
+    of the GPU adjoint's dot-product tests) against central differences of the
+    primal steps; its primal part is the primal loop bit for bit."""
+    N, mu, dt, nsteps = 2, 0.05, 2e-3, 4
+    m = box_mesh(2, N, deform="sinprod", rotate_seed=33)
+    o = orc.Oracle(m, N, mu=mu, rk=rk)
+    U = random_state(m.n_elems, N, seed=4)
+    V = np.random.default_rng(6).normal(size=U.shape)
+    dmu = 0.3
+    UT, dUT = o.rk_steps_tl(U, V, dmu, 0.0, dt, nsteps)
+    np.testing.assert_array_equal(UT, o.rk_steps(U, 0.0, dt, nsteps))
+    h = 1e-6
+    op = orc.Oracle(m, N, mu=mu + h * dmu, rk=rk)
+    om = orc.Oracle(m, N, mu=mu - h * dmu, rk=rk)
+    fd = (op.rk_steps(U + h * V, 0.0, dt, nsteps) - om.rk_steps(U - h * V, 0.0, dt, nsteps)) / (2 * h)
+    assert np.abs(fd - dUT).max() < 1e-6 * np.abs(dUT).max()
+
+
 def test_bad_meshes_are_rejected(orc):
     m = box_mesh(2, 1, rotate_seed=3)
     bad = m.face_nbr.copy()
