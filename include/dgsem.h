@@ -210,7 +210,9 @@ dg_status dg_adjoint_solve(dg_ctx* ctx, const double* dU0, const double* dlamT, 
  * nsteps) states the first is t(nsteps, s) = r nsteps - C(s + r, s + 1), r the
  * least integer with C(s + r, s) >= nsteps (t = n (n - 1) / 2 for s = 1); the
  * second is nsteps.  DG_EINVAL for nsteps < 0, max_snapshots < 1 or a NULL
- * pointer.  Needs no GPU and no context. */
+ * pointer; DG_ENOMEM if the host cannot hold the schedule's interval stack
+ * (up to min(max_snapshots, nsteps) entries of 12 bytes).  Needs no GPU and
+ * no context. */
 dg_status dg_checkpoint_schedule(int32_t nsteps, int32_t max_snapshots, int64_t* host_counts2);
 
 /* Objective J = sum_nodes w_i w_j w_k J 1/2 rho |u|^2 (LGL quadrature of the

@@ -2,6 +2,7 @@
 // the adjoint of a whole time interval with binomial checkpointing, the
 // kinetic-energy objective, and the viscosity setter used for d/dmu checks.
 #include <cstdio>
+#include <new>
 #include <vector>
 
 #include "dg_internal.h"
@@ -273,7 +274,11 @@ dg_status dg_adjoint_solve(dg_ctx* ctx, const double* dU0, const double* dlamT, 
   X.dt = dt;
   X.s = s;
   const int nsnap = max_snapshots < nsteps ? max_snapshots : nsteps;
-  X.snap.assign(nsnap, nullptr);
+  try {
+    X.snap.assign(nsnap, nullptr);
+  } catch (const std::bad_alloc&) {
+    return afail(c, DG_ENOMEM, "dg_adjoint_solve: host memory for the snapshot table");
+  }
   for (int a = 0; a < nsnap; ++a) {
     cudaError_t e = cudaMalloc(&X.snap[a], bytes);
     if (e != cudaSuccess) {
@@ -283,7 +288,11 @@ dg_status dg_adjoint_solve(dg_ctx* ctx, const double* dU0, const double* dlamT, 
   }
   long long forward = 0, adjoints = 0;
   cudaError_t e = cudaMemcpyAsync(X.snap[0], dU0, bytes, cudaMemcpyDeviceToDevice, s);
-  st = e == cudaSuccess ? run_schedule(X, nsteps, nsnap, &forward, &adjoints) : afail(c, DG_ECUDA, "copy", e);
+  try {
+    st = e == cudaSuccess ? run_schedule(X, nsteps, nsnap, &forward, &adjoints) : afail(c, DG_ECUDA, "copy", e);
+  } catch (const std::bad_alloc&) {   // the schedule's interval stack
+    st = afail(c, DG_ENOMEM, "dg_adjoint_solve: host memory for the schedule");
+  }
   cudaError_t es = cudaStreamSynchronize(s);
   for (double* p : X.snap) cudaFree(p);
   if (st != DG_OK) return st;
@@ -298,7 +307,11 @@ dg_status dg_checkpoint_schedule(int32_t nsteps, int32_t max_snapshots, int64_t*
   long long forward = 0, adjoints = 0;
   if (nsteps > 0) {
     CountOnly X;
-    run_schedule(X, nsteps, nsnap, &forward, &adjoints);
+    try {
+      run_schedule(X, nsteps, nsnap, &forward, &adjoints);
+    } catch (const std::bad_alloc&) {
+      return DG_ENOMEM;
+    }
   }
   host_counts2[0] = forward;
   host_counts2[1] = adjoints;
