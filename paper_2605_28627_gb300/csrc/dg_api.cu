@@ -127,9 +127,7 @@ using namespace dg;
 
 struct dg_ctx : public dg::Ctx {};
 
-extern "C" {
-
-dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out) {
+static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out) {
   if (out) *out = nullptr;
   if (!mesh || !prm || !out) return fail(nullptr, DG_EINVAL, "dg_init: null argument");
   if (prm->N < 1 || prm->N > kMaxN) return fail(nullptr, DG_EUNSUPPORTED, "dg_init: N must be in 1..9");
@@ -298,6 +296,20 @@ dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx*
   c->err = "no error";
   *out = c;
   return DG_OK;
+}
+
+extern "C" {
+
+// Host containers (face lists, tables) may throw on a mesh too large for host
+// memory; no exception leaves the C ABI.
+dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out) {
+  try {
+    return init_impl(mesh, prm, device, out);
+  } catch (const std::bad_alloc&) {
+    if (out) *out = nullptr;
+    g_init_error = "dg_init: host memory exhausted";
+    return DG_ENOMEM;
+  }
 }
 
 dg_status dg_destroy(dg_ctx* c) {

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <new>
 #include <set>
 #include <string>
 #include <vector>
@@ -464,9 +465,8 @@ static dg_status autotune(dg_ensemble* e, cudaStream_t s) {
   return DG_OK;
 }
 
-extern "C" {
-
-dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune_cache_path, dg_ensemble** out) {
+static dg_status ensemble_create_impl(dg_ctx* const* members, int32_t n, const char* tune_cache_path,
+                                      dg_ensemble** out) {
   if (out) *out = nullptr;
   if (!members || n < 1 || !out) return DG_EINVAL;
   dg_ensemble* e = new dg_ensemble();
@@ -548,6 +548,19 @@ dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune
   e->cur_G.assign(n, nullptr);
   *out = e;
   return DG_OK;
+}
+
+extern "C" {
+
+// Host containers (tile tables, member lists) may throw when host memory runs
+// out; no exception leaves the C ABI.
+dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune_cache_path, dg_ensemble** out) {
+  try {
+    return ensemble_create_impl(members, n, tune_cache_path, out);
+  } catch (const std::bad_alloc&) {
+    if (out) *out = nullptr;
+    return DG_ENOMEM;
+  }
 }
 
 dg_status dg_ensemble_destroy(dg_ensemble* e) {
