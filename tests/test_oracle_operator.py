@@ -476,6 +476,32 @@ def test_tangent_linear_matches_central_differences(orc):
     assert np.abs(fd - dR).max() < 1e-6 * np.abs(dR).max()
 
 
+@pytest.mark.parametrize("N", [2, 3])
+def test_tangent_linear_at_llf_kinks_is_the_mean_derivative(orc, N):
+    """A state mirror-symmetric about the planes x = 0 and x = +-1 (normal
+    momentum reversed) puts both faces' LLF speeds max(|u.n| + c) at an exact
+    tie with a non-zero jump.  There the tangent-linear takes the mean of the
+    one-sided derivatives, which is what central differences converge to, at
+    the O(h) rate of a kink; a one-sided (primal-branch) derivative stays O(1)
+    away (about 5e-2 of max|dR| here)."""
+    K = 2
+    m = box_mesh(K, 1)
+    o = orc.Oracle(m, N, mu=0.02)
+    U = random_state(m.n_elems, N, seed=3)
+    for e in range(m.n_elems):
+        if e % K == 1:
+            Vm = U[e - 1][:, :, :, ::-1].copy()
+            Vm[1] = -Vm[1]
+            U[e] = Vm
+    V = np.random.default_rng(1).normal(size=U.shape)
+    _, dR = o.time_derivative_tl(U, V, 0.0)
+    err = []
+    for h in (1e-6, 1e-7):
+        fd = (o.time_derivative(U + h * V) - o.time_derivative(U - h * V)) / (2 * h)
+        err.append(np.abs(fd - dR).max() / np.abs(dR).max())
+    assert err[0] < 2e-6 and err[1] < err[0] / 5, err
+
+
 @pytest.mark.parametrize("rk", [0, 1])
 def test_tangent_linear_of_rk_steps_matches_central_differences(orc, rk):
     """The tangent of several steps of either 2N-storage scheme (the reference
