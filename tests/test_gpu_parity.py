@@ -400,3 +400,36 @@ def test_bench_workload_properties(orc, dg):
     rho = Um[:, 0]
     assert bool(torch.isfinite(Um).all()) and float(rho.min()) > 1.89 and float(rho.max()) < 2.11
     sm.close()
+
+
+@pytest.mark.parametrize("N", [2, 5])
+def test_max_dt_matches_the_stated_formula(orc, dg, N):
+    """dg_max_dt on LGL nodes against the step it states (Sec. 3.1, CFL and
+    viscous limits): dt = min(cfl h / max sum_d lambda_d, dfl h^2 / max
+    mu_eff sum_d |Ja^d|^2 / J^2), h = 2/(2N+1), lambda_d = (|u . Ja^d| +
+    c |Ja^d|)/J, mu_eff = max(4/3, gamma/Pr) mu / rho, evaluated here from the
+    oracle's geometry and the state; both limits take their turn."""
+    gamma, Pr, mu = 1.4, 0.72, 0.05
+    mesh = box_mesh(3, N, deform="sinprod", rotate_seed=41)
+    o, s = _pair(orc, dg, mesh, N, gamma=gamma, Pr=Pr, mu=mu)
+    U = random_state(mesh.n_elems, N, seed=8)
+    _, Ja, J = o.geometry()
+    q = U.reshape(mesh.n_elems, 5, -1)
+    rho = q[:, 0]
+    u = q[:, 1:4] / rho[:, None]
+    p = (gamma - 1) * (q[:, 4] - 0.5 * rho * (u ** 2).sum(1))
+    c = np.sqrt(gamma * p / rho)
+    lam = sum((np.abs(np.einsum("elp,elp->ep", u, Ja[:, d])) + c * np.linalg.norm(Ja[:, d], axis=1)) / J
+              for d in range(3))
+    visc = max(4.0 / 3.0, gamma / Pr) * mu / rho * sum((Ja[:, d] ** 2).sum(1) for d in range(3)) / J ** 2
+    h = 2.0 / (2 * N + 1)
+    Ud = _cuda(U)
+    limits = set()
+    for cfl, dfl in ((0.9, 5.0), (0.9, 1e-3)):
+        conv, vis = cfl * h / lam.max(), dfl * h * h / visc.max()
+        limits.add(conv < vis)
+        ref = min(conv, vis)
+        got = s.max_dt(Ud, cfl=cfl, dfl=dfl)
+        assert abs(got - ref) <= 1e-11 * ref, (got, ref)
+    assert limits == {True, False}
+    s.close()
