@@ -37,8 +37,19 @@
 #include <vector>
 #include <algorithm>
 #include <type_traits>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace orc {
+
+// The element and face loops of the FP64 operator may run on several host
+// threads when this file is built with OpenMP (the timed CPU baseline).  Each
+// iteration writes only its own element's (or master face's) values and
+// evaluates them with exactly the serial arithmetic, so the result is the
+// serial result bit for bit.  The dual-number and counting scalars always run
+// serially (the counter is a global).
+template <class T> constexpr bool kParallel = std::is_same<T, double>::value;
 
 // ---------------------------------------------------------------------------
 // Forward-mode dual number (value, one tangent direction).
@@ -598,6 +609,7 @@ static void lifting(const Ctx& c, const T* phi, T* G) {
   int n = c.n, P = c.P, E = c.E, N = c.N;
   const std::vector<double>& D = c.b.D;
   double wend = c.b.w[0];
+#pragma omp parallel for schedule(dynamic, 4) if (kParallel<T>)
   for (int e = 0; e < E; ++e) {
     for (int k = 0; k < n; ++k)
       for (int j = 0; j < n; ++j)
@@ -725,6 +737,7 @@ static void rhs(const Ctx& c, const T* U, T* Ut, double t, T mu) {
   double wend = c.b.w[0];
   std::vector<Prim<T>> W((size_t)E * P);
   std::vector<T> phi((size_t)E * 4 * P);       // [e][4][P]: u, v, w, T
+#pragma omp parallel for schedule(static) if (kParallel<T>)
   for (int e = 0; e < E; ++e)
     for (int id = 0; id < P; ++id) {
       T q[5];
@@ -747,6 +760,7 @@ static void rhs(const Ctx& c, const T* U, T* Ut, double t, T mu) {
   };
   // --- face fluxes on master faces: F* = (F_adv - F_visc) sJ, master orientation
   std::vector<T> Fs((size_t)c.nfaces * 5 * nn);
+#pragma omp parallel for schedule(dynamic, 4) if (kParallel<T>)
   for (int e = 0; e < E; ++e)
     for (int f = 0; f < 6; ++f) {
       if (!c.master[e * 6 + f]) continue;
@@ -777,6 +791,7 @@ static void rhs(const Ctx& c, const T* U, T* Ut, double t, T mu) {
         }
     }
   // --- volume integral, surface integral, Jacobian
+#pragma omp parallel for schedule(dynamic, 2) if (kParallel<T>)
   for (int e = 0; e < E; ++e) {
     std::vector<T> acc((size_t)5 * P, T(0.0));
     volume_advective(c, e, &W[(size_t)e * P], acc.data());
@@ -1341,6 +1356,18 @@ void* orc_create(int N, int n_elems, int ngeo, const double* xgeo, const int* fa
 }
 
 void orc_destroy(void* h) { delete (Ctx*)h; }
+
+// Host threads of the FP64 operator's loops (1 unless built with OpenMP):
+// sets the count if n > 0 and returns the count in effect.
+int orc_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 // Test hook: select the volume two-point flux (0: Chandrashekar, 1: central).
 void orc_set_vol_flux(void* h, int kind) { ((Ctx*)h)->prm.vol_flux = kind; }

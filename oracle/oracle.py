@@ -14,35 +14,47 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dgsem_oracle.cpp")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
-_lib = None
+_LIB_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
+_libs = {}
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 
+# -O3, no machine-specific flags (the same source builds on x86-64 and on
+# aarch64).  g++'s default contraction of a*b + c into fused multiply-adds
+# applies where the target has them (aarch64, not baseline x86-64), so the
+# last bits of the two machines' results may differ.
+_FLAGS = ["-O3", "-std=c++17", "-shared", "-fPIC"]
 
-def lib_path() -> str:
-    return _LIB
+
+def lib_path(omp: bool = False) -> str:
+    return _LIB_OMP if omp else _LIB
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (plain -O2, no vectorisation flags)."""
+    """Compile the oracle with g++: the serial library, and the same source
+    with OpenMP over the operator's element and face loops (the timed CPU
+    baseline on all host cores; bit-identical results)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
-        os.replace(tmp, _LIB)
+    for lib, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(_SRC),
+                                                                          os.path.getmtime(__file__)):
+            tmp = lib + ".tmp%d" % os.getpid()
+            subprocess.check_call(["g++", *_FLAGS, *extra, "-o", tmp, _SRC])
+            os.replace(tmp, lib)
     return _LIB
 
 
-def _load():
-    global _lib
-    if _lib is not None:
-        return _lib
+def _load(omp: bool = False):
+    if omp in _libs:
+        return _libs[omp]
     build()
-    L = C.CDLL(_LIB)
+    L = C.CDLL(lib_path(omp))
     L.orc_create.restype = C.c_void_p
     L.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _ip, _dp, C.c_int, C.c_int, C.c_char_p, C.c_int]
     L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_threads.argtypes = [C.c_int]
+    L.orc_threads.restype = C.c_int
     L.orc_nfaces.argtypes = [C.c_void_p]
     L.orc_nfaces.restype = C.c_int
     L.orc_basis.argtypes = [C.c_int, _dp, _dp, _dp]
@@ -67,8 +79,14 @@ def _load():
     L.orc_volume_term.argtypes = [C.c_void_p, _dp, _dp]
     L.orc_count_ops.argtypes = [C.c_void_p, _dp, C.c_double, _dp]
     L.orc_count_ec_flux_ops.argtypes = [_dp, _dp, _dp, _dp, _dp]
-    _lib = L
+    _libs[omp] = L
     return L
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the OpenMP build's operator loops (n > 0 sets the
+    count); returns the count in effect."""
+    return int(_load(omp=True).orc_threads(int(n)))
 
 
 def gauss_basis(N: int):
@@ -155,12 +173,15 @@ class Oracle:
     nodes: 0 = LGL nodes with the split form, 1 = Legendre-Gauss nodes with the
     standard weak form (no tangent-linear).
     rk: 0 = LSERK4-5 (Carpenter & Kennedy), 1 = RK4-14 (Niegemann et al.).
+    parallel: use the OpenMP build (the FP64 operator's element and face loops
+    on the host threads set by ``set_threads``; the same results bit for bit).
     """
 
     def __init__(self, mesh, N: int, gamma=1.4, R=1.0, Pr=0.72, mu=0.0,
                  surf_flux: int = 0, source: int = 0, mms_amp: float = 0.1,
-                 visc_law: int = 0, T_ref: float = 1.0, S_suth: float = 0.0, nodes: int = 0, rk: int = 0):
-        L = _load()
+                 visc_law: int = 0, T_ref: float = 1.0, S_suth: float = 0.0, nodes: int = 0, rk: int = 0,
+                 parallel: bool = False):
+        L = _load(omp=parallel)
         self.N, self.n, self.P = N, N + 1, (N + 1) ** 3
         self.E = int(mesh.xgeo.shape[0])
         self.gamma, self.R, self.Pr, self.mu = gamma, R, Pr, mu
