@@ -133,8 +133,11 @@ dg_status dg_time_derivative(dg_ctx* ctx, const double* dU, double* dUt, double 
  * Sec. 3.1) in place: per stage s,
  *   G <- A_s G + dt R(U, t + c_s dt);  U <- U + B_s G,
  * with G (device, dg_state_len doubles, caller-owned scratch) zeroed at the
- * start of every step.  The sequence of launches is captured once per
- * (dU, dG, nsteps) into a CUDA graph and replayed. */
+ * start of every step.  Both operations run in FP64 in either precision; with
+ * DG_FP32OP the register holds G/dt (G/dt <- A_s G/dt + R; U <- U + (B_s dt)
+ * G/dt), which makes both of them fused multiply-adds.  The sequence of
+ * launches is captured once per (dU, dG, nsteps) into a CUDA graph and
+ * replayed. */
 dg_status dg_rk_step(dg_ctx* ctx, double* dU, double* dG, double t, double dt, int32_t nsteps,
                      dg_stream stream);
 
@@ -280,14 +283,34 @@ dg_status dg_probe_peaks(int device, double* host_out2);
  * stream.  DG_EINVAL for n < 0 or null pointers with n > 0. */
 dg_status dg_check_conversions(const double* d_x, int32_t n, float* d_f, double* d_d, dg_stream stream);
 
+/* Check of the reciprocals the operator kernels use instead of divisions (no
+ * counterpart in the paper).  For the n device values d_x:
+ *   d_d[0..n)   the FP64 operator's 1/x: hardware approximation
+ *               (rcp.approx.ftz.f64) refined by one cubic Newton-Raphson step,
+ *               within 1 ulp of the correctly rounded 1/x;
+ *   d_d[n..2n)  the same refined by one quadratic step, relative error below
+ *               2^-38 (used where the error is damped, e.g. 1/(rho_a + rho_b)
+ *               of the log-mean series);
+ *   d_d[2n..3n) the adjoint kernels' 1/x (the cubic form);
+ *   d_f[0..n), d_f[n..2n)  the FP32 operator's 1/x of x rounded to FP32 (the
+ *               hardware approximation, within 1 FP32 ulp).
+ * Valid for positive normal x with a normal reciprocal (the operators' densities,
+ * pressures and their sums): the .ftz forms flush subnormals, so a subnormal
+ * 1/x becomes 0 and a zero or subnormal x gives a non-finite result.  All
+ * pointers are caller-owned device memory (d_d 3n doubles, d_f 2n floats).
+ * Synchronises the stream.  DG_EINVAL for n < 0 or null pointers with n > 0. */
+dg_status dg_check_reciprocals(const double* d_x, int32_t n, double* d_d, float* d_f, dg_stream stream);
+
 /* Conservation totals sum_nodes w_i w_j w_k J q_v (v = rho, rho u, rho v,
  * rho w, rho E), the first five values of dg_integrals, for callers that may
  * not allocate device memory while they run: a host framework that owns every
  * device buffer and only lends inputs and outputs to foreign code, or an
  * application that keeps the allocator out of its time loop.  The paper has
  * no counterpart; this entry exists for such callers.
- *   dU: device state [n_elems][5][P]; dJ: device Jacobian [n_elems][P] (e.g.
- *   from dg_geometry); N: degree 1..9; dOut5: device, receives 5 doubles.
+ *   dU: device state [n_elems][5][P]; dJ: device Jacobian [n_elems][P] at the
+ *   context's nodes (dg_geometry); N: degree 1..9; nodes: DG_NODES_LGL or
+ *   DG_NODES_LG, the node set of the context the state belongs to (its
+ *   quadrature weights are used); dOut5: device, receives 5 doubles.
  * It calls no cudaMalloc, cudaFree or allocating library routine.  Its only
  * scratch is a fixed device array of n_elems <= 131072 rows of 5 doubles
  * (5 MiB) that every GPU loading the library holds until the process exits;
@@ -295,10 +318,12 @@ dg_status dg_check_conversions(const double* d_x, int32_t n, float* d_f, double*
  * calls on a device and keeps the last call's contents, so calls that
  * overlap on the GPU (other streams, other threads) race.  The first call on
  * each device looks up the array's device address with that device current
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Runs on the current device and stream; does not synchronise. */
-dg_status dg_conserved_totals_noalloc(const double* dU, const double* dJ, int32_t N, int32_t n_elems,
-                                      double* dOut5, dg_stream stream);
+ * (cudaGetSymbolAddress) and keeps it; make that first call before any stream
+ * capture.  The kept address does not survive cudaDeviceReset (nor does any
+ * context of this library).  Runs on the current device; `stream` must be a
+ * stream of that device (DG_EINVAL otherwise).  Does not synchronise. */
+dg_status dg_conserved_totals_noalloc(const double* dU, const double* dJ, int32_t N, int32_t nodes,
+                                      int32_t n_elems, double* dOut5, dg_stream stream);
 
 /* Human-readable description of the last error on ctx (or of the last failed
  * dg_init when ctx is NULL).  Never NULL. */

@@ -35,7 +35,7 @@ EXPORTS = ["dg_init", "dg_destroy", "dg_state_len", "dg_time_derivative", "dg_rk
            "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
            "dg_ensemble_step", "dg_ensemble_plan", "dg_ensemble_last_error", "dg_time_derivative_vjp",
            "dg_adjoint_step", "dg_adjoint_solve", "dg_checkpoint_schedule", "dg_kinetic_energy", "dg_set_viscosity",
-           "dg_check_conversions", "dg_last_error"]
+           "dg_check_conversions", "dg_check_reciprocals", "dg_last_error"]
 
 
 class DGError(RuntimeError):
@@ -86,7 +86,8 @@ def load(build_if_missing: bool = True):
     L.dg_profile_stages.argtypes = [vp, vp, vp, f64, i32, C.POINTER(C.c_float), vp]
     L.dg_probe_peaks.argtypes = [C.c_int, dp]
     L.dg_check_conversions.argtypes = [vp, i32, vp, vp, vp]
-    L.dg_conserved_totals_noalloc.argtypes = [vp, vp, i32, i32, vp, vp]
+    L.dg_check_reciprocals.argtypes = [vp, i32, vp, vp, vp]
+    L.dg_conserved_totals_noalloc.argtypes = [vp, vp, i32, i32, i32, vp, vp]
     L.dg_ensemble_create.argtypes = [C.POINTER(vp), i32, C.c_char_p, C.POINTER(vp)]
     L.dg_ensemble_destroy.argtypes = [vp]
     L.dg_ensemble_step.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), dp, dp, i32, vp]
@@ -106,7 +107,7 @@ def load(build_if_missing: bool = True):
                  "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
                  "dg_ensemble_step", "dg_ensemble_plan", "dg_time_derivative_vjp", "dg_adjoint_step",
                  "dg_adjoint_solve", "dg_checkpoint_schedule", "dg_kinetic_energy", "dg_set_viscosity",
-                 "dg_check_conversions"):
+                 "dg_check_conversions", "dg_check_reciprocals"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -344,15 +345,32 @@ def check_conversions(x, stream=None):
     return f[:n], f[n:], d[:n], d[n:]
 
 
-def conserved_totals_noalloc(U, J, N: int, out=None, stream=None):
+def check_reciprocals(x, stream=None):
+    """The operator kernels' reciprocals of the positive device float64
+    tensor x: returns (cubic FP64, quadratic FP64, adjoint FP64, FP32 of x
+    rounded to FP32, FP32 quadratic form) as device tensors."""
+    import torch
+    L = load()
+    x = x.contiguous()
+    n = x.numel()
+    d = torch.empty(3 * n, dtype=torch.float64, device=x.device)
+    f = torch.empty(2 * n, dtype=torch.float32, device=x.device)
+    st = L.dg_check_reciprocals(_ptr(x), n, _ptr(d), _ptr(f), _stream_handle(stream))
+    if st != DG_OK:
+        raise DGError(st, "dg_check_reciprocals failed")
+    return d[:n], d[n:2 * n], d[2 * n:], f[:n], f[n:]
+
+
+def conserved_totals_noalloc(U, J, N: int, out=None, stream=None, nodes: int = NODES_LGL):
     """Conservation totals of U (device float64) with Jacobian J (device,
-    [E, P]) through the allocation-free entry point; returns the device
-    tensor `out` (5 doubles)."""
+    [E, P]) at the nodes of the node set `nodes` through the allocation-free
+    entry point; returns the device tensor `out` (5 doubles)."""
     import torch
     L = load()
     if out is None:
         out = torch.empty(5, dtype=torch.float64, device=U.device)
-    st = L.dg_conserved_totals_noalloc(_ptr(U), _ptr(J), int(N), int(J.shape[0]), _ptr(out), _stream_handle(stream))
+    st = L.dg_conserved_totals_noalloc(_ptr(U), _ptr(J), int(N), int(nodes), int(J.shape[0]), _ptr(out),
+                                       _stream_handle(stream))
     if st != DG_OK:
         raise DGError(st, "dg_conserved_totals_noalloc rejected its arguments")
     return out

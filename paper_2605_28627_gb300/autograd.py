@@ -16,20 +16,31 @@ import torch
 class _RKSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, U0, mu, solver, t0, dt, nsteps, max_snapshots):
-        solver.set_viscosity(float(mu))
+        mu_val = float(mu)
+        solver.set_viscosity(mu_val)
         U = U0.detach().clone()
         G = torch.empty_like(U)
         solver.rk_step(U, G, t0, dt, nsteps)
         ctx.save_for_backward(U0.detach().clone())
         ctx.solver, ctx.t0, ctx.dt, ctx.nsteps, ctx.snap = solver, t0, dt, nsteps, max_snapshots
         ctx.mu_shape = mu.shape
+        ctx.mu = mu_val
         return U
 
     @staticmethod
     def backward(ctx, gU):
         (U0,) = ctx.saved_tensors
         dmu = torch.zeros(1, dtype=torch.float64, device=U0.device)
-        lam0, _ = ctx.solver.adjoint_solve(U0, gU.contiguous(), ctx.t0, ctx.dt, ctx.nsteps, ctx.snap, dJdmu=dmu)
+        # The adjoint recomputes the forward steps, so it must run with the
+        # viscosity of this forward call, not whatever the solver holds now
+        # (another rk_solve on the same solver may have changed it).
+        solver = ctx.solver
+        mu_now = solver.mu
+        solver.set_viscosity(ctx.mu)
+        try:
+            lam0, _ = solver.adjoint_solve(U0, gU.contiguous(), ctx.t0, ctx.dt, ctx.nsteps, ctx.snap, dJdmu=dmu)
+        finally:
+            solver.set_viscosity(mu_now)
         return lam0, dmu.reshape(ctx.mu_shape), None, None, None, None, None
 
 

@@ -127,7 +127,22 @@ using namespace dg;
 
 struct dg_ctx : public dg::Ctx {};
 
-static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out) {
+// Set-up temporaries of dg_init (mesh samples on the device, the Jacobian
+// flag, the set-up stream), freed on every exit, exceptions included.
+struct InitScratch {
+  cudaStream_t s = nullptr;
+  double* d_xgeo = nullptr;
+  int* d_bad = nullptr;
+  ~InitScratch() {
+    if (d_xgeo) cudaFree(d_xgeo);
+    if (d_bad) cudaFree(d_bad);
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
+// `c` holds the context under construction, so that the caller can free it
+// if a host allocation throws half-way.
+static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out, dg_ctx*& c) {
   if (out) *out = nullptr;
   if (!mesh || !prm || !out) return fail(nullptr, DG_EINVAL, "dg_init: null argument");
   if (prm->N < 1 || prm->N > kMaxN) return fail(nullptr, DG_EUNSUPPORTED, "dg_init: N must be in 1..9");
@@ -162,12 +177,13 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
       if (b[0] != e || b[1] != f) return fail(nullptr, DG_EMESH, "dg_init: face connectivity not reciprocal");
       if (r[0] == e && r[1] == f) return fail(nullptr, DG_EMESH, "dg_init: face is its own neighbour");
     }
-  dg_ctx* c = new (std::nothrow) dg_ctx();
+  c = new (std::nothrow) dg_ctx();
   if (!c) return fail(nullptr, DG_ENOMEM, "dg_init: host allocation failed");
   auto bail = [&](dg_status st) {
     g_init_error = c->err;
     release(c);
     delete c;
+    c = nullptr;
     return st;
   };
   c->device = device;
@@ -241,24 +257,28 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
     fail(c, DG_ENOMEM, "dg_init: pinned host allocation failed");
     return bail(DG_ENOMEM);
   }
-  cudaStream_t s;
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-    fail(c, DG_ECUDA, "dg_init: stream");
-    return bail(DG_ECUDA);
-  }
-  const int minmask = 1 << 8;
-  double* d_xgeo = nullptr;
-  int* d_bad = nullptr;
-  const size_t m3 = (size_t)(mesh->ngeo + 1) * (mesh->ngeo + 1) * (mesh->ngeo + 1);
-  cudaError_t err = cudaMalloc(&d_xgeo, sizeof(double) * E * 3 * m3);
-  if (err == cudaSuccess) err = cudaMalloc(&d_bad, sizeof(int));
-  if (err == cudaSuccess) err = cudaMemcpyAsync(d_xgeo, mesh->xgeo, sizeof(double) * E * 3 * m3, cudaMemcpyHostToDevice, s);
-  if (err == cudaSuccess) err = cudaMemsetAsync(d_bad, 0, sizeof(int), s);
-  if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_D, c->D.data(), sizeof(double) * NN, cudaMemcpyHostToDevice, s);
   std::vector<double> gtab;
   if (prm->nodes == DG_NODES_LG) {
     gauss_table(c->N, c->x, gtab);
     c->dt_factor = gauss_dt_factor(c->N, c->x, c->w, c->D, gtab);
+  }
+  InitScratch tmp;
+  if (cudaStreamCreateWithFlags(&tmp.s, cudaStreamNonBlocking) != cudaSuccess) {
+    tmp.s = nullptr;
+    fail(c, DG_ECUDA, "dg_init: stream");
+    return bail(DG_ECUDA);
+  }
+  cudaStream_t s = tmp.s;
+  const int minmask = 1 << 8;
+  const size_t m3 = (size_t)(mesh->ngeo + 1) * (mesh->ngeo + 1) * (mesh->ngeo + 1);
+  cudaError_t err = cudaMalloc(&tmp.d_xgeo, sizeof(double) * E * 3 * m3);
+  if (err == cudaSuccess) err = cudaMalloc(&tmp.d_bad, sizeof(int));
+  double* d_xgeo = tmp.d_xgeo;
+  int* d_bad = tmp.d_bad;
+  if (err == cudaSuccess) err = cudaMemcpyAsync(d_xgeo, mesh->xgeo, sizeof(double) * E * 3 * m3, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(d_bad, 0, sizeof(int), s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_D, c->D.data(), sizeof(double) * NN, cudaMemcpyHostToDevice, s);
+  if (prm->nodes == DG_NODES_LG) {
     if (err == cudaSuccess)
       err = cudaMemcpyAsync(c->d_lgb, gtab.data(), sizeof(double) * gtab.size(), cudaMemcpyHostToDevice, s);
     // quadrature weights of the Gauss nodes for the integrals
@@ -281,10 +301,8 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   }
   int bad = 0;
-  if (err == cudaSuccess) err = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
-  if (d_xgeo) cudaFree(d_xgeo);
-  if (d_bad) cudaFree(d_bad);
-  cudaStreamDestroy(s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) {
     fail(c, err == cudaErrorMemoryAllocation ? DG_ENOMEM : DG_ECUDA, "dg_init: geometry", err);
     return bail(err == cudaErrorMemoryAllocation ? DG_ENOMEM : DG_ECUDA);
@@ -303,9 +321,14 @@ extern "C" {
 // Host containers (face lists, tables) may throw on a mesh too large for host
 // memory; no exception leaves the C ABI.
 dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out) {
+  dg_ctx* c = nullptr;
   try {
-    return init_impl(mesh, prm, device, out);
+    return init_impl(mesh, prm, device, out, c);
   } catch (const std::bad_alloc&) {
+    if (c) {                // the half-built context and its device buffers
+      release(c);
+      delete c;
+    }
     if (out) *out = nullptr;
     g_init_error = "dg_init: host memory exhausted";
     return DG_ENOMEM;

@@ -465,17 +465,25 @@ static dg_status autotune(dg_ensemble* e, cudaStream_t s) {
   return DG_OK;
 }
 
+// `e` holds the ensemble under construction, so that the caller can free it
+// if a host allocation throws half-way.
 static dg_status ensemble_create_impl(dg_ctx* const* members, int32_t n, const char* tune_cache_path,
-                                      dg_ensemble** out) {
+                                      dg_ensemble** out, dg_ensemble*& e) {
   if (out) *out = nullptr;
   if (!members || n < 1 || !out) return DG_EINVAL;
-  dg_ensemble* e = new dg_ensemble();
-  auto bail = [&](dg_status st) {
+  e = new dg_ensemble();
+  auto bail = [&](dg_status st) {   // frees the device buffers the groups hold so far
     dg_ensemble_destroy(e);
+    e = nullptr;
+    return st;
+  };
+  auto drop = [&](dg_status st) {   // before any device allocation
+    delete e;
+    e = nullptr;
     return st;
   };
   Ctx* c0 = reinterpret_cast<Ctx*>(members[0]);
-  if (!c0) { delete e; return DG_EINVAL; }
+  if (!c0) return drop(DG_EINVAL);
   e->device = c0->device;
   e->precision = c0->prm.precision;
   e->cache_path = tune_cache_path ? tune_cache_path : "";
@@ -483,19 +491,15 @@ static dg_status ensemble_create_impl(dg_ctx* const* members, int32_t n, const c
   for (int r = 0; r < n; ++r) {
     Ctx* c = reinterpret_cast<Ctx*>(members[r]);
     // a context twice would have two members share its work buffers
-    if (!c || c->device != e->device || c->prm.precision != e->precision || !seen.insert(c).second) {
-      delete e;
-      return DG_EINVAL;
-    }
-    if (c->prm.nodes != DG_NODES_LGL || c->prm.rk_scheme != DG_RK45) {   // LGL split form, LSERK4-5
-      delete e;
-      return DG_EUNSUPPORTED;
-    }
+    if (!c || c->device != e->device || c->prm.precision != e->precision || !seen.insert(c).second)
+      return drop(DG_EINVAL);
+    if (c->prm.nodes != DG_NODES_LGL || c->prm.rk_scheme != DG_RK45)   // LGL split form, LSERK4-5
+      return drop(DG_EUNSUPPORTED);
     e->members.push_back(c);
   }
-  if (cudaSetDevice(e->device) != cudaSuccess) { delete e; return DG_ECUDA; }
+  if (cudaSetDevice(e->device) != cudaSuccess) return drop(DG_ECUDA);
   cudaDeviceProp prop;
-  if (cudaGetDeviceProperties(&prop, e->device) != cudaSuccess) { delete e; return DG_ECUDA; }
+  if (cudaGetDeviceProperties(&prop, e->device) != cudaSuccess) return drop(DG_ECUDA);
   e->gpu_name = prop.name;
   e->sms = prop.multiProcessorCount;
   std::map<int, std::vector<int>> byN;
@@ -555,9 +559,11 @@ extern "C" {
 // Host containers (tile tables, member lists) may throw when host memory runs
 // out; no exception leaves the C ABI.
 dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune_cache_path, dg_ensemble** out) {
+  dg_ensemble* e = nullptr;
   try {
-    return ensemble_create_impl(members, n, tune_cache_path, out);
+    return ensemble_create_impl(members, n, tune_cache_path, out, e);
   } catch (const std::bad_alloc&) {
+    if (e) dg_ensemble_destroy(e);   // the half-built ensemble and its device buffers
     if (out) *out = nullptr;
     return DG_ENOMEM;
   }

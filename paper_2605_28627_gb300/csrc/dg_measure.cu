@@ -1,6 +1,9 @@
 // Measurement helpers: per-kernel event timing of an LSERK stage and an
-// arithmetic-throughput probe (FP64 DFMA and FP32 FFMA chains).
-#include "dg_physics.cuh"
+// arithmetic-throughput probe (FP64 DFMA and FP32 FFMA chains); checks of the
+// operator kernels' conversions and reciprocals against the hardware and IEEE
+// division.
+#include "dg_adjoint_fn.cuh"
+#include "dg_stage.cuh"
 
 namespace dg {
 
@@ -52,9 +55,33 @@ __global__ void k_convert_check(const double* __restrict__ x, int n, float* __re
   }
 }
 
+// The reciprocals of the operator kernels next to each other: the FP64
+// operators' cubic and quadratic refinements, the adjoint's, and the FP32
+// operators' approximation (of x rounded to FP32).
+__global__ void k_rcp_check(const double* __restrict__ x, int n, double* __restrict__ d, float* __restrict__ f) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const double v = x[t];
+    d[t] = rcp_op(v);
+    d[n + t] = rcp_op_q(v);
+    d[2 * n + t] = adj_rcp(v);
+    const float vf = __double2float_rn(v);
+    f[t] = rcp_op(vf);
+    f[n + t] = rcp_op_q(vf);
+  }
+}
+
 }  // namespace dg
 
 using namespace dg;
+
+extern "C" dg_status dg_check_reciprocals(const double* d_x, int32_t n, double* d_d, float* d_f, dg_stream stream) {
+  if (n < 0 || (n > 0 && (!d_x || !d_d || !d_f))) return DG_EINVAL;
+  if (n == 0) return DG_OK;
+  const int blocks = (n + 255) / 256;
+  k_rcp_check<<<blocks < 152 * 8 ? blocks : 152 * 8, 256, 0, (cudaStream_t)stream>>>(d_x, n, d_d, d_f);
+  if (cudaGetLastError() != cudaSuccess) return DG_ECUDA;
+  return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? DG_OK : DG_ECUDA;
+}
 
 extern "C" dg_status dg_check_conversions(const double* d_x, int32_t n, float* d_f, double* d_d, dg_stream stream) {
   if (n < 0 || (n > 0 && (!d_x || !d_f || !d_d))) return DG_EINVAL;

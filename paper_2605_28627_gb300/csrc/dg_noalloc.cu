@@ -100,6 +100,38 @@ static void lgl_weights_fixed(int N, double* w) {
   }
 }
 
+// Legendre-Gauss weights 2 / ((1 - x_j^2) P_n'(x_j)^2), n = N + 1, at the
+// zeros x_j of P_n, on fixed-size storage: Newton's method from the
+// asymptotic start cos(pi (j + 3/4) / (n + 1/2)), symmetric partner mirrored.
+static void gauss_weights_fixed(int N, double* w) {
+  const int n = N + 1;
+  for (int j = 0; j < (n + 1) / 2; ++j) {
+    double t = std::cos(M_PI * (j + 0.75) / (n + 0.5)), dP = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      // P_n(t) by the three-term recurrence, P_n' from (1 - t^2) P_n' = n (P_{n-1} - t P_n)
+      double a = 1.0, b = t;
+      for (int k = 1; k < n; ++k) {
+        const double c = ((2.0 * k + 1.0) * t * b - k * a) / (k + 1.0);
+        a = b; b = c;
+      }
+      dP = n * (a - t * b) / (1.0 - t * t);
+      const double step = b / dP;
+      t -= step;
+      if (std::fabs(step) < 1e-17) break;
+    }
+    // weight from P_n' at the converged node
+    double a = 1.0, b = t;
+    for (int k = 1; k < n; ++k) {
+      const double c = ((2.0 * k + 1.0) * t * b - k * a) / (k + 1.0);
+      a = b; b = c;
+    }
+    dP = n * (a - t * b) / (1.0 - t * t);
+    const double wj = 2.0 / ((1.0 - t * t) * dP * dP);
+    w[j] = wj;
+    w[n - 1 - j] = wj;
+  }
+}
+
 // Device address of the scratch array, looked up once per device with that
 // device current (in host code the array's name is only a host-side stand-in).
 static std::mutex g_scratch_mu;
@@ -122,18 +154,27 @@ static cudaError_t scratch_address(int device, double** out) {
 
 using namespace dg;
 
-extern "C" dg_status dg_conserved_totals_noalloc(const double* dU, const double* dJ, int32_t N, int32_t n_elems,
-                                                 double* dOut5, dg_stream stream) {
+extern "C" dg_status dg_conserved_totals_noalloc(const double* dU, const double* dJ, int32_t N, int32_t nodes,
+                                                 int32_t n_elems, double* dOut5, dg_stream stream) {
   if (!dU || !dJ || !dOut5) return DG_EINVAL;
   if (N < 1 || N > kMaxN) return DG_EUNSUPPORTED;
+  if (nodes != DG_NODES_LGL && nodes != DG_NODES_LG) return DG_EINVAL;
   if (n_elems < 1 || n_elems > kNoAllocMaxElems) return DG_EINVAL;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return DG_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the scratch address is the current device's: a stream of another device
+  // would run the kernels there on the wrong array
+  if (s) {
+    int sdev = -1;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) return DG_ECUDA;
+    if (sdev != device) return DG_EINVAL;
+  }
   double* scratch = nullptr;
   if (scratch_address(device, &scratch) != cudaSuccess) return DG_ECUDA;
   Weights wt{};
-  lgl_weights_fixed(N, wt.w);
-  cudaStream_t s = (cudaStream_t)stream;
+  if (nodes == DG_NODES_LG) gauss_weights_fixed(N, wt.w);
+  else lgl_weights_fixed(N, wt.w);
   const int threads = 256, warps_per_block = threads / 32;
   const int blocks = (n_elems + warps_per_block - 1) / warps_per_block;
   k_totals_elem<<<blocks, threads, 0, s>>>(dU, dJ, wt, N + 1, n_elems, scratch);

@@ -96,6 +96,10 @@ constexpr size_t volume_smem_bytes() {
 // 1/x: hardware reciprocal approximation refined by one cubic Newton-Raphson
 // step y <- y (1 + e + e^2), e = 1 - x y, which cubes the relative error
 // (2^-20 -> below 1 ulp).  In FP32 the approximation alone is within 1 ulp.
+// The .ftz forms flush subnormals: valid for positive normal x whose
+// reciprocal is normal (a subnormal 1/x becomes 0, a zero or subnormal x
+// gives a non-finite result), which covers the operators' densities,
+// pressures and their sums.  dg_check_reciprocals tests these bounds.
 __device__ __forceinline__ double rcp_op(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
@@ -491,9 +495,11 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
   R* sDl = tile0 + EPB * PER_ELEM + le * P;   // FP32 only: rho (p - p_ref) / p
   const int e = blk * EPB + le;
   const bool active = e < E;
-  __shared__ double s_tc[2];          // sin, cos of pi t (manufactured source)
-  if (threadIdx.x == 0 && g.source == DG_SOURCE_MMS)
-    sincospi(a.clock[0] + a.c_stage * a.clock[1], &s_tc[0], &s_tc[1]);
+  __shared__ double s_tc[3];          // sin, cos of pi t (manufactured source); B_s dt (FP32 operator)
+  if (threadIdx.x == 0) {
+    if (g.source == DG_SOURCE_MMS) sincospi(a.clock[0] + a.c_stage * a.clock[1], &s_tc[0], &s_tc[1]);
+    if constexpr (sizeof(R) == 4) s_tc[2] = a.B * a.clock[1];
+  }
   // The epilogue's operands (LSERK register, 1/J, source phases) and the face
   // fluxes are read only after the sweeps: ask for them in L2 now, one bulk
   // prefetch per contiguous range, so that those loads do not wait on DRAM.
@@ -794,18 +800,18 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
       a.Uw[o] = fma(a.B, gk, q[c]);
     }
   } else {
-    // FP32 operator: the register G (an O(dt R) increment, stored in FP64) is
-    // accumulated in FP32 with the FP32 1/J; only U + B G is an FP64 operation.
-    // G's rounding (2^-24 of dt |R|) is far below the operator's own FP32
-    // error, and the FP64 pipe is left to the state update.
+    // FP32 operator: R (sums, 1/J and source in FP32) is widened exactly and
+    // the 2N-storage update runs in FP64.  The register holds G/dt, so that
+    // both FP64 operations are fused multiply-adds:
+    //   G' <- A_s G' + R,  U <- U + (B_s dt) G'   (G' = G/dt; zero at a step's start).
     const R iJ = metrics[(size_t)e * 10 * P + 9 * P + id];
-    const R dtf = to_op<R>(a.clock[1]), Af = to_op<R>(a.A);
+    const double bdt = s_tc[2];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       const size_t o = o0 + (size_t)c * P;
-      const double gk = to_f64(fma(Af, to_op<R>(a.Gk[o]), dtf * fma(-acc[c], iJ, src[c])));
+      const double gk = fma(a.A, a.Gk[o], to_f64(fma(-acc[c], iJ, src[c])));
       a.Gk[o] = gk;
-      a.Uw[o] = fma(a.B, gk, q[c]);
+      a.Uw[o] = fma(bdt, gk, q[c]);
     }
   }
 }

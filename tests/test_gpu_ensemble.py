@@ -1,6 +1,6 @@
-"""Batched ensemble vs the single-context path: every member's state after
-the ensemble steps equals, bit for bit, the same member advanced alone with
-dg_rk_step (the ensemble kernels run the same per-element arithmetic)."""
+"""Batched ensemble: every member advanced by the tile-table kernels against
+the oracle's LSERK4-5 steps at the FP64 bar, and against the single-context
+path bit for bit (the ensemble kernels run the same per-element arithmetic)."""
 import math
 import os
 
@@ -30,6 +30,51 @@ def _make(dg, spec, precision):
     U = s.initial_state("tgv", prm["p0"])
     dt = s.max_dt(U, cfl=0.9, dfl=0.9)
     return s, U, dt
+
+
+@pytest.mark.parametrize("choice,grid", [(0, 3), (1, 5)])
+def test_ensemble_tile_tables_vs_oracle(orc, dg, tmp_path, choice, grid):
+    """FP64 members of mixed N (1, 2, 3, 5, 7) on small meshes, advanced three
+    steps by the persistent tile-table kernels -- forced through the tuning
+    cache: the default (choice 0) or doubled (choice 1) element tile and a
+    grid of a few blocks, so that every block walks many tiles of several
+    members -- against the oracle's LSERK4-5 steps of each member:
+    max |U - U_oracle| / max |U_oracle| <= 1e-10."""
+    gpu = torch.cuda.get_device_name()
+    Ns = sorted({m["N"] for m in MEMBERS})
+    (tmp_path / "tune.txt").write_text("".join("%s|N=%d|fp64\t%d\t%d\t%d\t%d\n" % (gpu, N, choice, grid, grid, grid)
+                                                for N in Ns))
+    runs, orcs, U0s = [], [], []
+    for m in MEMBERS:
+        prm = tgv_params(Ma=m["Ma"], Re=m["Re"])
+        mesh = box_mesh(m["K"], 1, lo=0.0, hi=2 * math.pi, rotate_seed=m["K"] + m["N"])
+        kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"])
+        o = orc.Oracle(mesh, m["N"], **kw)
+        U0 = o.initial_state("tgv", prm["p0"])
+        s = dg.Solver(mesh, m["N"], **kw)
+        dt = s.max_dt(torch.from_numpy(U0).cuda(), cfl=0.9, dfl=0.9)
+        runs.append((s, dt))
+        orcs.append(o)
+        U0s.append(U0)
+    ens = dg.Ensemble([r[0] for r in runs], tune_cache_path=str(tmp_path / "tune.txt"))
+    Us = [torch.from_numpy(U0).cuda() for U0 in U0s]
+    Gs = [torch.empty_like(U) for U in Us]
+    t0 = [0.02 * i for i in range(len(runs))]
+    dts = [r[1] for r in runs]
+    ens.step(Us, Gs, t0, dts, nsteps=3)
+    torch.cuda.synchronize()
+    plan = ens.plan()
+    assert len(plan["groups"]) == len(Ns)
+    for g in plan["groups"]:
+        assert g["mode"] == "tile table" and g["cached"], g
+        assert 1 <= g["volume_grid"] <= grid and g["element_tiles"] >= g["volume_grid"]
+    for o, U0, U, t, dt in zip(orcs, U0s, Us, t0, dts):
+        ref = o.rk_steps(U0, t, dt, 3)
+        err = np.abs(U.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err <= 1e-10, (o.N, err)
+    ens.close()
+    for r in runs:
+        r[0].close()
 
 
 @pytest.mark.parametrize("precision", [0, 1])
