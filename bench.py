@@ -66,6 +66,56 @@ def volume_flops_per_dof(N):
     return 1.5 * (n - 1) * pair + diag + visc + prim + surf + epi
 
 
+# ---------------------------------------------------------------------------
+# Algorithmic DRAM bytes per node and stage of the FP32-operator volume kernel
+# (HBM-bound): FP64 state U and register G read and written (160 B), FP32
+# metric terms J a^d and 1/J (40 B), FP32 lifted gradients (48 B), the
+# manufactured source's phases (16 B, FP64) and the six faces' FP32 fluxes
+# F* (6 (N+1)^2 points x 20 B per element = 120/(N+1) B per node).
+def fp32_volume_bytes_per_dof(N, mms=True):
+    return 160.0 + 40.0 + 48.0 + (16.0 if mms else 0.0) + 120.0 / (N + 1)
+
+
+def hbm_peak_gbs():
+    """(GB/s, source): the measured copy bandwidth if the file is
+    present, else the recipe's fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s, one earlier GB300 copy measurement)"
+
+
+def host_cpu():
+    """(usable cores, CPU model) of this host."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip().lower() in ("model name", "cpu model") and v.strip():
+                    model = v.strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    import platform
+    return cores, (model or "unknown") + " (%s)" % platform.machine()
+
+
 class ClockSampler:
     """Samples SM clocks and throttle reasons with nvidia-smi while running."""
 
@@ -143,27 +193,41 @@ def max_over_ranks(x, world):
 
 
 def cpu_oracle_rate(N, n_evals=2):
-    """The plain oracle (single thread) on the same workload: seconds per R(U)
-    of the whole mesh -> DOF*stage/s."""
+    """The plain oracle on the same workload, single-threaded and with its
+    element and face loops on all host cores (OpenMP build, bit-identical
+    results): DOF*stage/s of R(U) of the whole mesh for each."""
     import oracle
     from workloads import mms_params
     prm = mms_params()
     mesh = build_mesh(N)
-    o = oracle.Oracle(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1)
-    U = o.initial_state("mms", 0.0)
     dof = mesh.n_elems * (N + 1) ** 3
-    t0 = time.perf_counter()
-    for _ in range(n_evals):
-        o.time_derivative(U, t=0.0)
-    dt = (time.perf_counter() - t0) / n_evals
-    return dof / dt, dt
+    cores, model = host_cpu()
+    out = {}
+    for name, par in (("single", False), ("all_cores", True)):
+        o = oracle.Oracle(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1,
+                          parallel=par)
+        threads = oracle.set_threads(cores) if par else 1
+        U = o.initial_state("mms", 0.0)
+        reps = n_evals if not par else max(n_evals, 4)
+        if par:
+            o.time_derivative(U, t=0.0)                   # starts the thread pool
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            o.time_derivative(U, t=0.0)
+        dt = (time.perf_counter() - t0) / reps
+        out[name] = {"value": dof / dt, "threads": threads, "s_per_eval": dt, "evals": reps}
+        del o
+    return out, cores, model
 
 
 def run_reference(args, world, rank):
     """The plain oracle on the host: each step is one R(U) of a bounded
     sample of the workload -- the same mesh family (deformation, seeded
-    rotations, MMS state, N) at 8^3 elements -- so that K steps stay within
-    a few minutes on one core; DOF*stage/s does not depend on the mesh size."""
+    rotations, MMS state, N) at 8^3 elements -- on all host cores (its
+    element and face loops split by OpenMP, bit-identical to the serial
+    oracle), so that K steps stay within a few minutes; DOF*stage/s does not
+    depend on the mesh size.  The single-threaded rate of the same sample is
+    reported beside it."""
     if rank != 0:
         return 0
     N = args.order
@@ -171,33 +235,46 @@ def run_reference(args, world, rank):
     from workloads import box_mesh, mms_params
     prm = mms_params()
     mesh = box_mesh(8, N, deform="sinprod", rotate_seed=MMS_SEED)
-    o = oracle.Oracle(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1)
-    U = o.initial_state("mms", 0.0)
     dof = mesh.n_elems * (N + 1) ** 3
-    for _ in range(args.warmup):
-        o.time_derivative(U, t=0.0)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        o.time_derivative(U, t=0.0)
-    el = time.perf_counter() - t0
-    val = dof * args.steps / el
+    cores, model = host_cpu()
+    rates = {}
+    for name, par in (("all_cores", True), ("single", False)):
+        o = oracle.Oracle(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1,
+                          parallel=par)
+        threads = oracle.set_threads(cores) if par else 1
+        U = o.initial_state("mms", 0.0)
+        steps = args.steps if par else max(2, args.steps // 10)
+        for _ in range(args.warmup if par else 1):
+            o.time_derivative(U, t=0.0)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            o.time_derivative(U, t=0.0)
+        el = time.perf_counter() - t0
+        rates[name] = (dof * steps / el, el, steps, threads)
+        del o
+    val, el, steps, threads = rates["all_cores"]
     line = {
-        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(N), "elements": K_ELEMS ** 3, "N": N,
                    "dof": K_ELEMS ** 3 * (N + 1) ** 3, "sample_elements": mesh.n_elems, "pid_ns": 1e9 / val},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "each step = one R(U) evaluation (one RK stage) by the single-threaded plain "
-                                   "C++ oracle of an 8^3-element sample of the workload's mesh family (same N, "
-                                   "deformation, seeded rotations and MMS state), %d nodes" % dof},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": model,
+                         "pid_ns_times_cores": 1e9 * threads / val,
+                         "single_core_value": rates["single"][0],
+                         "sample": "each step = one R(U) evaluation (one RK stage) by the plain C++ oracle (-O3, "
+                                   "element and face loops on %d OpenMP threads, bit-identical to the serial "
+                                   "oracle) of an 8^3-element sample of the workload's mesh family (same N, "
+                                   "deformation, seeded rotations and MMS state), %d nodes; single_core_value: "
+                                   "the same sample single-threaded (%d evaluations)"
+                                   % (threads, dof, rates["single"][2])},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
 
 
-def run_tgv_large(args, local):
+def tgv_large(nsteps, local):
     """Large Taylor-Green vortex: 48^3 Cartesian elements, N=7 (56.6 M nodes),
     Ma 0.1, Re 1600, LSERK4-5 at CFL 0.9 (dt from the initial state), run once
     with the FP64 operator and twice with the FP32 operator (without and with
@@ -208,7 +285,7 @@ def run_tgv_large(args, local):
     import torch
     import paper_2605_28627_gb300 as dg
     from workloads import box_mesh, tgv_params
-    K, N, nsteps = 48, 7, args.tgv_steps
+    K, N = 48, 7
     prm = tgv_params(Ma=0.1, Re=1600.0)
     mesh = box_mesh(K, 1, lo=0.0, hi=2 * math.pi)
     dofs = mesh.n_elems * (N + 1) ** 3
@@ -230,11 +307,14 @@ def run_tgv_large(args, local):
             s.rk_step(U, G, k * dt, dt, 1, stream=st)
             e1.record(st)
             e1.synchronize()
-            ms_tot += e0.elapsed_time(e1)
+            # the first step also captures the step graph: not timed
+            if k > 0 or nsteps == 1:
+                ms_tot += e0.elapsed_time(e1)
             ek.append(s.integrals(U, stream=st)[5])
         hist[name] = np.array(ek)
-        rate = dofs * 5 * nsteps / (ms_tot * 1e-3)
-        out[name] = {"dof_stage_per_s": rate, "pid_ns": 1e9 / rate, "ms_per_step": ms_tot / nsteps,
+        timed = max(nsteps - 1, 1)
+        rate = dofs * 5 * timed / (ms_tot * 1e-3)
+        out[name] = {"dof_stage_per_s": rate, "pid_ns": 1e9 / rate, "ms_per_step": ms_tot / timed,
                      "ek_final": float(ek[-1])}
         del U, G
         s.close()
@@ -251,23 +331,27 @@ def run_tgv_large(args, local):
         line[name]["dissipation_rate_rel_err"] = float(np.abs(eps[name] - eps["fp64"]).max() /
                                                        np.abs(eps["fp64"]).max())
         line[name]["ek_rel_diff_final"] = abs(out[name]["ek_final"] - out["fp64"]["ek_final"]) / out["fp64"]["ek_final"]
-    print(json.dumps(line))
+    return line
+
+
+def run_tgv_large(args, local):
+    print(json.dumps(tgv_large(args.tgv_steps, local)))
     return 0
 
 
-def run_ensemble(args, local):
-    """Batched ensemble: 64 uneven Taylor-Green runs (seed 20260529: K ~ U{8..24}
-    elements per direction, N ~ U{3..7}, Ma ~ U[0.1, 0.5], Re ~ U[400, 1600]),
-    each with its own CFL-0.9 time step, FP32 operator with FP64 state, 10
-    steps in one graph launch of the autotuned ensemble kernels.  Compared
-    with the same 64 runs advanced one after the other by the single-context
-    path, in FP64 and in FP32-operator precision."""
+def ensemble_study(k_lo, k_hi, nsteps, local, cache_dir=None):
+    """Batched ensemble: 64 uneven Taylor-Green runs (seed 20260529: K ~
+    U{k_lo..k_hi} elements per direction, N ~ U{3..7}, Ma ~ U[0.1, 0.5], Re ~
+    U[400, 1600]), each with its own CFL-0.9 time step, FP32 operator with FP64
+    state, nsteps steps in one graph launch of the autotuned ensemble kernels.
+    Compared with the same 64 runs advanced one after the other by the
+    single-context path (each run's step graph launched back to back on one
+    stream, the gaps between runs included), in FP64 and in FP32-operator
+    precision."""
     import torch
     import paper_2605_28627_gb300 as dg
     from workloads import box_mesh, ensemble_members, tgv_params
-    k_lo, k_hi = (int(v) for v in args.ens_K.split(","))
     specs = ensemble_members(64, 20260529, k_lo, k_hi)
-    nsteps = args.ens_steps
     dev = "cuda:%d" % local
     st = torch.cuda.Stream(device=dev)
 
@@ -283,11 +367,12 @@ def run_ensemble(args, local):
     dofs = [sp["K"] ** 3 * (sp["N"] + 1) ** 3 for sp in specs]
     total = sum(dofs)
     runs = [member(sp, dg.FP32OP) for sp in specs]
-    cache_dir = os.path.join(ROOT, "paper_2605_28627_gb300", "_build")
     # the tuned plan depends on the member sizes: one cache file per size range
-    cache = "ensemble_tune.txt" if (k_lo, k_hi) == (8, 24) else "ensemble_tune_K%d-%d.txt" % (k_lo, k_hi)
-    ens = dg.Ensemble([r[0] for r in runs],
-                      tune_cache_path=os.path.join(cache_dir, cache) if os.path.isdir(cache_dir) else None)
+    cache = None
+    if cache_dir and os.path.isdir(cache_dir):
+        name = "ensemble_tune.txt" if (k_lo, k_hi) == (8, 24) else "ensemble_tune_K%d-%d.txt" % (k_lo, k_hi)
+        cache = os.path.join(cache_dir, name)
+    ens = dg.Ensemble([r[0] for r in runs], tune_cache_path=cache)
     Us = [r[1] for r in runs]
     Gs = [torch.empty_like(U) for U in Us]
     dts = [r[2] for r in runs]
@@ -313,39 +398,48 @@ def run_ensemble(args, local):
     torch.cuda.empty_cache()
 
     def sequential(precision):
-        # the same 1 + 2 nsteps steps as the ensemble members took
-        ms_tot, ek = 0.0, []
-        for sp in specs:
-            s, U, dt = member(sp, precision)
-            G = torch.empty_like(U)
+        # the same 1 + 2 nsteps steps as the ensemble members took; the timed
+        # part launches the 64 runs' step graphs back to back on one stream
+        mem = [member(sp, precision) for sp in specs]
+        Gq = [torch.empty_like(U) for _, U, _ in mem]
+        for (s, U, dt), G in zip(mem, Gq):
             s.rk_step(U, G, 0.0, dt, 1, stream=st)
             s.rk_step(U, G, dt, dt, nsteps, stream=st)            # warm-up + graph capture
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(st)
+        st.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for (s, U, dt), G in zip(mem, Gq):
             s.rk_step(U, G, (1 + nsteps) * dt, dt, nsteps, stream=st)
-            b.record(st)
-            b.synchronize()
-            ms_tot += a.elapsed_time(b)
-            ek.append(s.integrals(U, stream=st)[5])
+        b.record(st)
+        b.synchronize()
+        ek = [s.integrals(U, stream=st)[5] for s, U, _ in mem]
+        for s, _, _ in mem:
             s.close()
-            del U, G
-        return ms_tot, ek
+        del mem, Gq
+        torch.cuda.empty_cache()
+        return a.elapsed_time(b), ek
 
     ms_seq64, ek64 = sequential(dg.FP64)
     ms_seq32, ek32 = sequential(dg.FP32OP)
     ek_err = [abs(a - b) / abs(b) for a, b in zip(ek_ens, ek64)]
     rate = total * 5 * nsteps / (ms_ens * 1e-3)
-    line = {"experiment": "ensemble of 64 uneven Taylor-Green runs (seed 20260529, K^3 elements, K in %d..%d), "
+    return {"experiment": "ensemble of 64 uneven Taylor-Green runs (seed 20260529, K^3 elements, K in %d..%d), "
                           "FP32 operator / FP64 state, %d LSERK4-5 steps in one graph launch" % (k_lo, k_hi, nsteps),
             "members": 64, "total_dof": total, "value": rate, "unit": UNIT, "pid_ns": 1e9 / rate,
             "ms_per_step": ms_ens / nsteps,
             "sequential_fp64_ms_per_step": ms_seq64 / nsteps, "sequential_fp32op_ms_per_step": ms_seq32 / nsteps,
             "speedup_vs_sequential_fp64": ms_seq64 / ms_ens, "speedup_vs_sequential_fp32op": ms_seq32 / ms_ens,
+            "sequential_timing": "the 64 step graphs launched back to back on one stream, gaps included",
             "first_step_with_tuning_s": tune_s,
             "ek_rel_err_vs_fp64_max": max(ek_err), "ek_rel_err_vs_fp64_median": float(np.median(ek_err)),
             "ek_rel_diff_ensemble_vs_sequential_fp32op_max": max(abs(a - b) / abs(b) for a, b in zip(ek_ens, ek32)),
             "steps_compared": 1 + 2 * nsteps, "plan": plan}
-    print(json.dumps(line))
+
+
+def run_ensemble(args, local):
+    k_lo, k_hi = (int(v) for v in args.ens_K.split(","))
+    print(json.dumps(ensemble_study(k_lo, k_hi, args.ens_steps, local,
+                                    os.path.join(ROOT, "paper_2605_28627_gb300", "_build"))))
     return 0
 
 
@@ -555,6 +649,9 @@ def main():
     ap.add_argument("--pid-steps", type=int, default=10)
     ap.add_argument("--pid-cases", default="", help="comma list of PID case names ('' = all)")
     ap.add_argument("--pid-K", type=int, default=0, help="elements per direction instead of the cases' own")
+    ap.add_argument("--no-extra-legs", dest="extra_legs", action="store_false",
+                    help="skip the 48^3 Taylor-Green and ensemble legs of the default line")
+    ap.add_argument("--tgv-leg-steps", type=int, default=6, help="steps of the 48^3 leg of the default line")
     ap.add_argument("--adj-steps", type=int, default=200)
     ap.add_argument("--adj-dirs", type=int, default=32)
     args = ap.parse_args()
@@ -643,7 +740,9 @@ def main():
     e2e = {"value": world * dof * 5 * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": nb,
            "d2h_bytes_per_step": nb}
 
-    fp32 = fp32_operator_rate(dg, N, local, prm, U0, args.steps, value / world) if rank == 0 else None
+    hbm_peak, hbm_src = hbm_peak_gbs()
+    fp32 = fp32_operator_rate(dg, N, local, prm, U0, args.steps, value / world, hbm_peak, hbm_src) \
+        if rank == 0 else None
     tgv_small = small_tgv_rate(dg, local) if rank == 0 else None
 
     sweep = {}
@@ -666,16 +765,34 @@ def main():
             ms32, _ = sweep_rate(dg, Ns, local, prm, precision=dg.FP32OP, keep_state=states)
             sweep[str(Ns)]["fp32op_dof_stage_per_s"] = dofs * 5 / (ms32 * 1e-3)
             sweep[str(Ns)]["fp32op_speedup"] = sweep[str(Ns)]["pid_ns"] / (ms32 * 1e6 / (dofs * 5))
+            torch.cuda.synchronize()
             sweep[str(Ns)]["fp32op_max_rel_state_diff"] = float((states[1] - states[0]).abs().max() /
                                                                 states[0].abs().max())
             del states
 
+    # the larger workloads, each a few steps (their own studies run them longer)
+    extra = {}
+    if rank == 0 and args.extra_legs:
+        for key, fn in (("tgv_large", lambda: tgv_large(args.tgv_leg_steps, local)),
+                        ("ensemble", lambda: ensemble_study(8, 24, 10, local)),
+                        ("ensemble_small_members", lambda: ensemble_study(2, 6, 10, local))):
+            try:
+                extra[key] = fn()
+            except Exception as exc:          # a failed leg must not cost the headline line
+                extra[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+            torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, sec = cpu_oracle_rate(N, n_evals=2)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "2 evaluations of R(U) (one RK stage each) on the whole %d^3, N=%d mesh, single-threaded "
-                         "plain C++ oracle, %.1f s each" % (K_ELEMS, N, sec)}
+        rates, cores, model = cpu_oracle_rate(N, n_evals=2)
+        a, s1 = rates["all_cores"], rates["single"]
+        cpu = {"value": a["value"], "unit": UNIT, "cores": a["threads"], "kind": "oracle", "cpu": model,
+               "pid_ns_times_cores": 1e9 * a["threads"] / a["value"], "single_core_value": s1["value"],
+               "sample": "R(U) (one RK stage) of the whole %d^3, N=%d mesh by the plain C++ oracle (-O3): %d "
+                         "evaluations with its element and face loops on %d OpenMP threads (%.2f s each; "
+                         "bit-identical to the serial oracle), and %d single-threaded (%.1f s each) for "
+                         "single_core_value" % (K_ELEMS, N, a["evals"], a["threads"], a["s_per_eval"],
+                                                s1["evals"], s1["s_per_eval"])}
 
     if rank == 0:
         line = {
@@ -690,18 +807,20 @@ def main():
             "clocks": clk, "sweep": sweep, "fp32_operator": fp32, "tgv_small": tgv_small,
             "peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
         }
+        line.update(extra)
         print(json.dumps(line))
     solver.close()
     return 0
 
 
-def fp32_operator_rate(dg, N, dev, prm, U0, steps, fp64_rate):
+def fp32_operator_rate(dg, N, dev, prm, U0, steps, fp64_rate, hbm_peak, hbm_src):
     """The FP32-operator path on the same workload: throughput, speedup over
-    the FP64 path, and its deviation from the FP64 path after warm-up + steps."""
+    the FP64 path, its deviation from the FP64 path after warm-up + steps, and
+    the HBM roofline of its volume kernel (algorithmic bytes / event time)."""
     import torch
     mesh = build_mesh(N)
-    out = {}
     results = {}
+    ms3 = None
     for name, prec in (("fp64", dg.FP64), ("fp32op", dg.FP32OP)):
         s = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=dg.SOURCE_MMS,
                       precision=prec, device=dev)
@@ -720,17 +839,30 @@ def fp32_operator_rate(dg, N, dev, prm, U0, steps, fp64_rate):
         e1.synchronize()
         ms = e0.elapsed_time(e1) / steps
         results[name] = (U, s.integrals(U, stream=st), ms)
+        if prec == dg.FP32OP:
+            with torch.cuda.stream(st):
+                Up, Gp = U.clone(), torch.empty_like(U)
+            ms3 = s.profile_stages(Up, Gp, DT, reps=10, stream=st)
+            del Up, Gp
         s.close()
     dofs = mesh.n_elems * (N + 1) ** 3
     U64, I64, ms64 = results["fp64"]
     U32, I32, ms32 = results["fp32op"]
     rate = dofs * 5 / (ms32 * 1e-3)
-    out = {"value": rate, "unit": UNIT, "pid_ns": 1e9 / rate, "speedup_vs_fp64": ms64 / ms32,
-           "steps_compared": 3 + steps,
-           "max_rel_state_diff_vs_fp64": float((U32 - U64).abs().max() / U64.abs().max()),
-           "ek_rel_diff_vs_fp64": float(abs(I32[5] - I64[5]) / abs(I64[5])),
-           "note": "same workload and steps as the headline; operator arithmetic FP32, state, U update and reductions FP64, LSERK register accumulated in FP32"}
-    return out
+    vb = fp32_volume_bytes_per_dof(N) * dofs
+    ach = vb / (ms3[2] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+            "traffic": MEASURED_TRAFFIC.get((N, "fp32op")),
+            "kernel": "k_volume2<%d, float> (FP32 split-form volume + surface + Jacobian, FP64 LSERK update)" % N,
+            "algorithmic_bytes_per_dof": fp32_volume_bytes_per_dof(N), "peak_source": hbm_src,
+            "stage_ms": {"lift": ms3[0], "face": ms3[1], "volume": ms3[2]}}
+    return {"value": rate, "unit": UNIT, "pid_ns": 1e9 / rate, "speedup_vs_fp64": ms64 / ms32,
+            "steps_compared": 3 + steps,
+            "max_rel_state_diff_vs_fp64": float((U32 - U64).abs().max() / U64.abs().max()),
+            "ek_rel_diff_vs_fp64": float(abs(I32[5] - I64[5]) / abs(I64[5])),
+            "roofline": roof,
+            "note": "same workload and steps as the headline; operator arithmetic FP32; state, LSERK register "
+                    "update, U update and reductions FP64"}
 
 
 def working_set_mb(s):
