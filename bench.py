@@ -117,6 +117,22 @@ def host_cpu():
     return cores, (model or "unknown") + " (%s)" % platform.machine()
 
 
+# Algorithmic FP64 operations per node of one VJP (dR/dU)^T v in the adjoint
+# volume kernel (same counting: FMA = 2, divide/log = 1), counted from the
+# formulas it evaluates: per unique pair 214 (the two log means with their
+# partial derivatives 2 x 35, the reverse sweep of the two-point flux 118, the
+# metric average 6, the pair's two adjoint seeds 15, the partner's share 5),
+# 1.5 (n-1) pairs per node; per node the primitives and reciprocals (19),
+# -lambda/J (5), the viscous-flux adjoint in three directions (90 each) with
+# its D^T line sums (8 n) and the primitive adjoint (25).
+ADJ_PAIR_FLOPS = 214.0
+
+
+def adjoint_volume_flops_per_dof(N):
+    n = N + 1
+    return 1.5 * (n - 1) * ADJ_PAIR_FLOPS + 19.0 + 5.0 + 3 * 90.0 + 3 * 8.0 * n + 25.0
+
+
 class ClockSampler:
     """Samples SM clocks and throttle reasons with nvidia-smi while running."""
 
@@ -584,6 +600,37 @@ def run_adjoint(args, local):
     lamT = torch.empty_like(U0)
     s.kinetic_energy(UT.detach(), grad=lamT)
     _, counts = s.adjoint_solve(U0, lamT, 0.0, dt, nsteps, max_snapshots=16)
+    # one VJP of R (volume, face, gather and lifting adjoint kernels), CUDA
+    # events on its stream, against the forward R(U) on the same state
+    st = torch.cuda.Stream(device="cuda:%d" % local)
+    with torch.cuda.stream(st):
+        vj = torch.empty_like(U0)
+        Rt = torch.empty_like(U0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(3):
+        s.time_derivative_vjp(U0, lamT, out=vj, stream=st)
+        s.time_derivative(U0, Rt, stream=st)
+    reps = 20
+    ev[0].record(st)
+    for _ in range(reps):
+        s.time_derivative_vjp(U0, lamT, out=vj, stream=st)
+    ev[1].record(st)
+    for _ in range(reps):
+        s.time_derivative(U0, Rt, stream=st)
+    ev[2].record(st)
+    ev[2].synchronize()
+    ms_vjp = ev[0].elapsed_time(ev[1]) / reps
+    ms_fwd = ev[1].elapsed_time(ev[2]) / reps
+    fp64_peak, _ = dg.probe_peaks(local)
+    dof = s.E * (N + 1) ** 3
+    adj_flops = adjoint_volume_flops_per_dof(N) * dof
+    adj_roof = {"bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak,
+                "achieved_lower_bound": adj_flops / (ms_vjp * 1e-3) / 1e12,
+                "frac_lower_bound": adj_flops / (ms_vjp * 1e-3) / 1e12 / fp64_peak,
+                "algorithmic_flops_per_dof": adjoint_volume_flops_per_dof(N),
+                "note": "the adjoint volume kernel's algorithmic FP64 count over the time of the whole VJP call "
+                        "(volume, face, gather and lifting adjoint kernels): a lower bound of the volume "
+                        "kernel's own fraction; its share of the VJP time is in the ncu launch list"}
 
     def Jof(U, m):
         with torch.no_grad():
@@ -644,6 +691,8 @@ def run_adjoint(args, local):
             "dJ_dU0_fd_rel_err_max_h1e-7": max(errs_small),
             "dJ_dU0_fd_rel_err_median_h1e-7": float(np.median(errs_small)),
             "forward_s": t_fwd, "adjoint_s": t_adj, "adjoint_over_forward": t_adj / t_fwd,
+            "vjp_ms": ms_vjp, "time_derivative_ms": ms_fwd, "vjp_over_time_derivative": ms_vjp / ms_fwd,
+            "roofline": adj_roof,
             "snapshots": 16, "recomputed_forward_steps": counts[0], "adjoint_steps": counts[1]}
     print(json.dumps(line))
     return 0
@@ -763,6 +812,7 @@ def main():
     fp32 = fp32_operator_rate(dg, N, local, prm, U0, args.steps, value / world, hbm_peak, hbm_src) \
         if rank == 0 else None
     tgv_small = small_tgv_rate(dg, local) if rank == 0 else None
+    indicator = indicator_rate(solver, U, stream, fp64_peak) if rank == 0 else None
 
     sweep = {}
     if args.sweep and rank == 0:
@@ -823,7 +873,7 @@ def main():
                        "l2": "inputs larger than L2: %.0f MB of state, metrics, gradients and face data touched "
                              "per stage" % working_set_mb(solver)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-            "clocks": clk, "sweep": sweep, "fp32_operator": fp32, "tgv_small": tgv_small,
+            "clocks": clk, "sweep": sweep, "fp32_operator": fp32, "tgv_small": tgv_small, "indicator": indicator,
             "peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
         }
         line.update(extra)
@@ -882,6 +932,38 @@ def fp32_operator_rate(dg, N, dev, prm, U0, steps, fp64_rate, hbm_peak, hbm_src)
             "roofline": roof,
             "note": "same workload and steps as the headline; operator arithmetic FP32; state, LSERK register "
                     "update, U update and reductions FP64"}
+
+
+def indicator_flops_per_dof(N):
+    """Algorithmic FP64 operations per node of the Persson indicator (FMA = 2,
+    divide = 1): p and rho p from the state (11), the modal transform in three
+    directions (2 (N+1) each), the mode's square and its share of the two
+    element sums (4)."""
+    return 6.0 * (N + 1) + 15.0
+
+
+def indicator_rate(solver, U, stream, fp64_peak, reps=20):
+    """The Persson troubled-cell indicator (rho p) on the headline state: CUDA
+    events around `reps` launches.  It reads 40 B and does 6 (N+1) + 15 FP64
+    operations per node, so it is bound by the FP64 pipe, not by HBM."""
+    import torch
+    for _ in range(3):
+        solver.indicator(U, log10_threshold=-4.0, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        eta, flag = solver.indicator(U, log10_threshold=-4.0, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    fl = indicator_flops_per_dof(solver.N) * solver.E * solver.P
+    tf = fl / (ms * 1e-3) / 1e12
+    return {"kernel": "k_indicator<%d> (Persson modal indicator of rho p, FP64)" % solver.N, "ms": ms,
+            "elements_flagged_at_log10_eta_gt_-4": int(flag.sum().item()), "max_eta": float(eta.max().item()),
+            "dram_gbs_algorithmic": solver.E * (40.0 * solver.P + 12.0) / (ms * 1e-3) / 1e9,
+            "roofline": {"bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": tf / fp64_peak,
+                         "algorithmic_flops_per_dof": indicator_flops_per_dof(solver.N),
+                         "peak_source": "measured FP64 DFMA chain throughput on this GPU (dg_probe_peaks)"}}
 
 
 def working_set_mb(s):

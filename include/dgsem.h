@@ -68,6 +68,7 @@ enum { DG_VISC_CONSTANT = 0, DG_VISC_SUTHERLAND = 1 };   /* viscosity law: const
                                                            node's temperature (the law of the dissipation
                                                            diagnostic, Sec. 4.2) */
 enum { DG_IC_TGV = 0, DG_IC_MMS = 1 };            /* built-in initial states */
+enum { DG_IND_RHO = 0, DG_IND_P = 1, DG_IND_RHOP = 2 };   /* quantity of the troubled-cell indicator */
 
 /*
  * Mesh (Sec. 3.1: non-overlapping hexahedra, each the image of E = [-1,1]^3
@@ -164,6 +165,22 @@ dg_status dg_max_dt(dg_ctx* ctx, const double* dU, double cfl, double dfl, doubl
 /* Built-in initial states at the LGL nodes: DG_IC_TGV (Sec. 4.2, Eq. 6) with
  * rho0 = U0 = L = R = 1 and p0 = prm0; DG_IC_MMS at time prm0. */
 dg_status dg_initial_state(dg_ctx* ctx, int32_t kind, double prm0, double* dU, dg_stream stream);
+
+/* Modal troubled-cell indicator of Persson & Peraire (2006), the detector of
+ * the FV sub-cell shock capturing (Sec. 3.1): per element, the quantity q
+ * (var: DG_IND_RHO, DG_IND_P or DG_IND_RHOP = rho p) at the context's nodes is
+ * expanded in the orthonormal Legendre basis sqrt((2m+1)/2) P_m per
+ * direction, and
+ *   dEta[e] = sum_{max(a,b,c) = N} qh_abc^2 / sum_abc qh_abc^2
+ * (the energy share of the modes that truncation to degree N-1 in every
+ * direction removes; 0 for a field of degree < N in each direction, 1 for a
+ * pure top mode; 0 where q vanishes).  dFlag (may be NULL) receives 1 where
+ * eta > 0 and log10(eta) > log10_threshold, else 0 (FP64 decision).  The FV
+ * sub-cell operator itself is not built.  dU: device state; dEta: device,
+ * n_elems doubles; dFlag: device, n_elems int32.  DG_EINVAL for a null
+ * argument or an unknown var.  Does not synchronise. */
+dg_status dg_indicator(dg_ctx* ctx, const double* dU, int32_t var, double log10_threshold, double* dEta,
+                       int32_t* dFlag, dg_stream stream);
 
 /* Physical node positions X[e][c][k][j][i] (device, n_elems*3*(N+1)^3). */
 dg_status dg_node_coords(dg_ctx* ctx, double* dX, dg_stream stream);

@@ -1312,11 +1312,108 @@ static void integrals_lg(const Ctx& c, const double* U, double* out) {
   out[7] = pmin;
 }
 
+// ---------------------------------------------------------------------------
+// Modal troubled-cell indicator of Persson & Peraire (2006), the detector that
+// marks DG elements for the FV sub-cell shock capturing (Sec. 3.1).  The
+// indicator quantity q of an element, given at its n = N+1 nodes per
+// direction, is expanded in the orthonormal Legendre basis
+//   Lt_m(xi) = sqrt((2m + 1)/2) P_m(xi),  q(x) = sum_abc qh_abc Lt_a Lt_b Lt_c,
+// the unique interpolant of the nodal values (a Vandermonde solve per
+// direction), and the indicator is the share of the L2 energy in the modes
+// that the truncation to degree N-1 in every direction removes:
+//   eta = sum_{max(a,b,c) = N} qh_abc^2 / sum_abc qh_abc^2
+// (readings: the tensor-product truncation Q_{N-1}; q = rho, p or rho p).
+
+// Orthonormal Legendre value Lt_m(x).
+static double legendre_orthonormal(int m, double x) {
+  double a = 1.0, b = x;
+  if (m == 0) return std::sqrt(0.5);
+  for (int k = 1; k < m; ++k) {
+    const double c = ((2.0 * k + 1.0) * x * b - k * a) / (k + 1.0);
+    a = b; b = c;
+  }
+  return std::sqrt((2.0 * m + 1.0) / 2.0) * b;
+}
+
+// Inverse of the Vandermonde matrix V[i][m] = Lt_m(x_i) by Gauss-Jordan
+// elimination with partial pivoting: the map from nodal values to modes.
+static std::vector<double> modal_transform(const std::vector<double>& x) {
+  const int n = (int)x.size();
+  std::vector<double> A((size_t)n * 2 * n, 0.0);   // [V | I]
+  for (int i = 0; i < n; ++i) {
+    for (int m = 0; m < n; ++m) A[(size_t)i * 2 * n + m] = legendre_orthonormal(m, x[i]);
+    A[(size_t)i * 2 * n + n + i] = 1.0;
+  }
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * 2 * n + col]) > std::fabs(A[(size_t)piv * 2 * n + col])) piv = r;
+    for (int k = 0; k < 2 * n; ++k) std::swap(A[(size_t)col * 2 * n + k], A[(size_t)piv * 2 * n + k]);
+    const double d = A[(size_t)col * 2 * n + col];
+    for (int k = 0; k < 2 * n; ++k) A[(size_t)col * 2 * n + k] /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double f = A[(size_t)r * 2 * n + col];
+      for (int k = 0; k < 2 * n; ++k) A[(size_t)r * 2 * n + k] -= f * A[(size_t)col * 2 * n + k];
+    }
+  }
+  std::vector<double> Vi((size_t)n * n);
+  for (int m = 0; m < n; ++m)
+    for (int i = 0; i < n; ++i) Vi[(size_t)m * n + i] = A[(size_t)m * 2 * n + n + i];
+  return Vi;
+}
+
+// eta of one element from its nodal values q[k][j][i].
+static double persson_eta(int n, const std::vector<double>& Vi, const double* q) {
+  const int N = n - 1;
+  double top = 0.0, all = 0.0;
+  for (int c = 0; c < n; ++c)
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        double qh = 0.0;
+        for (int k = 0; k < n; ++k)
+          for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i)
+              qh += Vi[(size_t)a * n + i] * Vi[(size_t)b * n + j] * Vi[(size_t)c * n + k] * q[i + n * (j + n * k)];
+        all += qh * qh;
+        if (a == N || b == N || c == N) top += qh * qh;
+      }
+  return all > 0.0 ? top / all : 0.0;
+}
+
 }  // namespace orc
 
 using namespace orc;
 
 extern "C" {
+
+// Persson indicator of nodal fields q[E][(N+1)^3] given at the nodes x (n
+// values): out[e] = eta_e.
+void orc_persson_field(int N, const double* x, int E, const double* q, double* out) {
+  const int n = N + 1, P = n * n * n;
+  std::vector<double> xs(x, x + n);
+  const std::vector<double> Vi = modal_transform(xs);
+  for (int e = 0; e < E; ++e) out[e] = persson_eta(n, Vi, q + (size_t)e * P);
+}
+
+// Persson indicator of the state U of an oracle context at its own nodes
+// (LGL, or Gauss for a Gauss-node context); var = 0: rho, 1: p, 2: rho p.
+void orc_persson(void* h, const double* U, int var, double* out) {
+  Ctx* c = (Ctx*)h;
+  const int n = c->n, P = c->P;
+  const std::vector<double>& x = c->nodes == 1 ? c->g.x : c->b.x;
+  const std::vector<double> Vi = modal_transform(x);
+  std::vector<double> q(P);
+  for (int e = 0; e < c->E; ++e) {
+    for (int id = 0; id < P; ++id) {
+      double qs[5];
+      for (int v = 0; v < 5; ++v) qs[v] = U[((size_t)e * 5 + v) * P + id];
+      const Prim<double> w = cons2prim(c->prm, qs);
+      q[id] = var == 0 ? w.rho : (var == 1 ? w.p : w.rho * w.p);
+    }
+    out[e] = persson_eta(n, Vi, q.data());
+  }
+}
 
 // Create an oracle context.  prm = {gamma, R, Pr, mu, mms_amp}; returns NULL
 // and fills errbuf on a bad mesh.

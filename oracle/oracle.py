@@ -79,6 +79,8 @@ def _load(omp: bool = False):
     L.orc_volume_term.argtypes = [C.c_void_p, _dp, _dp]
     L.orc_count_ops.argtypes = [C.c_void_p, _dp, C.c_double, _dp]
     L.orc_count_ec_flux_ops.argtypes = [_dp, _dp, _dp, _dp, _dp]
+    L.orc_persson_field.argtypes = [C.c_int, _dp, C.c_int, _dp, _dp]
+    L.orc_persson.argtypes = [C.c_void_p, _dp, C.c_int, _dp]
     _libs[omp] = L
     return L
 
@@ -157,6 +159,15 @@ def count_ec_flux_ops(qL, qR, nv, gamma=1.4):
                                   np.ascontiguousarray(qR, dtype=np.float64),
                                   np.ascontiguousarray(nv, dtype=np.float64), out)
     return dict(zip(_OP_NAMES, (int(v) for v in out)))
+
+
+def persson_field(N: int, x, q):
+    """Persson modal indicator eta of nodal fields q [E, (N+1)^3] given at
+    the nodes x (N+1 values per direction)."""
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(q.shape[0], -1)
+    out = np.zeros(q.shape[0])
+    _load().orc_persson_field(int(N), np.ascontiguousarray(x, dtype=np.float64), q.shape[0], q, out)
+    return out
 
 
 def log_mean(a, b):
@@ -259,6 +270,13 @@ class Oracle:
     def volume_term(self, U):
         out = np.zeros((self.E, 5, self.P))
         self._L.orc_volume_term(self._h, np.ascontiguousarray(U, dtype=np.float64), out)
+        return out
+
+    def persson(self, U, var: int = 2):
+        """Persson modal indicator eta per element of rho (var 0), p (1) or
+        rho p (2), at the context's nodes."""
+        out = np.zeros(self.E)
+        self._L.orc_persson(self._h, np.ascontiguousarray(U, dtype=np.float64), int(var), out)
         return out
 
     def integrals(self, U):

@@ -15,7 +15,10 @@ import numpy as np
 
 from . import build as _build
 
-LIB_PATH = _build.LIB
+# DGSEM_CHECKED=1 loads the checked build (every indirect gather index
+# bounds-checked, see csrc/dg_check.cuh), for debugging; same API and results.
+CHECKED = os.environ.get("DGSEM_CHECKED", "") == "1"
+LIB_PATH = _build.LIB_CHECKED if CHECKED else _build.LIB
 
 # dg_status codes
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_EMESH, DG_ENONFINITE, DG_ETIMEOUT, DG_EUNSUPPORTED = range(8)
@@ -28,6 +31,7 @@ VISC_CONSTANT, VISC_SUTHERLAND = 0, 1
 NODES_LGL, NODES_LG = 0, 1
 RK45, RK414 = 0, 1
 IC_TGV, IC_MMS = 0, 1
+IND_RHO, IND_P, IND_RHOP = 0, 1, 2
 
 # Every symbol that include/dgsem.h declares.
 EXPORTS = ["dg_init", "dg_destroy", "dg_state_len", "dg_time_derivative", "dg_rk_step", "dg_advance_host",
@@ -35,7 +39,7 @@ EXPORTS = ["dg_init", "dg_destroy", "dg_state_len", "dg_time_derivative", "dg_rk
            "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
            "dg_ensemble_step", "dg_ensemble_plan", "dg_ensemble_last_error", "dg_time_derivative_vjp",
            "dg_adjoint_step", "dg_adjoint_solve", "dg_checkpoint_schedule", "dg_kinetic_energy", "dg_set_viscosity",
-           "dg_check_conversions", "dg_check_reciprocals", "dg_last_error"]
+           "dg_check_conversions", "dg_check_reciprocals", "dg_indicator", "dg_last_error"]
 
 
 class DGError(RuntimeError):
@@ -65,10 +69,10 @@ def load(build_if_missing: bool = True):
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH) or not _build.up_to_date():
+    if not os.path.exists(LIB_PATH) or not _build.up_to_date(CHECKED):
         if not build_if_missing:
             raise RuntimeError("libdgsem.so is not built (run __graft_entry__.build())")
-        _build.build()
+        _build.build(checked=CHECKED)
     L = C.CDLL(LIB_PATH)
     vp, dp, i32, f64 = C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.c_double
     L.dg_init.argtypes = [C.POINTER(dg_mesh), C.POINTER(dg_params), C.c_int, C.POINTER(vp)]
@@ -87,6 +91,7 @@ def load(build_if_missing: bool = True):
     L.dg_probe_peaks.argtypes = [C.c_int, dp]
     L.dg_check_conversions.argtypes = [vp, i32, vp, vp, vp]
     L.dg_check_reciprocals.argtypes = [vp, i32, vp, vp, vp]
+    L.dg_indicator.argtypes = [vp, vp, i32, f64, vp, vp, vp]
     L.dg_conserved_totals_noalloc.argtypes = [vp, vp, i32, i32, i32, vp, vp]
     L.dg_ensemble_create.argtypes = [C.POINTER(vp), i32, C.c_char_p, C.POINTER(vp)]
     L.dg_ensemble_destroy.argtypes = [vp]
@@ -107,7 +112,7 @@ def load(build_if_missing: bool = True):
                  "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
                  "dg_ensemble_step", "dg_ensemble_plan", "dg_time_derivative_vjp", "dg_adjoint_step",
                  "dg_adjoint_solve", "dg_checkpoint_schedule", "dg_kinetic_energy", "dg_set_viscosity",
-                 "dg_check_conversions", "dg_check_reciprocals"):
+                 "dg_check_conversions", "dg_check_reciprocals", "dg_indicator"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -236,6 +241,20 @@ class Solver:
         self._check(self._L.dg_initial_state(self._h, {"tgv": IC_TGV, "mms": IC_MMS}[kind], float(prm0), _ptr(U),
                                              _stream_handle(stream)))
         return U
+
+    def indicator(self, U, var=IND_RHOP, log10_threshold=None, stream=None):
+        """Persson modal indicator per element: eta (device float64 [E]) and,
+        with a threshold, the troubled-cell flags (device int32 [E])."""
+        import torch
+        self._chk_state(U)
+        eta = torch.empty(self.E, dtype=torch.float64, device="cuda:%d" % self.device)
+        flag = None
+        if log10_threshold is not None:
+            flag = torch.empty(self.E, dtype=torch.int32, device="cuda:%d" % self.device)
+        self._check(self._L.dg_indicator(self._h, _ptr(U), int(var),
+                                         float(log10_threshold) if log10_threshold is not None else 0.0, _ptr(eta),
+                                         _ptr(flag) if flag is not None else None, _stream_handle(stream)))
+        return eta, flag
 
     def node_coords(self, stream=None):
         import torch

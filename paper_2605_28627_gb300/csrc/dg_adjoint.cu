@@ -206,7 +206,7 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
       const int id_d = ijk[d];
       if (id_d != 0 && id_d != N) continue;
       const int code = elem_face[e * 6 + 2 * d + (id_d == N ? 1 : 0)];
-      const int fid = code >> 4;
+      const int fid = dg_idx(code >> 4, 3L * E, kSiteAdjFace);
       const int pp = d == 0 ? j : i;
       const int qq = d == 2 ? j : k;
       if (code & 8) {
@@ -247,7 +247,8 @@ k_adj_face(const double* __restrict__ U, const double* __restrict__ grad, const 
     const int f = (int)(gid / NN), pq = (int)(gid % NN);
     const int p = pq % n, q = pq / n;
     const FaceInfo fi = faces[f];
-    const int eM = fi.master >> 3, fM = fi.master & 7, eS = fi.slave >> 3, fS = fi.slave & 7;
+    const int eM = dg_idx(fi.master >> 3, F / 3, kSiteAdjFace), fM = fi.master & 7;
+    const int eS = dg_idx(fi.slave >> 3, F / 3, kSiteAdjFace), fS = fi.slave & 7;
     int p2, q2;
     apply_flip<n>(fi.flip, p, q, p2, q2);
     const int idM = face_node<n>(fM, p, q), idS = face_node<n>(fS, p2, q2);
@@ -335,7 +336,7 @@ k_adj_gather(const double* __restrict__ metrics, const int* __restrict__ elem_fa
     const int id_d = ijk[d];
     if (id_d != 0 && id_d != N) continue;
     const int code = elem_face[e * 6 + 2 * d + (id_d == N ? 1 : 0)];
-    const int fid = code >> 4;
+    const int fid = dg_idx(code >> 4, 3L * E, kSiteAdjFace);
     const int pp = d == 0 ? j : i;
     const int qq = d == 2 ? j : k;
     int pm = pp, qm = qq, side = 0;
@@ -413,7 +414,7 @@ k_adj_lift(const double* __restrict__ U, const double* __restrict__ metrics, con
     const int f = 2 * d + s;
     const int code = elem_face[e * 6 + f];
     const int nb = elem_nbr[e * 6 + f];
-    const int e2 = nb >> 3, f2 = nb & 7;
+    const int e2 = dg_idx(nb >> 3, E, kSiteAdjFace), f2 = nb & 7;
     const int pp = d == 0 ? j : i;
     const int qq = d == 2 ? j : k;
     int p2, q2;
@@ -622,5 +623,8 @@ cudaError_t launch_axpby(double* y, const double* x, double a, double b, size_t 
   k_axpby<<<(unsigned)blocks, 256, 0, s>>>(y, x, a, b, len);
   return cudaGetLastError();
 }
+
+// Host reader of this file's bounds-check error word (0 in normal builds).
+DG_BOUNDS_READER(bounds_word_adjoint)
 
 }  // namespace dg

@@ -24,6 +24,13 @@ static dg_status afail(Ctx* c, dg_status st, const char* what, cudaError_t e = c
       return afail(ctx, _e == cudaErrorMemoryAllocation ? DG_ENOMEM : DG_ECUDA, what, _e);      \
   } while (0)
 
+// Checked builds: report a recorded out-of-range gather index (synchronises).
+static dg_status adj_checked(Ctx* c, cudaStream_t s) {
+  char msg[160];
+  if (bounds_failed(s, msg, sizeof msg)) return afail(c, DG_ECUDA, msg);
+  return DG_OK;
+}
+
 static dg_status ensure_adjoint(Ctx* c) {
   if (c->d_adj_qbar) return DG_OK;
   if (c->prm.precision != DG_FP64) return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the FP64 operator");
@@ -235,7 +242,7 @@ dg_status dg_time_derivative_vjp(dg_ctx* ctx, const double* dU, const double* dv
   dg_status st = ensure_adjoint(c);
   if (st != DG_OK) return st;
   ADJ_CUDA(launch_vjp(*c, dU, dv, dout, dJdmu, 1.0, (cudaStream_t)stream), c, "vjp");
-  return DG_OK;
+  return adj_checked(c, (cudaStream_t)stream);
 }
 
 dg_status dg_adjoint_step(dg_ctx* ctx, const double* dU_n, const double* dlam_np1, double* dlam_n, double* dJdmu,
@@ -249,7 +256,8 @@ dg_status dg_adjoint_step(dg_ctx* ctx, const double* dU_n, const double* dlam_np
   if (st != DG_OK) return st;
   const size_t bytes = sizeof(double) * (size_t)c->E * 5 * c->P;
   if (dlam_n != dlam_np1) ADJ_CUDA(cudaMemcpyAsync(dlam_n, dlam_np1, bytes, cudaMemcpyDeviceToDevice, s), c, "copy");
-  return step_adjoint(c, dU_n, dlam_n, dJdmu, t, dt, s);
+  st = step_adjoint(c, dU_n, dlam_n, dJdmu, t, dt, s);
+  return st != DG_OK ? st : adj_checked(c, s);
 }
 
 dg_status dg_adjoint_solve(dg_ctx* ctx, const double* dU0, const double* dlamT, double* dlam0, double* dJdmu,
@@ -298,7 +306,7 @@ dg_status dg_adjoint_solve(dg_ctx* ctx, const double* dU0, const double* dlamT, 
   if (st != DG_OK) return st;
   if (es != cudaSuccess) return afail(c, DG_ECUDA, "dg_adjoint_solve: sync", es);
   if (host_counts2) { host_counts2[0] = forward; host_counts2[1] = adjoints; }
-  return DG_OK;
+  return adj_checked(c, s);
 }
 
 dg_status dg_checkpoint_schedule(int32_t nsteps, int32_t max_snapshots, int64_t* host_counts2) {

@@ -71,12 +71,39 @@ static void lgl_basis(int N, std::vector<double>& x, std::vector<double>& w, std
   }
 }
 
+bool bounds_failed(cudaStream_t s, char* msg, size_t len) {
+#ifdef DG_BOUNDS_CHECK
+  cudaStreamSynchronize(s);
+  const unsigned long long words[6] = {bounds_word_operator(), bounds_word_volume(), bounds_word_gauss(),
+                                       bounds_word_geometry(), bounds_word_adjoint(), bounds_word_ensemble()};
+  for (unsigned long long w : words)
+    if (w) {
+      long long idx = (long long)(w & 0xffffffffffffull);
+      if (idx & (1ll << 47)) idx -= (1ll << 48);   // sign of the recorded index
+      std::snprintf(msg, len, "bounds check: gather site %d read index %lld out of range",
+                    (int)((w >> 48) & 0x7fff), idx);
+      return true;
+    }
+#else
+  (void)s; (void)msg; (void)len;
+#endif
+  return false;
+}
+
 static dg_status fail(Ctx* c, dg_status st, const char* what, cudaError_t e = cudaSuccess) {
   char buf[512];
   if (e != cudaSuccess) std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
   else std::snprintf(buf, sizeof buf, "%s", what);
   if (c) c->err = buf; else g_init_error = buf;
   return st;
+}
+
+// Checked builds: report a recorded out-of-range gather index after the
+// call's launches (synchronises the stream); normal builds: DG_OK at once.
+static dg_status checked(Ctx* c, cudaStream_t s) {
+  char msg[160];
+  if (bounds_failed(s, msg, sizeof msg)) return fail(c, DG_ECUDA, msg);
+  return DG_OK;
 }
 
 #define DG_CUDA(call, ctx, what)                                   \
@@ -89,7 +116,7 @@ static dg_status fail(Ctx* c, dg_status st, const char* what, cudaError_t e = cu
 static void release(Ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
-  void* bufs[] = {c->d_D, c->d_metrics, c->d_J, c->d_X, c->d_mms, c->d_Uf, c->d_gf, c->d_lgb, c->d_facegeo, c->d_metrics_f, c->d_facegeo_f,
+  void* bufs[] = {c->d_modal, c->d_D, c->d_metrics, c->d_J, c->d_X, c->d_mms, c->d_Uf, c->d_gf, c->d_lgb, c->d_facegeo, c->d_metrics_f, c->d_facegeo_f,
                   c->d_grad, c->d_fstar, c->d_red, c->d_w, c->d_clock, c->d_U, c->d_G,
                   c->d_adj_qbar, c->d_adj_gbar, c->d_adj_gtil, c->d_adj_fseed, c->d_adj_face, c->d_adj_mu,
                   c->d_adj_stage, c->d_adj_work};
@@ -241,6 +268,7 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
       !alloc((void**)&c->d_fstar, sizeof(double) * c->nfaces * 5 * NN, "alloc fstar") ||
       !alloc((void**)&c->d_red, sizeof(double) * (red_rows + 1) * kRedValues, "alloc reduction") ||
       !alloc((void**)&c->d_w, sizeof(double) * c->n, "alloc w") ||
+      !alloc((void**)&c->d_modal, sizeof(double) * NN, "alloc modal table") ||
       !alloc((void**)&c->d_minmask, sizeof(int), "alloc mask") ||
       !alloc((void**)&c->d_clock, sizeof(double) * 2, "alloc clock") ||
       (prm->source == DG_SOURCE_MMS && !alloc((void**)&c->d_mms, sizeof(double) * E * 2 * P, "alloc source phases")) ||
@@ -257,10 +285,15 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
     fail(c, DG_ENOMEM, "dg_init: pinned host allocation failed");
     return bail(DG_ENOMEM);
   }
-  std::vector<double> gtab;
+  std::vector<double> gtab, modal;
   if (prm->nodes == DG_NODES_LG) {
-    gauss_table(c->N, c->x, gtab);
+    std::vector<double> gx;
+    gauss_table(c->N, c->x, gtab, &gx);
     c->dt_factor = gauss_dt_factor(c->N, c->x, c->w, c->D, gtab);
+    const std::vector<double> gw(gtab.begin() + 2 * NN + 4 * c->n, gtab.begin() + 2 * NN + 5 * c->n);
+    modal_table(c->N, gx, gw, false, modal);
+  } else {
+    modal_table(c->N, c->x, c->w, true, modal);
   }
   InitScratch tmp;
   if (cudaStreamCreateWithFlags(&tmp.s, cudaStreamNonBlocking) != cudaSuccess) {
@@ -288,6 +321,8 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
     err = cudaMemcpyAsync(c->d_w, c->w.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice, s);
   }
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_minmask, &minmask, sizeof(int), cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(c->d_modal, modal.data(), sizeof(double) * NN, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_faces, faces.data(), sizeof(FaceInfo) * c->nfaces, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_elem_face, elem_face.data(), sizeof(int) * E * 6, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_elem_nbr, elem_nbr.data(), sizeof(int) * E * 6, cudaMemcpyHostToDevice, s);
@@ -310,6 +345,13 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
   if (bad) {
     fail(c, DG_EMESH, "dg_init: non-positive Jacobian at a node");
     return bail(DG_EMESH);
+  }
+  {
+    char msg[160];
+    if (bounds_failed(s, msg, sizeof msg)) {
+      fail(c, DG_ECUDA, msg);
+      return bail(DG_ECUDA);
+    }
   }
   c->err = "no error";
   *out = c;
@@ -358,7 +400,7 @@ dg_status dg_time_derivative(dg_ctx* c, const double* dU, double* dUt, double t,
   DG_CUDA(launch_face(*c, dU, s), c, "face kernel");
   StageArgs a{dU, nullptr, nullptr, dUt, c->d_clock, 0.0, 0.0, 0.0, 0};
   DG_CUDA(launch_volume(*c, a, s), c, "volume kernel");
-  return DG_OK;
+  return checked(c, s);
 }
 
 dg_status dg_rk_step(dg_ctx* c, double* dU, double* dG, double t, double dt, int32_t nsteps, dg_stream stream) {
@@ -387,7 +429,7 @@ dg_status dg_rk_step(dg_ctx* c, double* dU, double* dG, double t, double dt, int
     c->graph_U = dU; c->graph_G = dG; c->graph_nsteps = nsteps;
   }
   DG_CUDA(cudaGraphLaunch(c->graph, s), c, "dg_rk_step: graph launch");
-  return DG_OK;
+  return checked(c, s);
 }
 
 dg_status dg_advance_host(dg_ctx* c, double* hU, double t, double dt, int32_t nsteps, dg_stream stream) {
@@ -414,6 +456,7 @@ dg_status dg_integrals(dg_ctx* c, const double* dU, double* out, dg_stream strea
   DG_CUDA(cudaMemcpyAsync(c->h_out, c->d_red + (size_t)rows * kRedValues, sizeof(double) * kRedValues,
                           cudaMemcpyDeviceToHost, s), c, "integrals copy");
   DG_CUDA(cudaStreamSynchronize(s), c, "integrals sync");
+  if (checked(c, s) != DG_OK) return DG_ECUDA;
   const double* h = c->h_out;
   for (int a = 0; a < 5; ++a) out[a] = h[a];
   const double vol = h[5];
@@ -445,6 +488,16 @@ dg_status dg_max_dt(dg_ctx* c, const double* dU, double cfl, double dfl, double*
   if (lv > 0.0) dt = std::fmin(dt, fa * fa * dfl * h * h / lv);
   *host_dt = dt;
   return DG_OK;
+}
+
+dg_status dg_indicator(dg_ctx* c, const double* dU, int32_t var, double log10_threshold, double* dEta,
+                       int32_t* dFlag, dg_stream stream) {
+  if (!c || !dU || !dEta) return fail(c, DG_EINVAL, "dg_indicator: null argument");
+  if (var < DG_IND_RHO || var > DG_IND_RHOP) return fail(c, DG_EINVAL, "dg_indicator: unknown indicator quantity");
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  DG_CUDA(launch_indicator(*c, dU, var, log10_threshold, dEta, dFlag, s), c, "indicator kernel");
+  return checked(c, s);
 }
 
 dg_status dg_initial_state(dg_ctx* c, int32_t kind, double prm0, double* dU, dg_stream stream) {

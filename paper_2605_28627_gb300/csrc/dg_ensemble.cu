@@ -43,11 +43,11 @@ struct MemberDev {
 // gridDim.x, ...; tile = (member, block index inside the member).
 template <int N, typename R, int EPB>
 __global__ void __launch_bounds__(Shape<N, EPB>::THREADS)
-k_lift_ens(const MemberDev<R>* __restrict__ mem, const int2* __restrict__ tiles, int ntiles,
+k_lift_ens(const MemberDev<R>* __restrict__ mem, int nmem, const int2* __restrict__ tiles, int ntiles,
            const double* __restrict__ Dg) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int2 tl = tiles[t];
-    const MemberDev<R>& m = mem[tl.x];
+    const MemberDev<R>& m = mem[dg_idx(tl.x, nmem, kSiteEnsMember)];
     lift_body<N, R, EPB>(m.U, m.metrics, m.elem_nbr, m.elem_face, Dg, m.grad, m.E, m.gas, m.inv_w0, tl.y);
     __syncthreads();
   }
@@ -55,21 +55,21 @@ k_lift_ens(const MemberDev<R>* __restrict__ mem, const int2* __restrict__ tiles,
 
 template <int N, typename R>
 __global__ void __launch_bounds__(128)
-k_face_ens(const MemberDev<R>* __restrict__ mem, const int2* __restrict__ tiles, int ntiles) {
+k_face_ens(const MemberDev<R>* __restrict__ mem, int nmem, const int2* __restrict__ tiles, int ntiles) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int2 tl = tiles[t];
-    const MemberDev<R>& m = mem[tl.x];
+    const MemberDev<R>& m = mem[dg_idx(tl.x, nmem, kSiteEnsMember)];
     face_body<N, R>(m.U, m.grad, m.faces, m.facegeo, m.fstar, m.F, m.gas, (long)tl.y * 128 + threadIdx.x);
   }
 }
 
 template <int N, typename R, int EPB>
 __global__ void __launch_bounds__(VShape<N, EPB>::THREADS)
-k_volume_ens(const MemberDev<R>* __restrict__ mem, const int2* __restrict__ tiles, int ntiles,
+k_volume_ens(const MemberDev<R>* __restrict__ mem, int nmem, const int2* __restrict__ tiles, int ntiles,
              const double* __restrict__ Dg, double c_stage, double A, double B) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int2 tl = tiles[t];
-    const MemberDev<R>& m = mem[tl.x];
+    const MemberDev<R>& m = mem[dg_idx(tl.x, nmem, kSiteEnsMember)];
     StageArgs a{m.U, m.U, m.G, nullptr, m.clock, c_stage, A, B, 1};
     volume_body<N, R, EPB>(a, m.metrics, m.metrics64, m.grad, m.fstar, m.elem_face, m.mms, Dg, m.E, m.gas,
                            m.inv_w0, tl.y);
@@ -128,15 +128,16 @@ static cudaError_t launch_group_stage(const Group& g, int k, const double* A, co
   const MemberDev<R>* mem = (const MemberDev<R>*)g.d_mem;
   const int ch = g.plan.epb_choice;
   // lifting always uses the default tile (its tile table is choice 0)
+  const int nmem = (int)g.members.size();
   k_lift_ens<N, R, e0><<<g.plan.lift_grid, Shape<N, e0>::THREADS, lift_smem_bytes<N, R, e0>(), s>>>(
-      mem, g.d_elem_tiles[0], g.n_elem_tiles[0], g.d_D);
-  k_face_ens<N, R><<<g.plan.face_grid, 128, 0, s>>>(mem, g.d_face_tiles, g.n_face_tiles);
+      mem, nmem, g.d_elem_tiles[0], g.n_elem_tiles[0], g.d_D);
+  k_face_ens<N, R><<<g.plan.face_grid, 128, 0, s>>>(mem, nmem, g.d_face_tiles, g.n_face_tiles);
   if (ch == 0)
     k_volume_ens<N, R, e0><<<g.plan.vol_grid, VShape<N, e0>::THREADS, volume_smem_bytes<N, R, e0>(), s>>>(
-        mem, g.d_elem_tiles[0], g.n_elem_tiles[0], g.d_D, C[k], A[k], B[k]);
+        mem, nmem, g.d_elem_tiles[0], g.n_elem_tiles[0], g.d_D, C[k], A[k], B[k]);
   else
     k_volume_ens<N, R, e1><<<g.plan.vol_grid, VShape<N, e1>::THREADS, volume_smem_bytes<N, R, e1>(), s>>>(
-        mem, g.d_elem_tiles[1], g.n_elem_tiles[1], g.d_D, C[k], A[k], B[k]);
+        mem, nmem, g.d_elem_tiles[1], g.n_elem_tiles[1], g.d_D, C[k], A[k], B[k]);
   return cudaGetLastError();
 }
 
@@ -201,6 +202,9 @@ static int epb_of_t(int N, int choice) {
 static int epb_of(int N, int choice, int precision) {
   return precision == DG_FP32OP ? epb_of_t<float>(N, choice) : epb_of_t<double>(N, choice);
 }
+
+// Host reader of this file's bounds-check error word (0 in normal builds).
+DG_BOUNDS_READER(bounds_word_ensemble)
 
 }  // namespace dg
 
@@ -700,6 +704,8 @@ dg_status dg_ensemble_step(dg_ensemble* e, double* const* dU, double* const* dG,
     e->graph_nsteps = nsteps;
   }
   ENS_CUDA(cudaGraphLaunch(e->graph, s), e, "ensemble graph launch");
+  char msg[160];
+  if (bounds_failed(s, msg, sizeof msg)) return ens_fail(e, DG_ECUDA, msg);   // checked builds only
   return DG_OK;
 }
 

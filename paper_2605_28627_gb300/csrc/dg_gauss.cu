@@ -45,7 +45,7 @@ static void legendre_pn(int n, double x, double& p, double& dp) {
 }
 
 // Host table of the Gauss basis of degree N; xl are the LGL nodes of degree N.
-void gauss_table(int N, const std::vector<double>& xl, std::vector<double>& tab) {
+void gauss_table(int N, const std::vector<double>& xl, std::vector<double>& tab, std::vector<double>* gx) {
   const int n = N + 1;
   std::vector<double> x(n), w(n), D((size_t)n * n), c(n), lm(n), lp(n);
   for (int k = 0; k < (n + 1) / 2; ++k) {
@@ -90,6 +90,7 @@ void gauss_table(int N, const std::vector<double>& xl, std::vector<double>& tab)
     lm[j] = a;
     lp[j] = b;
   }
+  if (gx) *gx = x;
   tab.assign(GaussTab::size(n), 0.0);
   for (int r = 0; r < n; ++r)
     for (int m = 0; m < n; ++m) tab[GaussTab::Dw(n) + r * n + m] = (w[m] / w[r]) * D[(size_t)m * n + r];
@@ -193,7 +194,7 @@ __global__ void k_face_geometry_lg(const FaceInfo* __restrict__ faces, const dou
   const int f = (int)(gid / NN), pq = (int)(gid % NN);
   const int p = pq % n, q = pq / n;
   const FaceInfo fi = faces[f];
-  const int e = fi.master >> 3, lf = fi.master & 7, d = lf >> 1;
+  const int e = dg_idx(fi.master >> 3, F / 3, kSiteGaussFace), lf = fi.master & 7, d = lf >> 1;
   const double sg = (lf & 1) ? 1.0 : -1.0;
   const double* V = tab + GaussTab::V(n);
   double nv[3] = {0.0, 0.0, 0.0};
@@ -380,7 +381,7 @@ k_lift_lg(const double* __restrict__ U, const double* __restrict__ Uf, const dou
     for (int o = id; o < 6 * NN; o += P) {
       const int f = o / NN, pq = o - f * NN, p = pq % n, q = pq / n;
       const int code = elem_face[e * 6 + f], nb = elem_nbr[e * 6 + f];
-      const int e2 = nb >> 3, f2 = nb & 7, fid = code >> 4;
+      const int e2 = dg_idx(nb >> 3, E, kSiteGaussLift), f2 = nb & 7, fid = dg_idx(code >> 4, 3L * E, kSiteGaussLift);
       int p2, q2;
       apply_flip<n>(code & 7, p, q, p2, q2);
       const int pq2 = p2 + n * q2;
@@ -474,7 +475,8 @@ k_face_lg(const double* __restrict__ Uf, const double* __restrict__ gf, const Fa
   const int f = (int)(gid / NN), pq = (int)(gid % NN);
   const int p = pq % n, q = pq / n;
   const FaceInfo fi = faces[f];
-  const int eM = fi.master >> 3, fM = fi.master & 7, eS = fi.slave >> 3, fS = fi.slave & 7;
+  const int eM = dg_idx(fi.master >> 3, F / 3, kSiteGaussFace), fM = fi.master & 7;
+  const int eS = dg_idx(fi.slave >> 3, F / 3, kSiteGaussFace), fS = fi.slave & 7;
   int p2, q2;
   apply_flip<n>(fi.flip, p, q, p2, q2);
   const int pq2 = p2 + n * q2;
@@ -556,7 +558,7 @@ k_volume_lg(StageArgs a, const double* __restrict__ metrics, const double* __res
     }
     for (int o = id; o < 30 * NN; o += P) {
       const int f = o / (5 * NN), r = o - f * 5 * NN, v2 = r / NN, pq = r - v2 * NN;
-      const int code = elem_face[e * 6 + f], fid = code >> 4;
+      const int code = elem_face[e * 6 + f], fid = dg_idx(code >> 4, 3L * E, kSiteGaussVol);
       double val;
       if (code & 8) {
         val = fstar[((size_t)fid * 5 + v2) * NN + pq];
@@ -721,5 +723,8 @@ cudaError_t launch_face_lg(const Ctx& c, cudaStream_t s) { DG_LG_DISPATCH(face_l
 cudaError_t launch_volume_lg(const Ctx& c, const StageArgs& a, cudaStream_t s) {
   DG_LG_DISPATCH(volume_lg_N, c, a, s)
 }
+
+// Host reader of this file's bounds-check error word (0 in normal builds).
+DG_BOUNDS_READER(bounds_word_gauss)
 
 }  // namespace dg

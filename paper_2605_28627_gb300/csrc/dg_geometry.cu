@@ -110,7 +110,7 @@ __global__ void k_face_geometry(const FaceInfo* __restrict__ faces, const double
   const int f = (int)(gid / NN), pq = (int)(gid % NN);
   const int p = pq % n, q = pq / n;
   const FaceInfo fi = faces[f];
-  const int e = fi.master >> 3, lf = fi.master & 7;
+  const int e = dg_idx(fi.master >> 3, F / 3, kSiteGeomFace), lf = fi.master & 7;   // F = 3 E
   const int d = lf >> 1;
   const double sg = (lf & 1) ? 1.0 : -1.0;
   const int node = face_node<n>(lf, p, q);
@@ -188,5 +188,8 @@ cudaError_t build_geometry(Ctx& c, const double* d_xgeo, int ngeo, int* d_bad, c
   cudaFree(d_V);
   return err != cudaSuccess ? err : e2;
 }
+
+// Host reader of this file's bounds-check error word (0 in normal builds).
+DG_BOUNDS_READER(bounds_word_geometry)
 
 }  // namespace dg

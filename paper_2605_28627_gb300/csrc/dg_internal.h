@@ -132,6 +132,7 @@ struct Ctx {
   double* d_red = nullptr;       // reduction partials [red_len + 1][9]; the last row holds the fold
   int red_len = 0;               // maximum number of partial rows
   double* d_w = nullptr;         // [n] quadrature weights of the node set
+  double* d_modal = nullptr;     // [n][n] nodal -> orthonormal Legendre modes of the node set (indicator)
   int* d_minmask = nullptr;      // bit a set: value a of the integrals is a minimum
   double* d_clock = nullptr;     // {t, dt}
   double* h_clock = nullptr;     // pinned staging for the clock
@@ -162,8 +163,8 @@ cudaError_t launch_lift_fp64(const Ctx& c, const double* U, cudaStream_t s);   /
 cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s);
 cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s);
 cudaError_t setup_kernels(int N);
-// Gauss-node operator (dg_gauss.cu)
-void gauss_table(int N, const std::vector<double>& xl, std::vector<double>& tab);
+// Gauss-node operator (dg_gauss.cu); gx (may be NULL) receives the Gauss nodes
+void gauss_table(int N, const std::vector<double>& xl, std::vector<double>& tab, std::vector<double>* gx = nullptr);
 double gauss_dt_factor(int N, const std::vector<double>& xl, const std::vector<double>& wl,
                        const std::vector<double>& Dl, const std::vector<double>& tab);
 cudaError_t setup_gauss(int N);
@@ -172,6 +173,12 @@ cudaError_t launch_lift_lg(const Ctx& c, const double* U, cudaStream_t s);
 cudaError_t launch_face_lg(const Ctx& c, cudaStream_t s);
 cudaError_t launch_volume_lg(const Ctx& c, const StageArgs& a, cudaStream_t s);
 cudaError_t setup_volume(int N);
+
+// Modal troubled-cell indicator (dg_indicator.cu).
+void modal_table(int N, const std::vector<double>& x, const std::vector<double>& w, bool lobatto,
+                 std::vector<double>& T);
+cudaError_t launch_indicator(const Ctx& c, const double* U, int var, double log_thresh, double* eta, int* flag,
+                             cudaStream_t s);
 
 // Geometry kernels (dg_geometry.cu).
 cudaError_t build_geometry(Ctx& c, const double* d_xgeo, int ngeo, int* d_bad, cudaStream_t s);
@@ -194,5 +201,19 @@ cudaError_t launch_vjp(const Ctx& c, const double* U, const double* lam, double*
 cudaError_t launch_axpby(double* y, const double* x, double a, double b, size_t len, cudaStream_t s);
 cudaError_t launch_kinetic(const Ctx& c, const double* U, double* grad, double* d_out, cudaStream_t s);
 constexpr int kRedValues = 9;
+
+// Bounds checks of the indirect gathers (dg_check.cuh): each file with such
+// gathers keeps its own error word; the readers return it and clear it (0 in
+// normal builds).
+unsigned long long bounds_word_adjoint();
+unsigned long long bounds_word_ensemble();
+unsigned long long bounds_word_gauss();
+unsigned long long bounds_word_geometry();
+unsigned long long bounds_word_operator();
+unsigned long long bounds_word_volume();
+// Checked builds: wait for the work on stream s and describe the first
+// recorded out-of-range index in msg; returns true if there was one.  Normal
+// builds: returns false at once.
+bool bounds_failed(cudaStream_t s, char* msg, size_t len);
 
 }  // namespace dg

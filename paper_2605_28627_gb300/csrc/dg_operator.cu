@@ -108,4 +108,7 @@ cudaError_t setup_kernels(int N) {
   return e == cudaSuccess ? setup_gauss(N) : e;
 }
 
+// Host reader of this file's bounds-check error word (0 in normal builds).
+DG_BOUNDS_READER(bounds_word_operator)
+
 }  // namespace dg

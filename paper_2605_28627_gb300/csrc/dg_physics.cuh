@@ -2,6 +2,7 @@
 // (GALAEXI Sec. 3.1, Eq. 1), templated on the operator arithmetic type.
 #pragma once
 
+#include "dg_check.cuh"
 #include "dg_internal.h"
 
 namespace dg {

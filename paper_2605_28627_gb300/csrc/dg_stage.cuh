@@ -168,7 +168,8 @@ __device__ __forceinline__ void lift_body(const double* __restrict__ U, const R*
       const int code = elem_face[e2 * 6 + f], nb = elem_nbr[e2 * 6 + f];
       int p2, q2;
       apply_flip<n>(code & 7, pq % n, pq / n, p2, q2);
-      const double* q = U + (size_t)(nb >> 3) * 5 * P + face_node<n>(nb & 7, p2, q2);
+      const int enb = dg_idx(nb >> 3, E, kSiteLiftNbr);
+      const double* q = U + (size_t)enb * 5 * P + face_node<n>(nb & 7, p2, q2);
 #pragma unroll
       for (int v = 0; v < 5; ++v) qv[v] = q[v * P];
     }
@@ -341,7 +342,9 @@ __device__ __forceinline__ void face_body(const double* __restrict__ U, const R*
   const int f = (int)(gid / NN), pq = (int)(gid % NN);
   const int p = pq % n, q = pq / n;
   const FaceInfo fi = faces[f];
-  const int eM = fi.master >> 3, fM = fi.master & 7, eS = fi.slave >> 3, fS = fi.slave & 7;
+  // every local face of a periodic mesh has a neighbour: F = 3 E
+  const int eM = dg_idx(fi.master >> 3, F / 3, kSiteFaceElems), fM = fi.master & 7;
+  const int eS = dg_idx(fi.slave >> 3, F / 3, kSiteFaceElems), fS = fi.slave & 7;
   int p2, q2;
   apply_flip<n>(fi.flip, p, q, p2, q2);
   const int idM = face_node<n>(fM, p, q), idS = face_node<n>(fS, p2, q2);
@@ -509,7 +512,9 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
       if constexpr (sizeof(R) == 8) l2_prefetch(iJ64 + (size_t)e * 10 * P + 9 * P, P * sizeof(double));
       else l2_prefetch(metrics + (size_t)e * 10 * P + 9 * P, P * sizeof(R));
     } else if (id == 2 && g.source == DG_SOURCE_MMS) l2_prefetch(mms + (size_t)e * 2 * P, 2 * P * sizeof(double));
-    else if (id >= 3) l2_prefetch(fstar + (size_t)(elem_face[e * 6 + id - 3] >> 4) * 5 * NN, 5 * NN * sizeof(R));
+    else if (id >= 3)
+      l2_prefetch(fstar + (size_t)dg_idx(elem_face[e * 6 + id - 3] >> 4, 3L * E, kSiteVolFace) * 5 * NN,
+                  5 * NN * sizeof(R));
   }
   const R inv_w0 = to_op<R>(inv_w0d);
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
@@ -745,7 +750,7 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     if (id_d != 0 && id_d != N) continue;
     const int sgn = id_d == N ? 1 : 0;
     const int code = elem_face[e * 6 + 2 * d + sgn];
-    const int fid = code >> 4;
+    const int fid = dg_idx(code >> 4, 3L * E, kSiteVolFace);   // F = 3 E
     const int pp = d == 0 ? j : i;
     const int qq = d == 2 ? j : k;
     const R* fsr;

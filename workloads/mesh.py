@@ -100,7 +100,7 @@ def _local_lattice(R, ngeo):
 
 def box_mesh(K: int, ngeo: int, lo: float = -1.0, hi: float = 1.0,
              deform: str | None = None, amp: float = 0.1,
-             rotate_seed: int | None = None) -> Mesh:
+             rotate_seed: int | None = None, dims: tuple | None = None) -> Mesh:
     """Periodic ``K^3`` box mesh on ``[lo, hi]^3``.
 
     deform: None (Cartesian) or ``"sinprod"``: every coordinate is displaced by
@@ -108,10 +108,13 @@ def box_mesh(K: int, ngeo: int, lo: float = -1.0, hi: float = 1.0,
     ``[-1, 1]^3`` (zero on the box faces, so periodic faces still match).
     rotate_seed: None (identity frames) or the seed of each element's random
     proper rotation.
+    dims: (Kx, Ky, Kz) elements per direction instead of K^3 (e.g. (2, 1, 1):
+    two elements, each its own neighbour across its y and z faces).
     """
-    if K < 1 or ngeo < 1:
+    Kd = tuple(int(k) for k in dims) if dims is not None else (K, K, K)
+    if min(Kd) < 1 or ngeo < 1:
         raise ValueError("K and ngeo must be >= 1")
-    E = K ** 3
+    E = Kd[0] * Kd[1] * Kd[2]
     n = ngeo + 1
     if rotate_seed is None:
         rot = np.zeros(E, dtype=np.int64)
@@ -119,11 +122,11 @@ def box_mesh(K: int, ngeo: int, lo: float = -1.0, hi: float = 1.0,
         rot[:] = ident
     else:
         rot = np.random.default_rng(rotate_seed).integers(0, 24, size=E)
-    L = K * ngeo
+    L = (np.array(Kd) * ngeo)[None, :, None, None, None]
     xgeo = np.empty((E, 3, n, n, n), dtype=np.float64)
     offs = [_local_lattice(R, ngeo) for R in ROTATIONS]
     eidx = np.arange(E)
-    corner = np.stack([eidx % K, (eidx // K) % K, eidx // (K * K)], 1) * ngeo
+    corner = np.stack([eidx % Kd[0], (eidx // Kd[0]) % Kd[1], eidx // (Kd[0] * Kd[1])], 1) * ngeo
     for r in np.unique(rot):
         sel = np.nonzero(rot == r)[0]
         lat = offs[r][None] + corner[sel][:, :, None, None, None]
@@ -135,8 +138,8 @@ def box_mesh(K: int, ngeo: int, lo: float = -1.0, hi: float = 1.0,
         elif deform is not None:
             raise ValueError(deform)
         xgeo[sel] = y
-    face_nbr = _connectivity(K, rot)
-    return Mesh(K=K, ngeo=ngeo, lo=lo, hi=hi, xgeo=xgeo, face_nbr=face_nbr, rot=rot)
+    face_nbr = _connectivity(Kd, rot)
+    return Mesh(K=Kd[0], ngeo=ngeo, lo=lo, hi=hi, xgeo=xgeo, face_nbr=face_nbr, rot=rot)
 
 
 def _face_lattice_points(R, d, s, ec, t):
@@ -193,13 +196,14 @@ def _orientation_table():
 _ORIENT = None
 
 
-def _connectivity(K: int, rot: np.ndarray) -> np.ndarray:
+def _connectivity(Kd, rot: np.ndarray) -> np.ndarray:
     global _ORIENT
     if _ORIENT is None:
         _ORIENT = _orientation_table()
-    E = K ** 3
+    Kd = np.array(Kd)
+    E = int(Kd.prod())
     e = np.arange(E)
-    ec = np.stack([e % K, (e // K) % K, e // (K * K)], 1)
+    ec = np.stack([e % Kd[0], (e // Kd[0]) % Kd[1], e // (Kd[0] * Kd[1])], 1)
     nbr = np.zeros((E, 6, 3), dtype=np.int32)
     Rs = np.stack(ROTATIONS)                      # [24, 3, 3]
     for f in range(6):
@@ -208,8 +212,8 @@ def _connectivity(K: int, rot: np.ndarray) -> np.ndarray:
         gax = np.argmax(np.abs(col), axis=1)
         gsg = col[np.arange(E), gax] * (2 * s - 1)
         ec2 = ec.copy()
-        ec2[np.arange(E), gax] = (ec2[np.arange(E), gax] + gsg) % K
-        e2 = ec2[:, 0] + K * (ec2[:, 1] + K * ec2[:, 2])
+        ec2[np.arange(E), gax] = (ec2[np.arange(E), gax] + gsg) % Kd[gax]
+        e2 = ec2[:, 0] + Kd[0] * (ec2[:, 1] + Kd[1] * ec2[:, 2])
         ft = _ORIENT[rot, f, rot[e2]]
         nbr[:, f, 0] = e2
         nbr[:, f, 1] = ft[:, 0]
