@@ -74,8 +74,9 @@ static void lgl_basis(int N, std::vector<double>& x, std::vector<double>& w, std
 bool bounds_failed(cudaStream_t s, char* msg, size_t len) {
 #ifdef DG_BOUNDS_CHECK
   cudaStreamSynchronize(s);
-  const unsigned long long words[6] = {bounds_word_operator(), bounds_word_volume(), bounds_word_gauss(),
-                                       bounds_word_geometry(), bounds_word_adjoint(), bounds_word_ensemble()};
+  const unsigned long long words[7] = {bounds_word_operator(), bounds_word_volume(), bounds_word_gauss(),
+                                       bounds_word_geometry(), bounds_word_adjoint(), bounds_word_ensemble(),
+                                       bounds_word_latency()};
   for (unsigned long long w : words)
     if (w) {
       long long idx = (long long)(w & 0xffffffffffffull);

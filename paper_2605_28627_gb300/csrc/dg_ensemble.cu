@@ -303,10 +303,10 @@ static cudaError_t one_member_stage(dg_ensemble* e, int r, int k, const double* 
   const Ctx& c = *e->members[r];
   double* U = e->cur_U[r];
   cudaError_t err;
-  if ((err = launch_lift(c, U, s)) != cudaSuccess) return err;
-  if ((err = launch_face(c, U, s)) != cudaSuccess) return err;
+  if ((err = launch_lift(c, U, s, false)) != cudaSuccess) return err;
+  if ((err = launch_face(c, U, s, false)) != cudaSuccess) return err;
   StageArgs a{U, U, e->cur_G[r], nullptr, e->clocks + 2 * r, kRkC[k], A[k], B[k], 1};
-  return launch_volume(c, a, s);
+  return launch_volume(c, a, s, false);
 }
 
 static cudaError_t member_stage(dg_ensemble* e, const Group& g, int k, const double* A, const double* B,

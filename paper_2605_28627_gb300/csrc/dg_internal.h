@@ -157,11 +157,21 @@ struct Ctx {
   std::string err;
 };
 
-// Launchers implemented per polynomial degree (dg_operator.cu).
-cudaError_t launch_lift(const Ctx& c, const double* U, cudaStream_t s);
+// Launchers implemented per polynomial degree (dg_operator.cu).  With
+// latency_ok the FP64 lifting and volume launchers take the latency kernels
+// (dg_latency.cu) for meshes too small to fill the GPU; the ensemble passes
+// false, so its results do not depend on its tuned plan.
+cudaError_t launch_lift(const Ctx& c, const double* U, cudaStream_t s, bool latency_ok = true);
 cudaError_t launch_lift_fp64(const Ctx& c, const double* U, cudaStream_t s);   // diagnostics: always FP64
-cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s);
-cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s, bool latency_ok = true);
+cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s, bool latency_ok = true);
+// Latency kernels (dg_latency.cu): FP64, LGL, N <= 3, E (N+1)^3 <= kLatencyNodes.
+constexpr long kLatencyNodes = 16384;
+bool use_latency_kernels(const Ctx& c);
+cudaError_t setup_latency(int N);
+cudaError_t launch_lift_lat(const Ctx& c, const double* U, cudaStream_t s);
+cudaError_t launch_volume_lat(const Ctx& c, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_face_lat(const Ctx& c, const double* U, cudaStream_t s);   // LLF surface flux only
 cudaError_t setup_kernels(int N);
 // Gauss-node operator (dg_gauss.cu); gx (may be NULL) receives the Gauss nodes
 void gauss_table(int N, const std::vector<double>& xl, std::vector<double>& tab, std::vector<double>* gx = nullptr);
@@ -209,6 +219,7 @@ unsigned long long bounds_word_adjoint();
 unsigned long long bounds_word_ensemble();
 unsigned long long bounds_word_gauss();
 unsigned long long bounds_word_geometry();
+unsigned long long bounds_word_latency();
 unsigned long long bounds_word_operator();
 unsigned long long bounds_word_volume();
 // Checked builds: wait for the work on stream s and describe the first

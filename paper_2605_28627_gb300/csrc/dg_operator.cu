@@ -68,16 +68,19 @@ static cudaError_t face_N(const Ctx& c, const double* U, cudaStream_t s) {
 
 // On Gauss nodes the lifting launcher also computes the face values of U
 // first (k_prolong_lg), and the face kernel works on face values.
-cudaError_t launch_lift(const Ctx& c, const double* U, cudaStream_t s) {
+cudaError_t launch_lift(const Ctx& c, const double* U, cudaStream_t s, bool latency_ok) {
   if (c.prm.nodes == DG_NODES_LG) return launch_lift_lg(c, U, s);
+  if (latency_ok && use_latency_kernels(c)) return launch_lift_lat(c, U, s);
   DG_DISPATCH(lift_N, c, U, c.prm.precision != DG_FP32OP, s)
 }
 cudaError_t launch_lift_fp64(const Ctx& c, const double* U, cudaStream_t s) {
   if (c.prm.nodes == DG_NODES_LG) return launch_lift_lg(c, U, s);
+  if (use_latency_kernels(c)) return launch_lift_lat(c, U, s);
   DG_DISPATCH(lift_N, c, U, true, s)
 }
-cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s) {
+cudaError_t launch_face(const Ctx& c, const double* U, cudaStream_t s, bool latency_ok) {
   if (c.prm.nodes == DG_NODES_LG) return launch_face_lg(c, s);
+  if (latency_ok && use_latency_kernels(c) && c.prm.surf_flux == DG_FLUX_LLF) return launch_face_lat(c, U, s);
   DG_DISPATCH(face_N, c, U, s)
 }
 template <int N>
@@ -105,6 +108,7 @@ cudaError_t setup_kernels(int N) {
     default: return cudaErrorInvalidValue;
   }
   if (e == cudaSuccess) e = setup_volume(N);
+  if (e == cudaSuccess) e = setup_latency(N);
   return e == cudaSuccess ? setup_gauss(N) : e;
 }
 

@@ -46,8 +46,9 @@ static cudaError_t setup_any() {
   return e != cudaSuccess ? e : volume2_setup<N, float>();
 }
 
-cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s) {
+cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s, bool latency_ok) {
   if (c.prm.nodes == DG_NODES_LG) return launch_volume_lg(c, a, s);
+  if (latency_ok && use_latency_kernels(c)) return launch_volume_lat(c, a, s);
   switch (c.N) {
     case 1: return volume_any<1>(c, a, s);
     case 2: return volume_any<2>(c, a, s);

@@ -1,6 +1,7 @@
 """Batched ensemble: every member advanced by the tile-table kernels against
 the oracle's LSERK4-5 steps at the FP64 bar, and against the single-context
-path bit for bit (the ensemble kernels run the same per-element arithmetic)."""
+path bit for bit (the ensemble kernels run the same per-element arithmetic;
+small FP64 runs alone take the latency kernels, which agree to rounding)."""
 import math
 import os
 
@@ -94,7 +95,12 @@ def test_ensemble_matches_single_runs_bitwise(dg, tmp_path, precision):
         G = torch.empty_like(ref)
         s.rk_step(ref, G, t, dt, 3)
         torch.cuda.synchronize()
-        assert torch.equal(U, ref)
+        if precision == 0 and s.N <= 3 and s.E * s.P <= 16384:
+            # a small FP64 run alone takes the latency kernels, whose sums are
+            # grouped by direction: the same to rounding, not bit for bit
+            assert ((U - ref).abs().max() / ref.abs().max()).item() < 1e-13
+        else:
+            assert torch.equal(U, ref)
     plan = ens.plan()
     assert plan is not None and len(plan["groups"]) == len({m["N"] for m in MEMBERS})
     assert os.path.exists(cache)

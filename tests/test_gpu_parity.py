@@ -88,6 +88,58 @@ def test_time_derivative_parity_random_state(orc, dg, N, flux):
     assert (err < RTOL_R * _geo_amp(orc, N, N)).all(), err
 
 
+def latency_kernels(N, n_elems, precision=0, nodes=0):
+    """Whether the library runs this context with its latency kernels (FP64,
+    LGL nodes, N <= 3, at most 16384 nodes): the rule of use_latency_kernels
+    in the library."""
+    return precision == 0 and nodes == 0 and N <= 3 and n_elems * (N + 1) ** 3 <= 16384
+
+
+@pytest.mark.parametrize("N,K", [(1, 13), (2, 9), (3, 7)])
+@pytest.mark.parametrize("flux", [0, 2])
+def test_time_derivative_parity_above_latency_threshold(orc, dg, N, K, flux):
+    """The one-thread-per-node kernels at N <= 3: meshes just above the node
+    count below which the latency kernels take over (the small meshes of the
+    other tests run those), with a ragged last block."""
+    mesh = box_mesh(K, N, deform="sinprod", rotate_seed=230 + N)
+    assert not latency_kernels(N, mesh.n_elems)
+    o, s = _pair(orc, dg, mesh, N, mu=0.02, surf_flux=flux)
+    U = random_state(mesh.n_elems, N, seed=330 + N)
+    err = _rel_err_per_var(s.time_derivative(_cuda(U)).cpu().numpy(), o.time_derivative(U, t=0.0))
+    assert (err < RTOL_R).all(), err
+    if flux != 0:
+        return
+    # ten RK steps
+    dt = 2e-4
+    Ud = _cuda(U)
+    G = torch.empty_like(Ud)
+    s.rk_step(Ud, G, 0.0, dt, 10)
+    ref = o.rk_steps(U, 0.0, dt, 10)
+    assert np.abs(Ud.cpu().numpy() - ref).max() / np.abs(ref).max() < RTOL_RK
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_latency_kernels_sutherland_and_mms(orc, dg, N):
+    """The latency kernels (small meshes) with Sutherland's law and with the
+    manufactured source, R(U) and RK steps against the oracle."""
+    mesh = box_mesh(2, N, deform="sinprod", rotate_seed=240 + N)
+    assert latency_kernels(N, mesh.n_elems)
+    kw = dict(mu=0.03, visc_law=1, T_ref=1.0, S_suth=0.4)
+    o, s = _pair(orc, dg, mesh, N, **kw)
+    U = random_state(mesh.n_elems, N, seed=340 + N)
+    err = _rel_err_per_var(s.time_derivative(_cuda(U)).cpu().numpy(), o.time_derivative(U))
+    assert (err < RTOL_R).all(), err
+    prm = mms_params()
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1)
+    o, s = _pair(orc, dg, mesh, N, **kw)
+    U = o.initial_state("mms", 0.1)
+    Ud = _cuda(U)
+    G = torch.empty_like(Ud)
+    s.rk_step(Ud, G, 0.1, 1e-3, 10)
+    ref = o.rk_steps(U, 0.1, 1e-3, 10)
+    assert np.abs(Ud.cpu().numpy() - ref).max() / np.abs(ref).max() < RTOL_RK
+
+
 @pytest.mark.parametrize("N", [2, 3, 5])
 def test_time_derivative_parity_mms_source(orc, dg, N):
     prm = mms_params()
