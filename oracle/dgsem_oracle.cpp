@@ -253,6 +253,7 @@ struct Ctx {
   int nfaces;
   std::vector<double> fn;     // [face][3][n*n]  unit normal of the master side
   std::vector<double> fsJ;    // [face][n*n]     surface element of the master side
+  std::vector<int> fv_mask;   // [e] 1: FV sub-cell element (empty: none)
   std::string err;
 };
 
@@ -723,6 +724,25 @@ static void volume_viscous(const Ctx& c, int e, const Prim<T>* W, const T* G, T 
 }
 
 // ---------------------------------------------------------------------------
+// FV sub-cell shock capturing (Sec. 3.1: a 2nd-order FV operator on (N+1)^3
+// sub-cells replaces the DG operator of troubled elements), FP64 only.  The
+// data of one evaluation; the functions follow the Gauss section below.
+struct FVData {
+  int n = 0;
+  double h = 0.0;                  // sub-cell width 2/n in reference space
+  std::vector<double> V, Vi;       // [n][n]: J-weighted means of the nodal interpolant, its inverse
+  std::vector<double> L;           // [n+1][n]: LGL Lagrange values at the sub-cell planes
+  std::vector<double> Jb;          // [e][P]: sub-cell mean of J (sub-cell volume / h^3)
+  std::vector<double> Ub;          // [e][5][P]: sub-cell means of U
+  std::vector<double> Gb;          // [e][12][P]: sub-cell means of the lifted gradients
+  std::vector<double> S;           // [e][d][plane][n*n][3]: sub-face area vectors (+xi_d)
+  std::vector<double> Fb;          // [face][n*n][5]: master-outward flux of each boundary sub-face
+};
+static void fv_prepare(const Ctx& c, const double* U, const double* G, FVData& fv);
+static void fv_faces(const Ctx& c, FVData& fv, double* Fs);
+static void fv_elements(const Ctx& c, const FVData& fv, double* Ut, double t);
+
+// ---------------------------------------------------------------------------
 // U_t = R(U): BR1 lifting, face fluxes, split-form volume integral, surface
 // integral and Jacobian scaling (Sec. 3.1, Eqs. 2-3), in strong form:
 //   g_l = (1/J) [ sum_d Ja^d_l d_d phi + sum_faces (phi* - phi) (n_l sJ) / w_end ]
@@ -790,9 +810,21 @@ static void rhs(const Ctx& c, const T* U, T* Ut, double t, T mu) {
             Fs[((size_t)fid * 5 + v) * nn + p + n * q] = (fa[v] - 0.5 * (fvL[v] + fvR[v])) * sJ;
         }
     }
+  // --- FV sub-cell elements: faces with an FV side take the sub-face fluxes
+  // (on a DG side converted to face nodes), flagged elements the FV residual
+  bool use_fv = false;
+  FVData fv;
+  if constexpr (std::is_same<T, double>::value) {
+    use_fv = !c.fv_mask.empty();
+    if (use_fv) {
+      fv_prepare(c, U, G.data(), fv);
+      fv_faces(c, fv, Fs.data());
+    }
+  }
   // --- volume integral, surface integral, Jacobian
 #pragma omp parallel for schedule(dynamic, 2) if (kParallel<T>)
   for (int e = 0; e < E; ++e) {
+    if (use_fv && c.fv_mask[e]) continue;
     std::vector<T> acc((size_t)5 * P, T(0.0));
     volume_advective(c, e, &W[(size_t)e * P], acc.data());
     volume_viscous(c, e, &W[(size_t)e * P], &G[(size_t)e * 12 * P], mu, acc.data());
@@ -833,6 +865,9 @@ static void rhs(const Ctx& c, const T* U, T* Ut, double t, T mu) {
       for (int v = 0; v < 5; ++v)
         Ut[((size_t)e * 5 + v) * P + id] = -acc[(size_t)v * P + id] / c.J[(size_t)e * P + id] + Qs[v];
     }
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    if (use_fv) fv_elements(c, fv, Ut, t);
   }
 }
 
@@ -1272,6 +1307,333 @@ static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double m
 }
 
 // Lifted gradients on either node set (test hook and diagnostics).
+// ---------------------------------------------------------------------------
+// FV sub-cell operator (Sec. 3.1; readings F1-F9 in the design notes).
+//  F1 sub-cells: the n^3 = (N+1)^3 equal sub-cubes of the reference element,
+//     width h = 2/n; sub-cells and sub-faces are indexed like nodes and face
+//     nodes (the same flip codes map sub-faces across element faces).
+//  F2 unknowns: J-weighted sub-cell means of the nodal interpolant,
+//     ub = V3 (J u) / V3 J with V[i][j] = (1/h) int_{cell i} l_j (exact,
+//     Gauss quadrature); V3 = V (x) V (x) V is invertible, so nodal values and
+//     means map one to one and the element integrals agree.
+//  F3 sub-face area vectors: S = int over the sub-face of J a^d, exact for the
+//     metric polynomial (interpolated to the plane along d, means across):
+//     each sub-cell's surface closes exactly (curl-form metrics), which keeps
+//     free streams.
+//  F4 reconstruction: primitive (rho, u, v, w, p) of the means, slopes along
+//     each reference direction by minmod of the two one-sided differences of
+//     neighbouring sub-cells (across element faces the neighbour element's
+//     sub-cell), face values w +- slope/2.
+//  F5 sub-face flux: local Lax-Friedrichs in the unit direction S/|S| of the
+//     reconstructed states, minus the average of the two sub-cells' viscous
+//     fluxes (means of the state and of the BR1-lifted gradients), times |S|.
+//  F6 residual: dub/dt = -(sum of the sub-cell's outward sub-face fluxes) /
+//     (Jb h^3); back to nodes by the inverse means map, J R = V3^-1 (Jb Rb),
+//     plus the manufactured source at the nodes.
+//  F7 element faces with an FV side are evaluated on sub-faces (both sides'
+//     means and slopes, the master's area vectors); an FV side uses the
+//     sub-face fluxes, a DG side their nodal form F* = (V (x) V)^-1 (Fb / h^2),
+//     whose integral over the face equals the sub-face fluxes' sum.
+
+// Gauss-Legendre rule of n points on [-1, 1].
+static void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    double t = std::cos(M_PI * (k + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre_p(n, t, P, dP);
+      const double step = P / dP;
+      t -= step;
+      if (std::fabs(step) < 1e-16) break;
+    }
+    double P, dP;
+    legendre_p(n, t, P, dP);
+    x[k] = t;
+    w[k] = 2.0 / ((1.0 - t * t) * dP * dP);
+  }
+}
+
+// Inverse of a small dense matrix by Gauss-Jordan elimination with partial pivoting.
+static std::vector<double> invert_small(int n, const std::vector<double>& A0) {
+  std::vector<double> A((size_t)n * 2 * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) A[(size_t)i * 2 * n + j] = A0[(size_t)i * n + j];
+    A[(size_t)i * 2 * n + n + i] = 1.0;
+  }
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * 2 * n + col]) > std::fabs(A[(size_t)piv * 2 * n + col])) piv = r;
+    for (int k = 0; k < 2 * n; ++k) std::swap(A[(size_t)col * 2 * n + k], A[(size_t)piv * 2 * n + k]);
+    const double dgl = A[(size_t)col * 2 * n + col];
+    for (int k = 0; k < 2 * n; ++k) A[(size_t)col * 2 * n + k] /= dgl;
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double f = A[(size_t)r * 2 * n + col];
+      for (int k = 0; k < 2 * n; ++k) A[(size_t)r * 2 * n + k] -= f * A[(size_t)col * 2 * n + k];
+    }
+  }
+  std::vector<double> B((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) B[(size_t)i * n + j] = A[(size_t)i * 2 * n + n + j];
+  return B;
+}
+
+// out = (M x M x M) in on n^3 values, i fastest.
+static void apply3(int n, const std::vector<double>& M, const double* in, double* out) {
+  const int P = n * n * n;
+  std::vector<double> t1(P), t2(P);
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int a = 0; a < n; ++a) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += M[(size_t)a * n + i] * in[vidx(n, i, j, k)];
+        t1[vidx(n, a, j, k)] = s;
+      }
+  for (int k = 0; k < n; ++k)
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) s += M[(size_t)b * n + j] * t1[vidx(n, a, j, k)];
+        t2[vidx(n, a, b, k)] = s;
+      }
+  for (int c3 = 0; c3 < n; ++c3)
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += M[(size_t)c3 * n + k] * t2[vidx(n, a, b, k)];
+        out[vidx(n, a, b, c3)] = s;
+      }
+}
+
+// The means matrix V, its inverse and the Lagrange values at the sub-cell planes.
+static void fv_matrices(const Ctx& c, FVData& fv) {
+  const int n = c.n;
+  fv.n = n;
+  fv.h = 2.0 / n;
+  std::vector<double> gx, gw;
+  gauss_rule(n, gx, gw);
+  fv.V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const double a = -1.0 + i * fv.h;
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int q = 0; q < n; ++q) s += gw[q] * lagrange(c.b.x, j, a + 0.5 * fv.h * (1.0 + gx[q]));
+      fv.V[(size_t)i * n + j] = 0.5 * s;   // (1/h) (h/2) sum_q w_q l_j
+    }
+  }
+  fv.Vi = invert_small(n, fv.V);
+  fv.L.assign((size_t)(n + 1) * n, 0.0);
+  for (int pl = 0; pl <= n; ++pl)
+    for (int m = 0; m < n; ++m) fv.L[(size_t)pl * n + m] = lagrange(c.b.x, m, -1.0 + pl * fv.h);
+}
+
+static void fv_prepare(const Ctx& c, const double* U, const double* G, FVData& fv) {
+  fv_matrices(c, fv);
+  const int n = c.n, P = c.P, E = c.E, nn = n * n;
+  fv.Jb.assign((size_t)E * P, 0.0);
+  fv.Ub.assign((size_t)E * 5 * P, 0.0);
+  fv.Gb.assign((size_t)E * 12 * P, 0.0);
+  fv.S.assign((size_t)E * 3 * (n + 1) * nn * 3, 0.0);
+  std::vector<double> tmp(P), out(P);
+  for (int e = 0; e < E; ++e) {
+    const double* J = &c.J[(size_t)e * P];
+    apply3(n, fv.V, J, &fv.Jb[(size_t)e * P]);
+    for (int v = 0; v < 17; ++v) {
+      const double* src = v < 5 ? &U[((size_t)e * 5 + v) * P] : &G[((size_t)e * 12 + v - 5) * P];
+      for (int id = 0; id < P; ++id) tmp[id] = J[id] * src[id];
+      apply3(n, fv.V, tmp.data(), out.data());
+      double* dst = v < 5 ? &fv.Ub[((size_t)e * 5 + v) * P] : &fv.Gb[((size_t)e * 12 + v - 5) * P];
+      for (int id = 0; id < P; ++id) dst[id] = out[id] / fv.Jb[(size_t)e * P + id];
+    }
+    // sub-face area vectors: J a^d at the plane (along d), means across, times h^2
+    for (int d = 0; d < 3; ++d)
+      for (int pl = 0; pl <= n; ++pl)
+        for (int l = 0; l < 3; ++l) {
+          std::vector<double> T((size_t)nn);
+          for (int b = 0; b < n; ++b)
+            for (int a = 0; a < n; ++a) {
+              double s = 0.0;
+              for (int m = 0; m < n; ++m)
+                s += fv.L[(size_t)pl * n + m] * c.Ja[(((size_t)e * 3 + d) * 3 + l) * P + line_node(n, d, m, a, b)];
+              T[a + n * b] = s;
+            }
+          for (int b = 0; b < n; ++b)
+            for (int a = 0; a < n; ++a) {
+              double s = 0.0;
+              for (int q = 0; q < n; ++q)
+                for (int p = 0; p < n; ++p) s += fv.V[(size_t)a * n + p] * fv.V[(size_t)b * n + q] * T[p + n * q];
+              fv.S[((((size_t)e * 3 + d) * (n + 1) + pl) * nn + a + n * b) * 3 + l] = fv.h * fv.h * s;
+            }
+        }
+  }
+}
+
+// Primitive (rho, u, v, w, p) of element e's sub-cell at position m along d,
+// transverse (a, b); m = -1 and m = n are the neighbours' sub-cells across
+// the faces 2d and 2d + 1.
+static void fv_prim(const Ctx& c, const FVData& fv, int e, int d, int m, int a, int b, double w[5]) {
+  const int n = c.n, N = c.N, P = c.P;
+  int ee = e, cell;
+  if (m < 0 || m > N) {
+    const int f = 2 * d + (m > N ? 1 : 0);
+    const int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1], fl = c.nbr[(e * 6 + f) * 3 + 2];
+    int a2, b2;
+    flip_map(fl, N, a, b, a2, b2);
+    ee = e2;
+    cell = line_node(n, f2 / 2, (f2 % 2) * N, a2, b2);
+  } else {
+    cell = line_node(n, d, m, a, b);
+  }
+  double q[5];
+  for (int v = 0; v < 5; ++v) q[v] = fv.Ub[((size_t)ee * 5 + v) * P + cell];
+  const Prim<double> pw = cons2prim(c.prm, q);
+  w[0] = pw.rho; w[1] = pw.u[0]; w[2] = pw.u[1]; w[3] = pw.u[2]; w[4] = pw.p;
+}
+
+static inline double minmod(double x, double y) {
+  if (x * y <= 0.0) return 0.0;
+  return x > 0.0 ? std::min(x, y) : std::max(x, y);
+}
+
+// Reconstructed conservative state of element e's sub-cell (m along d, (a, b))
+// at its face on side s (0: -xi_d, 1: +xi_d).
+static void fv_face_state(const Ctx& c, const FVData& fv, int e, int d, int m, int a, int b, int s, double q[5]) {
+  double wm[5], w0[5], wp[5];
+  fv_prim(c, fv, e, d, m - 1, a, b, wm);
+  fv_prim(c, fv, e, d, m, a, b, w0);
+  fv_prim(c, fv, e, d, m + 1, a, b, wp);
+  double w[5];
+  for (int v = 0; v < 5; ++v) {
+    const double sl = minmod(wp[v] - w0[v], w0[v] - wm[v]);
+    w[v] = w0[v] + (s ? 0.5 : -0.5) * sl;
+  }
+  q[0] = w[0];
+  for (int a3 = 0; a3 < 3; ++a3) q[1 + a3] = w[0] * w[1 + a3];
+  q[4] = w[4] / (c.prm.gamma - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+}
+
+// Sub-face flux for the area vector Sv from the reconstructed states (qL, qR)
+// and the two sub-cells' means (left: element eL cell cL, right: eR, cR).
+static void fv_flux(const Ctx& c, const FVData& fv, const double qL[5], const double qR[5], int eL, int cL, int eR,
+                    int cR, const double Sv[3], double out[5]) {
+  const int P = c.P;
+  const double A = std::sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
+  const double nv[3] = {Sv[0] / A, Sv[1] / A, Sv[2] / A};
+  const Prim<double> L = cons2prim(c.prm, qL), R = cons2prim(c.prm, qR);
+  double fa[5];
+  llf_flux(c.prm, qL, L, qR, R, nv, fa);
+  double mL[5], mR[5], gL[12], gR[12];
+  for (int v = 0; v < 5; ++v) {
+    mL[v] = fv.Ub[((size_t)eL * 5 + v) * P + cL];
+    mR[v] = fv.Ub[((size_t)eR * 5 + v) * P + cR];
+  }
+  for (int r = 0; r < 12; ++r) {
+    gL[r] = fv.Gb[((size_t)eL * 12 + r) * P + cL];
+    gR[r] = fv.Gb[((size_t)eR * 12 + r) * P + cR];
+  }
+  double fvL[5], fvR[5];
+  visc_flux(c.prm, cons2prim(c.prm, mL), gL, c.prm.mu, nv, fvL);
+  visc_flux(c.prm, cons2prim(c.prm, mR), gR, c.prm.mu, nv, fvR);
+  for (int v = 0; v < 5; ++v) out[v] = (fa[v] - 0.5 * (fvL[v] + fvR[v])) * A;
+}
+
+// Faces with an FV side: master-outward sub-face fluxes; on a DG side their
+// nodal form replaces the DG face flux.
+static void fv_faces(const Ctx& c, FVData& fv, double* Fs) {
+  const int n = c.n, N = c.N, nn = n * n;
+  fv.Fb.assign((size_t)c.nfaces * nn * 5, 0.0);
+  for (int e = 0; e < c.E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      if (!c.master[e * 6 + f]) continue;
+      const int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1], fl = c.nbr[(e * 6 + f) * 3 + 2];
+      const bool fvM = c.fv_mask[e] != 0, fvS = c.fv_mask[e2] != 0;
+      if (!fvM && !fvS) continue;
+      const int fid = c.face_id[e * 6 + f];
+      const int d = f / 2, sM = f % 2, d2 = f2 / 2, sS = f2 % 2;
+      for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a) {
+          int a2, b2;
+          flip_map(fl, N, a, b, a2, b2);
+          double qM[5], qS[5];
+          fv_face_state(c, fv, e, d, sM * N, a, b, sM, qM);
+          fv_face_state(c, fv, e2, d2, sS * N, a2, b2, sS, qS);
+          const double* Sp = &fv.S[((((size_t)e * 3 + d) * (n + 1) + sM * n) * nn + a + n * b) * 3];
+          const double sg = 2.0 * sM - 1.0;
+          const double Sout[3] = {sg * Sp[0], sg * Sp[1], sg * Sp[2]};
+          fv_flux(c, fv, qM, qS, e, line_node(n, d, sM * N, a, b), e2, line_node(n, d2, sS * N, a2, b2), Sout,
+                  &fv.Fb[((size_t)fid * nn + a + n * b) * 5]);
+        }
+      if (fvM && fvS) continue;
+      // DG side: F* at the face nodes (master orientation), (V x V)^-1 (Fb / h^2)
+      for (int v = 0; v < 5; ++v)
+        for (int q = 0; q < n; ++q)
+          for (int p = 0; p < n; ++p) {
+            double s = 0.0;
+            for (int b = 0; b < n; ++b)
+              for (int a = 0; a < n; ++a)
+                s += fv.Vi[(size_t)p * n + a] * fv.Vi[(size_t)q * n + b] * fv.Fb[((size_t)fid * nn + a + n * b) * 5 + v];
+            Fs[((size_t)fid * 5 + v) * nn + p + n * q] = s / (fv.h * fv.h);
+          }
+    }
+}
+
+// FV residual of the flagged elements, mapped to their nodes.
+static void fv_elements(const Ctx& c, const FVData& fv, double* Ut, double t) {
+  const int n = c.n, N = c.N, P = c.P, nn = n * n;
+  const double h3 = fv.h * fv.h * fv.h;
+  std::vector<double> JR((size_t)5 * P), out(P);
+  for (int e = 0; e < c.E; ++e) {
+    if (!c.fv_mask[e]) continue;
+    std::fill(JR.begin(), JR.end(), 0.0);   // sum of outward sub-face fluxes per sub-cell
+    for (int d = 0; d < 3; ++d)
+      for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a)
+          for (int pl = 0; pl <= n; ++pl) {
+            double F[5];   // flux through plane pl in +xi_d
+            if (pl > 0 && pl < n) {
+              double qL[5], qR[5];
+              fv_face_state(c, fv, e, d, pl - 1, a, b, 1, qL);
+              fv_face_state(c, fv, e, d, pl, a, b, 0, qR);
+              const double* Sv = &fv.S[((((size_t)e * 3 + d) * (n + 1) + pl) * nn + a + n * b) * 3];
+              fv_flux(c, fv, qL, qR, e, line_node(n, d, pl - 1, a, b), e, line_node(n, d, pl, a, b), Sv, F);
+            } else {
+              const int s = pl == n ? 1 : 0, f = 2 * d + s;
+              const int fid = c.face_id[e * 6 + f];
+              int am = a, bm = b;
+              double sgn = 1.0;   // outward flux of this element: the master's, or minus it
+              if (!c.master[e * 6 + f]) {
+                flip_map(c.nbr[(e * 6 + f) * 3 + 2], N, a, b, am, bm);
+                sgn = -1.0;
+              }
+              for (int v = 0; v < 5; ++v)
+                F[v] = (2.0 * s - 1.0) * sgn * fv.Fb[((size_t)fid * nn + am + n * bm) * 5 + v];
+            }
+            // +F leaves the sub-cell before the plane, enters the one after
+            for (int v = 0; v < 5; ++v) {
+              if (pl > 0) JR[(size_t)v * P + line_node(n, d, pl - 1, a, b)] += F[v];
+              if (pl < n) JR[(size_t)v * P + line_node(n, d, pl, a, b)] -= F[v];
+            }
+          }
+    for (int v = 0; v < 5; ++v) {
+      // Jb Rb h^3 = -(outward fluxes): J R at the nodes = V3^-1 (Jb Rb)
+      for (int id = 0; id < P; ++id) JR[(size_t)v * P + id] = -JR[(size_t)v * P + id] / h3;
+      apply3(n, fv.Vi, &JR[(size_t)v * P], out.data());
+      for (int id = 0; id < P; ++id) {
+        double Qs[5] = {0, 0, 0, 0, 0};
+        if (c.prm.source == 1) {
+          const double x[3] = {c.X[((size_t)e * 3 + 0) * P + id], c.X[((size_t)e * 3 + 1) * P + id],
+                               c.X[((size_t)e * 3 + 2) * P + id]};
+          mms_source(c.prm, x, t, Qs);
+        }
+        Ut[((size_t)e * 5 + v) * P + id] = out[id] / c.J[(size_t)e * P + id] + Qs[v];
+      }
+    }
+  }
+}
+
 static void lifted_gradients(const Ctx& c, const double* U, double* G) {
   std::vector<double> phi, Uf, phif;
   lg_phi(c, U, phi, Uf, phif);
@@ -1468,6 +1830,17 @@ int orc_threads(int n) {
 
 // Test hook: select the volume two-point flux (0: Chandrashekar, 1: central).
 void orc_set_vol_flux(void* h, int kind) { ((Ctx*)h)->prm.vol_flux = kind; }
+
+// FV sub-cell elements: mask[e] != 0 switches element e to the FV sub-cell
+// operator (FP64, LGL nodes); NULL restores the pure DG operator.  Returns 0,
+// or -1 for a Gauss-node context.
+int orc_set_fv_mask(void* h, const int* mask) {
+  Ctx* c = (Ctx*)h;
+  if (!mask) { c->fv_mask.clear(); return 0; }
+  if (c->nodes != 0) return -1;
+  c->fv_mask.assign(mask, mask + c->E);
+  return 0;
+}
 
 // Lifted gradients G [E][12][P] (row phi*3 + l = d phi / d x_l).
 void orc_lifting(void* h, const double* U, double* G) {

@@ -75,6 +75,8 @@ def _load(omp: bool = False):
     L.orc_node_coords.argtypes = [C.c_void_p, _dp]
     L.orc_initial_state.argtypes = [C.c_void_p, C.c_int, C.c_double, _dp]
     L.orc_set_vol_flux.argtypes = [C.c_void_p, C.c_int]
+    L.orc_set_fv_mask.argtypes = [C.c_void_p, C.c_void_p]
+    L.orc_set_fv_mask.restype = C.c_int
     L.orc_lifting.argtypes = [C.c_void_p, _dp, _dp]
     L.orc_volume_term.argtypes = [C.c_void_p, _dp, _dp]
     L.orc_count_ops.argtypes = [C.c_void_p, _dp, C.c_double, _dp]
@@ -207,6 +209,7 @@ class Oracle:
             raise ValueError("oracle: " + err.value.decode())
         self._h = C.c_void_p(h)
         self._L = L
+        self.fv_mask = None
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -230,9 +233,14 @@ class Oracle:
         self._L.orc_time_derivative(self._h, U, out, float(t))
         return out
 
-    def time_derivative_tl(self, U, dU, dmu=0.0, t=0.0):
+    def _tl_check(self):
         if self.nodes != 0:
             raise ValueError("oracle: the tangent-linear is built for the LGL operator")
+        if self.fv_mask is not None:
+            raise ValueError("oracle: the tangent-linear is built for the DG operator (no FV elements)")
+
+    def time_derivative_tl(self, U, dU, dmu=0.0, t=0.0):
+        self._tl_check()
         U = np.ascontiguousarray(U, dtype=np.float64)
         dU = np.ascontiguousarray(dU, dtype=np.float64)
         Ut, dUt = np.zeros_like(U), np.zeros_like(U)
@@ -245,8 +253,7 @@ class Oracle:
         return U
 
     def rk_steps_tl(self, U, dU, dmu, t, dt, nsteps):
-        if self.nodes != 0:
-            raise ValueError("oracle: the tangent-linear is built for the LGL operator")
+        self._tl_check()
         U = np.array(U, dtype=np.float64, copy=True, order="C")
         dU = np.array(dU, dtype=np.float64, copy=True, order="C")
         self._L.orc_rk_steps_tl(self._h, U, dU, float(dmu), float(t), float(dt), int(nsteps))
@@ -261,6 +268,21 @@ class Oracle:
 
     def set_vol_flux(self, kind: int):
         self._L.orc_set_vol_flux(self._h, int(kind))
+
+    def set_fv_mask(self, mask):
+        """Switch the elements with mask[e] != 0 to the FV sub-cell operator
+        ((N+1)^3 sub-cells, MUSCL-minmod reconstruction, LLF sub-face fluxes);
+        None restores the pure DG operator.  LGL nodes only."""
+        if mask is None:
+            self._L.orc_set_fv_mask(self._h, None)
+            self.fv_mask = None
+            return
+        m = np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0, dtype=np.int32)
+        if m.shape[0] != self.E:
+            raise ValueError("oracle: the FV mask needs one entry per element")
+        if self._L.orc_set_fv_mask(self._h, m.ctypes.data) != 0:
+            raise ValueError("oracle: the FV sub-cell operator is built for LGL nodes")
+        self.fv_mask = m
 
     def lifting(self, U):
         G = np.zeros((self.E, 12, self.P))
