@@ -737,6 +737,8 @@ struct FVData {
   std::vector<double> Gb;          // [e][12][P]: sub-cell means of the lifted gradients
   std::vector<double> S;           // [e][d][plane][n*n][3]: sub-face area vectors (+xi_d)
   std::vector<double> Fb;          // [face][n*n][5]: master-outward flux of each boundary sub-face
+  const double* U = nullptr;       // the nodal state and lifted gradients (DG traces of mixed faces)
+  const double* G = nullptr;
 };
 static void fv_prepare(const Ctx& c, const double* U, const double* G, FVData& fv);
 static void fv_faces(const Ctx& c, FVData& fv, double* Fs);
@@ -1432,6 +1434,8 @@ static void fv_matrices(const Ctx& c, FVData& fv) {
 
 static void fv_prepare(const Ctx& c, const double* U, const double* G, FVData& fv) {
   fv_matrices(c, fv);
+  fv.U = U;
+  fv.G = G;
   const int n = c.n, P = c.P, E = c.E, nn = n * n;
   fv.Jb.assign((size_t)E * P, 0.0);
   fv.Ub.assign((size_t)E * 5 * P, 0.0);
@@ -1515,33 +1519,51 @@ static void fv_face_state(const Ctx& c, const FVData& fv, int e, int d, int m, i
   q[4] = w[4] / (c.prm.gamma - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
 }
 
-// Sub-face flux for the area vector Sv from the reconstructed states (qL, qR)
-// and the two sub-cells' means (left: element eL cell cL, right: eR, cR).
-static void fv_flux(const Ctx& c, const FVData& fv, const double qL[5], const double qR[5], int eL, int cL, int eR,
-                    int cR, const double Sv[3], double out[5]) {
+// Viscous flux . nv of element e's sub-cell `cell` from its means.
+static void cell_visc(const Ctx& c, const FVData& fv, int e, int cell, const double nv[3], double out[5]) {
   const int P = c.P;
-  const double A = std::sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
-  const double nv[3] = {Sv[0] / A, Sv[1] / A, Sv[2] / A};
+  double m[5], g[12];
+  for (int v = 0; v < 5; ++v) m[v] = fv.Ub[((size_t)e * 5 + v) * P + cell];
+  for (int r = 0; r < 12; ++r) g[r] = fv.Gb[((size_t)e * 12 + r) * P + cell];
+  visc_flux(c.prm, cons2prim(c.prm, m), g, c.prm.mu, nv, out);
+}
+
+// DG side of a mixed face: means over its sub-face (a, b) (in its own
+// face-local indices) of its face trace -- the state and the viscous flux . nv
+// at the face nodes of element e's face f.
+static void dg_trace_means(const Ctx& c, const FVData& fv, int e, int f, int a, int b, const double nv[3], double q[5],
+                           double fvis[5]) {
+  const int n = c.n, P = c.P;
+  for (int v = 0; v < 5; ++v) q[v] = fvis[v] = 0.0;
+  for (int qq = 0; qq < n; ++qq)
+    for (int pp = 0; pp < n; ++pp) {
+      const double w = fv.V[(size_t)a * n + pp] * fv.V[(size_t)b * n + qq];
+      const int id = face_vol(n, f, pp, qq);
+      double qn[5], g[12], fn[5];
+      for (int v = 0; v < 5; ++v) qn[v] = fv.U[((size_t)e * 5 + v) * P + id];
+      for (int r = 0; r < 12; ++r) g[r] = fv.G[((size_t)e * 12 + r) * P + id];
+      visc_flux(c.prm, cons2prim(c.prm, qn), g, c.prm.mu, nv, fn);
+      for (int v = 0; v < 5; ++v) {
+        q[v] += w * qn[v];
+        fvis[v] += w * fn[v];
+      }
+    }
+}
+
+// Sub-face flux through area A in the unit direction nv: LLF of the two
+// states minus the average of the two viscous fluxes, times A.
+static void fv_flux(const Ctx& c, const double qL[5], const double qR[5], const double fvL[5], const double fvR[5],
+                    const double nv[3], double A, double out[5]) {
   const Prim<double> L = cons2prim(c.prm, qL), R = cons2prim(c.prm, qR);
   double fa[5];
   llf_flux(c.prm, qL, L, qR, R, nv, fa);
-  double mL[5], mR[5], gL[12], gR[12];
-  for (int v = 0; v < 5; ++v) {
-    mL[v] = fv.Ub[((size_t)eL * 5 + v) * P + cL];
-    mR[v] = fv.Ub[((size_t)eR * 5 + v) * P + cR];
-  }
-  for (int r = 0; r < 12; ++r) {
-    gL[r] = fv.Gb[((size_t)eL * 12 + r) * P + cL];
-    gR[r] = fv.Gb[((size_t)eR * 12 + r) * P + cR];
-  }
-  double fvL[5], fvR[5];
-  visc_flux(c.prm, cons2prim(c.prm, mL), gL, c.prm.mu, nv, fvL);
-  visc_flux(c.prm, cons2prim(c.prm, mR), gR, c.prm.mu, nv, fvR);
   for (int v = 0; v < 5; ++v) out[v] = (fa[v] - 0.5 * (fvL[v] + fvR[v])) * A;
 }
 
-// Faces with an FV side: master-outward sub-face fluxes; on a DG side their
-// nodal form replaces the DG face flux.
+// Faces with an FV side: master-outward sub-face fluxes.  An FV side enters
+// with its reconstructed state and the viscous flux of its sub-cell means, a
+// DG side (mixed face) with the sub-face means of its trace; on the DG side
+// the nodal form of the sub-face fluxes replaces the DG face flux.
 static void fv_faces(const Ctx& c, FVData& fv, double* Fs) {
   const int n = c.n, N = c.N, nn = n * n;
   fv.Fb.assign((size_t)c.nfaces * nn * 5, 0.0);
@@ -1557,14 +1579,24 @@ static void fv_faces(const Ctx& c, FVData& fv, double* Fs) {
         for (int a = 0; a < n; ++a) {
           int a2, b2;
           flip_map(fl, N, a, b, a2, b2);
-          double qM[5], qS[5];
-          fv_face_state(c, fv, e, d, sM * N, a, b, sM, qM);
-          fv_face_state(c, fv, e2, d2, sS * N, a2, b2, sS, qS);
           const double* Sp = &fv.S[((((size_t)e * 3 + d) * (n + 1) + sM * n) * nn + a + n * b) * 3];
           const double sg = 2.0 * sM - 1.0;
-          const double Sout[3] = {sg * Sp[0], sg * Sp[1], sg * Sp[2]};
-          fv_flux(c, fv, qM, qS, e, line_node(n, d, sM * N, a, b), e2, line_node(n, d2, sS * N, a2, b2), Sout,
-                  &fv.Fb[((size_t)fid * nn + a + n * b) * 5]);
+          const double A = std::sqrt(Sp[0] * Sp[0] + Sp[1] * Sp[1] + Sp[2] * Sp[2]);
+          const double nv[3] = {sg * Sp[0] / A, sg * Sp[1] / A, sg * Sp[2] / A};
+          double qM[5], qS[5], vM[5], vS[5];
+          if (fvM) {
+            fv_face_state(c, fv, e, d, sM * N, a, b, sM, qM);
+            cell_visc(c, fv, e, line_node(n, d, sM * N, a, b), nv, vM);
+          } else {
+            dg_trace_means(c, fv, e, f, a, b, nv, qM, vM);
+          }
+          if (fvS) {
+            fv_face_state(c, fv, e2, d2, sS * N, a2, b2, sS, qS);
+            cell_visc(c, fv, e2, line_node(n, d2, sS * N, a2, b2), nv, vS);
+          } else {
+            dg_trace_means(c, fv, e2, f2, a2, b2, nv, qS, vS);
+          }
+          fv_flux(c, qM, qS, vM, vS, nv, A, &fv.Fb[((size_t)fid * nn + a + n * b) * 5]);
         }
       if (fvM && fvS) continue;
       // DG side: F* at the face nodes (master orientation), (V x V)^-1 (Fb / h^2)
@@ -1598,7 +1630,12 @@ static void fv_elements(const Ctx& c, const FVData& fv, double* Ut, double t) {
               fv_face_state(c, fv, e, d, pl - 1, a, b, 1, qL);
               fv_face_state(c, fv, e, d, pl, a, b, 0, qR);
               const double* Sv = &fv.S[((((size_t)e * 3 + d) * (n + 1) + pl) * nn + a + n * b) * 3];
-              fv_flux(c, fv, qL, qR, e, line_node(n, d, pl - 1, a, b), e, line_node(n, d, pl, a, b), Sv, F);
+              const double A = std::sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
+              const double nv[3] = {Sv[0] / A, Sv[1] / A, Sv[2] / A};
+              double vL[5], vR[5];
+              cell_visc(c, fv, e, line_node(n, d, pl - 1, a, b), nv, vL);
+              cell_visc(c, fv, e, line_node(n, d, pl, a, b), nv, vR);
+              fv_flux(c, qL, qR, vL, vR, nv, A, F);
             } else {
               const int s = pl == n ? 1 : 0, f = 2 * d + s;
               const int fid = c.face_id[e * 6 + f];

@@ -5,13 +5,15 @@ citation; the oracle follows these readings: J-weighted sub-cell means of the
 nodal interpolant, sub-face area vectors integrated from the metric terms,
 minmod-limited linear reconstruction of the primitive variables, LLF sub-face
 fluxes minus the central viscous flux of the sub-cell means, and on a face
-between a DG and an FV element the sub-face fluxes as the DG face flux.
+between a DG and an FV element the DG side entering with the sub-face means of
+its trace and taking the nodal form of the sub-face fluxes as its face flux.
 
 Pins: a one-dimensional MUSCL-LLF finite-volume scheme written here with numpy
 polynomials (a Cartesian mesh whose state varies along x only), invariance
 under the elements' local frames (24 rotations, eight face orientations),
 free-stream preservation and discrete conservation with mixed DG/FV meshes on
-curved elements, and that an all-DG mask is the DG operator bit for bit."""
+curved elements, bounded free-stream rounding over many steps in a mixed mesh,
+and that an all-DG mask is the DG operator bit for bit."""
 import numpy as np
 import pytest
 
@@ -78,6 +80,29 @@ def test_all_dg_mask_is_the_dg_operator(orc):
     assert not np.allclose(o.time_derivative(U), R0)
     o.set_fv_mask(None)
     assert np.array_equal(o.time_derivative(U), R0)
+
+
+@pytest.mark.parametrize("N", [4, 7])
+def test_mixed_mesh_free_stream_rounding_does_not_grow(orc, N):
+    """A free stream on a checkerboard of DG and FV elements, 100 LSERK4-5
+    steps: the rounding-level departure stays bounded (a coupling of the DG
+    side through the inverse means map of its interior sub-cells, instead of
+    the means of its trace, lets it grow 1.8x (N = 4) to 14x (N = 7) every 25
+    steps)."""
+    K = 2
+    m = box_mesh(K, 1, lo=0.0, hi=2 * np.pi)
+    o = orc.Oracle(m, N, mu=1.0 / 1600)
+    U = np.zeros(o.shape)
+    u = np.array([0.1, 0.05, 0.02])
+    U[:, 0] = 1.0
+    U[:, 1:4] = u[None, :, None, None, None]
+    U[:, 4] = 1.0 / GAMMA / (GAMMA - 1) + 0.5 * u @ u
+    o.set_fv_mask(_checkerboard(m, K))
+    U0, drift = U.copy(), []
+    for blk in range(4):
+        U = o.rk_steps(U, blk * 0.25, 0.01, 25)
+        drift.append(np.abs(U - U0).max() / np.abs(U0).max())
+    assert max(drift) < 1e-10 and drift[-1] < 3.0 * drift[0], drift
 
 
 def _means_matrix(x, n):
