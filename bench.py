@@ -501,7 +501,9 @@ def run_pid(args, local):
     the per-GPU load of the paper's weak-scaling runs of the split-form LGL
     operator), 10 steps each: LGL split form in FP64 and with the FP32 operator,
     Gauss nodes (standard weak form) in FP64, each FP64 case also with RK4-14
-    (PID counts stages, so it is per stage).  Uniform flow
+    (PID counts stages, so it is per stage), and the LGL cases with half of the
+    elements in the FV sub-cell representation (checkerboard, as the paper's
+    DG/FV runs force it).  Uniform flow
     rho = 1, u = (0.1, 0.05, 0.02), p = 1/gamma, mu = 1/1600; every kernel
     does its full work on it.  Reports DOF*stage/s, PID and the free-stream
     preservation error max|U - U0| / max|U0| after the steps."""
@@ -523,12 +525,18 @@ def run_pid(args, local):
         dofs = mesh.n_elems * (N + 1) ** 3
         res = {"N": N, "elements": mesh.n_elems, "dof": dofs,
                "nodes": "Legendre-Gauss, standard weak form" if nodes == dg.NODES_LG else "LGL, split form"}
-        precs = [("fp64", dg.FP64, dg.RK45), ("fp64_rk414", dg.FP64, dg.RK414)]
+        precs = [("fp64", dg.FP64, dg.RK45, False), ("fp64_rk414", dg.FP64, dg.RK414, False)]
         if nodes == dg.NODES_LGL:
-            precs.append(("fp32op", dg.FP32OP, dg.RK45))
-        for prec_name, prec, rk in precs:
+            precs.append(("fp32op", dg.FP32OP, dg.RK45, False))
+            precs.append(("fp64_fv50", dg.FP64, dg.RK45, True))
+        if args.pid_variants:
+            precs = [p for p in precs if p[0] in args.pid_variants.split(",")]
+        for prec_name, prec, rk, fv in precs:
             s = dg.Solver(mesh, N, gamma=gamma, R=1.0, Pr=0.72, mu=1.0 / 1600.0, precision=prec, device=local,
                           nodes=nodes, rk_scheme=rk)
+            if fv:   # half of the elements in the FV representation, checkerboard (the paper's forcing)
+                e = torch.arange(mesh.n_elems, device="cuda:%d" % local)
+                s.set_fv_mask(((e % K) + (e // K) % K + e // (K * K)) % 2)
             stages = 14 if rk == dg.RK414 else 5
             st = torch.cuda.Stream(device="cuda:%d" % local)
             with torch.cuda.stream(st):
@@ -553,6 +561,8 @@ def run_pid(args, local):
             drift = float((U - U0).abs().max() / U0.abs().max())
             res[prec_name] = {"dof_stage_per_s": rate, "pid_ns": 1e9 / rate, "ms_per_step": ms / nsteps,
                               "freestream_drift": drift}
+            if fv:
+                res[prec_name]["fv_elements"] = "50 %, checkerboard"
             del U, U0, G
             s.close()
             torch.cuda.empty_cache()
@@ -560,6 +570,7 @@ def run_pid(args, local):
     line = {"experiment": "free-stream PID, %d steps after 3 warm-up steps, one graph launch" % nsteps,
             "cases": out,
             "paper_context": {"pid_ns_full_dg_N3_16.78M_dof_per_MI300A_gauss_nodes": 3.56864,
+                              "pid_ns_50pct_fv_N3_16.78M_dof_per_MI300A_gauss_nodes": 8.35923,
                               "weak_scaling_N9_dof_per_gpu_range": [1.024e6, 8.192e6]}}
     print(json.dumps(line))
     return 0
@@ -717,6 +728,8 @@ def main():
     ap.add_argument("--pid-steps", type=int, default=10)
     ap.add_argument("--pid-cases", default="", help="comma list of PID case names ('' = all)")
     ap.add_argument("--pid-K", type=int, default=0, help="elements per direction instead of the cases' own")
+    ap.add_argument("--pid-variants", default="", help="comma list of PID variants (fp64, fp64_rk414, fp32op, "
+                    "fp64_fv50; '' = all)")
     ap.add_argument("--no-extra-legs", dest="extra_legs", action="store_false",
                     help="skip the 48^3 Taylor-Green and ensemble legs of the default line")
     ap.add_argument("--tgv-leg-steps", type=int, default=6, help="steps of the 48^3 leg of the default line")

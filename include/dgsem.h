@@ -175,12 +175,34 @@ dg_status dg_initial_state(dg_ctx* ctx, int32_t kind, double prm0, double* dU, d
  * (the energy share of the modes that truncation to degree N-1 in every
  * direction removes; 0 for a field of degree < N in each direction, 1 for a
  * pure top mode; 0 where q vanishes).  dFlag (may be NULL) receives 1 where
- * eta > 0 and log10(eta) > log10_threshold, else 0 (FP64 decision).  The FV
- * sub-cell operator itself is not built.  dU: device state; dEta: device,
+ * eta > 0 and log10(eta) > log10_threshold, else 0 (FP64 decision); it can
+ * be passed to dg_set_fv_mask as it is.  dU: device state; dEta: device,
  * n_elems doubles; dFlag: device, n_elems int32.  DG_EINVAL for a null
  * argument or an unknown var.  Does not synchronise. */
 dg_status dg_indicator(dg_ctx* ctx, const double* dU, int32_t var, double log10_threshold, double* dEta,
                        int32_t* dFlag, dg_stream stream);
+
+/* FV sub-cell elements of the shock capturing (Sec. 3.1: a second-order
+ * finite-volume scheme on (N+1)^3 integral means per element for the
+ * elements the troubled-cell indicator selects).  dMask: device, n_elems
+ * int32; element e is advanced by the FV operator where dMask[e] != 0, by the
+ * DG operator elsewhere, in every later dg_time_derivative and dg_rk_step
+ * (also in an RK graph captured before: the kernels read the mask at run
+ * time).  The mask is copied on `stream` (the caller may reuse dMask after
+ * the stream has passed this call).  dMask = NULL switches the FV operator
+ * off (the pure DG operator, bit for bit).
+ * The FV scheme: J-weighted sub-cell means of the nodal interpolant on the
+ * (N+1)^3 equal sub-cubes of the reference element, sub-face area vectors
+ * integrated exactly from the metric terms, minmod-limited linear
+ * reconstruction of (rho, u, v, w, p), local Lax-Friedrichs sub-face fluxes
+ * minus the central viscous flux of the sub-cell means (mean BR1 gradients);
+ * a face between a DG and an FV element uses the sub-face fluxes, on the DG
+ * side in nodal form with the same face integral.  The first call allocates
+ * about 18 + 12 (N+2)/(N+1) doubles per node plus 5 per face node and sets
+ * up the sub-cell geometry.  FP64 operator on LGL nodes only: DG_EUNSUPPORTED
+ * otherwise; the adjoint entry points return DG_EUNSUPPORTED while a mask is
+ * set.  dg_max_dt keeps the DG time-step restriction.  Does not synchronise. */
+dg_status dg_set_fv_mask(dg_ctx* ctx, const int32_t* dMask, dg_stream stream);
 
 /* Physical node positions X[e][c][k][j][i] (device, n_elems*3*(N+1)^3). */
 dg_status dg_node_coords(dg_ctx* ctx, double* dX, dg_stream stream);

@@ -39,7 +39,7 @@ EXPORTS = ["dg_init", "dg_destroy", "dg_state_len", "dg_time_derivative", "dg_rk
            "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
            "dg_ensemble_step", "dg_ensemble_plan", "dg_ensemble_last_error", "dg_time_derivative_vjp",
            "dg_adjoint_step", "dg_adjoint_solve", "dg_checkpoint_schedule", "dg_kinetic_energy", "dg_set_viscosity",
-           "dg_check_conversions", "dg_check_reciprocals", "dg_indicator", "dg_last_error"]
+           "dg_check_conversions", "dg_check_reciprocals", "dg_indicator", "dg_set_fv_mask", "dg_last_error"]
 
 
 class DGError(RuntimeError):
@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
     L.dg_check_conversions.argtypes = [vp, i32, vp, vp, vp]
     L.dg_check_reciprocals.argtypes = [vp, i32, vp, vp, vp]
     L.dg_indicator.argtypes = [vp, vp, i32, f64, vp, vp, vp]
+    L.dg_set_fv_mask.argtypes = [vp, vp, vp]
     L.dg_conserved_totals_noalloc.argtypes = [vp, vp, i32, i32, i32, vp, vp]
     L.dg_ensemble_create.argtypes = [C.POINTER(vp), i32, C.c_char_p, C.POINTER(vp)]
     L.dg_ensemble_destroy.argtypes = [vp]
@@ -112,7 +113,7 @@ def load(build_if_missing: bool = True):
                  "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
                  "dg_ensemble_step", "dg_ensemble_plan", "dg_time_derivative_vjp", "dg_adjoint_step",
                  "dg_adjoint_solve", "dg_checkpoint_schedule", "dg_kinetic_energy", "dg_set_viscosity",
-                 "dg_check_conversions", "dg_check_reciprocals", "dg_indicator"):
+                 "dg_check_conversions", "dg_check_reciprocals", "dg_indicator", "dg_set_fv_mask"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -255,6 +256,22 @@ class Solver:
                                          float(log10_threshold) if log10_threshold is not None else 0.0, _ptr(eta),
                                          _ptr(flag) if flag is not None else None, _stream_handle(stream)))
         return eta, flag
+
+    def set_fv_mask(self, mask, stream=None):
+        """Advance the elements with mask[e] != 0 by the FV sub-cell operator
+        (device int32 [E], e.g. the flags of ``indicator``; a host array is
+        copied to the device first); None restores the pure DG operator."""
+        import torch
+        if mask is None:
+            self._check(self._L.dg_set_fv_mask(self._h, None, _stream_handle(stream)))
+            self._fv_mask = None
+            return
+        m = torch.as_tensor(mask)
+        if m.numel() != self.E:
+            raise ValueError("FV mask: one entry per element")
+        m = (m.reshape(-1) != 0).to(device="cuda:%d" % self.device, dtype=torch.int32).contiguous()
+        self._check(self._L.dg_set_fv_mask(self._h, _ptr(m), _stream_handle(stream)))
+        self._fv_mask = m   # kept until the stream has passed the copy
 
     def node_coords(self, stream=None):
         import torch

@@ -74,9 +74,9 @@ static void lgl_basis(int N, std::vector<double>& x, std::vector<double>& w, std
 bool bounds_failed(cudaStream_t s, char* msg, size_t len) {
 #ifdef DG_BOUNDS_CHECK
   cudaStreamSynchronize(s);
-  const unsigned long long words[7] = {bounds_word_operator(), bounds_word_volume(), bounds_word_gauss(),
+  const unsigned long long words[8] = {bounds_word_operator(), bounds_word_volume(), bounds_word_gauss(),
                                        bounds_word_geometry(), bounds_word_adjoint(), bounds_word_ensemble(),
-                                       bounds_word_latency()};
+                                       bounds_word_latency(), bounds_word_fv()};
   for (unsigned long long w : words)
     if (w) {
       long long idx = (long long)(w & 0xffffffffffffull);
@@ -120,12 +120,14 @@ static void release(Ctx* c) {
   void* bufs[] = {c->d_modal, c->d_D, c->d_metrics, c->d_J, c->d_X, c->d_mms, c->d_Uf, c->d_gf, c->d_lgb, c->d_facegeo, c->d_metrics_f, c->d_facegeo_f,
                   c->d_grad, c->d_fstar, c->d_red, c->d_w, c->d_clock, c->d_U, c->d_G,
                   c->d_adj_qbar, c->d_adj_gbar, c->d_adj_gtil, c->d_adj_fseed, c->d_adj_face, c->d_adj_mu,
-                  c->d_adj_stage, c->d_adj_work};
+                  c->d_adj_stage, c->d_adj_work, c->d_fv_tab, c->d_fv_iJb, c->d_fv_S, c->d_fv_M, c->d_fv_Fb};
   for (void* p : bufs) if (p) cudaFree(p);
   if (c->d_faces) cudaFree(c->d_faces);
   if (c->d_elem_face) cudaFree(c->d_elem_face);
   if (c->d_elem_nbr) cudaFree(c->d_elem_nbr);
   if (c->d_minmask) cudaFree(c->d_minmask);
+  if (c->d_fv_mask) cudaFree(c->d_fv_mask);
+  if (c->d_fv_lists) cudaFree(c->d_fv_lists);
   if (c->h_out) cudaFreeHost(c->h_out);
   if (c->h_clock) cudaFreeHost(c->h_clock);
 }
@@ -498,6 +500,43 @@ dg_status dg_indicator(dg_ctx* c, const double* dU, int32_t var, double log10_th
   cudaStream_t s = (cudaStream_t)stream;
   DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
   DG_CUDA(launch_indicator(*c, dU, var, log10_threshold, dEta, dFlag, s), c, "indicator kernel");
+  return checked(c, s);
+}
+
+dg_status dg_set_fv_mask(dg_ctx* c, const int32_t* dMask, dg_stream stream) {
+  if (!c) return fail(c, DG_EINVAL, "dg_set_fv_mask: null context");
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  const bool on = dMask != nullptr;
+  if (on && (c->prm.precision != DG_FP64 || c->prm.nodes != DG_NODES_LGL))
+    return fail(c, DG_EUNSUPPORTED, "dg_set_fv_mask: the FV sub-cell operator is built for the FP64 LGL operator");
+  if (on && !c->d_fv_mask) {
+    const size_t E = c->E, P = c->P, NN = c->NN, n = c->n;
+    std::vector<double> tab;
+    fv_tables(c->N, c->x, tab);
+    DG_CUDA(cudaMalloc(&c->d_fv_tab, sizeof(double) * tab.size()), c, "FV tables");
+    DG_CUDA(cudaMalloc(&c->d_fv_iJb, sizeof(double) * E * P), c, "FV sub-cell Jacobians");
+    DG_CUDA(cudaMalloc(&c->d_fv_S, sizeof(double) * E * 3 * (n + 1) * NN * 4), c, "FV area vectors");
+    DG_CUDA(cudaMalloc(&c->d_fv_M, sizeof(double) * E * 17 * P), c, "FV sub-cell means");
+    DG_CUDA(cudaMalloc(&c->d_fv_Fb, sizeof(double) * (size_t)c->nfaces * 5 * NN), c, "FV sub-face fluxes");
+    DG_CUDA(cudaMemcpyAsync(c->d_fv_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s), c,
+            "FV tables copy");
+    DG_CUDA(fv_setup(*c, s), c, "FV geometry kernel");
+    // the host table must outlive the copy
+    DG_CUDA(cudaStreamSynchronize(s), c, "FV set-up");
+    DG_CUDA(cudaMalloc(&c->d_fv_lists, sizeof(int) * (2 * E + 2)), c, "FV element lists");
+    DG_CUDA(cudaMalloc(&c->d_fv_mask, sizeof(int) * E), c, "FV mask");
+  }
+  if (on) {
+    DG_CUDA(cudaMemcpyAsync(c->d_fv_mask, dMask, sizeof(int) * c->E, cudaMemcpyDeviceToDevice, s), c,
+            "FV mask copy");
+    DG_CUDA(launch_fv_lists(*c, s), c, "FV element lists kernel");
+  }
+  if (on != c->fv_on && c->graph) {   // the captured RK graph has the other launch sequence
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->fv_on = on;
   return checked(c, s);
 }
 

@@ -27,7 +27,9 @@ enum BoundsSite {
   kSiteGaussVol = 6,     // Gauss nodes: volume face id
   kSiteGeomFace = 7,     // face geometry: master element
   kSiteAdjFace = 8,      // adjoint: face elements, face ids, neighbours
-  kSiteEnsMember = 9     // ensemble: member of a tile
+  kSiteEnsMember = 9,    // ensemble: member of a tile
+  kSiteFvNbr = 10,       // FV sub-cells: neighbour element across a face
+  kSiteFvFace = 11       // FV sub-cells: face elements, face id of an element face
 };
 
 #ifdef DG_BOUNDS_CHECK

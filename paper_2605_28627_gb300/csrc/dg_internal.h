@@ -100,6 +100,11 @@ struct StageArgs {
   const double* clock;   // device {t, dt}
   double c_stage, A, B;  // stage time fraction and LSERK coefficients
   int mode;              // 0: write Ut; 1: LSERK update
+  // Element slots of the DG volume kernel: NULL, every element; else slot s <
+  // *list_len is element list[s] (the DG elements when FV sub-cell elements
+  // exist; both device memory, read at run time) and the other slots are idle
+  const int* list = nullptr;
+  const int* list_len = nullptr;
 };
 
 struct Ctx {
@@ -133,6 +138,15 @@ struct Ctx {
   int red_len = 0;               // maximum number of partial rows
   double* d_w = nullptr;         // [n] quadrature weights of the node set
   double* d_modal = nullptr;     // [n][n] nodal -> orthonormal Legendre modes of the node set (indicator)
+  // FV sub-cell elements (dg_fv.cu), allocated by the first dg_set_fv_mask
+  bool fv_on = false;            // a mask is set: every stage runs the FV kernels
+  int* d_fv_mask = nullptr;      // [E] 1: FV element
+  int* d_fv_lists = nullptr;     // [2E + 2]: DG elements, FV elements (ascending), their counts
+  double* d_fv_tab = nullptr;    // V [n][n], V^-1 [n][n], L [n+1][n]
+  double* d_fv_iJb = nullptr;     // [E][P] 1 / (sub-cell means of J)
+  double* d_fv_S = nullptr;      // [E][3][n+1][NN][4] sub-face unit normals and areas
+  double* d_fv_M = nullptr;      // [E][17][P] mean primitives and viscous flux tensors
+  double* d_fv_Fb = nullptr;     // [F][5][NN] master-outward sub-face fluxes of faces with an FV side
   int* d_minmask = nullptr;      // bit a set: value a of the integrals is a minimum
   double* d_clock = nullptr;     // {t, dt}
   double* h_clock = nullptr;     // pinned staging for the clock
@@ -184,6 +198,14 @@ cudaError_t launch_face_lg(const Ctx& c, cudaStream_t s);
 cudaError_t launch_volume_lg(const Ctx& c, const StageArgs& a, cudaStream_t s);
 cudaError_t setup_volume(int N);
 
+// FV sub-cell operator (dg_fv.cu): tables of the node set, the once-per-context
+// geometry (Jb, area vectors) and one stage (means, sub-face fluxes, the DG
+// volume kernel with the FV elements skipped, the FV residual and update).
+void fv_tables(int N, const std::vector<double>& x, std::vector<double>& tab);
+cudaError_t fv_setup(const Ctx& c, cudaStream_t s);
+cudaError_t launch_fv_lists(const Ctx& c, cudaStream_t s);
+cudaError_t launch_fv_stage(const Ctx& c, const StageArgs& a, cudaStream_t s);
+
 // Modal troubled-cell indicator (dg_indicator.cu).
 void modal_table(int N, const std::vector<double>& x, const std::vector<double>& w, bool lobatto,
                  std::vector<double>& T);
@@ -220,6 +242,7 @@ unsigned long long bounds_word_ensemble();
 unsigned long long bounds_word_gauss();
 unsigned long long bounds_word_geometry();
 unsigned long long bounds_word_latency();
+unsigned long long bounds_word_fv();
 unsigned long long bounds_word_operator();
 unsigned long long bounds_word_volume();
 // Checked builds: wait for the work on stream s and describe the first

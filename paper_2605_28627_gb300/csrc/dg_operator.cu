@@ -15,11 +15,22 @@ k_lift(const double* __restrict__ U, const R* __restrict__ metrics, const int* _
   lift_body<N, R, Shape<N>::EPB>(U, metrics, elem_nbr, elem_face, Dg, grad, E, g, inv_w0, blockIdx.x);
 }
 
-template <int N, typename R>
+// FVSKIP: faces with an FV sub-cell element on either side are left to the FV
+// face kernel (fv_mask: [E], 1 for an FV element).
+template <int N, typename R, bool FVSKIP>
 __global__ void __launch_bounds__(128)
 k_face(const double* __restrict__ U, const R* __restrict__ grad, const FaceInfo* __restrict__ faces,
-       const R* __restrict__ facegeo, R* __restrict__ fstar, int F, Gas g) {
-  face_body<N, R>(U, grad, faces, facegeo, fstar, F, g, (long)blockIdx.x * blockDim.x + threadIdx.x);
+       const R* __restrict__ facegeo, R* __restrict__ fstar, int F, Gas g, const int* __restrict__ fv_mask) {
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (FVSKIP) {
+    constexpr int NN = (N + 1) * (N + 1);
+    if (gid >= (long)F * NN) return;
+    const FaceInfo fi = faces[gid / NN];
+    if (fv_mask[dg_idx(fi.master >> 3, F / 3, kSiteFaceElems)] ||
+        fv_mask[dg_idx(fi.slave >> 3, F / 3, kSiteFaceElems)])
+      return;
+  }
+  face_body<N, R>(U, grad, faces, facegeo, fstar, F, g, gid);
 }
 
 // ---------------------------------------------------------------------------
@@ -33,12 +44,13 @@ static cudaError_t lift_NR(const Ctx& c, const double* U, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int N, typename R>
+template <int N, typename R, bool FVSKIP>
 static cudaError_t face_NR(const Ctx& c, const double* U, cudaStream_t s) {
   const long tot = (long)c.nfaces * (N + 1) * (N + 1);
   const int blocks = (int)((tot + 127) / 128);
   const R* fgeo = (const R*)(sizeof(R) == 8 ? (const void*)c.d_facegeo : (const void*)c.d_facegeo_f);
-  k_face<N, R><<<blocks, 128, 0, s>>>(U, (const R*)c.d_grad, c.d_faces, fgeo, (R*)c.d_fstar, c.nfaces, c.gas);
+  k_face<N, R, FVSKIP><<<blocks, 128, 0, s>>>(U, (const R*)c.d_grad, c.d_faces, fgeo, (R*)c.d_fstar, c.nfaces,
+                                               c.gas, c.d_fv_mask);
   return cudaGetLastError();
 }
 
@@ -49,7 +61,8 @@ static cudaError_t lift_N(const Ctx& c, const double* U, bool fp64, cudaStream_t
 
 template <int N>
 static cudaError_t face_N(const Ctx& c, const double* U, cudaStream_t s) {
-  return c.prm.precision == DG_FP32OP ? face_NR<N, float>(c, U, s) : face_NR<N, double>(c, U, s);
+  if (c.prm.precision == DG_FP32OP) return face_NR<N, float, false>(c, U, s);
+  return c.fv_on ? face_NR<N, double, true>(c, U, s) : face_NR<N, double, false>(c, U, s);
 }
 
 #define DG_DISPATCH(FN, ...)                 \

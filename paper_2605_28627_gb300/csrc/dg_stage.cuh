@@ -469,7 +469,31 @@ __device__ __forceinline__ void ec_pair(R ra, R rb, R ba, R bb, R su0, R su1, R 
 
 // R is the operator arithmetic: double (FP64 path) or float (FP32-operator
 // path, state and RK update stay FP64).  metrics, grad and fstar are stored in R.
-template <int N, typename R, int EPB_>
+// Manufactured source, density wave rho = 2 + A sin(phi), phi = pi (x+y+z-t),
+// u = (1,1,1), p = 1: residual of Eq. 1 = [2r', 2r', 2r', 2r', 3r' - lambda Lap T],
+// r' = pi A cos(phi).  sin/cos of phi from those of pi (x+y+z) (per node, set
+// up once: mms [E][2][P]) and of pi t (st, ct; once per block) by the
+// angle-difference identities.  Evaluated in the operator type.
+template <typename R>
+__device__ __forceinline__ void mms_source(const Gas& g, const double* __restrict__ mms, int e, int P, int id,
+                                           double st_d, double ct_d, R src[5]) {
+  const R sa = to_op<R>(mms[((size_t)e * 2) * P + id]), ca = to_op<R>(mms[((size_t)e * 2 + 1) * P + id]);
+  const R st = to_op<R>(st_d), ct = to_op<R>(ct_d);
+  const R sphi = fma(sa, ct, -ca * st);
+  const R cphi = fma(ca, ct, sa * st);
+  const R A = gsel<R>(g.mms_amp, g.f_mms_amp);
+  const R rw = R(2) + A * sphi;
+  const R irw = rcp_op(rw);
+  const R rp = R(M_PI) * A * cphi;
+  const R lapT = R(3) * gsel<R>(g.inv_R, g.f_inv_R) * fma(R(M_PI) * R(M_PI) * A, sphi, R(2) * rp * rp * irw) *
+                 (irw * irw);
+  src[0] = src[1] = src[2] = src[3] = R(2) * rp;
+  src[4] = fma(-gsel<R>(g.mu * g.kappa, g.f_lam), lapT, R(3) * rp);
+}
+
+// LIST: the element slots come from a.list (the DG elements when FV sub-cell
+// elements exist); without it slot = element, as in every other launch.
+template <int N, typename R, int EPB_, bool LIST = false>
 __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restrict__ metrics,
                                             const double* __restrict__ iJ64, const R* __restrict__ grad,
                                             const R* __restrict__ fstar, const int* __restrict__ elem_face,
@@ -496,7 +520,15 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
   R* sFv = sJd + 3 * P;               // [3][4][P] (f_v . Ja^d), momentum + energy
   R* sX = sFv + 12 * P;               // [XB][5][P] exchange of partner shares (one per round if XB > 1)
   R* sDl = tile0 + EPB * PER_ELEM + le * P;   // FP32 only: rho (p - p_ref) / p
-  const int e = blk * EPB + le;
+  // element slot -> element (with LIST, idle slots past the list's end)
+  int nslot = E, e = blk * EPB + le;
+  if constexpr (LIST) {
+    nslot = *a.list_len;
+    e = e < nslot ? a.list[e] : E;
+    if constexpr (EPB == 1) {
+      if (e >= E) return;   // the whole block, before any barrier
+    }
+  }
   const bool active = e < E;
   __shared__ double s_tc[3];          // sin, cos of pi t (manufactured source); B_s dt (FP32 operator)
   if (threadIdx.x == 0) {
@@ -672,7 +704,7 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
       } else {
         le2 = t / (P / 2); w2 = t - le2 * (P / 2); take = t < EPB * (P / 2);
       }
-      if (take && blk * EPB + le2 < E) {
+      if (take && blk * EPB + le2 < nslot) {
         const int hi = w2 / stride;
         const int ia = w2 - hi * stride + stride * (hi % H + n * (hi / H));   // node with r < n/2
         const int ib = ia + H * stride;                                          // its partner
@@ -767,26 +799,8 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
 #pragma unroll
     for (int c = 0; c < 5; ++c) acc[c] = fma(fs_sign, fsr[c * NN], acc[c]);
   }
-  // Manufactured source, density wave rho = 2 + A sin(phi), phi = pi (x+y+z-t),
-  // u = (1,1,1), p = 1: residual of Eq. 1 = [2r', 2r', 2r', 2r', 3r' - lambda Lap T],
-  // r' = pi A cos(phi).  sin/cos of phi from those of pi (x+y+z) (per node, set
-  // up once) and of pi t (once per block) by the angle-difference identities.
-  // Evaluated in the operator type.
   R src[5] = {0, 0, 0, 0, 0};
-  if (g.source == DG_SOURCE_MMS) {
-    const R sa = to_op<R>(mms[((size_t)e * 2) * P + id]), ca = to_op<R>(mms[((size_t)e * 2 + 1) * P + id]);
-    const R st = to_op<R>(s_tc[0]), ct = to_op<R>(s_tc[1]);
-    const R sphi = fma(sa, ct, -ca * st);
-    const R cphi = fma(ca, ct, sa * st);
-    const R A = gsel<R>(g.mms_amp, g.f_mms_amp);
-    const R rw = R(2) + A * sphi;
-    const R irw = rcp_op(rw);
-    const R rp = R(M_PI) * A * cphi;
-    const R lapT = R(3) * gsel<R>(g.inv_R, g.f_inv_R) * fma(R(M_PI) * R(M_PI) * A, sphi, R(2) * rp * rp * irw) *
-                   (irw * irw);
-    src[0] = src[1] = src[2] = src[3] = R(2) * rp;
-    src[4] = fma(-gsel<R>(g.mu * g.kappa, g.f_lam), lapT, R(3) * rp);
-  }
+  if (g.source == DG_SOURCE_MMS) mms_source<R>(g, mms, e, P, id, s_tc[0], s_tc[1], src);
   const size_t o0 = (size_t)e * 5 * P + id;
   if (a.mode == 0) {
     // R(U) itself, scaled by 1/J in FP64

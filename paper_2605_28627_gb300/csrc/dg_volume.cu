@@ -5,12 +5,14 @@
 
 namespace dg {
 
-template <int N, typename R>
+// LIST: the DG elements of a context with FV sub-cell elements (FP64 only).
+template <int N, typename R, bool LIST>
 __global__ void __launch_bounds__(VShape<N>::THREADS, vol_min_blocks<N, R>())
 k_volume2(StageArgs a, const R* __restrict__ metrics, const double* __restrict__ iJ64,
           const R* __restrict__ grad, const R* __restrict__ fstar, const int* __restrict__ elem_face,
           const double* __restrict__ mms, const double* __restrict__ Dg, int E, Gas g, double inv_w0) {
-  volume_body<N, R, VShape<N>::EPB>(a, metrics, iJ64, grad, fstar, elem_face, mms, Dg, E, g, inv_w0, blockIdx.x);
+  volume_body<N, R, VShape<N>::EPB, LIST>(a, metrics, iJ64, grad, fstar, elem_face, mms, Dg, E, g, inv_w0,
+                                          blockIdx.x);
 }
 
 template <int N, typename R>
@@ -18,18 +20,18 @@ static size_t volume2_smem() {
   return volume_smem_bytes<N, R, VShape<N>::EPB>();
 }
 
-template <int N, typename R>
+template <int N, typename R, bool LIST>
 cudaError_t volume2_setup() {
-  return cudaFuncSetAttribute(k_volume2<N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_volume2<N, R, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)volume2_smem<N, R>());
 }
 
-template <int N, typename R>
+template <int N, typename R, bool LIST>
 cudaError_t volume2_launch(const Ctx& c, const StageArgs& a, cudaStream_t s) {
   using S = VShape<N>;
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
   const R* metrics = (const R*)(sizeof(R) == 8 ? (const void*)c.d_metrics : (const void*)c.d_metrics_f);
-  k_volume2<N, R><<<blocks, S::THREADS, volume2_smem<N, R>(), s>>>(
+  k_volume2<N, R, LIST><<<blocks, S::THREADS, volume2_smem<N, R>(), s>>>(
       a, metrics, c.d_metrics, (const R*)c.d_grad, (const R*)c.d_fstar, c.d_elem_face, c.d_mms, c.d_D, c.E, c.gas,
       1.0 / c.w[0]);
   return cudaGetLastError();
@@ -37,17 +39,22 @@ cudaError_t volume2_launch(const Ctx& c, const StageArgs& a, cudaStream_t s) {
 
 template <int N>
 static cudaError_t volume_any(const Ctx& c, const StageArgs& a, cudaStream_t s) {
-  return c.prm.precision == DG_FP32OP ? volume2_launch<N, float>(c, a, s) : volume2_launch<N, double>(c, a, s);
+  if (c.prm.precision == DG_FP32OP) return volume2_launch<N, float, false>(c, a, s);
+  return a.list != nullptr ? volume2_launch<N, double, true>(c, a, s) : volume2_launch<N, double, false>(c, a, s);
 }
 
 template <int N>
 static cudaError_t setup_any() {
-  cudaError_t e = volume2_setup<N, double>();
-  return e != cudaSuccess ? e : volume2_setup<N, float>();
+  cudaError_t e = volume2_setup<N, double, false>();
+  if (e == cudaSuccess) e = volume2_setup<N, double, true>();
+  return e != cudaSuccess ? e : volume2_setup<N, float, false>();
 }
 
 cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s, bool latency_ok) {
   if (c.prm.nodes == DG_NODES_LG) return launch_volume_lg(c, a, s);
+  // with FV sub-cell elements: the FV stage, which calls back here with the
+  // list of the DG elements
+  if (c.fv_on && a.list == nullptr) return launch_fv_stage(c, a, s);
   if (latency_ok && use_latency_kernels(c)) return launch_volume_lat(c, a, s);
   switch (c.N) {
     case 1: return volume_any<1>(c, a, s);
