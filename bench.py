@@ -46,7 +46,7 @@ def build_mesh(N):
 # DRAM bytes (read + write) per launch of the volume kernel on this workload,
 # the median over the launches of one ncu capture of the current kernels
 # (profiles/volume_traffic_N7_mms16.txt); absent = not captured.
-MEASURED_TRAFFIC = {(7, "fp64"): 669.154048e6 + 214.732032e6, (7, "fp32op"): 406.702592e6 + 143.723008e6}
+MEASURED_TRAFFIC = {(7, "fp64"): 670.667520e6 + 217.116672e6, (7, "fp32op"): 406.712064e6 + 143.888640e6}
 
 
 # ---------------------------------------------------------------------------

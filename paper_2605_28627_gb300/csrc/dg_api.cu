@@ -77,6 +77,10 @@ bool bounds_failed(cudaStream_t s, char* msg, size_t len) {
   const unsigned long long words[8] = {bounds_word_operator(), bounds_word_volume(), bounds_word_gauss(),
                                        bounds_word_geometry(), bounds_word_adjoint(), bounds_word_ensemble(),
                                        bounds_word_latency(), bounds_word_fv()};
+  if (bulk_word_volume() || bulk_word_ensemble()) {
+    std::snprintf(msg, len, "a bulk copy into shared memory did not complete within its wait limit");
+    return true;
+  }
   for (unsigned long long w : words)
     if (w) {
       long long idx = (long long)(w & 0xffffffffffffull);

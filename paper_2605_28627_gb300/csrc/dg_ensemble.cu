@@ -205,6 +205,7 @@ static int epb_of(int N, int choice, int precision) {
 
 // Host reader of this file's bounds-check error word (0 in normal builds).
 DG_BOUNDS_READER(bounds_word_ensemble)
+DG_BULK_READER(bulk_word_ensemble)
 
 }  // namespace dg
 

@@ -243,6 +243,8 @@ unsigned long long bounds_word_gauss();
 unsigned long long bounds_word_geometry();
 unsigned long long bounds_word_latency();
 unsigned long long bounds_word_fv();
+unsigned bulk_word_volume();     // bulk-copy waits that gave up (volume kernels)
+unsigned bulk_word_ensemble();
 unsigned long long bounds_word_operator();
 unsigned long long bounds_word_volume();
 // Checked builds: wait for the work on stream s and describe the first

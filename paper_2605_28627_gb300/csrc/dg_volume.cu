@@ -87,5 +87,6 @@ cudaError_t setup_volume(int N) {
 
 // Host reader of this file's bounds-check error word (0 in normal builds).
 DG_BOUNDS_READER(bounds_word_volume)
+DG_BULK_READER(bulk_word_volume)
 
 }  // namespace dg

@@ -2,8 +2,10 @@
 table is bounds-checked inside the kernels; a violation would be recorded and
 reported as DG_ECUDA) on one- and two-element meshes, where every face of an
 element meets the element itself or its single neighbour: the operator, RK
-steps, diagnostics, the Gauss-node operator, the adjoint and the ensemble run
-without a report and match the oracle and the normal build.  Runs in a child
+steps, diagnostics, the Gauss-node operator, the adjoint and the ensemble (its
+persistent tile-table kernels) run without a report -- neither an index out of
+range nor a bulk-copy wait that gave up -- and match the oracle and the normal
+build.  Runs in a child
 process (the checked library is loaded instead of the normal one)."""
 import json
 import os
@@ -53,10 +55,19 @@ for dims, N in (((1, 1, 1), 3), ((2, 1, 1), 3), ((1, 1, 2), 2)):
     mesh = box_mesh(1, 1, lo=0.0, hi=2 * math.pi, dims=dims)
     s = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"])
     runs.append((s, s.initial_state("tgv", prm["p0"])))
-ens = dg.Ensemble([r[0] for r in runs])
+# the tile-table kernels, forced through the tuning cache with one block, so
+# that it walks every tile of a group (a persistent loop re-arms the volume
+# body's bulk-copy barriers once per tile)
+import tempfile
+gpu = torch.cuda.get_device_name()
+cache = tempfile.NamedTemporaryFile("w", suffix=".txt", delete=False)
+cache.write("".join("%s|N=%d|fp64\t0\t1\t1\t1\n" % (gpu, N) for N in (2, 3)))
+cache.close()
+ens = dg.Ensemble([r[0] for r in runs], tune_cache_path=cache.name)
 Us = [r[1].clone() for r in runs]
 Gs = [torch.empty_like(U) for U in Us]
 ens.step(Us, Gs, [0.0] * 3, [1e-3] * 3, nsteps=2)
+out["ensemble_tile_tables"] = all(g["mode"] == "tile table" for g in ens.plan()["groups"])
 refs = []
 for s, U0 in runs:
     ref = U0.clone(); G = torch.empty_like(ref); s.rk_step(ref, G, 0.0, 1e-3, 2); refs.append(ref)
@@ -78,3 +89,4 @@ def test_checked_build_on_one_and_two_element_meshes():
         assert res[name]["err_rk"] < 1e-10, res
         assert res[name]["finite"], res
     assert res["ensemble_bitwise"], res   # to rounding: see the child's note
+    assert res["ensemble_tile_tables"], res
