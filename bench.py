@@ -67,6 +67,33 @@ def volume_flops_per_dof(N):
     return 1.5 * (n - 1) * pair + diag + visc + prim + surf + epi
 
 
+# Algorithmic FP64 count of the lifting kernel per node and stage: the
+# primitives (a reciprocal, velocities, pressure, temperature: 14), the face
+# jumps at the 6 n^2 face points of an element (the neighbour's primitives and
+# four scaled differences: 22 per point, 6/n per node), the line derivatives of
+# four fields in three directions (12 n FMAs), the metric products (12
+# components of three terms, 5 each) and the 1/J scaling (12).
+def lift_flops_per_dof(N):
+    n = N + 1
+    return 14.0 + 22.0 * 6.0 / n + 24.0 * n + 60.0 + 12.0
+
+
+# Algorithmic FP64 count of the LLF face kernel per face point and stage: both
+# sides' primitives (24), the two Euler fluxes in n (28), sound speeds and the
+# wave-speed bound (19), the dissipative combination (20), the two viscous
+# fluxes in n (92) and the BR1 average times sJ (17).  3 (N+1)^2 face points
+# per element: 3/(N+1) per node.
+FACE_POINT_FLOPS = 24.0 + 28.0 + 19.0 + 20.0 + 92.0 + 17.0
+
+
+def face_flops_per_dof(N):
+    return FACE_POINT_FLOPS * 3.0 / (N + 1)
+
+
+def step_flops_per_dof(N):
+    return lift_flops_per_dof(N) + face_flops_per_dof(N) + volume_flops_per_dof(N)
+
+
 # ---------------------------------------------------------------------------
 # Algorithmic DRAM bytes per node and stage of the FP32-operator volume kernel
 # (HBM-bound): FP64 state U and register G read and written (160 B), FP32
@@ -840,6 +867,15 @@ def main():
                 "kernel": "k_volume2<%d> (split-form volume + surface + Jacobian + LSERK update)" % N,
                 "peak_source": "measured FP64 DFMA chain throughput on this GPU (dg_probe_peaks)",
                 "stage_ms": {"lift": ms3[0], "face": ms3[1], "volume": ms3[2]}}
+    # the whole stage (lifting, face fluxes, volume) by the same count
+    stage_tf = step_flops_per_dof(N) * dof / (sum(ms3) * 1e-3) / 1e12
+    roofline["stage"] = {
+        "achieved": stage_tf, "frac": stage_tf / fp64_peak,
+        "algorithmic_flops_per_dof": {"lift": lift_flops_per_dof(N), "face": face_flops_per_dof(N),
+                                      "volume": volume_flops_per_dof(N)},
+        "kernel_frac": {"lift": lift_flops_per_dof(N) * dof / (ms3[0] * 1e-3) / 1e12 / fp64_peak,
+                        "face": face_flops_per_dof(N) * dof / (ms3[1] * 1e-3) / 1e12 / fp64_peak,
+                        "volume": achieved / fp64_peak}}
 
     # end to end through the C ABI with host buffers (pinned)
     host = U0.cpu().pin_memory()

@@ -46,3 +46,15 @@ def test_volume_model_is_below_the_oracle_operator(orc, N):
     # counting does not change the result
     Ut = o.time_derivative(U)
     assert np.isfinite(Ut).all()
+
+
+@pytest.mark.parametrize("N", [1, 3, 5, 7, 9])
+def test_stage_model_is_below_the_oracle_operator(orc, N):
+    """Lifting + face + volume models together (the whole-stage roofline of
+    the bench line) stay below the oracle's count for the whole R(U)."""
+    prm = mms_params()
+    m = box_mesh(2, N, deform="sinprod", rotate_seed=20260528)
+    o = orc.Oracle(m, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1)
+    U = o.initial_state("mms", 0.0)
+    per_node = sum(o.count_ops(U).values()) / (o.E * o.P)
+    assert bench.step_flops_per_dof(N) < per_node, (bench.step_flops_per_dof(N), per_node)
