@@ -739,6 +739,8 @@ struct FVData {
   std::vector<double> Fb;          // [face][n*n][5]: master-outward flux of each boundary sub-face
   const double* U = nullptr;       // the nodal state and lifted gradients (DG traces of mixed faces)
   const double* G = nullptr;
+  const double* Uf = nullptr;      // Gauss nodes: face values [e][6][5][n*n] and [e][6][12][n*n]
+  const double* Gf = nullptr;
 };
 static void fv_prepare(const Ctx& c, const double* U, const double* G, FVData& fv);
 static void fv_faces(const Ctx& c, FVData& fv, double* Fs);
@@ -1248,7 +1250,18 @@ static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double m
             Fs[((size_t)fid * 5 + v) * nn + p + n * q] = (fa[v] - 0.5 * (fvL[v] + fvR[v])) * sJ;
         }
     }
+  // FV sub-cell elements (as on LGL nodes; the DG side of a mixed face
+  // enters with its interpolated face values)
+  const bool use_fv = !c.fv_mask.empty();
+  FVData fv;
+  if (use_fv) {
+    fv_prepare(c, U, G.data(), fv);
+    fv.Uf = Uf.data();
+    fv.Gf = Gf.data();
+    fv_faces(c, fv, Fs.data());
+  }
   for (int e = 0; e < E; ++e) {
+    if (use_fv && c.fv_mask[e]) continue;
     // contravariant fluxes at the nodes
     std::vector<double> Ft((size_t)3 * 5 * P);
     for (int id = 0; id < P; ++id) {
@@ -1306,11 +1319,13 @@ static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double m
       for (int v = 0; v < 5; ++v) Ut[((size_t)e * 5 + v) * P + id] = -acc[(size_t)v * P + id] / c.J[(size_t)e * P + id] + Qs[v];
     }
   }
+  if (use_fv) fv_elements(c, fv, Ut, t);
 }
 
 // Lifted gradients on either node set (test hook and diagnostics).
 // ---------------------------------------------------------------------------
-// FV sub-cell operator (Sec. 3.1; readings F1-F9 in the design notes).
+// FV sub-cell operator (Sec. 3.1, which fixes the scheme by citation; the
+// readings taken here, on either node set):
 //  F1 sub-cells: the n^3 = (N+1)^3 equal sub-cubes of the reference element,
 //     width h = 2/n; sub-cells and sub-faces are indexed like nodes and face
 //     nodes (the same flip codes map sub-faces across element faces).
@@ -1332,10 +1347,13 @@ static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double m
 //  F6 residual: dub/dt = -(sum of the sub-cell's outward sub-face fluxes) /
 //     (Jb h^3); back to nodes by the inverse means map, J R = V3^-1 (Jb Rb),
 //     plus the manufactured source at the nodes.
-//  F7 element faces with an FV side are evaluated on sub-faces (both sides'
-//     means and slopes, the master's area vectors); an FV side uses the
-//     sub-face fluxes, a DG side their nodal form F* = (V (x) V)^-1 (Fb / h^2),
-//     whose integral over the face equals the sub-face fluxes' sum.
+//  F7 element faces with an FV side are evaluated on sub-faces with the
+//     master's area vectors.  An FV side enters with its reconstructed state
+//     and the viscous flux of its sub-cell means; a DG side with the means of
+//     its trace over each sub-face (the face nodes on LGL nodes, the values
+//     interpolated to the face points on Gauss nodes), and its face flux is
+//     the nodal form F* = (V (x) V)^-1 (Fb / h^2) of the sub-face fluxes,
+//     whose integral over the face equals their sum.
 
 // Gauss-Legendre rule of n points on [-1, 1].
 static void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w) {
@@ -1412,6 +1430,7 @@ static void apply3(int n, const std::vector<double>& M, const double* in, double
 
 // The means matrix V, its inverse and the Lagrange values at the sub-cell planes.
 static void fv_matrices(const Ctx& c, FVData& fv) {
+  const std::vector<double>& xs = c.nodes == 1 ? c.g.x : c.b.x;   // the context's node set
   const int n = c.n;
   fv.n = n;
   fv.h = 2.0 / n;
@@ -1422,14 +1441,14 @@ static void fv_matrices(const Ctx& c, FVData& fv) {
     const double a = -1.0 + i * fv.h;
     for (int j = 0; j < n; ++j) {
       double s = 0.0;
-      for (int q = 0; q < n; ++q) s += gw[q] * lagrange(c.b.x, j, a + 0.5 * fv.h * (1.0 + gx[q]));
+      for (int q = 0; q < n; ++q) s += gw[q] * lagrange(xs, j, a + 0.5 * fv.h * (1.0 + gx[q]));
       fv.V[(size_t)i * n + j] = 0.5 * s;   // (1/h) (h/2) sum_q w_q l_j
     }
   }
   fv.Vi = invert_small(n, fv.V);
   fv.L.assign((size_t)(n + 1) * n, 0.0);
   for (int pl = 0; pl <= n; ++pl)
-    for (int m = 0; m < n; ++m) fv.L[(size_t)pl * n + m] = lagrange(c.b.x, m, -1.0 + pl * fv.h);
+    for (int m = 0; m < n; ++m) fv.L[(size_t)pl * n + m] = lagrange(xs, m, -1.0 + pl * fv.h);
 }
 
 static void fv_prepare(const Ctx& c, const double* U, const double* G, FVData& fv) {
@@ -1538,10 +1557,16 @@ static void dg_trace_means(const Ctx& c, const FVData& fv, int e, int f, int a, 
   for (int qq = 0; qq < n; ++qq)
     for (int pp = 0; pp < n; ++pp) {
       const double w = fv.V[(size_t)a * n + pp] * fv.V[(size_t)b * n + qq];
-      const int id = face_vol(n, f, pp, qq);
       double qn[5], g[12], fn[5];
-      for (int v = 0; v < 5; ++v) qn[v] = fv.U[((size_t)e * 5 + v) * P + id];
-      for (int r = 0; r < 12; ++r) g[r] = fv.G[((size_t)e * 12 + r) * P + id];
+      if (fv.Uf) {   // Gauss nodes: the values interpolated to the face points
+        const int nn = n * n, fp = pp + n * qq;
+        for (int v = 0; v < 5; ++v) qn[v] = fv.Uf[(((size_t)e * 6 + f) * 5 + v) * nn + fp];
+        for (int r = 0; r < 12; ++r) g[r] = fv.Gf[(((size_t)e * 6 + f) * 12 + r) * nn + fp];
+      } else {
+        const int id = face_vol(n, f, pp, qq);
+        for (int v = 0; v < 5; ++v) qn[v] = fv.U[((size_t)e * 5 + v) * P + id];
+        for (int r = 0; r < 12; ++r) g[r] = fv.G[((size_t)e * 12 + r) * P + id];
+      }
       visc_flux(c.prm, cons2prim(c.prm, qn), g, c.prm.mu, nv, fn);
       for (int v = 0; v < 5; ++v) {
         q[v] += w * qn[v];
@@ -1869,12 +1894,11 @@ int orc_threads(int n) {
 void orc_set_vol_flux(void* h, int kind) { ((Ctx*)h)->prm.vol_flux = kind; }
 
 // FV sub-cell elements: mask[e] != 0 switches element e to the FV sub-cell
-// operator (FP64, LGL nodes); NULL restores the pure DG operator.  Returns 0,
-// or -1 for a Gauss-node context.
+// operator (FP64, either node set); NULL restores the pure DG operator.
+// Returns 0.
 int orc_set_fv_mask(void* h, const int* mask) {
   Ctx* c = (Ctx*)h;
   if (!mask) { c->fv_mask.clear(); return 0; }
-  if (c->nodes != 0) return -1;
   c->fv_mask.assign(mask, mask + c->E);
   return 0;
 }

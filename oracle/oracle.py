@@ -272,7 +272,7 @@ class Oracle:
     def set_fv_mask(self, mask):
         """Switch the elements with mask[e] != 0 to the FV sub-cell operator
         ((N+1)^3 sub-cells, MUSCL-minmod reconstruction, LLF sub-face fluxes);
-        None restores the pure DG operator.  LGL nodes only."""
+        None restores the pure DG operator.  Either node set."""
         if mask is None:
             self._L.orc_set_fv_mask(self._h, None)
             self.fv_mask = None
@@ -280,8 +280,7 @@ class Oracle:
         m = np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0, dtype=np.int32)
         if m.shape[0] != self.E:
             raise ValueError("oracle: the FV mask needs one entry per element")
-        if self._L.orc_set_fv_mask(self._h, m.ctypes.data) != 0:
-            raise ValueError("oracle: the FV sub-cell operator is built for LGL nodes")
+        self._L.orc_set_fv_mask(self._h, m.ctypes.data)
         self.fv_mask = m
 
     def lifting(self, U):

@@ -22,8 +22,14 @@ from workloads import box_mesh, random_state
 GAMMA, RGAS, PR = 1.4, 1.0, 0.72
 
 
-def _quad_weights(orc, N):
-    _, w, _ = orc.basis(N)
+def _nodes(orc, N, nodes):
+    """Nodes and weights of the node set (0: LGL, 1: Legendre-Gauss)."""
+    x, w = (orc.basis(N) if nodes == 0 else orc.gauss_basis(N))[:2]
+    return x, w
+
+
+def _quad_weights(orc, N, nodes=0):
+    _, w = _nodes(orc, N, nodes)
     return np.einsum("k,j,i->kji", w, w, w).reshape(-1)
 
 
@@ -41,10 +47,11 @@ def _checkerboard(m, K):
     return ((e % K) + (e // K) % K + e // (K * K)) % 2
 
 
+@pytest.mark.parametrize("nodes", [0, 1])
 @pytest.mark.parametrize("N", [1, 2, 3, 5])
-def test_free_stream_with_fv_elements(orc, N):
+def test_free_stream_with_fv_elements(orc, N, nodes):
     m = box_mesh(2, N, deform="sinprod", rotate_seed=7)
-    o = orc.Oracle(m, N, mu=0.01)
+    o = orc.Oracle(m, N, mu=0.01, nodes=nodes)
     U = _free_stream(o)
     for mask in (_checkerboard(m, 2), np.ones(m.n_elems)):
         o.set_fv_mask(mask)
@@ -52,13 +59,13 @@ def test_free_stream_with_fv_elements(orc, N):
         assert np.abs(R).max() < 2e-12 * N * N
 
 
-@pytest.mark.parametrize("N,flux", [(2, 0), (3, 1), (4, 2)])
-def test_conservation_with_fv_elements(orc, N, flux):
+@pytest.mark.parametrize("N,flux,nodes", [(2, 0, 0), (3, 1, 0), (4, 2, 0), (2, 0, 1), (3, 2, 1)])
+def test_conservation_with_fv_elements(orc, N, flux, nodes):
     m = box_mesh(2, N, deform="sinprod", rotate_seed=13)
-    o = orc.Oracle(m, N, mu=0.02, surf_flux=flux)
-    U = random_state(m.n_elems, N, seed=3)
+    o = orc.Oracle(m, N, mu=0.02, surf_flux=flux, nodes=nodes)
+    U = random_state(m.n_elems, N, seed=3, **({} if nodes == 0 else dict(rho=(0.95, 1.05), vel=0.2, p=(0.95, 1.05))))
     _, _, J = o.geometry()
-    wq = _quad_weights(orc, N)
+    wq = _quad_weights(orc, N, nodes)
     rng = np.random.default_rng(5)
     for mask in (_checkerboard(m, 2), np.ones(m.n_elems), rng.integers(0, 2, m.n_elems)):
         o.set_fv_mask(mask)
@@ -68,11 +75,12 @@ def test_conservation_with_fv_elements(orc, N, flux):
         assert (np.abs(tot) < 1e-13 * scale).all(), (mask, tot, scale)
 
 
-def test_all_dg_mask_is_the_dg_operator(orc):
+@pytest.mark.parametrize("nodes", [0, 1])
+def test_all_dg_mask_is_the_dg_operator(orc, nodes):
     N = 3
     m = box_mesh(2, N, deform="sinprod", rotate_seed=21)
-    o = orc.Oracle(m, N, mu=0.01)
-    U = random_state(m.n_elems, N, seed=4)
+    o = orc.Oracle(m, N, mu=0.01, nodes=nodes)
+    U = random_state(m.n_elems, N, seed=4, rho=(0.95, 1.05), vel=0.2, p=(0.95, 1.05))
     R0 = o.time_derivative(U)
     o.set_fv_mask(np.zeros(m.n_elems))
     assert np.array_equal(o.time_derivative(U), R0)
@@ -82,8 +90,8 @@ def test_all_dg_mask_is_the_dg_operator(orc):
     assert np.array_equal(o.time_derivative(U), R0)
 
 
-@pytest.mark.parametrize("N", [4, 7])
-def test_mixed_mesh_free_stream_rounding_does_not_grow(orc, N):
+@pytest.mark.parametrize("N,nodes", [(4, 0), (7, 0), (4, 1), (7, 1)])
+def test_mixed_mesh_free_stream_rounding_does_not_grow(orc, N, nodes):
     """A free stream on a checkerboard of DG and FV elements, 100 LSERK4-5
     steps: the rounding-level departure stays bounded (a coupling of the DG
     side through the inverse means map of its interior sub-cells, instead of
@@ -91,7 +99,7 @@ def test_mixed_mesh_free_stream_rounding_does_not_grow(orc, N):
     steps)."""
     K = 2
     m = box_mesh(K, 1, lo=0.0, hi=2 * np.pi)
-    o = orc.Oracle(m, N, mu=1.0 / 1600)
+    o = orc.Oracle(m, N, mu=1.0 / 1600, nodes=nodes)
     U = np.zeros(o.shape)
     u = np.array([0.1, 0.05, 0.02])
     U[:, 0] = 1.0
@@ -103,6 +111,38 @@ def test_mixed_mesh_free_stream_rounding_does_not_grow(orc, N):
         U = o.rk_steps(U, blk * 0.25, 0.01, 25)
         drift.append(np.abs(U - U0).max() / np.abs(U0).max())
     assert max(drift) < 1e-10 and drift[-1] < 3.0 * drift[0], drift
+
+
+@pytest.mark.parametrize("N,nodes", [(2, 0), (3, 0), (2, 1), (3, 1)])
+def test_mixed_faces_exact_for_a_linear_density(orc, N, nodes):
+    """rho = 1 + 0.1 x with constant velocity and pressure, inviscid, on a
+    Cartesian mesh of DG and FV elements (checkerboard in x and y, random
+    element frames), central volume flux: every part of the scheme is exact
+    for it -- the FV means and unlimited slopes, the DG side's trace means at
+    the mixed faces (equal to the FV side's face values, so the LLF flux is the
+    physical flux), the nodal form of the sub-face fluxes and the DG operator
+    -- so R = -(u, u^2, u v, u w, |u|^2 u / 2) d rho/dx at every node of the
+    elements clear of the periodic jump of rho at x = +-1."""
+    Kx, Ky = 4, 2
+    m = box_mesh(1, 1, dims=(Kx, Ky, 1), rotate_seed=5 + N)
+    o = orc.Oracle(m, N, mu=0.0, nodes=nodes)
+    o.set_vol_flux(1)
+    e = np.arange(m.n_elems)
+    ex, ey = e % Kx, (e // Kx) % Ky
+    o.set_fv_mask((ex + ey) % 2)
+    X = o.node_coords()
+    u = np.array([0.3, 0.1, -0.2])
+    rho = 1.0 + 0.1 * X[:, 0]
+    U = np.zeros((m.n_elems, 5, X.shape[-1]))
+    U[:, 0] = rho
+    U[:, 1:4] = rho[:, None, :] * u[None, :, None]
+    U[:, 4] = 1.0 / (GAMMA - 1) + 0.5 * rho * (u @ u)
+    R = o.time_derivative(U.reshape(o.shape)).reshape(m.n_elems, 5, -1)
+    ref = -0.1 * np.array([u[0], u[0] ** 2, u[0] * u[1], u[0] * u[2], 0.5 * (u @ u) * u[0]])
+    inner = (ex == 1) | (ex == 2)
+    err = np.abs(R[inner] - ref[None, :, None]).max()
+    assert err < 1e-10, err   # rounding of O(1) fluxes over sub-cells of width 1/(2 (N+1))
+    assert np.abs(R[~inner] - ref[None, :, None]).max() > 1e-3   # the jump is felt next to it
 
 
 def _means_matrix(x, n):
@@ -154,13 +194,14 @@ def _muscl_llf_1d(qb, gb, dx, mu):
     return -(F - np.roll(F, 1, 1)) / dx
 
 
-@pytest.mark.parametrize("N,mu", [(2, 0.0), (3, 0.0), (3, 0.02), (5, 0.01)])
-def test_fv_matches_one_dimensional_muscl_llf(orc, N, mu):
+@pytest.mark.parametrize("N,mu,nodes", [(2, 0.0, 0), (3, 0.0, 0), (3, 0.02, 0), (5, 0.01, 0), (3, 0.0, 1),
+                                        (4, 0.02, 1)])
+def test_fv_matches_one_dimensional_muscl_llf(orc, N, mu, nodes):
     K, n = 3, N + 1
     m = box_mesh(K, 1)
-    o = orc.Oracle(m, N, gamma=GAMMA, R=RGAS, Pr=PR, mu=mu)
+    o = orc.Oracle(m, N, gamma=GAMMA, R=RGAS, Pr=PR, mu=mu, nodes=nodes)
     o.set_fv_mask(np.ones(m.n_elems))
-    x, _, _ = orc.basis(N)
+    x, _ = _nodes(orc, N, nodes)
     rng = np.random.default_rng(17 + N)
     rho = rng.uniform(0.7, 1.3, (K, n))
     u = rng.uniform(-0.4, 0.4, (K, n))
@@ -193,8 +234,8 @@ def _state_field(X):
     return U
 
 
-@pytest.mark.parametrize("N,fv", [(2, "all"), (3, "checker"), (4, "random")])
-def test_fv_invariant_under_local_element_frames(orc, N, fv):
+@pytest.mark.parametrize("N,fv,nodes", [(2, "all", 0), (3, "checker", 0), (4, "random", 0), (3, "random", 1)])
+def test_fv_invariant_under_local_element_frames(orc, N, fv, nodes):
     """The same physical state on a Cartesian mesh with identity frames and with
     random element rotations (all face orientations): the residual at each
     physical node agrees."""
@@ -205,7 +246,7 @@ def test_fv_invariant_under_local_element_frames(orc, N, fv):
             "random": np.random.default_rng(3).integers(0, 2, m0.n_elems)}[fv]
     out = []
     for m in (m0, m1):
-        o = orc.Oracle(m, N, gamma=GAMMA, R=RGAS, Pr=PR, mu=0.01)
+        o = orc.Oracle(m, N, gamma=GAMMA, R=RGAS, Pr=PR, mu=0.01, nodes=nodes)
         o.set_fv_mask(mask)
         X = o.node_coords()                                     # [E][3][P]
         U = np.stack([_state_field(X[e]) for e in range(o.E)])  # [E][5][P]
@@ -226,6 +267,3 @@ def test_fv_mask_rejections(orc):
     U = _free_stream(o)
     with pytest.raises(ValueError):
         o.time_derivative_tl(U, U)
-    g = orc.Oracle(m, 2, nodes=1)
-    with pytest.raises(ValueError):
-        g.set_fv_mask(np.ones(m.n_elems))
