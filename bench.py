@@ -561,9 +561,9 @@ def run_pid(args, local):
     the per-GPU load of the paper's weak-scaling runs of the split-form LGL
     operator), 10 steps each: LGL split form in FP64 and with the FP32 operator,
     Gauss nodes (standard weak form) in FP64, each FP64 case also with RK4-14
-    (PID counts stages, so it is per stage), and the LGL cases with half of the
+    (PID counts stages, so it is per stage), and every case with half of the
     elements in the FV sub-cell representation (checkerboard, as the paper's
-    DG/FV runs force it).  Uniform flow
+    DG/FV runs force it; its Table 4 runs are on Gauss nodes).  Uniform flow
     rho = 1, u = (0.1, 0.05, 0.02), p = 1/gamma, mu = 1/1600; every kernel
     does its full work on it.  Reports DOF*stage/s, PID and the free-stream
     preservation error max|U - U0| / max|U0| after the steps."""
@@ -588,7 +588,7 @@ def run_pid(args, local):
         precs = [("fp64", dg.FP64, dg.RK45, False), ("fp64_rk414", dg.FP64, dg.RK414, False)]
         if nodes == dg.NODES_LGL:
             precs.append(("fp32op", dg.FP32OP, dg.RK45, False))
-            precs.append(("fp64_fv50", dg.FP64, dg.RK45, True))
+        precs.append(("fp64_fv50", dg.FP64, dg.RK45, True))
         if args.pid_variants:
             precs = [p for p in precs if p[0] in args.pid_variants.split(",")]
         for prec_name, prec, rk, fv in precs:

@@ -196,10 +196,12 @@ dg_status dg_indicator(dg_ctx* ctx, const double* dU, int32_t var, double log10_
  * integrated exactly from the metric terms, minmod-limited linear
  * reconstruction of (rho, u, v, w, p), local Lax-Friedrichs sub-face fluxes
  * minus the central viscous flux of the sub-cell means (mean BR1 gradients);
- * a face between a DG and an FV element uses the sub-face fluxes, on the DG
- * side in nodal form with the same face integral.  The first call allocates
+ * a face between a DG and an FV element is evaluated on sub-faces, the DG side
+ * entering with the means of its trace over each sub-face (its face nodes, or
+ * on Gauss nodes its values interpolated to the face) and taking the sub-face
+ * fluxes in nodal form, with the same face integral.  The first call allocates
  * about 18 + 12 (N+2)/(N+1) doubles per node plus 5 per face node and sets
- * up the sub-cell geometry.  FP64 operator on LGL nodes only: DG_EUNSUPPORTED
+ * up the sub-cell geometry.  FP64 operator (either node set): DG_EUNSUPPORTED
  * otherwise; the adjoint entry points return DG_EUNSUPPORTED while a mask is
  * set.  dg_max_dt keeps the DG time-step restriction.  Does not synchronise. */
 dg_status dg_set_fv_mask(dg_ctx* ctx, const int32_t* dMask, dg_stream stream);

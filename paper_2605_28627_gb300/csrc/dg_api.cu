@@ -512,12 +512,16 @@ dg_status dg_set_fv_mask(dg_ctx* c, const int32_t* dMask, dg_stream stream) {
   cudaStream_t s = (cudaStream_t)stream;
   DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
   const bool on = dMask != nullptr;
-  if (on && (c->prm.precision != DG_FP64 || c->prm.nodes != DG_NODES_LGL))
-    return fail(c, DG_EUNSUPPORTED, "dg_set_fv_mask: the FV sub-cell operator is built for the FP64 LGL operator");
+  if (on && c->prm.precision != DG_FP64)
+    return fail(c, DG_EUNSUPPORTED, "dg_set_fv_mask: the FV sub-cell operator is built for the FP64 operator");
   if (on && !c->d_fv_mask) {
     const size_t E = c->E, P = c->P, NN = c->NN, n = c->n;
-    std::vector<double> tab;
-    fv_tables(c->N, c->x, tab);
+    std::vector<double> tab, nodes = c->x;   // the context's node set: LGL, or Gauss below
+    if (c->prm.nodes == DG_NODES_LG) {
+      std::vector<double> gtab;
+      gauss_table(c->N, c->x, gtab, &nodes);
+    }
+    fv_tables(c->N, nodes, tab);
     DG_CUDA(cudaMalloc(&c->d_fv_tab, sizeof(double) * tab.size()), c, "FV tables");
     DG_CUDA(cudaMalloc(&c->d_fv_iJb, sizeof(double) * E * P), c, "FV sub-cell Jacobians");
     DG_CUDA(cudaMalloc(&c->d_fv_S, sizeof(double) * E * 3 * (n + 1) * NN * 4), c, "FV area vectors");

@@ -2,7 +2,7 @@
 // finite-volume scheme on (N+1)^3 integral means per DG element, switched on
 // for the elements a troubled-cell indicator selects).
 //
-// The scheme, as built here (FP64, LGL nodes):
+// The scheme, as built here (FP64, on either node set):
 //  * sub-cells: the (N+1)^3 equal sub-cubes of the reference element, width
 //    h = 2/(N+1), indexed like the nodes; sub-faces like the face nodes;
 //  * unknowns: J-weighted sub-cell means of the nodal interpolant,
@@ -294,8 +294,9 @@ k_fv_means(const double* __restrict__ U, const double* __restrict__ grad, const 
 template <int N>
 __global__ void __launch_bounds__(FvShape<N>::FACE_THREADS)
 k_fv_face(const FaceInfo* __restrict__ faces, const int* __restrict__ mask, const double* __restrict__ U,
-          const double* __restrict__ grad, const double* __restrict__ M, const double* __restrict__ S,
-          const double* __restrict__ tab, double* __restrict__ Fb, double* __restrict__ fstar, int F, int E, Gas g) {
+          const double* __restrict__ grad, const double* __restrict__ Uf, const double* __restrict__ gf,
+          const double* __restrict__ M, const double* __restrict__ S, const double* __restrict__ tab,
+          double* __restrict__ Fb, double* __restrict__ fstar, int F, int E, Gas g) {
   using Fs = FvShape<N>;
   constexpr int n = Fs::n, P = Fs::P, NN = Fs::NN, FPB = Fs::FPB;
   __shared__ double sV[NN], sVi[NN];
@@ -322,15 +323,25 @@ k_fv_face(const FaceInfo* __restrict__ faces, const int* __restrict__ mask, cons
     mixed = fvM != fvS;
   }
   const int a = ab % n, b = ab / n;
-  // the DG side's trace at its face node (a, b) of its own face-local indices
+  // the DG side's trace at its face point (a, b) of its own face-local indices:
+  // the face node (LGL nodes), or the values interpolated to the face (Uf, gf:
+  // Gauss nodes)
   if (mixed) {
     const int eD = fvM ? eS : eM, fD = fvM ? fS : fM;
-    const int node = face_node<n>(fD, a, b);
     double q[5], gr[12], vt[12];
+    if (Uf != nullptr) {
+      const size_t o = (size_t)eD * 6 + fD;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) q[v] = U[((size_t)eD * 5 + v) * P + node];
+      for (int v = 0; v < 5; ++v) q[v] = Uf[(o * 5 + v) * NN + ab];
 #pragma unroll
-    for (int r = 0; r < 12; ++r) gr[r] = grad[((size_t)eD * 12 + r) * P + node];
+      for (int r = 0; r < 12; ++r) gr[r] = gf[(o * 12 + r) * NN + ab];
+    } else {
+      const int node = face_node<n>(fD, a, b);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) q[v] = U[((size_t)eD * 5 + v) * P + node];
+#pragma unroll
+      for (int r = 0; r < 12; ++r) gr[r] = grad[((size_t)eD * 12 + r) * P + node];
+    }
     const double ir = 1.0 / q[0];
     const double u = q[1] * ir, v = q[2] * ir, w = q[3] * ir;
     const double p = g.gm1 * (q[4] - 0.5 * (q[1] * u + q[2] * v + q[3] * w));
@@ -729,8 +740,9 @@ static cudaError_t fv_stage_N(const Ctx& c, const StageArgs& a, cudaStream_t s) 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_fv_face<N><<<(c.nfaces + F::FPB - 1) / F::FPB, F::FACE_THREADS, 0, s>>>(
-      c.d_faces, c.d_fv_mask, a.U, (const double*)c.d_grad, c.d_fv_M, c.d_fv_S, c.d_fv_tab, c.d_fv_Fb,
-      (double*)c.d_fstar, c.nfaces, c.E, c.gas);
+      c.d_faces, c.d_fv_mask, a.U, (const double*)c.d_grad, c.prm.nodes == DG_NODES_LG ? c.d_Uf : nullptr,
+      c.prm.nodes == DG_NODES_LG ? c.d_gf : nullptr, c.d_fv_M, c.d_fv_S, c.d_fv_tab, c.d_fv_Fb, (double*)c.d_fstar,
+      c.nfaces, c.E, c.gas);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   StageArgs b = a;
   b.list = c.d_fv_lists;

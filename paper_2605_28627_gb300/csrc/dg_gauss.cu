@@ -465,10 +465,13 @@ k_lift_lg(const double* __restrict__ U, const double* __restrict__ Uf, const dou
 
 // Surface flux at the Gauss face points of each master face, from both sides'
 // face values of the state and of the lifted gradients.
-template <int N>
+// FVSKIP: faces with an FV sub-cell element on either side are left to the FV
+// face kernel (fv_mask: [E], 1 for an FV element).
+template <int N, bool FVSKIP>
 __global__ void __launch_bounds__(128)
 k_face_lg(const double* __restrict__ Uf, const double* __restrict__ gf, const FaceInfo* __restrict__ faces,
-          const double* __restrict__ facegeo, double* __restrict__ fstar, int F, Gas g) {
+          const double* __restrict__ facegeo, double* __restrict__ fstar, int F, Gas g,
+          const int* __restrict__ fv_mask) {
   constexpr int n = N + 1, NN = n * n;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long)F * NN) return;
@@ -477,6 +480,9 @@ k_face_lg(const double* __restrict__ Uf, const double* __restrict__ gf, const Fa
   const FaceInfo fi = faces[f];
   const int eM = dg_idx(fi.master >> 3, F / 3, kSiteGaussFace), fM = fi.master & 7;
   const int eS = dg_idx(fi.slave >> 3, F / 3, kSiteGaussFace), fS = fi.slave & 7;
+  if constexpr (FVSKIP) {
+    if (fv_mask[eM] || fv_mask[eS]) return;
+  }
   int p2, q2;
   apply_flip<n>(fi.flip, p, q, p2, q2);
   const int pq2 = p2 + n * q2;
@@ -509,7 +515,9 @@ constexpr size_t volume_lg_smem() {
 // Weak volume and surface terms (Eq. 2):
 //   J U_t,i = - sum_faces l_{i_d}(+-1)/w_{i_d} F*_out + sum_d sum_m (w_m/w_{i_d}) D_{m i_d} Ft^d_m,
 // Ft^d = (f - f_v)(q, g) . Ja^d; then 1/J, the source and the LSERK update.
-template <int N, int EPB>
+// LIST: the element slots come from a.list (the DG elements when FV sub-cell
+// elements exist), idle past its end.
+template <int N, int EPB, bool LIST>
 __global__ void __launch_bounds__(Shape<N, EPB>::THREADS)
 k_volume_lg(StageArgs a, const double* __restrict__ metrics, const double* __restrict__ grad,
             const double* __restrict__ fstar, const int* __restrict__ elem_face, const double* __restrict__ mms,
@@ -520,7 +528,14 @@ k_volume_lg(StageArgs a, const double* __restrict__ metrics, const double* __res
   __shared__ double sDw[n * n], sT[2 * n];   // weak D; l(-1)/w, l(+1)/w
   __shared__ double s_tc[2];                 // sin, cos of pi t (manufactured source)
   const int le = threadIdx.x / P, id = threadIdx.x - le * P;
-  const int e = blockIdx.x * EPB + le;
+  int e = blockIdx.x * EPB + le;
+  if constexpr (LIST) {
+    const int nslot = *a.list_len;
+    e = e < nslot ? a.list[e] : E;
+    if constexpr (EPB == 1) {
+      if (e >= E) return;   // the whole block, before any barrier
+    }
+  }
   const bool active = e < E;
   double* sF = sm + le * PER;   // [3][5][P] contravariant fluxes
   double* sFs = sF + 15 * P;    // [6][5][NN] outward surface fluxes
@@ -633,7 +648,10 @@ static cudaError_t setup_lg_N() {
   cudaError_t e = cudaFuncSetAttribute(k_lift_lg<N, S::EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)lift_lg_smem<N, S::EPB>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_volume_lg<N, S::EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_volume_lg<N, S::EPB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)volume_lg_smem<N, S::EPB>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_volume_lg<N, S::EPB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)volume_lg_smem<N, S::EPB>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_prolong_lg<N, S::EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -674,8 +692,12 @@ static cudaError_t lift_lg_N(const Ctx& c, const double* U, cudaStream_t s) {
 template <int N>
 static cudaError_t face_lg_N(const Ctx& c, cudaStream_t s) {
   const long tot = (long)c.nfaces * (N + 1) * (N + 1);
-  k_face_lg<N><<<(int)((tot + 127) / 128), 128, 0, s>>>(c.d_Uf, c.d_gf, c.d_faces, c.d_facegeo,
-                                                         (double*)c.d_fstar, c.nfaces, c.gas);
+  if (c.fv_on)
+    k_face_lg<N, true><<<(int)((tot + 127) / 128), 128, 0, s>>>(c.d_Uf, c.d_gf, c.d_faces, c.d_facegeo,
+                                                               (double*)c.d_fstar, c.nfaces, c.gas, c.d_fv_mask);
+  else
+    k_face_lg<N, false><<<(int)((tot + 127) / 128), 128, 0, s>>>(c.d_Uf, c.d_gf, c.d_faces, c.d_facegeo,
+                                                                (double*)c.d_fstar, c.nfaces, c.gas, nullptr);
   return cudaGetLastError();
 }
 
@@ -683,8 +705,14 @@ template <int N>
 static cudaError_t volume_lg_N(const Ctx& c, const StageArgs& a, cudaStream_t s) {
   using S = Shape<N>;
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
-  k_volume_lg<N, S::EPB><<<blocks, S::THREADS, volume_lg_smem<N, S::EPB>(), s>>>(
-      a, c.d_metrics, (const double*)c.d_grad, (const double*)c.d_fstar, c.d_elem_face, c.d_mms, c.d_lgb, c.E, c.gas);
+  if (a.list != nullptr)
+    k_volume_lg<N, S::EPB, true><<<blocks, S::THREADS, volume_lg_smem<N, S::EPB>(), s>>>(
+        a, c.d_metrics, (const double*)c.d_grad, (const double*)c.d_fstar, c.d_elem_face, c.d_mms, c.d_lgb, c.E,
+        c.gas);
+  else
+    k_volume_lg<N, S::EPB, false><<<blocks, S::THREADS, volume_lg_smem<N, S::EPB>(), s>>>(
+        a, c.d_metrics, (const double*)c.d_grad, (const double*)c.d_fstar, c.d_elem_face, c.d_mms, c.d_lgb, c.E,
+        c.gas);
   return cudaGetLastError();
 }
 

@@ -51,10 +51,10 @@ static cudaError_t setup_any() {
 }
 
 cudaError_t launch_volume(const Ctx& c, const StageArgs& a, cudaStream_t s, bool latency_ok) {
-  if (c.prm.nodes == DG_NODES_LG) return launch_volume_lg(c, a, s);
   // with FV sub-cell elements: the FV stage, which calls back here with the
   // list of the DG elements
   if (c.fv_on && a.list == nullptr) return launch_fv_stage(c, a, s);
+  if (c.prm.nodes == DG_NODES_LG) return launch_volume_lg(c, a, s);
   if (latency_ok && use_latency_kernels(c)) return launch_volume_lat(c, a, s);
   switch (c.N) {
     case 1: return volume_any<1>(c, a, s);

@@ -1,6 +1,7 @@
 """FV sub-cell elements on the GPU (dg_set_fv_mask) against the oracle's FV
 branch, element by element, through the C ABI.
 
+Both node sets (LGL with the split form, Legendre-Gauss with the weak form).
 Bar: the DG operator's, R(U) within 1e-12 relative per variable (scaled by
 max |R|), grown with the conditioning of the mesh-sample interpolation as for
 the DG tests; RK steps within 1e-10.  The FV residual reaches the nodes
@@ -52,10 +53,13 @@ def _rel_err_per_var(got, ref):
     return np.array([np.abs(got[:, v] - ref[:, v]).max() / max(np.abs(ref[:, v]).max(), 1e-300) for v in range(5)])
 
 
-def _state(n_elems, N, seed):
+def _state(n_elems, N, seed, nodes=0):
     """Random admissible state of moderate amplitude: its sub-cell means stay
     admissible up to N = 9 (the means map has row sums 1 but |V| row sums up
-    to 1.9 per direction)."""
+    to 1.9 per direction); narrower on Gauss nodes, whose face values are
+    extrapolated from the nodes."""
+    if nodes == 1:
+        return random_state(n_elems, N, seed=seed, rho=(0.95, 1.05), vel=0.2, p=(0.95, 1.05))
     return random_state(n_elems, N, seed=seed, rho=(0.9, 1.1), vel=0.3, p=(0.9, 1.1))
 
 
@@ -91,6 +95,24 @@ def test_fv_time_derivative_parity(orc, dg, N, kind):
     assert (err < _rtol(N)).all(), err
 
 
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 7, 9])
+@pytest.mark.parametrize("kind", ["checker", "random"])
+def test_fv_time_derivative_parity_gauss_nodes(orc, dg, N, kind):
+    K = 3 if N <= 5 else 2
+    mesh = box_mesh(K, N, deform="sinprod", rotate_seed=760 + N)
+    kw = dict(mu=0.02, surf_flux=N % 3, nodes=1)
+    o, s = orc.Oracle(mesh, N, **kw), dg.Solver(mesh, N, **kw)
+    mask = _mask(kind, K, seed=N + 20)
+    o.set_fv_mask(mask)
+    s.set_fv_mask(_cuda(mask))
+    U = _state(mesh.n_elems, N, 860 + N, nodes=1)
+    ref = o.time_derivative(U)
+    assert np.isfinite(ref).all()
+    err = _rel_err_per_var(s.time_derivative(_cuda(U)).cpu().numpy(), ref)
+    print("FV parity (Gauss nodes) N=%d %s: max rel err %.3e (bar %.1e)" % (N, kind, err.max(), _rtol(N)))
+    assert (err < _rtol(N)).all(), err
+
+
 @pytest.mark.parametrize("N", [2, 3])
 def test_fv_parity_sutherland_and_roe(orc, dg, N):
     mesh = box_mesh(3, N, deform="sinprod", rotate_seed=720 + N)
@@ -104,13 +126,14 @@ def test_fv_parity_sutherland_and_roe(orc, dg, N):
     assert (err < _rtol(N)).all(), err
 
 
-def test_all_dg_mask_and_mask_off_are_the_dg_operator_bitwise(dg):
+@pytest.mark.parametrize("nodes", [0, 1])
+def test_all_dg_mask_and_mask_off_are_the_dg_operator_bitwise(dg, nodes):
     """Above the latency-kernel size (21952 nodes), where the DG operator runs
     the same kernels with and without a mask."""
     N = 3
     mesh = box_mesh(7, N, deform="sinprod", rotate_seed=31)
-    s = dg.Solver(mesh, N, mu=0.01)
-    U = _cuda(_state(mesh.n_elems, N, 5))
+    s = dg.Solver(mesh, N, mu=0.01, nodes=nodes)
+    U = _cuda(_state(mesh.n_elems, N, 5, nodes))
     R0 = s.time_derivative(U).clone()
     s.set_fv_mask(torch.zeros(mesh.n_elems, dtype=torch.int32, device="cuda"))
     assert torch.equal(s.time_derivative(U), R0)
@@ -120,14 +143,14 @@ def test_all_dg_mask_and_mask_off_are_the_dg_operator_bitwise(dg):
     assert torch.equal(s.time_derivative(U), R0)
 
 
-@pytest.mark.parametrize("N", [3, 5])
-def test_fv_mms_rk_parity_with_mask_changes(orc, dg, N):
+@pytest.mark.parametrize("N,nodes", [(3, 0), (5, 0), (3, 1)])
+def test_fv_mms_rk_parity_with_mask_changes(orc, dg, N, nodes):
     """LSERK4-5 steps with a checkerboard, then another mask inside the same
     captured graph (the kernels read the mask at run time), then DG again."""
     prm = mms_params()
     K = 3
     mesh = box_mesh(K, N, deform="sinprod", rotate_seed=740 + N)
-    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1, nodes=nodes)
     o, s = orc.Oracle(mesh, N, **kw), dg.Solver(mesh, N, **kw)
     U0 = o.initial_state("mms", 0.0)
     Ud = _cuda(U0)
@@ -150,10 +173,11 @@ def test_fv_mms_rk_parity_with_mask_changes(orc, dg, N):
     assert np.abs(got - ref).max() / np.abs(ref).max() < RTOL_RK
 
 
-def test_fv_free_stream_and_conservation_on_gpu(orc, dg):
+@pytest.mark.parametrize("nodes", [0, 1])
+def test_fv_free_stream_and_conservation_on_gpu(orc, dg, nodes):
     N, K = 3, 8
     mesh = box_mesh(K, N, deform="sinprod", rotate_seed=77)
-    s = dg.Solver(mesh, N, mu=0.01)
+    s = dg.Solver(mesh, N, mu=0.01, nodes=nodes)
     s.set_fv_mask(_checkerboard(K))
     U = np.zeros(s.shape)
     r, u, p = 1.2, np.array([0.3, -0.2, 0.45]), 0.9
@@ -162,24 +186,24 @@ def test_fv_free_stream_and_conservation_on_gpu(orc, dg):
     U[:, 4] = p / 0.4 + 0.5 * r * u @ u
     R = s.time_derivative(_cuda(U))
     assert float(R.abs().max()) < 1e-11
-    U = _cuda(_state(mesh.n_elems, N, 9))
+    U = _cuda(_state(mesh.n_elems, N, 9, nodes))
     R = s.time_derivative(U)
     _, J = s.geometry()
-    _, w, _ = orc.basis(N)
+    w = (orc.basis(N) if nodes == 0 else orc.gauss_basis(N))[1]
     wq = torch.from_numpy(np.einsum("k,j,i->kji", w, w, w).reshape(-1)).cuda()
     tot = torch.einsum("evp,ep->v", R.reshape(s.E, 5, -1), J * wq)
     scale = torch.einsum("evp,ep->v", R.reshape(s.E, 5, -1).abs(), J * wq)
     assert bool((tot.abs() <= 1e-13 * scale).all()), (tot, scale)
 
 
-@pytest.mark.parametrize("N", [4, 7, 9])
-def test_fv_mixed_free_stream_stays_bounded_on_gpu(dg, N):
+@pytest.mark.parametrize("N,nodes", [(4, 0), (7, 0), (9, 0), (3, 1), (7, 1)])
+def test_fv_mixed_free_stream_stays_bounded_on_gpu(dg, N, nodes):
     """A free stream on a DG/FV checkerboard, 200 LSERK4-5 steps at CFL 0.9:
     the rounding-level departure stays bounded (no growing mode at the DG/FV
     interfaces)."""
     K = 4
     mesh = box_mesh(K, 1, lo=0.0, hi=2 * math.pi)
-    s = dg.Solver(mesh, N, mu=1.0 / 1600)
+    s = dg.Solver(mesh, N, mu=1.0 / 1600, nodes=nodes)
     s.set_fv_mask(_checkerboard(K))
     u = (0.1, 0.05, 0.02)
     U = torch.zeros(s.shape, dtype=torch.float64, device="cuda")
@@ -266,9 +290,6 @@ def test_fv_rejections(dg):
     s32 = dg.Solver(mesh, 2, precision=1)
     with pytest.raises(dg.DGError):
         s32.set_fv_mask(np.ones(mesh.n_elems, dtype=np.int32))
-    slg = dg.Solver(mesh, 2, nodes=1)
-    with pytest.raises(dg.DGError):
-        slg.set_fv_mask(np.ones(mesh.n_elems, dtype=np.int32))
     s = dg.Solver(mesh, 2, mu=0.01)
     s.set_fv_mask(np.ones(mesh.n_elems, dtype=np.int32))
     U = _cuda(_state(mesh.n_elems, 2, 1))
