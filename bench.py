@@ -47,6 +47,13 @@ def build_mesh(N):
 # the median over the launches of one ncu capture of the current kernels
 # (profiles/volume_traffic_N7_mms16.txt); absent = not captured.
 MEASURED_TRAFFIC = {(7, "fp64"): 670.667520e6 + 217.116672e6, (7, "fp32op"): 406.712064e6 + 143.888640e6}
+# The other orders of the sweep, DRAM read + write per launch (medians, MB) from one capture of
+# the volume kernels of `--sweep 1,2,3,4,5,6,8,9`; up to N = 4 the working set stays in the
+# 129 MB L2 between launches, so DRAM sees less than the kernel's algorithmic bytes.
+for _N, _f64, _f32 in ((1, 11.0, 7.1), (2, 34.7, 22.7), (3, 79.7, 52.3), (4, 165.9, 102.6), (5, 302.5, 203.7),
+                       (6, 499.7, 344.3), (8, 1084.3, 800.5), (9, 1765.2, 1067.8)):
+    MEASURED_TRAFFIC[(_N, "fp64")] = _f64 * 1e6
+    MEASURED_TRAFFIC[(_N, "fp32op")] = _f32 * 1e6
 
 
 # ---------------------------------------------------------------------------
@@ -910,6 +917,8 @@ def main():
                 ach = volume_flops_per_dof(Ns) * dofs / (ms3n[2] * 1e-3) / 1e12
                 sweep[str(Ns)] = {"dof_stage_per_s": dofs * 5 / (ms * 1e-3), "pid_ns": ms * 1e6 / (dofs * 5),
                                   "volume_ms": ms3n[2], "volume_roofline_frac": ach / fp64_peak}
+            sweep[str(Ns)]["volume_traffic"] = MEASURED_TRAFFIC.get((Ns, "fp64"))
+            sweep[str(Ns)]["fp32op_volume_traffic"] = MEASURED_TRAFFIC.get((Ns, "fp32op"))
             # the FP32-operator path on the same mesh and state, and its
             # deviation from the FP64 path after the same 8 steps
             states = []
