@@ -293,7 +293,8 @@ dg_status dg_ensemble_destroy(dg_ensemble* ens);
 /* nsteps LSERK4-5 steps of every member r: state dU[r] with register dG[r]
  * (device arrays of the member's dg_state_len), from time t[r] with step
  * dt[r] (host arrays of n doubles).  Identical per member to dg_rk_step.
- * DG_EINVAL if a pointer is NULL or the 2n arrays are not all distinct.
+ * DG_EINVAL if a pointer is NULL or the 2n arrays are not all distinct;
+ * DG_EUNSUPPORTED while a member has FV sub-cell elements (dg_set_fv_mask).
  * Waits for earlier work on `stream`, then enqueues one graph launch. */
 dg_status dg_ensemble_step(dg_ensemble* ens, double* const* dU, double* const* dG, const double* t,
                            const double* dt, int32_t nsteps, dg_stream stream);

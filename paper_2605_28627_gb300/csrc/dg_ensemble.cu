@@ -597,6 +597,9 @@ dg_status dg_ensemble_step(dg_ensemble* e, double* const* dU, double* const* dG,
   if (!e || !dU || !dG || !t || !dt || nsteps < 0) return ens_fail(e, DG_EINVAL, "dg_ensemble_step: bad argument");
   if (nsteps == 0) return DG_OK;
   const int n = (int)e->members.size();
+  for (int r = 0; r < n; ++r)
+    if (e->members[r]->fv_on)
+      return ens_fail(e, DG_EUNSUPPORTED, "dg_ensemble_step: a member has FV sub-cell elements (not in the ensemble)");
   cudaStream_t s = (cudaStream_t)stream;
   ENS_CUDA(cudaSetDevice(e->device), e, "cudaSetDevice");
   bool changed = false;

@@ -297,3 +297,11 @@ def test_fv_rejections(dg):
         s.time_derivative_vjp(U, torch.ones_like(U))
     with pytest.raises(ValueError):
         s.set_fv_mask(np.ones(mesh.n_elems + 1, dtype=np.int32))
+    # an ensemble member with FV elements is refused when stepped
+    ens = dg.Ensemble([s])
+    G = torch.empty_like(U)
+    with pytest.raises(dg.DGError):
+        ens.step([U], [G], [0.0], [1e-3], nsteps=1)
+    s.set_fv_mask(None)
+    ens.step([U], [G], [0.0], [1e-3], nsteps=1)
+    ens.close()
