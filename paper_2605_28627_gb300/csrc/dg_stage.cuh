@@ -668,8 +668,53 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     }
   };
   static_assert(FULL + (HALF ? 1 : 0) == S::ROUNDS, "pair-loop rounds");
+  // FP32 with n = 2, 4 or 8: a xi-line is n consecutive lanes of one warp, so
+  // the xi sweep passes the partner's share by a warp shuffle (no exchange
+  // buffer, no barrier) and does its half-used shift on the lower half of each
+  // line.  (FP64 keeps the packed exchange: its pipe charges masked lanes.)
+  constexpr bool SHFL_XI = sizeof(R) == 4 && (n == 2 || n == 4 || n == 8);
+  if constexpr (SHFL_XI) {
+    const int r = i;
+    const int line0 = id - r;
+    const unsigned base = (threadIdx.x & 31u) & ~unsigned(n - 1);
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
+    for (int s = 1; s <= (HALF ? n / 2 : FULL); ++s) {
+      const bool half = HALF && s == n / 2;
+      const int m = (r + s) & (n - 1);
+      R F[5] = {0, 0, 0, 0, 0};
+      if (active && (!half || r < n / 2)) {
+        const int mid = line0 + m;
+        R sdl = 0;
+        if constexpr (sizeof(R) == 4) sdl = sDl[id] + sDl[mid];
+        ec_pair<R>(rho, sR[mid], beta, sB[mid], u + sU[mid], v + sU[P + mid], w + sU[2 * P + mid], kk + sK[mid],
+                   sdl, Ja[0] + sJd[mid], Ja[1] + sJd[P + mid], Ja[2] + sJd[2 * P + mid], inv_gm1, g, F);
+        const R dm = sD[r * n + m];
+        acc[0] = fma(dm, F[0], acc[0]);
+        acc[1] = fma(dm, F[1], acc[1]);
+        acc[2] = fma(dm, F[2], acc[2]);
+        acc[3] = fma(dm, F[3], acc[3]);
+        acc[4] = fma(dm, F[4], acc[4]);
+      }
+      // the share of the pair (r - s, r), computed by the lane of node r - s
+      const int src = (r - s) & (n - 1);
+      R Fs[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Fs[c] = __shfl_sync(0xffffffffu, F[c], (int)(base | unsigned(src)));
+      if (active && (!half || r >= n / 2)) {
+        const R dm = sD[r * n + src];
+        acc[0] = fma(dm, Fs[0], acc[0]);
+        acc[1] = fma(dm, Fs[1], acc[1]);
+        acc[2] = fma(dm, Fs[2], acc[2]);
+        acc[3] = fma(dm, Fs[3], acc[3]);
+        acc[4] = fma(dm, Fs[4], acc[4]);
+      }
+    }
+    // the eta sweep overwrites this node's metric entries, which the other
+    // lanes of its xi-line (this warp) have read above
+    __syncwarp();
+  }
+#pragma unroll
+  for (int d = SHFL_XI ? 1 : 0; d < 3; ++d) {
     const int r = ijk[d];
     const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
     const int line0 = id - r * stride;
