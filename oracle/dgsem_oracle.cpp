@@ -254,6 +254,10 @@ struct Ctx {
   std::vector<double> fn;     // [face][3][n*n]  unit normal of the master side
   std::vector<double> fsJ;    // [face][n*n]     surface element of the master side
   std::vector<int> fv_mask;   // [e] 1: FV sub-cell element (empty: none)
+  // mortars (non-conforming faces, 2:1): [m][14] = big (e, f), four small (e, f, flip)
+  int M = 0;
+  std::vector<int> mortars;
+  std::vector<double> mI;     // [2][n][n]: l_j at the nodes of half k of [-1, 1] (interpolation)
   std::string err;
 };
 
@@ -370,24 +374,55 @@ static bool build_faces(Ctx& c, const int* face_nbr) {
   c.nbr.assign(face_nbr, face_nbr + (size_t)E * 18);
   c.face_id.assign(E * 6, -1);
   c.master.assign(E * 6, 0);
+  for (int m = 0; m < c.M; ++m) {   // every side of a mortar names it back
+    const int* r = &c.mortars[(size_t)m * 14];
+    bool ok = r[0] >= 0 && r[0] < E && r[1] >= 0 && r[1] < 6 &&
+              c.nbr[(r[0] * 6 + r[1]) * 3] == -1 - m && c.nbr[(r[0] * 6 + r[1]) * 3 + 1] == 0;
+    for (int k = 0; k < 4 && ok; ++k) {
+      const int es = r[2 + 3 * k], fs = r[3 + 3 * k], fl = r[4 + 3 * k];
+      ok = es >= 0 && es < E && fs >= 0 && fs < 6 && fl >= 0 && fl < 8 && c.nbr[(es * 6 + fs) * 3] == -1 - m &&
+           c.nbr[(es * 6 + fs) * 3 + 1] == k;
+    }
+    if (!ok) { c.err = "mortar table does not match the connectivity"; return false; }
+  }
   for (int e = 0; e < E; ++e)
     for (int f = 0; f < 6; ++f) {
       int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1];
       int fl = c.nbr[(e * 6 + f) * 3 + 2];
-      if (e2 < 0 || e2 >= E || f2 < 0 || f2 > 5 || fl < 0 || fl > 7) { c.err = "connectivity out of range"; return false; }
+      if (e2 < 0) {   // a side of mortar -1 - e2
+        const int m = -1 - e2;
+        if (m >= c.M || f2 < 0 || f2 > 3) { c.err = "connectivity out of range"; return false; }
+        const int* r = &c.mortars[(size_t)m * 14];
+        const bool big = r[0] == e && r[1] == f, small = r[2 + 3 * f2] == e && r[3 + 3 * f2] == f;
+        if (!big && !small) { c.err = "connectivity not reciprocal"; return false; }
+        continue;
+      }
+      if (e2 >= E || f2 < 0 || f2 > 5 || fl < 0 || fl > 7) { c.err = "connectivity out of range"; return false; }
       if (c.nbr[(e2 * 6 + f2) * 3 + 0] != e || c.nbr[(e2 * 6 + f2) * 3 + 1] != f) { c.err = "connectivity not reciprocal"; return false; }
     }
   int nf = 0;
   for (int e = 0; e < E; ++e)
     for (int f = 0; f < 6; ++f) {
       int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1];
-      if (e * 6 + f < e2 * 6 + f2) { c.master[e * 6 + f] = 1; c.face_id[e * 6 + f] = nf++; }
+      // the two sides of a conforming face share one; each side of a mortar has its own
+      if (e2 < 0 || e * 6 + f < e2 * 6 + f2) { c.master[e * 6 + f] = 1; c.face_id[e * 6 + f] = nf++; }
     }
   for (int e = 0; e < E; ++e)
     for (int f = 0; f < 6; ++f)
       if (!c.master[e * 6 + f]) {
         int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1];
         c.face_id[e * 6 + f] = c.face_id[e2 * 6 + f2];
+      }
+  // mortar interpolation: l_j at the LGL nodes of each half of [-1, 1]
+  c.mI.assign((size_t)2 * n * n, 0.0);
+  for (int k = 0; k < 2; ++k)
+    for (int a = 0; a < n; ++a)
+      for (int j = 0; j < n; ++j) {
+        const double xs = 0.5 * (c.b.x[a] + 2.0 * k - 1.0);
+        double l = 1.0;
+        for (int m = 0; m < n; ++m)
+          if (m != j) l *= (xs - c.b.x[m]) / (c.b.x[j] - c.b.x[m]);
+        c.mI[((size_t)k * n + a) * n + j] = l;
       }
   c.nfaces = nf;
   c.fn.assign((size_t)nf * 3 * nn, 0.0);
@@ -605,11 +640,87 @@ static void mms_source(const Params& pr, const double x[3], double t, double out
 // phi = (u, v, w, T) of every element:
 //   g_l = (1/J) [ sum_d Ja^d_l (D_d phi) + sum_faces (phi* - phi) (n_l sJ) / w_end ],
 // phi* = 1/2 (phi + phi_neighbour), n sJ the element's own outward normal.
+// ---------------------------------------------------------------------------
+// Mortars (Sec. 3.2.2, Algorithm 1; Kopriva 1996): a big face split into four
+// quadrants k = a + 2 b that are faces of four small elements.  Values of the
+// big face are interpolated to the nodes of each quadrant (numbered (pp, qq)
+// in the big face's directions),
+//   v_k(pp, qq) = sum_ij I_a[pp][i] I_b[qq][j] v(i, j),  I_h[x][j] = l_j((x_x + 2h - 1)/2),
+// and quadrant data go back onto the big face by the projection with the LGL
+// quadrature (exact for the constant mode, so face integrals are kept):
+//   v(i, j) = scale / (w_i w_j) sum_k sum_{pp,qq} w_pp w_qq I_a[pp][i] I_b[qq][j] v_k(pp, qq),
+// scale = 1/4 for point values (the lifting's face average), 1 for fluxes
+// times sJ (a quadrant's surface element is a quarter of the big face's).
+template <class T>
+static void mortar_interp(const Ctx& c, const T* big, int k, T* out) {
+  const int n = c.n, a = k & 1, b = k >> 1;
+  const double* Ia = &c.mI[(size_t)a * n * n];
+  const double* Ib = &c.mI[(size_t)b * n * n];
+  for (int qq = 0; qq < n; ++qq)
+    for (int pp = 0; pp < n; ++pp) {
+      T s = T(0.0);
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) s += (Ia[pp * n + i] * Ib[qq * n + j]) * big[i + n * j];
+      out[pp + n * qq] = s;
+    }
+}
+
+template <class T>
+static void mortar_project(const Ctx& c, const T* const quad[4], double scale, T* out) {
+  const int n = c.n;
+  const std::vector<double>& w = c.b.w;
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      T s = T(0.0);
+      for (int k = 0; k < 4; ++k) {
+        const double* Ia = &c.mI[(size_t)(k & 1) * n * n];
+        const double* Ib = &c.mI[(size_t)(k >> 1) * n * n];
+        for (int qq = 0; qq < n; ++qq)
+          for (int pp = 0; pp < n; ++pp)
+            s += (w[pp] * w[qq] * Ia[pp * n + i] * Ib[qq * n + j]) * quad[k][pp + n * qq];
+      }
+      out[i + n * j] = s * (scale / (w[i] * w[j]));
+    }
+}
+
+// Whether local face f of element e is the big side of mortar m.
+static inline bool mortar_big(const Ctx& c, int m, int e, int f) {
+  return c.mortars[(size_t)m * 14] == e && c.mortars[(size_t)m * 14 + 1] == f;
+}
+
 template <class T>
 static void lifting(const Ctx& c, const T* phi, T* G) {
   int n = c.n, P = c.P, E = c.E, N = c.N;
   const std::vector<double>& D = c.b.D;
   double wend = c.b.w[0];
+  // mortar face averages: on each quadrant (the small side's own node order)
+  // and projected onto the big face
+  const int nn = n * n;
+  std::vector<T> star_s((size_t)c.M * 4 * 4 * nn), star_b((size_t)c.M * 4 * nn);
+  for (int m = 0; m < c.M; ++m) {
+    const int* r = &c.mortars[(size_t)m * 14];
+    for (int ph = 0; ph < 4; ++ph) {
+      std::vector<T> big(nn), q[4];
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) big[i + n * j] = phi[((size_t)r[0] * 4 + ph) * P + face_vol(n, r[1], i, j)];
+      const T* qp[4];
+      for (int k = 0; k < 4; ++k) {
+        q[k].resize(nn);
+        mortar_interp(c, big.data(), k, q[k].data());
+        const int es = r[2 + 3 * k], fs = r[3 + 3 * k], fl = r[4 + 3 * k];
+        for (int qq = 0; qq < n; ++qq)
+          for (int pp = 0; pp < n; ++pp) {
+            int p2, q2;
+            flip_map(fl, N, pp, qq, p2, q2);
+            const T st = 0.5 * (phi[((size_t)es * 4 + ph) * P + face_vol(n, fs, p2, q2)] + q[k][pp + n * qq]);
+            star_s[(((size_t)m * 4 + k) * 4 + ph) * nn + p2 + n * q2] = st;
+            q[k][pp + n * qq] = st;
+          }
+        qp[k] = q[k].data();
+      }
+      mortar_project(c, qp, 0.25, &star_b[((size_t)m * 4 + ph) * nn]);
+    }
+  }
 #pragma omp parallel for schedule(dynamic, 4) if (kParallel<T>)
   for (int e = 0; e < E; ++e) {
     for (int k = 0; k < n; ++k)
@@ -639,16 +750,20 @@ static void lifting(const Ctx& c, const T* phi, T* G) {
     for (int f = 0; f < 6; ++f) {
       int d = f / 2, s = f % 2;
       int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1], fl = c.nbr[(e * 6 + f) * 3 + 2];
+      const int mo = e2 < 0 ? -1 - e2 : -1;
+      const bool mbig = mo >= 0 && mortar_big(c, mo, e, f);
       for (int q = 0; q < n; ++q)
         for (int p = 0; p < n; ++p) {
           int id = face_vol(n, f, p, q);
-          int p2, q2;
-          flip_map(fl, N, p, q, p2, q2);
-          int id2 = face_vol(n, f2, p2, q2);
+          int p2 = 0, q2 = 0;
+          if (mo < 0) flip_map(fl, N, p, q, p2, q2);
+          const int id2 = mo < 0 ? face_vol(n, f2, p2, q2) : 0;
           for (int ph = 0; ph < 4; ++ph) {
             T mine = phi[((size_t)e * 4 + ph) * P + id];
-            T other = phi[((size_t)e2 * 4 + ph) * P + id2];
-            T star = 0.5 * (mine + other);
+            T star;
+            if (mo < 0) star = 0.5 * (mine + phi[((size_t)e2 * 4 + ph) * P + id2]);
+            else if (mbig) star = star_b[((size_t)mo * 4 + ph) * nn + p + n * q];
+            else star = star_s[(((size_t)mo * 4 + f2) * 4 + ph) * nn + p + n * q];
             for (int l = 0; l < 3; ++l) {
               double nsJ = (2.0 * s - 1.0) * c.Ja[(((size_t)e * 3 + d) * 3 + l) * P + id];
               G[((size_t)e * 12 + ph * 3 + l) * P + id] += (star - mine) * (nsJ / wend);
@@ -790,6 +905,7 @@ static void rhs(const Ctx& c, const T* U, T* Ut, double t, T mu) {
       if (!c.master[e * 6 + f]) continue;
       int fid = c.face_id[e * 6 + f];
       int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1], fl = c.nbr[(e * 6 + f) * 3 + 2];
+      if (e2 < 0) continue;   // a mortar side: below
       for (int q = 0; q < n; ++q)
         for (int p = 0; p < n; ++p) {
           int id = face_vol(n, f, p, q);
@@ -814,6 +930,57 @@ static void rhs(const Ctx& c, const T* U, T* Ut, double t, T mu) {
             Fs[((size_t)fid * 5 + v) * nn + p + n * q] = (fa[v] - 0.5 * (fvL[v] + fvR[v])) * sJ;
         }
     }
+  // --- mortars: fluxes on the quadrants (the small side's normal and surface
+  // element, the big side's state and gradients interpolated), the big face's
+  // flux their projection, pointing out of the big element
+  for (int m = 0; m < c.M; ++m) {
+    const int* r = &c.mortars[(size_t)m * 14];
+    const int fidB = c.face_id[r[0] * 6 + r[1]];
+    std::vector<T> big((size_t)17 * nn), qi((size_t)17 * nn), Fq((size_t)4 * 5 * nn);
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        const int id = face_vol(n, r[1], i, j);
+        for (int v = 0; v < 5; ++v) big[(size_t)v * nn + i + n * j] = U[((size_t)r[0] * 5 + v) * P + id];
+        for (int rr = 0; rr < 12; ++rr) big[(size_t)(5 + rr) * nn + i + n * j] = G[((size_t)r[0] * 12 + rr) * P + id];
+      }
+    for (int k = 0; k < 4; ++k) {
+      const int es = r[2 + 3 * k], fs = r[3 + 3 * k], fl = r[4 + 3 * k];
+      const int fidS = c.face_id[es * 6 + fs];
+      for (int x = 0; x < 17; ++x) mortar_interp(c, &big[(size_t)x * nn], k, &qi[(size_t)x * nn]);
+      for (int qq = 0; qq < n; ++qq)
+        for (int pp = 0; pp < n; ++pp) {
+          int p2, q2;
+          flip_map(fl, N, pp, qq, p2, q2);
+          const int id = face_vol(n, fs, p2, q2), o = p2 + n * q2;
+          T qL[5], qR[5], gL[12], gR[12];
+          q_at(es, id, qL);
+          grad_at(es, id, gL);
+          for (int v = 0; v < 5; ++v) qR[v] = qi[(size_t)v * nn + pp + n * qq];
+          for (int rr = 0; rr < 12; ++rr) gR[rr] = qi[(size_t)(5 + rr) * nn + pp + n * qq];
+          const Prim<T>& L = W[(size_t)es * P + id];
+          const Prim<T> Rr = cons2prim(pr, qR);
+          T nv[3];
+          for (int l = 0; l < 3; ++l) nv[l] = T(c.fn[((size_t)fidS * 3 + l) * nn + o]);
+          const double sJ = c.fsJ[(size_t)fidS * nn + o];
+          T fa[5], fvL[5], fvR[5];
+          if (pr.surf_flux == 1) ec_flux(pr, L, Rr, nv, fa);
+          else if (pr.surf_flux == 2) roe_flux(pr, qL, L, qR, Rr, nv, fa);
+          else llf_flux(pr, qL, L, qR, Rr, nv, fa);
+          visc_flux(pr, L, gL, mu, nv, fvL);
+          visc_flux(pr, Rr, gR, mu, nv, fvR);
+          for (int v = 0; v < 5; ++v) {
+            const T F = (fa[v] - 0.5 * (fvL[v] + fvR[v])) * sJ;
+            Fs[((size_t)fidS * 5 + v) * nn + o] = F;
+            Fq[((size_t)k * 5 + v) * nn + pp + n * qq] = -F;   // out of the big element
+          }
+        }
+    }
+    for (int v = 0; v < 5; ++v) {
+      const T* qp[4] = {&Fq[(size_t)(0 * 5 + v) * nn], &Fq[(size_t)(1 * 5 + v) * nn], &Fq[(size_t)(2 * 5 + v) * nn],
+                        &Fq[(size_t)(3 * 5 + v) * nn]};
+      mortar_project(c, qp, 1.0, &Fs[((size_t)fidB * 5 + v) * nn]);
+    }
+  }
   // --- FV sub-cell elements: faces with an FV side take the sub-face fluxes
   // (on a DG side converted to face nodes), flagged elements the FV residual
   bool use_fv = false;
@@ -1841,8 +2008,8 @@ void orc_persson(void* h, const double* U, int var, double* out) {
 
 // Create an oracle context.  prm = {gamma, R, Pr, mu, mms_amp}; returns NULL
 // and fills errbuf on a bad mesh.
-void* orc_create(int N, int n_elems, int ngeo, const double* xgeo, const int* face_nbr,
-                 const double* prm, int surf_flux, int source, char* errbuf, int errlen) {
+void* orc_create(int N, int n_elems, int ngeo, const double* xgeo, const int* face_nbr, int n_mortars,
+                 const int* mortars, const double* prm, int surf_flux, int source, char* errbuf, int errlen) {
   Ctx* c = new Ctx();
   c->N = N; c->n = N + 1; c->P = c->n * c->n * c->n; c->E = n_elems;
   c->prm.gamma = prm[0]; c->prm.R = prm[1]; c->prm.Pr = prm[2]; c->prm.mu = prm[3];
@@ -1859,6 +2026,11 @@ void* orc_create(int N, int n_elems, int ngeo, const double* xgeo, const int* fa
   c->b = make_basis(N);
   if (c->nodes != 0 && c->nodes != 1) c->err = "unknown node set";
   if (c->rk != 0 && c->rk != 1) c->err = "unknown Runge-Kutta scheme";
+  c->M = n_mortars > 0 ? n_mortars : 0;
+  if (c->M > 0) {
+    c->mortars.assign(mortars, mortars + (size_t)c->M * 14);
+    if (c->nodes != 0) c->err = "mortars are built for LGL nodes";
+  }
   if (!c->err.empty() || !build_geometry(*c, ngeo, xgeo) || !build_faces(*c, face_nbr)) {
     if (errbuf && errlen > 0) std::snprintf(errbuf, errlen, "%s", c->err.c_str());
     delete c;
@@ -1895,10 +2067,11 @@ void orc_set_vol_flux(void* h, int kind) { ((Ctx*)h)->prm.vol_flux = kind; }
 
 // FV sub-cell elements: mask[e] != 0 switches element e to the FV sub-cell
 // operator (FP64, either node set); NULL restores the pure DG operator.
-// Returns 0.
+// Returns 0, or -1 on a mesh with mortars.
 int orc_set_fv_mask(void* h, const int* mask) {
   Ctx* c = (Ctx*)h;
   if (!mask) { c->fv_mask.clear(); return 0; }
+  if (c->M > 0) return -1;   // the FV sub-cells are built for conforming meshes
   c->fv_mask.assign(mask, mask + c->E);
   return 0;
 }

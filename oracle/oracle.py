@@ -51,7 +51,8 @@ def _load(omp: bool = False):
     build()
     L = C.CDLL(lib_path(omp))
     L.orc_create.restype = C.c_void_p
-    L.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _ip, _dp, C.c_int, C.c_int, C.c_char_p, C.c_int]
+    L.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _ip, C.c_int, C.c_void_p, _dp, C.c_int, C.c_int,
+                             C.c_char_p, C.c_int]
     L.orc_destroy.argtypes = [C.c_void_p]
     L.orc_threads.argtypes = [C.c_int]
     L.orc_threads.restype = C.c_int
@@ -202,7 +203,11 @@ class Oracle:
         xgeo = np.ascontiguousarray(mesh.xgeo, dtype=np.float64)
         nbr = np.ascontiguousarray(mesh.face_nbr, dtype=np.int32)
         err = C.create_string_buffer(256)
-        h = L.orc_create(N, self.E, int(mesh.xgeo.shape[-1]) - 1, xgeo, nbr,
+        mortars = getattr(mesh, "mortars", None)
+        self._mortars = None if mortars is None or len(mortars) == 0 else np.ascontiguousarray(mortars, dtype=np.int32)
+        nm = 0 if self._mortars is None else self._mortars.shape[0]
+        h = L.orc_create(N, self.E, int(mesh.xgeo.shape[-1]) - 1, xgeo, nbr, nm,
+                         None if self._mortars is None else self._mortars.ctypes.data,
                          _prm(gamma, R, Pr, mu, mms_amp, visc_law, T_ref, S_suth, nodes, rk), surf_flux, source, err,
                          256)
         if not h:
@@ -280,7 +285,8 @@ class Oracle:
         m = np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0, dtype=np.int32)
         if m.shape[0] != self.E:
             raise ValueError("oracle: the FV mask needs one entry per element")
-        self._L.orc_set_fv_mask(self._h, m.ctypes.data)
+        if self._L.orc_set_fv_mask(self._h, m.ctypes.data) != 0:
+            raise ValueError("oracle: the FV sub-cell operator is built for conforming meshes")
         self.fv_mask = m
 
     def lifting(self, U):

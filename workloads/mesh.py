@@ -219,3 +219,130 @@ def _connectivity(Kd, rot: np.ndarray) -> np.ndarray:
         nbr[:, f, 1] = ft[:, 0]
         nbr[:, f, 2] = ft[:, 1]
     return nbr
+
+
+# ---------------------------------------------------------------------------
+# Non-conforming meshes: a periodic K^3 box whose selected cells are split into
+# 2 x 2 x 2 children.  A face between an unsplit cell and a split neighbour is
+# a mortar: the big face meets four small faces.
+#
+# Additional format (identical to the C-ABI ``dg_mesh`` mortar fields):
+# * ``mortars[m] = (eB, fB, eS0, fS0, flip0, ..., eS3, fS3, flip3)``: the big
+#   face ``fB`` of element ``eB`` is split into quadrants k = a + 2 b, (a, b)
+#   the halves along its face-local (p, q) directions; quadrant k is local
+#   face ``fS_k`` of element ``eS_k``, and ``flip_k`` maps a node (p, q) of the
+#   quadrant, numbered in the big face's directions, to the small face's own
+#   node (the ``flip`` code of the conforming faces).
+# * ``face_nbr[e, f] = (-1 - m, 0, 0)`` on the big side of mortar m and
+#   ``(-1 - m, k, 0)`` on its quadrant k.
+@dataclass
+class MortarMesh(Mesh):
+    mortars: np.ndarray = None   # [M, 14] int32
+    size: np.ndarray = None      # [E] element edge in fine lattice units (2: unsplit, 1: child)
+    origin: np.ndarray = None    # [E, 3] lower corner in fine lattice units
+
+
+def refined_box_mesh(K: int, refine, lo: float = -1.0, hi: float = 1.0, rotate_seed: int | None = None) -> MortarMesh:
+    """Periodic Cartesian ``K^3`` box (ngeo = 1) with the cells where
+    ``refine`` (a boolean array of K^3 entries, cell index x fastest) is true
+    split into eight children.  Elements: the cells in order, a split cell
+    replaced by its eight children (x fastest).  Element frames are seeded
+    proper rotations (identity if rotate_seed is None); all connectivity,
+    mortar quadrants and flips are found by matching corner points."""
+    refine = np.asarray(refine, dtype=bool).reshape(-1)
+    if refine.size != K ** 3:
+        raise ValueError("refine needs K^3 entries")
+    L = 2 * K                                     # the periodic box in fine lattice units
+    origin, size = [], []
+    for cell in range(K ** 3):
+        c = np.array([cell % K, (cell // K) % K, cell // (K * K)]) * 2
+        if refine[cell]:
+            for ch in range(8):
+                origin.append(c + np.array([ch & 1, (ch >> 1) & 1, (ch >> 2) & 1]))
+                size.append(1)
+        else:
+            origin.append(c)
+            size.append(2)
+    origin = np.array(origin, dtype=np.int64)
+    size = np.array(size, dtype=np.int64)
+    E = len(size)
+    if rotate_seed is None:
+        ident = next(i for i, m in enumerate(ROTATIONS) if (m == np.eye(3, dtype=np.int64)).all())
+        rot = np.full(E, ident, dtype=np.int64)
+    else:
+        rot = np.random.default_rng(rotate_seed).integers(0, 24, size=E)
+    # corner lattice points of each element's local reference cube [E][8][3] (local corner index i + 2 j + 4 k)
+    xgeo = np.empty((E, 3, 2, 2, 2), dtype=np.float64)
+    corners = np.empty((E, 2, 2, 2, 3), dtype=np.int64)
+    for e in range(E):
+        R = ROTATIONS[rot[e]]
+        off = _local_lattice(R, 1)                # [3, k, j, i] in {0, 1}
+        pts = origin[e][:, None, None, None] + size[e] * off
+        corners[e] = np.moveaxis(pts, 0, -1)
+        xgeo[e] = lo + (hi - lo) * pts / L
+    # face corner points, face-local (p, q) order, wrapped into the box
+    def face_pts(e, f):
+        d, s = divmod(f, 2)
+        tang = [a for a in range(3) if a != d]
+        out = np.empty((2, 2, 3), dtype=np.int64)
+        for p in range(2):
+            for q in range(2):
+                loc = [0, 0, 0]
+                loc[d] = s
+                loc[tang[0]] = p
+                loc[tang[1]] = q
+                out[p, q] = corners[e, loc[2], loc[1], loc[0]]
+        return out
+    # a face is identified by its centre (four times it, wrapped into the box):
+    # corner sets alone are ambiguous in a box two cells wide
+    key = lambda pts: tuple(int(v) % (4 * L) for v in pts.reshape(-1, 3).sum(0))
+    index = {}
+    for e in range(E):
+        for f in range(6):
+            index.setdefault(key(face_pts(e, f)), []).append((e, f))
+
+    def flip_between(P1, P2):
+        for flip in range(8):
+            if all(((P1[p, q] - P2[face_node_flip(flip, p, q, 1)]) % L == 0).all() for p in range(2) for q in range(2)):
+                return flip
+        raise RuntimeError("no face orientation found")
+
+    face_nbr = np.zeros((E, 6, 3), dtype=np.int32)
+    done = np.zeros((E, 6), dtype=bool)
+    mortars = []
+    for e in range(E):
+        for f in range(6):
+            if done[e, f]:
+                continue
+            P1 = face_pts(e, f)
+            others = [x for x in index[key(P1)] if x != (e, f)]
+            if others:                            # conforming (same size on both sides)
+                (e2, f2), = others
+                face_nbr[e, f] = (e2, f2, flip_between(P1, face_pts(e2, f2)))
+                face_nbr[e2, f2] = (e, f, flip_between(face_pts(e2, f2), P1))
+                done[e, f] = done[e2, f2] = True
+                continue
+            if size[e] != 2:
+                continue                          # a small face: registered from its big side
+            m = len(mortars)
+            rec = [e, f]
+            for k in range(4):
+                a, b = k & 1, k >> 1
+                Q = np.empty((2, 2, 3), dtype=np.int64)
+                for p in range(2):
+                    for q in range(2):
+                        Q[p, q] = P1[0, 0] + ((a + p) * (P1[1, 0] - P1[0, 0]) + (b + q) * (P1[0, 1] - P1[0, 0])) // 2
+                cand = index.get(key(Q), [])
+                if len(cand) != 1:
+                    raise RuntimeError("mortar quadrant not matched")
+                (es, fs), = cand
+                rec += [es, fs, flip_between(Q, face_pts(es, fs))]
+                face_nbr[es, fs] = (-1 - m, k, 0)
+                done[es, fs] = True
+            face_nbr[e, f] = (-1 - m, 0, 0)
+            done[e, f] = True
+            mortars.append(rec)
+    if not done.all():
+        raise RuntimeError("unmatched faces: a split cell next to an unsplit one needs 2:1 balance")
+    return MortarMesh(K=K, ngeo=1, lo=lo, hi=hi, xgeo=xgeo, face_nbr=face_nbr, rot=rot,
+                      mortars=np.array(mortars, dtype=np.int32).reshape(-1, 14), size=size, origin=origin)
