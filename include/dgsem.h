@@ -82,12 +82,24 @@ enum { DG_IND_RHO = 0, DG_IND_P = 1, DG_IND_RHOP = 2 };   /* quantity of the tro
  *       (a, b) = flip & 1 ? (q, p) : (p, q);  p2 = flip & 2 ? N - a : a;
  *       q2 = flip & 4 ? N - b : b.  Every face must have a neighbour
  *       (periodic meshes); the relation must be reciprocal.
+ *   Mortars (Sec. 3.2.2, Algorithm 1: non-conforming faces, 2:1): n_mortars
+ *       records mortars[m][0..13] = (eB, fB, eS0, fS0, flip0, ..., eS3,
+ *       fS3, flip3): big face fB of element eB is split into quadrants
+ *       k = a + 2b (a, b: the halves along its face-local p, q directions),
+ *       quadrant k being local face fS_k of element eS_k; flip_k maps a node
+ *       (p, q) of the quadrant, numbered along the big face's directions, to
+ *       the small face's own node.  face_nbr[eB][fB] = (-1 - m, 0, 0) and
+ *       face_nbr[eS_k][fS_k] = (-1 - m, k, 0).  The quadrants must be the
+ *       exact quarters of the big face (affine faces).  n_mortars = 0 and
+ *       mortars = NULL for a conforming mesh.
  */
 typedef struct {
   int32_t n_elems;
   int32_t ngeo;               /* >= 1 */
   const double* xgeo;
   const int32_t* face_nbr;
+  int32_t n_mortars;          /* >= 0 */
+  const int32_t* mortars;     /* [n_mortars][14] or NULL */
 } dg_mesh;
 
 /* Gas and discretisation (Sec. 3.1, Eq. 1: perfect gas p = (gamma-1) rho eps,
@@ -115,7 +127,8 @@ typedef struct {
  * metric terms are those of the LGL construction evaluated at the Gauss nodes
  * and face points (Sec. 3.1 leaves this open).  Synchronous.
  * Errors: DG_EINVAL (null/size, unknown option, constants out of range),
- * DG_EUNSUPPORTED (N outside 1..9, Gauss nodes with DG_FP32OP), DG_EMESH
+ * DG_EUNSUPPORTED (N outside 1..9, Gauss nodes with DG_FP32OP, mortars with
+ * Gauss nodes or DG_FP32OP: the mortar path is the FP64 LGL operator), DG_EMESH
  * (connectivity out of range or not reciprocal, Jacobian <= 0 at a node),
  * DG_ENOMEM, DG_ECUDA.  On failure *out is NULL. */
 dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out);
@@ -201,8 +214,8 @@ dg_status dg_indicator(dg_ctx* ctx, const double* dU, int32_t var, double log10_
  * on Gauss nodes its values interpolated to the face) and taking the sub-face
  * fluxes in nodal form, with the same face integral.  The first call allocates
  * about 18 + 12 (N+2)/(N+1) doubles per node plus 5 per face node and sets
- * up the sub-cell geometry.  FP64 operator (either node set): DG_EUNSUPPORTED
- * otherwise; the adjoint entry points return DG_EUNSUPPORTED while a mask is
+ * up the sub-cell geometry.  FP64 operator (either node set) on a conforming
+ * mesh: DG_EUNSUPPORTED otherwise; the adjoint entry points return DG_EUNSUPPORTED while a mask is
  * set.  dg_max_dt keeps the DG time-step restriction.  Does not synchronise. */
 dg_status dg_set_fv_mask(dg_ctx* ctx, const int32_t* dMask, dg_stream stream);
 
@@ -219,8 +232,9 @@ dg_status dg_geometry(dg_ctx* ctx, double* dJa, double* dJ, dg_stream stream);
  * log-mean switch follow the primal state; at a kink of the LLF speed maximum
  * the mean of the one-sided derivatives is taken).  The paper has no
  * adjoint; these entries exist for gradient-based use of the solver.  Built
- * for LGL nodes, the LLF and EC surface fluxes and constant viscosity, for
- * both time schemes; other contexts get DG_EUNSUPPORTED.
+ * for LGL nodes, the LLF and EC surface fluxes and constant viscosity on a
+ * conforming mesh without FV sub-cell elements, for both time schemes;
+ * other contexts get DG_EUNSUPPORTED.
  * dJdmu, where present, is a device double that is ACCUMULATED (+=) with
  * lambda . dR/dmu (R is linear in the constant viscosity mu); NULL skips it. */
 
@@ -285,7 +299,8 @@ typedef struct dg_ensemble dg_ensemble;
 /* The members stay owned by the caller and must outlive the ensemble.
  * DG_EINVAL if a member is NULL, appears twice (its work buffers would be
  * shared by two members) or is on another device or precision;
- * DG_EUNSUPPORTED for a member on Gauss nodes or with RK4-14 (the ensemble
+ * DG_EUNSUPPORTED for a member on Gauss nodes, with RK4-14 or on a mesh with
+ * mortars (the ensemble
  * kernels are the LGL split-form ones, its steps LSERK4-5). */
 dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune_cache_path, dg_ensemble** out);
 dg_status dg_ensemble_destroy(dg_ensemble* ens);

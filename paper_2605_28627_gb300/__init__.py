@@ -50,7 +50,7 @@ class DGError(RuntimeError):
 
 class dg_mesh(C.Structure):
     _fields_ = [("n_elems", C.c_int32), ("ngeo", C.c_int32), ("xgeo", C.POINTER(C.c_double)),
-                ("face_nbr", C.POINTER(C.c_int32))]
+                ("face_nbr", C.POINTER(C.c_int32)), ("n_mortars", C.c_int32), ("mortars", C.POINTER(C.c_int32))]
 
 
 class dg_params(C.Structure):
@@ -147,8 +147,11 @@ class Solver:
         xgeo = np.ascontiguousarray(mesh.xgeo, dtype=np.float64)
         nbr = np.ascontiguousarray(mesh.face_nbr, dtype=np.int32)
         self.E = int(xgeo.shape[0])
+        mortars = getattr(mesh, "mortars", None)
+        mortars = None if mortars is None or len(mortars) == 0 else np.ascontiguousarray(mortars, dtype=np.int32)
         m = dg_mesh(self.E, int(xgeo.shape[-1]) - 1, xgeo.ctypes.data_as(C.POINTER(C.c_double)),
-                    nbr.ctypes.data_as(C.POINTER(C.c_int32)))
+                    nbr.ctypes.data_as(C.POINTER(C.c_int32)), 0 if mortars is None else mortars.shape[0],
+                    None if mortars is None else mortars.ctypes.data_as(C.POINTER(C.c_int32)))
         p = dg_params(N, gamma, R, Pr, mu, surf_flux, precision, source, mms_amp, p_ref, visc_law, T_ref, S_suth,
                       nodes, rk_scheme)
         h = C.c_void_p()

@@ -34,6 +34,7 @@ static dg_status adj_checked(Ctx* c, cudaStream_t s) {
 static dg_status ensure_adjoint(Ctx* c) {
   if (c->fv_on)
     return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the DG operator (no FV sub-cell elements)");
+  if (c->M > 0) return afail(c, DG_EUNSUPPORTED, "the adjoint is built for conforming meshes");
   if (c->d_adj_qbar) return DG_OK;
   if (c->prm.precision != DG_FP64) return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the FP64 operator");
   if (c->prm.surf_flux == DG_FLUX_ROE)

@@ -74,9 +74,9 @@ static void lgl_basis(int N, std::vector<double>& x, std::vector<double>& w, std
 bool bounds_failed(cudaStream_t s, char* msg, size_t len) {
 #ifdef DG_BOUNDS_CHECK
   cudaStreamSynchronize(s);
-  const unsigned long long words[8] = {bounds_word_operator(), bounds_word_volume(), bounds_word_gauss(),
+  const unsigned long long words[9] = {bounds_word_operator(), bounds_word_volume(), bounds_word_gauss(),
                                        bounds_word_geometry(), bounds_word_adjoint(), bounds_word_ensemble(),
-                                       bounds_word_latency(), bounds_word_fv()};
+                                       bounds_word_latency(), bounds_word_fv(), bounds_word_mortar()};
   if (bulk_word_volume() || bulk_word_ensemble()) {
     std::snprintf(msg, len, "a bulk copy into shared memory did not complete within its wait limit");
     return true;
@@ -132,6 +132,9 @@ static void release(Ctx* c) {
   if (c->d_minmask) cudaFree(c->d_minmask);
   if (c->d_fv_mask) cudaFree(c->d_fv_mask);
   if (c->d_fv_lists) cudaFree(c->d_fv_lists);
+  if (c->d_mortars) cudaFree(c->d_mortars);
+  if (c->d_mortar_tab) cudaFree(c->d_mortar_tab);
+  if (c->d_mortar_virt) cudaFree(c->d_mortar_virt);
   if (c->h_out) cudaFreeHost(c->h_out);
   if (c->h_clock) cudaFreeHost(c->h_clock);
 }
@@ -198,14 +201,38 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
     return fail(nullptr, DG_EINVAL, "dg_init: unknown viscosity law");
   if (prm->visc_law == DG_VISC_SUTHERLAND && (!(prm->T_ref > 0.0) || !(prm->S_suth >= 0.0)))
     return fail(nullptr, DG_EINVAL, "dg_init: Sutherland constants out of range");
-  if (mesh->n_elems < 1 || mesh->ngeo < 1 || mesh->ngeo > 12 || !mesh->xgeo || !mesh->face_nbr)
+  if (mesh->n_elems < 1 || mesh->ngeo < 1 || mesh->ngeo > 12 || !mesh->xgeo || !mesh->face_nbr ||
+      mesh->n_mortars < 0 || (mesh->n_mortars > 0 && !mesh->mortars))
     return fail(nullptr, DG_EINVAL, "dg_init: bad mesh sizes or null arrays");
-  const int E = mesh->n_elems;
+  const int E = mesh->n_elems, M = mesh->n_mortars;
+  if (M > 0 && (prm->precision != DG_FP64 || prm->nodes != DG_NODES_LGL))
+    return fail(nullptr, DG_EUNSUPPORTED, "dg_init: mortars are built for the FP64 LGL operator");
+  // mortar table: every side names its mortar back
+  for (int m = 0; m < M; ++m) {
+    const int* r = mesh->mortars + (size_t)m * 14;
+    bool ok = r[0] >= 0 && r[0] < E && r[1] >= 0 && r[1] < 6 &&
+              mesh->face_nbr[(size_t)(r[0] * 6 + r[1]) * 3] == -1 - m &&
+              mesh->face_nbr[(size_t)(r[0] * 6 + r[1]) * 3 + 1] == 0;
+    for (int k = 0; k < 4 && ok; ++k) {
+      const int es = r[2 + 3 * k], fs = r[3 + 3 * k], fl = r[4 + 3 * k];
+      ok = es >= 0 && es < E && fs >= 0 && fs < 6 && fl >= 0 && fl < 8 &&
+           mesh->face_nbr[(size_t)(es * 6 + fs) * 3] == -1 - m && mesh->face_nbr[(size_t)(es * 6 + fs) * 3 + 1] == k;
+    }
+    if (!ok) return fail(nullptr, DG_EMESH, "dg_init: mortar table does not match the face connectivity");
+  }
   // connectivity checks: range and reciprocity
   for (int e = 0; e < E; ++e)
     for (int f = 0; f < 6; ++f) {
       const int* r = mesh->face_nbr + (size_t)(e * 6 + f) * 3;
-      if (r[0] < 0 || r[0] >= E || r[1] < 0 || r[1] > 5 || r[2] < 0 || r[2] > 7)
+      if (r[0] < 0) {   // a side of mortar -1 - r[0]
+        const int m = -1 - r[0];
+        if (m >= M || r[1] < 0 || r[1] > 3) return fail(nullptr, DG_EMESH, "dg_init: face connectivity out of range");
+        const int* mr = mesh->mortars + (size_t)m * 14;
+        if (!(mr[0] == e && mr[1] == f) && !(mr[2 + 3 * r[1]] == e && mr[3 + 3 * r[1]] == f))
+          return fail(nullptr, DG_EMESH, "dg_init: face connectivity not reciprocal");
+        continue;
+      }
+      if (r[0] >= E || r[1] < 0 || r[1] > 5 || r[2] < 0 || r[2] > 7)
         return fail(nullptr, DG_EMESH, "dg_init: face connectivity out of range");
       const int* b = mesh->face_nbr + (size_t)(r[0] * 6 + r[1]) * 3;
       if (b[0] != e || b[1] != f) return fail(nullptr, DG_EMESH, "dg_init: face connectivity not reciprocal");
@@ -242,6 +269,7 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
   for (int e = 0; e < E; ++e)
     for (int f = 0; f < 6; ++f) {
       const int* r = mesh->face_nbr + (size_t)(e * 6 + f) * 3;
+      if (r[0] < 0) continue;   // mortar sides: below
       elem_nbr[e * 6 + f] = r[0] * 8 + r[1];
       if (e * 6 + f < r[0] * 6 + r[1]) {
         elem_face[e * 6 + f] = (int)faces.size() * 16 + 8 + r[2];
@@ -251,8 +279,35 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
   for (int e = 0; e < E; ++e)
     for (int f = 0; f < 6; ++f) {
       const int* r = mesh->face_nbr + (size_t)(e * 6 + f) * 3;
-      if (e * 6 + f > r[0] * 6 + r[1]) elem_face[e * 6 + f] = (elem_face[r[0] * 6 + r[1]] >> 4) * 16 + r[2];
+      if (r[0] >= 0 && e * 6 + f > r[0] * 6 + r[1])
+        elem_face[e * 6 + f] = (elem_face[r[0] * 6 + r[1]] >> 4) * 16 + r[2];
     }
+  c->nfaces_conf = (int)faces.size();
+  // mortars: a face slot of its own for each small side and the big side, each
+  // the master of its slot; the lifting reads the side's neighbour state from
+  // the mortar array (elem_nbr = -1 - (5 m + side), side 4 = big)
+  c->M = M;
+  std::vector<int> mtab((size_t)M * 20, 0);
+  for (int m = 0; m < M; ++m) {
+    const int* r = mesh->mortars + (size_t)m * 14;
+    int* t = &mtab[(size_t)m * 20];
+    t[0] = r[0];
+    t[1] = r[1];
+    for (int k = 0; k < 4; ++k) {
+      const int es = r[2 + 3 * k], fs = r[3 + 3 * k];
+      t[3 + 4 * k] = es;
+      t[4 + 4 * k] = fs;
+      t[5 + 4 * k] = r[4 + 3 * k];
+      t[6 + 4 * k] = (int)faces.size();
+      elem_face[es * 6 + fs] = (int)faces.size() * 16 + 8;
+      elem_nbr[es * 6 + fs] = -1 - (5 * m + k);
+      faces.push_back(FaceInfo{es * 8 + fs, r[0] * 8 + r[1], r[4 + 3 * k], m});
+    }
+    t[2] = (int)faces.size();
+    elem_face[r[0] * 6 + r[1]] = (int)faces.size() * 16 + 8;
+    elem_nbr[r[0] * 6 + r[1]] = -1 - (5 * m + 4);
+    faces.push_back(FaceInfo{r[0] * 8 + r[1], r[0] * 8 + r[1], 0, m});
+  }
   c->nfaces = (int)faces.size();
   if (cudaSetDevice(device) != cudaSuccess) { fail(c, DG_ECUDA, "dg_init: cudaSetDevice"); return bail(DG_ECUDA); }
   const size_t P = c->P, NN = c->NN;
@@ -278,6 +333,9 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
       !alloc((void**)&c->d_modal, sizeof(double) * NN, "alloc modal table") ||
       !alloc((void**)&c->d_minmask, sizeof(int), "alloc mask") ||
       !alloc((void**)&c->d_clock, sizeof(double) * 2, "alloc clock") ||
+      (M > 0 && (!alloc((void**)&c->d_mortars, sizeof(int) * M * 20, "alloc mortar table") ||
+                 !alloc((void**)&c->d_mortar_tab, sizeof(double) * (2 * NN + c->n), "alloc mortar interpolation") ||
+                 !alloc((void**)&c->d_mortar_virt, sizeof(double) * M * 25 * NN, "alloc mortar states"))) ||
       (prm->source == DG_SOURCE_MMS && !alloc((void**)&c->d_mms, sizeof(double) * E * 2 * P, "alloc source phases")) ||
       (prm->nodes == DG_NODES_LG &&
        (!alloc((void**)&c->d_Uf, sizeof(double) * E * 6 * 5 * NN, "alloc face states") ||
@@ -333,6 +391,26 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_faces, faces.data(), sizeof(FaceInfo) * c->nfaces, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_elem_face, elem_face.data(), sizeof(int) * E * 6, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_elem_nbr, elem_nbr.data(), sizeof(int) * E * 6, cudaMemcpyHostToDevice, s);
+  // mortars: the table and the interpolation of the LGL basis to the LGL
+  // nodes of each half of [-1, 1], I[k][a][j] = l_j((x_a + 2k - 1)/2), with w
+  std::vector<double> mI(M > 0 ? 2 * NN + c->n : 0);
+  if (M > 0) {
+    const int n = c->n;
+    for (int k = 0; k < 2; ++k)
+      for (int a = 0; a < n; ++a)
+        for (int j = 0; j < n; ++j) {
+          const double xs = 0.5 * (c->x[a] + 2.0 * k - 1.0);
+          double l = 1.0;
+          for (int m = 0; m < n; ++m)
+            if (m != j) l *= (xs - c->x[m]) / (c->x[j] - c->x[m]);
+          mI[(size_t)(k * n + a) * n + j] = l;
+        }
+    for (int a = 0; a < n; ++a) mI[2 * NN + a] = c->w[a];
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(c->d_mortars, mtab.data(), sizeof(int) * mtab.size(), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(c->d_mortar_tab, mI.data(), sizeof(double) * mI.size(), cudaMemcpyHostToDevice, s);
+  }
   if (err == cudaSuccess) err = setup_kernels(c->N);
   if (err == cudaSuccess) err = build_geometry(*c, d_xgeo, mesh->ngeo, d_bad, s);
   if (err == cudaSuccess && prm->nodes == DG_NODES_LG) err = gauss_geometry(*c, d_bad, s);
@@ -514,6 +592,8 @@ dg_status dg_set_fv_mask(dg_ctx* c, const int32_t* dMask, dg_stream stream) {
   const bool on = dMask != nullptr;
   if (on && c->prm.precision != DG_FP64)
     return fail(c, DG_EUNSUPPORTED, "dg_set_fv_mask: the FV sub-cell operator is built for the FP64 operator");
+  if (on && c->M > 0)
+    return fail(c, DG_EUNSUPPORTED, "dg_set_fv_mask: the FV sub-cell operator is built for conforming meshes");
   if (on && !c->d_fv_mask) {
     const size_t E = c->E, P = c->P, NN = c->NN, n = c->n;
     std::vector<double> tab, nodes = c->x;   // the context's node set: LGL, or Gauss below

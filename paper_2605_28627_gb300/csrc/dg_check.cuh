@@ -29,7 +29,8 @@ enum BoundsSite {
   kSiteAdjFace = 8,      // adjoint: face elements, face ids, neighbours
   kSiteEnsMember = 9,    // ensemble: member of a tile
   kSiteFvNbr = 10,       // FV sub-cells: neighbour element across a face
-  kSiteFvFace = 11       // FV sub-cells: face elements, face id of an element face
+  kSiteFvFace = 11,      // FV sub-cells: face elements, face id of an element face
+  kSiteMortar = 12       // mortars: the elements and face slots of a mortar
 };
 
 #ifdef DG_BOUNDS_CHECK

@@ -59,7 +59,7 @@ k_face_ens(const MemberDev<R>* __restrict__ mem, int nmem, const int2* __restric
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int2 tl = tiles[t];
     const MemberDev<R>& m = mem[dg_idx(tl.x, nmem, kSiteEnsMember)];
-    face_body<N, R>(m.U, m.grad, m.faces, m.facegeo, m.fstar, m.F, m.gas, (long)tl.y * 128 + threadIdx.x);
+    face_body<N, R>(m.U, m.grad, m.faces, m.facegeo, m.fstar, m.F, m.E, m.gas, (long)tl.y * 128 + threadIdx.x);
   }
 }
 
@@ -498,8 +498,8 @@ static dg_status ensemble_create_impl(dg_ctx* const* members, int32_t n, const c
     // a context twice would have two members share its work buffers
     if (!c || c->device != e->device || c->prm.precision != e->precision || !seen.insert(c).second)
       return drop(DG_EINVAL);
-    if (c->prm.nodes != DG_NODES_LGL || c->prm.rk_scheme != DG_RK45)   // LGL split form, LSERK4-5
-      return drop(DG_EUNSUPPORTED);
+    if (c->prm.nodes != DG_NODES_LGL || c->prm.rk_scheme != DG_RK45 || c->M > 0)   // LGL split form, LSERK4-5,
+      return drop(DG_EUNSUPPORTED);                                                  // conforming meshes
     e->members.push_back(c);
   }
   if (cudaSetDevice(e->device) != cudaSuccess) return drop(DG_ECUDA);

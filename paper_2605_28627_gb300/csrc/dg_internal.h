@@ -105,6 +105,7 @@ struct StageArgs {
   // exist; both device memory, read at run time) and the other slots are idle
   const int* list = nullptr;
   const int* list_len = nullptr;
+  int nfaces = 0;              // face slots (bound of the face ids; 0: 3 E, a conforming periodic mesh)
 };
 
 struct Ctx {
@@ -124,7 +125,13 @@ struct Ctx {
   double* d_facegeo = nullptr;   // [F][4][NN]: unit normal (3), surface element
   float* d_metrics_f = nullptr;  // FP32 copies for the FP32-operator path
   float* d_facegeo_f = nullptr;
-  FaceInfo* d_faces = nullptr;   // [F]
+  FaceInfo* d_faces = nullptr;   // [F]: the conforming faces, then the mortars' small and big sides
+  int nfaces_conf = 0;           // conforming faces (the face kernel's range)
+  // mortars (non-conforming faces, 2:1)
+  int M = 0;
+  int* d_mortars = nullptr;      // [M][20]: eB, fB, slot of the big side, then per quadrant eS, fS, flip, slot
+  double* d_mortar_tab = nullptr;   // [2][n][n] interpolation to each half, [n] LGL weights
+  double* d_mortar_virt = nullptr;  // [M][5][5][NN]: the lifting's neighbour state of each mortar side
   int* d_elem_face = nullptr;    // [E][6]: face_id * 16 + master * 8 + flip (own -> neighbour)
   int* d_elem_nbr = nullptr;     // [E][6]: e2 * 8 + f2
   // work buffers
@@ -206,6 +213,11 @@ cudaError_t fv_setup(const Ctx& c, cudaStream_t s);
 cudaError_t launch_fv_lists(const Ctx& c, cudaStream_t s);
 cudaError_t launch_fv_stage(const Ctx& c, const StageArgs& a, cudaStream_t s);
 
+// Mortars (dg_mortar.cu): the lifting's neighbour states of the mortar sides
+// (before the lifting kernel) and the mortar fluxes (after the lifting).
+cudaError_t launch_mortar_lift(const Ctx& c, const double* U, cudaStream_t s);
+cudaError_t launch_mortar_flux(const Ctx& c, const double* U, cudaStream_t s);
+
 // Modal troubled-cell indicator (dg_indicator.cu).
 void modal_table(int N, const std::vector<double>& x, const std::vector<double>& w, bool lobatto,
                  std::vector<double>& T);
@@ -243,6 +255,7 @@ unsigned long long bounds_word_gauss();
 unsigned long long bounds_word_geometry();
 unsigned long long bounds_word_latency();
 unsigned long long bounds_word_fv();
+unsigned long long bounds_word_mortar();
 unsigned bulk_word_volume();     // bulk-copy waits that gave up (volume kernels)
 unsigned bulk_word_ensemble();
 unsigned long long bounds_word_operator();

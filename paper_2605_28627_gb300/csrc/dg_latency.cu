@@ -421,7 +421,7 @@ cudaError_t setup_latency(int N) {
 // 39.1 -> 25.2 us, 6^3 N = 3 40.0 -> 35.5 us; but 8^3 N = 3 59.3 -> 64.1 us
 // and 4^3 N = 5 61.4 -> 66.0 us).
 bool use_latency_kernels(const Ctx& c) {
-  return c.prm.precision == DG_FP64 && c.prm.nodes == DG_NODES_LGL && c.N <= 3 &&
+  return c.prm.precision == DG_FP64 && c.prm.nodes == DG_NODES_LGL && c.N <= 3 && c.M == 0 &&
          (long)c.E * c.P <= kLatencyNodes;
 }
 

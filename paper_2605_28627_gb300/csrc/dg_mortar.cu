@@ -1,0 +1,228 @@
+// Mortars (GALAEXI Sec. 3.2.2, Algorithm 1; Kopriva 1996): a big face split
+// into four quadrants k = a + 2 b that are faces of four small elements.
+//
+// Data of the big face go to the nodes of each quadrant (numbered (pp, qq)
+// along the big face's directions) by interpolation,
+//   v_k(pp, qq) = sum_ij I_a[pp][i] I_b[qq][j] v(i, j),  I_h[x][j] = l_j((x_x + 2h - 1)/2),
+// and quadrant data come back onto the big face by the projection with the
+// LGL quadrature, which keeps face integrals:
+//   v(i, j) = scale / (w_i w_j) sum_k sum_{pp,qq} w_pp w_qq I_a[pp][i] I_b[qq][j] v_k(pp, qq),
+// scale = 1/4 for point values, 1 for fluxes times sJ.
+//
+// k_mortar_lift (before the lifting kernel): the lifting's neighbour state of
+//   every mortar side, stored as a conservative state in the side's own
+//   face-node order: on a quadrant, the big face's interpolated lifting
+//   variables (u, v, w, T); on the big face, the one whose average with the
+//   big side's values is the projection of the quadrants' averages.
+// k_mortar_flux (after the lifting): the Riemann and viscous fluxes on the
+//   quadrants from the small side's state and gradients and the big side's
+//   interpolated ones, with the small face's geometry, and on the big face
+//   their projection, pointing out of the big element.
+// One block per mortar, a thread per quadrant node.
+#include "dg_stage.cuh"
+
+namespace dg {
+
+template <int N>
+struct MortarShape {
+  static constexpr int n = N + 1, P = n * n * n, NN = n * n, THREADS = 4 * NN;
+};
+
+// (u, v, w, T) of a conservative state
+__device__ __forceinline__ void lift_vars(const double* q, int st, const Gas& g, double ph[4]) {
+  const double ir = 1.0 / q[0];
+  const double u = q[st] * ir, v = q[2 * st] * ir, w = q[3 * st] * ir;
+  const double p = g.gm1 * (q[4 * st] - 0.5 * (q[st] * u + q[2 * st] * v + q[3 * st] * w));
+  ph[0] = u;
+  ph[1] = v;
+  ph[2] = w;
+  ph[3] = p * ir * g.inv_R;
+}
+
+// the conservative state with density 1 whose lifting variables are ph
+__device__ __forceinline__ void encode_vars(const double ph[4], const Gas& g, double* o, int st) {
+  o[0] = 1.0;
+  o[st] = ph[0];
+  o[2 * st] = ph[1];
+  o[3 * st] = ph[2];
+  o[4 * st] = g.R * ph[3] * g.inv_gm1 + 0.5 * (ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
+}
+
+template <int N>
+__global__ void __launch_bounds__(MortarShape<N>::THREADS)
+k_mortar_lift(const double* __restrict__ U, const int* __restrict__ mortars, const double* __restrict__ tab,
+              double* __restrict__ virt, int E, Gas g) {
+  using S = MortarShape<N>;
+  constexpr int n = S::n, P = S::P, NN = S::NN;
+  __shared__ double sI[2 * NN], sw[n];
+  __shared__ double sB[4][NN];      // lifting variables at the big face's nodes
+  __shared__ double sS[4][4][NN];   // face averages on the quadrants, big-face order
+  const int m = blockIdx.x, t = threadIdx.x;
+  const int* r = mortars + (size_t)m * 20;
+  const int eB = dg_idx(r[0], E, kSiteMortar), fB = r[1];
+  for (int x = t; x < 2 * NN; x += S::THREADS) sI[x] = tab[x];
+  for (int x = t; x < n; x += S::THREADS) sw[x] = tab[2 * NN + x];
+  if (t < NN) {
+    double ph[4];
+    lift_vars(U + (size_t)eB * 5 * P + face_node<n>(fB, t % n, t / n), P, g, ph);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) sB[a][t] = ph[a];
+  }
+  __syncthreads();
+  const int k = t / NN, pq = t % NN, pp = pq % n, qq = pq / n;
+  const double* Ia = sI + (k & 1) * NN;
+  const double* Ib = sI + (k >> 1) * NN;
+  {
+    double ib[4] = {0, 0, 0, 0};
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        const double c = Ia[pp * n + i] * Ib[qq * n + j];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) ib[a] = fma(c, sB[a][i + n * j], ib[a]);
+      }
+    const int es = dg_idx(r[3 + 4 * k], E, kSiteMortar), fs = r[4 + 4 * k], fl = r[5 + 4 * k];
+    int p2, q2;
+    apply_flip<n>(fl, pp, qq, p2, q2);
+    double ps[4];
+    lift_vars(U + (size_t)es * 5 * P + face_node<n>(fs, p2, q2), P, g, ps);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) sS[k][a][pq] = 0.5 * (ps[a] + ib[a]);
+    encode_vars(ib, g, virt + (size_t)(5 * m + k) * 5 * NN + p2 + n * q2, NN);
+  }
+  __syncthreads();
+  if (t < NN) {
+    const int i = t % n, j = t / n;
+    double sb[4] = {0, 0, 0, 0};
+    for (int kk = 0; kk < 4; ++kk) {
+      const double* Ja = sI + (kk & 1) * NN;
+      const double* Jb = sI + (kk >> 1) * NN;
+      for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a) {
+          const double c = sw[a] * sw[b] * Ja[a * n + i] * Jb[b * n + j];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) sb[x] = fma(c, sS[kk][x][a + n * b], sb[x]);
+        }
+    }
+    const double sc = 0.25 / (sw[i] * sw[j]);
+    double ph[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) ph[x] = 2.0 * sb[x] * sc - sB[x][t];   // average with the big side = projection
+    encode_vars(ph, g, virt + (size_t)(5 * m + 4) * 5 * NN + t, NN);
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(MortarShape<N>::THREADS)
+k_mortar_flux(const double* __restrict__ U, const double* __restrict__ grad, const double* __restrict__ facegeo,
+              const int* __restrict__ mortars, const double* __restrict__ tab, double* __restrict__ fstar, int E,
+              int F, Gas g) {
+  using S = MortarShape<N>;
+  constexpr int n = S::n, P = S::P, NN = S::NN;
+  __shared__ double sI[2 * NN], sw[n];
+  __shared__ double sB[17][NN];     // the big face's state and gradients
+  __shared__ double sF[4][5][NN];   // quadrant fluxes, big-face order
+  const int m = blockIdx.x, t = threadIdx.x;
+  const int* r = mortars + (size_t)m * 20;
+  const int eB = dg_idx(r[0], E, kSiteMortar), fB = r[1], slotB = dg_idx(r[2], F, kSiteMortar);
+  for (int x = t; x < 2 * NN; x += S::THREADS) sI[x] = tab[x];
+  for (int x = t; x < n; x += S::THREADS) sw[x] = tab[2 * NN + x];
+  if (t < NN) {
+    const int node = face_node<n>(fB, t % n, t / n);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sB[v][t] = U[((size_t)eB * 5 + v) * P + node];
+#pragma unroll
+    for (int x = 0; x < 12; ++x) sB[5 + x][t] = grad[((size_t)eB * 12 + x) * P + node];
+  }
+  __syncthreads();
+  const int k = t / NN, pq = t % NN, pp = pq % n, qq = pq / n;
+  {
+    const double* Ia = sI + (k & 1) * NN;
+    const double* Ib = sI + (k >> 1) * NN;
+    double dR[5] = {0, 0, 0, 0, 0}, gR[12];
+#pragma unroll
+    for (int x = 0; x < 12; ++x) gR[x] = 0.0;
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        const double c = Ia[pp * n + i] * Ib[qq * n + j];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) dR[v] = fma(c, sB[v][i + n * j], dR[v]);
+#pragma unroll
+        for (int x = 0; x < 12; ++x) gR[x] = fma(c, sB[5 + x][i + n * j], gR[x]);
+      }
+    const int es = dg_idx(r[3 + 4 * k], E, kSiteMortar), fs = r[4 + 4 * k], fl = r[5 + 4 * k];
+    const int slot = dg_idx(r[6 + 4 * k], F, kSiteMortar);
+    int p2, q2;
+    apply_flip<n>(fl, pp, qq, p2, q2);
+    const int node = face_node<n>(fs, p2, q2), o = p2 + n * q2;
+    double dL[5], gL[12];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) dL[v] = U[((size_t)es * 5 + v) * P + node];
+#pragma unroll
+    for (int x = 0; x < 12; ++x) gL[x] = grad[((size_t)es * 12 + x) * P + node];
+    const double* fg = facegeo + (size_t)slot * 4 * NN + o;
+    face_flux_core<double>(dL, dR, gL, gR, fg[0], fg[NN], fg[2 * NN], fg[3 * NN], g, &sF[k][0][pq], NN);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) fstar[((size_t)slot * 5 + v) * NN + o] = sF[k][v][pq];
+  }
+  __syncthreads();
+  if (t < NN) {
+    const int i = t % n, j = t / n;
+    double sb[5] = {0, 0, 0, 0, 0};
+    for (int kk = 0; kk < 4; ++kk) {
+      const double* Ja = sI + (kk & 1) * NN;
+      const double* Jb = sI + (kk >> 1) * NN;
+      for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a) {
+          const double c = sw[a] * sw[b] * Ja[a * n + i] * Jb[b * n + j];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) sb[v] = fma(c, sF[kk][v][a + n * b], sb[v]);
+        }
+    }
+    const double sc = -1.0 / (sw[i] * sw[j]);   // out of the big element
+#pragma unroll
+    for (int v = 0; v < 5; ++v) fstar[((size_t)slotB * 5 + v) * NN + t] = sb[v] * sc;
+  }
+}
+
+template <int N>
+static cudaError_t mortar_lift_N(const Ctx& c, const double* U, cudaStream_t s) {
+  k_mortar_lift<N><<<c.M, MortarShape<N>::THREADS, 0, s>>>(U, c.d_mortars, c.d_mortar_tab, c.d_mortar_virt, c.E,
+                                                           c.gas);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t mortar_flux_N(const Ctx& c, const double* U, cudaStream_t s) {
+  k_mortar_flux<N><<<c.M, MortarShape<N>::THREADS, 0, s>>>(U, (const double*)c.d_grad, c.d_facegeo, c.d_mortars,
+                                                           c.d_mortar_tab, (double*)c.d_fstar, c.E, c.nfaces, c.gas);
+  return cudaGetLastError();
+}
+
+#define DG_MORTAR_DISPATCH(FN, ...)          \
+  switch (c.N) {                             \
+    case 1: return FN<1>(__VA_ARGS__);       \
+    case 2: return FN<2>(__VA_ARGS__);       \
+    case 3: return FN<3>(__VA_ARGS__);       \
+    case 4: return FN<4>(__VA_ARGS__);       \
+    case 5: return FN<5>(__VA_ARGS__);       \
+    case 6: return FN<6>(__VA_ARGS__);       \
+    case 7: return FN<7>(__VA_ARGS__);       \
+    case 8: return FN<8>(__VA_ARGS__);       \
+    case 9: return FN<9>(__VA_ARGS__);       \
+    default: return cudaErrorInvalidValue;   \
+  }
+
+cudaError_t launch_mortar_lift(const Ctx& c, const double* U, cudaStream_t s) {
+  if (c.M == 0) return cudaSuccess;
+  DG_MORTAR_DISPATCH(mortar_lift_N, c, U, s)
+}
+
+cudaError_t launch_mortar_flux(const Ctx& c, const double* U, cudaStream_t s) {
+  if (c.M == 0) return cudaSuccess;
+  DG_MORTAR_DISPATCH(mortar_flux_N, c, U, s)
+}
+
+// Host reader of this file's bounds-check error word (0 in normal builds).
+DG_BOUNDS_READER(bounds_word_mortar)
+
+}  // namespace dg

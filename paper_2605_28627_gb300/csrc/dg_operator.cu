@@ -6,13 +6,15 @@ namespace dg {
 
 // The FP32 lifting is latency-bound: its register allocation must leave room
 // for 48 warps per SM (three 512-thread blocks at N = 7, twelve at N = 3).
-template <int N, typename R>
+// MORTAR (FP64): mortar sides read their neighbour state from mvirt.
+template <int N, typename R, bool MORTAR = false>
 __global__ void __launch_bounds__(Shape<N>::THREADS,
                                   sizeof(R) == 4 && Shape<N>::THREADS < 1536 ? 1536 / Shape<N>::THREADS : 1)
 k_lift(const double* __restrict__ U, const R* __restrict__ metrics, const int* __restrict__ elem_nbr,
        const int* __restrict__ elem_face, const double* __restrict__ Dg, R* __restrict__ grad, int E, Gas g,
-       double inv_w0) {
-  lift_body<N, R, Shape<N>::EPB>(U, metrics, elem_nbr, elem_face, Dg, grad, E, g, inv_w0, blockIdx.x);
+       double inv_w0, const double* __restrict__ mvirt, int n_mortar) {
+  lift_body<N, R, Shape<N>::EPB, MORTAR>(U, metrics, elem_nbr, elem_face, Dg, grad, E, g, inv_w0, blockIdx.x,
+                                         mvirt, n_mortar);
 }
 
 // FVSKIP: faces with an FV sub-cell element on either side are left to the FV
@@ -20,17 +22,16 @@ k_lift(const double* __restrict__ U, const R* __restrict__ metrics, const int* _
 template <int N, typename R, bool FVSKIP>
 __global__ void __launch_bounds__(128)
 k_face(const double* __restrict__ U, const R* __restrict__ grad, const FaceInfo* __restrict__ faces,
-       const R* __restrict__ facegeo, R* __restrict__ fstar, int F, Gas g, const int* __restrict__ fv_mask) {
+       const R* __restrict__ facegeo, R* __restrict__ fstar, int F, int E, Gas g, const int* __restrict__ fv_mask) {
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if constexpr (FVSKIP) {
     constexpr int NN = (N + 1) * (N + 1);
     if (gid >= (long)F * NN) return;
     const FaceInfo fi = faces[gid / NN];
-    if (fv_mask[dg_idx(fi.master >> 3, F / 3, kSiteFaceElems)] ||
-        fv_mask[dg_idx(fi.slave >> 3, F / 3, kSiteFaceElems)])
+    if (fv_mask[dg_idx(fi.master >> 3, E, kSiteFaceElems)] || fv_mask[dg_idx(fi.slave >> 3, E, kSiteFaceElems)])
       return;
   }
-  face_body<N, R>(U, grad, faces, facegeo, fstar, F, g, gid);
+  face_body<N, R>(U, grad, faces, facegeo, fstar, F, E, g, gid);
 }
 
 // ---------------------------------------------------------------------------
@@ -39,19 +40,32 @@ static cudaError_t lift_NR(const Ctx& c, const double* U, cudaStream_t s) {
   using S = Shape<N>;
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
   const R* metrics = (const R*)(sizeof(R) == 8 ? (const void*)c.d_metrics : (const void*)c.d_metrics_f);
+  if constexpr (sizeof(R) == 8) {
+    if (c.M > 0) {   // the mortar sides' neighbour states first
+      cudaError_t e = launch_mortar_lift(c, U, s);
+      if (e != cudaSuccess) return e;
+      k_lift<N, R, true><<<blocks, S::THREADS, lift_smem_bytes<N, R, S::EPB>(), s>>>(
+          U, metrics, c.d_elem_nbr, c.d_elem_face, c.d_D, (R*)c.d_grad, c.E, c.gas, 1.0 / c.w[0], c.d_mortar_virt, c.M);
+      return cudaGetLastError();
+    }
+  }
   k_lift<N, R><<<blocks, S::THREADS, lift_smem_bytes<N, R, S::EPB>(), s>>>(
-      U, metrics, c.d_elem_nbr, c.d_elem_face, c.d_D, (R*)c.d_grad, c.E, c.gas, 1.0 / c.w[0]);
+      U, metrics, c.d_elem_nbr, c.d_elem_face, c.d_D, (R*)c.d_grad, c.E, c.gas, 1.0 / c.w[0], nullptr, 0);
   return cudaGetLastError();
 }
 
 template <int N, typename R, bool FVSKIP>
 static cudaError_t face_NR(const Ctx& c, const double* U, cudaStream_t s) {
-  const long tot = (long)c.nfaces * (N + 1) * (N + 1);
+  // the conforming faces (the mortars' slots follow them)
+  const long tot = (long)c.nfaces_conf * (N + 1) * (N + 1);
   const int blocks = (int)((tot + 127) / 128);
   const R* fgeo = (const R*)(sizeof(R) == 8 ? (const void*)c.d_facegeo : (const void*)c.d_facegeo_f);
-  k_face<N, R, FVSKIP><<<blocks, 128, 0, s>>>(U, (const R*)c.d_grad, c.d_faces, fgeo, (R*)c.d_fstar, c.nfaces,
-                                               c.gas, c.d_fv_mask);
-  return cudaGetLastError();
+  if (blocks > 0)
+    k_face<N, R, FVSKIP><<<blocks, 128, 0, s>>>(U, (const R*)c.d_grad, c.d_faces, fgeo, (R*)c.d_fstar, c.nfaces_conf,
+                                                 c.E, c.gas, c.d_fv_mask);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && c.M > 0) e = launch_mortar_flux(c, U, s);
+  return e;
 }
 
 template <int N>
@@ -100,6 +114,9 @@ template <int N>
 static cudaError_t setup_lift_N() {
   cudaError_t e = cudaFuncSetAttribute(k_lift<N, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)lift_smem_bytes<N, double, Shape<N>::EPB>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_lift<N, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lift_smem_bytes<N, double, Shape<N>::EPB>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_lift<N, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lift_smem_bytes<N, float, Shape<N>::EPB>());

@@ -145,11 +145,17 @@ constexpr size_t lift_smem_bytes() {
   return sizeof(R) * (size_t)EPB * (4 * (N + 1) * (N + 1) * (N + 1) + 24 * (N + 1) * (N + 1));
 }
 
-template <int N, typename R, int EPB>
+// MORTAR: a face whose neighbour entry is negative is a mortar side, whose
+// neighbour state (the big face's interpolated state on a quadrant, or the
+// state that gives the projected face average on a big face) is read from
+// mvirt[-1 - entry][5][NN] (entry -1 - (5 m + side), m < n_mortar) in the
+// side's own face-node order.
+template <int N, typename R, int EPB, bool MORTAR = false>
 __device__ __forceinline__ void lift_body(const double* __restrict__ U, const R* __restrict__ metrics,
                                           const int* __restrict__ elem_nbr, const int* __restrict__ elem_face,
                                           const double* __restrict__ Dg, R* __restrict__ grad, int E, const Gas& g,
-                                          double inv_w0d, int blk) {
+                                          double inv_w0d, int blk, const double* __restrict__ mvirt = nullptr,
+                                          int n_mortar = 0) {
   using S = Shape<N, EPB>;
   constexpr int n = S::n, P = S::P, NN = S::NN, NF = 6 * NN;
   constexpr int NI = (EPB * NF + S::THREADS - 1) / S::THREADS;   // face points per thread
@@ -167,6 +173,14 @@ __device__ __forceinline__ void lift_body(const double* __restrict__ U, const R*
     if (t < EPB * NF && e2 < E) {
       const int f = r2 / NN, pq = r2 - f * NN;
       const int code = elem_face[e2 * 6 + f], nb = elem_nbr[e2 * 6 + f];
+      if constexpr (MORTAR) {
+        if (nb < 0) {
+          const double* q = mvirt + (size_t)dg_idx(-1 - nb, 5L * n_mortar, kSiteMortar) * 5 * NN + pq;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) qv[v] = q[v * NN];
+          return;
+        }
+      }
       int p2, q2;
       apply_flip<n>(code & 7, pq % n, pq / n, p2, q2);
       const int enb = dg_idx(nb >> 3, E, kSiteLiftNbr);
@@ -337,15 +351,15 @@ __device__ __forceinline__ void face_flux_core(const double dL[5], const double 
 template <int N, typename R>
 __device__ __forceinline__ void face_body(const double* __restrict__ U, const R* __restrict__ grad,
                                           const FaceInfo* __restrict__ faces, const R* __restrict__ facegeo,
-                                          R* __restrict__ fstar, int F, const Gas& g, long gid) {
+                                          R* __restrict__ fstar, int F, int E, const Gas& g, long gid) {
   constexpr int n = N + 1, P = n * n * n, NN = n * n;
   if (gid >= (long)F * NN) return;
   const int f = (int)(gid / NN), pq = (int)(gid % NN);
   const int p = pq % n, q = pq / n;
   const FaceInfo fi = faces[f];
   // every local face of a periodic mesh has a neighbour: F = 3 E
-  const int eM = dg_idx(fi.master >> 3, F / 3, kSiteFaceElems), fM = fi.master & 7;
-  const int eS = dg_idx(fi.slave >> 3, F / 3, kSiteFaceElems), fS = fi.slave & 7;
+  const int eM = dg_idx(fi.master >> 3, E, kSiteFaceElems), fM = fi.master & 7;
+  const int eS = dg_idx(fi.slave >> 3, E, kSiteFaceElems), fS = fi.slave & 7;
   int p2, q2;
   apply_flip<n>(fi.flip, p, q, p2, q2);
   const int idM = face_node<n>(fM, p, q), idS = face_node<n>(fS, p2, q2);
@@ -546,7 +560,8 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
       else l2_prefetch(metrics + (size_t)e * 10 * P + 9 * P, P * sizeof(R));
     } else if (id == 2 && g.source == DG_SOURCE_MMS) l2_prefetch(mms + (size_t)e * 2 * P, 2 * P * sizeof(double));
     else if (id >= 3)
-      l2_prefetch(fstar + (size_t)dg_idx(elem_face[e * 6 + id - 3] >> 4, 3L * E, kSiteVolFace) * 5 * NN,
+      l2_prefetch(fstar + (size_t)dg_idx(elem_face[e * 6 + id - 3] >> 4, a.nfaces > 0 ? a.nfaces : 3L * E,
+                                         kSiteVolFace) * 5 * NN,
                   5 * NN * sizeof(R));
   }
   const R inv_w0 = to_op<R>(inv_w0d);
@@ -862,7 +877,7 @@ __device__ __forceinline__ void volume_body(const StageArgs& a, const R* __restr
     if (id_d != 0 && id_d != N) continue;
     const int sgn = id_d == N ? 1 : 0;
     const int code = elem_face[e * 6 + 2 * d + sgn];
-    const int fid = dg_idx(code >> 4, 3L * E, kSiteVolFace);   // F = 3 E
+    const int fid = dg_idx(code >> 4, a.nfaces > 0 ? a.nfaces : 3L * E, kSiteVolFace);   // F = 3 E if conforming
     const int pp = d == 0 ? j : i;
     const int qq = d == 2 ? j : k;
     const R* fsr;

@@ -27,10 +27,12 @@ cudaError_t volume2_setup() {
 }
 
 template <int N, typename R, bool LIST>
-cudaError_t volume2_launch(const Ctx& c, const StageArgs& a, cudaStream_t s) {
+cudaError_t volume2_launch(const Ctx& c, const StageArgs& a0, cudaStream_t s) {
   using S = VShape<N>;
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
   const R* metrics = (const R*)(sizeof(R) == 8 ? (const void*)c.d_metrics : (const void*)c.d_metrics_f);
+  StageArgs a = a0;
+  a.nfaces = c.nfaces;
   k_volume2<N, R, LIST><<<blocks, S::THREADS, volume2_smem<N, R>(), s>>>(
       a, metrics, c.d_metrics, (const R*)c.d_grad, (const R*)c.d_fstar, c.d_elem_face, c.d_mms, c.d_D, c.E, c.gas,
       1.0 / c.w[0]);

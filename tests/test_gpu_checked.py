@@ -1,7 +1,8 @@
 """The checked build (-DDG_BOUNDS_CHECK: every index read from a connectivity
 table is bounds-checked inside the kernels; a violation would be recorded and
 reported as DG_ECUDA) on one- and two-element meshes, where every face of an
-element meets the element itself or its single neighbour: the operator, RK
+element meets the element itself or its single neighbour, and on a small 2:1
+mesh with mortar faces: the operator, RK
 steps, diagnostics, the Gauss-node operator, the adjoint and the ensemble (its
 persistent tile-table kernels) run without a report -- neither an index out of
 range nor a bulk-copy wait that gave up -- and match the oracle and the normal
@@ -49,6 +50,20 @@ for name, dims, N in (("one", (1, 1, 1), 3), ("two", (2, 1, 1), 4), ("two_rot", 
     Rg = sg.time_derivative(Ug)
     out[name] = dict(err_r=err_r, err_rk=err_rk, finite=bool(torch.isfinite(vj).all() and torch.isfinite(lam0).all()
                      and torch.isfinite(Rg).all() and np.isfinite(I).all()))
+# a 2:1 mesh: every mortar table entry and the mortar neighbour states checked
+from workloads.mesh import refined_box_mesh
+ref = np.zeros(8, dtype=bool); ref[0] = True
+mesh = refined_box_mesh(2, ref, rotate_seed=5)
+U = random_state(mesh.n_elems, 3, seed=12)
+o = oracle.Oracle(mesh, 3, mu=0.02)
+s = dg.Solver(mesh, 3, mu=0.02)
+Ud = torch.from_numpy(U).cuda()
+Ro = o.time_derivative(U)
+err_r = float(np.abs(s.time_derivative(Ud).cpu().numpy() - Ro).max() / np.abs(Ro).max())
+G = torch.empty_like(Ud)
+s.rk_step(Ud, G, 0.0, 1e-3, 3)
+Uo = o.rk_steps(U, 0.0, 1e-3, 3)
+out["mortar"] = dict(err_r=err_r, err_rk=float(np.abs(Ud.cpu().numpy() - Uo).max() / np.abs(Uo).max()), finite=True)
 prm = tgv_params(Ma=0.2, Re=800.0)
 runs = []
 for dims, N in (((1, 1, 1), 3), ((2, 1, 1), 3), ((1, 1, 2), 2)):
@@ -84,7 +99,7 @@ def test_checked_build_on_one_and_two_element_meshes():
                        timeout=1500)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
     res = json.loads(r.stdout.strip().splitlines()[-1])
-    for name in ("one", "two", "two_rot"):
+    for name in ("one", "two", "two_rot", "mortar"):
         assert res[name]["err_r"] < 1e-12, res
         assert res[name]["err_rk"] < 1e-10, res
         assert res[name]["finite"], res

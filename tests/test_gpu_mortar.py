@@ -1,0 +1,103 @@
+"""Mortar faces on the GPU (non-conforming 2:1 meshes, Sec. 3.2.2, Algorithm 1)
+against the oracle, through the C ABI.  Bars as for conforming meshes: R(U)
+within 1e-12 relative per variable, RK steps within 1e-10."""
+import numpy as np
+import pytest
+
+from workloads import mms_params, random_state
+from workloads.mesh import refined_box_mesh
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import paper_2605_28627_gb300 as m
+    m.load()
+    return m
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _refine(K, cells):
+    r = np.zeros(K ** 3, dtype=bool)
+    r[list(cells)] = True
+    return r
+
+
+def _rel_err_per_var(got, ref):
+    got = got.reshape(got.shape[0], 5, -1)
+    ref = ref.reshape(ref.shape[0], 5, -1)
+    return np.array([np.abs(got[:, v] - ref[:, v]).max() / max(np.abs(ref[:, v]).max(), 1e-300) for v in range(5)])
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("flux", [0, 1, 2])
+def test_mortar_time_derivative_parity(orc, dg, N, flux):
+    K = 3
+    mesh = refined_box_mesh(K, _refine(K, [0, 13]), rotate_seed=40 + N)
+    kw = dict(mu=0.02, surf_flux=flux)
+    o, s = orc.Oracle(mesh, N, **kw), dg.Solver(mesh, N, **kw)
+    U = random_state(mesh.n_elems, N, seed=60 + N)
+    err = _rel_err_per_var(s.time_derivative(_cuda(U)).cpu().numpy(), o.time_derivative(U))
+    assert (err < 1e-12).all(), err
+
+
+@pytest.mark.parametrize("N", [2, 5])
+def test_mortar_mms_rk_parity(orc, dg, N):
+    prm = mms_params()
+    K = 3
+    mesh = refined_box_mesh(K, _refine(K, [4, 13, 22]), rotate_seed=70 + N)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1)
+    o, s = orc.Oracle(mesh, N, **kw), dg.Solver(mesh, N, **kw)
+    U0 = o.initial_state("mms", 0.0)
+    ref = o.rk_steps(U0, 0.0, 1e-3, 10)
+    Ud = _cuda(U0)
+    G = torch.empty_like(Ud)
+    s.rk_step(Ud, G, 0.0, 1e-3, 10)
+    got = Ud.cpu().numpy()
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-10
+
+
+def test_mortar_free_stream_and_conservation(orc, dg):
+    N, K = 4, 4
+    mesh = refined_box_mesh(K, _refine(K, [0, 21, 42, 63]), rotate_seed=8)
+    s = dg.Solver(mesh, N, mu=0.01)
+    U = np.zeros(s.shape)
+    r, u, p = 1.2, np.array([0.3, -0.2, 0.45]), 0.9
+    U[:, 0] = r
+    U[:, 1:4] = (r * u)[None, :, None, None, None]
+    U[:, 4] = p / 0.4 + 0.5 * r * u @ u
+    R = s.time_derivative(_cuda(U))
+    _, J = s.geometry()
+    _, w, _ = orc.basis(N)
+    assert float(R.abs().max()) < 2e-15 * 2.0 / (w[0] * float(J.min())) * N ** 3
+    U = _cuda(random_state(mesh.n_elems, N, seed=9))
+    R = s.time_derivative(U)
+    wq = torch.from_numpy(np.einsum("k,j,i->kji", w, w, w).reshape(-1)).cuda()
+    tot = torch.einsum("evp,ep->v", R.reshape(s.E, 5, -1), J * wq)
+    scale = torch.einsum("evp,ep->v", R.reshape(s.E, 5, -1).abs(), J * wq)
+    assert bool((tot.abs() <= 1e-13 * scale).all()), (tot, scale)
+
+
+def test_mortar_rejections(dg):
+    mesh = refined_box_mesh(2, _refine(2, [0]))
+    for kw in (dict(precision=1), dict(nodes=1)):
+        with pytest.raises(dg.DGError):
+            dg.Solver(mesh, 2, **kw)
+    s = dg.Solver(mesh, 2, mu=0.01)
+    U = _cuda(random_state(mesh.n_elems, 2, seed=1))
+    with pytest.raises(dg.DGError):
+        s.set_fv_mask(np.ones(mesh.n_elems, dtype=np.int32))
+    with pytest.raises(dg.DGError):
+        s.time_derivative_vjp(U, torch.ones_like(U))
+    with pytest.raises(dg.DGError):
+        dg.Ensemble([s])
+    bad = refined_box_mesh(2, _refine(2, [0]))
+    bad.mortars = bad.mortars.copy()
+    bad.mortars[0, 2] = bad.mortars[0, 5]
+    with pytest.raises(dg.DGError):
+        dg.Solver(bad, 2)
