@@ -527,6 +527,55 @@ def fv50_rate(dg, N, dev, prm, dg_rate, steps=5):
             "stage_ms": {"lift": ms3[0], "face": ms3[1], "volume_dg_and_fv": ms3[2]}, "state_finite": finite}
 
 
+def mortar_rate(dg, N, dev, prm, dg_rate, K=12, steps=5):
+    """A non-conforming 2:1 mesh: a periodic K^3 box (rotated element frames)
+    whose cells with three even indices are split into eight, so that every
+    split cell meets its six neighbours through mortars (Algorithm 1); MMS
+    LSERK4-5 steps as one graph launch after 3 warm-up steps, CUDA events."""
+    import numpy as np
+    import torch
+    from workloads.mesh import refined_box_mesh
+    i = np.arange(K ** 3)
+    mesh = refined_box_mesh(K, (i % 2 == 0) & ((i // K) % 2 == 0) & ((i // (K * K)) % 2 == 0), rotate_seed=3)
+    s = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=dg.SOURCE_MMS,
+                  device=dev)
+    st = torch.cuda.Stream(device="cuda:%d" % dev)
+    with torch.cuda.stream(st):
+        U = s.initial_state("mms", 0.0, stream=st)
+        G = torch.empty_like(U)
+    dt = min(DT, s.max_dt(U, cfl=0.9, dfl=0.9, stream=st))
+    s.rk_step(U, G, 0.0, dt, 3, stream=st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    s.rk_step(U, G, 3 * dt, dt, steps, stream=st)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    dofs = mesh.n_elems * (N + 1) ** 3
+    rate = dofs * 5 * steps / (ms * 1e-3)
+    ms3 = s.profile_stages(U, G, dt, reps=5, stream=st)
+    finite = bool(torch.isfinite(U).all().item())
+    s.close()
+    return {"workload": "MMS density wave, periodic %d^3 box with 1/8 of its cells split 2:1 (%d elements, %d "
+                        "mortars), N=%d, rotated element frames" % (K, mesh.n_elems, len(mesh.mortars), N),
+            "value": rate, "unit": UNIT, "pid_ns": 1e9 / rate, "ms_per_step": ms / steps,
+            "vs_headline": rate / dg_rate,
+            "stage_ms": {"lift_with_mortar_states": ms3[0], "face_with_mortar_fluxes": ms3[1], "volume": ms3[2]},
+            "state_finite": finite}
+
+
+def run_mortar(args, local):
+    import torch
+    import paper_2605_28627_gb300 as dg
+    from workloads import mms_params
+    torch.cuda.set_device(local)
+    prm = mms_params()
+    ms, _ = sweep_rate(dg, args.order, local, prm)
+    dg_rate = K_ELEMS ** 3 * (args.order + 1) ** 3 * 5 / (ms * 1e-3)
+    print(json.dumps({"mortar": mortar_rate(dg, args.order, local, prm, dg_rate, steps=args.steps)}))
+    return 0
+
+
 def small_tgv_rate(dg, local, reps=20):
     """The small Taylor-Green case (4^3 Cartesian elements of [0, 2pi]^3, N=3,
     4096 nodes, Ma 0.1, Re 1600, LLF + BR1 + split form, dt at CFL 0.9): ten
@@ -800,6 +849,7 @@ def main():
     ap.add_argument("--no-extra-legs", dest="extra_legs", action="store_false",
                     help="skip the 48^3 Taylor-Green and ensemble legs of the default line")
     ap.add_argument("--tgv-leg-steps", type=int, default=6, help="steps of the 48^3 leg of the default line")
+    ap.add_argument("--mortar", action="store_true", help="run the 2:1 non-conforming mesh leg alone")
     ap.add_argument("--adj-steps", type=int, default=200)
     ap.add_argument("--adj-dirs", type=int, default=32)
     args = ap.parse_args()
@@ -813,6 +863,8 @@ def main():
         return run_pid(args, local) if rank == 0 else 0
     if args.adjoint:
         return run_adjoint(args, local) if rank == 0 else 0
+    if args.mortar:
+        return run_mortar(args, local) if rank == 0 else 0
     if args.impl == "reference":
         return run_reference(args, world, rank)
 
@@ -903,6 +955,7 @@ def main():
     tgv_small = small_tgv_rate(dg, local) if rank == 0 else None
     indicator = indicator_rate(solver, U, stream, fp64_peak) if rank == 0 else None
     fv50 = fv50_rate(dg, N, local, prm, value / world) if rank == 0 else None
+    mortar = mortar_rate(dg, N, local, prm, value / world) if rank == 0 else None
 
     sweep = {}
     if args.sweep and rank == 0:
@@ -965,7 +1018,8 @@ def main():
                        "l2": "inputs larger than L2: %.0f MB of state, metrics, gradients and face data touched "
                              "per stage" % working_set_mb(solver)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-            "clocks": clk, "sweep": sweep, "fp32_operator": fp32, "tgv_small": tgv_small, "indicator": indicator, "fv50": fv50,
+            "clocks": clk, "sweep": sweep, "fp32_operator": fp32, "tgv_small": tgv_small, "indicator": indicator,
+            "fv50": fv50, "mortar": mortar,
             "peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
         }
         line.update(extra)

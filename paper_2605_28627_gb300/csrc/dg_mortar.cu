@@ -28,6 +28,91 @@ struct MortarShape {
   static constexpr int n = N + 1, P = n * n * n, NN = n * n, THREADS = 4 * NN;
 };
 
+// Both kernels work in tensor-product sweeps (one direction at a time) over
+// shared memory.  Tables, from the interpolation I_h[x][j] and the weights w:
+//   sI [h][x][j] = I_h[x][j]        (second sweep of the interpolation)
+//   sIT[h][j][x] = I_h[x][j]        (first sweep: consecutive threads, consecutive x)
+//   sW [h][x][j] = w_x I_h[x][j]    (both sweeps of the projection)
+template <int n>
+__device__ __forceinline__ void mortar_tables(const double* __restrict__ tab, double* sI, double* sIT, double* sW,
+                                              double* sw, int t, int nthr) {
+  constexpr int NN = n * n;
+  for (int x = t; x < 2 * NN; x += nthr) {
+    const int h = x / NN, r = x - h * NN, a = r / n, j = r - a * n;   // r = a n + j
+    const double v = tab[x];
+    sI[x] = v;
+    sIT[h * NN + j * n + a] = v;
+    sW[x] = tab[2 * NN + a] * v;
+  }
+  for (int x = t; x < n; x += nthr) sw[x] = tab[2 * NN + x];
+}
+
+// First interpolation sweep, along the big face's first direction:
+//   T[h][f][pp + n j] = sum_i I_h[pp][i] B[f][i + n j]   for both halves h.
+template <int n, int NF>
+__device__ __forceinline__ void mortar_sweep1(const double* sIT, const double* B, double* T, int t, int nthr) {
+  constexpr int NN = n * n;
+  for (int o = t; o < 2 * NF * NN; o += nthr) {
+    const int h = o / (NF * NN), r = o - h * NF * NN, f = r / NN, pj = r - f * NN, pp = pj % n, j = pj / n;
+    const double* it = sIT + h * NN + pp;
+    const double* b = B + f * NN + j * n;
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) s = fma(it[i * n], b[i], s);
+    T[o] = s;
+  }
+}
+
+// Second sweep for quadrant k = a + 2 b at its node (pp, qq):
+//   out[f] = sum_j I_b[qq][j] T[a][f][pp + n j].
+template <int n, int NF>
+__device__ __forceinline__ void mortar_sweep2(const double* sI, const double* T, int k, int pp, int qq,
+                                              double out[NF]) {
+  constexpr int NN = n * n;
+  const double* ib = sI + (k >> 1) * NN + qq * n;
+  const double* tr = T + (k & 1) * NF * NN + pp;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) out[f] = 0.0;
+#pragma unroll
+  for (int j = 0; j < n; ++j) {
+    const double c = ib[j];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) out[f] = fma(c, tr[f * NN + j * n], out[f]);
+  }
+}
+
+// The projection's first sweep, along the quadrants' second direction:
+//   S[k][f][pp + n j] = sum_qq w_qq I_b[qq][j] Q[k][f][pp + n qq].
+template <int n, int NF>
+__device__ __forceinline__ void mortar_proj1(const double* sW, const double* Q, double* S, int t, int nthr) {
+  constexpr int NN = n * n;
+  for (int o = t; o < 4 * NF * NN; o += nthr) {
+    const int k = o / (NF * NN), r = o - k * NF * NN, f = r / NN, pj = r - f * NN, pp = pj % n, j = pj / n;
+    const double* wb = sW + (k >> 1) * NN + j;
+    const double* q = Q + (k * NF + f) * NN + pp;
+    double s = 0.0;
+#pragma unroll
+    for (int qq = 0; qq < n; ++qq) s = fma(wb[qq * n], q[qq * n], s);
+    S[o] = s;
+  }
+}
+
+// Second sweep, summed over the quadrants, at big-face node (i, j):
+//   sum_k sum_pp w_pp I_a[pp][i] S[k][f][pp + n j].
+template <int n, int NF>
+__device__ __forceinline__ double mortar_proj2(const double* sW, const double* S, int f, int i, int j) {
+  constexpr int NN = n * n;
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double* wa = sW + (k & 1) * NN + i;
+    const double* sr = S + (k * NF + f) * NN + j * n;
+#pragma unroll
+    for (int pp = 0; pp < n; ++pp) s = fma(wa[pp * n], sr[pp], s);
+  }
+  return s;
+}
+
 // (u, v, w, T) of a conservative state
 __device__ __forceinline__ void lift_vars(const double* q, int st, const Gas& g, double ph[4]) {
   const double ir = 1.0 / q[0];
@@ -53,60 +138,49 @@ __global__ void __launch_bounds__(MortarShape<N>::THREADS)
 k_mortar_lift(const double* __restrict__ U, const int* __restrict__ mortars, const double* __restrict__ tab,
               double* __restrict__ virt, int E, Gas g) {
   using S = MortarShape<N>;
-  constexpr int n = S::n, P = S::P, NN = S::NN;
-  __shared__ double sI[2 * NN], sw[n];
-  __shared__ double sB[4][NN];      // lifting variables at the big face's nodes
-  __shared__ double sS[4][4][NN];   // face averages on the quadrants, big-face order
+  constexpr int n = S::n, P = S::P, NN = S::NN, T = S::THREADS;
+  __shared__ double sI[2 * NN], sIT[2 * NN], sW[2 * NN], sw[n];
+  __shared__ double buf[44 * NN];
+  double* sB = buf;                 // [4][NN]  lifting variables at the big face's nodes
+  double* sT = buf + 4 * NN;        // [2][4][NN] first interpolation sweep
+  double* sS = buf + 12 * NN;       // [4][4][NN] face averages on the quadrants, big-face order
+  double* sP = buf + 28 * NN;       // [4][4][NN] first projection sweep
   const int m = blockIdx.x, t = threadIdx.x;
   const int* r = mortars + (size_t)m * 20;
   const int eB = dg_idx(r[0], E, kSiteMortar), fB = r[1];
-  for (int x = t; x < 2 * NN; x += S::THREADS) sI[x] = tab[x];
-  for (int x = t; x < n; x += S::THREADS) sw[x] = tab[2 * NN + x];
+  mortar_tables<n>(tab, sI, sIT, sW, sw, t, T);
   if (t < NN) {
     double ph[4];
     lift_vars(U + (size_t)eB * 5 * P + face_node<n>(fB, t % n, t / n), P, g, ph);
 #pragma unroll
-    for (int a = 0; a < 4; ++a) sB[a][t] = ph[a];
+    for (int a = 0; a < 4; ++a) sB[a * NN + t] = ph[a];
   }
   __syncthreads();
+  mortar_sweep1<n, 4>(sIT, sB, sT, t, T);
+  __syncthreads();
   const int k = t / NN, pq = t % NN, pp = pq % n, qq = pq / n;
-  const double* Ia = sI + (k & 1) * NN;
-  const double* Ib = sI + (k >> 1) * NN;
   {
-    double ib[4] = {0, 0, 0, 0};
-    for (int j = 0; j < n; ++j)
-      for (int i = 0; i < n; ++i) {
-        const double c = Ia[pp * n + i] * Ib[qq * n + j];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) ib[a] = fma(c, sB[a][i + n * j], ib[a]);
-      }
+    double ib[4];
+    mortar_sweep2<n, 4>(sI, sT, k, pp, qq, ib);
     const int es = dg_idx(r[3 + 4 * k], E, kSiteMortar), fs = r[4 + 4 * k], fl = r[5 + 4 * k];
     int p2, q2;
     apply_flip<n>(fl, pp, qq, p2, q2);
     double ps[4];
     lift_vars(U + (size_t)es * 5 * P + face_node<n>(fs, p2, q2), P, g, ps);
 #pragma unroll
-    for (int a = 0; a < 4; ++a) sS[k][a][pq] = 0.5 * (ps[a] + ib[a]);
+    for (int a = 0; a < 4; ++a) sS[(k * 4 + a) * NN + pq] = 0.5 * (ps[a] + ib[a]);
     encode_vars(ib, g, virt + (size_t)(5 * m + k) * 5 * NN + p2 + n * q2, NN);
   }
   __syncthreads();
+  mortar_proj1<n, 4>(sW, sS, sP, t, T);
+  __syncthreads();
   if (t < NN) {
     const int i = t % n, j = t / n;
-    double sb[4] = {0, 0, 0, 0};
-    for (int kk = 0; kk < 4; ++kk) {
-      const double* Ja = sI + (kk & 1) * NN;
-      const double* Jb = sI + (kk >> 1) * NN;
-      for (int b = 0; b < n; ++b)
-        for (int a = 0; a < n; ++a) {
-          const double c = sw[a] * sw[b] * Ja[a * n + i] * Jb[b * n + j];
-#pragma unroll
-          for (int x = 0; x < 4; ++x) sb[x] = fma(c, sS[kk][x][a + n * b], sb[x]);
-        }
-    }
     const double sc = 0.25 / (sw[i] * sw[j]);
     double ph[4];
 #pragma unroll
-    for (int x = 0; x < 4; ++x) ph[x] = 2.0 * sb[x] * sc - sB[x][t];   // average with the big side = projection
+    for (int x = 0; x < 4; ++x)   // average with the big side's values = the projection
+      ph[x] = 2.0 * (mortar_proj2<n, 4>(sW, sP, x, i, j) * sc) - sB[x * NN + t];
     encode_vars(ph, g, virt + (size_t)(5 * m + 4) * 5 * NN + t, NN);
   }
 }
@@ -117,38 +191,32 @@ k_mortar_flux(const double* __restrict__ U, const double* __restrict__ grad, con
               const int* __restrict__ mortars, const double* __restrict__ tab, double* __restrict__ fstar, int E,
               int F, Gas g) {
   using S = MortarShape<N>;
-  constexpr int n = S::n, P = S::P, NN = S::NN;
-  __shared__ double sI[2 * NN], sw[n];
-  __shared__ double sB[17][NN];     // the big face's state and gradients
-  __shared__ double sF[4][5][NN];   // quadrant fluxes, big-face order
+  constexpr int n = S::n, P = S::P, NN = S::NN, T = S::THREADS;
+  __shared__ double sI[2 * NN], sIT[2 * NN], sW[2 * NN], sw[n];
+  __shared__ double buf[51 * NN];
+  double* sB = buf;                 // [17][NN] the big face's state and gradients
+  double* sT = buf + 17 * NN;       // [2][17][NN] first interpolation sweep
+  double* sF = buf;                 // [4][5][NN] quadrant fluxes, big-face order (after the sweeps)
+  double* sP = buf + 20 * NN;       // [4][5][NN] first projection sweep
   const int m = blockIdx.x, t = threadIdx.x;
   const int* r = mortars + (size_t)m * 20;
   const int eB = dg_idx(r[0], E, kSiteMortar), fB = r[1], slotB = dg_idx(r[2], F, kSiteMortar);
-  for (int x = t; x < 2 * NN; x += S::THREADS) sI[x] = tab[x];
-  for (int x = t; x < n; x += S::THREADS) sw[x] = tab[2 * NN + x];
+  mortar_tables<n>(tab, sI, sIT, sW, sw, t, T);
   if (t < NN) {
     const int node = face_node<n>(fB, t % n, t / n);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sB[v][t] = U[((size_t)eB * 5 + v) * P + node];
+    for (int v = 0; v < 5; ++v) sB[v * NN + t] = U[((size_t)eB * 5 + v) * P + node];
 #pragma unroll
-    for (int x = 0; x < 12; ++x) sB[5 + x][t] = grad[((size_t)eB * 12 + x) * P + node];
+    for (int x = 0; x < 12; ++x) sB[(5 + x) * NN + t] = grad[((size_t)eB * 12 + x) * P + node];
   }
   __syncthreads();
+  mortar_sweep1<n, 17>(sIT, sB, sT, t, T);
+  __syncthreads();
   const int k = t / NN, pq = t % NN, pp = pq % n, qq = pq / n;
+  double qR[17];
+  mortar_sweep2<n, 17>(sI, sT, k, pp, qq, qR);
+  __syncthreads();   // sT is read; its space takes the fluxes
   {
-    const double* Ia = sI + (k & 1) * NN;
-    const double* Ib = sI + (k >> 1) * NN;
-    double dR[5] = {0, 0, 0, 0, 0}, gR[12];
-#pragma unroll
-    for (int x = 0; x < 12; ++x) gR[x] = 0.0;
-    for (int j = 0; j < n; ++j)
-      for (int i = 0; i < n; ++i) {
-        const double c = Ia[pp * n + i] * Ib[qq * n + j];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) dR[v] = fma(c, sB[v][i + n * j], dR[v]);
-#pragma unroll
-        for (int x = 0; x < 12; ++x) gR[x] = fma(c, sB[5 + x][i + n * j], gR[x]);
-      }
     const int es = dg_idx(r[3 + 4 * k], E, kSiteMortar), fs = r[4 + 4 * k], fl = r[5 + 4 * k];
     const int slot = dg_idx(r[6 + 4 * k], F, kSiteMortar);
     int p2, q2;
@@ -160,27 +228,16 @@ k_mortar_flux(const double* __restrict__ U, const double* __restrict__ grad, con
 #pragma unroll
     for (int x = 0; x < 12; ++x) gL[x] = grad[((size_t)es * 12 + x) * P + node];
     const double* fg = facegeo + (size_t)slot * 4 * NN + o;
-    face_flux_core<double>(dL, dR, gL, gR, fg[0], fg[NN], fg[2 * NN], fg[3 * NN], g, &sF[k][0][pq], NN);
+    face_flux_core<double>(dL, qR, gL, qR + 5, fg[0], fg[NN], fg[2 * NN], fg[3 * NN], g, sF + k * 5 * NN + pq, NN);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) fstar[((size_t)slot * 5 + v) * NN + o] = sF[k][v][pq];
+    for (int v = 0; v < 5; ++v) fstar[((size_t)slot * 5 + v) * NN + o] = sF[(k * 5 + v) * NN + pq];
   }
   __syncthreads();
-  if (t < NN) {
-    const int i = t % n, j = t / n;
-    double sb[5] = {0, 0, 0, 0, 0};
-    for (int kk = 0; kk < 4; ++kk) {
-      const double* Ja = sI + (kk & 1) * NN;
-      const double* Jb = sI + (kk >> 1) * NN;
-      for (int b = 0; b < n; ++b)
-        for (int a = 0; a < n; ++a) {
-          const double c = sw[a] * sw[b] * Ja[a * n + i] * Jb[b * n + j];
-#pragma unroll
-          for (int v = 0; v < 5; ++v) sb[v] = fma(c, sF[kk][v][a + n * b], sb[v]);
-        }
-    }
-    const double sc = -1.0 / (sw[i] * sw[j]);   // out of the big element
-#pragma unroll
-    for (int v = 0; v < 5; ++v) fstar[((size_t)slotB * 5 + v) * NN + t] = sb[v] * sc;
+  mortar_proj1<n, 5>(sW, sF, sP, t, T);
+  __syncthreads();
+  for (int o = t; o < 5 * NN; o += T) {   // out of the big element
+    const int v = o / NN, ij = o - v * NN, i = ij % n, j = ij / n;
+    fstar[((size_t)slotB * 5 + v) * NN + ij] = mortar_proj2<n, 5>(sW, sP, v, i, j) * (-1.0 / (sw[i] * sw[j]));
   }
 }
 
