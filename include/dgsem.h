@@ -219,6 +219,29 @@ dg_status dg_indicator(dg_ctx* ctx, const double* dU, int32_t var, double log10_
  * set.  dg_max_dt keeps the DG time-step restriction.  Does not synchronise. */
 dg_status dg_set_fv_mask(dg_ctx* ctx, const int32_t* dMask, dg_stream stream);
 
+/* Automatic switching of troubled cells between the DG and the FV sub-cell
+ * operator (Sec. 3.1: the modal indicator selects the elements the FV scheme
+ * takes over; Sec. 3.2.2 lists the switch as a kernel step of its own).
+ * Before every later evaluation of R(U) (dg_time_derivative, each stage of
+ * dg_rk_step, also inside its captured graph) the indicator of dg_indicator
+ * (quantity var) of the evaluated state sets the FV mask in place: element e
+ * becomes an FV element where log10(eta_e) > log10_upper or where its nodal
+ * state is not admissible (density or pressure not positive at a node), a DG
+ * element where log10(eta_e) < log10_lower and every node is admissible, and
+ * keeps its representation in between (hysteresis; FP64 decisions).  The
+ * state stays nodal in both representations, so a switch moves no data.  The
+ * mask starts from the one set by dg_set_fv_mask, else all DG; dg_set_fv_mask
+ * (NULL) clears it while switching is on.  var < 0 turns switching off and
+ * keeps the mask in effect.  DG_EINVAL for an unknown var or thresholds that
+ * are not finite with upper >= lower; DG_EUNSUPPORTED where dg_set_fv_mask
+ * would be.  Allocates as dg_set_fv_mask does.  Does not synchronise. */
+dg_status dg_set_fv_switch(dg_ctx* ctx, int32_t var, double log10_upper, double log10_lower, dg_stream stream);
+
+/* The FV mask in effect (1: FV element), into dMask (device, n_elems int32);
+ * all zero when no FV elements are set.  Stream-ordered after the launches
+ * before it, so after an RK call it holds the mask of its last stage. */
+dg_status dg_get_fv_mask(dg_ctx* ctx, int32_t* dMask, dg_stream stream);
+
 /* Physical node positions X[e][c][k][j][i] (device, n_elems*3*(N+1)^3). */
 dg_status dg_node_coords(dg_ctx* ctx, double* dX, dg_stream stream);
 

@@ -253,7 +253,13 @@ struct Ctx {
   int nfaces;
   std::vector<double> fn;     // [face][3][n*n]  unit normal of the master side
   std::vector<double> fsJ;    // [face][n*n]     surface element of the master side
-  std::vector<int> fv_mask;   // [e] 1: FV sub-cell element (empty: none)
+  mutable std::vector<int> fv_mask;   // [e] 1: FV sub-cell element (empty: none)
+  // automatic DG/FV switching before every evaluation of R(U): the Persson
+  // indicator of the evaluated state against two log10 thresholds
+  bool sw_on = false;
+  int sw_var = 2;
+  double sw_up = 0.0, sw_low = 0.0;
+  mutable double sw_margin = 1e300;   // smallest |log10 eta - threshold| met (test hook)
   // mortars (non-conforming faces, 2:1): [m][14] = big (e, f), four small (e, f, flip)
   int M = 0;
   std::vector<int> mortars;
@@ -1069,11 +1075,43 @@ static const double RK14_C[14] = {0.0, 0.0367762454319673, 0.1249685262725025, 0
                                   0.8734213127600976};
 
 static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double mu);
+static void state_persson(const Ctx& c, const double* U, int var, double* out);
+
+// Automatic switching of troubled cells (Sec. 3.1: the modal indicator marks
+// the DG elements that the FV sub-cell operator takes over; Sec. 3.2.2 names
+// the switch as a step of its own): before R(U) is evaluated, element e
+// becomes an FV element where log10 eta_e > sw_up, a DG element where
+// log10 eta_e < sw_low, and keeps its representation in between.  The state
+// stays nodal in both representations, so the switch converts no data; but
+// the nodal polynomial of an FV element's sub-cell means may leave the
+// admissible states where its means do not, so an element goes to DG only
+// with positive density and pressure at every node, and a DG element
+// without them goes to FV whatever its indicator says.
+static void fv_switch(const Ctx& c, const double* U) {
+  std::vector<double> eta(c.E);
+  state_persson(c, U, c.sw_var, eta.data());
+  if (c.fv_mask.empty()) c.fv_mask.assign(c.E, 0);
+  const int P = c.P;
+  for (int e = 0; e < c.E; ++e) {
+    bool admissible = true;
+    for (int id = 0; id < P; ++id) {
+      double qs[5];
+      for (int v = 0; v < 5; ++v) qs[v] = U[((size_t)e * 5 + v) * P + id];
+      const Prim<double> w = cons2prim(c.prm, qs);
+      if (!(w.rho > 0.0 && w.p > 0.0)) admissible = false;
+    }
+    const double l = eta[e] > 0.0 ? std::log10(eta[e]) : -HUGE_VAL;
+    c.sw_margin = std::min(c.sw_margin, std::min(std::fabs(l - c.sw_up), std::fabs(l - c.sw_low)));
+    if (l > c.sw_up || !admissible) c.fv_mask[e] = 1;
+    else if (l < c.sw_low) c.fv_mask[e] = 0;
+  }
+}
 
 // R(U) on the context's node set (the Gauss-node operator is FP64 only).
 template <class T>
 static void rhs_any(const Ctx& c, const T* U, T* Ut, double t, T mu) {
   if constexpr (std::is_same<T, double>::value) {
+    if (c.sw_on) fv_switch(c, U);
     if (c.nodes == 1) { rhs_lg(c, U, Ut, t, mu); return; }
   }
   rhs(c, U, Ut, t, mu);
@@ -1955,6 +1993,24 @@ static std::vector<double> modal_transform(const std::vector<double>& x) {
 }
 
 // eta of one element from its nodal values q[k][j][i].
+static double persson_eta(int n, const std::vector<double>& Vi, const double* q);
+
+static void state_persson(const Ctx& c, const double* U, int var, double* out) {
+  const int n = c.n, P = c.P;
+  const std::vector<double>& x = c.nodes == 1 ? c.g.x : c.b.x;
+  const std::vector<double> Vi = modal_transform(x);
+  std::vector<double> q(P);
+  for (int e = 0; e < c.E; ++e) {
+    for (int id = 0; id < P; ++id) {
+      double qs[5];
+      for (int v = 0; v < 5; ++v) qs[v] = U[((size_t)e * 5 + v) * P + id];
+      const Prim<double> w = cons2prim(c.prm, qs);
+      q[id] = var == 0 ? w.rho : (var == 1 ? w.p : w.rho * w.p);
+    }
+    out[e] = persson_eta(n, Vi, q.data());
+  }
+}
+
 static double persson_eta(int n, const std::vector<double>& Vi, const double* q) {
   const int N = n - 1;
   double top = 0.0, all = 0.0;
@@ -1989,22 +2045,7 @@ void orc_persson_field(int N, const double* x, int E, const double* q, double* o
 
 // Persson indicator of the state U of an oracle context at its own nodes
 // (LGL, or Gauss for a Gauss-node context); var = 0: rho, 1: p, 2: rho p.
-void orc_persson(void* h, const double* U, int var, double* out) {
-  Ctx* c = (Ctx*)h;
-  const int n = c->n, P = c->P;
-  const std::vector<double>& x = c->nodes == 1 ? c->g.x : c->b.x;
-  const std::vector<double> Vi = modal_transform(x);
-  std::vector<double> q(P);
-  for (int e = 0; e < c->E; ++e) {
-    for (int id = 0; id < P; ++id) {
-      double qs[5];
-      for (int v = 0; v < 5; ++v) qs[v] = U[((size_t)e * 5 + v) * P + id];
-      const Prim<double> w = cons2prim(c->prm, qs);
-      q[id] = var == 0 ? w.rho : (var == 1 ? w.p : w.rho * w.p);
-    }
-    out[e] = persson_eta(n, Vi, q.data());
-  }
-}
+void orc_persson(void* h, const double* U, int var, double* out) { state_persson(*(Ctx*)h, U, var, out); }
 
 // Create an oracle context.  prm = {gamma, R, Pr, mu, mms_amp}; returns NULL
 // and fills errbuf on a bad mesh.
@@ -2074,6 +2115,32 @@ int orc_set_fv_mask(void* h, const int* mask) {
   if (c->M > 0) return -1;   // the FV sub-cells are built for conforming meshes
   c->fv_mask.assign(mask, mask + c->E);
   return 0;
+}
+
+// Automatic DG/FV switching (fv_switch) with the indicator of var (0: rho,
+// 1: p, 2: rho p) against log10 thresholds up >= low; var < 0 turns it off
+// (the mask stays as it is).  Returns 0, -1 on a mesh with mortars, -2 for
+// bad arguments.
+int orc_set_fv_switch(void* h, int var, double log10_up, double log10_low) {
+  Ctx* c = (Ctx*)h;
+  if (var < 0) { c->sw_on = false; return 0; }
+  if (c->M > 0) return -1;
+  if (var > 2 || !(log10_up >= log10_low)) return -2;
+  c->sw_on = true;
+  c->sw_var = var;
+  c->sw_up = log10_up;
+  c->sw_low = log10_low;
+  return 0;
+}
+
+// The FV mask in effect (all zero if none); returns and resets the smallest
+// distance of a log10 eta from a threshold since the last call.
+double orc_fv_state(void* h, int* mask) {
+  Ctx* c = (Ctx*)h;
+  for (int e = 0; e < c->E; ++e) mask[e] = c->fv_mask.empty() ? 0 : c->fv_mask[e];
+  const double m = c->sw_margin;
+  c->sw_margin = 1e300;
+  return m;
 }
 
 // Lifted gradients G [E][12][P] (row phi*3 + l = d phi / d x_l).

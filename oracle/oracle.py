@@ -84,6 +84,10 @@ def _load(omp: bool = False):
     L.orc_count_ec_flux_ops.argtypes = [_dp, _dp, _dp, _dp, _dp]
     L.orc_persson_field.argtypes = [C.c_int, _dp, C.c_int, _dp, _dp]
     L.orc_persson.argtypes = [C.c_void_p, _dp, C.c_int, _dp]
+    L.orc_set_fv_switch.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
+    L.orc_set_fv_switch.restype = C.c_int
+    L.orc_fv_state.argtypes = [C.c_void_p, C.c_void_p]
+    L.orc_fv_state.restype = C.c_double
     _libs[omp] = L
     return L
 
@@ -288,6 +292,30 @@ class Oracle:
         if self._L.orc_set_fv_mask(self._h, m.ctypes.data) != 0:
             raise ValueError("oracle: the FV sub-cell operator is built for conforming meshes")
         self.fv_mask = m
+
+    def set_fv_switch(self, var, log10_upper=None, log10_lower=None):
+        """Automatic DG/FV switching before every evaluation of R(U): the
+        Persson indicator of rho (var 0), p (1) or rho p (2) of the evaluated
+        state; above 10^log10_upper an element becomes an FV element, below
+        10^log10_lower a DG element, in between it keeps its representation.
+        var None turns it off (the mask in effect stays)."""
+        if var is None:
+            self._L.orc_set_fv_switch(self._h, -1, 0.0, 0.0)
+            return
+        if log10_lower is None:
+            log10_lower = log10_upper
+        r = self._L.orc_set_fv_switch(self._h, int(var), float(log10_upper), float(log10_lower))
+        if r == -1:
+            raise ValueError("oracle: the FV sub-cell operator is built for conforming meshes")
+        if r != 0:
+            raise ValueError("oracle: bad switching arguments")
+
+    def fv_state(self):
+        """(the FV mask in effect, the smallest distance of a log10 indicator
+        value from a switching threshold since the last call)."""
+        m = np.zeros(self.E, dtype=np.int32)
+        margin = self._L.orc_fv_state(self._h, m.ctypes.data)
+        return m, margin
 
     def lifting(self, U):
         G = np.zeros((self.E, 12, self.P))

@@ -39,7 +39,8 @@ EXPORTS = ["dg_init", "dg_destroy", "dg_state_len", "dg_time_derivative", "dg_rk
            "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
            "dg_ensemble_step", "dg_ensemble_plan", "dg_ensemble_last_error", "dg_time_derivative_vjp",
            "dg_adjoint_step", "dg_adjoint_solve", "dg_checkpoint_schedule", "dg_kinetic_energy", "dg_set_viscosity",
-           "dg_check_conversions", "dg_check_reciprocals", "dg_indicator", "dg_set_fv_mask", "dg_last_error"]
+           "dg_check_conversions", "dg_check_reciprocals", "dg_indicator", "dg_set_fv_mask", "dg_set_fv_switch",
+           "dg_get_fv_mask", "dg_last_error"]
 
 
 class DGError(RuntimeError):
@@ -93,6 +94,8 @@ def load(build_if_missing: bool = True):
     L.dg_check_reciprocals.argtypes = [vp, i32, vp, vp, vp]
     L.dg_indicator.argtypes = [vp, vp, i32, f64, vp, vp, vp]
     L.dg_set_fv_mask.argtypes = [vp, vp, vp]
+    L.dg_set_fv_switch.argtypes = [vp, i32, f64, f64, vp]
+    L.dg_get_fv_mask.argtypes = [vp, vp, vp]
     L.dg_conserved_totals_noalloc.argtypes = [vp, vp, i32, i32, i32, vp, vp]
     L.dg_ensemble_create.argtypes = [C.POINTER(vp), i32, C.c_char_p, C.POINTER(vp)]
     L.dg_ensemble_destroy.argtypes = [vp]
@@ -113,7 +116,8 @@ def load(build_if_missing: bool = True):
                  "dg_probe_peaks", "dg_conserved_totals_noalloc", "dg_ensemble_create", "dg_ensemble_destroy",
                  "dg_ensemble_step", "dg_ensemble_plan", "dg_time_derivative_vjp", "dg_adjoint_step",
                  "dg_adjoint_solve", "dg_checkpoint_schedule", "dg_kinetic_energy", "dg_set_viscosity",
-                 "dg_check_conversions", "dg_check_reciprocals", "dg_indicator", "dg_set_fv_mask"):
+                 "dg_check_conversions", "dg_check_reciprocals", "dg_indicator", "dg_set_fv_mask",
+                 "dg_set_fv_switch", "dg_get_fv_mask"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -275,6 +279,25 @@ class Solver:
         m = (m.reshape(-1) != 0).to(device="cuda:%d" % self.device, dtype=torch.int32).contiguous()
         self._check(self._L.dg_set_fv_mask(self._h, _ptr(m), _stream_handle(stream)))
         self._fv_mask = m   # kept until the stream has passed the copy
+
+    def set_fv_switch(self, var=IND_RHOP, log10_upper=None, log10_lower=None, stream=None):
+        """Automatic DG/FV switching before every evaluation of R(U): above
+        10^log10_upper an element becomes an FV element, below 10^log10_lower
+        (with an admissible nodal state) a DG element; var None turns it off."""
+        if var is None:
+            self._check(self._L.dg_set_fv_switch(self._h, -1, 0.0, 0.0, _stream_handle(stream)))
+            return
+        if log10_lower is None:
+            log10_lower = log10_upper
+        self._check(self._L.dg_set_fv_switch(self._h, int(var), float(log10_upper), float(log10_lower),
+                                             _stream_handle(stream)))
+
+    def fv_mask(self, stream=None):
+        """The FV mask in effect (device int32 [E])."""
+        import torch
+        m = torch.empty(self.E, dtype=torch.int32, device="cuda:%d" % self.device)
+        self._check(self._L.dg_get_fv_mask(self._h, _ptr(m), _stream_handle(stream)))
+        return m
 
     def node_coords(self, stream=None):
         import torch

@@ -148,6 +148,7 @@ static cudaError_t enqueue_steps(Ctx& c, double* U, double* G, int nsteps, cudaS
   for (int st = 0; st < nsteps; ++st) {
     if ((err = cudaMemsetAsync(G, 0, bytes, s)) != cudaSuccess) return err;
     for (int k = 0; k < rk.stages; ++k) {
+      if ((err = launch_fv_switch(c, U, s)) != cudaSuccess) return err;
       if ((err = launch_lift(c, U, s)) != cudaSuccess) return err;
       if ((err = launch_face(c, U, s)) != cudaSuccess) return err;
       StageArgs a{U, U, G, nullptr, c.d_clock, rk.C[k], rk.A[k], rk.B[k], 1};
@@ -481,6 +482,7 @@ dg_status dg_time_derivative(dg_ctx* c, const double* dU, double* dUt, double t,
   cudaStream_t s = (cudaStream_t)stream;
   DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
   DG_CUDA(launch_set_clock(c->d_clock, t, 0.0, s), c, "clock");
+  DG_CUDA(launch_fv_switch(*c, dU, s), c, "FV switch kernels");
   DG_CUDA(launch_lift(*c, dU, s), c, "lift kernel");
   DG_CUDA(launch_face(*c, dU, s), c, "face kernel");
   StageArgs a{dU, nullptr, nullptr, dUt, c->d_clock, 0.0, 0.0, 0.0, 0};
@@ -585,6 +587,41 @@ dg_status dg_indicator(dg_ctx* c, const double* dU, int32_t var, double log10_th
   return checked(c, s);
 }
 
+// The FV sub-cell buffers and tables, set up once per context.
+static dg_status fv_alloc(dg_ctx* c, cudaStream_t s) {
+  if (c->d_fv_mask) return DG_OK;
+  const size_t E = c->E, P = c->P, NN = c->NN, n = c->n;
+  std::vector<double> tab, nodes = c->x;   // the context's node set: LGL, or Gauss below
+  if (c->prm.nodes == DG_NODES_LG) {
+    std::vector<double> gtab;
+    gauss_table(c->N, c->x, gtab, &nodes);
+  }
+  fv_tables(c->N, nodes, tab);
+  DG_CUDA(cudaMalloc(&c->d_fv_tab, sizeof(double) * tab.size()), c, "FV tables");
+  DG_CUDA(cudaMalloc(&c->d_fv_iJb, sizeof(double) * E * P), c, "FV sub-cell Jacobians");
+  DG_CUDA(cudaMalloc(&c->d_fv_S, sizeof(double) * E * 3 * (n + 1) * NN * 4), c, "FV area vectors");
+  DG_CUDA(cudaMalloc(&c->d_fv_M, sizeof(double) * E * 17 * P), c, "FV sub-cell means");
+  DG_CUDA(cudaMalloc(&c->d_fv_Fb, sizeof(double) * (size_t)c->nfaces * 5 * NN), c, "FV sub-face fluxes");
+  DG_CUDA(cudaMemcpyAsync(c->d_fv_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s), c,
+          "FV tables copy");
+  DG_CUDA(fv_setup(*c, s), c, "FV geometry kernel");
+  // the host table must outlive the copy
+  DG_CUDA(cudaStreamSynchronize(s), c, "FV set-up");
+  DG_CUDA(cudaMalloc(&c->d_fv_lists, sizeof(int) * (2 * E + 2)), c, "FV element lists");
+  DG_CUDA(cudaMalloc(&c->d_fv_mask, sizeof(int) * E), c, "FV mask");
+  return DG_OK;
+}
+
+// Whether the stages run the FV kernels; a captured RK graph has the other
+// launch sequence after a change.
+static void set_fv_on(dg_ctx* c, bool on) {
+  if (on != c->fv_on && c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->fv_on = on;
+}
+
 dg_status dg_set_fv_mask(dg_ctx* c, const int32_t* dMask, dg_stream stream) {
   if (!c) return fail(c, DG_EINVAL, "dg_set_fv_mask: null context");
   cudaStream_t s = (cudaStream_t)stream;
@@ -594,38 +631,63 @@ dg_status dg_set_fv_mask(dg_ctx* c, const int32_t* dMask, dg_stream stream) {
     return fail(c, DG_EUNSUPPORTED, "dg_set_fv_mask: the FV sub-cell operator is built for the FP64 operator");
   if (on && c->M > 0)
     return fail(c, DG_EUNSUPPORTED, "dg_set_fv_mask: the FV sub-cell operator is built for conforming meshes");
-  if (on && !c->d_fv_mask) {
-    const size_t E = c->E, P = c->P, NN = c->NN, n = c->n;
-    std::vector<double> tab, nodes = c->x;   // the context's node set: LGL, or Gauss below
-    if (c->prm.nodes == DG_NODES_LG) {
-      std::vector<double> gtab;
-      gauss_table(c->N, c->x, gtab, &nodes);
-    }
-    fv_tables(c->N, nodes, tab);
-    DG_CUDA(cudaMalloc(&c->d_fv_tab, sizeof(double) * tab.size()), c, "FV tables");
-    DG_CUDA(cudaMalloc(&c->d_fv_iJb, sizeof(double) * E * P), c, "FV sub-cell Jacobians");
-    DG_CUDA(cudaMalloc(&c->d_fv_S, sizeof(double) * E * 3 * (n + 1) * NN * 4), c, "FV area vectors");
-    DG_CUDA(cudaMalloc(&c->d_fv_M, sizeof(double) * E * 17 * P), c, "FV sub-cell means");
-    DG_CUDA(cudaMalloc(&c->d_fv_Fb, sizeof(double) * (size_t)c->nfaces * 5 * NN), c, "FV sub-face fluxes");
-    DG_CUDA(cudaMemcpyAsync(c->d_fv_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s), c,
-            "FV tables copy");
-    DG_CUDA(fv_setup(*c, s), c, "FV geometry kernel");
-    // the host table must outlive the copy
-    DG_CUDA(cudaStreamSynchronize(s), c, "FV set-up");
-    DG_CUDA(cudaMalloc(&c->d_fv_lists, sizeof(int) * (2 * E + 2)), c, "FV element lists");
-    DG_CUDA(cudaMalloc(&c->d_fv_mask, sizeof(int) * E), c, "FV mask");
-  }
   if (on) {
+    const dg_status st = fv_alloc(c, s);
+    if (st != DG_OK) return st;
     DG_CUDA(cudaMemcpyAsync(c->d_fv_mask, dMask, sizeof(int) * c->E, cudaMemcpyDeviceToDevice, s), c,
             "FV mask copy");
     DG_CUDA(launch_fv_lists(*c, s), c, "FV element lists kernel");
+  } else if (c->fv_switch) {   // all DG until the switch marks elements again
+    DG_CUDA(cudaMemsetAsync(c->d_fv_mask, 0, sizeof(int) * c->E, s), c, "FV mask clear");
+    DG_CUDA(launch_fv_lists(*c, s), c, "FV element lists kernel");
   }
-  if (on != c->fv_on && c->graph) {   // the captured RK graph has the other launch sequence
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
-  c->fv_on = on;
+  set_fv_on(c, on || c->fv_switch);
   return checked(c, s);
+}
+
+// Automatic DG/FV switching before every evaluation of R(U).
+dg_status dg_set_fv_switch(dg_ctx* c, int32_t var, double log10_upper, double log10_lower, dg_stream stream) {
+  if (!c) return fail(c, DG_EINVAL, "dg_set_fv_switch: null context");
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  if (var < 0) {   // off; the mask in effect stays
+    if (c->fv_switch && c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    c->fv_switch = false;
+    return DG_OK;
+  }
+  if (var > DG_IND_RHOP) return fail(c, DG_EINVAL, "dg_set_fv_switch: unknown indicator quantity");
+  if (!(log10_upper >= log10_lower) || !std::isfinite(log10_upper) || !std::isfinite(log10_lower))
+    return fail(c, DG_EINVAL, "dg_set_fv_switch: thresholds must be finite with upper >= lower");
+  if (c->prm.precision != DG_FP64)
+    return fail(c, DG_EUNSUPPORTED, "dg_set_fv_switch: the FV sub-cell operator is built for the FP64 operator");
+  if (c->M > 0)
+    return fail(c, DG_EUNSUPPORTED, "dg_set_fv_switch: the FV sub-cell operator is built for conforming meshes");
+  const bool fresh = !c->d_fv_mask;
+  const dg_status st = fv_alloc(c, s);
+  if (st != DG_OK) return st;
+  if (fresh || !c->fv_on) {   // start from the all-DG mask
+    DG_CUDA(cudaMemsetAsync(c->d_fv_mask, 0, sizeof(int) * c->E, s), c, "FV mask clear");
+    DG_CUDA(launch_fv_lists(*c, s), c, "FV element lists kernel");
+  }
+  if (!c->fv_switch && c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  c->fv_switch = true;
+  c->fv_sw_var = var;
+  c->fv_sw_up = log10_upper;
+  c->fv_sw_low = log10_lower;
+  set_fv_on(c, true);
+  return checked(c, s);
+}
+
+// The FV mask in effect (all zero without FV elements).
+dg_status dg_get_fv_mask(dg_ctx* c, int32_t* dMask, dg_stream stream) {
+  if (!c || !dMask) return fail(c, DG_EINVAL, "dg_get_fv_mask: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(c->device), c, "cudaSetDevice");
+  if (c->fv_on)
+    DG_CUDA(cudaMemcpyAsync(dMask, c->d_fv_mask, sizeof(int) * c->E, cudaMemcpyDeviceToDevice, s), c, "mask copy");
+  else
+    DG_CUDA(cudaMemsetAsync(dMask, 0, sizeof(int) * c->E, s), c, "mask clear");
+  return DG_OK;
 }
 
 dg_status dg_initial_state(dg_ctx* c, int32_t kind, double prm0, double* dU, dg_stream stream) {
@@ -672,7 +734,8 @@ dg_status dg_profile_stages(dg_ctx* c, double* dU, double* dG, double dt, int32_
     const int k = r % rk.stages;
     StageArgs a{dU, dU, dG, nullptr, c->d_clock, rk.C[k], rk.A[k], rk.B[k], 1};
     cudaEventRecord(ev[0], s);
-    err = launch_lift(*c, dU, s);
+    err = launch_fv_switch(*c, dU, s);   // counted with the lifting
+    if (err == cudaSuccess) err = launch_lift(*c, dU, s);
     cudaEventRecord(ev[1], s);
     if (err == cudaSuccess) err = launch_face(*c, dU, s);
     cudaEventRecord(ev[2], s);

@@ -12,6 +12,15 @@
 // per element (several for small N), the three directions as line sums of
 // the n x n transform through shared memory, FP64 throughout (eta decides the
 // flag), a fixed-order reduction per element.
+//
+// Automatic DG/FV switching (switch_mask): the flag array is the FV mask of
+// the context, updated before each evaluation of R(U): an element becomes an
+// FV element where log10 eta > the upper threshold or where its nodal state
+// is not admissible (density or pressure not positive at some node), a DG
+// element where log10 eta < the lower threshold and every node is admissible,
+// and otherwise keeps its representation.  The nodal polynomial of an FV
+// element's sub-cell means can leave the admissible states where the means do
+// not; the rule keeps such an element off the DG operator.
 #include <cmath>
 #include <vector>
 
@@ -45,22 +54,28 @@ void modal_table(int N, const std::vector<double>& x, const std::vector<double>&
 template <int N>
 __global__ void __launch_bounds__(Shape<N>::THREADS)
 k_indicator(const double* __restrict__ U, const double* __restrict__ T, int E, Gas g, int var, double log_thresh,
-            double* __restrict__ eta, int* __restrict__ flag) {
+            double* __restrict__ eta, int* __restrict__ flag, bool switch_mask, double log_low) {
   using S = Shape<N>;
   constexpr int n = S::n, P = S::P, EPB = S::EPB;
   __shared__ double sT[n * n];
   __shared__ double s0[EPB * P], s1[EPB * P];
+  __shared__ int s_bad[EPB];
   const int le = threadIdx.x / P, id = threadIdx.x - le * P;
   const int e = blockIdx.x * EPB + le;
   const bool active = e < E;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) sT[t] = T[t];
+  if (id == 0) s_bad[le] = 0;
   double q = 0.0;
+  bool bad = false;
   if (active) {
     const double* u = U + (size_t)e * 5 * P + id;
     const double rho = u[0], ir = rcp_op(rho);
     const double p = g.gm1 * (u[4 * P] - 0.5 * ir * (u[P] * u[P] + u[2 * P] * u[2 * P] + u[3 * P] * u[3 * P]));
     q = var == 0 ? rho : (var == 1 ? p : rho * p);
+    bad = !(rho > 0.0 && p > 0.0);
   }
+  __syncthreads();   // s_bad cleared
+  if (bad) s_bad[le] = 1;
   double* q0 = s0 + le * P;
   double* q1 = s1 + le * P;
   q0[id] = q;
@@ -99,34 +114,44 @@ k_indicator(const double* __restrict__ U, const double* __restrict__ T, int E, G
   if (active && id == 0) {
     const double sa = q0[0], st = q1[0];
     const double r = sa > 0.0 ? st / sa : 0.0;
-    eta[e] = r;
-    if (flag) flag[e] = r > 0.0 && log10(r) > log_thresh ? 1 : 0;
+    if (eta) eta[e] = r;
+    const double l = r > 0.0 ? log10(r) : -HUGE_VAL;
+    if (switch_mask) {
+      if (l > log_thresh || s_bad[le]) flag[e] = 1;
+      else if (l < log_low) flag[e] = 0;
+    } else if (flag) {
+      flag[e] = l > log_thresh ? 1 : 0;
+    }
   }
 }
 
 template <int N>
 static cudaError_t indicator_N(const Ctx& c, const double* U, const double* T, int var, double log_thresh,
-                               double* eta, int* flag, cudaStream_t s) {
+                               double* eta, int* flag, cudaStream_t s, bool switch_mask, double log_low) {
   using S = Shape<N>;
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
-  k_indicator<N><<<blocks, S::THREADS, 0, s>>>(U, T, c.E, c.gas, var, log_thresh, eta, flag);
+  k_indicator<N><<<blocks, S::THREADS, 0, s>>>(U, T, c.E, c.gas, var, log_thresh, eta, flag, switch_mask,
+                                                log_low);
   return cudaGetLastError();
 }
 
 cudaError_t launch_indicator(const Ctx& c, const double* U, int var, double log_thresh, double* eta, int* flag,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool switch_mask, double log_low) {
   switch (c.N) {
-    case 1: return indicator_N<1>(c, U, c.d_modal, var, log_thresh, eta, flag, s);
-    case 2: return indicator_N<2>(c, U, c.d_modal, var, log_thresh, eta, flag, s);
-    case 3: return indicator_N<3>(c, U, c.d_modal, var, log_thresh, eta, flag, s);
-    case 4: return indicator_N<4>(c, U, c.d_modal, var, log_thresh, eta, flag, s);
-    case 5: return indicator_N<5>(c, U, c.d_modal, var, log_thresh, eta, flag, s);
-    case 6: return indicator_N<6>(c, U, c.d_modal, var, log_thresh, eta, flag, s);
-    case 7: return indicator_N<7>(c, U, c.d_modal, var, log_thresh, eta, flag, s);
-    case 8: return indicator_N<8>(c, U, c.d_modal, var, log_thresh, eta, flag, s);
-    case 9: return indicator_N<9>(c, U, c.d_modal, var, log_thresh, eta, flag, s);
+#define DG_IND_CASE(K) \
+    case K: return indicator_N<K>(c, U, c.d_modal, var, log_thresh, eta, flag, s, switch_mask, log_low);
+    DG_IND_CASE(1) DG_IND_CASE(2) DG_IND_CASE(3) DG_IND_CASE(4) DG_IND_CASE(5)
+    DG_IND_CASE(6) DG_IND_CASE(7) DG_IND_CASE(8) DG_IND_CASE(9)
+#undef DG_IND_CASE
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_fv_switch(const Ctx& c, const double* U, cudaStream_t s) {
+  if (!c.fv_switch) return cudaSuccess;
+  cudaError_t e = launch_indicator(c, U, c.fv_sw_var, c.fv_sw_up, nullptr, c.d_fv_mask, s, true, c.fv_sw_low);
+  if (e == cudaSuccess) e = launch_fv_lists(c, s);
+  return e;
 }
 
 }  // namespace dg

@@ -147,6 +147,9 @@ struct Ctx {
   double* d_modal = nullptr;     // [n][n] nodal -> orthonormal Legendre modes of the node set (indicator)
   // FV sub-cell elements (dg_fv.cu), allocated by the first dg_set_fv_mask
   bool fv_on = false;            // a mask is set: every stage runs the FV kernels
+  bool fv_switch = false;        // the indicator sets the mask before every evaluation of R(U)
+  int fv_sw_var = 2;             // its quantity (DG_IND_*) and log10 thresholds
+  double fv_sw_up = 0.0, fv_sw_low = 0.0;
   int* d_fv_mask = nullptr;      // [E] 1: FV element
   int* d_fv_lists = nullptr;     // [2E + 2]: DG elements, FV elements (ascending), their counts
   double* d_fv_tab = nullptr;    // V [n][n], V^-1 [n][n], L [n+1][n]
@@ -221,8 +224,13 @@ cudaError_t launch_mortar_flux(const Ctx& c, const double* U, cudaStream_t s);
 // Modal troubled-cell indicator (dg_indicator.cu).
 void modal_table(int N, const std::vector<double>& x, const std::vector<double>& w, bool lobatto,
                  std::vector<double>& T);
+// switch_mask: flag is the FV mask, updated with hysteresis (log_thresh the
+// upper, log_low the lower threshold) and the admissibility rule.
 cudaError_t launch_indicator(const Ctx& c, const double* U, int var, double log_thresh, double* eta, int* flag,
-                             cudaStream_t s);
+                             cudaStream_t s, bool switch_mask = false, double log_low = 0.0);
+// Before an evaluation of R(U) with automatic switching: the mask from the
+// indicator of U, then the element lists (nothing without switching).
+cudaError_t launch_fv_switch(const Ctx& c, const double* U, cudaStream_t s);
 
 // Geometry kernels (dg_geometry.cu).
 cudaError_t build_geometry(Ctx& c, const double* d_xgeo, int ngeo, int* d_bad, cudaStream_t s);

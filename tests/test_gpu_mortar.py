@@ -34,11 +34,12 @@ def _rel_err_per_var(got, ref):
     return np.array([np.abs(got[:, v] - ref[:, v]).max() / max(np.abs(ref[:, v]).max(), 1e-300) for v in range(5)])
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 @pytest.mark.parametrize("flux", [0, 1, 2])
 def test_mortar_time_derivative_parity(orc, dg, N, flux):
-    K = 3
-    mesh = refined_box_mesh(K, _refine(K, [0, 13]), rotate_seed=40 + N)
+    # straight-sided elements: no geometric amplification of the rounding at N = 8, 9
+    K = 3 if N <= 7 else 2
+    mesh = refined_box_mesh(K, _refine(K, [0, 13] if K == 3 else [0, 7]), rotate_seed=40 + N)
     kw = dict(mu=0.02, surf_flux=flux)
     o, s = orc.Oracle(mesh, N, **kw), dg.Solver(mesh, N, **kw)
     U = random_state(mesh.n_elems, N, seed=60 + N)
