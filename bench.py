@@ -385,6 +385,95 @@ def tgv_large(nsteps, local):
     return line
 
 
+def tgv_shock(t_end, local, every=20, thr=(-1.9, -2.4), variants=""):
+    """Compressible Taylor-Green vortex of Sec. 4.2: Ma 1.25, Re 1600, 16^3
+    Cartesian elements on [0, 2 pi]^3, N = 3, Sutherland viscosity (T_ref = T0,
+    S = 110.4 K / 273.15 K T0), LSERK4-5 at CFL 0.9 (dt from the state every
+    `every` steps), to t_end.  Variants: Gauss nodes with automatic DG/FV
+    switching (the paper's setup), LGL split form with and without switching,
+    Gauss nodes without it.  Switching on rho p, log10 thresholds thr (upper,
+    lower).  Reports E_k and eps_S at
+    every unit of time, the FV fraction, the time of the eps_S peak, and the
+    PID of the timed RK calls (indicator and switch included); a run whose
+    state becomes non-finite records the time."""
+    import torch
+    import paper_2605_28627_gb300 as dg
+    from workloads import box_mesh, tgv_params
+    K, N = 16, 3
+    prm = tgv_params(Ma=1.25, Re=1600.0)
+    mesh = box_mesh(K, 1, lo=0.0, hi=2 * math.pi)
+    dofs = mesh.n_elems * (N + 1) ** 3
+    runs = (("gauss_fv_switch", dg.NODES_LG, True), ("lgl_split_fv_switch", dg.NODES_LGL, True),
+            ("lgl_split_dg", dg.NODES_LGL, False), ("gauss_dg", dg.NODES_LG, False))
+    line = {"experiment": "compressible Taylor-Green vortex, Ma 1.25, Re 1600, 16^3 elements, N=3, Sutherland, "
+                          "to t=%g" % t_end, "dof": dofs, "switch": {"var": "rho p", "log10_upper": thr[0],
+                                                                     "log10_lower": thr[1]}}
+    for name, nodes, sw in runs:
+        if variants and name not in variants.split(","):
+            continue
+        s = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], nodes=nodes,
+                      visc_law=dg.VISC_SUTHERLAND, T_ref=prm["T0"], S_suth=110.4 / 273.15 * prm["T0"],
+                      device=local)
+        st = torch.cuda.Stream(device="cuda:%d" % local)
+        U = s.initial_state("tgv", prm["p0"], stream=st)
+        G = torch.empty_like(U)
+        if sw:
+            s.set_fv_switch(dg.IND_RHOP, thr[0], thr[1], stream=st)
+        t, steps, ms_tot, failed = 0.0, 0, 0.0, None
+        hist = {"t": [], "ek": [], "eps_s": [], "fv_fraction": []}
+        next_rec = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        first = True
+        fv_chunks = []
+        while t < t_end - 1e-12:
+            try:
+                if t >= next_rec - 1e-12:
+                    I = s.integrals(U, stream=st)
+                    hist["t"].append(round(t, 4))
+                    hist["ek"].append(float(I[5]))
+                    hist["eps_s"].append(float(I[6]))
+                    hist["fv_fraction"].append(float(s.fv_mask(stream=st).sum().item()) / mesh.n_elems)
+                    next_rec += 1.0
+                dt = min(s.max_dt(U, cfl=0.9, dfl=0.9, stream=st), t_end - t)
+            except dg.DGError:
+                failed = t
+                break
+            e0.record(st)
+            s.rk_step(U, G, t, dt, every, stream=st)
+            e1.record(st)
+            e1.synchronize()
+            if not first:             # the first call captures the graph
+                ms_tot += e0.elapsed_time(e1)
+                steps += every
+            first = False
+            t += every * dt
+            if sw:   # the mask of the chunk's last stage
+                fv_chunks.append(float(s.fv_mask(stream=st).sum().item()) / mesh.n_elems)
+        res = {"steps_timed": steps, "t_reached": round(t, 4), "nonfinite_at_t": failed}
+        if fv_chunks:
+            res.update({"fv_fraction_max_over_chunks": max(fv_chunks),
+                        "fv_fraction_mean_over_chunks": float(np.mean(fv_chunks))})
+        if steps:
+            rate = dofs * 5 * steps / (ms_tot * 1e-3)
+            res.update({"dof_stage_per_s": rate, "pid_ns": 1e9 / rate})
+        if hist["eps_s"]:
+            k = int(np.argmax(hist["eps_s"]))
+            res.update({"eps_s_peak": hist["eps_s"][k], "t_eps_s_peak": hist["t"][k],
+                        "fv_fraction_max": max(hist["fv_fraction"])})
+        res["history"] = hist
+        line[name] = res
+        del U, G
+        s.close()
+        torch.cuda.empty_cache()
+    return line
+
+
+def run_tgv_shock(args, local):
+    thr = tuple(float(v) for v in args.tgv_shock_thr.split(","))
+    print(json.dumps(tgv_shock(args.tgv_shock_t, local, thr=thr, variants=args.tgv_shock_variants)))
+    return 0
+
+
 def run_tgv_large(args, local):
     print(json.dumps(tgv_large(args.tgv_steps, local)))
     return 0
@@ -850,6 +939,11 @@ def main():
                     help="skip the 48^3 Taylor-Green and ensemble legs of the default line")
     ap.add_argument("--tgv-leg-steps", type=int, default=6, help="steps of the 48^3 leg of the default line")
     ap.add_argument("--mortar", action="store_true", help="run the 2:1 non-conforming mesh leg alone")
+    ap.add_argument("--tgv-shock", action="store_true",
+                    help="run the Ma 1.25 Taylor-Green study with automatic DG/FV switching")
+    ap.add_argument("--tgv-shock-t", type=float, default=20.0)
+    ap.add_argument("--tgv-shock-thr", default="-3.0,-3.5", help="log10 switching thresholds: upper,lower")
+    ap.add_argument("--tgv-shock-variants", default="", help="comma list of the study's variants ('' = all)")
     ap.add_argument("--adj-steps", type=int, default=200)
     ap.add_argument("--adj-dirs", type=int, default=32)
     args = ap.parse_args()
@@ -865,6 +959,8 @@ def main():
         return run_adjoint(args, local) if rank == 0 else 0
     if args.mortar:
         return run_mortar(args, local) if rank == 0 else 0
+    if args.tgv_shock:
+        return run_tgv_shock(args, local) if rank == 0 else 0
     if args.impl == "reference":
         return run_reference(args, world, rank)
 

@@ -162,17 +162,23 @@ dg_status dg_advance_host(dg_ctx* ctx, double* hU, double t, double dt, int32_t 
 
 /* Volume integrals with the LGL quadrature (Sec. 4.2 diagnostics), host_out8 =
  * { int rho, int rho u, int rho v, int rho w, int rho E,
- *   E_k = 1/(2|Omega|) int rho |u|^2, eps = mu/|Omega| int |omega|^2 (vorticity
- *   from the BR1-lifted velocity gradient), min p }, in units rho0 = U0 = L = 1.
+ *   E_k = 1/(2|Omega|) int rho |u|^2, eps = 1/|Omega| int mu(T) |omega|^2 (vorticity
+ *   from the BR1-lifted velocity gradient; with Sutherland's law a node with
+ *   T <= 0, possible only inside an FV element, adds nothing), min p }, in
+ *   units rho0 = U0 = L = 1.
  * Synchronises the stream.  DG_ENONFINITE if any value is NaN/Inf. */
 dg_status dg_integrals(dg_ctx* ctx, const double* dU, double* host_out8, dg_stream stream);
 
-/* Time step of Sec. 3.1 ("CFL = 0.9, same for the viscous restriction"):
+/* Time step of Sec. 3.1 (CFL number 0.9 for the convective and for the
+ * viscous limit there):
  * dt = min(cfl * 2/((2N+1) max_nodes sum_d lambda_d),
  *          dfl * (2/(2N+1))^2 / max_nodes (mu_eff sum_d |Ja^d|^2 / J^2)),
  * lambda_d = (|u . Ja^d| + c |Ja^d|) / J, mu_eff = max(4/3, gamma/Pr) mu / rho.
- * Synchronises the stream.  DG_ENONFINITE if a node's state gives a NaN or
- * infinite speed (NaN/Inf in the state, non-positive density or pressure). */
+ * Nodes of FV sub-cell elements whose density or pressure is not positive
+ * (the nodal polynomial of admissible sub-cell means can have them) do not
+ * enter.  Synchronises the stream.  DG_ENONFINITE if a node's state gives a
+ * NaN or infinite speed (NaN/Inf in the state, non-positive density or
+ * pressure outside FV elements). */
 dg_status dg_max_dt(dg_ctx* ctx, const double* dU, double cfl, double dfl, double* host_dt, dg_stream stream);
 
 /* Built-in initial states at the LGL nodes: DG_IC_TGV (Sec. 4.2, Eq. 6) with

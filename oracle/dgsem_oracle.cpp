@@ -2384,7 +2384,11 @@ void orc_integrals(void* h, const double* U, double* out) {
           double om2 = gg[1 * 3 + 0] - gg[0 * 3 + 1];
           double q[5];
           for (int v = 0; v < 5; ++v) q[v] = U[((size_t)e * 5 + v) * P + id];
-          const double mu_n = visc_mu(pr, pr.mu, cons2prim(pr, q).T_);
+          // Sutherland's mu(T) needs T > 0: a node with T <= 0 (only inside an FV
+          // element, whose nodal polynomial of admissible sub-cell means may
+          // leave the admissible states) adds nothing
+          const double Tn = cons2prim(pr, q).T_;
+          const double mu_n = (pr.visc_law == 1 && Tn <= 0.0) ? 0.0 : visc_mu(pr, pr.mu, Tn);
           ens += wq * mu_n * (om0 * om0 + om1 * om1 + om2 * om2);
         }
   }

@@ -61,7 +61,11 @@ k_integrals(const double* __restrict__ U, const double* __restrict__ J, const do
     const double o1 = g[2 * P] - g[6 * P];   // du/dz - dw/dx
     const double o2 = g[3 * P] - g[1 * P];   // dv/dx - du/dy
     const double p = gm1 * (q[4] - 0.5 * m2 * ir);
-    const double sf = visc_factor<double>(gas, p * ir * gas.inv_R);   // mu(T) / mu_ref
+    // mu(T) / mu_ref; Sutherland's law needs T > 0: a node with T <= 0 (only
+    // inside an FV element, whose nodal polynomial of admissible sub-cell
+    // means may leave the admissible states) adds nothing; NaN stays NaN
+    const double Tn = p * ir * gas.inv_R;
+    const double sf = (gas.visc_law == DG_VISC_SUTHERLAND && Tn <= 0.0) ? 0.0 : visc_factor<double>(gas, Tn);
     v[7] += wq * sf * (o0 * o0 + o1 * o1 + o2 * o2);
     v[8] = fmin(v[8], p);
   }
@@ -93,7 +97,8 @@ __global__ void __launch_bounds__(kRedThreads) k_fold(double* part, int nblk, in
 // and viscous mu_eff sum_d |Ja^d|^2 / J^2, maxima over all nodes.
 template <int N>
 __global__ void __launch_bounds__(kRedThreads)
-k_dt(const double* __restrict__ U, const double* __restrict__ metrics, double* __restrict__ part, int E, Gas g) {
+k_dt(const double* __restrict__ U, const double* __restrict__ metrics, double* __restrict__ part, int E, Gas g,
+     const int* __restrict__ fv_mask) {
   constexpr int n = N + 1, P = n * n * n;
   double v[2] = {0.0, 0.0};
   const bool is_min[2] = {false, false};
@@ -106,6 +111,10 @@ k_dt(const double* __restrict__ U, const double* __restrict__ metrics, double* _
     const double ir = 1.0 / q[0];
     const double u = q[1] * ir, vv = q[2] * ir, w = q[3] * ir;
     const double p = g.gm1 * (q[4] - 0.5 * (q[1] * u + q[2] * vv + q[3] * w));
+    // an FV element's nodes hold the polynomial of its sub-cell means, which
+    // may leave the admissible states where the means do not: such nodes do
+    // not enter (the DG bound used here is below the sub-cells' own one)
+    if (fv_mask && fv_mask[e] && !(q[0] > 0.0 && p > 0.0)) continue;
     const double cs = sqrt(g.gamma * p * ir);
     const double* mt = metrics + (size_t)e * 10 * P + id;
     const double iJ = mt[9 * P];
@@ -220,7 +229,7 @@ static cudaError_t integrals_N(Ctx& c, const double* U, double* d_w, cudaStream_
 template <int N>
 static cudaError_t dt_N(Ctx& c, const double* U, cudaStream_t s) {
   const int nb = red_blocks(c);
-  k_dt<N><<<nb, kRedThreads, 0, s>>>(U, c.d_metrics, c.d_red, c.E, c.gas);
+  k_dt<N><<<nb, kRedThreads, 0, s>>>(U, c.d_metrics, c.d_red, c.E, c.gas, c.fv_on ? c.d_fv_mask : nullptr);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   k_fold_max<<<1, kRedThreads, 0, s>>>(c.d_red, nb);
