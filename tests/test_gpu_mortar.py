@@ -102,3 +102,48 @@ def test_mortar_rejections(dg):
     bad.mortars[0, 2] = bad.mortars[0, 5]
     with pytest.raises(dg.DGError):
         dg.Solver(bad, 2)
+
+
+def _term_scale(orc, o, U, N):
+    """Per variable: max_i sum_m |2 D_im| x 3 max |f(q) . Ja^d| / min J, the
+    size of the flux-differencing terms whose sum is R (as in the MMS test of
+    the conforming operator)."""
+    _, Ja, J = o.geometry()
+    _, _, D = orc.basis(N)
+    Uf = U.reshape(U.shape[0], 5, -1)
+    r = Uf[:, 0]
+    u = Uf[:, 1:4] / r[:, None]
+    p = 0.4 * (Uf[:, 4] - 0.5 * r * (u ** 2).sum(1))
+    out = np.zeros(5)
+    for d in range(3):
+        un = np.einsum("elp,elp->ep", u, Ja[:, d])
+        f = [r * un] + [Uf[:, 1 + a] * un + p * Ja[:, d, a] for a in range(3)] + [(Uf[:, 4] + p) * un]
+        for v in range(5):
+            out[v] = max(out[v], np.abs(f[v]).max())
+    return 3 * out * 2 * np.abs(D).sum(1).max() / J.min()
+
+
+def test_mortar_bench_mesh_full_size(orc, dg):
+    """The 2:1 mesh of the bench (12^3 box, the cells with three even indices
+    split: 3240 elements, 1296 mortars, N = 7, MMS source) at its full size,
+    every node against the oracle: R(U) of a random state (1e-12 of max |R|),
+    R(U) of the manufactured solution (a small residual of cancelling terms:
+    1e-12 of the terms' size, the metric terms of the two codes differing by
+    their rounding, 1e-13 relative at N = 7), and one RK step."""
+    prm = mms_params()
+    K, N = 12, 7
+    i = np.arange(K ** 3)
+    mesh = refined_box_mesh(K, (i % 2 == 0) & ((i // K) % 2 == 0) & ((i // (K * K)) % 2 == 0), rotate_seed=3)
+    assert len(mesh.mortars) == 1296
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1)
+    o, s = orc.Oracle(mesh, N, **kw), dg.Solver(mesh, N, **kw)
+    Ur = random_state(mesh.n_elems, N, seed=11)
+    err = _rel_err_per_var(s.time_derivative(_cuda(Ur), t=0.0).cpu().numpy(), o.time_derivative(Ur, t=0.0))
+    assert (err < 1e-12).all(), err
+    U0 = o.initial_state("mms", 0.0)
+    d = np.abs(s.time_derivative(_cuda(U0), t=0.0).cpu().numpy() - o.time_derivative(U0, t=0.0))
+    assert (d.reshape(mesh.n_elems, 5, -1).max(axis=(0, 2)) < 1e-12 * _term_scale(orc, o, U0, N)).all()
+    ref = o.rk_steps(U0, 0.0, 5e-4, 1)
+    Ud = _cuda(U0)
+    s.rk_step(Ud, torch.empty_like(Ud), 0.0, 5e-4, 1)
+    assert np.abs(Ud.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-10
