@@ -587,6 +587,8 @@ dg_status dg_indicator(dg_ctx* c, const double* dU, int32_t var, double log10_th
   return checked(c, s);
 }
 
+}  // extern "C"
+
 // The FV sub-cell buffers and tables, set up once per context.
 static dg_status fv_alloc(dg_ctx* c, cudaStream_t s) {
   if (c->d_fv_mask) return DG_OK;
@@ -621,6 +623,8 @@ static void set_fv_on(dg_ctx* c, bool on) {
   }
   c->fv_on = on;
 }
+
+extern "C" {
 
 dg_status dg_set_fv_mask(dg_ctx* c, const int32_t* dMask, dg_stream stream) {
   if (!c) return fail(c, DG_EINVAL, "dg_set_fv_mask: null context");
