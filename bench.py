@@ -645,12 +645,25 @@ def mortar_rate(dg, N, dev, prm, dg_rate, K=12, steps=5):
     ms3 = s.profile_stages(U, G, dt, reps=5, stream=st)
     finite = bool(torch.isfinite(U).all().item())
     s.close()
+    # the same steps with the FP32 operator
+    s32 = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=dg.SOURCE_MMS,
+                    device=dev, precision=dg.FP32OP)
+    with torch.cuda.stream(st):
+        U32 = s32.initial_state("mms", 0.0, stream=st)
+    s32.rk_step(U32, G, 0.0, dt, 3, stream=st)
+    e0.record(st)
+    s32.rk_step(U32, G, 3 * dt, dt, steps, stream=st)
+    e1.record(st)
+    e1.synchronize()
+    rate32 = dofs * 5 * steps / (e0.elapsed_time(e1) * 1e-3)
+    s32.close()
     return {"workload": "MMS density wave, periodic %d^3 box with 1/8 of its cells split 2:1 (%d elements, %d "
                         "mortars), N=%d, rotated element frames" % (K, mesh.n_elems, len(mesh.mortars), N),
             "value": rate, "unit": UNIT, "pid_ns": 1e9 / rate, "ms_per_step": ms / steps,
             "vs_headline": rate / dg_rate,
             "stage_ms": {"lift_with_mortar_states": ms3[0], "face_with_mortar_fluxes": ms3[1], "volume": ms3[2]},
-            "state_finite": finite}
+            "state_finite": finite,
+            "fp32_operator": {"value": rate32, "pid_ns": 1e9 / rate32, "speedup_vs_fp64": rate32 / rate}}
 
 
 def run_mortar(args, local):

@@ -128,7 +128,7 @@ typedef struct {
  * and face points (Sec. 3.1 leaves this open).  Synchronous.
  * Errors: DG_EINVAL (null/size, unknown option, constants out of range),
  * DG_EUNSUPPORTED (N outside 1..9, Gauss nodes with DG_FP32OP, mortars with
- * Gauss nodes or DG_FP32OP: the mortar path is the FP64 LGL operator), DG_EMESH
+ * Gauss nodes: the mortar path is built for LGL nodes, FP64 or DG_FP32OP), DG_EMESH
  * (connectivity out of range or not reciprocal, Jacobian <= 0 at a node),
  * DG_ENOMEM, DG_ECUDA.  On failure *out is NULL. */
 dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out);

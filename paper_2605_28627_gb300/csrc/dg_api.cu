@@ -206,8 +206,8 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
       mesh->n_mortars < 0 || (mesh->n_mortars > 0 && !mesh->mortars))
     return fail(nullptr, DG_EINVAL, "dg_init: bad mesh sizes or null arrays");
   const int E = mesh->n_elems, M = mesh->n_mortars;
-  if (M > 0 && (prm->precision != DG_FP64 || prm->nodes != DG_NODES_LGL))
-    return fail(nullptr, DG_EUNSUPPORTED, "dg_init: mortars are built for the FP64 LGL operator");
+  if (M > 0 && prm->nodes != DG_NODES_LGL)
+    return fail(nullptr, DG_EUNSUPPORTED, "dg_init: mortars are built for LGL nodes");
   // mortar table: every side names its mortar back
   for (int m = 0; m < M; ++m) {
     const int* r = mesh->mortars + (size_t)m * 14;

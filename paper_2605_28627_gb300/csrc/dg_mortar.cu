@@ -18,7 +18,9 @@
 //   quadrants from the small side's state and gradients and the big side's
 //   interpolated ones, with the small face's geometry, and on the big face
 //   their projection, pointing out of the big element.
-// One block per mortar, a thread per quadrant node.
+// One block per mortar, a thread per quadrant node.  With the FP32 operator
+// (R = float) the gradients, face geometry and fluxes are FP32 as in the
+// conforming face kernel; the states stay FP64 and the maps run in FP64.
 #include "dg_stage.cuh"
 
 namespace dg {
@@ -185,11 +187,11 @@ k_mortar_lift(const double* __restrict__ U, const int* __restrict__ mortars, con
   }
 }
 
-template <int N>
+template <int N, typename R>
 __global__ void __launch_bounds__(MortarShape<N>::THREADS)
-k_mortar_flux(const double* __restrict__ U, const double* __restrict__ grad, const double* __restrict__ facegeo,
-              const int* __restrict__ mortars, const double* __restrict__ tab, double* __restrict__ fstar, int E,
-              int F, Gas g) {
+k_mortar_flux(const double* __restrict__ U, const R* __restrict__ grad, const R* __restrict__ facegeo,
+              const int* __restrict__ mortars, const double* __restrict__ tab, R* __restrict__ fstar, int E, int F,
+              Gas g) {
   using S = MortarShape<N>;
   constexpr int n = S::n, P = S::P, NN = S::NN, T = S::THREADS;
   __shared__ double sI[2 * NN], sIT[2 * NN], sW[2 * NN], sw[n];
@@ -207,7 +209,7 @@ k_mortar_flux(const double* __restrict__ U, const double* __restrict__ grad, con
 #pragma unroll
     for (int v = 0; v < 5; ++v) sB[v * NN + t] = U[((size_t)eB * 5 + v) * P + node];
 #pragma unroll
-    for (int x = 0; x < 12; ++x) sB[(5 + x) * NN + t] = grad[((size_t)eB * 12 + x) * P + node];
+    for (int x = 0; x < 12; ++x) sB[(5 + x) * NN + t] = (double)grad[((size_t)eB * 12 + x) * P + node];
   }
   __syncthreads();
   mortar_sweep1<n, 17>(sIT, sB, sT, t, T);
@@ -222,22 +224,30 @@ k_mortar_flux(const double* __restrict__ U, const double* __restrict__ grad, con
     int p2, q2;
     apply_flip<n>(fl, pp, qq, p2, q2);
     const int node = face_node<n>(fs, p2, q2), o = p2 + n * q2;
-    double dL[5], gL[12];
+    double dL[5];
+    R gL[12], gR[12];
 #pragma unroll
     for (int v = 0; v < 5; ++v) dL[v] = U[((size_t)es * 5 + v) * P + node];
 #pragma unroll
-    for (int x = 0; x < 12; ++x) gL[x] = grad[((size_t)es * 12 + x) * P + node];
-    const double* fg = facegeo + (size_t)slot * 4 * NN + o;
-    face_flux_core<double>(dL, qR, gL, qR + 5, fg[0], fg[NN], fg[2 * NN], fg[3 * NN], g, sF + k * 5 * NN + pq, NN);
+    for (int x = 0; x < 12; ++x) {
+      gL[x] = grad[((size_t)es * 12 + x) * P + node];
+      gR[x] = (R)qR[5 + x];
+    }
+    const R* fg = facegeo + (size_t)slot * 4 * NN + o;
+    R Fq[5];
+    face_flux_core<R>(dL, qR, gL, gR, fg[0], fg[NN], fg[2 * NN], fg[3 * NN], g, Fq, 1);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) fstar[((size_t)slot * 5 + v) * NN + o] = sF[(k * 5 + v) * NN + pq];
+    for (int v = 0; v < 5; ++v) {
+      sF[(k * 5 + v) * NN + pq] = (double)Fq[v];
+      fstar[((size_t)slot * 5 + v) * NN + o] = Fq[v];
+    }
   }
   __syncthreads();
   mortar_proj1<n, 5>(sW, sF, sP, t, T);
   __syncthreads();
   for (int o = t; o < 5 * NN; o += T) {   // out of the big element
     const int v = o / NN, ij = o - v * NN, i = ij % n, j = ij / n;
-    fstar[((size_t)slotB * 5 + v) * NN + ij] = mortar_proj2<n, 5>(sW, sP, v, i, j) * (-1.0 / (sw[i] * sw[j]));
+    fstar[((size_t)slotB * 5 + v) * NN + ij] = (R)(mortar_proj2<n, 5>(sW, sP, v, i, j) * (-1.0 / (sw[i] * sw[j])));
   }
 }
 
@@ -250,8 +260,14 @@ static cudaError_t mortar_lift_N(const Ctx& c, const double* U, cudaStream_t s) 
 
 template <int N>
 static cudaError_t mortar_flux_N(const Ctx& c, const double* U, cudaStream_t s) {
-  k_mortar_flux<N><<<c.M, MortarShape<N>::THREADS, 0, s>>>(U, (const double*)c.d_grad, c.d_facegeo, c.d_mortars,
-                                                           c.d_mortar_tab, (double*)c.d_fstar, c.E, c.nfaces, c.gas);
+  if (c.prm.precision == DG_FP32OP)
+    k_mortar_flux<N, float><<<c.M, MortarShape<N>::THREADS, 0, s>>>(
+        U, (const float*)c.d_grad, c.d_facegeo_f, c.d_mortars, c.d_mortar_tab, (float*)c.d_fstar, c.E, c.nfaces,
+        c.gas);
+  else
+    k_mortar_flux<N, double><<<c.M, MortarShape<N>::THREADS, 0, s>>>(
+        U, (const double*)c.d_grad, c.d_facegeo, c.d_mortars, c.d_mortar_tab, (double*)c.d_fstar, c.E, c.nfaces,
+        c.gas);
   return cudaGetLastError();
 }
 

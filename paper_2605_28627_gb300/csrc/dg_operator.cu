@@ -6,7 +6,7 @@ namespace dg {
 
 // The FP32 lifting is latency-bound: its register allocation must leave room
 // for 48 warps per SM (three 512-thread blocks at N = 7, twelve at N = 3).
-// MORTAR (FP64): mortar sides read their neighbour state from mvirt.
+// MORTAR: mortar sides read their neighbour state from mvirt.
 template <int N, typename R, bool MORTAR = false>
 __global__ void __launch_bounds__(Shape<N>::THREADS,
                                   sizeof(R) == 4 && Shape<N>::THREADS < 1536 ? 1536 / Shape<N>::THREADS : 1)
@@ -40,14 +40,12 @@ static cudaError_t lift_NR(const Ctx& c, const double* U, cudaStream_t s) {
   using S = Shape<N>;
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
   const R* metrics = (const R*)(sizeof(R) == 8 ? (const void*)c.d_metrics : (const void*)c.d_metrics_f);
-  if constexpr (sizeof(R) == 8) {
-    if (c.M > 0) {   // the mortar sides' neighbour states first
-      cudaError_t e = launch_mortar_lift(c, U, s);
-      if (e != cudaSuccess) return e;
-      k_lift<N, R, true><<<blocks, S::THREADS, lift_smem_bytes<N, R, S::EPB>(), s>>>(
-          U, metrics, c.d_elem_nbr, c.d_elem_face, c.d_D, (R*)c.d_grad, c.E, c.gas, 1.0 / c.w[0], c.d_mortar_virt, c.M);
-      return cudaGetLastError();
-    }
+  if (c.M > 0) {   // the mortar sides' neighbour states first
+    cudaError_t e = launch_mortar_lift(c, U, s);
+    if (e != cudaSuccess) return e;
+    k_lift<N, R, true><<<blocks, S::THREADS, lift_smem_bytes<N, R, S::EPB>(), s>>>(
+        U, metrics, c.d_elem_nbr, c.d_elem_face, c.d_D, (R*)c.d_grad, c.E, c.gas, 1.0 / c.w[0], c.d_mortar_virt, c.M);
+    return cudaGetLastError();
   }
   k_lift<N, R><<<blocks, S::THREADS, lift_smem_bytes<N, R, S::EPB>(), s>>>(
       U, metrics, c.d_elem_nbr, c.d_elem_face, c.d_D, (R*)c.d_grad, c.E, c.gas, 1.0 / c.w[0], nullptr, 0);
@@ -119,6 +117,9 @@ static cudaError_t setup_lift_N() {
                              (int)lift_smem_bytes<N, double, Shape<N>::EPB>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_lift<N, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lift_smem_bytes<N, float, Shape<N>::EPB>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_lift<N, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lift_smem_bytes<N, float, Shape<N>::EPB>());
   return e;
 }

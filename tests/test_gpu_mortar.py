@@ -84,11 +84,48 @@ def test_mortar_free_stream_and_conservation(orc, dg):
     assert bool((tot.abs() <= 1e-13 * scale).all()), (tot, scale)
 
 
+@pytest.mark.parametrize("N", [2, 3, 5, 7])
+def test_mortar_fp32_operator_vs_oracle(orc, dg, N):
+    """FP32 operator arithmetic (FP64 states and maps in the mortar kernels):
+    R(U) within the FP32 operator's bar, 2e-5 of max |R| per variable."""
+    K = 3 if N <= 5 else 2
+    mesh = refined_box_mesh(K, _refine(K, [0, 13] if K == 3 else [0, 7]), rotate_seed=90 + N)
+    o = orc.Oracle(mesh, N, mu=0.02)
+    s = dg.Solver(mesh, N, mu=0.02, precision=dg.FP32OP)
+    U = random_state(mesh.n_elems, N, seed=70 + N)
+    err = _rel_err_per_var(s.time_derivative(_cuda(U)).cpu().numpy(), o.time_derivative(U))
+    assert (err < 2e-5).all(), err
+
+
+def test_mortar_fp32_mms_steps_and_conservation(orc, dg):
+    prm = mms_params()
+    N, K = 4, 3
+    mesh = refined_box_mesh(K, _refine(K, [4, 13, 22]), rotate_seed=5)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1)
+    o = orc.Oracle(mesh, N, **kw)
+    s = dg.Solver(mesh, N, precision=dg.FP32OP, **kw)
+    U0 = o.initial_state("mms", 0.0)
+    ref = o.rk_steps(U0, 0.0, 1e-3, 10)
+    Ud = _cuda(U0)
+    s.rk_step(Ud, torch.empty_like(Ud), 0.0, 1e-3, 10)
+    # the FP32 operator's state bar: FP32 rounding of the stage updates relative to |U|
+    assert np.abs(Ud.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-6
+    # discrete conservation through the mortars: FP32 flux rounding only
+    s2 = dg.Solver(mesh, N, mu=0.02, precision=dg.FP32OP)
+    Ur = _cuda(random_state(mesh.n_elems, N, seed=9))
+    R = s2.time_derivative(Ur)
+    _, J = s2.geometry()
+    _, w, _ = orc.basis(N)
+    wq = torch.from_numpy(np.einsum("k,j,i->kji", w, w, w).reshape(-1)).cuda()
+    tot = torch.einsum("evp,ep->v", R.reshape(s2.E, 5, -1), J * wq)
+    scale = torch.einsum("evp,ep->v", R.reshape(s2.E, 5, -1).abs(), J * wq)
+    assert bool((tot.abs() <= 1e-6 * scale).all()), (tot, scale)
+
+
 def test_mortar_rejections(dg):
     mesh = refined_box_mesh(2, _refine(2, [0]))
-    for kw in (dict(precision=1), dict(nodes=1)):
-        with pytest.raises(dg.DGError):
-            dg.Solver(mesh, 2, **kw)
+    with pytest.raises(dg.DGError):
+        dg.Solver(mesh, 2, nodes=1)
     s = dg.Solver(mesh, 2, mu=0.01)
     U = _cuda(random_state(mesh.n_elems, 2, seed=1))
     with pytest.raises(dg.DGError):
