@@ -375,6 +375,22 @@ static bool build_geometry(Ctx& c, int ngeo, const double* xgeo) {
   return true;
 }
 
+// Mortar interpolation: the Lagrange basis l_j of the node set x at the nodes
+// of each half of [-1, 1], mI[h][a][j] = l_j((x_a + 2h - 1)/2).
+static void mortar_table(Ctx& c, const std::vector<double>& x) {
+  const int n = c.n;
+  c.mI.assign((size_t)2 * n * n, 0.0);
+  for (int k = 0; k < 2; ++k)
+    for (int a = 0; a < n; ++a)
+      for (int j = 0; j < n; ++j) {
+        const double xs = 0.5 * (x[a] + 2.0 * k - 1.0);
+        double l = 1.0;
+        for (int m = 0; m < n; ++m)
+          if (m != j) l *= (xs - x[m]) / (x[j] - x[m]);
+        c.mI[((size_t)k * n + a) * n + j] = l;
+      }
+}
+
 static bool build_faces(Ctx& c, const int* face_nbr) {
   int E = c.E, n = c.n, nn = n * n;
   c.nbr.assign(face_nbr, face_nbr + (size_t)E * 18);
@@ -419,17 +435,7 @@ static bool build_faces(Ctx& c, const int* face_nbr) {
         int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1];
         c.face_id[e * 6 + f] = c.face_id[e2 * 6 + f2];
       }
-  // mortar interpolation: l_j at the LGL nodes of each half of [-1, 1]
-  c.mI.assign((size_t)2 * n * n, 0.0);
-  for (int k = 0; k < 2; ++k)
-    for (int a = 0; a < n; ++a)
-      for (int j = 0; j < n; ++j) {
-        const double xs = 0.5 * (c.b.x[a] + 2.0 * k - 1.0);
-        double l = 1.0;
-        for (int m = 0; m < n; ++m)
-          if (m != j) l *= (xs - c.b.x[m]) / (c.b.x[j] - c.b.x[m]);
-        c.mI[((size_t)k * n + a) * n + j] = l;
-      }
+  mortar_table(c, c.b.x);   // LGL; a Gauss-node context replaces it
   c.nfaces = nf;
   c.fn.assign((size_t)nf * 3 * nn, 0.0);
   c.fsJ.assign((size_t)nf * nn, 0.0);
@@ -652,8 +658,9 @@ static void mms_source(const Params& pr, const double x[3], double t, double out
 // big face are interpolated to the nodes of each quadrant (numbered (pp, qq)
 // in the big face's directions),
 //   v_k(pp, qq) = sum_ij I_a[pp][i] I_b[qq][j] v(i, j),  I_h[x][j] = l_j((x_x + 2h - 1)/2),
-// and quadrant data go back onto the big face by the projection with the LGL
-// quadrature (exact for the constant mode, so face integrals are kept):
+// and quadrant data go back onto the big face by the projection with the
+// quadrature of the node set (exact for the constant mode, so face integrals
+// are kept; on Gauss nodes, exact to degree 2N+1, it is the L2 projection):
 //   v(i, j) = scale / (w_i w_j) sum_k sum_{pp,qq} w_pp w_qq I_a[pp][i] I_b[qq][j] v_k(pp, qq),
 // scale = 1/4 for point values (the lifting's face average), 1 for fluxes
 // times sJ (a quadrant's surface element is a quarter of the big face's).
@@ -674,7 +681,7 @@ static void mortar_interp(const Ctx& c, const T* big, int k, T* out) {
 template <class T>
 static void mortar_project(const Ctx& c, const T* const quad[4], double scale, T* out) {
   const int n = c.n;
-  const std::vector<double>& w = c.b.w;
+  const std::vector<double>& w = c.nodes == 1 ? c.g.w : c.b.w;   // the node set's quadrature
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < n; ++i) {
       T s = T(0.0);
@@ -1336,6 +1343,32 @@ static void lifting_lg(const Ctx& c, const double* phi, const std::vector<double
   int n = c.n, P = c.P, nn = n * n, N = c.N;
   const std::vector<double>& w = c.g.w;
   const std::vector<double>& D = c.g.D;
+  // mortar face averages at the face points, as on LGL nodes: on each
+  // quadrant (the small side's own point order) and projected onto the big face
+  std::vector<double> star_s((size_t)c.M * 4 * 4 * nn), star_b((size_t)c.M * 4 * nn);
+  for (int m = 0; m < c.M; ++m) {
+    const int* r = &c.mortars[(size_t)m * 14];
+    for (int ph = 0; ph < 4; ++ph) {
+      const double* big = &phif[(((size_t)r[0] * 6 + r[1]) * 4 + ph) * nn];
+      std::vector<double> q[4];
+      const double* qp[4];
+      for (int k = 0; k < 4; ++k) {
+        q[k].resize(nn);
+        mortar_interp(c, big, k, q[k].data());
+        const int es = r[2 + 3 * k], fs = r[3 + 3 * k], fl = r[4 + 3 * k];
+        for (int qq = 0; qq < n; ++qq)
+          for (int pp = 0; pp < n; ++pp) {
+            int p2, q2;
+            flip_map(fl, N, pp, qq, p2, q2);
+            const double st = 0.5 * (phif[(((size_t)es * 6 + fs) * 4 + ph) * nn + p2 + n * q2] + q[k][pp + n * qq]);
+            star_s[(((size_t)m * 4 + k) * 4 + ph) * nn + p2 + n * q2] = st;
+            q[k][pp + n * qq] = st;
+          }
+        qp[k] = q[k].data();
+      }
+      mortar_project(c, qp, 0.25, &star_b[((size_t)m * 4 + ph) * nn]);
+    }
+  }
   for (int e = 0; e < c.E; ++e) {
     std::vector<double> acc((size_t)12 * P, 0.0);
     for (int k = 0; k < n; ++k)
@@ -1366,10 +1399,19 @@ static void lifting_lg(const Ctx& c, const double* phi, const std::vector<double
           flip_map(fl, N, p, q, p2, q2);
           double nsJ[3];
           outward_nsJ(c, e, f, p, q, nsJ);
+          const int mo = e2 < 0 ? -1 - e2 : -1;
+          const bool mbig = mo >= 0 && mortar_big(c, mo, e, f);
           for (int ph = 0; ph < 4; ++ph) {
-            double mine = phif[(((size_t)e * 6 + f) * 4 + ph) * nn + p + n * q];
-            double other = phif[(((size_t)e2 * 6 + f2) * 4 + ph) * nn + p2 + n * q2];
-            double star = 0.5 * (mine + other);
+            double star;
+            if (mo < 0) {
+              double mine = phif[(((size_t)e * 6 + f) * 4 + ph) * nn + p + n * q];
+              double other = phif[(((size_t)e2 * 6 + f2) * 4 + ph) * nn + p2 + n * q2];
+              star = 0.5 * (mine + other);
+            } else if (mbig) {
+              star = star_b[((size_t)mo * 4 + ph) * nn + p + n * q];
+            } else {
+              star = star_s[(((size_t)mo * 4 + f2) * 4 + ph) * nn + p + n * q];
+            }
             for (int i = 0; i < n; ++i) {
               int id = line_node(n, d, i, p, q);
               for (int l = 0; l < 3; ++l) acc[(size_t)(ph * 3 + l) * P + id] += lend[i] / w[i] * star * nsJ[l];
@@ -1429,6 +1471,7 @@ static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double m
       if (!c.master[e * 6 + f]) continue;
       int fid = c.face_id[e * 6 + f];
       int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1], fl = c.nbr[(e * 6 + f) * 3 + 2];
+      if (e2 < 0) continue;   // a mortar side: below
       for (int q = 0; q < n; ++q)
         for (int p = 0; p < n; ++p) {
           int p2, q2;
@@ -1455,6 +1498,57 @@ static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double m
             Fs[((size_t)fid * 5 + v) * nn + p + n * q] = (fa[v] - 0.5 * (fvL[v] + fvR[v])) * sJ;
         }
     }
+  // mortars, as on LGL nodes, from the face values: fluxes on the quadrants
+  // (small side's normal and surface element, big side's face values of the
+  // state and gradients interpolated), the big face's flux their projection
+  for (int m = 0; m < c.M; ++m) {
+    const int* r = &c.mortars[(size_t)m * 14];
+    const int fidB = c.face_id[r[0] * 6 + r[1]];
+    std::vector<double> big((size_t)17 * nn), qi((size_t)17 * nn), Fq((size_t)4 * 5 * nn);
+    for (int ij = 0; ij < nn; ++ij) {
+      for (int v = 0; v < 5; ++v) big[(size_t)v * nn + ij] = Uf[(((size_t)r[0] * 6 + r[1]) * 5 + v) * nn + ij];
+      for (int rr = 0; rr < 12; ++rr) big[(size_t)(5 + rr) * nn + ij] = Gf[(((size_t)r[0] * 6 + r[1]) * 12 + rr) * nn + ij];
+    }
+    for (int k = 0; k < 4; ++k) {
+      const int es = r[2 + 3 * k], fs = r[3 + 3 * k], fl = r[4 + 3 * k];
+      const int fidS = c.face_id[es * 6 + fs];
+      for (int x = 0; x < 17; ++x) mortar_interp(c, &big[(size_t)x * nn], k, &qi[(size_t)x * nn]);
+      for (int qq = 0; qq < n; ++qq)
+        for (int pp = 0; pp < n; ++pp) {
+          int p2, q2;
+          flip_map(fl, N, pp, qq, p2, q2);
+          const int o = p2 + n * q2;
+          double qL[5], qR[5], gL[12], gR[12], nv[3];
+          for (int v = 0; v < 5; ++v) {
+            qL[v] = Uf[(((size_t)es * 6 + fs) * 5 + v) * nn + o];
+            qR[v] = qi[(size_t)v * nn + pp + n * qq];
+          }
+          for (int rr = 0; rr < 12; ++rr) {
+            gL[rr] = Gf[(((size_t)es * 6 + fs) * 12 + rr) * nn + o];
+            gR[rr] = qi[(size_t)(5 + rr) * nn + pp + n * qq];
+          }
+          for (int l = 0; l < 3; ++l) nv[l] = c.fn[((size_t)fidS * 3 + l) * nn + o];
+          const double sJ = c.fsJ[(size_t)fidS * nn + o];
+          Prim<double> L = cons2prim(pr, qL), Rr = cons2prim(pr, qR);
+          double fa[5], fvL[5], fvR[5];
+          if (pr.surf_flux == 1) ec_flux(pr, L, Rr, nv, fa);
+          else if (pr.surf_flux == 2) roe_flux(pr, qL, L, qR, Rr, nv, fa);
+          else llf_flux(pr, qL, L, qR, Rr, nv, fa);
+          visc_flux(pr, L, gL, mu, nv, fvL);
+          visc_flux(pr, Rr, gR, mu, nv, fvR);
+          for (int v = 0; v < 5; ++v) {
+            const double F = (fa[v] - 0.5 * (fvL[v] + fvR[v])) * sJ;
+            Fs[((size_t)fidS * 5 + v) * nn + o] = F;
+            Fq[((size_t)k * 5 + v) * nn + pp + n * qq] = -F;   // out of the big element
+          }
+        }
+    }
+    for (int v = 0; v < 5; ++v) {
+      const double* qp[4] = {&Fq[(size_t)(0 * 5 + v) * nn], &Fq[(size_t)(1 * 5 + v) * nn],
+                             &Fq[(size_t)(2 * 5 + v) * nn], &Fq[(size_t)(3 * 5 + v) * nn]};
+      mortar_project(c, qp, 1.0, &Fs[((size_t)fidB * 5 + v) * nn]);
+    }
+  }
   // FV sub-cell elements (as on LGL nodes; the DG side of a mixed face
   // enters with its interpolated face values)
   const bool use_fv = !c.fv_mask.empty();
@@ -2070,7 +2164,6 @@ void* orc_create(int N, int n_elems, int ngeo, const double* xgeo, const int* fa
   c->M = n_mortars > 0 ? n_mortars : 0;
   if (c->M > 0) {
     c->mortars.assign(mortars, mortars + (size_t)c->M * 14);
-    if (c->nodes != 0) c->err = "mortars are built for LGL nodes";
   }
   if (!c->err.empty() || !build_geometry(*c, ngeo, xgeo) || !build_faces(*c, face_nbr)) {
     if (errbuf && errlen > 0) std::snprintf(errbuf, errlen, "%s", c->err.c_str());
@@ -2079,6 +2172,7 @@ void* orc_create(int N, int n_elems, int ngeo, const double* xgeo, const int* fa
   }
   if (c->nodes == 1) {
     c->g = make_gauss_basis(N, c->b);
+    mortar_table(*c, c->g.x);
     gauss_geometry(*c);
     if (!c->err.empty()) {
       if (errbuf && errlen > 0) std::snprintf(errbuf, errlen, "%s", c->err.c_str());

@@ -53,28 +53,30 @@ def _uniform(o, r=1.2, u=(0.3, -0.2, 0.45), p=0.9):
     return U
 
 
+@pytest.mark.parametrize("nodes", [0, 1])
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
-def test_free_stream_on_a_split_mesh(orc, N):
+def test_free_stream_on_a_split_mesh(orc, N, nodes):
     K = 3
     m = refined_box_mesh(K, _refine(K, [0, 13]), rotate_seed=5)
-    o = orc.Oracle(m, N, mu=0.01)
+    o = orc.Oracle(m, N, mu=0.01, nodes=nodes)
     U = _uniform(o)
     R = o.time_derivative(U)
     # rounding of O(1) fluxes through 1/(w_0 J) of the small elements
     _, Ja, J = o.geometry()
-    x, w, _ = orc.basis(N)
+    x, w = (orc.basis(N) if nodes == 0 else orc.gauss_basis(N))[:2]
     scale = 2.0 / (w[0] * J.min())
     assert np.abs(R).max() < 2e-15 * scale * N ** 3, (np.abs(R).max(), scale)
 
 
-@pytest.mark.parametrize("N,flux", [(1, 0), (2, 0), (3, 1), (4, 2), (3, 0)])
-def test_conservation_on_a_split_mesh(orc, N, flux):
+@pytest.mark.parametrize("N,flux,nodes", [(1, 0, 0), (2, 0, 0), (3, 1, 0), (4, 2, 0), (3, 0, 0),
+                                          (1, 0, 1), (2, 1, 1), (3, 0, 1), (4, 2, 1)])
+def test_conservation_on_a_split_mesh(orc, N, flux, nodes):
     K = 3
     m = refined_box_mesh(K, _refine(K, [0, 13, 20]), rotate_seed=9)
-    o = orc.Oracle(m, N, mu=0.02, surf_flux=flux)
-    U = random_state(m.n_elems, N, seed=4)
+    o = orc.Oracle(m, N, mu=0.02, surf_flux=flux, nodes=nodes)
+    U = random_state(m.n_elems, N, seed=4, **(dict(rho=(0.95, 1.05), vel=0.2, p=(0.95, 1.05)) if nodes else {}))
     _, _, J = o.geometry()
-    _, w, _ = orc.basis(N)
+    w = (orc.basis(N) if nodes == 0 else orc.gauss_basis(N))[1]
     wq = np.einsum("k,j,i->kji", w, w, w).reshape(-1)
     R = o.time_derivative(U).reshape(o.E, 5, -1)
     tot = np.einsum("evp,ep->v", R, J * wq)
@@ -82,16 +84,17 @@ def test_conservation_on_a_split_mesh(orc, N, flux):
     assert (np.abs(tot) < 1e-13 * scale).all(), (tot, scale)
 
 
-@pytest.mark.parametrize("N,seed", [(2, None), (3, 11), (4, 12)])
-def test_linear_density_exact_across_mortars(orc, N, seed):
+@pytest.mark.parametrize("N,seed,nodes", [(2, None, 0), (3, 11, 0), (4, 12, 0), (2, None, 1), (3, 11, 1), (4, 12, 1)])
+def test_linear_density_exact_across_mortars(orc, N, seed, nodes):
     """rho = 1 + 0.1 x, constant velocity and pressure, inviscid, central
-    volume flux: R = -(u, u^2, u v, u w, |u|^2 u / 2) d rho/dx exactly at
+    volume flux on LGL nodes (the weak form on Gauss nodes takes the flux at
+    the nodes): R = -(u, u^2, u v, u w, |u|^2 u / 2) d rho/dx exactly at
     every node of the elements clear of the periodic jump at x = +-1; the split
     cells sit in the middle of the box, so every mortar is among them."""
     K = 4
     cells = [1 + 4 * 1 + 16 * 1, 2 + 4 * 2 + 16 * 2, 1 + 4 * 2 + 16 * 3]
     m = refined_box_mesh(K, _refine(K, cells), rotate_seed=seed)
-    o = orc.Oracle(m, N, mu=0.0)
+    o = orc.Oracle(m, N, mu=0.0, nodes=nodes)
     o.set_vol_flux(1)
     X = o.node_coords()
     u = np.array([0.3, 0.1, -0.2])
@@ -125,8 +128,6 @@ def test_tangent_linear_through_mortars(orc):
 
 def test_mortar_rejections(orc):
     m = refined_box_mesh(2, _refine(2, [0]))
-    with pytest.raises(ValueError):
-        orc.Oracle(m, 2, nodes=1)
     o = orc.Oracle(m, 2)
     with pytest.raises(ValueError):
         o.set_fv_mask(np.ones(m.n_elems))
