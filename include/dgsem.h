@@ -91,7 +91,9 @@ enum { DG_IND_RHO = 0, DG_IND_P = 1, DG_IND_RHOP = 2 };   /* quantity of the tro
  *       the small face's own node.  face_nbr[eB][fB] = (-1 - m, 0, 0) and
  *       face_nbr[eS_k][fS_k] = (-1 - m, k, 0).  The quadrants must be the
  *       exact quarters of the big face (affine faces).  n_mortars = 0 and
- *       mortars = NULL for a conforming mesh.
+ *       mortars = NULL for a conforming mesh.  Either node set (the maps use
+ *       its basis and quadrature); the FV sub-cell operator, the adjoint and
+ *       the ensemble need a conforming mesh.
  */
 typedef struct {
   int32_t n_elems;
@@ -127,8 +129,7 @@ typedef struct {
  * metric terms are those of the LGL construction evaluated at the Gauss nodes
  * and face points (Sec. 3.1 leaves this open).  Synchronous.
  * Errors: DG_EINVAL (null/size, unknown option, constants out of range),
- * DG_EUNSUPPORTED (N outside 1..9, Gauss nodes with DG_FP32OP, mortars with
- * Gauss nodes: the mortar path is built for LGL nodes, FP64 or DG_FP32OP), DG_EMESH
+ * DG_EUNSUPPORTED (N outside 1..9, Gauss nodes with DG_FP32OP), DG_EMESH
  * (connectivity out of range or not reciprocal, Jacobian <= 0 at a node),
  * DG_ENOMEM, DG_ECUDA.  On failure *out is NULL. */
 dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out);

@@ -206,8 +206,6 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
       mesh->n_mortars < 0 || (mesh->n_mortars > 0 && !mesh->mortars))
     return fail(nullptr, DG_EINVAL, "dg_init: bad mesh sizes or null arrays");
   const int E = mesh->n_elems, M = mesh->n_mortars;
-  if (M > 0 && prm->nodes != DG_NODES_LGL)
-    return fail(nullptr, DG_EUNSUPPORTED, "dg_init: mortars are built for LGL nodes");
   // mortar table: every side names its mortar back
   for (int m = 0; m < M; ++m) {
     const int* r = mesh->mortars + (size_t)m * 14;
@@ -392,21 +390,27 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_faces, faces.data(), sizeof(FaceInfo) * c->nfaces, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_elem_face, elem_face.data(), sizeof(int) * E * 6, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->d_elem_nbr, elem_nbr.data(), sizeof(int) * E * 6, cudaMemcpyHostToDevice, s);
-  // mortars: the table and the interpolation of the LGL basis to the LGL
-  // nodes of each half of [-1, 1], I[k][a][j] = l_j((x_a + 2k - 1)/2), with w
+  // mortars: the table and the interpolation of the node set's Lagrange
+  // basis to its nodes on each half of [-1, 1], I[k][a][j] = l_j((x_a + 2k - 1)/2),
+  // with the node set's weights w (LGL, or Legendre-Gauss)
   std::vector<double> mI(M > 0 ? 2 * NN + c->n : 0);
   if (M > 0) {
     const int n = c->n;
+    std::vector<double> xs_set = c->x, ws_set = c->w;
+    if (prm->nodes == DG_NODES_LG) {
+      std::vector<double> gtab;
+      gauss_table(c->N, c->x, gtab, &xs_set, &ws_set);
+    }
     for (int k = 0; k < 2; ++k)
       for (int a = 0; a < n; ++a)
         for (int j = 0; j < n; ++j) {
-          const double xs = 0.5 * (c->x[a] + 2.0 * k - 1.0);
+          const double xs = 0.5 * (xs_set[a] + 2.0 * k - 1.0);
           double l = 1.0;
           for (int m = 0; m < n; ++m)
-            if (m != j) l *= (xs - c->x[m]) / (c->x[j] - c->x[m]);
+            if (m != j) l *= (xs - xs_set[m]) / (xs_set[j] - xs_set[m]);
           mI[(size_t)(k * n + a) * n + j] = l;
         }
-    for (int a = 0; a < n; ++a) mI[2 * NN + a] = c->w[a];
+    for (int a = 0; a < n; ++a) mI[2 * NN + a] = ws_set[a];
     if (err == cudaSuccess)
       err = cudaMemcpyAsync(c->d_mortars, mtab.data(), sizeof(int) * mtab.size(), cudaMemcpyHostToDevice, s);
     if (err == cudaSuccess)

@@ -45,7 +45,8 @@ static void legendre_pn(int n, double x, double& p, double& dp) {
 }
 
 // Host table of the Gauss basis of degree N; xl are the LGL nodes of degree N.
-void gauss_table(int N, const std::vector<double>& xl, std::vector<double>& tab, std::vector<double>* gx) {
+void gauss_table(int N, const std::vector<double>& xl, std::vector<double>& tab, std::vector<double>* gx,
+                 std::vector<double>* gw) {
   const int n = N + 1;
   std::vector<double> x(n), w(n), D((size_t)n * n), c(n), lm(n), lp(n);
   for (int k = 0; k < (n + 1) / 2; ++k) {
@@ -91,6 +92,7 @@ void gauss_table(int N, const std::vector<double>& xl, std::vector<double>& tab,
     lp[j] = b;
   }
   if (gx) *gx = x;
+  if (gw) *gw = w;
   tab.assign(GaussTab::size(n), 0.0);
   for (int r = 0; r < n; ++r)
     for (int m = 0; m < n; ++m) tab[GaussTab::Dw(n) + r * n + m] = (w[m] / w[r]) * D[(size_t)m * n + r];
@@ -187,14 +189,14 @@ __device__ __forceinline__ int line_node(int d, int i, int p, int q) {
 // replaced by their Gauss values.
 template <int N>
 __global__ void k_face_geometry_lg(const FaceInfo* __restrict__ faces, const double* __restrict__ metrics,
-                                   const double* __restrict__ tab, double* __restrict__ facegeo, int F) {
+                                   const double* __restrict__ tab, double* __restrict__ facegeo, int F, int E) {
   constexpr int n = N + 1, P = n * n * n, NN = n * n;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long)F * NN) return;
   const int f = (int)(gid / NN), pq = (int)(gid % NN);
   const int p = pq % n, q = pq / n;
   const FaceInfo fi = faces[f];
-  const int e = dg_idx(fi.master >> 3, F / 3, kSiteGaussFace), lf = fi.master & 7, d = lf >> 1;
+  const int e = dg_idx(fi.master >> 3, E, kSiteGaussFace), lf = fi.master & 7, d = lf >> 1;
   const double sg = (lf & 1) ? 1.0 : -1.0;
   const double* V = tab + GaussTab::V(n);
   double nv[3] = {0.0, 0.0, 0.0};
@@ -352,11 +354,14 @@ constexpr size_t lift_lg_smem() {
 // Weak BR1 lifting (Eq. 3): J g_l,i = sum_faces l_{i_d}(+-1)/w_{i_d} phi* (n_l sJ)
 //   - sum_d sum_m (w_m/w_{i_d}) D_{m i_d} (phi Ja^d_l)_m, phi* the face average;
 // then the face values of g for the face kernel.
-template <int N, int EPB>
+// MORTAR: a face whose neighbour entry is negative is a mortar side, whose
+// neighbour face state is mvirt[-1 - entry][5][NN] in its own point order.
+template <int N, int EPB, bool MORTAR = false>
 __global__ void __launch_bounds__(Shape<N, EPB>::THREADS)
 k_lift_lg(const double* __restrict__ U, const double* __restrict__ Uf, const double* __restrict__ metrics,
           const double* __restrict__ facegeo, const int* __restrict__ elem_face, const int* __restrict__ elem_nbr,
-          const double* __restrict__ tab, double* __restrict__ grad, double* __restrict__ gf, int E, Gas g) {
+          const double* __restrict__ tab, double* __restrict__ grad, double* __restrict__ gf, int E, int F, Gas g,
+          const double* __restrict__ mvirt, int n_mortar) {
   using S = Shape<N, EPB>;
   constexpr int n = S::n, P = S::P, NN = n * n, PER = 16 * P + 72 * NN;
   extern __shared__ double sm[];
@@ -381,13 +386,18 @@ k_lift_lg(const double* __restrict__ U, const double* __restrict__ Uf, const dou
     for (int o = id; o < 6 * NN; o += P) {
       const int f = o / NN, pq = o - f * NN, p = pq % n, q = pq / n;
       const int code = elem_face[e * 6 + f], nb = elem_nbr[e * 6 + f];
-      const int e2 = dg_idx(nb >> 3, E, kSiteGaussLift), f2 = nb & 7, fid = dg_idx(code >> 4, 3L * E, kSiteGaussLift);
+      const int fid = dg_idx(code >> 4, F, kSiteGaussLift);
       int p2, q2;
       apply_flip<n>(code & 7, p, q, p2, q2);
       const int pq2 = p2 + n * q2;
       double pm[4], pn[4];
       state_phi(Uf + ((size_t)e * 6 + f) * 5 * NN + pq, NN, g, pm);
-      state_phi(Uf + ((size_t)e2 * 6 + f2) * 5 * NN + pq2, NN, g, pn);
+      if (MORTAR && nb < 0) {
+        state_phi(mvirt + (size_t)dg_idx(-1 - nb, 5L * n_mortar, kSiteMortar) * 5 * NN + pq, NN, g, pn);
+      } else {
+        const int e2 = dg_idx(nb >> 3, E, kSiteGaussLift), f2 = nb & 7;
+        state_phi(Uf + ((size_t)e2 * 6 + f2) * 5 * NN + pq2, NN, g, pn);
+      }
       const bool master = code & 8;
       const double* fg = facegeo + (size_t)fid * 4 * NN + (master ? pq : pq2);
       const double sJ = master ? fg[3 * NN] : -fg[3 * NN];
@@ -470,7 +480,7 @@ k_lift_lg(const double* __restrict__ U, const double* __restrict__ Uf, const dou
 template <int N, bool FVSKIP>
 __global__ void __launch_bounds__(128)
 k_face_lg(const double* __restrict__ Uf, const double* __restrict__ gf, const FaceInfo* __restrict__ faces,
-          const double* __restrict__ facegeo, double* __restrict__ fstar, int F, Gas g,
+          const double* __restrict__ facegeo, double* __restrict__ fstar, int F, int E, Gas g,
           const int* __restrict__ fv_mask) {
   constexpr int n = N + 1, NN = n * n;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -478,8 +488,8 @@ k_face_lg(const double* __restrict__ Uf, const double* __restrict__ gf, const Fa
   const int f = (int)(gid / NN), pq = (int)(gid % NN);
   const int p = pq % n, q = pq / n;
   const FaceInfo fi = faces[f];
-  const int eM = dg_idx(fi.master >> 3, F / 3, kSiteGaussFace), fM = fi.master & 7;
-  const int eS = dg_idx(fi.slave >> 3, F / 3, kSiteGaussFace), fS = fi.slave & 7;
+  const int eM = dg_idx(fi.master >> 3, E, kSiteGaussFace), fM = fi.master & 7;
+  const int eS = dg_idx(fi.slave >> 3, E, kSiteGaussFace), fS = fi.slave & 7;
   if constexpr (FVSKIP) {
     if (fv_mask[eM] || fv_mask[eS]) return;
   }
@@ -573,7 +583,7 @@ k_volume_lg(StageArgs a, const double* __restrict__ metrics, const double* __res
     }
     for (int o = id; o < 30 * NN; o += P) {
       const int f = o / (5 * NN), r = o - f * 5 * NN, v2 = r / NN, pq = r - v2 * NN;
-      const int code = elem_face[e * 6 + f], fid = dg_idx(code >> 4, 3L * E, kSiteGaussVol);
+      const int code = elem_face[e * 6 + f], fid = dg_idx(code >> 4, a.nfaces > 0 ? a.nfaces : 3L * E, kSiteGaussVol);
       double val;
       if (code & 8) {
         val = fstar[((size_t)fid * 5 + v2) * NN + pq];
@@ -648,6 +658,9 @@ static cudaError_t setup_lg_N() {
   cudaError_t e = cudaFuncSetAttribute(k_lift_lg<N, S::EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)lift_lg_smem<N, S::EPB>());
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_lift_lg<N, S::EPB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lift_lg_smem<N, S::EPB>());
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_volume_lg<N, S::EPB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)volume_lg_smem<N, S::EPB>());
   if (e == cudaSuccess)
@@ -668,7 +681,7 @@ static cudaError_t geometry_lg_N(Ctx& c, int* d_bad, cudaStream_t s) {
   constexpr int n = N + 1, P = n * n * n;
   const long tot = (long)c.nfaces * n * n;
   k_face_geometry_lg<N><<<(int)((tot + 127) / 128), 128, 0, s>>>(c.d_faces, c.d_metrics, c.d_lgb, c.d_facegeo,
-                                                                c.nfaces);
+                                                                c.nfaces, c.E);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   k_geometry_to_gauss<N><<<c.E, P, sizeof(double) * 5 * P, s>>>(c.d_X, c.d_metrics, c.d_J, c.d_D, c.d_lgb, d_bad,
@@ -683,27 +696,42 @@ static cudaError_t lift_lg_N(const Ctx& c, const double* U, cudaStream_t s) {
   k_prolong_lg<N, S::EPB><<<blocks, S::THREADS, sizeof(double) * S::EPB * 5 * S::P, s>>>(U, c.d_lgb, c.d_Uf, c.E);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
+  if (c.M > 0) {   // the mortar sides' neighbour face states first
+    err = launch_mortar_lift(c, U, s);
+    if (err != cudaSuccess) return err;
+    k_lift_lg<N, S::EPB, true><<<blocks, S::THREADS, lift_lg_smem<N, S::EPB>(), s>>>(
+        U, c.d_Uf, c.d_metrics, c.d_facegeo, c.d_elem_face, c.d_elem_nbr, c.d_lgb, (double*)c.d_grad, c.d_gf, c.E,
+        c.nfaces, c.gas, c.d_mortar_virt, c.M);
+    return cudaGetLastError();
+  }
   k_lift_lg<N, S::EPB><<<blocks, S::THREADS, lift_lg_smem<N, S::EPB>(), s>>>(
       U, c.d_Uf, c.d_metrics, c.d_facegeo, c.d_elem_face, c.d_elem_nbr, c.d_lgb, (double*)c.d_grad, c.d_gf, c.E,
-      c.gas);
+      c.nfaces, c.gas, nullptr, 0);
   return cudaGetLastError();
 }
 
 template <int N>
 static cudaError_t face_lg_N(const Ctx& c, cudaStream_t s) {
-  const long tot = (long)c.nfaces * (N + 1) * (N + 1);
-  if (c.fv_on)
-    k_face_lg<N, true><<<(int)((tot + 127) / 128), 128, 0, s>>>(c.d_Uf, c.d_gf, c.d_faces, c.d_facegeo,
-                                                               (double*)c.d_fstar, c.nfaces, c.gas, c.d_fv_mask);
-  else
-    k_face_lg<N, false><<<(int)((tot + 127) / 128), 128, 0, s>>>(c.d_Uf, c.d_gf, c.d_faces, c.d_facegeo,
-                                                                (double*)c.d_fstar, c.nfaces, c.gas, nullptr);
-  return cudaGetLastError();
+  // the conforming faces (the mortars' slots follow them)
+  const long tot = (long)c.nfaces_conf * (N + 1) * (N + 1);
+  if (tot > 0) {
+    if (c.fv_on)
+      k_face_lg<N, true><<<(int)((tot + 127) / 128), 128, 0, s>>>(
+          c.d_Uf, c.d_gf, c.d_faces, c.d_facegeo, (double*)c.d_fstar, c.nfaces_conf, c.E, c.gas, c.d_fv_mask);
+    else
+      k_face_lg<N, false><<<(int)((tot + 127) / 128), 128, 0, s>>>(
+          c.d_Uf, c.d_gf, c.d_faces, c.d_facegeo, (double*)c.d_fstar, c.nfaces_conf, c.E, c.gas, nullptr);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && c.M > 0) e = launch_mortar_flux(c, nullptr, s);
+  return e;
 }
 
 template <int N>
-static cudaError_t volume_lg_N(const Ctx& c, const StageArgs& a, cudaStream_t s) {
+static cudaError_t volume_lg_N(const Ctx& c, const StageArgs& a0, cudaStream_t s) {
   using S = Shape<N>;
+  StageArgs a = a0;
+  a.nfaces = c.nfaces;
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
   if (a.list != nullptr)
     k_volume_lg<N, S::EPB, true><<<blocks, S::THREADS, volume_lg_smem<N, S::EPB>(), s>>>(

@@ -198,7 +198,8 @@ cudaError_t launch_volume_lat(const Ctx& c, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_face_lat(const Ctx& c, const double* U, cudaStream_t s);   // LLF surface flux only
 cudaError_t setup_kernels(int N);
 // Gauss-node operator (dg_gauss.cu); gx (may be NULL) receives the Gauss nodes
-void gauss_table(int N, const std::vector<double>& xl, std::vector<double>& tab, std::vector<double>* gx = nullptr);
+void gauss_table(int N, const std::vector<double>& xl, std::vector<double>& tab, std::vector<double>* gx = nullptr,
+                 std::vector<double>* gw = nullptr);
 double gauss_dt_factor(int N, const std::vector<double>& xl, const std::vector<double>& wl,
                        const std::vector<double>& Dl, const std::vector<double>& tab);
 cudaError_t setup_gauss(int N);

@@ -18,6 +18,9 @@
 //   quadrants from the small side's state and gradients and the big side's
 //   interpolated ones, with the small face's geometry, and on the big face
 //   their projection, pointing out of the big element.
+// On Legendre-Gauss nodes (FACE) the same maps act on the face values of the
+// state and of the lifted gradients at the Gauss face points (Uf, gf), and the
+// projection with the Gauss weights is the L2 projection.
 // One block per mortar, a thread per quadrant node.  With the FP32 operator
 // (R = float) the gradients, face geometry and fluxes are FP32 as in the
 // conforming face kernel; the states stay FP64 and the maps run in FP64.
@@ -29,6 +32,21 @@ template <int N>
 struct MortarShape {
   static constexpr int n = N + 1, P = n * n * n, NN = n * n, THREADS = 4 * NN;
 };
+
+// Where the values of side (e, f) at its face point (p, q) start, and the
+// stride between their fields: the volume nodes (LGL, the face points are
+// nodes) or the face values [E][6][NF][NN] (Gauss nodes).
+template <int n, bool FACE, int NF, typename T>
+__device__ __forceinline__ const T* side_ptr(const T* base, int e, int f, int p, int q, int& st) {
+  constexpr int NN = n * n, P = n * n * n;
+  if constexpr (FACE) {
+    st = NN;
+    return base + ((size_t)e * 6 + f) * NF * NN + p + n * q;
+  } else {
+    st = P;
+    return base + (size_t)e * NF * P + face_node<n>(f, p, q);
+  }
+}
 
 // Both kernels work in tensor-product sweeps (one direction at a time) over
 // shared memory.  Tables, from the interpolation I_h[x][j] and the weights w:
@@ -135,7 +153,7 @@ __device__ __forceinline__ void encode_vars(const double ph[4], const Gas& g, do
   o[4 * st] = g.R * ph[3] * g.inv_gm1 + 0.5 * (ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
 }
 
-template <int N>
+template <int N, bool FACE>
 __global__ void __launch_bounds__(MortarShape<N>::THREADS)
 k_mortar_lift(const double* __restrict__ U, const int* __restrict__ mortars, const double* __restrict__ tab,
               double* __restrict__ virt, int E, Gas g) {
@@ -153,7 +171,9 @@ k_mortar_lift(const double* __restrict__ U, const int* __restrict__ mortars, con
   mortar_tables<n>(tab, sI, sIT, sW, sw, t, T);
   if (t < NN) {
     double ph[4];
-    lift_vars(U + (size_t)eB * 5 * P + face_node<n>(fB, t % n, t / n), P, g, ph);
+    int st;
+    const double* q = side_ptr<n, FACE, 5>(U, eB, fB, t % n, t / n, st);
+    lift_vars(q, st, g, ph);
 #pragma unroll
     for (int a = 0; a < 4; ++a) sB[a * NN + t] = ph[a];
   }
@@ -168,7 +188,9 @@ k_mortar_lift(const double* __restrict__ U, const int* __restrict__ mortars, con
     int p2, q2;
     apply_flip<n>(fl, pp, qq, p2, q2);
     double ps[4];
-    lift_vars(U + (size_t)es * 5 * P + face_node<n>(fs, p2, q2), P, g, ps);
+    int st;
+    const double* q = side_ptr<n, FACE, 5>(U, es, fs, p2, q2, st);
+    lift_vars(q, st, g, ps);
 #pragma unroll
     for (int a = 0; a < 4; ++a) sS[(k * 4 + a) * NN + pq] = 0.5 * (ps[a] + ib[a]);
     encode_vars(ib, g, virt + (size_t)(5 * m + k) * 5 * NN + p2 + n * q2, NN);
@@ -187,7 +209,7 @@ k_mortar_lift(const double* __restrict__ U, const int* __restrict__ mortars, con
   }
 }
 
-template <int N, typename R>
+template <int N, typename R, bool FACE>
 __global__ void __launch_bounds__(MortarShape<N>::THREADS)
 k_mortar_flux(const double* __restrict__ U, const R* __restrict__ grad, const R* __restrict__ facegeo,
               const int* __restrict__ mortars, const double* __restrict__ tab, R* __restrict__ fstar, int E, int F,
@@ -205,11 +227,13 @@ k_mortar_flux(const double* __restrict__ U, const R* __restrict__ grad, const R*
   const int eB = dg_idx(r[0], E, kSiteMortar), fB = r[1], slotB = dg_idx(r[2], F, kSiteMortar);
   mortar_tables<n>(tab, sI, sIT, sW, sw, t, T);
   if (t < NN) {
-    const int node = face_node<n>(fB, t % n, t / n);
+    int su, sg;
+    const double* qb = side_ptr<n, FACE, 5>(U, eB, fB, t % n, t / n, su);
+    const R* gb = side_ptr<n, FACE, 12>(grad, eB, fB, t % n, t / n, sg);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sB[v * NN + t] = U[((size_t)eB * 5 + v) * P + node];
+    for (int v = 0; v < 5; ++v) sB[v * NN + t] = qb[v * su];
 #pragma unroll
-    for (int x = 0; x < 12; ++x) sB[(5 + x) * NN + t] = (double)grad[((size_t)eB * 12 + x) * P + node];
+    for (int x = 0; x < 12; ++x) sB[(5 + x) * NN + t] = (double)gb[x * sg];
   }
   __syncthreads();
   mortar_sweep1<n, 17>(sIT, sB, sT, t, T);
@@ -223,14 +247,17 @@ k_mortar_flux(const double* __restrict__ U, const R* __restrict__ grad, const R*
     const int slot = dg_idx(r[6 + 4 * k], F, kSiteMortar);
     int p2, q2;
     apply_flip<n>(fl, pp, qq, p2, q2);
-    const int node = face_node<n>(fs, p2, q2), o = p2 + n * q2;
+    const int o = p2 + n * q2;
+    int su, sg;
+    const double* qs = side_ptr<n, FACE, 5>(U, es, fs, p2, q2, su);
+    const R* gs = side_ptr<n, FACE, 12>(grad, es, fs, p2, q2, sg);
     double dL[5];
     R gL[12], gR[12];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) dL[v] = U[((size_t)es * 5 + v) * P + node];
+    for (int v = 0; v < 5; ++v) dL[v] = qs[v * su];
 #pragma unroll
     for (int x = 0; x < 12; ++x) {
-      gL[x] = grad[((size_t)es * 12 + x) * P + node];
+      gL[x] = gs[x * sg];
       gR[x] = (R)qR[5 + x];
     }
     const R* fg = facegeo + (size_t)slot * 4 * NN + o;
@@ -253,21 +280,27 @@ k_mortar_flux(const double* __restrict__ U, const R* __restrict__ grad, const R*
 
 template <int N>
 static cudaError_t mortar_lift_N(const Ctx& c, const double* U, cudaStream_t s) {
-  k_mortar_lift<N><<<c.M, MortarShape<N>::THREADS, 0, s>>>(U, c.d_mortars, c.d_mortar_tab, c.d_mortar_virt, c.E,
-                                                           c.gas);
+  if (c.prm.nodes == DG_NODES_LG)
+    k_mortar_lift<N, true><<<c.M, MortarShape<N>::THREADS, 0, s>>>(c.d_Uf, c.d_mortars, c.d_mortar_tab,
+                                                                   c.d_mortar_virt, c.E, c.gas);
+  else
+    k_mortar_lift<N, false><<<c.M, MortarShape<N>::THREADS, 0, s>>>(U, c.d_mortars, c.d_mortar_tab,
+                                                                    c.d_mortar_virt, c.E, c.gas);
   return cudaGetLastError();
 }
 
 template <int N>
 static cudaError_t mortar_flux_N(const Ctx& c, const double* U, cudaStream_t s) {
-  if (c.prm.precision == DG_FP32OP)
-    k_mortar_flux<N, float><<<c.M, MortarShape<N>::THREADS, 0, s>>>(
-        U, (const float*)c.d_grad, c.d_facegeo_f, c.d_mortars, c.d_mortar_tab, (float*)c.d_fstar, c.E, c.nfaces,
-        c.gas);
+  constexpr int T = MortarShape<N>::THREADS;
+  if (c.prm.nodes == DG_NODES_LG)   // FP64 only: the face values of the state and gradients
+    k_mortar_flux<N, double, true><<<c.M, T, 0, s>>>(c.d_Uf, c.d_gf, c.d_facegeo, c.d_mortars, c.d_mortar_tab,
+                                                     (double*)c.d_fstar, c.E, c.nfaces, c.gas);
+  else if (c.prm.precision == DG_FP32OP)
+    k_mortar_flux<N, float, false><<<c.M, T, 0, s>>>(U, (const float*)c.d_grad, c.d_facegeo_f, c.d_mortars,
+                                                     c.d_mortar_tab, (float*)c.d_fstar, c.E, c.nfaces, c.gas);
   else
-    k_mortar_flux<N, double><<<c.M, MortarShape<N>::THREADS, 0, s>>>(
-        U, (const double*)c.d_grad, c.d_facegeo, c.d_mortars, c.d_mortar_tab, (double*)c.d_fstar, c.E, c.nfaces,
-        c.gas);
+    k_mortar_flux<N, double, false><<<c.M, T, 0, s>>>(U, (const double*)c.d_grad, c.d_facegeo, c.d_mortars,
+                                                      c.d_mortar_tab, (double*)c.d_fstar, c.E, c.nfaces, c.gas);
   return cudaGetLastError();
 }
 

@@ -64,6 +64,13 @@ G = torch.empty_like(Ud)
 s.rk_step(Ud, G, 0.0, 1e-3, 3)
 Uo = o.rk_steps(U, 0.0, 1e-3, 3)
 out["mortar"] = dict(err_r=err_r, err_rk=float(np.abs(Ud.cpu().numpy() - Uo).max() / np.abs(Uo).max()), finite=True)
+# the same mesh on Gauss nodes (mortar maps on the face values)
+Ug = random_state(mesh.n_elems, 3, seed=13, rho=(0.95, 1.05), vel=0.2, p=(0.95, 1.05))
+og = oracle.Oracle(mesh, 3, mu=0.02, nodes=1)
+sg = dg.Solver(mesh, 3, mu=0.02, nodes=dg.NODES_LG)
+Rgo = og.time_derivative(Ug)
+out["mortar_gauss"] = dict(err_r=float(np.abs(sg.time_derivative(torch.from_numpy(Ug).cuda()).cpu().numpy() - Rgo).max()
+                                       / np.abs(Rgo).max()), err_rk=0.0, finite=True)
 prm = tgv_params(Ma=0.2, Re=800.0)
 runs = []
 for dims, N in (((1, 1, 1), 3), ((2, 1, 1), 3), ((1, 1, 2), 2)):
@@ -99,7 +106,7 @@ def test_checked_build_on_one_and_two_element_meshes():
                        timeout=1500)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
     res = json.loads(r.stdout.strip().splitlines()[-1])
-    for name in ("one", "two", "two_rot", "mortar"):
+    for name in ("one", "two", "two_rot", "mortar", "mortar_gauss"):
         assert res[name]["err_r"] < 1e-12, res
         assert res[name]["err_rk"] < 1e-10, res
         assert res[name]["finite"], res

@@ -122,10 +122,60 @@ def test_mortar_fp32_mms_steps_and_conservation(orc, dg):
     assert bool((tot.abs() <= 1e-6 * scale).all()), (tot, scale)
 
 
+_GAUSS_STATE = dict(rho=(0.95, 1.05), vel=0.2, p=(0.95, 1.05))   # face values extrapolated from the nodes
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("flux", [0, 1, 2])
+def test_mortar_time_derivative_parity_gauss_nodes(orc, dg, N, flux):
+    K = 3
+    mesh = refined_box_mesh(K, _refine(K, [0, 13]), rotate_seed=140 + N)
+    kw = dict(mu=0.02, surf_flux=flux, nodes=1)
+    o, s = orc.Oracle(mesh, N, **kw), dg.Solver(mesh, N, **kw)
+    U = random_state(mesh.n_elems, N, seed=160 + N, **_GAUSS_STATE)
+    err = _rel_err_per_var(s.time_derivative(_cuda(U)).cpu().numpy(), o.time_derivative(U))
+    assert (err < 1e-12).all(), err
+
+
+@pytest.mark.parametrize("N", [3, 6])
+def test_mortar_mms_rk_parity_gauss_nodes(orc, dg, N):
+    prm = mms_params()
+    K = 3
+    mesh = refined_box_mesh(K, _refine(K, [4, 13, 22]), rotate_seed=170 + N)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], source=1, nodes=1)
+    o, s = orc.Oracle(mesh, N, **kw), dg.Solver(mesh, N, **kw)
+    U0 = o.initial_state("mms", 0.0)
+    ref = o.rk_steps(U0, 0.0, 1e-3, 10)
+    Ud = _cuda(U0)
+    s.rk_step(Ud, torch.empty_like(Ud), 0.0, 1e-3, 10)
+    assert np.abs(Ud.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-10
+
+
+def test_mortar_free_stream_and_conservation_gauss_nodes(orc, dg):
+    N, K = 4, 4
+    mesh = refined_box_mesh(K, _refine(K, [0, 21, 42, 63]), rotate_seed=8)
+    s = dg.Solver(mesh, N, mu=0.01, nodes=1)
+    U = np.zeros(s.shape)
+    r, u, p = 1.2, np.array([0.3, -0.2, 0.45]), 0.9
+    U[:, 0] = r
+    U[:, 1:4] = (r * u)[None, :, None, None, None]
+    U[:, 4] = p / 0.4 + 0.5 * r * u @ u
+    R = s.time_derivative(_cuda(U))
+    _, J = s.geometry()
+    w = orc.gauss_basis(N)[1]
+    assert float(R.abs().max()) < 2e-15 * 2.0 / (w[0] * float(J.min())) * N ** 3
+    U = _cuda(random_state(mesh.n_elems, N, seed=9, **_GAUSS_STATE))
+    R = s.time_derivative(U)
+    wq = torch.from_numpy(np.einsum("k,j,i->kji", w, w, w).reshape(-1)).cuda()
+    tot = torch.einsum("evp,ep->v", R.reshape(s.E, 5, -1), J * wq)
+    scale = torch.einsum("evp,ep->v", R.reshape(s.E, 5, -1).abs(), J * wq)
+    assert bool((tot.abs() <= 1e-13 * scale).all()), (tot, scale)
+
+
 def test_mortar_rejections(dg):
     mesh = refined_box_mesh(2, _refine(2, [0]))
     with pytest.raises(dg.DGError):
-        dg.Solver(mesh, 2, nodes=1)
+        dg.Solver(mesh, 2, nodes=1, precision=dg.FP32OP)
     s = dg.Solver(mesh, 2, mu=0.01)
     U = _cuda(random_state(mesh.n_elems, 2, seed=1))
     with pytest.raises(dg.DGError):
