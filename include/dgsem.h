@@ -329,13 +329,14 @@ typedef struct dg_ensemble dg_ensemble;
 /* The members stay owned by the caller and must outlive the ensemble.
  * DG_EINVAL if a member is NULL, appears twice (its work buffers would be
  * shared by two members) or is on another device or precision;
- * DG_EUNSUPPORTED for a member on Gauss nodes, with RK4-14 or on a mesh with
- * mortars (the ensemble
- * kernels are the LGL split-form ones, its steps LSERK4-5). */
+ * DG_EUNSUPPORTED for a member on Gauss nodes, on a mesh with mortars (the
+ * ensemble kernels are the LGL split-form ones for conforming meshes) or
+ * with another time scheme than the first member's (the steps of all
+ * members follow one scheme, LSERK4-5 or RK4-14). */
 dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune_cache_path, dg_ensemble** out);
 dg_status dg_ensemble_destroy(dg_ensemble* ens);
 
-/* nsteps LSERK4-5 steps of every member r: state dU[r] with register dG[r]
+/* nsteps steps of the members' time scheme for every member r: state dU[r] with register dG[r]
  * (device arrays of the member's dg_state_len), from time t[r] with step
  * dt[r] (host arrays of n doubles).  Identical per member to dg_rk_step.
  * DG_EINVAL if a pointer is NULL or the 2n arrays are not all distinct;

@@ -219,6 +219,7 @@ struct dg_ensemble {
   std::vector<Ctx*> members;
   int device = 0;
   int precision = DG_FP64;
+  RkScheme rk = rk_scheme(DG_RK45);   // the members' common time scheme
   std::vector<Group> groups;
   std::string cache_path;
   std::string gpu_name;
@@ -306,7 +307,7 @@ static cudaError_t one_member_stage(dg_ensemble* e, int r, int k, const double* 
   cudaError_t err;
   if ((err = launch_lift(c, U, s, false)) != cudaSuccess) return err;
   if ((err = launch_face(c, U, s, false)) != cudaSuccess) return err;
-  StageArgs a{U, U, e->cur_G[r], nullptr, e->clocks + 2 * r, kRkC[k], A[k], B[k], 1};
+  StageArgs a{U, U, e->cur_G[r], nullptr, e->clocks + 2 * r, e->rk.C[k], A[k], B[k], 1};
   return launch_volume(c, a, s, false);
 }
 
@@ -321,12 +322,12 @@ static cudaError_t member_stage(dg_ensemble* e, const Group& g, int k, const dou
 static cudaError_t enqueue_group(dg_ensemble* e, const Group& g, int k, const double* A, const double* B,
                                  cudaStream_t s) {
   if (g.plan.epb_choice == 2) return member_stage(e, g, k, A, B, s);
-  return e->precision == DG_FP32OP ? dispatch_stage<float>(g, k, A, B, kRkC, s)
-                                   : dispatch_stage<double>(g, k, A, B, kRkC, s);
+  return e->precision == DG_FP32OP ? dispatch_stage<float>(g, k, A, B, e->rk.C, s)
+                                   : dispatch_stage<double>(g, k, A, B, e->rk.C, s);
 }
 
 static cudaError_t enqueue_stage(dg_ensemble* e, const Group& g, int k, cudaStream_t s) {
-  return enqueue_group(e, g, k, kRkA, kRkB, s);
+  return enqueue_group(e, g, k, e->rk.A, e->rk.B, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -334,17 +335,17 @@ static cudaError_t enqueue_stage(dg_ensemble* e, const Group& g, int k, cudaStre
 // candidate and the lifting / face kernels for each grid, on the members' own
 // data, with B = 0 so the state is left untouched (the register is zeroed at
 // the start of every step anyway).
-static const double kZero5[5] = {0, 0, 0, 0, 0};
+static const double kZero14[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 
 static float time_stage(dg_ensemble* e, const Group& g, cudaStream_t s, int reps, int which) {
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  const double* Bz = kZero5;
+  const double* Bz = kZero14;
   float best = 1e30f;
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(a, s);
-    cudaError_t err = enqueue_group(e, g, 0, kRkA, Bz, s);
+    cudaError_t err = enqueue_group(e, g, 0, e->rk.A, Bz, s);
     cudaEventRecord(b, s);
     cudaEventSynchronize(b);
     float ms = 0.f;
@@ -491,6 +492,7 @@ static dg_status ensemble_create_impl(dg_ctx* const* members, int32_t n, const c
   if (!c0) return drop(DG_EINVAL);
   e->device = c0->device;
   e->precision = c0->prm.precision;
+  e->rk = rk_scheme(c0->prm.rk_scheme);
   e->cache_path = tune_cache_path ? tune_cache_path : "";
   std::set<const Ctx*> seen;
   for (int r = 0; r < n; ++r) {
@@ -498,8 +500,9 @@ static dg_status ensemble_create_impl(dg_ctx* const* members, int32_t n, const c
     // a context twice would have two members share its work buffers
     if (!c || c->device != e->device || c->prm.precision != e->precision || !seen.insert(c).second)
       return drop(DG_EINVAL);
-    if (c->prm.nodes != DG_NODES_LGL || c->prm.rk_scheme != DG_RK45 || c->M > 0)   // LGL split form, LSERK4-5,
-      return drop(DG_EUNSUPPORTED);                                                  // conforming meshes
+    // LGL split form, one time scheme for all members, conforming meshes
+    if (c->prm.nodes != DG_NODES_LGL || c->prm.rk_scheme != c0->prm.rk_scheme || c->M > 0)
+      return drop(DG_EUNSUPPORTED);
     e->members.push_back(c);
   }
   if (cudaSetDevice(e->device) != cudaSuccess) return drop(DG_ECUDA);
@@ -686,8 +689,8 @@ dg_status dg_ensemble_step(dg_ensemble* e, double* const* dU, double* const* dG,
             if (err != cudaSuccess || (u.r >= 0 && r != u.r)) continue;
             err = cudaMemsetAsync(e->cur_G[r], 0, sizeof(double) * (size_t)e->members[r]->E * e->members[r]->P * 5, bs);
           }
-          for (int k = 0; k < 5 && err == cudaSuccess; ++k)
-            err = u.r >= 0 ? one_member_stage(e, u.r, k, kRkA, kRkB, bs) : enqueue_stage(e, g, k, bs);
+          for (int k = 0; k < e->rk.stages && err == cudaSuccess; ++k)
+            err = u.r >= 0 ? one_member_stage(e, u.r, k, e->rk.A, e->rk.B, bs) : enqueue_stage(e, g, k, bs);
         }
         cudaEvent_t join;
         if (err == cudaSuccess && (err = event(&join)) == cudaSuccess && (err = cudaEventRecord(join, bs)) == cudaSuccess)

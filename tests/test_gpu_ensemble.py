@@ -33,14 +33,14 @@ def _make(dg, spec, precision):
     return s, U, dt
 
 
-@pytest.mark.parametrize("choice,grid", [(0, 3), (1, 5)])
-def test_ensemble_tile_tables_vs_oracle(orc, dg, tmp_path, choice, grid):
+@pytest.mark.parametrize("choice,grid,rk", [(0, 3, 0), (1, 5, 0), (0, 3, 1)])
+def test_ensemble_tile_tables_vs_oracle(orc, dg, tmp_path, choice, grid, rk):
     """FP64 members of mixed N (1, 2, 3, 5, 7) on small meshes, advanced three
     steps by the persistent tile-table kernels -- forced through the tuning
     cache: the default (choice 0) or doubled (choice 1) element tile and a
     grid of a few blocks, so that every block walks many tiles of several
-    members -- against the oracle's LSERK4-5 steps of each member:
-    max |U - U_oracle| / max |U_oracle| <= 1e-10."""
+    members -- against the oracle's steps of each member (LSERK4-5, or RK4-14
+    for all members): max |U - U_oracle| / max |U_oracle| <= 1e-10."""
     gpu = torch.cuda.get_device_name()
     Ns = sorted({m["N"] for m in MEMBERS})
     (tmp_path / "tune.txt").write_text("".join("%s|N=%d|fp64\t%d\t%d\t%d\t%d\n" % (gpu, N, choice, grid, grid, grid)
@@ -50,9 +50,9 @@ def test_ensemble_tile_tables_vs_oracle(orc, dg, tmp_path, choice, grid):
         prm = tgv_params(Ma=m["Ma"], Re=m["Re"])
         mesh = box_mesh(m["K"], 1, lo=0.0, hi=2 * math.pi, rotate_seed=m["K"] + m["N"])
         kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"])
-        o = orc.Oracle(mesh, m["N"], **kw)
+        o = orc.Oracle(mesh, m["N"], rk=rk, **kw)
         U0 = o.initial_state("tgv", prm["p0"])
-        s = dg.Solver(mesh, m["N"], **kw)
+        s = dg.Solver(mesh, m["N"], rk_scheme=rk, **kw)
         dt = s.max_dt(torch.from_numpy(U0).cuda(), cfl=0.9, dfl=0.9)
         runs.append((s, dt))
         orcs.append(o)
@@ -167,3 +167,15 @@ def test_repeated_members_and_states_are_rejected(dg):
     ens.close()
     for r in runs:
         r[0].close()
+
+
+def test_mixed_time_schemes_are_rejected(dg):
+    m = MEMBERS[0]
+    prm = tgv_params(Ma=m["Ma"], Re=m["Re"])
+    mesh = box_mesh(m["K"], 1, lo=0.0, hi=2 * math.pi)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"])
+    a = dg.Solver(mesh, m["N"], rk_scheme=dg.RK45, **kw)
+    b = dg.Solver(mesh, m["N"], rk_scheme=dg.RK414, **kw)
+    with pytest.raises(dg.DGError):
+        dg.Ensemble([a, b])
+    dg.Ensemble([b]).close()      # one scheme, RK4-14: accepted
