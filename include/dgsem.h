@@ -92,8 +92,8 @@ enum { DG_IND_RHO = 0, DG_IND_P = 1, DG_IND_RHOP = 2 };   /* quantity of the tro
  *       face_nbr[eS_k][fS_k] = (-1 - m, k, 0).  The quadrants must be the
  *       exact quarters of the big face (affine faces).  n_mortars = 0 and
  *       mortars = NULL for a conforming mesh.  Either node set (the maps use
- *       its basis and quadrature); the FV sub-cell operator, the adjoint and
- *       the ensemble need a conforming mesh.
+ *       its basis and quadrature); the FV sub-cell operator and the adjoint
+ *       need a conforming mesh.
  */
 typedef struct {
   int32_t n_elems;
@@ -329,18 +329,22 @@ typedef struct dg_ensemble dg_ensemble;
 /* The members stay owned by the caller and must outlive the ensemble.
  * DG_EINVAL if a member is NULL, appears twice (its work buffers would be
  * shared by two members) or is on another device or precision;
- * DG_EUNSUPPORTED for a member on Gauss nodes, on a mesh with mortars (the
- * ensemble kernels are the LGL split-form ones for conforming meshes) or
- * with another time scheme than the first member's (the steps of all
- * members follow one scheme, LSERK4-5 or RK4-14). */
+ * DG_EUNSUPPORTED for a member with another time scheme than the first
+ * member's (the steps of all members follow one scheme, LSERK4-5 or RK4-14).
+ * Members on LGL nodes with a conforming mesh and no FV elements run by the
+ * tile-table kernels; members on Gauss nodes, on a mesh with mortars or with
+ * FV elements (set before the ensemble is created) run as single-member
+ * units of the same graph with their own stage kernels. */
 dg_status dg_ensemble_create(dg_ctx* const* members, int32_t n, const char* tune_cache_path, dg_ensemble** out);
 dg_status dg_ensemble_destroy(dg_ensemble* ens);
 
 /* nsteps steps of the members' time scheme for every member r: state dU[r] with register dG[r]
  * (device arrays of the member's dg_state_len), from time t[r] with step
- * dt[r] (host arrays of n doubles).  Identical per member to dg_rk_step.
+ * dt[r] (host arrays of n doubles).  The same steps per member as dg_rk_step
+ * (the ensemble does not use the latency kernels of small meshes).
  * DG_EINVAL if a pointer is NULL or the 2n arrays are not all distinct;
- * DG_EUNSUPPORTED while a member has FV sub-cell elements (dg_set_fv_mask).
+ * DG_EUNSUPPORTED while a member run by the tile-table kernels has FV
+ * sub-cell elements (set after the ensemble was created).
  * Waits for earlier work on `stream`, then enqueues one graph launch. */
 dg_status dg_ensemble_step(dg_ensemble* ens, double* const* dU, double* const* dG, const double* t,
                            const double* dt, int32_t nsteps, dg_stream stream);

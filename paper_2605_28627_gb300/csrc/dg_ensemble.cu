@@ -111,6 +111,10 @@ struct Epb2 {   // the doubled tile, if it still fits a block (<= 1024 threads, 
 
 struct Group {
   int N = 0;
+  // members the tile-table kernels (LGL split form, conforming mesh, no FV
+  // elements) do not cover: Gauss nodes, mortars or FV elements at creation;
+  // they run as single-member units with their own stage kernels
+  bool single_only = false;
   std::vector<int> members;            // indices into the ensemble
   void* d_mem = nullptr;               // MemberDev<R>[members]
   int2* d_elem_tiles[2] = {nullptr, nullptr};   // per EPB choice
@@ -234,6 +238,7 @@ struct dg_ensemble {
   std::vector<double*> cur_U, cur_G;
   cudaGraphExec_t graph = nullptr;
   int graph_nsteps = 0;
+  std::vector<int> graph_fv;      // each member's FV mode when the graph was captured
   std::vector<cudaStream_t> branch;   // side streams of the captured graph's parallel branches
   std::string err;
   std::string plan_json;
@@ -276,6 +281,7 @@ static void fill_member(MemberDev<R>& m, Ctx* c, double* U, double* G, double* c
 // Upload the member tables of every group for the given state/register pointers.
 static dg_status upload_members(dg_ensemble* e) {
   for (Group& g : e->groups) {
+    if (g.single_only) continue;   // no member table
     if (e->precision == DG_FP32OP) {
       std::vector<MemberDev<float>> h(g.members.size());
       for (size_t a = 0; a < g.members.size(); ++a) {
@@ -305,6 +311,7 @@ static cudaError_t one_member_stage(dg_ensemble* e, int r, int k, const double* 
   const Ctx& c = *e->members[r];
   double* U = e->cur_U[r];
   cudaError_t err;
+  if ((err = launch_fv_switch(c, U, s)) != cudaSuccess) return err;   // automatic DG/FV switching, if set
   if ((err = launch_lift(c, U, s, false)) != cudaSuccess) return err;
   if ((err = launch_face(c, U, s, false)) != cudaSuccess) return err;
   StageArgs a{U, U, e->cur_G[r], nullptr, e->clocks + 2 * r, e->rk.C[k], A[k], B[k], 1};
@@ -408,6 +415,7 @@ static dg_status autotune(dg_ensemble* e, cudaStream_t s) {
   bool dirty = false;
   const int sms = e->sms;
   for (Group& g : e->groups) {
+    if (g.single_only) continue;   // nothing to tune: per-member launches
     const std::string key = cache_key(e, g.N);
     auto it = cache.find(key);
     if (it != cache.end()) {
@@ -460,7 +468,9 @@ static dg_status autotune(dg_ensemble* e, cudaStream_t s) {
     std::snprintf(buf, sizeof buf,
                   "%s{\"N\": %d, \"members\": %zu, \"mode\": \"%s\", \"elements_per_block\": %d, \"volume_grid\": %d, "
                   "\"lift_grid\": %d, \"face_grid\": %d, \"element_tiles\": %d, \"face_tiles\": %d, \"cached\": %s}",
-                  a ? ", " : "", g.N, g.members.size(), g.plan.epb_choice == 2 ? "per-member launches" : "tile table",
+                  a ? ", " : "", g.N, g.members.size(),
+                  g.single_only ? "per-member launches (Gauss nodes, mortars or FV elements)"
+                                : (g.plan.epb_choice == 2 ? "per-member launches" : "tile table"),
                   g.plan.epb_choice == 2 ? 0 : epb_of(g.N, g.plan.epb_choice, e->precision), g.plan.vol_grid,
                   g.plan.lift_grid, g.plan.face_grid, g.n_elem_tiles[g.plan.epb_choice == 1 ? 1 : 0], g.n_face_tiles,
                   g.plan.from_cache ? "true" : "false");
@@ -500,8 +510,7 @@ static dg_status ensemble_create_impl(dg_ctx* const* members, int32_t n, const c
     // a context twice would have two members share its work buffers
     if (!c || c->device != e->device || c->prm.precision != e->precision || !seen.insert(c).second)
       return drop(DG_EINVAL);
-    // LGL split form, one time scheme for all members, conforming meshes
-    if (c->prm.nodes != DG_NODES_LGL || c->prm.rk_scheme != c0->prm.rk_scheme || c->M > 0)
+    if (c->prm.rk_scheme != c0->prm.rk_scheme)   // one time scheme for all members
       return drop(DG_EUNSUPPORTED);
     e->members.push_back(c);
   }
@@ -510,8 +519,22 @@ static dg_status ensemble_create_impl(dg_ctx* const* members, int32_t n, const c
   if (cudaGetDeviceProperties(&prop, e->device) != cudaSuccess) return drop(DG_ECUDA);
   e->gpu_name = prop.name;
   e->sms = prop.multiProcessorCount;
-  std::map<int, std::vector<int>> byN;
-  for (int r = 0; r < n; ++r) byN[e->members[r]->N].push_back(r);
+  // the members of the tile-table kernels by N; the others by N as single-member units
+  std::map<int, std::vector<int>> byN, singles;
+  for (int r = 0; r < n; ++r) {
+    const Ctx* c = e->members[r];
+    if (c->prm.nodes == DG_NODES_LGL && c->M == 0 && !c->fv_on) byN[c->N].push_back(r);
+    else singles[c->N].push_back(r);
+  }
+  for (auto& kv : singles) {
+    e->groups.emplace_back();
+    Group& g = e->groups.back();
+    g.N = kv.first;
+    g.members = kv.second;
+    g.single_only = true;
+    g.plan.epb_choice = 2;
+    g.plan.tuned = true;
+  }
   for (auto& kv : byN) {
     e->groups.emplace_back();   // owned by e from here on, so bail() frees what it holds
     Group& g = e->groups.back();
@@ -600,9 +623,11 @@ dg_status dg_ensemble_step(dg_ensemble* e, double* const* dU, double* const* dG,
   if (!e || !dU || !dG || !t || !dt || nsteps < 0) return ens_fail(e, DG_EINVAL, "dg_ensemble_step: bad argument");
   if (nsteps == 0) return DG_OK;
   const int n = (int)e->members.size();
-  for (int r = 0; r < n; ++r)
-    if (e->members[r]->fv_on)
-      return ens_fail(e, DG_EUNSUPPORTED, "dg_ensemble_step: a member has FV sub-cell elements (not in the ensemble)");
+  for (const Group& g : e->groups)
+    for (int r : g.members)
+      if (!g.single_only && e->members[r]->fv_on)
+        return ens_fail(e, DG_EUNSUPPORTED,
+                        "dg_ensemble_step: a member got FV sub-cell elements after the ensemble was created");
   cudaStream_t s = (cudaStream_t)stream;
   ENS_CUDA(cudaSetDevice(e->device), e, "cudaSetDevice");
   bool changed = false;
@@ -625,8 +650,12 @@ dg_status dg_ensemble_step(dg_ensemble* e, double* const* dU, double* const* dG,
   ENS_CUDA(cudaMemcpyAsync(e->d_tdt, e->h_tdt, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, s), e, "clock copy");
   k_ens_set_clocks<<<(n + 127) / 128, 128, 0, s>>>(e->d_clocks, e->d_tdt, n);
   ENS_CUDA(cudaGetLastError(), e, "clock kernel");
-  bool need_tune = false;
+  bool need_tune = e->plan_json.empty();
   for (const Group& g : e->groups) need_tune |= !g.plan.tuned;
+  // a member's FV mode changes its own launch sequence: capture again
+  std::vector<int> fv_now(n);
+  for (int r = 0; r < n; ++r) fv_now[r] = (e->members[r]->fv_on ? 1 : 0) + (e->members[r]->fv_switch ? 2 : 0);
+  if (e->graph && fv_now != e->graph_fv) { cudaGraphExecDestroy(e->graph); e->graph = nullptr; }
   if (need_tune) {
     ENS_CUDA(cudaStreamSynchronize(s), e, "sync before tuning");
     dg_status st = autotune(e, s);
@@ -709,6 +738,7 @@ dg_status dg_ensemble_step(dg_ensemble* e, double* const* dU, double* const* dG,
     cudaStreamDestroy(cs);
     if (err != cudaSuccess) { e->graph = nullptr; return ens_fail(e, DG_ECUDA, "ensemble graph capture", err); }
     e->graph_nsteps = nsteps;
+    e->graph_fv = fv_now;
   }
   ENS_CUDA(cudaGraphLaunch(e->graph, s), e, "ensemble graph launch");
   char msg[160];

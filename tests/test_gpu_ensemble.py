@@ -179,3 +179,42 @@ def test_mixed_time_schemes_are_rejected(dg):
     with pytest.raises(dg.DGError):
         dg.Ensemble([a, b])
     dg.Ensemble([b]).close()      # one scheme, RK4-14: accepted
+
+
+def test_members_outside_the_tile_tables_run_as_single_units(orc, dg):
+    """An ensemble of a conforming LGL member, a Gauss-node member, a 2:1
+    mortar mesh and a member with FV elements (mask set before creation):
+    the last three run as single-member units of the graph; every member
+    matches the oracle after three steps (1e-10)."""
+    from workloads import random_state
+    from workloads.mesh import refined_box_mesh
+    ref2 = np.zeros(8, dtype=bool)
+    ref2[0] = True
+    specs = [dict(mesh=box_mesh(3, 1, rotate_seed=1), N=3, kw={}),
+             dict(mesh=box_mesh(3, 1, rotate_seed=2), N=3, kw=dict(nodes=1)),
+             dict(mesh=refined_box_mesh(2, ref2, rotate_seed=3), N=2, kw={}),
+             dict(mesh=box_mesh(2, 1, rotate_seed=4), N=4, kw={}, fv=True)]
+    runs, orcs, U0s = [], [], []
+    for i, sp in enumerate(specs):
+        o = orc.Oracle(sp["mesh"], sp["N"], mu=0.01, **sp["kw"])
+        s = dg.Solver(sp["mesh"], sp["N"], mu=0.01, **sp["kw"])
+        if sp.get("fv"):
+            mask = (np.arange(sp["mesh"].n_elems) % 2).astype(np.int32)
+            o.set_fv_mask(mask)
+            s.set_fv_mask(mask)
+        U0s.append(random_state(sp["mesh"].n_elems, sp["N"], seed=20 + i, rho=(0.95, 1.05), vel=0.2,
+                                p=(0.95, 1.05)))
+        runs.append(s)
+        orcs.append(o)
+    ens = dg.Ensemble(runs)
+    Us = [torch.from_numpy(U).cuda() for U in U0s]
+    Gs = [torch.empty_like(U) for U in Us]
+    ens.step(Us, Gs, [0.0] * 4, [1e-3] * 4, nsteps=3)
+    torch.cuda.synchronize()
+    modes = [g["mode"] for g in ens.plan()["groups"]]
+    assert sum(m.startswith("per-member launches (Gauss") for m in modes) >= 2, modes
+    for o, U0, U in zip(orcs, U0s, Us):
+        ref = o.rk_steps(U0, 0.0, 1e-3, 3)
+        err = np.abs(U.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err <= 1e-10, (o.N, err)
+    ens.close()

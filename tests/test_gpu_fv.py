@@ -297,9 +297,16 @@ def test_fv_rejections(dg):
         s.time_derivative_vjp(U, torch.ones_like(U))
     with pytest.raises(ValueError):
         s.set_fv_mask(np.ones(mesh.n_elems + 1, dtype=np.int32))
-    # an ensemble member with FV elements is refused when stepped
-    ens = dg.Ensemble([s])
+    # with its FV elements set before the ensemble is created, the member runs
+    # as a single-member unit; a tile-table member that gets FV elements later
+    # is refused when stepped
     G = torch.empty_like(U)
+    ens = dg.Ensemble([s])
+    ens.step([U], [G], [0.0], [1e-3], nsteps=1)
+    ens.close()
+    s.set_fv_mask(None)
+    ens = dg.Ensemble([s])
+    s.set_fv_mask(np.ones(mesh.n_elems, dtype=np.int32))
     with pytest.raises(dg.DGError):
         ens.step([U], [G], [0.0], [1e-3], nsteps=1)
     s.set_fv_mask(None)
