@@ -262,11 +262,13 @@ dg_status dg_geometry(dg_ctx* ctx, double* dJa, double* dJ, dg_stream stream);
  * log-mean switch follow the primal state; at a kink of the LLF speed maximum
  * the mean of the one-sided derivatives is taken).  The paper has no
  * adjoint; these entries exist for gradient-based use of the solver.  Built
- * for LGL nodes, the LLF and EC surface fluxes and constant viscosity on a
+ * for LGL nodes, the LLF and EC surface fluxes and constant or Sutherland
+ * viscosity (the derivative of mu(T) enters through the state) on a
  * conforming mesh without FV sub-cell elements, for both time schemes;
  * other contexts get DG_EUNSUPPORTED.
  * dJdmu, where present, is a device double that is ACCUMULATED (+=) with
- * lambda . dR/dmu (R is linear in the constant viscosity mu); NULL skips it. */
+ * lambda . dR/dmu, mu the constant viscosity or Sutherland's reference
+ * viscosity (R is linear in it); NULL skips it. */
 
 /* dout = (dR/dU)^T dv at dU (all device [state_len]); dout may alias dv. */
 dg_status dg_time_derivative_vjp(dg_ctx* ctx, const double* dU, const double* dv, double* dout, double* dJdmu,
@@ -308,7 +310,8 @@ dg_status dg_checkpoint_schedule(int32_t nsteps, int32_t max_snapshots, int64_t*
  * receives dJ/dU.  Synchronises the stream. */
 dg_status dg_kinetic_energy(dg_ctx* ctx, const double* dU, double* dgrad, double* host_J, dg_stream stream);
 
-/* Change the constant viscosity mu of a context (e.g. for derivative checks). */
+/* Change the viscosity mu of a context (the constant one, or Sutherland's
+ * reference value; e.g. for derivative checks). */
 dg_status dg_set_viscosity(dg_ctx* ctx, double mu);
 
 /* ---- Batched ensemble (independent runs advanced together) ----------------

@@ -172,6 +172,10 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
     for (int r2 = 0; r2 < 12; ++r2) gr[r2] = gg[r2 * P];
     double gb[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     double ub[3] = {0, 0, 0};
+    // viscosity law: mu = mu_ref s(T), T = p / (rho R)
+    const double Tn = me.p / me.rho * g.inv_R;
+    double sv, dsv, vr = 0.0;
+    visc_factor_d(g, Tn, sv, dsv);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int r = ijk[d];
@@ -190,9 +194,16 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
 #pragma unroll
         for (int c = 0; c < 4; ++c) fb[c] += vs * lv[1 + c];
       }
-      mub += visc_flux_vjp(gr, me.u, me.v, me.w, g.mu, g.kappa, Ja[d * 3], Ja[d * 3 + 1], Ja[d * 3 + 2], fb, gb, ub);
+      vr += visc_flux_vjp(gr, me.u, me.v, me.w, g.mu * sv, g.kappa, Ja[d * 3], Ja[d * 3 + 1], Ja[d * 3 + 2], fb,
+                          gb, ub);
     }
+    mub += sv * vr;
     pr[1] += ub[0]; pr[2] += ub[1]; pr[3] += ub[2];
+    if (dsv != 0.0) {   // through T = p / (rho R)
+      const double Tb = g.mu * dsv * vr;
+      pr[4] += Tb * g.inv_R / me.rho;
+      pr[0] -= Tb * Tn / me.rho;
+    }
     double qb[5] = {0, 0, 0, 0, 0};
     const double uu[3] = {pr[1], pr[2], pr[3]};
     prim_vjp(q, pr[0], uu, pr[4], g.gm1, qb);
@@ -297,10 +308,20 @@ k_adj_face(const double* __restrict__ U, const double* __restrict__ grad, const 
     }
     double ubL[3] = {0, 0, 0}, ubR[3] = {0, 0, 0};
     const double irL = 1.0 / qL[0], irR = 1.0 / qR[0];
-    mub += visc_flux_vjp(gL, qL[1] * irL, qL[2] * irL, qL[3] * irL, g.mu, g.kappa, nx, ny, nz, fvb, gbL, ubL);
-    mub += visc_flux_vjp(gR, qR[1] * irR, qR[2] * irR, qR[3] * irR, g.mu, g.kappa, nx, ny, nz, fvb, gbR, ubR);
-    prim_vjp(qL, 0.0, ubL, 0.0, g.gm1, qbL);
-    prim_vjp(qR, 0.0, ubR, 0.0, g.gm1, qbR);
+    // viscosity law on each side: mu = mu_ref s(T), T = p / (rho R)
+    const double uL = qL[1] * irL, vL = qL[2] * irL, wL = qL[3] * irL;
+    const double uR = qR[1] * irR, vR = qR[2] * irR, wR = qR[3] * irR;
+    const double TL = g.gm1 * (qL[4] - 0.5 * (qL[1] * uL + qL[2] * vL + qL[3] * wL)) * irL * g.inv_R;
+    const double TR = g.gm1 * (qR[4] - 0.5 * (qR[1] * uR + qR[2] * vR + qR[3] * wR)) * irR * g.inv_R;
+    double sL, dsL, sR, dsR;
+    visc_factor_d(g, TL, sL, dsL);
+    visc_factor_d(g, TR, sR, dsR);
+    const double vrL = visc_flux_vjp(gL, uL, vL, wL, g.mu * sL, g.kappa, nx, ny, nz, fvb, gbL, ubL);
+    const double vrR = visc_flux_vjp(gR, uR, vR, wR, g.mu * sR, g.kappa, nx, ny, nz, fvb, gbR, ubR);
+    mub += sL * vrL + sR * vrR;
+    const double TbL = g.mu * dsL * vrL, TbR = g.mu * dsR * vrR;   // through T = p / (rho R)
+    prim_vjp(qL, -TbL * TL * irL, ubL, TbL * g.inv_R * irL, g.gm1, qbL);
+    prim_vjp(qR, -TbR * TR * irR, ubR, TbR * g.inv_R * irR, g.gm1, qbR);
     double* oL = b.face + ((size_t)f * 2 + 0) * 17 * NN + pq;
     double* oR = b.face + ((size_t)f * 2 + 1) * 17 * NN + pq;
 #pragma unroll

@@ -41,8 +41,6 @@ static dg_status ensure_adjoint(Ctx* c) {
     return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the LLF and entropy-conservative surface fluxes");
   if (c->prm.nodes != DG_NODES_LGL)
     return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the LGL operator");
-  if (c->prm.visc_law != DG_VISC_CONSTANT)
-    return afail(c, DG_EUNSUPPORTED, "the adjoint is built for constant viscosity");
   const size_t st = (size_t)c->E * 5 * c->P;
   const size_t nn = (size_t)c->nfaces * c->NN;
   ADJ_CUDA(setup_adjoint(c->N), c, "adjoint kernel set-up");

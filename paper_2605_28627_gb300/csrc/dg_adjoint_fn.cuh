@@ -179,8 +179,25 @@ __device__ __forceinline__ void llf_vjp(const double qL[5], const double qR[5], 
   }
 }
 
+// Viscosity factor s(T) = mu(T)/mu_ref and ds/dT: Sutherland's law
+// s = x^(3/2) (T_ref + S)/(T + S), x = T/T_ref, so ds/dT = s (3/(2T) - 1/(T + S));
+// s = 1, ds = 0 for constant viscosity.
+__device__ __forceinline__ void visc_factor_d(const Gas& g, double T, double& s, double& ds) {
+  if (g.visc_law != DG_VISC_SUTHERLAND) {
+    s = 1.0;
+    ds = 0.0;
+    return;
+  }
+  const double x = T * g.inv_T_ref, den = 1.0 / (T + g.S_suth);
+  s = x * sqrt(x) * g.suth_c * den;
+  ds = s * (1.5 / T - den);
+}
+
 // Adjoint of visc_flux (f_v . n, 4 components) w.r.t. the gradients g (12)
-// and the velocity (3); returns d(fb . f_v)/d mu (f_v is linear in mu).
+// and the velocity (3); returns fb . f_v1, f_v1 the flux with unit viscosity
+// (f_v = mu f_v1 is linear in mu: the return value is d(fb . f_v)/d mu, and
+// with Sutherland's law the caller scales it by s(T) and, for the T-derivative,
+// by mu_ref ds/dT).
 __device__ __forceinline__ double visc_flux_vjp(const double g[12], double u, double v, double w, double mu,
                                                 double kappa, double nx, double ny, double nz, const double fb[4],
                                                 double gb[12], double ub[3]) {

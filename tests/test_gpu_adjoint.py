@@ -23,12 +23,16 @@ def _cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("N,flux", [(2, 0), (3, 0), (3, 1), (5, 0)])
-def test_vjp_dot_product_vs_oracle_tangent_linear(orc, dg, N, flux):
+@pytest.mark.parametrize("N,flux,law", [(2, 0, 0), (3, 0, 0), (3, 1, 0), (5, 0, 0), (3, 0, 1), (5, 1, 1)])
+def test_vjp_dot_product_vs_oracle_tangent_linear(orc, dg, N, flux, law):
+    """<(dR/dU)^T v, w> against <v, (dR/dU) w> of the oracle's tangent-linear,
+    and v . dR/dmu; law 1: Sutherland's viscosity (mu(T), T_ref 1, S 0.4),
+    whose T-derivative enters through the state."""
     mesh = box_mesh(3 if N < 5 else 2, N, deform="sinprod", rotate_seed=600 + N)
     mu = 0.03
-    o = orc.Oracle(mesh, N, mu=mu, surf_flux=flux)
-    s = dg.Solver(mesh, N, mu=mu, surf_flux=flux)
+    kw = dict(mu=mu, surf_flux=flux, visc_law=law, T_ref=1.0, S_suth=0.4)
+    o = orc.Oracle(mesh, N, **kw)
+    s = dg.Solver(mesh, N, **kw)
     U = random_state(mesh.n_elems, N, seed=700 + N)
     rng = np.random.default_rng(800 + N)
     w = rng.normal(size=U.shape)
