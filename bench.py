@@ -732,8 +732,8 @@ def run_pid(args, local):
     16.78 M DOF at N=3 (64^3 Cartesian elements; the paper's node-level PID
     comparison, run there on Gauss nodes) and N=9 at 20^3 elements (8.0 M DOF,
     the per-GPU load of the paper's weak-scaling runs of the split-form LGL
-    operator), 10 steps each: LGL split form in FP64 and with the FP32 operator,
-    Gauss nodes (standard weak form) in FP64, each FP64 case also with RK4-14
+    operator), 10 steps each: LGL split form and Gauss nodes (standard weak
+    form), each in FP64 and with the FP32 operator, each FP64 case also with RK4-14
     (PID counts stages, so it is per stage), and every case with half of the
     elements in the FV sub-cell representation (checkerboard, as the paper's
     DG/FV runs force it; its Table 4 runs are on Gauss nodes).  Uniform flow
@@ -759,8 +759,7 @@ def run_pid(args, local):
         res = {"N": N, "elements": mesh.n_elems, "dof": dofs,
                "nodes": "Legendre-Gauss, standard weak form" if nodes == dg.NODES_LG else "LGL, split form"}
         precs = [("fp64", dg.FP64, dg.RK45, False), ("fp64_rk414", dg.FP64, dg.RK414, False)]
-        if nodes == dg.NODES_LGL:
-            precs.append(("fp32op", dg.FP32OP, dg.RK45, False))
+        precs.append(("fp32op", dg.FP32OP, dg.RK45, False))
         precs.append(("fp64_fv50", dg.FP64, dg.RK45, True))
         if args.pid_variants:
             precs = [p for p in precs if p[0] in args.pid_variants.split(",")]

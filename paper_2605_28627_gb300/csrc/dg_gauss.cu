@@ -307,79 +307,86 @@ k_geometry_to_gauss(double* __restrict__ X, double* __restrict__ metrics, double
 // ---------------------------------------------------------------------------
 // Stage kernels
 
-// Face values of U: Uf[e][f][v][p + n q] = sum_i l_i(+-1) U(line of (p, q)).
-template <int N, int EPB>
+// Face values of U: Uf[e][f][v][p + n q] = sum_i l_i(+-1) U(line of (p, q)),
+// in the operator type R (the FP32 operator prolongs FP32 values: an FP64
+// prolongation would take the FP64 pipe for more than the whole FP32 stage).
+template <int N, int EPB, typename R = double>
 __global__ void __launch_bounds__(Shape<N, EPB>::THREADS)
-k_prolong_lg(const double* __restrict__ U, const double* __restrict__ tab, double* __restrict__ Uf, int E) {
+k_prolong_lg(const double* __restrict__ U, const double* __restrict__ tab, R* __restrict__ Uf, int E) {
   using S = Shape<N, EPB>;
   constexpr int n = S::n, P = S::P, NN = n * n;
-  extern __shared__ double sm[];   // [EPB][5][P]
-  __shared__ double sl[2 * n];     // l_i(-1), l_i(+1)
+  extern __shared__ __align__(16) unsigned char prolong_raw[];
+  R* sm = reinterpret_cast<R*>(prolong_raw);   // [EPB][5][P]
+  __shared__ R sl[2 * n];                       // l_i(-1), l_i(+1)
   const int le = threadIdx.x / P, id = threadIdx.x - le * P;
   const int e = blockIdx.x * EPB + le;
-  for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) sl[t] = tab[GaussTab::lm(n) + t];
+  for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) sl[t] = to_op<R>(tab[GaussTab::lm(n) + t]);
   if (e < E)
-    for (int v = 0; v < 5; ++v) sm[(le * 5 + v) * P + id] = U[((size_t)e * 5 + v) * P + id];
+    for (int v = 0; v < 5; ++v) sm[(le * 5 + v) * P + id] = to_op<R>(U[((size_t)e * 5 + v) * P + id]);
   __syncthreads();
   if (e >= E) return;
   for (int o = id; o < 30 * NN; o += P) {
     const int f = o / (5 * NN), r = o - f * 5 * NN, v = r / NN, pq = r - v * NN;
     const int p = pq % n, q = pq / n, d = f >> 1;
-    const double* l = sl + (f & 1) * n;
-    const double* u = sm + (le * 5 + v) * P;
-    double s = 0.0;
+    const R* l = sl + (f & 1) * n;
+    const R* u = sm + (le * 5 + v) * P;
+    R s = R(0);
 #pragma unroll
     for (int i = 0; i < n; ++i) s = fma(l[i], u[line_node<n>(d, i, p, q)], s);
     Uf[((size_t)e * 6 + f) * 5 * NN + (size_t)v * NN + pq] = s;
   }
 }
 
-// Lifting variables (u, v, w, T) of a state given with stride st.
-__device__ __forceinline__ void state_phi(const double* q, int st, const Gas& g, double ph[4]) {
-  const double ir = rcp_op(q[0]);
-  const double u = q[st] * ir, v = q[2 * st] * ir, w = q[3 * st] * ir;
-  const double p = g.gm1 * (q[4 * st] - 0.5 * (q[st] * u + q[2 * st] * v + q[3 * st] * w));
+// Lifting variables (u, v, w, T) of a state given with stride st, in R.
+template <typename R, typename Q>
+__device__ __forceinline__ void state_phi(const Q* q, int st, const Gas& g, R ph[4]) {
+  const R rho = to_op<R>(q[0]), ir = rcp_op(rho);
+  const R m0 = to_op<R>(q[st]), m1 = to_op<R>(q[2 * st]), m2 = to_op<R>(q[3 * st]);
+  const R u = m0 * ir, v = m1 * ir, w = m2 * ir;
+  const R p = gsel<R>(g.gm1, g.f_gm1) * (to_op<R>(q[4 * st]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
   ph[0] = u;
   ph[1] = v;
   ph[2] = w;
-  ph[3] = p * ir * g.inv_R;
+  ph[3] = p * ir * gsel<R>(g.inv_R, g.f_inv_R);
 }
 
-template <int N, int EPB>
+template <int N, int EPB, typename R = double>
 constexpr size_t lift_lg_smem() {
   constexpr int n = N + 1, P = n * n * n, NN = n * n;
-  return sizeof(double) * EPB * (16 * P + 72 * NN);
+  return sizeof(R) * EPB * (16 * P + 72 * NN);
 }
 
 // Weak BR1 lifting (Eq. 3): J g_l,i = sum_faces l_{i_d}(+-1)/w_{i_d} phi* (n_l sJ)
 //   - sum_d sum_m (w_m/w_{i_d}) D_{m i_d} (phi Ja^d_l)_m, phi* the face average;
-// then the face values of g for the face kernel.
-// MORTAR: a face whose neighbour entry is negative is a mortar side, whose
-// neighbour face state is mvirt[-1 - entry][5][NN] in its own point order.
-template <int N, int EPB, bool MORTAR = false>
+// then the face values of g for the face kernel.  R: the operator type (the
+// face values Uf, the metric terms, face geometry, g and its face values gf).
+// MORTAR (FP64): a face whose neighbour entry is negative is a mortar side,
+// whose neighbour face state is mvirt[-1 - entry][5][NN] in its own point order.
+template <int N, int EPB, bool MORTAR = false, typename R = double>
 __global__ void __launch_bounds__(Shape<N, EPB>::THREADS)
-k_lift_lg(const double* __restrict__ U, const double* __restrict__ Uf, const double* __restrict__ metrics,
-          const double* __restrict__ facegeo, const int* __restrict__ elem_face, const int* __restrict__ elem_nbr,
-          const double* __restrict__ tab, double* __restrict__ grad, double* __restrict__ gf, int E, int F, Gas g,
+k_lift_lg(const double* __restrict__ U, const R* __restrict__ Uf, const R* __restrict__ metrics,
+          const R* __restrict__ facegeo, const int* __restrict__ elem_face, const int* __restrict__ elem_nbr,
+          const double* __restrict__ tab, R* __restrict__ grad, R* __restrict__ gf, int E, int F, Gas g,
           const double* __restrict__ mvirt, int n_mortar) {
   using S = Shape<N, EPB>;
   constexpr int n = S::n, P = S::P, NN = n * n, PER = 16 * P + 72 * NN;
-  extern __shared__ double sm[];
-  __shared__ double sDw[n * n], sT[4 * n];   // weak D; l(-1)/w, l(+1)/w, l(-1), l(+1)
+  extern __shared__ __align__(16) unsigned char lift_lg_raw[];
+  R* sm = reinterpret_cast<R*>(lift_lg_raw);
+  __shared__ R sDw[n * n], sT[4 * n];   // weak D; l(-1)/w, l(+1)/w, l(-1), l(+1)
   const int le = threadIdx.x / P, id = threadIdx.x - le * P;
   const int e = blockIdx.x * EPB + le;
   const bool active = e < E;
-  double* sphi = sm + le * PER;     // [4][P]
-  double* sprod = sphi + 4 * P;     // [12][P]
-  double* sS = sprod + 12 * P;      // [6][12][NN]: phi* (n_l sJ) with the outward normal
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) sDw[t] = tab[GaussTab::Dw(n) + t];
-  for (int t = threadIdx.x; t < 4 * n; t += blockDim.x) sT[t] = tab[GaussTab::lmw(n) + t];
-  double Ja[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, iJ = 0.0;
+  R* sphi = sm + le * PER;     // [4][P]
+  R* sprod = sphi + 4 * P;     // [12][P]
+  R* sS = sprod + 12 * P;      // [6][12][NN]: phi* (n_l sJ) with the outward normal
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) sDw[t] = to_op<R>(tab[GaussTab::Dw(n) + t]);
+  for (int t = threadIdx.x; t < 4 * n; t += blockDim.x) sT[t] = to_op<R>(tab[GaussTab::lmw(n) + t]);
+  R Ja[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, iJ = R(0);
   if (active) {
-    double ph[4];
-    state_phi(U + (size_t)e * 5 * P + id, P, g, ph);
+    R ph[4];
+    state_phi<R>(U + (size_t)e * 5 * P + id, P, g, ph);
     for (int a = 0; a < 4; ++a) sphi[a * P + id] = ph[a];
-    const double* mt = metrics + (size_t)e * 10 * P + id;
+    const R* mt = metrics + (size_t)e * 10 * P + id;
 #pragma unroll
     for (int r = 0; r < 9; ++r) Ja[r] = mt[r * P];
     iJ = mt[9 * P];
@@ -390,21 +397,26 @@ k_lift_lg(const double* __restrict__ U, const double* __restrict__ Uf, const dou
       int p2, q2;
       apply_flip<n>(code & 7, p, q, p2, q2);
       const int pq2 = p2 + n * q2;
-      double pm[4], pn[4];
-      state_phi(Uf + ((size_t)e * 6 + f) * 5 * NN + pq, NN, g, pm);
-      if (MORTAR && nb < 0) {
-        state_phi(mvirt + (size_t)dg_idx(-1 - nb, 5L * n_mortar, kSiteMortar) * 5 * NN + pq, NN, g, pn);
-      } else {
+      R pm[4], pn[4];
+      state_phi<R>(Uf + ((size_t)e * 6 + f) * 5 * NN + pq, NN, g, pm);
+      bool done = false;
+      if constexpr (MORTAR) {
+        if (nb < 0) {
+          state_phi<R>(mvirt + (size_t)dg_idx(-1 - nb, 5L * n_mortar, kSiteMortar) * 5 * NN + pq, NN, g, pn);
+          done = true;
+        }
+      }
+      if (!done) {
         const int e2 = dg_idx(nb >> 3, E, kSiteGaussLift), f2 = nb & 7;
-        state_phi(Uf + ((size_t)e2 * 6 + f2) * 5 * NN + pq2, NN, g, pn);
+        state_phi<R>(Uf + ((size_t)e2 * 6 + f2) * 5 * NN + pq2, NN, g, pn);
       }
       const bool master = code & 8;
-      const double* fg = facegeo + (size_t)fid * 4 * NN + (master ? pq : pq2);
-      const double sJ = master ? fg[3 * NN] : -fg[3 * NN];
-      const double ns[3] = {sJ * fg[0], sJ * fg[NN], sJ * fg[2 * NN]};
+      const R* fg = facegeo + (size_t)fid * 4 * NN + (master ? pq : pq2);
+      const R sJ = master ? fg[3 * NN] : -fg[3 * NN];
+      const R ns[3] = {sJ * fg[0], sJ * fg[NN], sJ * fg[2 * NN]};
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const double star = 0.5 * (pm[a] + pn[a]);
+        const R star = R(0.5) * (pm[a] + pn[a]);
 #pragma unroll
         for (int l = 0; l < 3; ++l) sS[(f * 12 + a * 3 + l) * NN + pq] = star * ns[l];
       }
@@ -412,9 +424,9 @@ k_lift_lg(const double* __restrict__ U, const double* __restrict__ Uf, const dou
   }
   const int i = id % n, j = (id / n) % n, k = id / NN;
   const int ijk[3] = {i, j, k};
-  double acc[12];
+  R acc[12];
 #pragma unroll
-  for (int r = 0; r < 12; ++r) acc[r] = 0.0;
+  for (int r = 0; r < 12; ++r) acc[r] = R(0);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     __syncthreads();
@@ -429,7 +441,7 @@ k_lift_lg(const double* __restrict__ U, const double* __restrict__ Uf, const dou
       const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
       const int line0 = id - r * stride;
       for (int m = 0; m < n; ++m) {
-        const double c = sDw[r * n + m];
+        const R c = sDw[r * n + m];
         const int mid = line0 + m * stride;
 #pragma unroll
         for (int al = 0; al < 12; ++al) acc[al] = fma(-c, sprod[al * P + mid], acc[al]);
@@ -443,8 +455,8 @@ k_lift_lg(const double* __restrict__ U, const double* __restrict__ Uf, const dou
       const int pq = d == 0 ? j + n * k : (d == 1 ? i + n * k : i + n * j);
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        const double c = sT[s * n + r];
-        const double* src = sS + ((2 * d + s) * 12) * NN + pq;
+        const R c = sT[s * n + r];
+        const R* src = sS + ((2 * d + s) * 12) * NN + pq;
 #pragma unroll
         for (int al = 0; al < 12; ++al) acc[al] = fma(c, src[al * NN], acc[al]);
       }
@@ -452,10 +464,10 @@ k_lift_lg(const double* __restrict__ U, const double* __restrict__ Uf, const dou
   }
   __syncthreads();   // every thread is done with sprod
   if (active) {
-    double* go = grad + (size_t)e * 12 * P + id;
+    R* go = grad + (size_t)e * 12 * P + id;
 #pragma unroll
     for (int al = 0; al < 12; ++al) {
-      const double gv = acc[al] * iJ;
+      const R gv = acc[al] * iJ;
       go[al * P] = gv;
       sprod[al * P + id] = gv;
     }
@@ -465,8 +477,8 @@ k_lift_lg(const double* __restrict__ U, const double* __restrict__ Uf, const dou
   for (int o = id; o < 72 * NN; o += P) {
     const int f = o / (12 * NN), r = o - f * 12 * NN, al = r / NN, pq = r - al * NN;
     const int p = pq % n, q = pq / n, d = f >> 1;
-    const double* l = sT + (2 + (f & 1)) * n;
-    double s = 0.0;
+    const R* l = sT + (2 + (f & 1)) * n;
+    R s = R(0);
 #pragma unroll
     for (int m = 0; m < n; ++m) s = fma(l[m], sprod[al * P + line_node<n>(d, m, p, q)], s);
     gf[((size_t)e * 6 + f) * 12 * NN + (size_t)al * NN + pq] = s;
@@ -477,10 +489,10 @@ k_lift_lg(const double* __restrict__ U, const double* __restrict__ Uf, const dou
 // face values of the state and of the lifted gradients.
 // FVSKIP: faces with an FV sub-cell element on either side are left to the FV
 // face kernel (fv_mask: [E], 1 for an FV element).
-template <int N, bool FVSKIP>
+template <int N, bool FVSKIP, typename R = double>
 __global__ void __launch_bounds__(128)
-k_face_lg(const double* __restrict__ Uf, const double* __restrict__ gf, const FaceInfo* __restrict__ faces,
-          const double* __restrict__ facegeo, double* __restrict__ fstar, int F, int E, Gas g,
+k_face_lg(const R* __restrict__ Uf, const R* __restrict__ gf, const FaceInfo* __restrict__ faces,
+          const R* __restrict__ facegeo, R* __restrict__ fstar, int F, int E, Gas g,
           const int* __restrict__ fv_mask) {
   constexpr int n = N + 1, NN = n * n;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -496,30 +508,32 @@ k_face_lg(const double* __restrict__ Uf, const double* __restrict__ gf, const Fa
   int p2, q2;
   apply_flip<n>(fi.flip, p, q, p2, q2);
   const int pq2 = p2 + n * q2;
-  double dL[5], dR[5], gL[12], gR[12];
-  const double* uM = Uf + ((size_t)eM * 6 + fM) * 5 * NN + pq;
-  const double* uS = Uf + ((size_t)eS * 6 + fS) * 5 * NN + pq2;
+  // the face states enter the flux core as FP64 values (exact widening of FP32
+  // face values with the FP32 operator)
+  double dL[5], dR[5];
+  R gL[12], gR[12];
+  const R* uM = Uf + ((size_t)eM * 6 + fM) * 5 * NN + pq;
+  const R* uS = Uf + ((size_t)eS * 6 + fS) * 5 * NN + pq2;
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    dL[v] = uM[v * NN];
-    dR[v] = uS[v * NN];
+    dL[v] = to_f64(uM[v * NN]);
+    dR[v] = to_f64(uS[v * NN]);
   }
-  const double* gM = gf + ((size_t)eM * 6 + fM) * 12 * NN + pq;
-  const double* gS = gf + ((size_t)eS * 6 + fS) * 12 * NN + pq2;
+  const R* gM = gf + ((size_t)eM * 6 + fM) * 12 * NN + pq;
+  const R* gS = gf + ((size_t)eS * 6 + fS) * 12 * NN + pq2;
 #pragma unroll
   for (int r = 0; r < 12; ++r) {
     gL[r] = gM[r * NN];
     gR[r] = gS[r * NN];
   }
-  const double* fg = facegeo + (size_t)f * 4 * NN + pq;
-  face_flux_core<double>(dL, dR, gL, gR, fg[0], fg[NN], fg[2 * NN], fg[3 * NN], g, fstar + (size_t)f * 5 * NN + pq,
-                         NN);
+  const R* fg = facegeo + (size_t)f * 4 * NN + pq;
+  face_flux_core<R>(dL, dR, gL, gR, fg[0], fg[NN], fg[2 * NN], fg[3 * NN], g, fstar + (size_t)f * 5 * NN + pq, NN);
 }
 
-template <int N, int EPB>
+template <int N, int EPB, typename R = double>
 constexpr size_t volume_lg_smem() {
   constexpr int n = N + 1, P = n * n * n, NN = n * n;
-  return sizeof(double) * EPB * (15 * P + 30 * NN);
+  return sizeof(R) * EPB * (15 * P + 30 * NN);
 }
 
 // Weak volume and surface terms (Eq. 2):
@@ -527,15 +541,19 @@ constexpr size_t volume_lg_smem() {
 // Ft^d = (f - f_v)(q, g) . Ja^d; then 1/J, the source and the LSERK update.
 // LIST: the element slots come from a.list (the DG elements when FV sub-cell
 // elements exist), idle past its end.
-template <int N, int EPB, bool LIST>
+// R: the operator type (metric terms, gradients, surface fluxes and the
+// arithmetic of the residual); the state, 1/J of the final scaling and the RK
+// update are FP64 (metrics64: the FP64 metric array, row 9 = 1/J).
+template <int N, int EPB, bool LIST, typename R = double>
 __global__ void __launch_bounds__(Shape<N, EPB>::THREADS)
-k_volume_lg(StageArgs a, const double* __restrict__ metrics, const double* __restrict__ grad,
-            const double* __restrict__ fstar, const int* __restrict__ elem_face, const double* __restrict__ mms,
-            const double* __restrict__ tab, int E, Gas g) {
+k_volume_lg(StageArgs a, const R* __restrict__ metrics, const double* __restrict__ metrics64,
+            const R* __restrict__ grad, const R* __restrict__ fstar, const int* __restrict__ elem_face,
+            const double* __restrict__ mms, const double* __restrict__ tab, int E, Gas g) {
   using S = Shape<N, EPB>;
   constexpr int n = S::n, P = S::P, NN = n * n, PER = 15 * P + 30 * NN;
-  extern __shared__ double sm[];
-  __shared__ double sDw[n * n], sT[2 * n];   // weak D; l(-1)/w, l(+1)/w
+  extern __shared__ __align__(16) unsigned char volume_lg_raw[];
+  R* sm = reinterpret_cast<R*>(volume_lg_raw);
+  __shared__ R sDw[n * n], sT[2 * n];       // weak D; l(-1)/w, l(+1)/w
   __shared__ double s_tc[2];                 // sin, cos of pi t (manufactured source)
   const int le = threadIdx.x / P, id = threadIdx.x - le * P;
   int e = blockIdx.x * EPB + le;
@@ -547,36 +565,39 @@ k_volume_lg(StageArgs a, const double* __restrict__ metrics, const double* __res
     }
   }
   const bool active = e < E;
-  double* sF = sm + le * PER;   // [3][5][P] contravariant fluxes
-  double* sFs = sF + 15 * P;    // [6][5][NN] outward surface fluxes
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) sDw[t] = tab[GaussTab::Dw(n) + t];
-  for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) sT[t] = tab[GaussTab::lmw(n) + t];
+  R* sF = sm + le * PER;   // [3][5][P] contravariant fluxes
+  R* sFs = sF + 15 * P;    // [6][5][NN] outward surface fluxes
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) sDw[t] = to_op<R>(tab[GaussTab::Dw(n) + t]);
+  for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) sT[t] = to_op<R>(tab[GaussTab::lmw(n) + t]);
   if (threadIdx.x == 0 && g.source == DG_SOURCE_MMS)
     sincospi(a.clock[0] + a.c_stage * a.clock[1], &s_tc[0], &s_tc[1]);
   double q[5] = {0, 0, 0, 0, 0}, iJ = 0.0;
   if (active) {
-    const double* mt = metrics + (size_t)e * 10 * P + id;
+    const R* mt = metrics + (size_t)e * 10 * P + id;
 #pragma unroll
     for (int v = 0; v < 5; ++v) q[v] = a.U[((size_t)e * 5 + v) * P + id];
-    double gr[12];
+    R gr[12];
 #pragma unroll
     for (int r = 0; r < 12; ++r) gr[r] = grad[((size_t)e * 12 + r) * P + id];
-    iJ = mt[9 * P];
-    const double ir = rcp_op(q[0]);
-    const double u = q[1] * ir, v = q[2] * ir, w = q[3] * ir;
-    const double p = g.gm1 * (q[4] - 0.5 * (q[1] * u + q[2] * v + q[3] * w));
-    double mu = g.mu, lam = g.mu * g.kappa;
+    iJ = metrics64[((size_t)e * 10 + 9) * P + id];
+    R qo[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qo[v] = to_op<R>(q[v]);
+    const R ir = rcp_op(qo[0]);
+    const R u = qo[1] * ir, v = qo[2] * ir, w = qo[3] * ir;
+    const R p = gsel<R>(g.gm1, g.f_gm1) * (qo[4] - R(0.5) * (qo[1] * u + qo[2] * v + qo[3] * w));
+    R mu = gsel<R>(g.mu, g.f_mu), lam = gsel<R>(g.mu * g.kappa, g.f_lam);
     if (g.visc_law == DG_VISC_SUTHERLAND) {
-      const double sf = visc_factor<double>(g, p * ir * g.inv_R);
+      const R sf = visc_factor<R>(g, p * ir * gsel<R>(g.inv_R, g.f_inv_R));
       mu *= sf;
       lam *= sf;
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const double nx = mt[(d * 3) * P], ny = mt[(d * 3 + 1) * P], nz = mt[(d * 3 + 2) * P];
-      double fa[5], fv[4];
-      euler_flux<double>(q, u, v, w, p, nx, ny, nz, fa);
-      visc_flux<double>(gr, u, v, w, mu, lam, nx, ny, nz, fv);
+      const R nx = mt[(d * 3) * P], ny = mt[(d * 3 + 1) * P], nz = mt[(d * 3 + 2) * P];
+      R fa[5], fv[4];
+      euler_flux<R>(qo, u, v, w, p, nx, ny, nz, fa);
+      visc_flux<R>(gr, u, v, w, mu, lam, nx, ny, nz, fv);
       sF[(d * 5) * P + id] = fa[0];
 #pragma unroll
       for (int c = 0; c < 4; ++c) sF[(d * 5 + 1 + c) * P + id] = fa[1 + c] - fv[c];
@@ -584,7 +605,7 @@ k_volume_lg(StageArgs a, const double* __restrict__ metrics, const double* __res
     for (int o = id; o < 30 * NN; o += P) {
       const int f = o / (5 * NN), r = o - f * 5 * NN, v2 = r / NN, pq = r - v2 * NN;
       const int code = elem_face[e * 6 + f], fid = dg_idx(code >> 4, a.nfaces > 0 ? a.nfaces : 3L * E, kSiteGaussVol);
-      double val;
+      R val;
       if (code & 8) {
         val = fstar[((size_t)fid * 5 + v2) * NN + pq];
       } else {
@@ -599,14 +620,14 @@ k_volume_lg(StageArgs a, const double* __restrict__ metrics, const double* __res
   if (!active) return;
   const int i = id % n, j = (id / n) % n, k = id / NN;
   const int ijk[3] = {i, j, k};
-  double acc[5] = {0, 0, 0, 0, 0};
+  R acc[5] = {0, 0, 0, 0, 0};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int r = ijk[d];
     const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
     const int line0 = id - r * stride;
     for (int m = 0; m < n; ++m) {
-      const double c = sDw[r * n + m];
+      const R c = sDw[r * n + m];
       const int mid = line0 + m * stride;
 #pragma unroll
       for (int v = 0; v < 5; ++v) acc[v] = fma(-c, sF[(d * 5 + v) * P + mid], acc[v]);
@@ -614,35 +635,30 @@ k_volume_lg(StageArgs a, const double* __restrict__ metrics, const double* __res
     const int pq = d == 0 ? j + n * k : (d == 1 ? i + n * k : i + n * j);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      const double c = sT[s * n + r];
+      const R c = sT[s * n + r];
 #pragma unroll
       for (int v = 0; v < 5; ++v) acc[v] = fma(c, sFs[((2 * d + s) * 5 + v) * NN + pq], acc[v]);
     }
   }
-  double src[5] = {0, 0, 0, 0, 0};
-  if (g.source == DG_SOURCE_MMS) {
-    // density wave of the manufactured solution (see volume_body)
-    const double sa = mms[((size_t)e * 2) * P + id], ca = mms[((size_t)e * 2 + 1) * P + id];
-    const double sphi = fma(sa, s_tc[1], -ca * s_tc[0]);
-    const double cphi = fma(ca, s_tc[1], sa * s_tc[0]);
-    const double A = g.mms_amp;
-    const double rw = 2.0 + A * sphi;
-    const double irw = rcp_op(rw);
-    const double rp = M_PI * A * cphi;
-    const double lapT = 3.0 * g.inv_R * fma(M_PI * M_PI * A, sphi, 2.0 * rp * rp * irw) * (irw * irw);
-    src[0] = src[1] = src[2] = src[3] = 2.0 * rp;
-    src[4] = fma(-g.mu * g.kappa, lapT, 3.0 * rp);
+  // the manufactured source (density wave, see volume_body), in R
+  R srcr[5] = {0, 0, 0, 0, 0};
+  if (g.source == DG_SOURCE_MMS) mms_source<R>(g, mms, e, P, id, s_tc[0], s_tc[1], srcr);
+  double src[5], accd[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    src[c] = to_f64(srcr[c]);
+    accd[c] = to_f64(acc[c]);
   }
   const size_t o0 = (size_t)e * 5 * P + id;
   if (a.mode == 0) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) a.Ut[o0 + (size_t)c * P] = fma(-acc[c], iJ, src[c]);
+    for (int c = 0; c < 5; ++c) a.Ut[o0 + (size_t)c * P] = fma(-accd[c], iJ, src[c]);
   } else {
     const double dt = a.clock[1];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       const size_t o = o0 + (size_t)c * P;
-      const double gk = fma(a.A, a.Gk[o], dt * fma(-acc[c], iJ, src[c]));
+      const double gk = fma(a.A, a.Gk[o], dt * fma(-accd[c], iJ, src[c]));
       a.Gk[o] = gk;
       a.Uw[o] = fma(a.B, gk, q[c]);
     }
@@ -652,23 +668,30 @@ k_volume_lg(StageArgs a, const double* __restrict__ metrics, const double* __res
 // ---------------------------------------------------------------------------
 // Launchers
 
+template <int N, typename R>
+static cudaError_t setup_lg_NR() {
+  using S = Shape<N>;
+  cudaError_t e = cudaFuncSetAttribute(k_lift_lg<N, S::EPB, false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)lift_lg_smem<N, S::EPB, R>());
+  if (e == cudaSuccess && sizeof(R) == 8)
+    e = cudaFuncSetAttribute(k_lift_lg<N, S::EPB, true, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lift_lg_smem<N, S::EPB, R>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_volume_lg<N, S::EPB, false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)volume_lg_smem<N, S::EPB, R>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_volume_lg<N, S::EPB, true, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)volume_lg_smem<N, S::EPB, R>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_prolong_lg<N, S::EPB, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(R) * S::EPB * 5 * S::P));
+  return e;
+}
+
 template <int N>
 static cudaError_t setup_lg_N() {
-  using S = Shape<N>;
-  cudaError_t e = cudaFuncSetAttribute(k_lift_lg<N, S::EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)lift_lg_smem<N, S::EPB>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_lift_lg<N, S::EPB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)lift_lg_smem<N, S::EPB>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_volume_lg<N, S::EPB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)volume_lg_smem<N, S::EPB>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_volume_lg<N, S::EPB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)volume_lg_smem<N, S::EPB>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_prolong_lg<N, S::EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * S::EPB * 5 * S::P));
+  cudaError_t e = setup_lg_NR<N, double>();
+  if (e == cudaSuccess) e = setup_lg_NR<N, float>();
   constexpr int P = (N + 1) * (N + 1) * (N + 1);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_geometry_to_gauss<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -689,38 +712,59 @@ static cudaError_t geometry_lg_N(Ctx& c, int* d_bad, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int N>
-static cudaError_t lift_lg_N(const Ctx& c, const double* U, cudaStream_t s) {
+// The operator type's metric terms and face geometry.
+template <typename R>
+static const R* metrics_of(const Ctx& c) {
+  return sizeof(R) == 8 ? (const R*)c.d_metrics : (const R*)c.d_metrics_f;
+}
+template <typename R>
+static const R* facegeo_of(const Ctx& c) {
+  return sizeof(R) == 8 ? (const R*)c.d_facegeo : (const R*)c.d_facegeo_f;
+}
+
+template <int N, typename R>
+static cudaError_t lift_lg_NR(const Ctx& c, const double* U, cudaStream_t s) {
   using S = Shape<N>;
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
-  k_prolong_lg<N, S::EPB><<<blocks, S::THREADS, sizeof(double) * S::EPB * 5 * S::P, s>>>(U, c.d_lgb, c.d_Uf, c.E);
+  R* Uf = reinterpret_cast<R*>(c.d_Uf);
+  R* gf = reinterpret_cast<R*>(c.d_gf);
+  k_prolong_lg<N, S::EPB, R><<<blocks, S::THREADS, sizeof(R) * S::EPB * 5 * S::P, s>>>(U, c.d_lgb, Uf, c.E);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  if (c.M > 0) {   // the mortar sides' neighbour face states first
-    err = launch_mortar_lift(c, U, s);
-    if (err != cudaSuccess) return err;
-    k_lift_lg<N, S::EPB, true><<<blocks, S::THREADS, lift_lg_smem<N, S::EPB>(), s>>>(
-        U, c.d_Uf, c.d_metrics, c.d_facegeo, c.d_elem_face, c.d_elem_nbr, c.d_lgb, (double*)c.d_grad, c.d_gf, c.E,
-        c.nfaces, c.gas, c.d_mortar_virt, c.M);
-    return cudaGetLastError();
+  if constexpr (sizeof(R) == 8) {
+    if (c.M > 0) {   // the mortar sides' neighbour face states first
+      err = launch_mortar_lift(c, U, s);
+      if (err != cudaSuccess) return err;
+      k_lift_lg<N, S::EPB, true, R><<<blocks, S::THREADS, lift_lg_smem<N, S::EPB, R>(), s>>>(
+          U, Uf, metrics_of<R>(c), facegeo_of<R>(c), c.d_elem_face, c.d_elem_nbr, c.d_lgb, (R*)c.d_grad, gf, c.E,
+          c.nfaces, c.gas, c.d_mortar_virt, c.M);
+      return cudaGetLastError();
+    }
   }
-  k_lift_lg<N, S::EPB><<<blocks, S::THREADS, lift_lg_smem<N, S::EPB>(), s>>>(
-      U, c.d_Uf, c.d_metrics, c.d_facegeo, c.d_elem_face, c.d_elem_nbr, c.d_lgb, (double*)c.d_grad, c.d_gf, c.E,
+  k_lift_lg<N, S::EPB, false, R><<<blocks, S::THREADS, lift_lg_smem<N, S::EPB, R>(), s>>>(
+      U, Uf, metrics_of<R>(c), facegeo_of<R>(c), c.d_elem_face, c.d_elem_nbr, c.d_lgb, (R*)c.d_grad, gf, c.E,
       c.nfaces, c.gas, nullptr, 0);
   return cudaGetLastError();
 }
 
 template <int N>
-static cudaError_t face_lg_N(const Ctx& c, cudaStream_t s) {
+static cudaError_t lift_lg_N(const Ctx& c, const double* U, cudaStream_t s, bool fp64) {
+  return (fp64 || c.prm.precision != DG_FP32OP) ? lift_lg_NR<N, double>(c, U, s) : lift_lg_NR<N, float>(c, U, s);
+}
+
+template <int N, typename R>
+static cudaError_t face_lg_NR(const Ctx& c, cudaStream_t s) {
   // the conforming faces (the mortars' slots follow them)
   const long tot = (long)c.nfaces_conf * (N + 1) * (N + 1);
+  const R* Uf = reinterpret_cast<const R*>(c.d_Uf);
+  const R* gf = reinterpret_cast<const R*>(c.d_gf);
   if (tot > 0) {
     if (c.fv_on)
-      k_face_lg<N, true><<<(int)((tot + 127) / 128), 128, 0, s>>>(
-          c.d_Uf, c.d_gf, c.d_faces, c.d_facegeo, (double*)c.d_fstar, c.nfaces_conf, c.E, c.gas, c.d_fv_mask);
+      k_face_lg<N, true, R><<<(int)((tot + 127) / 128), 128, 0, s>>>(
+          Uf, gf, c.d_faces, facegeo_of<R>(c), (R*)c.d_fstar, c.nfaces_conf, c.E, c.gas, c.d_fv_mask);
     else
-      k_face_lg<N, false><<<(int)((tot + 127) / 128), 128, 0, s>>>(
-          c.d_Uf, c.d_gf, c.d_faces, c.d_facegeo, (double*)c.d_fstar, c.nfaces_conf, c.E, c.gas, nullptr);
+      k_face_lg<N, false, R><<<(int)((tot + 127) / 128), 128, 0, s>>>(
+          Uf, gf, c.d_faces, facegeo_of<R>(c), (R*)c.d_fstar, c.nfaces_conf, c.E, c.gas, nullptr);
   }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && c.M > 0) e = launch_mortar_flux(c, nullptr, s);
@@ -728,20 +772,30 @@ static cudaError_t face_lg_N(const Ctx& c, cudaStream_t s) {
 }
 
 template <int N>
-static cudaError_t volume_lg_N(const Ctx& c, const StageArgs& a0, cudaStream_t s) {
+static cudaError_t face_lg_N(const Ctx& c, cudaStream_t s) {
+  return c.prm.precision == DG_FP32OP ? face_lg_NR<N, float>(c, s) : face_lg_NR<N, double>(c, s);
+}
+
+template <int N, typename R>
+static cudaError_t volume_lg_NR(const Ctx& c, const StageArgs& a0, cudaStream_t s) {
   using S = Shape<N>;
   StageArgs a = a0;
   a.nfaces = c.nfaces;
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
   if (a.list != nullptr)
-    k_volume_lg<N, S::EPB, true><<<blocks, S::THREADS, volume_lg_smem<N, S::EPB>(), s>>>(
-        a, c.d_metrics, (const double*)c.d_grad, (const double*)c.d_fstar, c.d_elem_face, c.d_mms, c.d_lgb, c.E,
-        c.gas);
+    k_volume_lg<N, S::EPB, true, R><<<blocks, S::THREADS, volume_lg_smem<N, S::EPB, R>(), s>>>(
+        a, metrics_of<R>(c), c.d_metrics, (const R*)c.d_grad, (const R*)c.d_fstar, c.d_elem_face, c.d_mms, c.d_lgb,
+        c.E, c.gas);
   else
-    k_volume_lg<N, S::EPB, false><<<blocks, S::THREADS, volume_lg_smem<N, S::EPB>(), s>>>(
-        a, c.d_metrics, (const double*)c.d_grad, (const double*)c.d_fstar, c.d_elem_face, c.d_mms, c.d_lgb, c.E,
-        c.gas);
+    k_volume_lg<N, S::EPB, false, R><<<blocks, S::THREADS, volume_lg_smem<N, S::EPB, R>(), s>>>(
+        a, metrics_of<R>(c), c.d_metrics, (const R*)c.d_grad, (const R*)c.d_fstar, c.d_elem_face, c.d_mms, c.d_lgb,
+        c.E, c.gas);
   return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t volume_lg_N(const Ctx& c, const StageArgs& a, cudaStream_t s) {
+  return c.prm.precision == DG_FP32OP ? volume_lg_NR<N, float>(c, a, s) : volume_lg_NR<N, double>(c, a, s);
 }
 
 #define DG_LG_DISPATCH(FN, ...)              \
@@ -774,7 +828,9 @@ cudaError_t setup_gauss(int N) {
 }
 
 cudaError_t gauss_geometry(Ctx& c, int* d_bad, cudaStream_t s) { DG_LG_DISPATCH(geometry_lg_N, c, d_bad, s) }
-cudaError_t launch_lift_lg(const Ctx& c, const double* U, cudaStream_t s) { DG_LG_DISPATCH(lift_lg_N, c, U, s) }
+cudaError_t launch_lift_lg(const Ctx& c, const double* U, cudaStream_t s, bool fp64) {
+  DG_LG_DISPATCH(lift_lg_N, c, U, s, fp64)
+}
 cudaError_t launch_face_lg(const Ctx& c, cudaStream_t s) { DG_LG_DISPATCH(face_lg_N, c, s) }
 cudaError_t launch_volume_lg(const Ctx& c, const StageArgs& a, cudaStream_t s) {
   DG_LG_DISPATCH(volume_lg_N, c, a, s)

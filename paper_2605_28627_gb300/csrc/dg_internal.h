@@ -204,7 +204,8 @@ double gauss_dt_factor(int N, const std::vector<double>& xl, const std::vector<d
                        const std::vector<double>& Dl, const std::vector<double>& tab);
 cudaError_t setup_gauss(int N);
 cudaError_t gauss_geometry(Ctx& c, int* d_bad, cudaStream_t s);
-cudaError_t launch_lift_lg(const Ctx& c, const double* U, cudaStream_t s);
+// fp64: the FP64 lifting whatever the operator type (diagnostics)
+cudaError_t launch_lift_lg(const Ctx& c, const double* U, cudaStream_t s, bool fp64 = false);
 cudaError_t launch_face_lg(const Ctx& c, cudaStream_t s);
 cudaError_t launch_volume_lg(const Ctx& c, const StageArgs& a, cudaStream_t s);
 cudaError_t setup_volume(int N);

@@ -99,7 +99,7 @@ cudaError_t launch_lift(const Ctx& c, const double* U, cudaStream_t s, bool late
   DG_DISPATCH(lift_N, c, U, c.prm.precision != DG_FP32OP, s)
 }
 cudaError_t launch_lift_fp64(const Ctx& c, const double* U, cudaStream_t s) {
-  if (c.prm.nodes == DG_NODES_LG) return launch_lift_lg(c, U, s);
+  if (c.prm.nodes == DG_NODES_LG) return launch_lift_lg(c, U, s, true);
   if (use_latency_kernels(c)) return launch_lift_lat(c, U, s);
   DG_DISPATCH(lift_N, c, U, true, s)
 }

@@ -36,6 +36,12 @@ __device__ __forceinline__ R to_op(double x) {
   }
 }
 
+// FP32 value -> operator type (identity for FP32; exact widening for FP64).
+template <typename R>
+__device__ __forceinline__ R to_op(float x) {
+  return static_cast<R>(x);
+}
+
 // Operator type -> FP64, exact for normal floats (zero and subnormals give
 // +-0); integer instructions only, as in to_op.
 __device__ __forceinline__ double to_f64(double x) { return x; }

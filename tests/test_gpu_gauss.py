@@ -121,14 +121,57 @@ def test_gauss_integrals_parity(orc, dg):
 
 def test_gauss_rejections(dg):
     mesh = box_mesh(2, 2)
-    with pytest.raises(dg.DGError):
-        dg.Solver(mesh, 2, nodes=dg.NODES_LG, precision=dg.FP32OP)
+    with pytest.raises(dg.DGError):   # the pressure offset is built for LGL nodes
+        dg.Solver(mesh, 2, nodes=dg.NODES_LG, precision=dg.FP32OP, p_ref=1.0)
     s = dg.Solver(mesh, 2, mu=0.01, nodes=dg.NODES_LG)
     U = torch.from_numpy(_state(mesh, 2, 5)).cuda()
     with pytest.raises(dg.DGError):
         s.time_derivative_vjp(U, torch.ones_like(U))
-    with pytest.raises(dg.DGError):
-        dg.Ensemble([s])
+    ens = dg.Ensemble([s])            # a Gauss-node member runs as a single-member unit
+    ens.step([U], [torch.empty_like(U)], [0.0], [1e-3])
+    ens.close()
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 7])
+@pytest.mark.parametrize("flux", [0, 1, 2])
+def test_gauss_fp32_operator_vs_oracle(orc, dg, N, flux):
+    """FP32 operator on Gauss nodes (prolongation, lifting, face fluxes and the
+    weak volume integral in FP32; state and RK update FP64) against the FP64
+    oracle: the FP32 operator's bar, 2e-5 of max |R| per variable."""
+    mesh = box_mesh(3 if N <= 4 else 2, N, deform="sinprod", rotate_seed=1100 + N)
+    o = orc.Oracle(mesh, N, mu=0.02, surf_flux=flux, nodes=1)
+    s = dg.Solver(mesh, N, mu=0.02, surf_flux=flux, nodes=dg.NODES_LG, precision=dg.FP32OP)
+    U = _state(mesh, N, 1200 + N)
+    got = s.time_derivative(_cuda(U)).cpu().numpy()
+    ref = o.time_derivative(U)
+    assert (_rel_err(got, ref) < 2e-5).all(), _rel_err(got, ref)
+
+
+def test_gauss_fp32_operator_tgv_steps_and_free_stream(orc, dg):
+    prm = tgv_params(Ma=0.1, Re=1600.0)
+    N = 3
+    mesh = box_mesh(4, 1, lo=0.0, hi=2 * math.pi)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], nodes=1)
+    o = orc.Oracle(mesh, N, **kw)
+    s = dg.Solver(mesh, N, precision=dg.FP32OP, **kw)
+    U0 = o.initial_state("tgv", prm["p0"])
+    Ud = _cuda(U0)
+    dt = s.max_dt(Ud)
+    ref = o.rk_steps(U0, 0.0, dt, 10)
+    s.rk_step(Ud, torch.empty_like(Ud), 0.0, dt, 10)
+    # state: FP32 rounding of the stage residuals relative to |U|; E_k as for the LGL FP32 operator
+    assert np.abs(Ud.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-6
+    ek_ref, ek = o.integrals(ref)[5], s.integrals(Ud)[5]
+    assert abs(ek - ek_ref) / ek_ref < 1e-6
+    # free stream: FP32 rounding of O(1) fluxes through the weak operator
+    m2 = box_mesh(3, 3, deform="sinprod", rotate_seed=7)
+    s2 = dg.Solver(m2, 4, mu=0.01, nodes=dg.NODES_LG, precision=dg.FP32OP)
+    U = np.zeros(s2.shape)
+    r, u, p = 1.2, np.array([0.3, -0.2, 0.45]), 0.9
+    U[:, 0] = r
+    U[:, 1:4] = (r * u)[None, :, None, None, None]
+    U[:, 4] = p / 0.4 + 0.5 * r * u @ u
+    assert float(s2.time_derivative(_cuda(U)).abs().max()) < 1e-3
 
 
 def _dg1d_radius(w, D, lm, lp, K=8):
