@@ -264,7 +264,8 @@ dg_status dg_geometry(dg_ctx* ctx, double* dJa, double* dJ, dg_stream stream);
  * log-mean switch follow the primal state; at a kink of the LLF speed maximum
  * the mean of the one-sided derivatives is taken).  The paper has no
  * adjoint; these entries exist for gradient-based use of the solver.  Built
- * for LGL nodes, the LLF and EC surface fluxes and constant or Sutherland
+ * for LGL nodes, all three surface fluxes (the Roe flux differentiated on
+ * dual numbers, its kinks by the value) and constant or Sutherland
  * viscosity (the derivative of mu(T) enters through the state) on a
  * conforming mesh without FV sub-cell elements, for both time schemes;
  * other contexts get DG_EUNSUPPORTED.

@@ -291,6 +291,8 @@ k_adj_face(const double* __restrict__ U, const double* __restrict__ grad, const 
       const double ua[3] = {pa[1], pa[2], pa[3]}, ubv[3] = {pb[1], pb[2], pb[3]};
       prim_vjp(qL, pa[0], ua, pa[4], g.gm1, qbL);
       prim_vjp(qR, pb[0], ubv, pb[4], g.gm1, qbR);
+    } else if (g.surf_flux == DG_FLUX_ROE) {
+      roe_vjp(qL, qR, nx, ny, nz, g.gamma, g.gm1, fa_b, qbL, qbR);
     } else {
       llf_vjp(qL, qR, nx, ny, nz, g.gamma, g.gm1, fa_b, qbL, qbR);
     }

@@ -37,8 +37,6 @@ static dg_status ensure_adjoint(Ctx* c) {
   if (c->M > 0) return afail(c, DG_EUNSUPPORTED, "the adjoint is built for conforming meshes");
   if (c->d_adj_qbar) return DG_OK;
   if (c->prm.precision != DG_FP64) return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the FP64 operator");
-  if (c->prm.surf_flux == DG_FLUX_ROE)
-    return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the LLF and entropy-conservative surface fluxes");
   if (c->prm.nodes != DG_NODES_LGL)
     return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the LGL operator");
   const size_t st = (size_t)c->E * 5 * c->P;

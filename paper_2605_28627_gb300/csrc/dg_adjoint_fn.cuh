@@ -179,6 +179,67 @@ __device__ __forceinline__ void llf_vjp(const double qL[5], const double qR[5], 
   }
 }
 
+// Forward-mode dual number (value, one directional derivative) to
+// differentiate the Roe flux mechanically: the templated forward flux runs on
+// it.  Kinks follow the value as in the oracle's dual numbers: |x| by the sign
+// of the value (derivative +1 at 0), max ties to its first argument.  In a
+// namespace of its own, found by argument-dependent lookup, so that sqrt,
+// fabs and fmax of doubles keep their meaning everywhere else.
+namespace ad {
+struct Dual {
+  double v, d;
+  __device__ Dual() : v(0.0), d(0.0) {}
+  __device__ Dual(double x) : v(x), d(0.0) {}
+  __device__ Dual(double x, double dx) : v(x), d(dx) {}
+};
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, fma(a.d, b.v, a.v * b.d)); }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
+  const double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+__device__ __forceinline__ bool operator<(Dual a, Dual b) { return a.v < b.v; }
+__device__ __forceinline__ bool operator>(Dual a, Dual b) { return a.v > b.v; }
+__device__ __forceinline__ Dual sqrt(Dual a) {
+  const double s = ::sqrt(a.v);
+  return Dual(s, a.d / (2.0 * s));
+}
+__device__ __forceinline__ Dual fabs(Dual a) { return a.v < 0.0 ? -a : a; }
+__device__ __forceinline__ Dual fmax(Dual a, Dual b) { return b.v > a.v ? b : a; }
+}  // namespace ad
+
+// Adjoint of the Roe flux with the Harten-Hyman entropy fix (roe_flux, FP64,
+// no pressure offset) w.r.t. both conserved states: ten forward passes on
+// dual numbers, one per input component, each contracted with fb.
+static __device__ __noinline__ void roe_vjp(const double qL[5], const double qR[5], double nx, double ny, double nz,
+                                     double gamma, double gm1, const double fb[5], double qbL[5], double qbR[5]) {
+  using ad::Dual;
+#pragma unroll 1
+  for (int k = 0; k < 10; ++k) {
+    Dual a[5], b[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      a[v] = Dual(qL[v], k == v ? 1.0 : 0.0);
+      b[v] = Dual(qR[v], k == 5 + v ? 1.0 : 0.0);
+    }
+    const Dual irL = Dual(1.0) / a[0], irR = Dual(1.0) / b[0];
+    const Dual uL = a[1] * irL, vL = a[2] * irL, wL = a[3] * irL;
+    const Dual uR = b[1] * irR, vR = b[2] * irR, wR = b[3] * irR;
+    const Dual pL = Dual(gm1) * (a[4] - Dual(0.5) * (a[1] * uL + a[2] * vL + a[3] * wL));
+    const Dual pR = Dual(gm1) * (b[4] - Dual(0.5) * (b[1] * uR + b[2] * vR + b[3] * wR));
+    Dual F[5];
+    roe_flux<Dual>(a, uL, vL, wL, pL, b, uR, vR, wR, pR, Dual(nx), Dual(ny), Dual(nz), Dual(gamma), Dual(gm1), F, pL,
+                   pR, b[0] - a[0]);
+    double s = 0.0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) s = fma(fb[v], F[v].d, s);
+    if (k < 5) qbL[k] += s;
+    else qbR[k - 5] += s;
+  }
+}
+
 // Viscosity factor s(T) = mu(T)/mu_ref and ds/dT: Sutherland's law
 // s = x^(3/2) (T_ref + S)/(T + S), x = T/T_ref, so ds/dT = s (3/(2T) - 1/(T + S));
 // s = 1, ds = 0 for constant viscosity.
