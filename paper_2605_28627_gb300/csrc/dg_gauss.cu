@@ -360,7 +360,7 @@ constexpr size_t lift_lg_smem() {
 //   - sum_d sum_m (w_m/w_{i_d}) D_{m i_d} (phi Ja^d_l)_m, phi* the face average;
 // then the face values of g for the face kernel.  R: the operator type (the
 // face values Uf, the metric terms, face geometry, g and its face values gf).
-// MORTAR (FP64): a face whose neighbour entry is negative is a mortar side,
+// MORTAR: a face whose neighbour entry is negative is a mortar side,
 // whose neighbour face state is mvirt[-1 - entry][5][NN] in its own point order.
 template <int N, int EPB, bool MORTAR = false, typename R = double>
 __global__ void __launch_bounds__(Shape<N, EPB>::THREADS)
@@ -673,7 +673,7 @@ static cudaError_t setup_lg_NR() {
   using S = Shape<N>;
   cudaError_t e = cudaFuncSetAttribute(k_lift_lg<N, S::EPB, false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)lift_lg_smem<N, S::EPB, R>());
-  if (e == cudaSuccess && sizeof(R) == 8)
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_lift_lg<N, S::EPB, true, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lift_lg_smem<N, S::EPB, R>());
   if (e == cudaSuccess)
@@ -731,15 +731,13 @@ static cudaError_t lift_lg_NR(const Ctx& c, const double* U, cudaStream_t s) {
   k_prolong_lg<N, S::EPB, R><<<blocks, S::THREADS, sizeof(R) * S::EPB * 5 * S::P, s>>>(U, c.d_lgb, Uf, c.E);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  if constexpr (sizeof(R) == 8) {
-    if (c.M > 0) {   // the mortar sides' neighbour face states first
-      err = launch_mortar_lift(c, U, s);
-      if (err != cudaSuccess) return err;
-      k_lift_lg<N, S::EPB, true, R><<<blocks, S::THREADS, lift_lg_smem<N, S::EPB, R>(), s>>>(
-          U, Uf, metrics_of<R>(c), facegeo_of<R>(c), c.d_elem_face, c.d_elem_nbr, c.d_lgb, (R*)c.d_grad, gf, c.E,
-          c.nfaces, c.gas, c.d_mortar_virt, c.M);
-      return cudaGetLastError();
-    }
+  if (c.M > 0) {   // the mortar sides' neighbour face states first
+    err = launch_mortar_lift(c, U, s);
+    if (err != cudaSuccess) return err;
+    k_lift_lg<N, S::EPB, true, R><<<blocks, S::THREADS, lift_lg_smem<N, S::EPB, R>(), s>>>(
+        U, Uf, metrics_of<R>(c), facegeo_of<R>(c), c.d_elem_face, c.d_elem_nbr, c.d_lgb, (R*)c.d_grad, gf, c.E,
+        c.nfaces, c.gas, c.d_mortar_virt, c.M);
+    return cudaGetLastError();
   }
   k_lift_lg<N, S::EPB, false, R><<<blocks, S::THREADS, lift_lg_smem<N, S::EPB, R>(), s>>>(
       U, Uf, metrics_of<R>(c), facegeo_of<R>(c), c.d_elem_face, c.d_elem_nbr, c.d_lgb, (R*)c.d_grad, gf, c.E,

@@ -133,11 +133,13 @@ __device__ __forceinline__ double mortar_proj2(const double* sW, const double* S
   return s;
 }
 
-// (u, v, w, T) of a conservative state
-__device__ __forceinline__ void lift_vars(const double* q, int st, const Gas& g, double ph[4]) {
-  const double ir = 1.0 / q[0];
-  const double u = q[st] * ir, v = q[2 * st] * ir, w = q[3 * st] * ir;
-  const double p = g.gm1 * (q[4 * st] - 0.5 * (q[st] * u + q[2 * st] * v + q[3 * st] * w));
+// (u, v, w, T) of a conservative state (FP64 or FP32 values), in FP64
+template <typename T>
+__device__ __forceinline__ void lift_vars(const T* q, int st, const Gas& g, double ph[4]) {
+  const double q0 = q[0], q1 = q[st], q2 = q[2 * st], q3 = q[3 * st], q4 = q[4 * st];
+  const double ir = 1.0 / q0;
+  const double u = q1 * ir, v = q2 * ir, w = q3 * ir;
+  const double p = g.gm1 * (q4 - 0.5 * (q1 * u + q2 * v + q3 * w));
   ph[0] = u;
   ph[1] = v;
   ph[2] = w;
@@ -153,9 +155,11 @@ __device__ __forceinline__ void encode_vars(const double ph[4], const Gas& g, do
   o[4 * st] = g.R * ph[3] * g.inv_gm1 + 0.5 * (ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
 }
 
-template <int N, bool FACE>
+// Q: the type of the state or face values read (FP32 face values with the FP32
+// operator on Gauss nodes).
+template <int N, bool FACE, typename Q = double>
 __global__ void __launch_bounds__(MortarShape<N>::THREADS)
-k_mortar_lift(const double* __restrict__ U, const int* __restrict__ mortars, const double* __restrict__ tab,
+k_mortar_lift(const Q* __restrict__ U, const int* __restrict__ mortars, const double* __restrict__ tab,
               double* __restrict__ virt, int E, Gas g) {
   using S = MortarShape<N>;
   constexpr int n = S::n, P = S::P, NN = S::NN, T = S::THREADS;
@@ -172,7 +176,7 @@ k_mortar_lift(const double* __restrict__ U, const int* __restrict__ mortars, con
   if (t < NN) {
     double ph[4];
     int st;
-    const double* q = side_ptr<n, FACE, 5>(U, eB, fB, t % n, t / n, st);
+    const Q* q = side_ptr<n, FACE, 5>(U, eB, fB, t % n, t / n, st);
     lift_vars(q, st, g, ph);
 #pragma unroll
     for (int a = 0; a < 4; ++a) sB[a * NN + t] = ph[a];
@@ -189,7 +193,7 @@ k_mortar_lift(const double* __restrict__ U, const int* __restrict__ mortars, con
     apply_flip<n>(fl, pp, qq, p2, q2);
     double ps[4];
     int st;
-    const double* q = side_ptr<n, FACE, 5>(U, es, fs, p2, q2, st);
+    const Q* q = side_ptr<n, FACE, 5>(U, es, fs, p2, q2, st);
     lift_vars(q, st, g, ps);
 #pragma unroll
     for (int a = 0; a < 4; ++a) sS[(k * 4 + a) * NN + pq] = 0.5 * (ps[a] + ib[a]);
@@ -209,9 +213,9 @@ k_mortar_lift(const double* __restrict__ U, const int* __restrict__ mortars, con
   }
 }
 
-template <int N, typename R, bool FACE>
+template <int N, typename R, bool FACE, typename Q = double>
 __global__ void __launch_bounds__(MortarShape<N>::THREADS)
-k_mortar_flux(const double* __restrict__ U, const R* __restrict__ grad, const R* __restrict__ facegeo,
+k_mortar_flux(const Q* __restrict__ U, const R* __restrict__ grad, const R* __restrict__ facegeo,
               const int* __restrict__ mortars, const double* __restrict__ tab, R* __restrict__ fstar, int E, int F,
               Gas g) {
   using S = MortarShape<N>;
@@ -228,10 +232,10 @@ k_mortar_flux(const double* __restrict__ U, const R* __restrict__ grad, const R*
   mortar_tables<n>(tab, sI, sIT, sW, sw, t, T);
   if (t < NN) {
     int su, sg;
-    const double* qb = side_ptr<n, FACE, 5>(U, eB, fB, t % n, t / n, su);
+    const Q* qb = side_ptr<n, FACE, 5>(U, eB, fB, t % n, t / n, su);
     const R* gb = side_ptr<n, FACE, 12>(grad, eB, fB, t % n, t / n, sg);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sB[v * NN + t] = qb[v * su];
+    for (int v = 0; v < 5; ++v) sB[v * NN + t] = (double)qb[v * su];
 #pragma unroll
     for (int x = 0; x < 12; ++x) sB[(5 + x) * NN + t] = (double)gb[x * sg];
   }
@@ -249,12 +253,12 @@ k_mortar_flux(const double* __restrict__ U, const R* __restrict__ grad, const R*
     apply_flip<n>(fl, pp, qq, p2, q2);
     const int o = p2 + n * q2;
     int su, sg;
-    const double* qs = side_ptr<n, FACE, 5>(U, es, fs, p2, q2, su);
+    const Q* qs = side_ptr<n, FACE, 5>(U, es, fs, p2, q2, su);
     const R* gs = side_ptr<n, FACE, 12>(grad, es, fs, p2, q2, sg);
     double dL[5];
     R gL[12], gR[12];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) dL[v] = qs[v * su];
+    for (int v = 0; v < 5; ++v) dL[v] = (double)qs[v * su];
 #pragma unroll
     for (int x = 0; x < 12; ++x) {
       gL[x] = gs[x * sg];
@@ -280,7 +284,10 @@ k_mortar_flux(const double* __restrict__ U, const R* __restrict__ grad, const R*
 
 template <int N>
 static cudaError_t mortar_lift_N(const Ctx& c, const double* U, cudaStream_t s) {
-  if (c.prm.nodes == DG_NODES_LG)
+  if (c.prm.nodes == DG_NODES_LG && c.prm.precision == DG_FP32OP)
+    k_mortar_lift<N, true, float><<<c.M, MortarShape<N>::THREADS, 0, s>>>(
+        reinterpret_cast<const float*>(c.d_Uf), c.d_mortars, c.d_mortar_tab, c.d_mortar_virt, c.E, c.gas);
+  else if (c.prm.nodes == DG_NODES_LG)
     k_mortar_lift<N, true><<<c.M, MortarShape<N>::THREADS, 0, s>>>(c.d_Uf, c.d_mortars, c.d_mortar_tab,
                                                                    c.d_mortar_virt, c.E, c.gas);
   else
@@ -292,7 +299,11 @@ static cudaError_t mortar_lift_N(const Ctx& c, const double* U, cudaStream_t s) 
 template <int N>
 static cudaError_t mortar_flux_N(const Ctx& c, const double* U, cudaStream_t s) {
   constexpr int T = MortarShape<N>::THREADS;
-  if (c.prm.nodes == DG_NODES_LG)   // FP64 only: the face values of the state and gradients
+  if (c.prm.nodes == DG_NODES_LG && c.prm.precision == DG_FP32OP)   // FP32 face values
+    k_mortar_flux<N, float, true, float><<<c.M, T, 0, s>>>(
+        reinterpret_cast<const float*>(c.d_Uf), reinterpret_cast<const float*>(c.d_gf), c.d_facegeo_f, c.d_mortars,
+        c.d_mortar_tab, (float*)c.d_fstar, c.E, c.nfaces, c.gas);
+  else if (c.prm.nodes == DG_NODES_LG)   // the face values of the state and gradients
     k_mortar_flux<N, double, true><<<c.M, T, 0, s>>>(c.d_Uf, c.d_gf, c.d_facegeo, c.d_mortars, c.d_mortar_tab,
                                                      (double*)c.d_fstar, c.E, c.nfaces, c.gas);
   else if (c.prm.precision == DG_FP32OP)

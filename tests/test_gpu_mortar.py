@@ -172,10 +172,21 @@ def test_mortar_free_stream_and_conservation_gauss_nodes(orc, dg):
     assert bool((tot.abs() <= 1e-13 * scale).all()), (tot, scale)
 
 
+@pytest.mark.parametrize("N", [2, 3, 5])
+def test_mortar_fp32_operator_gauss_nodes_vs_oracle(orc, dg, N):
+    """FP32 operator on Gauss nodes (FP32 face values, FP64 maps) with
+    mortars: R(U) within the FP32 operator's bar."""
+    K = 3
+    mesh = refined_box_mesh(K, _refine(K, [0, 13]), rotate_seed=190 + N)
+    o = orc.Oracle(mesh, N, mu=0.02, nodes=1)
+    s = dg.Solver(mesh, N, mu=0.02, nodes=dg.NODES_LG, precision=dg.FP32OP)
+    U = random_state(mesh.n_elems, N, seed=200 + N, **_GAUSS_STATE)
+    err = _rel_err_per_var(s.time_derivative(_cuda(U)).cpu().numpy(), o.time_derivative(U))
+    assert (err < 2e-5).all(), err
+
+
 def test_mortar_rejections(dg):
     mesh = refined_box_mesh(2, _refine(2, [0]))
-    with pytest.raises(dg.DGError):
-        dg.Solver(mesh, 2, nodes=1, precision=dg.FP32OP)
     s = dg.Solver(mesh, 2, mu=0.01)
     U = _cuda(random_state(mesh.n_elems, 2, seed=1))
     with pytest.raises(dg.DGError):
