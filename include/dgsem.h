@@ -129,8 +129,7 @@ typedef struct {
  * metric terms are those of the LGL construction evaluated at the Gauss nodes
  * and face points (Sec. 3.1 leaves this open).  Synchronous.
  * Errors: DG_EINVAL (null/size, unknown option, constants out of range),
- * DG_EUNSUPPORTED (N outside 1..9; Gauss nodes with DG_FP32OP and p_ref != 0:
- * the pressure offset is built for LGL nodes), DG_EMESH
+ * DG_EUNSUPPORTED (N outside 1..9), DG_EMESH
  * (connectivity out of range or not reciprocal, Jacobian <= 0 at a node),
  * DG_ENOMEM, DG_ECUDA.  On failure *out is NULL. */
 dg_status dg_init(const dg_mesh* mesh, const dg_params* prm, int device, dg_ctx** out);

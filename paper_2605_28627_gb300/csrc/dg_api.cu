@@ -196,8 +196,6 @@ static dg_status init_impl(const dg_mesh* mesh, const dg_params* prm, int device
     return fail(nullptr, DG_EINVAL, "dg_init: unknown Runge-Kutta scheme");
   if (prm->nodes != DG_NODES_LGL && prm->nodes != DG_NODES_LG)
     return fail(nullptr, DG_EINVAL, "dg_init: unknown node set");
-  if (prm->nodes == DG_NODES_LG && prm->precision == DG_FP32OP && prm->p_ref != 0.0)
-    return fail(nullptr, DG_EUNSUPPORTED, "dg_init: the pressure offset p_ref is built for LGL nodes");
   if (prm->visc_law != DG_VISC_CONSTANT && prm->visc_law != DG_VISC_SUTHERLAND)
     return fail(nullptr, DG_EINVAL, "dg_init: unknown viscosity law");
   if (prm->visc_law == DG_VISC_SUTHERLAND && (!(prm->T_ref > 0.0) || !(prm->S_suth >= 0.0)))

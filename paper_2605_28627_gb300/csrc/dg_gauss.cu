@@ -310,9 +310,13 @@ k_geometry_to_gauss(double* __restrict__ X, double* __restrict__ metrics, double
 // Face values of U: Uf[e][f][v][p + n q] = sum_i l_i(+-1) U(line of (p, q)),
 // in the operator type R (the FP32 operator prolongs FP32 values: an FP64
 // prolongation would take the FP64 pipe for more than the whole FP32 stage).
+// The FP32 operator prolongs the energy as E - E_ref (E_ref = p_ref/(gamma-1),
+// the difference taken in FP64 per node), so that the face values keep the
+// digits of the pressure fluctuation at low Mach numbers; its readers add
+// E_ref back where they need the whole energy.
 template <int N, int EPB, typename R = double>
 __global__ void __launch_bounds__(Shape<N, EPB>::THREADS)
-k_prolong_lg(const double* __restrict__ U, const double* __restrict__ tab, R* __restrict__ Uf, int E) {
+k_prolong_lg(const double* __restrict__ U, const double* __restrict__ tab, R* __restrict__ Uf, int E, double E_off) {
   using S = Shape<N, EPB>;
   constexpr int n = S::n, P = S::P, NN = n * n;
   extern __shared__ __align__(16) unsigned char prolong_raw[];
@@ -322,7 +326,7 @@ k_prolong_lg(const double* __restrict__ U, const double* __restrict__ tab, R* __
   const int e = blockIdx.x * EPB + le;
   for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) sl[t] = to_op<R>(tab[GaussTab::lm(n) + t]);
   if (e < E)
-    for (int v = 0; v < 5; ++v) sm[(le * 5 + v) * P + id] = to_op<R>(U[((size_t)e * 5 + v) * P + id]);
+    for (int v = 0; v < 5; ++v) sm[(le * 5 + v) * P + id] = to_op<R>(U[((size_t)e * 5 + v) * P + id] - (v == 4 ? E_off : 0.0));
   __syncthreads();
   if (e >= E) return;
   for (int o = id; o < 30 * NN; o += P) {
@@ -337,13 +341,14 @@ k_prolong_lg(const double* __restrict__ U, const double* __restrict__ tab, R* __
   }
 }
 
-// Lifting variables (u, v, w, T) of a state given with stride st, in R.
+// Lifting variables (u, v, w, T) of a state given with stride st, in R; p_off
+// is added to the pressure (p_ref for face values that carry E - E_ref).
 template <typename R, typename Q>
-__device__ __forceinline__ void state_phi(const Q* q, int st, const Gas& g, R ph[4]) {
+__device__ __forceinline__ void state_phi(const Q* q, int st, const Gas& g, R ph[4], R p_off = R(0)) {
   const R rho = to_op<R>(q[0]), ir = rcp_op(rho);
   const R m0 = to_op<R>(q[st]), m1 = to_op<R>(q[2 * st]), m2 = to_op<R>(q[3 * st]);
   const R u = m0 * ir, v = m1 * ir, w = m2 * ir;
-  const R p = gsel<R>(g.gm1, g.f_gm1) * (to_op<R>(q[4 * st]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
+  const R p = p_off + gsel<R>(g.gm1, g.f_gm1) * (to_op<R>(q[4 * st]) - R(0.5) * (m0 * u + m1 * v + m2 * w));
   ph[0] = u;
   ph[1] = v;
   ph[2] = w;
@@ -398,7 +403,8 @@ k_lift_lg(const double* __restrict__ U, const R* __restrict__ Uf, const R* __res
       apply_flip<n>(code & 7, p, q, p2, q2);
       const int pq2 = p2 + n * q2;
       R pm[4], pn[4];
-      state_phi<R>(Uf + ((size_t)e * 6 + f) * 5 * NN + pq, NN, g, pm);
+      const R poff = sizeof(R) == 4 ? gsel<R>(g.p_ref, g.f_p_ref) : R(0);   // face values carry E - E_ref
+      state_phi<R>(Uf + ((size_t)e * 6 + f) * 5 * NN + pq, NN, g, pm, poff);
       bool done = false;
       if constexpr (MORTAR) {
         if (nb < 0) {
@@ -408,7 +414,7 @@ k_lift_lg(const double* __restrict__ U, const R* __restrict__ Uf, const R* __res
       }
       if (!done) {
         const int e2 = dg_idx(nb >> 3, E, kSiteGaussLift), f2 = nb & 7;
-        state_phi<R>(Uf + ((size_t)e2 * 6 + f2) * 5 * NN + pq2, NN, g, pn);
+        state_phi<R>(Uf + ((size_t)e2 * 6 + f2) * 5 * NN + pq2, NN, g, pn, poff);
       }
       const bool master = code & 8;
       const R* fg = facegeo + (size_t)fid * 4 * NN + (master ? pq : pq2);
@@ -519,6 +525,10 @@ k_face_lg(const R* __restrict__ Uf, const R* __restrict__ gf, const FaceInfo* __
     dL[v] = to_f64(uM[v * NN]);
     dR[v] = to_f64(uS[v * NN]);
   }
+  if constexpr (sizeof(R) == 4) {   // the FP32 face values carry E - E_ref
+    dL[4] += g.E_ref;
+    dR[4] += g.E_ref;
+  }
   const R* gM = gf + ((size_t)eM * 6 + fM) * 12 * NN + pq;
   const R* gS = gf + ((size_t)eS * 6 + fS) * 12 * NN + pq2;
 #pragma unroll
@@ -586,6 +596,9 @@ k_volume_lg(StageArgs a, const R* __restrict__ metrics, const double* __restrict
     const R ir = rcp_op(qo[0]);
     const R u = qo[1] * ir, v = qo[2] * ir, w = qo[3] * ir;
     const R p = gsel<R>(g.gm1, g.f_gm1) * (qo[4] - R(0.5) * (qo[1] * u + qo[2] * v + qo[3] * w));
+    R pmom = p;
+    if constexpr (sizeof(R) == 4)
+      pmom = g.f_gm1 * (to_op<R>(q[4] - g.E_ref) - R(0.5) * (qo[1] * u + qo[2] * v + qo[3] * w));
     R mu = gsel<R>(g.mu, g.f_mu), lam = gsel<R>(g.mu * g.kappa, g.f_lam);
     if (g.visc_law == DG_VISC_SUTHERLAND) {
       const R sf = visc_factor<R>(g, p * ir * gsel<R>(g.inv_R, g.f_inv_R));
@@ -596,7 +609,10 @@ k_volume_lg(StageArgs a, const R* __restrict__ metrics, const double* __restrict
     for (int d = 0; d < 3; ++d) {
       const R nx = mt[(d * 3) * P], ny = mt[(d * 3 + 1) * P], nz = mt[(d * 3 + 2) * P];
       R fa[5], fv[4];
-      euler_flux<R>(qo, u, v, w, p, nx, ny, nz, fa);
+      if constexpr (sizeof(R) == 4)   // p - p_ref in the momentum flux, from the FP64 energy difference
+        euler_flux_pm<R>(qo, u, v, w, p, pmom, nx, ny, nz, fa);
+      else
+        euler_flux<R>(qo, u, v, w, p, nx, ny, nz, fa);
       visc_flux<R>(gr, u, v, w, mu, lam, nx, ny, nz, fv);
       sF[(d * 5) * P + id] = fa[0];
 #pragma unroll
@@ -728,7 +744,8 @@ static cudaError_t lift_lg_NR(const Ctx& c, const double* U, cudaStream_t s) {
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
   R* Uf = reinterpret_cast<R*>(c.d_Uf);
   R* gf = reinterpret_cast<R*>(c.d_gf);
-  k_prolong_lg<N, S::EPB, R><<<blocks, S::THREADS, sizeof(R) * S::EPB * 5 * S::P, s>>>(U, c.d_lgb, Uf, c.E);
+  k_prolong_lg<N, S::EPB, R><<<blocks, S::THREADS, sizeof(R) * S::EPB * 5 * S::P, s>>>(
+      U, c.d_lgb, Uf, c.E, sizeof(R) == 4 ? c.gas.E_ref : 0.0);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   if (c.M > 0) {   // the mortar sides' neighbour face states first

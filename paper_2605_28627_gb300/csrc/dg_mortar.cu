@@ -133,10 +133,11 @@ __device__ __forceinline__ double mortar_proj2(const double* sW, const double* S
   return s;
 }
 
-// (u, v, w, T) of a conservative state (FP64 or FP32 values), in FP64
+// (u, v, w, T) of a conservative state (FP64 or FP32 values), in FP64; E_off
+// is added to the energy (E_ref for FP32 face values that carry E - E_ref)
 template <typename T>
-__device__ __forceinline__ void lift_vars(const T* q, int st, const Gas& g, double ph[4]) {
-  const double q0 = q[0], q1 = q[st], q2 = q[2 * st], q3 = q[3 * st], q4 = q[4 * st];
+__device__ __forceinline__ void lift_vars(const T* q, int st, const Gas& g, double ph[4], double E_off = 0.0) {
+  const double q0 = q[0], q1 = q[st], q2 = q[2 * st], q3 = q[3 * st], q4 = (double)q[4 * st] + E_off;
   const double ir = 1.0 / q0;
   const double u = q1 * ir, v = q2 * ir, w = q3 * ir;
   const double p = g.gm1 * (q4 - 0.5 * (q1 * u + q2 * v + q3 * w));
@@ -177,7 +178,7 @@ k_mortar_lift(const Q* __restrict__ U, const int* __restrict__ mortars, const do
     double ph[4];
     int st;
     const Q* q = side_ptr<n, FACE, 5>(U, eB, fB, t % n, t / n, st);
-    lift_vars(q, st, g, ph);
+    lift_vars(q, st, g, ph, sizeof(Q) == 4 ? g.E_ref : 0.0);
 #pragma unroll
     for (int a = 0; a < 4; ++a) sB[a * NN + t] = ph[a];
   }
@@ -194,7 +195,7 @@ k_mortar_lift(const Q* __restrict__ U, const int* __restrict__ mortars, const do
     double ps[4];
     int st;
     const Q* q = side_ptr<n, FACE, 5>(U, es, fs, p2, q2, st);
-    lift_vars(q, st, g, ps);
+    lift_vars(q, st, g, ps, sizeof(Q) == 4 ? g.E_ref : 0.0);
 #pragma unroll
     for (int a = 0; a < 4; ++a) sS[(k * 4 + a) * NN + pq] = 0.5 * (ps[a] + ib[a]);
     encode_vars(ib, g, virt + (size_t)(5 * m + k) * 5 * NN + p2 + n * q2, NN);
@@ -236,6 +237,7 @@ k_mortar_flux(const Q* __restrict__ U, const R* __restrict__ grad, const R* __re
     const R* gb = side_ptr<n, FACE, 12>(grad, eB, fB, t % n, t / n, sg);
 #pragma unroll
     for (int v = 0; v < 5; ++v) sB[v * NN + t] = (double)qb[v * su];
+    if (sizeof(Q) == 4) sB[4 * NN + t] += g.E_ref;   // FP32 face values carry E - E_ref
 #pragma unroll
     for (int x = 0; x < 12; ++x) sB[(5 + x) * NN + t] = (double)gb[x * sg];
   }
@@ -259,6 +261,7 @@ k_mortar_flux(const Q* __restrict__ U, const R* __restrict__ grad, const R* __re
     R gL[12], gR[12];
 #pragma unroll
     for (int v = 0; v < 5; ++v) dL[v] = (double)qs[v * su];
+    if (sizeof(Q) == 4) dL[4] += g.E_ref;
 #pragma unroll
     for (int x = 0; x < 12; ++x) {
       gL[x] = gs[x * sg];

@@ -72,16 +72,17 @@ def test_fp32_free_stream(dg):
     assert np.abs(R).max() < 1e-3
 
 
-@pytest.mark.parametrize("flux", [0, 1, 2])
-def test_fp32_pressure_offset_low_mach(orc, dg, flux):
+@pytest.mark.parametrize("flux,nodes", [(0, 0), (1, 0), (2, 0), (0, 1), (2, 1)])
+def test_fp32_pressure_offset_low_mach(orc, dg, flux, nodes):
     """The FP32 operator with the background pressure p_ref taken out of the
     momentum flux returns the same R(U) (the constant part has no discrete
     divergence), with momentum rounding errors set by p - p_ref instead of p:
-    at Ma 0.1 (p0 = 71) at least five times smaller."""
+    at Ma 0.1 (p0 = 71) at least five times smaller.  On Gauss nodes the FP32
+    face values carry E - E_ref (prolonged from the FP64 difference)."""
     prm = tgv_params(Ma=0.1, Re=1600.0)
     N = 5
     mesh = box_mesh(3, N, lo=0.0, hi=2 * math.pi, deform="sinprod", amp=0.05, rotate_seed=31)
-    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], surf_flux=flux)
+    kw = dict(gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], surf_flux=flux, nodes=nodes)
     o = orc.Oracle(mesh, N, **kw)
     U0 = o.initial_state("tgv", prm["p0"])
     ref = o.time_derivative(U0).reshape(mesh.n_elems, 5, -1)
@@ -92,9 +93,12 @@ def test_fp32_pressure_offset_low_mach(orc, dg, flux):
         errs[p_ref] = [np.abs(got[:, v] - ref[:, v]).max() / np.abs(ref[:, v]).max() for v in range(5)]
         s.close()
     e0, e1 = errs[0.0], errs[prm["p0"]]
-    # momentum: the offset removes the rounding of p0 from the pressure terms
+    # momentum: the offset removes the rounding of p0 from the pressure terms;
+    # on Gauss nodes the face values are FP32 interpolations, whose rounding
+    # enters the dissipation through the jumps (|lambda| ~ c = 10 at Ma 0.1)
+    cap = 1e-4 if nodes == 0 else 3e-4
     for v in (1, 2, 3):
-        assert e1[v] < 0.2 * e0[v] and e1[v] < 1e-4, (v, e0, e1)
+        assert e1[v] < 0.2 * e0[v] and e1[v] < cap, (v, e0, e1)
     # density and energy: unchanged by the offset (their relative errors are
     # large at low Mach numbers because R is O(Ma^2) smaller than its terms)
     for v in (0, 4):

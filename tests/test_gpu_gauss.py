@@ -121,8 +121,6 @@ def test_gauss_integrals_parity(orc, dg):
 
 def test_gauss_rejections(dg):
     mesh = box_mesh(2, 2)
-    with pytest.raises(dg.DGError):   # the pressure offset is built for LGL nodes
-        dg.Solver(mesh, 2, nodes=dg.NODES_LG, precision=dg.FP32OP, p_ref=1.0)
     s = dg.Solver(mesh, 2, mu=0.01, nodes=dg.NODES_LG)
     U = torch.from_numpy(_state(mesh, 2, 5)).cuda()
     with pytest.raises(dg.DGError):
