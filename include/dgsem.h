@@ -92,8 +92,8 @@ enum { DG_IND_RHO = 0, DG_IND_P = 1, DG_IND_RHOP = 2 };   /* quantity of the tro
  *       face_nbr[eS_k][fS_k] = (-1 - m, k, 0).  The quadrants must be the
  *       exact quarters of the big face (affine faces).  n_mortars = 0 and
  *       mortars = NULL for a conforming mesh.  Either node set (the maps use
- *       its basis and quadrature); the FV sub-cell operator and the adjoint
- *       need a conforming mesh.
+ *       its basis and quadrature); the FV sub-cell operator needs a
+ *       conforming mesh.
  */
 typedef struct {
   int32_t n_elems;
@@ -264,9 +264,10 @@ dg_status dg_geometry(dg_ctx* ctx, double* dJa, double* dJ, dg_stream stream);
  * adjoint; these entries exist for gradient-based use of the solver.  Built
  * for LGL nodes, all three surface fluxes (the Roe flux differentiated on
  * dual numbers, its kinks by the value) and constant or Sutherland
- * viscosity (the derivative of mu(T) enters through the state) on a
- * conforming mesh without FV sub-cell elements, for both time schemes;
- * other contexts get DG_EUNSUPPORTED.
+ * viscosity (the derivative of mu(T) enters through the state) on
+ * conforming or 2:1 mortar meshes (the transposes of the mortars'
+ * interpolation and projection) without FV sub-cell elements, for both time
+ * schemes; other contexts get DG_EUNSUPPORTED.
  * dJdmu, where present, is a device double that is ACCUMULATED (+=) with
  * lambda . dR/dmu, mu the constant viscosity or Sutherland's reference
  * viscosity (R is linear in it); NULL skips it. */

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "dg_adjoint_fn.cuh"
+#include "dg_mortar.cuh"
 #include "dg_stage.cuh"
 
 namespace dg {
@@ -30,6 +31,8 @@ struct AdjBufs {
   double* gtil;      // [E][12][P]  total gradient adjoint / J
   double* mupart;    // block partials of d/dmu
   int n_mu;
+  double* mx;        // [M][5][4][NN] mortar sides' terms of the lifting transpose (own point order)
+  int F;             // face slots (conforming faces, then the mortars' slots)
 };
 
 // ---------------------------------------------------------------------------
@@ -217,7 +220,7 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
       const int id_d = ijk[d];
       if (id_d != 0 && id_d != N) continue;
       const int code = elem_face[e * 6 + 2 * d + (id_d == N ? 1 : 0)];
-      const int fid = dg_idx(code >> 4, 3L * E, kSiteAdjFace);
+      const int fid = dg_idx(code >> 4, b.F, kSiteAdjFace);
       const int pp = d == 0 ? j : i;
       const int qq = d == 2 ? j : k;
       if (code & 8) {
@@ -245,11 +248,63 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
 }
 
 // ---------------------------------------------------------------------------
-// A2: face adjoint, one thread per face node (master orientation).
+// Face VJP at one face point: from the adjoint Fb of F* (F* = (f* - f_v avg) sJ)
+// to the conserved (5) and gradient (12) adjoints of the two sides, added to
+// qbL, gbL (side L, whose outward normal (nx, ny, nz) is) and qbR, gbR; returns
+// the d/dmu contribution.
+__device__ __forceinline__ double face_vjp_point(const double qL[5], const double qR[5], const double gL[12],
+                                                 const double gR[12], double nx, double ny, double nz, double sJ,
+                                                 const double Fb[5], const Gas& g, double qbL[5], double qbR[5],
+                                                 double gbL[12], double gbR[12]) {
+  double fa_b[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) fa_b[c] = Fb[c] * sJ;
+  if (g.surf_flux == DG_FLUX_EC) {
+    const double irL = 1.0 / qL[0], irR = 1.0 / qR[0];
+    NodePrim<double> A{qL[0], qL[1] * irL, qL[2] * irL, qL[3] * irL, 0, 0};
+    A.p = g.gm1 * (qL[4] - 0.5 * (qL[1] * A.u + qL[2] * A.v + qL[3] * A.w));
+    A.beta = 0.5 * qL[0] / A.p;
+    NodePrim<double> B{qR[0], qR[1] * irR, qR[2] * irR, qR[3] * irR, 0, 0};
+    B.p = g.gm1 * (qR[4] - 0.5 * (qR[1] * B.u + qR[2] * B.v + qR[3] * B.w));
+    B.beta = 0.5 * qR[0] / B.p;
+    double pa[5] = {0, 0, 0, 0, 0}, pb[5] = {0, 0, 0, 0, 0};
+    ec_flux_vjp(A, B, nx, ny, nz, g.inv_gm1, fa_b, pa, pb);
+    const double ua[3] = {pa[1], pa[2], pa[3]}, ubv[3] = {pb[1], pb[2], pb[3]};
+    prim_vjp(qL, pa[0], ua, pa[4], g.gm1, qbL);
+    prim_vjp(qR, pb[0], ubv, pb[4], g.gm1, qbR);
+  } else if (g.surf_flux == DG_FLUX_ROE) {
+    roe_vjp(qL, qR, nx, ny, nz, g.gamma, g.gm1, fa_b, qbL, qbR);
+  } else {
+    llf_vjp(qL, qR, nx, ny, nz, g.gamma, g.gm1, fa_b, qbL, qbR);
+  }
+  // viscous part: F* includes -1/2 (f_v(L) + f_v(R)) . n sJ
+  double fvb[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) fvb[c] = -0.5 * Fb[1 + c] * sJ;
+  double ubL[3] = {0, 0, 0}, ubR[3] = {0, 0, 0};
+  const double irL = 1.0 / qL[0], irR = 1.0 / qR[0];
+  // viscosity law on each side: mu = mu_ref s(T), T = p / (rho R)
+  const double uL = qL[1] * irL, vL = qL[2] * irL, wL = qL[3] * irL;
+  const double uR = qR[1] * irR, vR = qR[2] * irR, wR = qR[3] * irR;
+  const double TL = g.gm1 * (qL[4] - 0.5 * (qL[1] * uL + qL[2] * vL + qL[3] * wL)) * irL * g.inv_R;
+  const double TR = g.gm1 * (qR[4] - 0.5 * (qR[1] * uR + qR[2] * vR + qR[3] * wR)) * irR * g.inv_R;
+  double sL, dsL, sR, dsR;
+  visc_factor_d(g, TL, sL, dsL);
+  visc_factor_d(g, TR, sR, dsR);
+  const double vrL = visc_flux_vjp(gL, uL, vL, wL, g.mu * sL, g.kappa, nx, ny, nz, fvb, gbL, ubL);
+  const double vrR = visc_flux_vjp(gR, uR, vR, wR, g.mu * sR, g.kappa, nx, ny, nz, fvb, gbR, ubR);
+  const double TbL = g.mu * dsL * vrL, TbR = g.mu * dsR * vrR;   // through T = p / (rho R)
+  prim_vjp(qL, -TbL * TL * irL, ubL, TbL * g.inv_R * irL, g.gm1, qbL);
+  prim_vjp(qR, -TbR * TR * irR, ubR, TbR * g.inv_R * irR, g.gm1, qbR);
+  return sL * vrL + sR * vrR;
+}
+
+// A2: face adjoint, one thread per face node of the conforming faces (master
+// orientation); the mortars' slots follow them (k_adj_mortar_face).
 template <int N>
 __global__ void __launch_bounds__(128)
 k_adj_face(const double* __restrict__ U, const double* __restrict__ grad, const FaceInfo* __restrict__ faces,
-           const double* __restrict__ facegeo, int F, Gas g, AdjBufs b, int mu_offset) {
+           const double* __restrict__ facegeo, int F, int E, Gas g, AdjBufs b, int mu_offset) {
   constexpr int n = N + 1, P = n * n * n, NN = n * n;
   __shared__ double smu[4];
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -258,8 +313,8 @@ k_adj_face(const double* __restrict__ U, const double* __restrict__ grad, const 
     const int f = (int)(gid / NN), pq = (int)(gid % NN);
     const int p = pq % n, q = pq / n;
     const FaceInfo fi = faces[f];
-    const int eM = dg_idx(fi.master >> 3, F / 3, kSiteAdjFace), fM = fi.master & 7;
-    const int eS = dg_idx(fi.slave >> 3, F / 3, kSiteAdjFace), fS = fi.slave & 7;
+    const int eM = dg_idx(fi.master >> 3, E, kSiteAdjFace), fM = fi.master & 7;
+    const int eS = dg_idx(fi.slave >> 3, E, kSiteAdjFace), fS = fi.slave & 7;
     int p2, q2;
     apply_flip<n>(fi.flip, p, q, p2, q2);
     const int idM = face_node<n>(fM, p, q), idS = face_node<n>(fS, p2, q2);
@@ -273,33 +328,6 @@ k_adj_face(const double* __restrict__ U, const double* __restrict__ grad, const 
       Fb[c] = s0[c * NN] + s1[c * NN];
     }
     const double* fg = facegeo + (size_t)f * 4 * NN + pq;
-    const double nx = fg[0], ny = fg[NN], nz = fg[2 * NN], sJ = fg[3 * NN];
-    double fa_b[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) fa_b[c] = Fb[c] * sJ;
-    double qbL[5] = {0, 0, 0, 0, 0}, qbR[5] = {0, 0, 0, 0, 0};
-    if (g.surf_flux == DG_FLUX_EC) {
-      const double irL = 1.0 / qL[0], irR = 1.0 / qR[0];
-      NodePrim<double> A{qL[0], qL[1] * irL, qL[2] * irL, qL[3] * irL, 0, 0};
-      A.p = g.gm1 * (qL[4] - 0.5 * (qL[1] * A.u + qL[2] * A.v + qL[3] * A.w));
-      A.beta = 0.5 * qL[0] / A.p;
-      NodePrim<double> B{qR[0], qR[1] * irR, qR[2] * irR, qR[3] * irR, 0, 0};
-      B.p = g.gm1 * (qR[4] - 0.5 * (qR[1] * B.u + qR[2] * B.v + qR[3] * B.w));
-      B.beta = 0.5 * qR[0] / B.p;
-      double pa[5] = {0, 0, 0, 0, 0}, pb[5] = {0, 0, 0, 0, 0};
-      ec_flux_vjp(A, B, nx, ny, nz, g.inv_gm1, fa_b, pa, pb);
-      const double ua[3] = {pa[1], pa[2], pa[3]}, ubv[3] = {pb[1], pb[2], pb[3]};
-      prim_vjp(qL, pa[0], ua, pa[4], g.gm1, qbL);
-      prim_vjp(qR, pb[0], ubv, pb[4], g.gm1, qbR);
-    } else if (g.surf_flux == DG_FLUX_ROE) {
-      roe_vjp(qL, qR, nx, ny, nz, g.gamma, g.gm1, fa_b, qbL, qbR);
-    } else {
-      llf_vjp(qL, qR, nx, ny, nz, g.gamma, g.gm1, fa_b, qbL, qbR);
-    }
-    // viscous part: F* includes -1/2 (f_v(L) + f_v(R)) . n sJ
-    double fvb[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) fvb[c] = -0.5 * Fb[1 + c] * sJ;
     double gL[12], gR[12], gbL[12], gbR[12];
 #pragma unroll
     for (int r = 0; r < 12; ++r) {
@@ -308,22 +336,8 @@ k_adj_face(const double* __restrict__ U, const double* __restrict__ grad, const 
       gbL[r] = 0.0;
       gbR[r] = 0.0;
     }
-    double ubL[3] = {0, 0, 0}, ubR[3] = {0, 0, 0};
-    const double irL = 1.0 / qL[0], irR = 1.0 / qR[0];
-    // viscosity law on each side: mu = mu_ref s(T), T = p / (rho R)
-    const double uL = qL[1] * irL, vL = qL[2] * irL, wL = qL[3] * irL;
-    const double uR = qR[1] * irR, vR = qR[2] * irR, wR = qR[3] * irR;
-    const double TL = g.gm1 * (qL[4] - 0.5 * (qL[1] * uL + qL[2] * vL + qL[3] * wL)) * irL * g.inv_R;
-    const double TR = g.gm1 * (qR[4] - 0.5 * (qR[1] * uR + qR[2] * vR + qR[3] * wR)) * irR * g.inv_R;
-    double sL, dsL, sR, dsR;
-    visc_factor_d(g, TL, sL, dsL);
-    visc_factor_d(g, TR, sR, dsR);
-    const double vrL = visc_flux_vjp(gL, uL, vL, wL, g.mu * sL, g.kappa, nx, ny, nz, fvb, gbL, ubL);
-    const double vrR = visc_flux_vjp(gR, uR, vR, wR, g.mu * sR, g.kappa, nx, ny, nz, fvb, gbR, ubR);
-    mub += sL * vrL + sR * vrR;
-    const double TbL = g.mu * dsL * vrL, TbR = g.mu * dsR * vrR;   // through T = p / (rho R)
-    prim_vjp(qL, -TbL * TL * irL, ubL, TbL * g.inv_R * irL, g.gm1, qbL);
-    prim_vjp(qR, -TbR * TR * irR, ubR, TbR * g.inv_R * irR, g.gm1, qbR);
+    double qbL[5] = {0, 0, 0, 0, 0}, qbR[5] = {0, 0, 0, 0, 0};
+    mub = face_vjp_point(qL, qR, gL, gR, fg[0], fg[NN], fg[2 * NN], fg[3 * NN], Fb, g, qbL, qbR, gbL, gbR);
     double* oL = b.face + ((size_t)f * 2 + 0) * 17 * NN + pq;
     double* oR = b.face + ((size_t)f * 2 + 1) * 17 * NN + pq;
 #pragma unroll
@@ -337,7 +351,186 @@ k_adj_face(const double* __restrict__ U, const double* __restrict__ grad, const 
   if (threadIdx.x == 0) b.mupart[mu_offset + blockIdx.x] = smu[0] + smu[1] + smu[2] + smu[3];
 }
 
-// ---------------------------------------------------------------------------
+// A2': mortar faces (Sec. 3.2.2, Algorithm 1), one block per mortar, a thread
+// per quadrant node.  Forward: on quadrant k the flux of the small side's
+// state and gradients and the big side's interpolated ones, F_k; on the big
+// face F_B = -P1(F_k), P1 the projection with the quadrature (scale 1).  So
+// the quadrant flux's adjoint is its own slot's seed minus P1^T of the big
+// slot's seed; the face VJP at each quadrant point gives the small side's
+// adjoints (its slot, own point order) and those of the interpolated big-side
+// values, which go back to the big face's nodes by the transposed
+// interpolation (the big slot).
+template <int N>
+static size_t adj_mortar_face_smem() {
+  constexpr int n = N + 1, NN = n * n;
+  return sizeof(double) * ((size_t)8 * NN + n + 17 * NN + 34 * NN + 5 * NN + 10 * NN + 68 * NN + 68 * NN);
+}
+
+template <int N>
+__global__ void __launch_bounds__(MortarShape<N>::THREADS)
+k_adj_mortar_face(const double* __restrict__ U, const double* __restrict__ grad, const double* __restrict__ facegeo,
+                  const int* __restrict__ mortars, const double* __restrict__ tab, int E, Gas g, AdjBufs b,
+                  int mu_offset) {
+  using S = MortarShape<N>;
+  constexpr int n = S::n, P = S::P, NN = S::NN, T = S::THREADS;
+  extern __shared__ double am[];
+  double* sI = am;                  // [2][n][n] I_h[x][j]
+  double* sIT = sI + 2 * NN;        // [2][j][x]
+  double* sW = sIT + 2 * NN;        // [2][x][j] w_x I_h[x][j]
+  double* sWT = sW + 2 * NN;        // [2][j][x] w_x I_h[x][j]
+  double* sw = sWT + 2 * NN;        // [n]
+  double* sB = sw + n;              // [17][NN] big face: state, gradients
+  double* sT = sB + 17 * NN;        // [2][17][NN]
+  double* sY = sT + 34 * NN;        // [5][NN] big slot seed / (w_i w_j)
+  double* sT2 = sY + 5 * NN;        // [2][5][NN]
+  double* sX = sT2 + 10 * NN;       // [4][17][NN] adjoints of the interpolated big-side values
+  double* sS = sX + 68 * NN;        // [4][17][NN]
+  const int m = blockIdx.x, t = threadIdx.x;
+  const int* r = mortars + (size_t)m * 20;
+  const int eB = dg_idx(r[0], E, kSiteMortar), fB = r[1], slotB = dg_idx(r[2], b.F, kSiteMortar);
+  mortar_tables<n>(tab, sI, sIT, sW, sw, t, T);
+  for (int x = t; x < 2 * NN; x += T) {   // sWT[h][j][a] = w_a I_h[a][j]
+    const int h = x / NN, rr = x - h * NN, a = rr / n, j = rr - a * n;
+    sWT[h * NN + j * n + a] = tab[2 * NN + a] * tab[x];
+  }
+  if (t < NN) {
+    const int i = t % n, j = t / n, node = face_node<n>(fB, i, j);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sB[v * NN + t] = U[((size_t)eB * 5 + v) * P + node];
+#pragma unroll
+    for (int x = 0; x < 12; ++x) sB[(5 + x) * NN + t] = grad[((size_t)eB * 12 + x) * P + node];
+    const double iww = 1.0 / (tab[2 * NN + i] * tab[2 * NN + j]);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sY[v * NN + t] = b.fseed[((size_t)slotB * 2 * 5 + v) * NN + t] * iww;
+  }
+  __syncthreads();
+  mortar_sweep1<n, 17>(sIT, sB, sT, t, T);
+  mortar_sweep1<n, 5>(sWT, sY, sT2, t, T);
+  __syncthreads();
+  const int k = t / NN, pq = t % NN, pp = pq % n, qq = pq / n;
+  double qR[17], z[5];
+  mortar_sweep2<n, 17>(sI, sT, k, pp, qq, qR);
+  mortar_sweep2<n, 5>(sW, sT2, k, pp, qq, z);   // P1^T of the big slot's seed at this quadrant point
+  const int es = dg_idx(r[3 + 4 * k], E, kSiteMortar), fs = r[4 + 4 * k], fl = r[5 + 4 * k];
+  const int slot = dg_idx(r[6 + 4 * k], b.F, kSiteMortar);
+  int p2, q2;
+  apply_flip<n>(fl, pp, qq, p2, q2);
+  const int node = face_node<n>(fs, p2, q2), o = p2 + n * q2;
+  double qL[5], gL[12], Fb[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    qL[v] = U[((size_t)es * 5 + v) * P + node];
+    Fb[v] = b.fseed[((size_t)slot * 2 * 5 + v) * NN + o] - z[v];
+  }
+#pragma unroll
+  for (int x = 0; x < 12; ++x) gL[x] = grad[((size_t)es * 12 + x) * P + node];
+  const double* fg = facegeo + (size_t)slot * 4 * NN + o;
+  double qbL[5] = {0, 0, 0, 0, 0}, qbR[5] = {0, 0, 0, 0, 0}, gbL[12], gbR[12];
+#pragma unroll
+  for (int x = 0; x < 12; ++x) { gbL[x] = 0.0; gbR[x] = 0.0; }
+  double mub = face_vjp_point(qL, qR, gL, qR + 5, fg[0], fg[NN], fg[2 * NN], fg[3 * NN], Fb, g, qbL, qbR, gbL, gbR);
+  double* os = b.face + ((size_t)slot * 2 + 0) * 17 * NN + o;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    os[v * NN] = qbL[v];
+    sX[(k * 17 + v) * NN + pq] = qbR[v];
+  }
+#pragma unroll
+  for (int x = 0; x < 12; ++x) {
+    os[(5 + x) * NN] = gbL[x];
+    sX[(k * 17 + 5 + x) * NN + pq] = gbR[x];
+  }
+  __syncthreads();
+  mortar_proj1<n, 17>(sI, sX, sS, t, T);   // transposed interpolation, first direction
+  __syncthreads();
+  for (int ox = t; ox < 17 * NN; ox += T) {
+    const int f = ox / NN, ij = ox - f * NN;
+    b.face[((size_t)slotB * 2 + 0) * 17 * NN + (size_t)f * NN + ij] = mortar_proj2<n, 17>(sI, sS, f, ij % n, ij / n);
+  }
+  // d/dmu: the block's partial, summed in a fixed order
+  __shared__ double smu[MortarShape<N>::THREADS];
+  smu[t] = mub;
+  __syncthreads();
+  if (t == 0) {
+    double acc = 0.0;
+    for (int x = 0; x < T; ++x) acc += smu[x];
+    b.mupart[mu_offset + m] = acc;
+  }
+}
+
+// A3': the mortar sides' terms of the lifting transpose.  Forward: the face
+// average of quadrant k is star_k = (phi_s + I_k phi_B)/2, that of the big face
+// star_B = P(star_k) (point-value projection, scale 1/4).  With Y = the
+// lifting's own surface weight at a face point (Y = gtil . n sJ / w_0), the
+// derivative w.r.t. phi at each side's points, beside the own -Y/2:
+//   small side k: + (P^T Y_B)_k / 2,
+//   big side    : - Y_B / 2 + sum_k I_k^T ((P^T Y_B)_k + Y_k) / 2.
+template <int N>
+__global__ void __launch_bounds__(MortarShape<N>::THREADS)
+k_adj_mortar_lift(const double* __restrict__ metrics, const int* __restrict__ mortars, const double* __restrict__ tab,
+                  int E, double inv_w0, AdjBufs b) {
+  using S = MortarShape<N>;
+  constexpr int n = S::n, P = S::P, NN = S::NN, T = S::THREADS;
+  __shared__ double sI[2 * NN], sIT[2 * NN], sW[2 * NN], sWT[2 * NN], sw[n];
+  __shared__ double sYB[4 * NN], sYs[4 * NN];    // Y_B / (w_i w_j); Y_B
+  __shared__ double sT[8 * NN], sV[16 * NN], sS[16 * NN];
+  const int m = blockIdx.x, t = threadIdx.x;
+  const int* r = mortars + (size_t)m * 20;
+  const int eB = dg_idx(r[0], E, kSiteMortar), fB = r[1];
+  mortar_tables<n>(tab, sI, sIT, sW, sw, t, T);
+  for (int x = t; x < 2 * NN; x += T) {
+    const int h = x / NN, rr = x - h * NN, a = rr / n, j = rr - a * n;
+    sWT[h * NN + j * n + a] = tab[2 * NN + a] * tab[x];
+  }
+  // Y at a face point of (e, f): inv_w0 (2s-1) sum_l gtil_{phi,l} Ja^d_l
+  auto Yat = [&](int e, int f, int p, int q, double y[4]) {
+    const int node = face_node<n>(f, p, q), d = f >> 1;
+    const double sg = (f & 1) ? inv_w0 : -inv_w0;
+    const double* mt = metrics + (size_t)e * 10 * P + node;
+    const double a0 = mt[(d * 3) * P], a1 = mt[(d * 3 + 1) * P], a2 = mt[(d * 3 + 2) * P];
+    const double* gt = b.gtil + (size_t)e * 12 * P + node;
+#pragma unroll
+    for (int ph = 0; ph < 4; ++ph) y[ph] = sg * (gt[(ph * 3) * P] * a0 + gt[(ph * 3 + 1) * P] * a1 + gt[(ph * 3 + 2) * P] * a2);
+  };
+  if (t < NN) {
+    const int i = t % n, j = t / n;
+    double y[4];
+    Yat(eB, fB, i, j, y);
+    const double iww = 1.0 / (tab[2 * NN + i] * tab[2 * NN + j]);
+#pragma unroll
+    for (int ph = 0; ph < 4; ++ph) {
+      sYs[ph * NN + t] = y[ph];
+      sYB[ph * NN + t] = 0.25 * y[ph] * iww;
+    }
+  }
+  __syncthreads();
+  mortar_sweep1<n, 4>(sWT, sYB, sT, t, T);
+  __syncthreads();
+  const int k = t / NN, pq = t % NN, pp = pq % n, qq = pq / n;
+  double z[4];
+  mortar_sweep2<n, 4>(sW, sT, k, pp, qq, z);   // (P^T Y_B)_k at this quadrant point
+  const int es = dg_idx(r[3 + 4 * k], E, kSiteMortar), fs = r[4 + 4 * k], fl = r[5 + 4 * k];
+  int p2, q2;
+  apply_flip<n>(fl, pp, qq, p2, q2);
+  double ys[4];
+  Yat(es, fs, p2, q2, ys);
+  double* xs = b.mx + (size_t)(5 * m + k) * 4 * NN + p2 + n * q2;
+#pragma unroll
+  for (int ph = 0; ph < 4; ++ph) {
+    xs[ph * NN] = 0.5 * z[ph];
+    sV[(k * 4 + ph) * NN + pq] = z[ph] + ys[ph];
+  }
+  __syncthreads();
+  mortar_proj1<n, 4>(sI, sV, sS, t, T);   // transposed interpolation
+  __syncthreads();
+  if (t < NN) {
+    const int i = t % n, j = t / n;
+    double* xb = b.mx + (size_t)(5 * m + 4) * 4 * NN + t;
+#pragma unroll
+    for (int ph = 0; ph < 4; ++ph) xb[ph * NN] = -0.5 * sYs[ph * NN + t] + 0.5 * mortar_proj2<n, 4>(sI, sS, ph, i, j);
+  }
+}
+
 // A3: per node, add the face contributions of the node's faces; store the
 // total gradient adjoint divided by J, and the conserved adjoint so far.
 template <int N>
@@ -359,7 +552,7 @@ k_adj_gather(const double* __restrict__ metrics, const int* __restrict__ elem_fa
     const int id_d = ijk[d];
     if (id_d != 0 && id_d != N) continue;
     const int code = elem_face[e * 6 + 2 * d + (id_d == N ? 1 : 0)];
-    const int fid = dg_idx(code >> 4, 3L * E, kSiteAdjFace);
+    const int fid = dg_idx(code >> 4, b.F, kSiteAdjFace);
     const int pp = d == 0 ? j : i;
     const int qq = d == 2 ? j : k;
     int pm = pp, qm = qq, side = 0;
@@ -379,11 +572,13 @@ k_adj_gather(const double* __restrict__ metrics, const int* __restrict__ elem_fa
 
 // ---------------------------------------------------------------------------
 // A4: transpose of the lifting, then the primitive VJP; out = total adjoint.
-template <int N>
+// MORTAR: a face whose neighbour entry is negative is a mortar side, whose
+// partner term comes from b.mx (k_adj_mortar_lift).
+template <int N, bool MORTAR = false>
 __global__ void __launch_bounds__(Shape<N>::THREADS)
 k_adj_lift(const double* __restrict__ U, const double* __restrict__ metrics, const int* __restrict__ elem_nbr,
            const int* __restrict__ elem_face, const double* __restrict__ Dg, int E, Gas g, double inv_w0, AdjBufs b,
-           double* __restrict__ out) {
+           double* __restrict__ out, int n_mortar) {
   using S = Shape<N>;
   constexpr int n = S::n, P = S::P, NN = S::NN, EPB = S::EPB;
   extern __shared__ double adj_smem[];
@@ -437,9 +632,17 @@ k_adj_lift(const double* __restrict__ U, const double* __restrict__ metrics, con
     const int f = 2 * d + s;
     const int code = elem_face[e * 6 + f];
     const int nb = elem_nbr[e * 6 + f];
-    const int e2 = dg_idx(nb >> 3, E, kSiteAdjFace), f2 = nb & 7;
     const int pp = d == 0 ? j : i;
     const int qq = d == 2 ? j : k;
+    if constexpr (MORTAR) {
+      if (nb < 0) {
+        const double* xm = b.mx + (size_t)dg_idx(-1 - nb, 5L * n_mortar, kSiteMortar) * 4 * NN + pp + n * qq;
+#pragma unroll
+        for (int ph = 0; ph < 4; ++ph) phib[ph] += xm[ph * NN];
+        continue;
+      }
+    }
+    const int e2 = dg_idx(nb >> 3, E, kSiteAdjFace), f2 = nb & 7;
     int p2, q2;
     apply_flip<n>(code & 7, pp, qq, p2, q2);
     const int id2 = face_node<n>(f2, p2, q2);
@@ -508,6 +711,12 @@ static cudaError_t adj_setup_N() {
                                        (int)adj_volume_smem<N>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_adj_lift<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_lift_smem<N>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_lift<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)adj_lift_smem<N>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_mortar_face<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)adj_mortar_face_smem<N>());
   return e;
 }
 
@@ -529,7 +738,7 @@ cudaError_t setup_adjoint(int N) {
 // number of d/dmu partials one VJP writes
 int adjoint_mu_partials(const Ctx& c) {
   const int epb = default_epb(c.P);
-  return (c.E + epb - 1) / epb + (int)(((long)c.nfaces * c.NN + 127) / 128);
+  return (c.E + epb - 1) / epb + (int)(((long)c.nfaces_conf * c.NN + 127) / 128) + c.M;
 }
 
 template <int N>
@@ -544,18 +753,32 @@ static cudaError_t vjp_N(const Ctx& c, const double* U, const double* lam, doubl
                                                                    c.E, c.gas, inv_w0, b);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  const long tot = (long)c.nfaces * NN;
+  const long tot = (long)c.nfaces_conf * NN;   // the conforming faces; the mortars' slots follow
   const int fblocks = (int)((tot + 127) / 128);
-  k_adj_face<N><<<fblocks, 128, 0, s>>>(U, grad, c.d_faces, c.d_facegeo, c.nfaces, c.gas, b, blocks);
+  if (fblocks > 0)
+    k_adj_face<N><<<fblocks, 128, 0, s>>>(U, grad, c.d_faces, c.d_facegeo, c.nfaces_conf, c.E, c.gas, b, blocks);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (c.M > 0) {
+    k_adj_mortar_face<N><<<c.M, MortarShape<N>::THREADS, adj_mortar_face_smem<N>(), s>>>(
+        U, grad, c.d_facegeo, c.d_mortars, c.d_mortar_tab, c.E, c.gas, b, blocks + fblocks);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
   const long nodes = (long)c.E * c.P;
   k_adj_gather<N><<<(int)((nodes + 127) / 128), 128, 0, s>>>(c.d_metrics, c.d_elem_face, c.E, b);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  k_adj_lift<N><<<blocks, S::THREADS, adj_lift_smem<N>(), s>>>(U, c.d_metrics, c.d_elem_nbr, c.d_elem_face, c.d_D,
-                                                               c.E, c.gas, inv_w0, b, out);
+  if (c.M > 0) {
+    k_adj_mortar_lift<N><<<c.M, MortarShape<N>::THREADS, 0, s>>>(c.d_metrics, c.d_mortars, c.d_mortar_tab, c.E,
+                                                                 inv_w0, b);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    k_adj_lift<N, true><<<blocks, S::THREADS, adj_lift_smem<N>(), s>>>(U, c.d_metrics, c.d_elem_nbr, c.d_elem_face,
+                                                                       c.d_D, c.E, c.gas, inv_w0, b, out, c.M);
+  } else {
+    k_adj_lift<N><<<blocks, S::THREADS, adj_lift_smem<N>(), s>>>(U, c.d_metrics, c.d_elem_nbr, c.d_elem_face, c.d_D,
+                                                                 c.E, c.gas, inv_w0, b, out, 0);
+  }
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (dJdmu) {
-    k_adj_mu_fold<<<1, 256, 0, s>>>(b.mupart, blocks + fblocks, mu_scale, dJdmu);
+    k_adj_mu_fold<<<1, 256, 0, s>>>(b.mupart, blocks + fblocks + c.M, mu_scale, dJdmu);
     err = cudaGetLastError();
   }
   return err;
@@ -566,7 +789,8 @@ cudaError_t launch_vjp(const Ctx& c, const double* U, const double* lam, double*
   // forward recomputation of the FP64 lifted gradients at U
   cudaError_t err = launch_lift_fp64(c, U, s);
   if (err != cudaSuccess) return err;
-  AdjBufs b{c.d_adj_qbar, c.d_adj_gbar, c.d_adj_fseed, c.d_adj_face, c.d_adj_gtil, c.d_adj_mu, 0};
+  AdjBufs b{c.d_adj_qbar, c.d_adj_gbar, c.d_adj_fseed, c.d_adj_face, c.d_adj_gtil, c.d_adj_mu, 0, c.d_adj_mx,
+            c.nfaces};
   switch (c.N) {
     case 1: return vjp_N<1>(c, U, lam, out, b, dJdmu, mu_scale, s);
     case 2: return vjp_N<2>(c, U, lam, out, b, dJdmu, mu_scale, s);

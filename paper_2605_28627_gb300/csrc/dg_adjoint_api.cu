@@ -34,7 +34,6 @@ static dg_status adj_checked(Ctx* c, cudaStream_t s) {
 static dg_status ensure_adjoint(Ctx* c) {
   if (c->fv_on)
     return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the DG operator (no FV sub-cell elements)");
-  if (c->M > 0) return afail(c, DG_EUNSUPPORTED, "the adjoint is built for conforming meshes");
   if (c->d_adj_qbar) return DG_OK;
   if (c->prm.precision != DG_FP64) return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the FP64 operator");
   if (c->prm.nodes != DG_NODES_LGL)
@@ -51,6 +50,8 @@ static dg_status ensure_adjoint(Ctx* c) {
   ADJ_CUDA(cudaMalloc(&c->d_adj_stage, sizeof(double) * st * rk_scheme(c->prm.rk_scheme).stages), c,
            "adjoint stage states");
   ADJ_CUDA(cudaMalloc(&c->d_adj_work, sizeof(double) * st * 4), c, "adjoint work");
+  if (c->M > 0)
+    ADJ_CUDA(cudaMalloc(&c->d_adj_mx, sizeof(double) * (size_t)c->M * 5 * 4 * c->NN), c, "adjoint mortar buffer");
   return DG_OK;
 }
 

@@ -169,6 +169,7 @@ struct Ctx {
   double* d_adj_face = nullptr;  // [F][2][17][NN]
   double* d_adj_mu = nullptr;    // block partials of d/dmu
   double* d_adj_stage = nullptr; // [5][E][5][P] stage states of one step
+  double* d_adj_mx = nullptr;    // [M][5][4][NN] mortar sides' lifting-transpose terms
   double* d_adj_work = nullptr;  // [4][E][5][P]: work state, G, G-bar, VJP scratch
   // host-buffer path
   double* d_U = nullptr;

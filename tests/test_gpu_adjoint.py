@@ -51,6 +51,87 @@ def test_vjp_dot_product_vs_oracle_tangent_linear(orc, dg, N, flux, law):
     assert abs(dmu.item() - ref_mu) <= 1e-11 * float(np.abs(v * Rmu).sum()), (dmu.item(), ref_mu)
 
 
+def _mortar_mesh(N, seed):
+    from workloads.mesh import refined_box_mesh
+    K = 3 if N <= 7 else 2
+    r = np.zeros(K ** 3, dtype=bool)
+    r[[0, 13] if K == 3 else [0, 7]] = True
+    return refined_box_mesh(K, r, rotate_seed=seed)
+
+
+@pytest.mark.parametrize("N,flux,law", [(1, 0, 0), (2, 0, 0), (3, 1, 0), (3, 2, 1), (4, 0, 1), (5, 1, 0),
+                                        (7, 0, 0), (9, 2, 0)])
+def test_vjp_on_mortar_mesh_vs_oracle_tangent_linear(orc, dg, N, flux, law):
+    """2:1 non-conforming meshes (Sec. 3.2.2, Algorithm 1): the transposes of
+    the quadrant interpolation, of the flux projection and of the mortar
+    sides' lifting states, in the same dot-product test."""
+    mesh = _mortar_mesh(N, 900 + N)
+    kw = dict(mu=0.03, surf_flux=flux, visc_law=law, T_ref=1.0, S_suth=0.4)
+    o = orc.Oracle(mesh, N, **kw)
+    s = dg.Solver(mesh, N, **kw)
+    U = random_state(mesh.n_elems, N, seed=910 + N)
+    rng = np.random.default_rng(920 + N)
+    w = rng.normal(size=U.shape)
+    v = rng.normal(size=U.shape)
+    _, Jw = o.time_derivative_tl(U, w, 0.0)
+    _, Rmu = o.time_derivative_tl(U, np.zeros_like(U), 1.0)
+    dmu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    JTv = s.time_derivative_vjp(_cuda(U), _cuda(v), dJdmu=dmu).cpu().numpy()
+    lhs, rhs = float((JTv * w).sum()), float((v * Jw).sum())
+    scale = float(np.abs(JTv * w).sum())
+    assert abs(lhs - rhs) <= 1e-11 * scale, (lhs, rhs)
+    ref_mu = float((v * Rmu).sum())
+    assert abs(dmu.item() - ref_mu) <= 1e-11 * float(np.abs(v * Rmu).sum()), (dmu.item(), ref_mu)
+
+
+def test_vjp_on_mortar_mesh_per_entry(orc, dg):
+    """Column by column on a small mortar mesh: (dR/dU)^T e_i against the
+    oracle's tangent-linear rows, for seeds on the big face's and the small
+    faces' nodes (a dot product alone could hide two errors that cancel)."""
+    N = 2
+    mesh = _mortar_mesh(N, 930)
+    o = orc.Oracle(mesh, N, mu=0.03)
+    s = dg.Solver(mesh, N, mu=0.03)
+    U = random_state(mesh.n_elems, N, seed=931)
+    rng = np.random.default_rng(932)
+    n = N + 1
+    # the refined cell 0's children and its neighbours through the mortars
+    big = np.unique(mesh.mortars[:, 0])[:2]
+    small = np.unique(mesh.mortars[:, 2])[:2]
+    picks = [(int(e), c, int(rng.integers(0, n ** 3))) for e in list(big) + list(small) for c in (0, 4)]
+    lam = np.zeros(U.shape)
+    for e, c, node in picks:
+        lam.reshape(mesh.n_elems, 5, -1)[e, c, node] = rng.normal()
+    JTv = s.time_derivative_vjp(_cuda(U), _cuda(lam)).cpu().numpy()
+    for trial in range(6):
+        w = np.zeros(U.shape)
+        e = int(rng.choice(np.concatenate([big, small])))
+        w.reshape(mesh.n_elems, 5, -1)[e] = rng.normal(size=(5, n ** 3))
+        _, Jw = o.time_derivative_tl(U, w, 0.0)
+        lhs, rhs = float((JTv * w).sum()), float((lam * Jw).sum())
+        assert abs(lhs - rhs) <= 1e-11 * max(float(np.abs(JTv * w).sum()), 1e-300), (trial, lhs, rhs)
+
+
+def test_solve_adjoint_on_mortar_mesh_vs_oracle(orc, dg):
+    """Adjoint of LSERK4-5 steps on a 2:1 mesh against the oracle's
+    tangent-linear of the same steps, with d/dmu."""
+    N = 3
+    mesh = _mortar_mesh(N, 940)
+    o = orc.Oracle(mesh, N, mu=0.02)
+    s = dg.Solver(mesh, N, mu=0.02)
+    U0 = random_state(mesh.n_elems, N, seed=941, rho=(0.95, 1.05), vel=0.2, p=(0.95, 1.05))
+    dt, nsteps = 2e-3, 4
+    rng = np.random.default_rng(942)
+    w = rng.normal(size=U0.shape)
+    lam = rng.normal(size=U0.shape)
+    _, dUT = o.rk_steps_tl(U0, w, 0.3, 0.0, dt, nsteps)
+    dmu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lam0, _ = s.adjoint_solve(_cuda(U0), _cuda(lam), 0.0, dt, nsteps, max_snapshots=2, dJdmu=dmu)
+    lhs = float((lam0.cpu().numpy() * w).sum()) + 0.3 * dmu.item()
+    rhs = float((lam * dUT).sum())
+    assert abs(lhs - rhs) <= 1e-10 * abs(rhs), (lhs, rhs)
+
+
 @pytest.mark.parametrize("rk", [0, 1])
 def test_step_and_solve_adjoint_vs_oracle(orc, dg, rk):
     """Adjoint of LSERK4-5 (rk 0) and RK4-14 (rk 1) steps against the oracle's

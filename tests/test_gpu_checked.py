@@ -63,7 +63,11 @@ err_r = float(np.abs(s.time_derivative(Ud).cpu().numpy() - Ro).max() / np.abs(Ro
 G = torch.empty_like(Ud)
 s.rk_step(Ud, G, 0.0, 1e-3, 3)
 Uo = o.rk_steps(U, 0.0, 1e-3, 3)
-out["mortar"] = dict(err_r=err_r, err_rk=float(np.abs(Ud.cpu().numpy() - Uo).max() / np.abs(Uo).max()), finite=True)
+lam = torch.from_numpy(random_state(mesh.n_elems, 3, seed=14)).cuda()
+vj = s.time_derivative_vjp(Ud, lam)                 # the mortar kernels of the adjoint
+lam0, _ = s.adjoint_solve(Ud, lam, 0.0, 1e-3, 2, max_snapshots=2)
+out["mortar"] = dict(err_r=err_r, err_rk=float(np.abs(Ud.cpu().numpy() - Uo).max() / np.abs(Uo).max()),
+                     finite=bool(torch.isfinite(vj).all() and torch.isfinite(lam0).all()))
 # the same mesh on Gauss nodes (mortar maps on the face values)
 Ug = random_state(mesh.n_elems, 3, seed=13, rho=(0.95, 1.05), vel=0.2, p=(0.95, 1.05))
 og = oracle.Oracle(mesh, 3, mu=0.02, nodes=1)
