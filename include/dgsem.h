@@ -262,12 +262,14 @@ dg_status dg_geometry(dg_ctx* ctx, double* dJa, double* dJ, dg_stream stream);
  * log-mean switch follow the primal state; at a kink of the LLF speed maximum
  * the mean of the one-sided derivatives is taken).  The paper has no
  * adjoint; these entries exist for gradient-based use of the solver.  Built
- * for LGL nodes, all three surface fluxes (the Roe flux differentiated on
- * dual numbers, its kinks by the value) and constant or Sutherland
- * viscosity (the derivative of mu(T) enters through the state) on
+ * for both node sets (on Gauss nodes the transposes of the weak form and of
+ * the face prolongations), all three surface fluxes (the Roe flux
+ * differentiated on dual numbers, its kinks by the value) and constant or
+ * Sutherland viscosity (the derivative of mu(T) enters through the state) on
  * conforming or 2:1 mortar meshes (the transposes of the mortars'
  * interpolation and projection) without FV sub-cell elements, for both time
- * schemes; other contexts get DG_EUNSUPPORTED.
+ * schemes; other contexts (the FP32 operator, FV elements) get
+ * DG_EUNSUPPORTED.
  * dJdmu, where present, is a device double that is ACCUMULATED (+=) with
  * lambda . dR/dmu, mu the constant viscosity or Sutherland's reference
  * viscosity (R is linear in it); NULL skips it. */
@@ -307,8 +309,8 @@ dg_status dg_adjoint_solve(dg_ctx* ctx, const double* dU0, const double* dlamT, 
  * no context. */
 dg_status dg_checkpoint_schedule(int32_t nsteps, int32_t max_snapshots, int64_t* host_counts2);
 
-/* Objective J = sum_nodes w_i w_j w_k J 1/2 rho |u|^2 (LGL quadrature of the
- * volume-integrated kinetic energy) into *host_J; dgrad (device, may be NULL)
+/* Objective J = sum_nodes w_i w_j w_k J 1/2 rho |u|^2 (the node set's
+ * quadrature of the volume-integrated kinetic energy) into *host_J; dgrad (device, may be NULL)
  * receives dJ/dU.  Synchronises the stream. */
 dg_status dg_kinetic_energy(dg_ctx* ctx, const double* dU, double* dgrad, double* host_J, dg_stream stream);
 

@@ -1081,7 +1081,8 @@ static const double RK14_C[14] = {0.0, 0.0367762454319673, 0.1249685262725025, 0
                                   0.8527059887098624, 0.8604711817462826, 0.8627060376969976,
                                   0.8734213127600976};
 
-static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double mu);
+template <class T>
+static void rhs_lg(const Ctx& c, const T* U, T* Ut, double t, T mu);
 static void state_persson(const Ctx& c, const double* U, int var, double* out);
 
 // Automatic switching of troubled cells (Sec. 3.1: the modal indicator marks
@@ -1114,13 +1115,14 @@ static void fv_switch(const Ctx& c, const double* U) {
   }
 }
 
-// R(U) on the context's node set (the Gauss-node operator is FP64 only).
+// R(U) on the context's node set (the switching of troubled cells and the
+// FV elements are FP64 only).
 template <class T>
 static void rhs_any(const Ctx& c, const T* U, T* Ut, double t, T mu) {
   if constexpr (std::is_same<T, double>::value) {
     if (c.sw_on) fv_switch(c, U);
-    if (c.nodes == 1) { rhs_lg(c, U, Ut, t, mu); return; }
   }
+  if (c.nodes == 1) { rhs_lg(c, U, Ut, t, mu); return; }
   rhs(c, U, Ut, t, mu);
 }
 
@@ -1304,9 +1306,10 @@ static void gauss_geometry(Ctx& c) {
 
 // Face values of nv nodal fields of every element: out[e][f][v][p + n q] =
 // sum_i l_i(+-1) field(line of face point (p, q)).
-static void prolong_to_faces(const Ctx& c, const double* field, int nv, std::vector<double>& out) {
+template <class T>
+static void prolong_to_faces(const Ctx& c, const T* field, int nv, std::vector<T>& out) {
   int n = c.n, P = c.P, nn = n * n;
-  out.assign((size_t)c.E * 6 * nv * nn, 0.0);
+  out.assign((size_t)c.E * 6 * nv * nn, T(0.0));
   for (int e = 0; e < c.E; ++e)
     for (int f = 0; f < 6; ++f) {
       int d = f / 2;
@@ -1314,7 +1317,7 @@ static void prolong_to_faces(const Ctx& c, const double* field, int nv, std::vec
       for (int v = 0; v < nv; ++v)
         for (int q = 0; q < n; ++q)
           for (int p = 0; p < n; ++p) {
-            double s = 0.0;
+            T s = T(0.0);
             for (int i = 0; i < n; ++i) s += l[i] * field[((size_t)e * nv + v) * P + line_node(n, d, i, p, q)];
             out[(((size_t)e * 6 + f) * nv + v) * nn + p + n * q] = s;
           }
@@ -1339,19 +1342,20 @@ static inline void outward_nsJ(const Ctx& c, int e, int f, int p, int q, double 
 // face values phif [e][6][4][nn]:
 //   J g_l,i = sum_faces l_{i_d}(+-1)/w_{i_d} phi* (n_l sJ) - sum_d sum_m (w_m/w_{i_d}) D_{m i_d} (phi Ja^d_l)_m,
 // phi* = (phi_own + phi_nbr)/2 at each face point.
-static void lifting_lg(const Ctx& c, const double* phi, const std::vector<double>& phif, double* G) {
+template <class T>
+static void lifting_lg(const Ctx& c, const T* phi, const std::vector<T>& phif, T* G) {
   int n = c.n, P = c.P, nn = n * n, N = c.N;
   const std::vector<double>& w = c.g.w;
   const std::vector<double>& D = c.g.D;
   // mortar face averages at the face points, as on LGL nodes: on each
   // quadrant (the small side's own point order) and projected onto the big face
-  std::vector<double> star_s((size_t)c.M * 4 * 4 * nn), star_b((size_t)c.M * 4 * nn);
+  std::vector<T> star_s((size_t)c.M * 4 * 4 * nn), star_b((size_t)c.M * 4 * nn);
   for (int m = 0; m < c.M; ++m) {
     const int* r = &c.mortars[(size_t)m * 14];
     for (int ph = 0; ph < 4; ++ph) {
-      const double* big = &phif[(((size_t)r[0] * 6 + r[1]) * 4 + ph) * nn];
-      std::vector<double> q[4];
-      const double* qp[4];
+      const T* big = &phif[(((size_t)r[0] * 6 + r[1]) * 4 + ph) * nn];
+      std::vector<T> q[4];
+      const T* qp[4];
       for (int k = 0; k < 4; ++k) {
         q[k].resize(nn);
         mortar_interp(c, big, k, q[k].data());
@@ -1360,7 +1364,7 @@ static void lifting_lg(const Ctx& c, const double* phi, const std::vector<double
           for (int pp = 0; pp < n; ++pp) {
             int p2, q2;
             flip_map(fl, N, pp, qq, p2, q2);
-            const double st = 0.5 * (phif[(((size_t)es * 6 + fs) * 4 + ph) * nn + p2 + n * q2] + q[k][pp + n * qq]);
+            const T st = 0.5 * (phif[(((size_t)es * 6 + fs) * 4 + ph) * nn + p2 + n * q2] + q[k][pp + n * qq]);
             star_s[(((size_t)m * 4 + k) * 4 + ph) * nn + p2 + n * q2] = st;
             q[k][pp + n * qq] = st;
           }
@@ -1370,14 +1374,14 @@ static void lifting_lg(const Ctx& c, const double* phi, const std::vector<double
     }
   }
   for (int e = 0; e < c.E; ++e) {
-    std::vector<double> acc((size_t)12 * P, 0.0);
+    std::vector<T> acc((size_t)12 * P, T(0.0));
     for (int k = 0; k < n; ++k)
       for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) {
           int id = vidx(n, i, j, k), ijk[3] = {i, j, k};
           for (int ph = 0; ph < 4; ++ph)
             for (int l = 0; l < 3; ++l) {
-              double s = 0.0;
+              T s = T(0.0);
               for (int d = 0; d < 3; ++d) {
                 int r = ijk[d];
                 for (int m = 0; m < n; ++m) {
@@ -1402,10 +1406,10 @@ static void lifting_lg(const Ctx& c, const double* phi, const std::vector<double
           const int mo = e2 < 0 ? -1 - e2 : -1;
           const bool mbig = mo >= 0 && mortar_big(c, mo, e, f);
           for (int ph = 0; ph < 4; ++ph) {
-            double star;
+            T star;
             if (mo < 0) {
-              double mine = phif[(((size_t)e * 6 + f) * 4 + ph) * nn + p + n * q];
-              double other = phif[(((size_t)e2 * 6 + f2) * 4 + ph) * nn + p2 + n * q2];
+              T mine = phif[(((size_t)e * 6 + f) * 4 + ph) * nn + p + n * q];
+              T other = phif[(((size_t)e2 * 6 + f2) * 4 + ph) * nn + p2 + n * q2];
               star = 0.5 * (mine + other);
             } else if (mbig) {
               star = star_b[((size_t)mo * 4 + ph) * nn + p + n * q];
@@ -1426,25 +1430,25 @@ static void lifting_lg(const Ctx& c, const double* phi, const std::vector<double
 
 // Lifting variables (u, v, w, T) at the nodes and at the faces (from the
 // face values of the conservative state).
-static void lg_phi(const Ctx& c, const double* U, std::vector<double>& phi, std::vector<double>& Uf,
-                   std::vector<double>& phif) {
+template <class T>
+static void lg_phi(const Ctx& c, const T* U, std::vector<T>& phi, std::vector<T>& Uf, std::vector<T>& phif) {
   int P = c.P, nn = c.n * c.n;
-  phi.assign((size_t)c.E * 4 * P, 0.0);
+  phi.assign((size_t)c.E * 4 * P, T(0.0));
   for (int e = 0; e < c.E; ++e)
     for (int id = 0; id < P; ++id) {
-      double q[5];
+      T q[5];
       for (int v = 0; v < 5; ++v) q[v] = U[((size_t)e * 5 + v) * P + id];
-      Prim<double> w = cons2prim(c.prm, q);
+      Prim<T> w = cons2prim(c.prm, q);
       for (int a = 0; a < 3; ++a) phi[((size_t)e * 4 + a) * P + id] = w.u[a];
       phi[((size_t)e * 4 + 3) * P + id] = w.T_;
     }
   prolong_to_faces(c, U, 5, Uf);
-  phif.assign((size_t)c.E * 6 * 4 * nn, 0.0);
+  phif.assign((size_t)c.E * 6 * 4 * nn, T(0.0));
   for (int ef = 0; ef < c.E * 6; ++ef)
     for (int pq = 0; pq < nn; ++pq) {
-      double q[5];
+      T q[5];
       for (int v = 0; v < 5; ++v) q[v] = Uf[((size_t)ef * 5 + v) * nn + pq];
-      Prim<double> w = cons2prim(c.prm, q);
+      Prim<T> w = cons2prim(c.prm, q);
       for (int a = 0; a < 3; ++a) phif[((size_t)ef * 4 + a) * nn + pq] = w.u[a];
       phif[((size_t)ef * 4 + 3) * nn + pq] = w.T_;
     }
@@ -1454,18 +1458,19 @@ static void lg_phi(const Ctx& c, const double* U, std::vector<double>& phi, std:
 //   J U_t,i = - sum_faces l_{i_d}(+-1)/w_{i_d} F*_out + sum_d sum_m (w_m/w_{i_d}) D_{m i_d} Ft^d_m + J Q,
 // Ft^d = (f - f_v)(q, g) . Ja^d, F*_out = (F_adv(q-, q+; n) - {f_v} . n) sJ with
 // the element's outward n, face states and gradients from prolong_to_faces.
-static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double mu) {
+template <class T>
+static void rhs_lg(const Ctx& c, const T* U, T* Ut, double t, T mu) {
   const Params& pr = c.prm;
   int n = c.n, P = c.P, E = c.E, N = c.N, nn = n * n;
   const std::vector<double>& w = c.g.w;
   const std::vector<double>& D = c.g.D;
-  std::vector<double> phi, Uf, phif, Gf;
+  std::vector<T> phi, Uf, phif, Gf;
   lg_phi(c, U, phi, Uf, phif);
-  std::vector<double> G((size_t)E * 12 * P);
+  std::vector<T> G((size_t)E * 12 * P);
   lifting_lg(c, phi.data(), phif, G.data());
   prolong_to_faces(c, G.data(), 12, Gf);
   // face fluxes on master faces, master orientation
-  std::vector<double> Fs((size_t)c.nfaces * 5 * nn);
+  std::vector<T> Fs((size_t)c.nfaces * 5 * nn);
   for (int e = 0; e < E; ++e)
     for (int f = 0; f < 6; ++f) {
       if (!c.master[e * 6 + f]) continue;
@@ -1476,7 +1481,7 @@ static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double m
         for (int p = 0; p < n; ++p) {
           int p2, q2;
           flip_map(fl, N, p, q, p2, q2);
-          double qL[5], qR[5], gL[12], gR[12], nv[3];
+          T qL[5], qR[5], gL[12], gR[12], nv[3];
           for (int v = 0; v < 5; ++v) {
             qL[v] = Uf[(((size_t)e * 6 + f) * 5 + v) * nn + p + n * q];
             qR[v] = Uf[(((size_t)e2 * 6 + f2) * 5 + v) * nn + p2 + n * q2];
@@ -1485,10 +1490,10 @@ static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double m
             gL[r] = Gf[(((size_t)e * 6 + f) * 12 + r) * nn + p + n * q];
             gR[r] = Gf[(((size_t)e2 * 6 + f2) * 12 + r) * nn + p2 + n * q2];
           }
-          for (int l = 0; l < 3; ++l) nv[l] = c.fn[((size_t)fid * 3 + l) * nn + p + n * q];
+          for (int l = 0; l < 3; ++l) nv[l] = T(c.fn[((size_t)fid * 3 + l) * nn + p + n * q]);
           double sJ = c.fsJ[(size_t)fid * nn + p + n * q];
-          Prim<double> L = cons2prim(pr, qL), Rr = cons2prim(pr, qR);
-          double fa[5], fvL[5], fvR[5];
+          Prim<T> L = cons2prim(pr, qL), Rr = cons2prim(pr, qR);
+          T fa[5], fvL[5], fvR[5];
           if (pr.surf_flux == 1) ec_flux(pr, L, Rr, nv, fa);
           else if (pr.surf_flux == 2) roe_flux(pr, qL, L, qR, Rr, nv, fa);
           else llf_flux(pr, qL, L, qR, Rr, nv, fa);
@@ -1504,7 +1509,7 @@ static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double m
   for (int m = 0; m < c.M; ++m) {
     const int* r = &c.mortars[(size_t)m * 14];
     const int fidB = c.face_id[r[0] * 6 + r[1]];
-    std::vector<double> big((size_t)17 * nn), qi((size_t)17 * nn), Fq((size_t)4 * 5 * nn);
+    std::vector<T> big((size_t)17 * nn), qi((size_t)17 * nn), Fq((size_t)4 * 5 * nn);
     for (int ij = 0; ij < nn; ++ij) {
       for (int v = 0; v < 5; ++v) big[(size_t)v * nn + ij] = Uf[(((size_t)r[0] * 6 + r[1]) * 5 + v) * nn + ij];
       for (int rr = 0; rr < 12; ++rr) big[(size_t)(5 + rr) * nn + ij] = Gf[(((size_t)r[0] * 6 + r[1]) * 12 + rr) * nn + ij];
@@ -1518,7 +1523,7 @@ static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double m
           int p2, q2;
           flip_map(fl, N, pp, qq, p2, q2);
           const int o = p2 + n * q2;
-          double qL[5], qR[5], gL[12], gR[12], nv[3];
+          T qL[5], qR[5], gL[12], gR[12], nv[3];
           for (int v = 0; v < 5; ++v) {
             qL[v] = Uf[(((size_t)es * 6 + fs) * 5 + v) * nn + o];
             qR[v] = qi[(size_t)v * nn + pp + n * qq];
@@ -1527,56 +1532,59 @@ static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double m
             gL[rr] = Gf[(((size_t)es * 6 + fs) * 12 + rr) * nn + o];
             gR[rr] = qi[(size_t)(5 + rr) * nn + pp + n * qq];
           }
-          for (int l = 0; l < 3; ++l) nv[l] = c.fn[((size_t)fidS * 3 + l) * nn + o];
+          for (int l = 0; l < 3; ++l) nv[l] = T(c.fn[((size_t)fidS * 3 + l) * nn + o]);
           const double sJ = c.fsJ[(size_t)fidS * nn + o];
-          Prim<double> L = cons2prim(pr, qL), Rr = cons2prim(pr, qR);
-          double fa[5], fvL[5], fvR[5];
+          Prim<T> L = cons2prim(pr, qL), Rr = cons2prim(pr, qR);
+          T fa[5], fvL[5], fvR[5];
           if (pr.surf_flux == 1) ec_flux(pr, L, Rr, nv, fa);
           else if (pr.surf_flux == 2) roe_flux(pr, qL, L, qR, Rr, nv, fa);
           else llf_flux(pr, qL, L, qR, Rr, nv, fa);
           visc_flux(pr, L, gL, mu, nv, fvL);
           visc_flux(pr, Rr, gR, mu, nv, fvR);
           for (int v = 0; v < 5; ++v) {
-            const double F = (fa[v] - 0.5 * (fvL[v] + fvR[v])) * sJ;
+            const T F = (fa[v] - 0.5 * (fvL[v] + fvR[v])) * sJ;
             Fs[((size_t)fidS * 5 + v) * nn + o] = F;
             Fq[((size_t)k * 5 + v) * nn + pp + n * qq] = -F;   // out of the big element
           }
         }
     }
     for (int v = 0; v < 5; ++v) {
-      const double* qp[4] = {&Fq[(size_t)(0 * 5 + v) * nn], &Fq[(size_t)(1 * 5 + v) * nn],
+      const T* qp[4] = {&Fq[(size_t)(0 * 5 + v) * nn], &Fq[(size_t)(1 * 5 + v) * nn],
                              &Fq[(size_t)(2 * 5 + v) * nn], &Fq[(size_t)(3 * 5 + v) * nn]};
       mortar_project(c, qp, 1.0, &Fs[((size_t)fidB * 5 + v) * nn]);
     }
   }
   // FV sub-cell elements (as on LGL nodes; the DG side of a mixed face
   // enters with its interpolated face values)
-  const bool use_fv = !c.fv_mask.empty();
+  constexpr bool kFP64 = std::is_same<T, double>::value;   // FV elements: FP64 only
+  const bool use_fv = kFP64 && !c.fv_mask.empty();
   FVData fv;
-  if (use_fv) {
-    fv_prepare(c, U, G.data(), fv);
-    fv.Uf = Uf.data();
-    fv.Gf = Gf.data();
-    fv_faces(c, fv, Fs.data());
+  if constexpr (kFP64) {
+    if (use_fv) {
+      fv_prepare(c, U, G.data(), fv);
+      fv.Uf = Uf.data();
+      fv.Gf = Gf.data();
+      fv_faces(c, fv, Fs.data());
+    }
   }
   for (int e = 0; e < E; ++e) {
     if (use_fv && c.fv_mask[e]) continue;
     // contravariant fluxes at the nodes
-    std::vector<double> Ft((size_t)3 * 5 * P);
+    std::vector<T> Ft((size_t)3 * 5 * P);
     for (int id = 0; id < P; ++id) {
-      double q[5], g[12];
+      T q[5], g[12];
       for (int v = 0; v < 5; ++v) q[v] = U[((size_t)e * 5 + v) * P + id];
       for (int r = 0; r < 12; ++r) g[r] = G[((size_t)e * 12 + r) * P + id];
-      Prim<double> W = cons2prim(pr, q);
+      Prim<T> W = cons2prim(pr, q);
       for (int d = 0; d < 3; ++d) {
-        double nv[3], fa[5], fv[5];
+        T nv[3], fa[5], fv[5];
         for (int l = 0; l < 3; ++l) nv[l] = c.Ja[(((size_t)e * 3 + d) * 3 + l) * P + id];
         euler_flux(q, W, nv, fa);
         visc_flux(pr, W, g, mu, nv, fv);
         for (int v = 0; v < 5; ++v) Ft[((size_t)d * 5 + v) * P + id] = fa[v] - fv[v];
       }
     }
-    std::vector<double> acc((size_t)5 * P, 0.0);
+    std::vector<T> acc((size_t)5 * P, T(0.0));
     for (int k = 0; k < n; ++k)
       for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) {
@@ -1595,7 +1603,7 @@ static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double m
       const std::vector<double>& lend = (f % 2) ? c.g.lp : c.g.lm;
       for (int q = 0; q < n; ++q)
         for (int p = 0; p < n; ++p) {
-          double Fout[5];
+          T Fout[5];
           if (c.master[e * 6 + f]) {
             for (int v = 0; v < 5; ++v) Fout[v] = Fs[((size_t)fid * 5 + v) * nn + p + n * q];
           } else {
@@ -1618,7 +1626,9 @@ static void rhs_lg(const Ctx& c, const double* U, double* Ut, double t, double m
       for (int v = 0; v < 5; ++v) Ut[((size_t)e * 5 + v) * P + id] = -acc[(size_t)v * P + id] / c.J[(size_t)e * P + id] + Qs[v];
     }
   }
-  if (use_fv) fv_elements(c, fv, Ut, t);
+  if constexpr (kFP64) {
+    if (use_fv) fv_elements(c, fv, Ut, t);
+  }
 }
 
 // Lifted gradients on either node set (test hook and diagnostics).
@@ -2308,12 +2318,11 @@ int orc_nodes(void* h) { return ((Ctx*)h)->nodes; }
 // Tangent-linear: Ut = R(U) and dUt = dR/dU . dU + dR/dmu . dmu.
 void orc_time_derivative_tl(void* h, const double* U, const double* dU, double dmu,
                             double* Ut, double* dUt, double t) {
-  if (((Ctx*)h)->nodes != 0) return;   // the tangent-linear is built for the LGL operator
   Ctx* c = (Ctx*)h;
   size_t len = (size_t)c->E * 5 * c->P;
   std::vector<Dual> Ud(len), Utd(len);
   for (size_t a = 0; a < len; ++a) Ud[a] = Dual(U[a], dU ? dU[a] : 0.0);
-  rhs<Dual>(*c, Ud.data(), Utd.data(), t, Dual(c->prm.mu, dmu));
+  rhs_any<Dual>(*c, Ud.data(), Utd.data(), t, Dual(c->prm.mu, dmu));
   for (size_t a = 0; a < len; ++a) { if (Ut) Ut[a] = Utd[a].v; if (dUt) dUt[a] = Utd[a].d; }
 }
 
@@ -2354,7 +2363,6 @@ void orc_rk_steps(void* h, double* U, double t, double dt, int nsteps) {
 
 // Tangent-linear of nsteps LSERK steps: U and dU advanced together.
 void orc_rk_steps_tl(void* h, double* U, double* dU, double dmu, double t, double dt, int nsteps) {
-  if (((Ctx*)h)->nodes != 0) return;   // the tangent-linear is built for the LGL operator
   Ctx* c = (Ctx*)h;
   size_t len = (size_t)c->E * 5 * c->P;
   std::vector<Dual> Ud(len);

@@ -243,8 +243,6 @@ class Oracle:
         return out
 
     def _tl_check(self):
-        if self.nodes != 0:
-            raise ValueError("oracle: the tangent-linear is built for the LGL operator")
         if self.fv_mask is not None:
             raise ValueError("oracle: the tangent-linear is built for the DG operator (no FV elements)")
 

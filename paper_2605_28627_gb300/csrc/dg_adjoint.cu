@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "dg_adjoint_fn.cuh"
+#include "dg_gauss.cuh"
 #include "dg_mortar.cuh"
 #include "dg_stage.cuh"
 
@@ -300,12 +301,13 @@ __device__ __forceinline__ double face_vjp_point(const double qL[5], const doubl
 }
 
 // A2: face adjoint, one thread per face node of the conforming faces (master
-// orientation); the mortars' slots follow them (k_adj_mortar_face).
-template <int N>
+// orientation); the mortars' slots follow them (k_adj_mortar_face).  FACE:
+// Gauss nodes, where U and grad are the face values [E][6][5|12][NN].
+template <int N, bool FACE = false>
 __global__ void __launch_bounds__(128)
 k_adj_face(const double* __restrict__ U, const double* __restrict__ grad, const FaceInfo* __restrict__ faces,
            const double* __restrict__ facegeo, int F, int E, Gas g, AdjBufs b, int mu_offset) {
-  constexpr int n = N + 1, P = n * n * n, NN = n * n;
+  constexpr int n = N + 1, NN = n * n;
   __shared__ double smu[4];
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   double mub = 0.0;
@@ -317,22 +319,26 @@ k_adj_face(const double* __restrict__ U, const double* __restrict__ grad, const 
     const int eS = dg_idx(fi.slave >> 3, E, kSiteAdjFace), fS = fi.slave & 7;
     int p2, q2;
     apply_flip<n>(fi.flip, p, q, p2, q2);
-    const int idM = face_node<n>(fM, p, q), idS = face_node<n>(fS, p2, q2);
+    int su, sg;
+    const double* uM = side_ptr<n, FACE, 5>(U, eM, fM, p, q, su);
+    const double* uS = side_ptr<n, FACE, 5>(U, eS, fS, p2, q2, su);
+    const double* gM = side_ptr<n, FACE, 12>(grad, eM, fM, p, q, sg);
+    const double* gS = side_ptr<n, FACE, 12>(grad, eS, fS, p2, q2, sg);
     double qL[5], qR[5], Fb[5];
     const double* s0 = b.fseed + ((size_t)f * 2 + 0) * 5 * NN + pq;
     const double* s1 = b.fseed + ((size_t)f * 2 + 1) * 5 * NN + pq;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      qL[c] = U[((size_t)eM * 5 + c) * P + idM];
-      qR[c] = U[((size_t)eS * 5 + c) * P + idS];
+      qL[c] = uM[c * su];
+      qR[c] = uS[c * su];
       Fb[c] = s0[c * NN] + s1[c * NN];
     }
     const double* fg = facegeo + (size_t)f * 4 * NN + pq;
     double gL[12], gR[12], gbL[12], gbR[12];
 #pragma unroll
     for (int r = 0; r < 12; ++r) {
-      gL[r] = grad[((size_t)eM * 12 + r) * P + idM];
-      gR[r] = grad[((size_t)eS * 12 + r) * P + idS];
+      gL[r] = gM[r * sg];
+      gR[r] = gS[r * sg];
       gbL[r] = 0.0;
       gbR[r] = 0.0;
     }
@@ -366,13 +372,14 @@ static size_t adj_mortar_face_smem() {
   return sizeof(double) * ((size_t)8 * NN + n + 17 * NN + 34 * NN + 5 * NN + 10 * NN + 68 * NN + 68 * NN);
 }
 
-template <int N>
+// FACE: Gauss nodes, U and grad the face values [E][6][5|12][NN].
+template <int N, bool FACE = false>
 __global__ void __launch_bounds__(MortarShape<N>::THREADS)
 k_adj_mortar_face(const double* __restrict__ U, const double* __restrict__ grad, const double* __restrict__ facegeo,
                   const int* __restrict__ mortars, const double* __restrict__ tab, int E, Gas g, AdjBufs b,
                   int mu_offset) {
   using S = MortarShape<N>;
-  constexpr int n = S::n, P = S::P, NN = S::NN, T = S::THREADS;
+  constexpr int n = S::n, NN = S::NN, T = S::THREADS;
   extern __shared__ double am[];
   double* sI = am;                  // [2][n][n] I_h[x][j]
   double* sIT = sI + 2 * NN;        // [2][j][x]
@@ -394,11 +401,14 @@ k_adj_mortar_face(const double* __restrict__ U, const double* __restrict__ grad,
     sWT[h * NN + j * n + a] = tab[2 * NN + a] * tab[x];
   }
   if (t < NN) {
-    const int i = t % n, j = t / n, node = face_node<n>(fB, i, j);
+    const int i = t % n, j = t / n;
+    int su, sg;
+    const double* qb = side_ptr<n, FACE, 5>(U, eB, fB, i, j, su);
+    const double* gb = side_ptr<n, FACE, 12>(grad, eB, fB, i, j, sg);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sB[v * NN + t] = U[((size_t)eB * 5 + v) * P + node];
+    for (int v = 0; v < 5; ++v) sB[v * NN + t] = qb[v * su];
 #pragma unroll
-    for (int x = 0; x < 12; ++x) sB[(5 + x) * NN + t] = grad[((size_t)eB * 12 + x) * P + node];
+    for (int x = 0; x < 12; ++x) sB[(5 + x) * NN + t] = gb[x * sg];
     const double iww = 1.0 / (tab[2 * NN + i] * tab[2 * NN + j]);
 #pragma unroll
     for (int v = 0; v < 5; ++v) sY[v * NN + t] = b.fseed[((size_t)slotB * 2 * 5 + v) * NN + t] * iww;
@@ -415,15 +425,18 @@ k_adj_mortar_face(const double* __restrict__ U, const double* __restrict__ grad,
   const int slot = dg_idx(r[6 + 4 * k], b.F, kSiteMortar);
   int p2, q2;
   apply_flip<n>(fl, pp, qq, p2, q2);
-  const int node = face_node<n>(fs, p2, q2), o = p2 + n * q2;
+  const int o = p2 + n * q2;
+  int su, sg;
+  const double* qs = side_ptr<n, FACE, 5>(U, es, fs, p2, q2, su);
+  const double* gs = side_ptr<n, FACE, 12>(grad, es, fs, p2, q2, sg);
   double qL[5], gL[12], Fb[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    qL[v] = U[((size_t)es * 5 + v) * P + node];
+    qL[v] = qs[v * su];
     Fb[v] = b.fseed[((size_t)slot * 2 * 5 + v) * NN + o] - z[v];
   }
 #pragma unroll
-  for (int x = 0; x < 12; ++x) gL[x] = grad[((size_t)es * 12 + x) * P + node];
+  for (int x = 0; x < 12; ++x) gL[x] = gs[x * sg];
   const double* fg = facegeo + (size_t)slot * 4 * NN + o;
   double qbL[5] = {0, 0, 0, 0, 0}, qbR[5] = {0, 0, 0, 0, 0}, gbL[12], gbR[12];
 #pragma unroll
@@ -465,10 +478,12 @@ k_adj_mortar_face(const double* __restrict__ U, const double* __restrict__ grad,
 // derivative w.r.t. phi at each side's points, beside the own -Y/2:
 //   small side k: + (P^T Y_B)_k / 2,
 //   big side    : - Y_B / 2 + sum_k I_k^T ((P^T Y_B)_k + Y_k) / 2.
-template <int N>
+// FACE: Gauss nodes, where Y is the weak lifting's surface sum S of the face
+// point (lgf, own point order) and the own term is +Y/2 (no -phi term).
+template <int N, bool FACE = false>
 __global__ void __launch_bounds__(MortarShape<N>::THREADS)
 k_adj_mortar_lift(const double* __restrict__ metrics, const int* __restrict__ mortars, const double* __restrict__ tab,
-                  int E, double inv_w0, AdjBufs b) {
+                  int E, double inv_w0, AdjBufs b, const double* __restrict__ lgf) {
   using S = MortarShape<N>;
   constexpr int n = S::n, P = S::P, NN = S::NN, T = S::THREADS;
   __shared__ double sI[2 * NN], sIT[2 * NN], sW[2 * NN], sWT[2 * NN], sw[n];
@@ -484,6 +499,12 @@ k_adj_mortar_lift(const double* __restrict__ metrics, const int* __restrict__ mo
   }
   // Y at a face point of (e, f): inv_w0 (2s-1) sum_l gtil_{phi,l} Ja^d_l
   auto Yat = [&](int e, int f, int p, int q, double y[4]) {
+    if constexpr (FACE) {
+      const double* sf = lgf + ((size_t)e * 6 + f) * 9 * NN + p + n * q;
+#pragma unroll
+      for (int ph = 0; ph < 4; ++ph) y[ph] = sf[ph * NN];
+      return;
+    }
     const int node = face_node<n>(f, p, q), d = f >> 1;
     const double sg = (f & 1) ? inv_w0 : -inv_w0;
     const double* mt = metrics + (size_t)e * 10 * P + node;
@@ -672,6 +693,302 @@ k_adj_lift(const double* __restrict__ U, const double* __restrict__ metrics, con
   for (int c = 0; c < 5; ++c) out[((size_t)e * 5 + c) * P + id] = qb[c];
 }
 
+// ---------------------------------------------------------------------------
+// Legendre-Gauss nodes (the weak form of Eqs. 2 and 3, kernels of dg_gauss.cu).
+// Forward, at node i with index r along direction d (face point pq of its line):
+//   R_i = (1/J_i) [ sum_d sum_m Dw[r][m] Ft^d_m - sum_{d,s} l_s(r)/w_r Fout_{2d+s}(pq) ] + Q,
+//   Ft^d = (f - f_v)(q, g) . Ja^d, Fout the outward surface flux (master F*,
+//   slave -F* at the mapped point), Dw[r][m] = (w_m / w_r) D_{m r};
+//   J g_i = - sum_d sum_m Dw[r][m] (phi Ja^d)_m + sum_{d,s} l_s(r)/w_r phi*_{2d+s}(pq) n sJ,
+//   phi* = (phi(Uf own) + phi(Uf nbr)) / 2 at the face points;
+//   Uf_f(pq) = sum_m l_s(m) U(line m), gf likewise from g.
+// Five kernels: B1 volume and surface seeds, A2 (FACE) the face VJP on the
+// face values, B3 the gradients' adjoint per node and the lifting's surface
+// sums per face point, B4 the face values' adjoint, B5 the lifting's volume
+// transpose and the transposed prolongation.  lamV = lambda / J.
+// Per element face, lgf [E][6][9][NN]: the surface sums S (4) and the adjoint
+// of the face values Uf (5), own point order.
+
+// B1: Ft-bar^d_m = sum_r Dw[r][m] lamV_r along the line through m, then the
+// Euler and viscous flux VJPs (qbar, gbar, d/dmu); the surface seeds
+// Fout-bar_f(pq) = - sum_r l_s(r)/w_r lamV_r, stored as the adjoint of F*
+// (master: as is; slave: negated, at the master's point).
+template <int N>
+__global__ void __launch_bounds__(Shape<N>::THREADS)
+k_adjlg_volume(const double* __restrict__ U, const double* __restrict__ lam, const double* __restrict__ metrics,
+               const double* __restrict__ grad, const int* __restrict__ elem_face, const double* __restrict__ tab,
+               int E, Gas g, AdjBufs b) {
+  using S = Shape<N>;
+  constexpr int n = S::n, P = S::P, NN = S::NN;
+  extern __shared__ double adjlg_smem[];
+  __shared__ double sDw[n * n], sT[2 * n];
+  __shared__ double smu[S::THREADS];
+  const int le = threadIdx.x / P, id = threadIdx.x - le * P;
+  const int e = blockIdx.x * S::EPB + le;
+  const bool active = e < E;
+  double* sL = adjlg_smem + (size_t)le * 5 * P;   // lamV [5][P]
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) sDw[t] = tab[GaussTab::Dw(n) + t];
+  for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) sT[t] = tab[GaussTab::lmw(n) + t];
+  if (active) {
+    const double iJ = metrics[((size_t)e * 10 + 9) * P + id];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) sL[c * P + id] = lam[((size_t)e * 5 + c) * P + id] * iJ;
+  }
+  __syncthreads();
+  double mub = 0.0;
+  if (active) {
+    const int i = id % n, j = (id / n) % n, k = id / NN;
+    const int ijk[3] = {i, j, k};
+    double q[5], gr[12], Ja[9];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) q[c] = U[((size_t)e * 5 + c) * P + id];
+#pragma unroll
+    for (int r = 0; r < 12; ++r) gr[r] = grad[((size_t)e * 12 + r) * P + id];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) Ja[r] = metrics[((size_t)e * 10 + r) * P + id];
+    const double ir = 1.0 / q[0];
+    const double u = q[1] * ir, v = q[2] * ir, w = q[3] * ir;
+    const double p = g.gm1 * (q[4] - 0.5 * (q[1] * u + q[2] * v + q[3] * w));
+    const double Tn = p * ir * g.inv_R;
+    double sv, dsv;
+    visc_factor_d(g, Tn, sv, dsv);
+    double qb[5] = {0, 0, 0, 0, 0}, gb[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, ub[3] = {0, 0, 0}, vr = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int r = ijk[d];
+      const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
+      const int line0 = id - r * stride;
+      double fb[5] = {0, 0, 0, 0, 0};
+      for (int r2 = 0; r2 < n; ++r2) {
+        const double c = sDw[r2 * n + r];
+        const int nid = line0 + r2 * stride;
+#pragma unroll
+        for (int x = 0; x < 5; ++x) fb[x] = fma(c, sL[x * P + nid], fb[x]);
+      }
+      euler_flux_vjp(q, u, v, w, p, Ja[d * 3], Ja[d * 3 + 1], Ja[d * 3 + 2], fb, g.gm1, qb);
+      const double fvb[4] = {-fb[1], -fb[2], -fb[3], -fb[4]};
+      vr += visc_flux_vjp(gr, u, v, w, g.mu * sv, g.kappa, Ja[d * 3], Ja[d * 3 + 1], Ja[d * 3 + 2], fvb, gb, ub);
+    }
+    mub = sv * vr;
+    const double Tb = g.mu * dsv * vr;   // through T = p / (rho R)
+    prim_vjp(q, -Tb * Tn * ir, ub, Tb * g.inv_R * ir, g.gm1, qb);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) b.qbar[((size_t)e * 5 + c) * P + id] = qb[c];
+#pragma unroll
+    for (int r = 0; r < 12; ++r) b.gbar[((size_t)e * 12 + r) * P + id] = gb[r];
+    for (int o = id; o < 30 * NN; o += P) {
+      const int f = o / (5 * NN), rr = o - f * 5 * NN, x = rr / NN, pq = rr - x * NN;
+      const int pp = pq % n, qq = pq / n, d = f >> 1;
+      const double* lw = sT + (f & 1) * n;
+      double s = 0.0;
+      for (int r2 = 0; r2 < n; ++r2) s = fma(lw[r2], sL[x * P + line_node<n>(d, r2, pp, qq)], s);
+      const int code = elem_face[e * 6 + f];
+      const int fid = dg_idx(code >> 4, b.F, kSiteAdjFace);
+      if (code & 8) {
+        b.fseed[((size_t)fid * 2 * 5 + x) * NN + pq] = -s;
+      } else {
+        int p2, q2;
+        apply_flip<n>(code & 7, pp, qq, p2, q2);
+        b.fseed[(((size_t)fid * 2 + 1) * 5 + x) * NN + p2 + n * q2] = s;
+      }
+    }
+  }
+  smu[threadIdx.x] = mub;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int t = 0; t < S::THREADS; ++t) acc += smu[t];
+    b.mupart[blockIdx.x] = acc;
+  }
+}
+
+// B3: per node, the gradients' adjoint (the volume's, plus the transposed
+// prolongation of the face VJP's gf-adjoints, l_s(r) each), divided by J ->
+// gtil; then per face point of the element's faces the lifting's surface sum
+// S_f(pq) = sum_r l_s(r)/w_r (n sJ) . gtil(line r), per lifting variable.
+template <int N>
+__global__ void __launch_bounds__(Shape<N>::THREADS)
+k_adjlg_gather(const double* __restrict__ metrics, const double* __restrict__ facegeo,
+               const int* __restrict__ elem_face, const double* __restrict__ tab, int E, AdjBufs b,
+               double* __restrict__ lgf) {
+  using S = Shape<N>;
+  constexpr int n = S::n, P = S::P, NN = S::NN;
+  extern __shared__ double adjlg_smem[];
+  __shared__ double sT[4 * n];   // l(-1)/w, l(+1)/w, l(-1), l(+1)
+  const int le = threadIdx.x / P, id = threadIdx.x - le * P;
+  const int e = blockIdx.x * S::EPB + le;
+  const bool active = e < E;
+  double* sG = adjlg_smem + (size_t)le * 12 * P;   // gtil [12][P]
+  for (int t = threadIdx.x; t < 4 * n; t += blockDim.x) sT[t] = tab[GaussTab::lmw(n) + t];
+  __syncthreads();
+  if (active) {
+    const int i = id % n, j = (id / n) % n, k = id / NN;
+    const int ijk[3] = {i, j, k};
+    double gb[12];
+#pragma unroll
+    for (int r = 0; r < 12; ++r) gb[r] = b.gbar[((size_t)e * 12 + r) * P + id];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int pp = d == 0 ? j : i, qq = d == 2 ? j : k;
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int code = elem_face[e * 6 + 2 * d + s];
+        const int fid = dg_idx(code >> 4, b.F, kSiteAdjFace);
+        int pm = pp, qm = qq, side = 0;
+        if (!(code & 8)) { apply_flip<n>(code & 7, pp, qq, pm, qm); side = 1; }
+        const double c = sT[(2 + s) * n + ijk[d]];
+        const double* src = b.face + (((size_t)fid * 2 + side) * 17 + 5) * NN + pm + n * qm;
+#pragma unroll
+        for (int r = 0; r < 12; ++r) gb[r] = fma(c, src[r * NN], gb[r]);
+      }
+    }
+    const double iJ = metrics[((size_t)e * 10 + 9) * P + id];
+#pragma unroll
+    for (int r = 0; r < 12; ++r) {
+      const double gt = gb[r] * iJ;
+      b.gtil[((size_t)e * 12 + r) * P + id] = gt;
+      sG[r * P + id] = gt;
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  for (int o = id; o < 24 * NN; o += P) {
+    const int f = o / (4 * NN), rr = o - f * 4 * NN, ph = rr / NN, pq = rr - ph * NN;
+    const int pp = pq % n, qq = pq / n, d = f >> 1;
+    const int code = elem_face[e * 6 + f];
+    const int fid = dg_idx(code >> 4, b.F, kSiteAdjFace);
+    const bool master = code & 8;
+    int p2 = pp, q2 = qq;
+    if (!master) apply_flip<n>(code & 7, pp, qq, p2, q2);
+    const double* fg = facegeo + (size_t)fid * 4 * NN + p2 + n * q2;
+    const double sJ = master ? fg[3 * NN] : -fg[3 * NN];
+    const double n0 = sJ * fg[0], n1 = sJ * fg[NN], n2 = sJ * fg[2 * NN];
+    const double* lw = sT + (f & 1) * n;
+    double s = 0.0;
+    for (int r2 = 0; r2 < n; ++r2) {
+      const int node = line_node<n>(d, r2, pp, qq);
+      s = fma(lw[r2], n0 * sG[(ph * 3) * P + node] + n1 * sG[(ph * 3 + 1) * P + node] + n2 * sG[(ph * 3 + 2) * P + node], s);
+    }
+    lgf[(((size_t)e * 6 + f) * 9 + ph) * NN + pq] = s;
+  }
+}
+
+// B4: per element face point, the adjoint of the face values Uf: the face
+// VJP's share plus that of the face average phi* in the own and the
+// neighbour's lifting, (S_own + S_nbr)/2, through the lifting variables.
+// A mortar side (negative neighbour entry) takes, in place of the neighbour's
+// half, its term from b.mx (k_adj_mortar_lift in FACE mode).
+template <int N>
+__global__ void __launch_bounds__(128)
+k_adjlg_facephi(const double* __restrict__ Uf, const int* __restrict__ elem_face, const int* __restrict__ elem_nbr,
+                int E, Gas g, AdjBufs b, double* __restrict__ lgf, int n_mortar) {
+  constexpr int n = N + 1, NN = n * n;
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long)E * 6 * NN) return;
+  const int ef = (int)(gid / NN), pq = (int)(gid % NN);
+  const int e = ef / 6, f = ef - 6 * e, pp = pq % n, qq = pq / n;
+  const int code = elem_face[e * 6 + f], nb = elem_nbr[e * 6 + f];
+  const int fid = dg_idx(code >> 4, b.F, kSiteAdjFace);
+  int p2, q2;
+  apply_flip<n>(code & 7, pp, qq, p2, q2);
+  const double* So = lgf + (size_t)ef * 9 * NN + pq;
+  double phb[4];
+  if (nb < 0) {
+    const double* xm = b.mx + (size_t)dg_idx(-1 - nb, 5L * n_mortar, kSiteMortar) * 4 * NN + pq;
+#pragma unroll
+    for (int ph = 0; ph < 4; ++ph) phb[ph] = 0.5 * So[ph * NN] + xm[ph * NN];
+  } else {
+    const int e2 = dg_idx(nb >> 3, E, kSiteAdjFace), f2 = nb & 7;
+    const double* Sn = lgf + ((size_t)e2 * 6 + f2) * 9 * NN + p2 + n * q2;
+#pragma unroll
+    for (int ph = 0; ph < 4; ++ph) phb[ph] = 0.5 * (So[ph * NN] + Sn[ph * NN]);
+  }
+  const bool master = code & 8;
+  const double* fa = b.face + ((size_t)fid * 2 + (master ? 0 : 1)) * 17 * NN + (master ? pq : p2 + n * q2);
+  double q[5], qb[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    q[v] = Uf[(size_t)ef * 5 * NN + (size_t)v * NN + pq];
+    qb[v] = fa[v * NN];
+  }
+  const double ir = 1.0 / q[0];
+  const double u = q[1] * ir, v = q[2] * ir, w = q[3] * ir;
+  const double T = g.gm1 * (q[4] - 0.5 * (q[1] * u + q[2] * v + q[3] * w)) * ir * g.inv_R;
+  const double ub[3] = {phb[0], phb[1], phb[2]};
+  prim_vjp(q, -phb[3] * T * ir, ub, phb[3] * ir * g.inv_R, g.gm1, qb);
+  double* out = lgf + ((size_t)ef * 9 + 4) * NN + pq;
+#pragma unroll
+  for (int x = 0; x < 5; ++x) out[x * NN] = qb[x];
+}
+
+// B5: per node, the lifting's volume transpose
+//   phi-bar_a(m) = - sum_d sum_l Ja^d_l(m) sum_r Dw[r][m] gtil_{a,l}(line r),
+// through the lifting variables to the state, plus the transposed
+// prolongation of the face values' adjoint (l_s(r) each) and the volume's qbar.
+template <int N>
+__global__ void __launch_bounds__(Shape<N>::THREADS)
+k_adjlg_lift(const double* __restrict__ U, const double* __restrict__ metrics, const double* __restrict__ tab,
+             int E, Gas g, AdjBufs b, const double* __restrict__ lgf, double* __restrict__ out) {
+  using S = Shape<N>;
+  constexpr int n = S::n, P = S::P, NN = S::NN;
+  extern __shared__ double adjlg_smem[];
+  __shared__ double sDw[n * n], sL[2 * n];   // weak D; l(-1), l(+1)
+  const int le = threadIdx.x / P, id = threadIdx.x - le * P;
+  const int e = blockIdx.x * S::EPB + le;
+  const bool active = e < E;
+  double* sG = adjlg_smem + (size_t)le * 12 * P;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) sDw[t] = tab[GaussTab::Dw(n) + t];
+  for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) sL[t] = tab[GaussTab::lm(n) + t];
+  if (active)
+#pragma unroll
+    for (int r = 0; r < 12; ++r) sG[r * P + id] = b.gtil[((size_t)e * 12 + r) * P + id];
+  __syncthreads();
+  if (!active) return;
+  const int i = id % n, j = (id / n) % n, k = id / NN;
+  const int ijk[3] = {i, j, k};
+  double Ja[9];
+#pragma unroll
+  for (int r = 0; r < 9; ++r) Ja[r] = metrics[((size_t)e * 10 + r) * P + id];
+  double phib[4] = {0, 0, 0, 0};
+  double qb[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) qb[c] = b.qbar[((size_t)e * 5 + c) * P + id];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int r = ijk[d];
+    const int stride = d == 0 ? 1 : (d == 1 ? n : NN);
+    const int line0 = id - r * stride;
+    double W[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int r2 = 0; r2 < n; ++r2) {
+      const double c = sDw[r2 * n + r];
+      const int nid = line0 + r2 * stride;
+#pragma unroll
+      for (int x = 0; x < 12; ++x) W[x] = fma(c, sG[x * P + nid], W[x]);
+    }
+#pragma unroll
+    for (int ph = 0; ph < 4; ++ph)
+      phib[ph] -= Ja[d * 3] * W[ph * 3] + Ja[d * 3 + 1] * W[ph * 3 + 1] + Ja[d * 3 + 2] * W[ph * 3 + 2];
+    const int pq = d == 0 ? j + n * k : (d == 1 ? i + n * k : i + n * j);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const double c = sL[s * n + r];
+      const double* src = lgf + (((size_t)e * 6 + 2 * d + s) * 9 + 4) * NN + pq;
+#pragma unroll
+      for (int x = 0; x < 5; ++x) qb[x] = fma(c, src[x * NN], qb[x]);
+    }
+  }
+  double q[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) q[c] = U[((size_t)e * 5 + c) * P + id];
+  const double ir = 1.0 / q[0];
+  const double u = q[1] * ir, v = q[2] * ir, w = q[3] * ir;
+  const double T = g.gm1 * (q[4] - 0.5 * (q[1] * u + q[2] * v + q[3] * w)) * ir * g.inv_R;
+  const double ub[3] = {phib[0], phib[1], phib[2]};
+  prim_vjp(q, -phib[3] * T * ir, ub, phib[3] * ir * g.inv_R, g.gm1, qb);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) out[((size_t)e * 5 + c) * P + id] = qb[c];
+}
+
 // d/dmu: fold the block partials in a fixed order and add to *acc.
 __global__ void k_adj_mu_fold(const double* __restrict__ part, int n, double scale, double* __restrict__ acc) {
   __shared__ double sh[256];
@@ -717,6 +1034,19 @@ static cudaError_t adj_setup_N() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_adj_mortar_face<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)adj_mortar_face_smem<N>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_mortar_face<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)adj_mortar_face_smem<N>());
+  using S = Shape<N>;
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adjlg_volume<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * S::EPB * 5 * S::P));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adjlg_gather<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * S::EPB * 12 * S::P));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adjlg_lift<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * S::EPB * 12 * S::P));
   return e;
 }
 
@@ -768,7 +1098,7 @@ static cudaError_t vjp_N(const Ctx& c, const double* U, const double* lam, doubl
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (c.M > 0) {
     k_adj_mortar_lift<N><<<c.M, MortarShape<N>::THREADS, 0, s>>>(c.d_metrics, c.d_mortars, c.d_mortar_tab, c.E,
-                                                                 inv_w0, b);
+                                                                 inv_w0, b, nullptr);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     k_adj_lift<N, true><<<blocks, S::THREADS, adj_lift_smem<N>(), s>>>(U, c.d_metrics, c.d_elem_nbr, c.d_elem_face,
                                                                        c.d_D, c.E, c.gas, inv_w0, b, out, c.M);
@@ -784,6 +1114,49 @@ static cudaError_t vjp_N(const Ctx& c, const double* U, const double* lam, doubl
   return err;
 }
 
+// Gauss nodes (conforming meshes): B1, A2 on the face values, B3, B4, B5.
+template <int N>
+static cudaError_t vjp_lg_N(const Ctx& c, const double* U, const double* lam, double* out, const AdjBufs& b,
+                            double* dJdmu, double mu_scale, cudaStream_t s) {
+  using S = Shape<N>;
+  constexpr int NN = (N + 1) * (N + 1);
+  const int blocks = (c.E + S::EPB - 1) / S::EPB;
+  const size_t sm5 = sizeof(double) * S::EPB * 5 * S::P, sm12 = sizeof(double) * S::EPB * 12 * S::P;
+  k_adjlg_volume<N><<<blocks, S::THREADS, sm5, s>>>(U, lam, c.d_metrics, (const double*)c.d_grad, c.d_elem_face,
+                                                    c.d_lgb, c.E, c.gas, b);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const int fblocks = (int)(((long)c.nfaces_conf * NN + 127) / 128);
+  if (fblocks > 0)
+    k_adj_face<N, true><<<fblocks, 128, 0, s>>>(c.d_Uf, (const double*)c.d_gf, c.d_faces, c.d_facegeo,
+                                                c.nfaces_conf, c.E, c.gas, b, blocks);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (c.M > 0) {
+    k_adj_mortar_face<N, true><<<c.M, MortarShape<N>::THREADS, adj_mortar_face_smem<N>(), s>>>(
+        c.d_Uf, (const double*)c.d_gf, c.d_facegeo, c.d_mortars, c.d_mortar_tab, c.E, c.gas, b, blocks + fblocks);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  k_adjlg_gather<N><<<blocks, S::THREADS, sm12, s>>>(c.d_metrics, c.d_facegeo, c.d_elem_face, c.d_lgb, c.E, b,
+                                                     c.d_adj_lgf);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (c.M > 0) {
+    k_adj_mortar_lift<N, true><<<c.M, MortarShape<N>::THREADS, 0, s>>>(c.d_metrics, c.d_mortars, c.d_mortar_tab,
+                                                                       c.E, 0.0, b, c.d_adj_lgf);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  const long fp = (long)c.E * 6 * NN;
+  k_adjlg_facephi<N><<<(int)((fp + 127) / 128), 128, 0, s>>>(c.d_Uf, c.d_elem_face, c.d_elem_nbr, c.E, c.gas, b,
+                                                             c.d_adj_lgf, c.M);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  k_adjlg_lift<N><<<blocks, S::THREADS, sm12, s>>>(U, c.d_metrics, c.d_lgb, c.E, c.gas, b, c.d_adj_lgf, out);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (dJdmu) {
+    k_adj_mu_fold<<<1, 256, 0, s>>>(b.mupart, blocks + fblocks + c.M, mu_scale, dJdmu);
+    err = cudaGetLastError();
+  }
+  return err;
+}
+
 cudaError_t launch_vjp(const Ctx& c, const double* U, const double* lam, double* out, double* dJdmu,
                        double mu_scale, cudaStream_t s) {
   // forward recomputation of the FP64 lifted gradients at U
@@ -791,6 +1164,20 @@ cudaError_t launch_vjp(const Ctx& c, const double* U, const double* lam, double*
   if (err != cudaSuccess) return err;
   AdjBufs b{c.d_adj_qbar, c.d_adj_gbar, c.d_adj_fseed, c.d_adj_face, c.d_adj_gtil, c.d_adj_mu, 0, c.d_adj_mx,
             c.nfaces};
+  if (c.prm.nodes == DG_NODES_LG) {
+    switch (c.N) {
+      case 1: return vjp_lg_N<1>(c, U, lam, out, b, dJdmu, mu_scale, s);
+      case 2: return vjp_lg_N<2>(c, U, lam, out, b, dJdmu, mu_scale, s);
+      case 3: return vjp_lg_N<3>(c, U, lam, out, b, dJdmu, mu_scale, s);
+      case 4: return vjp_lg_N<4>(c, U, lam, out, b, dJdmu, mu_scale, s);
+      case 5: return vjp_lg_N<5>(c, U, lam, out, b, dJdmu, mu_scale, s);
+      case 6: return vjp_lg_N<6>(c, U, lam, out, b, dJdmu, mu_scale, s);
+      case 7: return vjp_lg_N<7>(c, U, lam, out, b, dJdmu, mu_scale, s);
+      case 8: return vjp_lg_N<8>(c, U, lam, out, b, dJdmu, mu_scale, s);
+      case 9: return vjp_lg_N<9>(c, U, lam, out, b, dJdmu, mu_scale, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (c.N) {
     case 1: return vjp_N<1>(c, U, lam, out, b, dJdmu, mu_scale, s);
     case 2: return vjp_N<2>(c, U, lam, out, b, dJdmu, mu_scale, s);

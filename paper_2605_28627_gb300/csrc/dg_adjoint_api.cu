@@ -36,8 +36,6 @@ static dg_status ensure_adjoint(Ctx* c) {
     return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the DG operator (no FV sub-cell elements)");
   if (c->d_adj_qbar) return DG_OK;
   if (c->prm.precision != DG_FP64) return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the FP64 operator");
-  if (c->prm.nodes != DG_NODES_LGL)
-    return afail(c, DG_EUNSUPPORTED, "the adjoint is built for the LGL operator");
   const size_t st = (size_t)c->E * 5 * c->P;
   const size_t nn = (size_t)c->nfaces * c->NN;
   ADJ_CUDA(setup_adjoint(c->N), c, "adjoint kernel set-up");
@@ -52,6 +50,8 @@ static dg_status ensure_adjoint(Ctx* c) {
   ADJ_CUDA(cudaMalloc(&c->d_adj_work, sizeof(double) * st * 4), c, "adjoint work");
   if (c->M > 0)
     ADJ_CUDA(cudaMalloc(&c->d_adj_mx, sizeof(double) * (size_t)c->M * 5 * 4 * c->NN), c, "adjoint mortar buffer");
+  if (c->prm.nodes == DG_NODES_LG)
+    ADJ_CUDA(cudaMalloc(&c->d_adj_lgf, sizeof(double) * (size_t)c->E * 6 * 9 * c->NN), c, "adjoint face buffer");
   return DG_OK;
 }
 

@@ -124,7 +124,7 @@ static void release(Ctx* c) {
   void* bufs[] = {c->d_modal, c->d_D, c->d_metrics, c->d_J, c->d_X, c->d_mms, c->d_Uf, c->d_gf, c->d_lgb, c->d_facegeo, c->d_metrics_f, c->d_facegeo_f,
                   c->d_grad, c->d_fstar, c->d_red, c->d_w, c->d_clock, c->d_U, c->d_G,
                   c->d_adj_qbar, c->d_adj_gbar, c->d_adj_gtil, c->d_adj_fseed, c->d_adj_face, c->d_adj_mu,
-                  c->d_adj_stage, c->d_adj_work, c->d_adj_mx, c->d_fv_tab, c->d_fv_iJb, c->d_fv_S, c->d_fv_M, c->d_fv_Fb};
+                  c->d_adj_stage, c->d_adj_work, c->d_adj_mx, c->d_adj_lgf, c->d_fv_tab, c->d_fv_iJb, c->d_fv_S, c->d_fv_M, c->d_fv_Fb};
   for (void* p : bufs) if (p) cudaFree(p);
   if (c->d_faces) cudaFree(c->d_faces);
   if (c->d_elem_face) cudaFree(c->d_elem_face);

@@ -13,24 +13,11 @@
 // Gauss points of each face.  Both sides of a face see the same face values of
 // the polynomial, and its discrete metric identities keep a uniform flow
 // uniform.  FP64 only.
-#include "dg_stage.cuh"
+#include "dg_gauss.cuh"
 
 #include <cmath>
 
 namespace dg {
-
-// Device table of the Gauss basis (doubles), n = N + 1.
-struct GaussTab {
-  // [r][m] = (w_m / w_r) D_{m r}, D_{m r} = l_r'(x_m): the weak derivative
-  __host__ __device__ static constexpr int Dw(int) { return 0; }
-  __host__ __device__ static constexpr int lmw(int n) { return n * n; }           // l_i(-1) / w_i
-  __host__ __device__ static constexpr int lpw(int n) { return n * n + n; }       // l_i(+1) / w_i
-  __host__ __device__ static constexpr int lm(int n) { return n * n + 2 * n; }    // l_i(-1)
-  __host__ __device__ static constexpr int lp(int n) { return n * n + 3 * n; }    // l_i(+1)
-  __host__ __device__ static constexpr int V(int n) { return n * n + 4 * n; }     // [i][j]: LGL l_j at Gauss x_i
-  __host__ __device__ static constexpr int w(int n) { return 2 * n * n + 4 * n; } // Gauss weights
-  __host__ __device__ static constexpr int size(int n) { return 2 * n * n + 5 * n; }
-};
 
 // P_n(x) and P_n'(x) for |x| < 1 by the three-term recurrence.
 static void legendre_pn(int n, double x, double& p, double& dp) {
@@ -171,13 +158,6 @@ double gauss_dt_factor(int N, const std::vector<double>& xl, const std::vector<d
     for (int m = 0; m < n; ++m) DG[(size_t)m * n + r] = tab[GaussTab::Dw(n) + r * n + m] * wG[r] / wG[m];
   (void)xl;
   return dg1d_spectral_radius(n, wl, Dl, lmL, lpL) / dg1d_spectral_radius(n, wG, DG, lmG, lpG);
-}
-
-// Volume node with index i along direction d and face-local indices (p, q)
-// along the two other directions in increasing order (the face_node order).
-template <int n>
-__device__ __forceinline__ int line_node(int d, int i, int p, int q) {
-  return d == 0 ? vidx<n>(i, p, q) : (d == 1 ? vidx<n>(p, i, q) : vidx<n>(p, q, i));
 }
 
 // ---------------------------------------------------------------------------

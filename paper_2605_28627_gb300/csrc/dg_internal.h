@@ -170,6 +170,7 @@ struct Ctx {
   double* d_adj_mu = nullptr;    // block partials of d/dmu
   double* d_adj_stage = nullptr; // [5][E][5][P] stage states of one step
   double* d_adj_mx = nullptr;    // [M][5][4][NN] mortar sides' lifting-transpose terms
+  double* d_adj_lgf = nullptr;   // [E][6][9][NN] Gauss nodes: lifting surface sums, face-value adjoints
   double* d_adj_work = nullptr;  // [4][E][5][P]: work state, G, G-bar, VJP scratch
   // host-buffer path
   double* d_U = nullptr;

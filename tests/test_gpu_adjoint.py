@@ -51,6 +51,75 @@ def test_vjp_dot_product_vs_oracle_tangent_linear(orc, dg, N, flux, law):
     assert abs(dmu.item() - ref_mu) <= 1e-11 * float(np.abs(v * Rmu).sum()), (dmu.item(), ref_mu)
 
 
+_GAUSS_STATE = dict(rho=(0.95, 1.05), vel=0.2, p=(0.95, 1.05))
+
+
+@pytest.mark.parametrize("N,flux,law", [(1, 0, 0), (2, 0, 0), (3, 0, 0), (3, 1, 0), (3, 2, 1), (4, 0, 1),
+                                        (5, 1, 1), (7, 0, 0), (9, 2, 0)])
+def test_vjp_gauss_nodes_vs_oracle_tangent_linear(orc, dg, N, flux, law):
+    """Legendre-Gauss nodes (the weak form of Eqs. 2 and 3): the transposes of
+    the face prolongation of the state and of the gradients, of the weak
+    lifting and of the weak volume and surface terms, in the dot-product test
+    against the oracle's tangent-linear of its Gauss-node operator."""
+    mesh = box_mesh(3 if N < 5 else 2, N, deform="sinprod", rotate_seed=950 + N)
+    kw = dict(mu=0.03, surf_flux=flux, visc_law=law, T_ref=1.0, S_suth=0.4)
+    o = orc.Oracle(mesh, N, nodes=1, **kw)
+    s = dg.Solver(mesh, N, nodes=dg.NODES_LG, **kw)
+    U = random_state(mesh.n_elems, N, seed=960 + N, **_GAUSS_STATE)
+    rng = np.random.default_rng(970 + N)
+    w = rng.normal(size=U.shape)
+    v = rng.normal(size=U.shape)
+    _, Jw = o.time_derivative_tl(U, w, 0.0)
+    _, Rmu = o.time_derivative_tl(U, np.zeros_like(U), 1.0)
+    dmu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    JTv = s.time_derivative_vjp(_cuda(U), _cuda(v), dJdmu=dmu).cpu().numpy()
+    lhs, rhs = float((JTv * w).sum()), float((v * Jw).sum())
+    scale = float(np.abs(JTv * w).sum())
+    assert abs(lhs - rhs) <= 1e-11 * scale, (lhs, rhs)
+    ref_mu = float((v * Rmu).sum())
+    assert abs(dmu.item() - ref_mu) <= 1e-11 * float(np.abs(v * Rmu).sum()), (dmu.item(), ref_mu)
+
+
+def test_vjp_gauss_nodes_per_element(orc, dg):
+    """Element by element on a small curved mesh: (dR/dU)^T v against the
+    oracle's tangent-linear with directions supported on one element each
+    (a dot product over the whole mesh could hide errors that cancel)."""
+    N = 3
+    mesh = box_mesh(2, N, deform="sinprod", rotate_seed=980)
+    o = orc.Oracle(mesh, N, nodes=1, mu=0.03)
+    s = dg.Solver(mesh, N, nodes=dg.NODES_LG, mu=0.03)
+    U = random_state(mesh.n_elems, N, seed=981, **_GAUSS_STATE)
+    rng = np.random.default_rng(982)
+    v = rng.normal(size=U.shape)
+    JTv = s.time_derivative_vjp(_cuda(U), _cuda(v)).cpu().numpy()
+    for e in range(mesh.n_elems):
+        w = np.zeros(U.shape)
+        w[e] = rng.normal(size=U.shape[1:])
+        _, Jw = o.time_derivative_tl(U, w, 0.0)
+        lhs, rhs = float((JTv * w).sum()), float((v * Jw).sum())
+        assert abs(lhs - rhs) <= 1e-11 * float(np.abs(JTv * w).sum()), (e, lhs, rhs)
+
+
+def test_solve_adjoint_gauss_nodes_vs_oracle(orc, dg):
+    """Adjoint of LSERK4-5 steps on Gauss nodes against the oracle's
+    tangent-linear of the same steps, with d/dmu."""
+    N = 3
+    mesh = box_mesh(2, N, deform="sinprod", rotate_seed=990)
+    o = orc.Oracle(mesh, N, nodes=1, mu=0.02)
+    s = dg.Solver(mesh, N, nodes=dg.NODES_LG, mu=0.02)
+    U0 = random_state(mesh.n_elems, N, seed=991, **_GAUSS_STATE)
+    dt, nsteps = 2e-3, 4
+    rng = np.random.default_rng(992)
+    w = rng.normal(size=U0.shape)
+    lam = rng.normal(size=U0.shape)
+    _, dUT = o.rk_steps_tl(U0, w, 0.3, 0.0, dt, nsteps)
+    dmu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lam0, _ = s.adjoint_solve(_cuda(U0), _cuda(lam), 0.0, dt, nsteps, max_snapshots=2, dJdmu=dmu)
+    lhs = float((lam0.cpu().numpy() * w).sum()) + 0.3 * dmu.item()
+    rhs = float((lam * dUT).sum())
+    assert abs(lhs - rhs) <= 1e-10 * abs(rhs), (lhs, rhs)
+
+
 def _mortar_mesh(N, seed):
     from workloads.mesh import refined_box_mesh
     K = 3 if N <= 7 else 2
@@ -59,17 +128,19 @@ def _mortar_mesh(N, seed):
     return refined_box_mesh(K, r, rotate_seed=seed)
 
 
-@pytest.mark.parametrize("N,flux,law", [(1, 0, 0), (2, 0, 0), (3, 1, 0), (3, 2, 1), (4, 0, 1), (5, 1, 0),
-                                        (7, 0, 0), (9, 2, 0)])
-def test_vjp_on_mortar_mesh_vs_oracle_tangent_linear(orc, dg, N, flux, law):
+@pytest.mark.parametrize("N,flux,law,nodes", [(1, 0, 0, 0), (2, 0, 0, 0), (3, 1, 0, 0), (3, 2, 1, 0), (4, 0, 1, 0),
+                                              (5, 1, 0, 0), (7, 0, 0, 0), (9, 2, 0, 0),
+                                              (1, 0, 0, 1), (2, 1, 1, 1), (3, 0, 0, 1), (5, 2, 0, 1), (8, 0, 1, 1)])
+def test_vjp_on_mortar_mesh_vs_oracle_tangent_linear(orc, dg, N, flux, law, nodes):
     """2:1 non-conforming meshes (Sec. 3.2.2, Algorithm 1): the transposes of
     the quadrant interpolation, of the flux projection and of the mortar
-    sides' lifting states, in the same dot-product test."""
+    sides' lifting states, in the same dot-product test; on Gauss nodes
+    (nodes 1) the maps act on the face values."""
     mesh = _mortar_mesh(N, 900 + N)
     kw = dict(mu=0.03, surf_flux=flux, visc_law=law, T_ref=1.0, S_suth=0.4)
-    o = orc.Oracle(mesh, N, **kw)
-    s = dg.Solver(mesh, N, **kw)
-    U = random_state(mesh.n_elems, N, seed=910 + N)
+    o = orc.Oracle(mesh, N, nodes=nodes, **kw)
+    s = dg.Solver(mesh, N, nodes=nodes, **kw)
+    U = random_state(mesh.n_elems, N, seed=910 + N, **(_GAUSS_STATE if nodes else {}))
     rng = np.random.default_rng(920 + N)
     w = rng.normal(size=U.shape)
     v = rng.normal(size=U.shape)

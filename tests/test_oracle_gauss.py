@@ -157,5 +157,31 @@ def test_gauss_taylor_green_closed_forms(orc):
     I = o.integrals(U)
     assert abs(I[5] - 0.125) < 1e-3
     assert abs(I[6] / (0.75 * prm["mu"]) - 1.0) < 0.05, I[6]
-    with pytest.raises(ValueError):
-        o.time_derivative_tl(U, U)
+
+
+@pytest.mark.parametrize("flux,law,mortar", [(0, 0, False), (1, 1, False), (2, 0, False), (0, 1, True)])
+def test_gauss_tangent_linear_matches_central_differences(orc, flux, law, mortar):
+    """The dual-number path runs the same Gauss-node code (prolongation, weak
+    lifting, face fluxes, weak volume integral, and the mortars): its
+    tangent-linear of R(U), and dR/dmu, match central differences."""
+    N = 3
+    if mortar:
+        from workloads.mesh import refined_box_mesh
+        r = np.zeros(8, dtype=bool)
+        r[0] = True
+        m = refined_box_mesh(2, r, rotate_seed=11)
+    else:
+        m = box_mesh(2, 2, deform="sinprod", rotate_seed=12)
+    kw = dict(surf_flux=flux, visc_law=law, T_ref=1.0, S_suth=0.4, nodes=1)
+    mu, h = 0.03, 1e-6
+    o = orc.Oracle(m, N, mu=mu, **kw)
+    U = random_state(m.n_elems, N, seed=13, rho=(0.95, 1.05), vel=0.2, p=(0.95, 1.05))
+    dU = np.random.default_rng(14).normal(size=U.shape)
+    R, dR = o.time_derivative_tl(U, dU)
+    assert np.array_equal(R, o.time_derivative(U))
+    fd = (o.time_derivative(U + h * dU) - o.time_derivative(U - h * dU)) / (2 * h)
+    assert np.abs(dR - fd).max() < 1e-8 * np.abs(fd).max()
+    _, Rmu = o.time_derivative_tl(U, np.zeros_like(U), 1.0)
+    fdmu = (orc.Oracle(m, N, mu=mu + h, **kw).time_derivative(U)
+            - orc.Oracle(m, N, mu=mu - h, **kw).time_derivative(U)) / (2 * h)
+    assert np.abs(Rmu - fdmu).max() < 1e-8 * np.abs(fdmu).max()
