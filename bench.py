@@ -681,6 +681,66 @@ def mortar_rate(dg, N, dev, prm, dg_rate, K=12, steps=5):
             "gauss_nodes": {"value": rate_lg, "pid_ns": 1e9 / rate_lg, "state_finite": finite_lg}}
 
 
+def run_adj_vjp(args, local):
+    """Cost of one VJP (dR/dU)^T lambda against one R(U) on the same state,
+    per node set and mesh: a periodic 16^3 box (Taylor-Green state, Ma 0.2)
+    and the 2:1 mortar mesh of the mortar leg (12^3 box, cells with three even
+    indices split, MMS state), LGL and Gauss nodes, FP64; CUDA events on one
+    stream, 20 calls each after 3 warm-up pairs."""
+    import numpy as np
+    import torch
+    import paper_2605_28627_gb300 as dg
+    from workloads import box_mesh, mms_params, tgv_params
+    from workloads.mesh import refined_box_mesh
+    torch.cuda.set_device(local)
+    K = 12
+    i = np.arange(K ** 3)
+    split = (i % 2 == 0) & ((i // K) % 2 == 0) & ((i // (K * K)) % 2 == 0)
+    st = torch.cuda.Stream(device="cuda:%d" % local)
+    out = []
+    for N in [int(x) for x in args.adj_vjp_orders.split(",")]:
+        for mesh_name in ("box16", "mortar12"):
+            for nodes in (dg.NODES_LGL, dg.NODES_LG):
+                if mesh_name == "box16":
+                    prm = tgv_params(Ma=0.2, Re=800.0)
+                    mesh = box_mesh(16, 1, lo=0.0, hi=2 * math.pi)
+                else:
+                    prm = mms_params()
+                    mesh = refined_box_mesh(K, split, rotate_seed=3)
+                s = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"], nodes=nodes,
+                              device=local)
+                with torch.cuda.stream(st):
+                    U = (s.initial_state("tgv", prm["p0"], stream=st) if mesh_name == "box16"
+                         else s.initial_state("mms", 0.0, stream=st))
+                    lam = torch.empty_like(U).normal_(generator=torch.Generator(device="cuda:%d" % local)
+                                                      .manual_seed(7))
+                    vj = torch.empty_like(U)
+                    Rt = torch.empty_like(U)
+                for _ in range(3):
+                    s.time_derivative_vjp(U, lam, out=vj, stream=st)
+                    s.time_derivative(U, Rt, stream=st)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                reps = 20
+                ev[0].record(st)
+                for _ in range(reps):
+                    s.time_derivative_vjp(U, lam, out=vj, stream=st)
+                ev[1].record(st)
+                for _ in range(reps):
+                    s.time_derivative(U, Rt, stream=st)
+                ev[2].record(st)
+                ev[2].synchronize()
+                ms_vjp = ev[0].elapsed_time(ev[1]) / reps
+                ms_r = ev[1].elapsed_time(ev[2]) / reps
+                dof = mesh.n_elems * (N + 1) ** 3
+                out.append({"N": N, "mesh": mesh_name, "nodes": "gauss" if nodes == dg.NODES_LG else "lgl",
+                            "elements": mesh.n_elems, "dof": dof, "ms_R": round(ms_r, 4), "ms_vjp": round(ms_vjp, 4),
+                            "vjp_over_R": round(ms_vjp / ms_r, 3), "ns_per_dof_vjp": round(ms_vjp * 1e6 / dof, 3),
+                            "finite": bool(torch.isfinite(vj).all().item())})
+                s.close()
+    print(json.dumps({"adjoint_vjp_cost": out}))
+    return 0
+
+
 def run_mortar(args, local):
     import torch
     import paper_2605_28627_gb300 as dg
@@ -971,6 +1031,8 @@ def main():
     ap.add_argument("--tgv-shock-t", type=float, default=20.0)
     ap.add_argument("--tgv-shock-thr", default="-3.0,-3.5", help="log10 switching thresholds: upper,lower")
     ap.add_argument("--tgv-shock-variants", default="", help="comma list of the study's variants ('' = all)")
+    ap.add_argument("--adj-vjp", action="store_true", help="time one VJP against one R(U) per node set and mesh")
+    ap.add_argument("--adj-vjp-orders", default="3,5", help="orders of the --adj-vjp study")
     ap.add_argument("--adj-steps", type=int, default=200)
     ap.add_argument("--adj-dirs", type=int, default=32)
     args = ap.parse_args()
@@ -984,6 +1046,8 @@ def main():
         return run_pid(args, local) if rank == 0 else 0
     if args.adjoint:
         return run_adjoint(args, local) if rank == 0 else 0
+    if args.adj_vjp:
+        return run_adj_vjp(args, local) if rank == 0 else 0
     if args.mortar:
         return run_mortar(args, local) if rank == 0 else 0
     if args.tgv_shock:
