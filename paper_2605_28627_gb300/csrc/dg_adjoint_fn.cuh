@@ -36,7 +36,9 @@ __device__ __forceinline__ double adj_rcp(double x) {
 }
 
 // Logarithmic mean and its partial derivatives, consistent with log_mean():
-// series branch L = s / (2 F(u)), u = ((a-b)/s)^2, F = 1 + u/3 + u^2/5 + u^3/7;
+// series branch L = s G(u), G = 1/F2, F2 = 2 (1 + u/3 + u^2/5 + u^3/7),
+// u = f^2, f = (a-b)/s; with du/da = 4 f b / s^2 and du/db = -4 f a / s^2,
+// dL/da = G + c b and dL/db = G - c a, c = 4 G'(u) f / s = -4 F2'(u) G^2 f / s;
 // logarithmic branch L = (a - b) / ln(a/b) with dL/da = (1 - L/a)/ln(a/b),
 // dL/db = (L/b - 1)/ln(a/b).
 __device__ __forceinline__ double log_mean_d(double a, double b, double& La, double& Lb) {
@@ -45,15 +47,13 @@ __device__ __forceinline__ double log_mean_d(double a, double b, double& La, dou
   const double f = (a - b) * is;
   const double u = f * f;
   if (u < 1e-4) {
-    const double F = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
-    const double Fp = 1.0 / 3.0 + u * (2.0 / 5.0 + u * (3.0 / 7.0));
-    const double i2F = adj_rcp(2.0 * F);            // 1/(2F)
-    const double L = s * i2F;
-    const double dLdu = -2.0 * s * Fp * i2F * i2F;   // -s F' / (2 F^2)
-    const double is2 = is * is;
-    La = i2F + dLdu * 2.0 * f * (2.0 * b * is2);
-    Lb = i2F + dLdu * 2.0 * f * (-2.0 * a * is2);
-    return L;
+    const double F2 = fma(u, fma(u, fma(u, 2.0 / 7.0, 2.0 / 5.0), 2.0 / 3.0), 2.0);
+    const double F2p_m4 = fma(u, fma(u, -24.0 / 7.0, -16.0 / 5.0), -8.0 / 3.0);   // -4 F2'(u)
+    const double G = adj_rcp(F2);
+    const double c = F2p_m4 * (G * G) * (f * is);
+    La = fma(c, b, G);
+    Lb = fma(-c, a, G);
+    return s * G;
   }
   const double z = a / b;
   const double F = log(z) / (2.0 * ((z - 1.0) / (z + 1.0)));
