@@ -37,8 +37,9 @@ struct AdjBufs {
 };
 
 // ---------------------------------------------------------------------------
-// Words per node of the volume adjoint's element tile: primitives, 1/p and
-// |u|^2 (8), metric terms (9), lamV (5), the partner's adjoint (5).
+// Words per node of the volume adjoint's element tile: rho, u, v, w, beta,
+// beta/p, 1/(2p) and |u|^2 (8), metric terms (9), lamV (5), the partner's
+// adjoint (5).
 constexpr int kAdjVolWords = 27;
 
 // A1: volume adjoint.  lamV = -lambda / J.  Two blocks per SM where a block
@@ -59,7 +60,7 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
   __shared__ double smu[S::THREADS];
   const int le = threadIdx.x / P, id = threadIdx.x - le * P;
   double* eb = base + (size_t)le * kAdjVolWords * P;
-  // rho, u, v, w, p, beta, 1/p, |u|^2
+  // rho, u, v, w, beta/p, beta, 1/(2p), |u|^2 (the flux VJP reads no p)
   auto sPr = [&](int c, int node) -> double& { return eb[c * P + node]; };
   auto sJa = [&](int c, int node) -> double& { return eb[(8 + c) * P + node]; };    // [9]
   auto sL = [&](int c, int node) -> double& { return eb[(17 + c) * P + node]; };    // lamV [5]
@@ -72,7 +73,7 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
   }
   double q[5] = {1, 0, 0, 0, 1}, Ja[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, iJ = 0.0, lv[5] = {0, 0, 0, 0, 0};
   NodePrim<double> me{1, 0, 0, 0, 1, 0.5};
-  double ip_me = 1.0, k_me = 0.0;
+  double hip_me = 0.5, bip_me = 0.5, k_me = 0.0;
   if (active) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) q[c] = U[((size_t)e * 5 + c) * P + id];
@@ -87,10 +88,12 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
     me.p = g.gm1 * (q[4] - 0.5 * (q[1] * me.u + q[2] * me.v + q[3] * me.w));
     me.beta = 0.5 * q[0] / me.p;
     sPr(0, id) = me.rho; sPr(1, id) = me.u; sPr(2, id) = me.v; sPr(3, id) = me.w;
-    sPr(4, id) = me.p; sPr(5, id) = me.beta;
-    ip_me = adj_rcp(me.p);
+    const double ip = adj_rcp(me.p);
+    hip_me = 0.5 * ip;
+    bip_me = me.beta * ip;
+    sPr(4, id) = bip_me; sPr(5, id) = me.beta;
     k_me = me.u * me.u + me.v * me.v + me.w * me.w;
-    sPr(6, id) = ip_me; sPr(7, id) = k_me;
+    sPr(6, id) = hip_me; sPr(7, id) = k_me;
   }
   __syncthreads();
   const int i = id % n, j = (id / n) % n, k = id / NN;
@@ -115,7 +118,8 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
         double wb[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) wb[c] = fma(Drm2, lv[c], Dmr2 * sL(c, mid));
-        ec_flux_vjp(me, ot, nx, ny, nz, g.inv_gm1, wb, pr, pm, ip_me, sPr(6, mid), k_me, sPr(7, mid));
+        ec_flux_vjp(me, ot, nx, ny, nz, g.inv_gm1, wb, pr, pm, hip_me, sPr(6, mid), bip_me, sPr(4, mid), k_me,
+                    sPr(7, mid));
 #pragma unroll
         for (int c = 0; c < 5; ++c) sX(c, mid) = pm[c];
       }
@@ -150,8 +154,8 @@ k_adj_volume(const double* __restrict__ U, const double* __restrict__ lam, const
         double wb[5], pa[5] = {0, 0, 0, 0, 0}, pb[5] = {0, 0, 0, 0, 0};
 #pragma unroll
         for (int c = 0; c < 5; ++c) wb[c] = fma(Drm2, l2[c * P + ia], Dmr2 * l2[c * P + ib]);
-        ec_flux_vjp(A, B, nx, ny, nz, g.inv_gm1, wb, pa, pb, e2[6 * P + ia], e2[6 * P + ib], e2[7 * P + ia],
-                    e2[7 * P + ib]);
+        ec_flux_vjp(A, B, nx, ny, nz, g.inv_gm1, wb, pa, pb, e2[6 * P + ia], e2[6 * P + ib], e2[4 * P + ia],
+                    e2[4 * P + ib], e2[7 * P + ia], e2[7 * P + ib]);
         double* x2 = e2 + 22 * P;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {

@@ -66,11 +66,13 @@ __device__ __forceinline__ double log_mean_d(double a, double b, double& La, dou
 
 // Adjoint of the Chandrashekar two-point flux f(a, b; n) (ec_flux): given
 // fb = df-bar (5), adds to the primitive adjoints (rho, u, v, w, p) of a and b.
-// ipA, ipB are 1/p and kA, kB are |u|^2 of the two states (per node, so the
-// volume kernel computes them once per node, not once per pair).
+// hipA, hipB are 1/(2p), bipA, bipB are beta/p and kA, kB are |u|^2 of the two
+// states (per node, so the volume kernel computes them once per node, not once
+// per pair; the p members of A and B are not read).
 __device__ __forceinline__ void ec_flux_vjp(const NodePrim<double>& A, const NodePrim<double>& B, double nx,
                                             double ny, double nz, double inv_gm1, const double fb[5], double pa[5],
-                                            double pbv[5], double ipA, double ipB, double kA, double kB) {
+                                            double pbv[5], double hipA, double hipB, double bipA, double bipB,
+                                            double kA, double kB) {
   double Lra, Lrb, Lba, Lbb;
   const double rho_ln = log_mean_d(A.rho, B.rho, Lra, Lrb);
   const double beta_ln = log_mean_d(A.beta, B.beta, Lba, Lbb);
@@ -105,9 +107,9 @@ __device__ __forceinline__ void ec_flux_vjp(const NodePrim<double>& A, const Nod
   const double sbb = -phb * p_hat * isb;
   double rab = srb + rlb * Lra, rbb = srb + rlb * Lrb;
   const double bab = sbb + blb * Lba, bbb = sbb + blb * Lbb;
-  // beta = rho / (2 p)
-  rab += bab * 0.5 * ipA;  pa[4] += -bab * A.beta * ipA;
-  rbb += bbb * 0.5 * ipB;  pbv[4] += -bbb * B.beta * ipB;
+  // beta = rho / (2 p): d beta / d rho = 1/(2p), d beta / d p = -beta/p
+  rab = fma(bab, hipA, rab);  pa[4] = fma(-bab, bipA, pa[4]);
+  rbb = fma(bbb, hipB, rbb);  pbv[4] = fma(-bbb, bipB, pbv[4]);
   pa[0] += rab;
   pbv[0] += rbb;
 }
@@ -115,8 +117,9 @@ __device__ __forceinline__ void ec_flux_vjp(const NodePrim<double>& A, const Nod
 __device__ __forceinline__ void ec_flux_vjp(const NodePrim<double>& A, const NodePrim<double>& B, double nx,
                                             double ny, double nz, double inv_gm1, const double fb[5], double pa[5],
                                             double pbv[5]) {
-  ec_flux_vjp(A, B, nx, ny, nz, inv_gm1, fb, pa, pbv, adj_rcp(A.p), adj_rcp(B.p), A.u * A.u + A.v * A.v + A.w * A.w,
-              B.u * B.u + B.v * B.v + B.w * B.w);
+  const double ipA = adj_rcp(A.p), ipB = adj_rcp(B.p);
+  ec_flux_vjp(A, B, nx, ny, nz, inv_gm1, fb, pa, pbv, 0.5 * ipA, 0.5 * ipB, A.beta * ipA, B.beta * ipB,
+              A.u * A.u + A.v * A.v + A.w * A.w, B.u * B.u + B.v * B.v + B.w * B.w);
 }
 
 // Adjoint of the Euler flux f(q) . n (q conserved, n any vector): adds to qb.
