@@ -185,3 +185,24 @@ def test_gauss_tangent_linear_matches_central_differences(orc, flux, law, mortar
     fdmu = (orc.Oracle(m, N, mu=mu + h, **kw).time_derivative(U)
             - orc.Oracle(m, N, mu=mu - h, **kw).time_derivative(U)) / (2 * h)
     assert np.abs(Rmu - fdmu).max() < 1e-8 * np.abs(fdmu).max()
+
+
+def test_gauss_rk_tangent_linear_matches_central_differences(orc):
+    """The step tangent-linear on Gauss nodes (the dual numbers through the
+    LSERK4-5 stages of the Gauss-node operator) against central differences
+    of the steps, for a direction in U and in mu together.  Entropy-
+    conservative faces: the LLF speed max(lambda_L, lambda_R) has a kink
+    where the two sides' speeds are equal, and over fifteen stages some face
+    point of a random state comes within the differences' step of one."""
+    N = 2
+    m = box_mesh(2, 2, deform="sinprod", rotate_seed=15)
+    mu, h, dt, nsteps, dmu = 0.02, 1e-6, 2e-3, 3, 0.3
+    kw = dict(nodes=1, surf_flux=1)
+    U = random_state(m.n_elems, N, seed=16, rho=(0.95, 1.05), vel=0.2, p=(0.95, 1.05))
+    dU = np.random.default_rng(17).normal(size=U.shape)
+    UT, dUT = orc.Oracle(m, N, mu=mu, **kw).rk_steps_tl(U, dU, dmu, 0.0, dt, nsteps)
+    assert np.array_equal(UT, orc.Oracle(m, N, mu=mu, **kw).rk_steps(U, 0.0, dt, nsteps))
+    fp = orc.Oracle(m, N, mu=mu + h * dmu, **kw).rk_steps(U + h * dU, 0.0, dt, nsteps)
+    fm = orc.Oracle(m, N, mu=mu - h * dmu, **kw).rk_steps(U - h * dU, 0.0, dt, nsteps)
+    fd = (fp - fm) / (2 * h)
+    assert np.abs(dUT - fd).max() < 1e-7 * np.abs(fd).max()
