@@ -221,9 +221,13 @@ dg_status dg_indicator(dg_ctx* ctx, const double* dU, int32_t var, double log10_
  * on Gauss nodes its values interpolated to the face) and taking the sub-face
  * fluxes in nodal form, with the same face integral.  The first call allocates
  * about 18 + 12 (N+2)/(N+1) doubles per node plus 5 per face node and sets
- * up the sub-cell geometry.  FP64 operator (either node set) on a conforming
- * mesh: DG_EUNSUPPORTED otherwise; the adjoint entry points return DG_EUNSUPPORTED while a mask is
- * set.  dg_max_dt keeps the DG time-step restriction.  Does not synchronise. */
+ * up the sub-cell geometry.  FP64 operator (either node set): DG_EUNSUPPORTED
+ * otherwise.  On a mesh with mortars an element with a mortar face stays a DG
+ * element (the mortar maps act on DG traces): a mask that flags one gets
+ * DG_EUNSUPPORTED, and the call then synchronises the stream to check the
+ * mask on the host.  The adjoint entry points return DG_EUNSUPPORTED while a
+ * mask is set.  dg_max_dt keeps the DG time-step restriction.  Does not
+ * synchronise on conforming meshes. */
 dg_status dg_set_fv_mask(dg_ctx* ctx, const int32_t* dMask, dg_stream stream);
 
 /* Automatic switching of troubled cells between the DG and the FV sub-cell
@@ -235,13 +239,14 @@ dg_status dg_set_fv_mask(dg_ctx* ctx, const int32_t* dMask, dg_stream stream);
  * becomes an FV element where log10(eta_e) > log10_upper or where its nodal
  * state is not admissible (density or pressure not positive at a node), a DG
  * element where log10(eta_e) < log10_lower and every node is admissible, and
- * keeps its representation in between (hysteresis; FP64 decisions).  The
+ * keeps its representation in between (hysteresis; FP64 decisions); an
+ * element with a mortar face stays DG.  The
  * state stays nodal in both representations, so a switch moves no data.  The
  * mask starts from the one set by dg_set_fv_mask, else all DG; dg_set_fv_mask
  * (NULL) clears it while switching is on.  var < 0 turns switching off and
  * keeps the mask in effect.  DG_EINVAL for an unknown var or thresholds that
- * are not finite with upper >= lower; DG_EUNSUPPORTED where dg_set_fv_mask
- * would be.  Allocates as dg_set_fv_mask does.  Does not synchronise. */
+ * are not finite with upper >= lower; DG_EUNSUPPORTED with the FP32
+ * operator.  Allocates as dg_set_fv_mask does.  Does not synchronise. */
 dg_status dg_set_fv_switch(dg_ctx* ctx, int32_t var, double log10_upper, double log10_lower, dg_stream stream);
 
 /* The FV mask in effect (1: FV element), into dMask (device, n_elems int32);

@@ -1085,6 +1085,16 @@ template <class T>
 static void rhs_lg(const Ctx& c, const T* U, T* Ut, double t, T mu);
 static void state_persson(const Ctx& c, const double* U, int var, double* out);
 
+// Whether element e has a mortar face (a 2:1 face, Algorithm 1).  The mortar
+// maps act on DG traces, so such an element stays a DG element: the FV mask
+// may not flag it and the switching keeps it DG (a reading; the paper does
+// not treat FV sub-cells at mortars).
+static bool touches_mortar(const Ctx& c, int e) {
+  for (int f = 0; f < 6; ++f)
+    if (c.nbr[(e * 6 + f) * 3] < 0) return true;
+  return false;
+}
+
 // Automatic switching of troubled cells (Sec. 3.1: the modal indicator marks
 // the DG elements that the FV sub-cell operator takes over; Sec. 3.2.2 names
 // the switch as a step of its own): before R(U) is evaluated, element e
@@ -1109,6 +1119,7 @@ static void fv_switch(const Ctx& c, const double* U) {
       if (!(w.rho > 0.0 && w.p > 0.0)) admissible = false;
     }
     const double l = eta[e] > 0.0 ? std::log10(eta[e]) : -HUGE_VAL;
+    if (c.M > 0 && touches_mortar(c, e)) { c.fv_mask[e] = 0; continue; }
     c.sw_margin = std::min(c.sw_margin, std::min(std::fabs(l - c.sw_up), std::fabs(l - c.sw_low)));
     if (l > c.sw_up || !admissible) c.fv_mask[e] = 1;
     else if (l < c.sw_low) c.fv_mask[e] = 0;
@@ -1905,6 +1916,7 @@ static void fv_faces(const Ctx& c, FVData& fv, double* Fs) {
     for (int f = 0; f < 6; ++f) {
       if (!c.master[e * 6 + f]) continue;
       const int e2 = c.nbr[(e * 6 + f) * 3 + 0], f2 = c.nbr[(e * 6 + f) * 3 + 1], fl = c.nbr[(e * 6 + f) * 3 + 2];
+      if (e2 < 0) continue;   // a mortar side: DG on both sides (touches_mortar)
       const bool fvM = c.fv_mask[e] != 0, fvS = c.fv_mask[e2] != 0;
       if (!fvM && !fvS) continue;
       const int fid = c.face_id[e * 6 + f];
@@ -2212,23 +2224,23 @@ void orc_set_vol_flux(void* h, int kind) { ((Ctx*)h)->prm.vol_flux = kind; }
 
 // FV sub-cell elements: mask[e] != 0 switches element e to the FV sub-cell
 // operator (FP64, either node set); NULL restores the pure DG operator.
-// Returns 0, or -1 on a mesh with mortars.
+// Returns 0, or -1 if the mask flags an element with a mortar face.
 int orc_set_fv_mask(void* h, const int* mask) {
   Ctx* c = (Ctx*)h;
   if (!mask) { c->fv_mask.clear(); return 0; }
-  if (c->M > 0) return -1;   // the FV sub-cells are built for conforming meshes
+  for (int e = 0; e < c->E; ++e)
+    if (mask[e] && c->M > 0 && touches_mortar(*c, e)) return -1;
   c->fv_mask.assign(mask, mask + c->E);
   return 0;
 }
 
 // Automatic DG/FV switching (fv_switch) with the indicator of var (0: rho,
 // 1: p, 2: rho p) against log10 thresholds up >= low; var < 0 turns it off
-// (the mask stays as it is).  Returns 0, -1 on a mesh with mortars, -2 for
-// bad arguments.
+// (the mask stays as it is); elements with a mortar face stay DG.  Returns 0,
+// or -2 for bad arguments.
 int orc_set_fv_switch(void* h, int var, double log10_up, double log10_low) {
   Ctx* c = (Ctx*)h;
   if (var < 0) { c->sw_on = false; return 0; }
-  if (c->M > 0) return -1;
   if (var > 2 || !(log10_up >= log10_low)) return -2;
   c->sw_on = true;
   c->sw_var = var;

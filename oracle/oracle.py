@@ -288,7 +288,7 @@ class Oracle:
         if m.shape[0] != self.E:
             raise ValueError("oracle: the FV mask needs one entry per element")
         if self._L.orc_set_fv_mask(self._h, m.ctypes.data) != 0:
-            raise ValueError("oracle: the FV sub-cell operator is built for conforming meshes")
+            raise ValueError("oracle: an element with a mortar face stays a DG element")
         self.fv_mask = m
 
     def set_fv_switch(self, var, log10_upper=None, log10_lower=None):
@@ -303,8 +303,6 @@ class Oracle:
         if log10_lower is None:
             log10_lower = log10_upper
         r = self._L.orc_set_fv_switch(self._h, int(var), float(log10_upper), float(log10_lower))
-        if r == -1:
-            raise ValueError("oracle: the FV sub-cell operator is built for conforming meshes")
         if r != 0:
             raise ValueError("oracle: bad switching arguments")
 

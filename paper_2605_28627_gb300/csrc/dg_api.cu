@@ -124,7 +124,7 @@ static void release(Ctx* c) {
   void* bufs[] = {c->d_modal, c->d_D, c->d_metrics, c->d_J, c->d_X, c->d_mms, c->d_Uf, c->d_gf, c->d_lgb, c->d_facegeo, c->d_metrics_f, c->d_facegeo_f,
                   c->d_grad, c->d_fstar, c->d_red, c->d_w, c->d_clock, c->d_U, c->d_G,
                   c->d_adj_qbar, c->d_adj_gbar, c->d_adj_gtil, c->d_adj_fseed, c->d_adj_face, c->d_adj_mu,
-                  c->d_adj_stage, c->d_adj_work, c->d_adj_mx, c->d_adj_lgf, c->d_fv_tab, c->d_fv_iJb, c->d_fv_S, c->d_fv_M, c->d_fv_Fb};
+                  c->d_adj_stage, c->d_adj_work, c->d_adj_mx, c->d_adj_lgf, c->d_fv_pin, c->d_fv_tab, c->d_fv_iJb, c->d_fv_S, c->d_fv_M, c->d_fv_Fb};
   for (void* p : bufs) if (p) cudaFree(p);
   if (c->d_faces) cudaFree(c->d_faces);
   if (c->d_elem_face) cudaFree(c->d_elem_face);
@@ -612,6 +612,19 @@ static dg_status fv_alloc(dg_ctx* c, cudaStream_t s) {
   // the host table must outlive the copy
   DG_CUDA(cudaStreamSynchronize(s), c, "FV set-up");
   DG_CUDA(cudaMalloc(&c->d_fv_lists, sizeof(int) * (2 * E + 2)), c, "FV element lists");
+  if (c->M > 0) {   // the elements with a mortar face, which stay DG (the mortar maps act on DG traces)
+    std::vector<int> nbr(E * 6), pin(E, 0);
+    DG_CUDA(cudaMemcpyAsync(nbr.data(), c->d_elem_nbr, sizeof(int) * E * 6, cudaMemcpyDeviceToHost, s), c,
+            "neighbour table copy");
+    DG_CUDA(cudaStreamSynchronize(s), c, "FV set-up");
+    c->fv_pin.assign(E, 0);
+    for (size_t e = 0; e < E; ++e)
+      for (int f = 0; f < 6; ++f)
+        if (nbr[e * 6 + f] < 0) pin[e] = c->fv_pin[e] = 1;
+    DG_CUDA(cudaMalloc(&c->d_fv_pin, sizeof(int) * E), c, "FV pins");
+    DG_CUDA(cudaMemcpyAsync(c->d_fv_pin, pin.data(), sizeof(int) * E, cudaMemcpyHostToDevice, s), c, "pin copy");
+    DG_CUDA(cudaStreamSynchronize(s), c, "FV set-up");   // the host table must outlive the copy
+  }
   DG_CUDA(cudaMalloc(&c->d_fv_mask, sizeof(int) * E), c, "FV mask");
   return DG_OK;
 }
@@ -635,11 +648,17 @@ dg_status dg_set_fv_mask(dg_ctx* c, const int32_t* dMask, dg_stream stream) {
   const bool on = dMask != nullptr;
   if (on && c->prm.precision != DG_FP64)
     return fail(c, DG_EUNSUPPORTED, "dg_set_fv_mask: the FV sub-cell operator is built for the FP64 operator");
-  if (on && c->M > 0)
-    return fail(c, DG_EUNSUPPORTED, "dg_set_fv_mask: the FV sub-cell operator is built for conforming meshes");
   if (on) {
     const dg_status st = fv_alloc(c, s);
     if (st != DG_OK) return st;
+    if (c->M > 0) {   // no element with a mortar face may be an FV element
+      std::vector<int32_t> h(c->E);
+      DG_CUDA(cudaMemcpyAsync(h.data(), dMask, sizeof(int32_t) * c->E, cudaMemcpyDeviceToHost, s), c, "mask copy");
+      DG_CUDA(cudaStreamSynchronize(s), c, "mask check");
+      for (int e = 0; e < c->E; ++e)
+        if (h[e] && c->fv_pin[e])
+          return fail(c, DG_EUNSUPPORTED, "dg_set_fv_mask: an element with a mortar face stays a DG element");
+    }
     DG_CUDA(cudaMemcpyAsync(c->d_fv_mask, dMask, sizeof(int) * c->E, cudaMemcpyDeviceToDevice, s), c,
             "FV mask copy");
     DG_CUDA(launch_fv_lists(*c, s), c, "FV element lists kernel");
@@ -666,8 +685,6 @@ dg_status dg_set_fv_switch(dg_ctx* c, int32_t var, double log10_upper, double lo
     return fail(c, DG_EINVAL, "dg_set_fv_switch: thresholds must be finite with upper >= lower");
   if (c->prm.precision != DG_FP64)
     return fail(c, DG_EUNSUPPORTED, "dg_set_fv_switch: the FV sub-cell operator is built for the FP64 operator");
-  if (c->M > 0)
-    return fail(c, DG_EUNSUPPORTED, "dg_set_fv_switch: the FV sub-cell operator is built for conforming meshes");
   const bool fresh = !c->d_fv_mask;
   const dg_status st = fv_alloc(c, s);
   if (st != DG_OK) return st;

@@ -256,7 +256,10 @@ k_fv_means(const double* __restrict__ U, const double* __restrict__ grad, const 
   __shared__ int s_fv;
   const int e = blockIdx.x, id = threadIdx.x;
   int mine = 0;
-  if (id < 6) mine = mask[dg_idx(elem_nbr[e * 6 + id] >> 3, E, kSiteFvNbr)];
+  if (id < 6) {   // a mortar neighbour (negative entry) is a DG side
+    const int nb = elem_nbr[e * 6 + id];
+    mine = nb < 0 ? 0 : mask[dg_idx(nb >> 3, E, kSiteFvNbr)];
+  }
   else if (id == 6) {
     mine = mask[e];
     s_fv = mine;
@@ -739,10 +742,12 @@ static cudaError_t fv_stage_N(const Ctx& c, const StageArgs& a, cudaStream_t s) 
                                       c.d_fv_tab, c.d_fv_M, c.E, c.gas);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_fv_face<N><<<(c.nfaces + F::FPB - 1) / F::FPB, F::FACE_THREADS, 0, s>>>(
-      c.d_faces, c.d_fv_mask, a.U, (const double*)c.d_grad, c.prm.nodes == DG_NODES_LG ? c.d_Uf : nullptr,
-      c.prm.nodes == DG_NODES_LG ? c.d_gf : nullptr, c.d_fv_M, c.d_fv_S, c.d_fv_tab, c.d_fv_Fb, (double*)c.d_fstar,
-      c.nfaces, c.E, c.gas);
+  // the conforming faces: an FV element has no mortar face
+  if (c.nfaces_conf > 0)
+    k_fv_face<N><<<(c.nfaces_conf + F::FPB - 1) / F::FPB, F::FACE_THREADS, 0, s>>>(
+        c.d_faces, c.d_fv_mask, a.U, (const double*)c.d_grad, c.prm.nodes == DG_NODES_LG ? c.d_Uf : nullptr,
+        c.prm.nodes == DG_NODES_LG ? c.d_gf : nullptr, c.d_fv_M, c.d_fv_S, c.d_fv_tab, c.d_fv_Fb,
+        (double*)c.d_fstar, c.nfaces_conf, c.E, c.gas);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   StageArgs b = a;
   b.list = c.d_fv_lists;

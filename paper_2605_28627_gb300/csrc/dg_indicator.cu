@@ -54,7 +54,8 @@ void modal_table(int N, const std::vector<double>& x, const std::vector<double>&
 template <int N>
 __global__ void __launch_bounds__(Shape<N>::THREADS)
 k_indicator(const double* __restrict__ U, const double* __restrict__ T, int E, Gas g, int var, double log_thresh,
-            double* __restrict__ eta, int* __restrict__ flag, bool switch_mask, double log_low) {
+            double* __restrict__ eta, int* __restrict__ flag, bool switch_mask, double log_low,
+            const int* __restrict__ pin) {
   using S = Shape<N>;
   constexpr int n = S::n, P = S::P, EPB = S::EPB;
   __shared__ double sT[n * n];
@@ -117,7 +118,8 @@ k_indicator(const double* __restrict__ U, const double* __restrict__ T, int E, G
     if (eta) eta[e] = r;
     const double l = r > 0.0 ? log10(r) : -HUGE_VAL;
     if (switch_mask) {
-      if (l > log_thresh || s_bad[le]) flag[e] = 1;
+      if (pin && pin[e]) flag[e] = 0;   // an element with a mortar face stays DG
+      else if (l > log_thresh || s_bad[le]) flag[e] = 1;
       else if (l < log_low) flag[e] = 0;
     } else if (flag) {
       flag[e] = l > log_thresh ? 1 : 0;
@@ -131,7 +133,7 @@ static cudaError_t indicator_N(const Ctx& c, const double* U, const double* T, i
   using S = Shape<N>;
   const int blocks = (c.E + S::EPB - 1) / S::EPB;
   k_indicator<N><<<blocks, S::THREADS, 0, s>>>(U, T, c.E, c.gas, var, log_thresh, eta, flag, switch_mask,
-                                                log_low);
+                                                log_low, switch_mask ? c.d_fv_pin : nullptr);
   return cudaGetLastError();
 }
 

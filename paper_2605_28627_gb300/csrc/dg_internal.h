@@ -151,6 +151,8 @@ struct Ctx {
   int fv_sw_var = 2;             // its quantity (DG_IND_*) and log10 thresholds
   double fv_sw_up = 0.0, fv_sw_low = 0.0;
   int* d_fv_mask = nullptr;      // [E] 1: FV element
+  int* d_fv_pin = nullptr;       // [E] 1: element with a mortar face, which stays DG (mortar meshes only)
+  std::vector<char> fv_pin;      // the same on the host
   int* d_fv_lists = nullptr;     // [2E + 2]: DG elements, FV elements (ascending), their counts
   double* d_fv_tab = nullptr;    // V [n][n], V^-1 [n][n], L [n+1][n]
   double* d_fv_iJb = nullptr;     // [E][P] 1 / (sub-cell means of J)

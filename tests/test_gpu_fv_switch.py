@@ -126,8 +126,7 @@ def test_switching_rejections(dg):
         dg.Solver(m, 2, precision=dg.FP32OP).set_fv_switch(dg.IND_RHOP, -2.0, -3.0)
     r = np.zeros(8, dtype=bool)
     r[0] = True
-    with pytest.raises(dg.DGError):
-        dg.Solver(refined_box_mesh(2, r), 2).set_fv_switch(dg.IND_RHOP, -2.0, -3.0)
+    dg.Solver(refined_box_mesh(2, r), 2).set_fv_switch(dg.IND_RHOP, -2.0, -3.0)   # allowed on mortar meshes
     s.set_fv_switch(dg.IND_RHOP, -2.0, -3.0)
     U = _cuda(random_state(m.n_elems, 2, seed=1))
     with pytest.raises(dg.DGError):
