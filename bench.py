@@ -741,6 +741,57 @@ def run_adj_vjp(args, local):
     return 0
 
 
+def run_mortar_fv(args, local):
+    """FV sub-cell elements on the 2:1 mortar mesh of the mortar leg (12^3 box,
+    cells with three even indices split): every other element without a
+    mortar face is an FV element (the elements with one stay DG); MMS
+    LSERK4-5 steps as one graph launch after 3 warm-up steps, CUDA events,
+    against the same steps all DG.  FP64, LGL and Gauss nodes."""
+    import numpy as np
+    import torch
+    import paper_2605_28627_gb300 as dg
+    from workloads import mms_params
+    from workloads.mesh import refined_box_mesh
+    torch.cuda.set_device(local)
+    prm = mms_params()
+    K = 12
+    i = np.arange(K ** 3)
+    mesh = refined_box_mesh(K, (i % 2 == 0) & ((i // K) % 2 == 0) & ((i // (K * K)) % 2 == 0), rotate_seed=3)
+    touching = (mesh.face_nbr[:, :, 0] < 0).any(axis=1)
+    mask = np.zeros(mesh.n_elems, dtype=np.int32)
+    mask[np.where(~touching)[0][::2]] = 1
+    st = torch.cuda.Stream(device="cuda:%d" % local)
+    out = []
+    for N in [int(x) for x in args.mortar_fv_orders.split(",")]:
+        for nodes in (dg.NODES_LGL, dg.NODES_LG):
+            row = {"N": N, "nodes": "gauss" if nodes == dg.NODES_LG else "lgl", "elements": mesh.n_elems,
+                   "fv_elements": int(mask.sum()), "elements_with_mortar_faces": int(touching.sum())}
+            for label, use in (("all_dg", False), ("fv", True)):
+                s = dg.Solver(mesh, N, gamma=prm["gamma"], R=prm["R"], Pr=prm["Pr"], mu=prm["mu"],
+                              source=dg.SOURCE_MMS, nodes=nodes, device=local)
+                if use:
+                    s.set_fv_mask(mask, stream=st)
+                with torch.cuda.stream(st):
+                    U = s.initial_state("mms", 0.0, stream=st)
+                    G = torch.empty_like(U)
+                dt = min(DT, s.max_dt(U, cfl=0.9, dfl=0.9, stream=st))
+                s.rk_step(U, G, 0.0, dt, 3, stream=st)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                s.rk_step(U, G, 3 * dt, dt, args.steps, stream=st)
+                e1.record(st)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                dof = mesh.n_elems * (N + 1) ** 3
+                row[label + "_pid_ns"] = round(ms * 1e6 / (dof * 5 * args.steps), 3)
+                row[label + "_finite"] = bool(torch.isfinite(U).all().item())
+                s.close()
+            row["fv_over_all_dg"] = round(row["fv_pid_ns"] / row["all_dg_pid_ns"], 3)
+            out.append(row)
+    print(json.dumps({"mortar_fv": out}))
+    return 0
+
+
 def run_mortar(args, local):
     import torch
     import paper_2605_28627_gb300 as dg
@@ -1026,6 +1077,8 @@ def main():
                     help="skip the 48^3 Taylor-Green and ensemble legs of the default line")
     ap.add_argument("--tgv-leg-steps", type=int, default=6, help="steps of the 48^3 leg of the default line")
     ap.add_argument("--mortar", action="store_true", help="run the 2:1 non-conforming mesh leg alone")
+    ap.add_argument("--mortar-fv", action="store_true", help="FV elements on the 2:1 mortar mesh against all DG")
+    ap.add_argument("--mortar-fv-orders", default="3,7", help="orders of the --mortar-fv study")
     ap.add_argument("--tgv-shock", action="store_true",
                     help="run the Ma 1.25 Taylor-Green study with automatic DG/FV switching")
     ap.add_argument("--tgv-shock-t", type=float, default=20.0)
@@ -1050,6 +1103,8 @@ def main():
         return run_adj_vjp(args, local) if rank == 0 else 0
     if args.mortar:
         return run_mortar(args, local) if rank == 0 else 0
+    if args.mortar_fv:
+        return run_mortar_fv(args, local) if rank == 0 else 0
     if args.tgv_shock:
         return run_tgv_shock(args, local) if rank == 0 else 0
     if args.impl == "reference":
