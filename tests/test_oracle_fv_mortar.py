@@ -95,13 +95,14 @@ def test_conservation_with_fv_elements_on_a_mortar_mesh(orc, flux, nodes):
     assert (np.abs(tot) < 1e-13 * scale).all(), (tot, scale)
 
 
-def test_switching_keeps_elements_with_mortar_faces_dg(orc):
+@pytest.mark.parametrize("nodes", [0, 1])
+def test_switching_keeps_elements_with_mortar_faces_dg(orc, nodes):
     """A density and pressure jump across the mesh: the switching flags
     elements away from the mortars, never one with a mortar face, and the
     totals stay conserved through the steps."""
     m = _mesh(seed=8)
     N = 3
-    o = orc.Oracle(m, N, mu=1e-3)
+    o = orc.Oracle(m, N, mu=1e-3, nodes=nodes)
     X = o.node_coords()
     sel = X[:, 0] < X[:, 0].mean()
     U = np.zeros((m.n_elems, 5, X.shape[-1]))
@@ -110,7 +111,7 @@ def test_switching_keeps_elements_with_mortar_faces_dg(orc):
     U = U.reshape(o.shape)
     o.set_fv_switch(2, -2.0, -3.0)
     J = o.geometry()[2]
-    wq = _weights(orc, N, 0)
+    wq = _weights(orc, N, nodes)
     tot0 = np.einsum("evp,ep->v", U.reshape(m.n_elems, 5, -1), J * wq)
     seen = np.zeros(m.n_elems, dtype=bool)
     for k in range(4):
