@@ -592,7 +592,7 @@ dg_status dg_indicator(dg_ctx* c, const double* dU, int32_t var, double log10_th
 }  // extern "C"
 
 // The FV sub-cell buffers and tables, set up once per context.
-static dg_status fv_alloc(dg_ctx* c, cudaStream_t s) {
+static dg_status fv_alloc_impl(dg_ctx* c, cudaStream_t s) {
   if (c->d_fv_mask) return DG_OK;
   const size_t E = c->E, P = c->P, NN = c->NN, n = c->n;
   std::vector<double> tab, nodes = c->x;   // the context's node set: LGL, or Gauss below
@@ -629,6 +629,17 @@ static dg_status fv_alloc(dg_ctx* c, cudaStream_t s) {
   return DG_OK;
 }
 
+// fv_alloc_impl with host-memory exhaustion turned into DG_ENOMEM (no C++
+// exception leaves the C entry points); buffers already made stay with the
+// context and are freed with it.
+static dg_status fv_alloc(dg_ctx* c, cudaStream_t s) {
+  try {
+    return fv_alloc_impl(c, s);
+  } catch (const std::bad_alloc&) {
+    return fail(c, DG_ENOMEM, "FV set-up: host memory exhausted");
+  }
+}
+
 // Whether the stages run the FV kernels; a captured RK graph has the other
 // launch sequence after a change.
 static void set_fv_on(dg_ctx* c, bool on) {
@@ -652,7 +663,12 @@ dg_status dg_set_fv_mask(dg_ctx* c, const int32_t* dMask, dg_stream stream) {
     const dg_status st = fv_alloc(c, s);
     if (st != DG_OK) return st;
     if (c->M > 0) {   // no element with a mortar face may be an FV element
-      std::vector<int32_t> h(c->E);
+      std::vector<int32_t> h;
+      try {
+        h.resize(c->E);
+      } catch (const std::bad_alloc&) {
+        return fail(c, DG_ENOMEM, "dg_set_fv_mask: host memory exhausted");
+      }
       DG_CUDA(cudaMemcpyAsync(h.data(), dMask, sizeof(int32_t) * c->E, cudaMemcpyDeviceToHost, s), c, "mask copy");
       DG_CUDA(cudaStreamSynchronize(s), c, "mask check");
       for (int e = 0; e < c->E; ++e)
